@@ -1,0 +1,177 @@
+/*
+ * qldpc.h -- C ABI of the GB300 (sm_103a) syndrome decoder for CSS quantum LDPC codes.
+ *
+ * The library runs normalized min-sum belief propagation driven by a syndrome (Algorithm 1,
+ * "MSA for syndrome-based LDPC decoding", Sec. 2 of arXiv 2508.07879) on one GPU.  Given the
+ * Tanner graph of a parity-check matrix H (M checks, N variables) and a batch of syndromes
+ * s = H e^T over GF(2), it returns for every shot the estimate e_hat, the number of iterations run
+ * and whether H e_hat^T = s holds.  For a CSS code, s_X = H_Z e_X^T is decoded with H_Z and
+ * s_Z = H_X e_Z^T with H_X (Sec. 2); qldpc_decode_pair does both in one launch, as the paper's
+ * decoder does (Fig. 2 caption).
+ *
+ * Arithmetic (identical, operation by operation, to the CPU oracle of the test suite):
+ *   q_{m,n}^(0) = gamma_n                                        (Alg. 1 initialization)
+ *   r_{m,n} = (-1)^{s_m} prod_{j in S_v(m)\n} sign(q_{m,j}) * (alpha * min_{j in S_v(m)\n} |q_{m,j}|)
+ *   q_{m,n} = gamma_n + sum_{i in S_c(n)\m} r_{i,n}   (sum in ascending check order)
+ *   Q_n     = gamma_n + sum_{i in S_c(n)} r_{i,n};    e_hat_n = [Q_n < 0]
+ *   sign(x) = -1 iff x < 0.  The stop test H e_hat^T = s runs before the first iteration and
+ *   after every iteration; decoding stops at the first success or after max_iter iterations.
+ *
+ * Precisions:
+ *   QLDPC_FP32  IEEE binary32 messages, every add and multiply rounded to nearest (no fusion).
+ *   QLDPC_INT16 16-bit fixed point with 8 fractional bits (the paper's integer proposal, Table 1):
+ *               gamma_q = clamp(round_half_away(gamma*256), +-32767); alpha_q = round(alpha*2^15);
+ *               |r| = floor(min*alpha_q/2^15); q = clamp(32-bit sum, +-32767); Q in 32 bits.
+ *               Requires 0 < alpha <= 1.
+ *
+ * Memory and ownership: graph arrays live on the device and are owned by the qldpc_graph.
+ * Every buffer passed to qldpc_decode* is caller-owned DEVICE memory (e.g. torch tensors) unless
+ * the function name says "host".  Row-major layouts: syndromes[b*m + i], out_err[b*n + j].
+ * Decodes are asynchronous on the given stream and allocate nothing; qldpc_decode_host is
+ * synchronous and uses device staging owned by the graph (grown on demand, or reserved ahead with
+ * qldpc_graph_reserve).  A graph must be used on the device that was current when it was created.
+ *
+ * Errors: every function returns a qldpc_status.  Arguments are validated on the host before any
+ * GPU work is enqueued; a rejected call enqueues nothing and writes no output.  A CUDA launch
+ * failure returns QLDPC_ERR_CUDA; faults during execution surface at the caller's next
+ * synchronization.  A non-finite prior LLR is detected on the device: every shot of that call
+ * returns iters = -1, ok = 0 and e_hat = 0.
+ */
+#ifndef QLDPC_H
+#define QLDPC_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define QLDPC_API __attribute__((visibility("default")))
+#else
+#define QLDPC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qldpc_graph qldpc_graph;   /* opaque; owned by the library */
+
+typedef enum qldpc_status {
+    QLDPC_OK = 0,
+    QLDPC_ERR_INVALID_ARG = -1,   /* bad pointer, size, CSR structure, alpha, flag or precision */
+    QLDPC_ERR_UNSUPPORTED = -2,   /* graph exceeds a kernel limit (degree, shared memory, size) */
+    QLDPC_ERR_OOM = -3,           /* device or pinned host allocation failed */
+    QLDPC_ERR_CUDA = -4,          /* CUDA runtime error (no device, launch failure, copy failure) */
+    QLDPC_ERR_TIMEOUT = -5        /* a bounded device-side wait expired */
+} qldpc_status;
+
+enum { QLDPC_FP32 = 0, QLDPC_INT16 = 1 };
+
+/* Decode flags (bitwise OR). */
+enum {
+    QLDPC_NO_EARLY_STOP = 1u      /* run exactly max_iter iterations (the paper's timed mode, Sec. 3);
+                                     ok still reports H e_hat^T = s after the last one */
+};
+
+/* Limits of the kernels in this build. */
+enum {
+    QLDPC_MAX_ROW_DEGREE = 32,    /* check-node degree d_c */
+    QLDPC_MAX_COL_DEGREE = 16     /* variable-node degree d_v */
+};
+
+/*
+ * Build a Tanner graph from H in CSR form (Sec. 2: S_v(m) = columns of row m).
+ *   row_ptr  host int32[m+1], row_ptr[0] = 0, non-decreasing
+ *   col_idx  host int32[row_ptr[m]], each in [0, n), no repeats within a row (any order)
+ *   m, n     number of checks (rows) and variables (columns), both >= 1
+ *   out      receives the new graph (set to NULL on failure)
+ * The caller keeps its arrays; the library copies what it needs.
+ * INVALID_ARG: null pointer, m or n <= 0, malformed row_ptr, column out of range, repeated column
+ *              in a row, or a row of degree < 2 (the check update needs two neighbours).
+ * UNSUPPORTED: a row degree > QLDPC_MAX_ROW_DEGREE, a column degree > QLDPC_MAX_COL_DEGREE, or one
+ *              shot's working set larger than the device's shared memory per block.
+ * CUDA / OOM:  no usable device or the upload failed.
+ */
+QLDPC_API int qldpc_graph_create(const int32_t *row_ptr, const int32_t *col_idx, int32_t m, int32_t n,
+                       qldpc_graph **out);
+
+/* Same as qldpc_graph_create, from H in CSC form (S_c(n) = rows of column n):
+ *   col_ptr host int32[n+1], row_idx host int32[col_ptr[n]] in [0, m). */
+QLDPC_API int qldpc_graph_create_csc(const int32_t *col_ptr, const int32_t *row_idx, int32_t m, int32_t n,
+                           qldpc_graph **out);
+
+/* Release the graph and its device memory.  NULL is ignored.  The caller must ensure no decode
+ * using the graph is still running. */
+QLDPC_API void qldpc_graph_destroy(qldpc_graph *g);
+
+/* Report the graph's shape: checks, variables, edges, maximum row and column degree (any output
+ * pointer may be NULL). */
+QLDPC_API int qldpc_graph_dims(const qldpc_graph *g, int32_t *m, int32_t *n, int32_t *nnz,
+                     int32_t *max_row_degree, int32_t *max_col_degree);
+
+/* Override the launch shape chosen by the library: threads per block (a multiple of 32 in
+ * [32, 1024]) and resident blocks per SM used to size the grid; 0 keeps the automatic choice.
+ * INVALID_ARG if out of range, UNSUPPORTED if the shape cannot be resident. */
+QLDPC_API int qldpc_graph_set_launch(qldpc_graph *g, int32_t threads_per_block, int32_t blocks_per_sm);
+
+/* Pre-size the device staging that qldpc_decode_host uses, for up to max_batch shots. */
+QLDPC_API int qldpc_graph_reserve(qldpc_graph *g, int32_t max_batch);
+
+/*
+ * Decode a batch of syndromes with H (Algorithm 1), FP32 messages, early stop on, legacy default
+ * stream.  All pointers are DEVICE memory:
+ *   syndromes  uint8[batch*m], values 0/1 (only bit 0 is read)
+ *   prior_llr  float[n], gamma_n = ln(P(e_n=0)/P(e_n=1)); must be finite
+ *   out_err    uint8[batch*n]  e_hat
+ *   out_iters  int32[batch]    CN+VN iterations run (0 if the prior's decision already met s)
+ *   out_ok     uint8[batch]    1 iff H e_hat^T = s
+ * batch >= 0 (0 is a no-op); max_iter >= 0 (0 returns the prior's hard decision); alpha finite > 0.
+ */
+QLDPC_API int qldpc_decode(const qldpc_graph *g, const uint8_t *syndromes, int32_t batch,
+                 const float *prior_llr, int32_t max_iter, float alpha,
+                 uint8_t *out_err, int32_t *out_iters, uint8_t *out_ok);
+
+/*
+ * qldpc_decode with a precision (QLDPC_FP32 / QLDPC_INT16), flags, a CUDA stream
+ * (cudaStream_t cast to void*, NULL = legacy default stream) and an optional device output
+ *   out_post  float[batch*n] or NULL: the a-posteriori LLR Q_n of the last iteration run
+ *             (INT16: the fixed-point value / 256, exact).
+ */
+QLDPC_API int qldpc_decode_ex(const qldpc_graph *g, const uint8_t *syndromes, int32_t batch,
+                    const float *prior_llr, int32_t max_iter, float alpha,
+                    uint8_t *out_err, int32_t *out_iters, uint8_t *out_ok, float *out_post,
+                    int32_t precision, uint32_t flags, void *stream);
+
+/*
+ * Decode both halves of a CSS syndrome round in one launch (Sec. 2 / Fig. 2: X and Z decoded in
+ * the same kernel).  g_z decodes s_x (X errors, s_x = H_Z e_x^T, uint8[batch*m_z]) with prior_x;
+ * g_x decodes s_z (Z errors, s_z = H_X e_z^T, uint8[batch*m_x]) with prior_z.  Each half stops at
+ * its own convergence, so the results equal two qldpc_decode_ex calls bit for bit.  Outputs as in
+ * qldpc_decode_ex (post pointers may be NULL).  Both graphs must have the same n.
+ */
+QLDPC_API int qldpc_decode_pair(const qldpc_graph *g_z, const qldpc_graph *g_x,
+                      const uint8_t *s_x, const uint8_t *s_z, int32_t batch,
+                      const float *prior_x, const float *prior_z, int32_t max_iter, float alpha,
+                      uint8_t *err_x, uint8_t *err_z, int32_t *iters_x, int32_t *iters_z,
+                      uint8_t *ok_x, uint8_t *ok_z, float *post_x, float *post_z,
+                      int32_t precision, uint32_t flags, void *stream);
+
+/*
+ * End-to-end decode from HOST memory, as the paper times it (Sec. 3: latency includes the
+ * host-to-device and device-to-host transfers).  Copies syndromes (host uint8[batch*m]) and the
+ * prior (host float[n], uploaded only when it changed since the last call) into the graph's device
+ * staging, decodes on `stream`, copies e_hat, iterations and ok back into the host buffers and
+ * synchronizes the stream before returning.  Page-locked (pinned) host buffers give the fastest
+ * copies.  Calls on the same graph are serialized by a lock inside the graph.
+ */
+QLDPC_API int qldpc_decode_host(qldpc_graph *g, const uint8_t *h_syndromes, int32_t batch,
+                      const float *h_prior, int32_t max_iter, float alpha,
+                      uint8_t *h_err, int32_t *h_iters, uint8_t *h_ok,
+                      int32_t precision, uint32_t flags, void *stream);
+
+/* Static, human-readable name of a status code. */
+QLDPC_API const char *qldpc_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QLDPC_H */

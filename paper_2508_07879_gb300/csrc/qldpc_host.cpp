@@ -1,0 +1,517 @@
+// Host side of the C ABI declared in include/qldpc.h: argument validation, the Tanner-graph
+// build (CSR -> check-major slots + per-variable slot lists), device upload, launch-shape choice
+// and the end-to-end host-buffer path.  No decoding arithmetic happens here; every step of the
+// decoder runs in the sm_103a kernels of msa_kernel.cuh.
+#include "qldpc.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "msa_launch.h"
+
+using namespace qldpc;
+
+struct qldpc_graph {
+    int device = 0;
+    int sm_count = 0;
+    size_t smem_optin = 0;      // max dynamic shared memory per block (opt-in)
+    int32_t m = 0, n = 0, nnz = 0, dc_max = 0, dv_max = 0;
+    int dcb = 0, dvb = 0;       // kernel buckets
+    void *d_block = nullptr;    // one device allocation for all graph arrays
+    DeviceGraph dg{};
+    // launch overrides (0 = automatic)
+    int user_threads = 0, user_blocks_per_sm = 0;
+    // staging for qldpc_decode_host
+    std::mutex host_mu;
+    int32_t cap = 0;
+    void *d_stage = nullptr;
+    uint8_t *d_syn = nullptr, *d_err = nullptr, *d_ok = nullptr;
+    int32_t *d_iters = nullptr;
+    float *d_prior = nullptr;
+    std::vector<float> prior_cache;
+    bool prior_valid = false;
+};
+
+namespace qldpc {
+
+int dc_bucket(int d) { return d <= 8 ? 8 : d <= 16 ? 16 : d <= 32 ? 32 : -1; }
+int dv_bucket(int d) { return d <= 4 ? 4 : d <= 8 ? 8 : d <= 16 ? 16 : -1; }
+
+const void *msa_kernel(int precision, int dcb, int dvb)
+{
+    return precision == kINT16 ? msa_kernel_i16(dcb, dvb) : msa_kernel_f32(dcb, dvb);
+}
+
+cudaError_t launch_msa(const LaunchParams &p, int precision, int dcb, int dvb, int threads,
+                       int grid_x, size_t smem, cudaStream_t stream)
+{
+    dim3 grid(unsigned(grid_x), unsigned(p.nprob));
+    return precision == kINT16 ? launch_msa_i16(p, dcb, dvb, grid, threads, smem, stream)
+                               : launch_msa_f32(p, dcb, dvb, grid, threads, smem, stream);
+}
+
+}  // namespace qldpc
+
+namespace {
+
+// ------------------------------------------------------------------------------------------
+// CSR validation and layout (pure host; runs before any CUDA call)
+// ------------------------------------------------------------------------------------------
+struct HostLayout {
+    int32_t dc_max = 0, dv_max = 0;
+    std::vector<uint8_t> rdeg, vdeg;
+    std::vector<uint32_t> vslot;   // [dv_max * n]
+};
+
+int validate_and_layout(const int32_t *row_ptr, const int32_t *col_idx, int32_t m, int32_t n,
+                        HostLayout &out)
+{
+    if (!row_ptr || m <= 0 || n <= 0) return QLDPC_ERR_INVALID_ARG;
+    if (row_ptr[0] != 0) return QLDPC_ERR_INVALID_ARG;
+    for (int32_t i = 0; i < m; ++i)
+        if (row_ptr[i + 1] < row_ptr[i]) return QLDPC_ERR_INVALID_ARG;
+    const int64_t nnz = row_ptr[m];
+    if (nnz > 0 && !col_idx) return QLDPC_ERR_INVALID_ARG;
+    std::vector<int32_t> seen(size_t(n), -1);
+    std::vector<int32_t> cdeg(size_t(n), 0);
+    int32_t dc_max = 0;
+    for (int32_t i = 0; i < m; ++i) {
+        const int32_t d = row_ptr[i + 1] - row_ptr[i];
+        if (d < 2) return QLDPC_ERR_INVALID_ARG;
+        dc_max = std::max(dc_max, d);
+        for (int32_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            const int32_t v = col_idx[e];
+            if (v < 0 || v >= n) return QLDPC_ERR_INVALID_ARG;
+            if (seen[size_t(v)] == i) return QLDPC_ERR_INVALID_ARG;   // repeated column in a row
+            seen[size_t(v)] = i;
+            cdeg[size_t(v)]++;
+        }
+    }
+    const int32_t dv_max = *std::max_element(cdeg.begin(), cdeg.end());
+    if (dc_max > QLDPC_MAX_ROW_DEGREE || dv_max > QLDPC_MAX_COL_DEGREE) return QLDPC_ERR_UNSUPPORTED;
+    if (int64_t(dc_max) * m > int64_t(UINT32_MAX)) return QLDPC_ERR_UNSUPPORTED;
+
+    out.dc_max = dc_max;
+    out.dv_max = dv_max;
+    out.rdeg.resize(size_t(m));
+    out.vdeg.assign(size_t(n), 0);
+    out.vslot.assign(size_t(std::max(dv_max, 1)) * size_t(n), 0u);
+    // Rows are visited in ascending order, so each variable's list is in ascending check order,
+    // the order in which the variable step accumulates its sums.
+    for (int32_t i = 0; i < m; ++i) {
+        out.rdeg[size_t(i)] = uint8_t(row_ptr[i + 1] - row_ptr[i]);
+        for (int32_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            const int32_t v = col_idx[e];
+            const int32_t j = e - row_ptr[i];
+            const int32_t k = out.vdeg[size_t(v)]++;
+            out.vslot[size_t(k) * n + v] = uint32_t(j) * uint32_t(m) + uint32_t(i);
+        }
+    }
+    return QLDPC_OK;
+}
+
+bool finite_alpha(float a) { return std::isfinite(a) && a > 0.0f; }
+
+int alpha_fixed(float alpha)   // round_half_away(alpha * 2^15), -1 outside (0, 1]
+{
+    if (!std::isfinite(alpha) || alpha <= 0.0f || alpha > 1.0f) return -1;
+    const int32_t a = int32_t(std::round(alpha * 32768.0f));
+    return (a >= 1 && a <= 32768) ? a : -1;
+}
+
+int cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess) return QLDPC_OK;
+    if (e == cudaErrorMemoryAllocation) return QLDPC_ERR_OOM;
+    return QLDPC_ERR_CUDA;
+}
+
+size_t shot_smem(const qldpc_graph *g, int precision)
+{
+    return smem_layout(g->m, g->n, g->dc_max, msg_bytes(precision)).total;
+}
+
+// Threads per block: for a latency-bound batch (every shot gets its own SM) make one pass over
+// the checks and as few passes over the variables as possible; for throughput use 256 threads and
+// many resident blocks.
+int choose_threads(const qldpc_graph *g, int32_t shots)
+{
+    if (g->user_threads) return g->user_threads;
+    const int big = std::max(g->m, g->n);
+    if (shots <= g->sm_count) {
+        int t = big <= 1024 ? big : std::max(g->m, (g->n + 1) / 2);
+        t = ((std::min(t, 1024) + 31) / 32) * 32;
+        return std::max(t, 32);
+    }
+    return 256;
+}
+
+// Opt in to more than 48 KB of dynamic shared memory once per kernel variant and size.
+int ensure_kernel_attrs(int precision, int dcb, int dvb, size_t smem, size_t smem_optin)
+{
+    static std::mutex mu;
+    static size_t granted[2][33][17] = {};
+    const void *k = msa_kernel(precision, dcb, dvb);
+    if (!k) return QLDPC_ERR_UNSUPPORTED;
+    if (smem > smem_optin) return QLDPC_ERR_UNSUPPORTED;
+    if (smem <= 48 * 1024) return QLDPC_OK;
+    std::lock_guard<std::mutex> lk(mu);
+    size_t &have = granted[precision][dcb][dvb];
+    if (smem <= have) return QLDPC_OK;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return cuda_status(e);
+    have = smem;
+    return QLDPC_OK;
+}
+
+int check_device(const qldpc_graph *g)
+{
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return QLDPC_ERR_CUDA;
+    return dev == g->device ? QLDPC_OK : QLDPC_ERR_INVALID_ARG;
+}
+
+int launch(const qldpc_graph *g0, const qldpc_graph *g1, const Problem *probs, int nprob,
+           int32_t batch, int32_t max_iter, float alpha, int32_t precision, uint32_t flags,
+           cudaStream_t stream)
+{
+    if (precision != QLDPC_FP32 && precision != QLDPC_INT16) return QLDPC_ERR_INVALID_ARG;
+    if ((flags & ~uint32_t(QLDPC_NO_EARLY_STOP)) != 0) return QLDPC_ERR_INVALID_ARG;
+    if (batch < 0 || max_iter < 0 || !finite_alpha(alpha)) return QLDPC_ERR_INVALID_ARG;
+    int aq = 0;
+    if (precision == QLDPC_INT16) {
+        aq = alpha_fixed(alpha);
+        if (aq < 0) return QLDPC_ERR_INVALID_ARG;
+    }
+    if (batch == 0) return QLDPC_OK;
+
+    LaunchParams p{};
+    p.nprob = nprob;
+    p.batch = batch;
+    p.max_iter = max_iter;
+    p.alpha = alpha;
+    p.alpha_q = aq;
+    p.flags = flags;
+    for (int i = 0; i < nprob; ++i) p.prob[i] = probs[i];
+
+    // One kernel variant and one block shape serve both problems of a pair.
+    const qldpc_graph *gs[2] = {g0, g1};
+    int dcb = 0, dvb = 0;
+    size_t smem = 0;
+    for (int i = 0; i < nprob; ++i) {
+        dcb = std::max(dcb, gs[i]->dcb);
+        dvb = std::max(dvb, gs[i]->dvb);
+        smem = std::max(smem, shot_smem(gs[i], precision));
+    }
+    const qldpc_graph *lead = (nprob == 2 && (g1->m + g1->n) > (g0->m + g0->n)) ? g1 : g0;
+    int rc = ensure_kernel_attrs(precision, dcb, dvb, smem, lead->smem_optin);
+    if (rc) return rc;
+
+    // Latency-bound batches (one block per shot fits on the SMs) launch one block per shot;
+    // larger batches size a persistent grid from the occupancy of the chosen shape.
+    const int threads = choose_threads(lead, batch * nprob);
+    int grid_x = batch;
+    if (int64_t(batch) * nprob > lead->sm_count || lead->user_blocks_per_sm) {
+        int per_sm = lead->user_blocks_per_sm;
+        if (!per_sm) {
+            cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &per_sm, msa_kernel(precision, dcb, dvb), threads, smem);
+            if (e != cudaSuccess) return cuda_status(e);
+            if (per_sm < 1) return QLDPC_ERR_UNSUPPORTED;
+        }
+        const int64_t slots = int64_t(per_sm) * lead->sm_count / nprob;
+        grid_x = int(std::max<int64_t>(1, std::min<int64_t>(batch, slots)));
+    }
+    return cuda_status(launch_msa(p, precision, dcb, dvb, threads, grid_x, smem, stream));
+}
+
+Problem make_problem(const qldpc_graph *g, const uint8_t *syn, const float *prior, uint8_t *err,
+                     int32_t *iters, uint8_t *ok, float *post)
+{
+    Problem pr{};
+    pr.g = g->dg;
+    pr.syn = syn;
+    pr.prior = prior;
+    pr.err = err;
+    pr.iters = iters;
+    pr.ok = ok;
+    pr.post = post;
+    return pr;
+}
+
+void free_stage(qldpc_graph *g)
+{
+    if (g->d_stage) cudaFree(g->d_stage);
+    g->d_stage = nullptr;
+    g->d_syn = g->d_err = g->d_ok = nullptr;
+    g->d_iters = nullptr;
+    g->cap = 0;
+}
+
+int reserve_stage(qldpc_graph *g, int32_t max_batch)
+{
+    if (max_batch <= g->cap && g->d_prior) return QLDPC_OK;
+    const int32_t cap = std::max(max_batch, g->cap);
+    const size_t syn_b = align16(size_t(cap) * g->m);
+    const size_t err_b = align16(size_t(cap) * g->n);
+    const size_t it_b = align16(size_t(cap) * 4);
+    const size_t ok_b = align16(size_t(cap));
+    const size_t pr_b = align16(size_t(g->n) * 4);
+    void *blk = nullptr;
+    cudaError_t e = cudaMalloc(&blk, syn_b + err_b + it_b + ok_b + pr_b);
+    if (e != cudaSuccess) return cuda_status(e);
+    free_stage(g);
+    char *b = static_cast<char *>(blk);
+    g->d_stage = blk;
+    g->d_syn = reinterpret_cast<uint8_t *>(b);
+    g->d_err = reinterpret_cast<uint8_t *>(b + syn_b);
+    g->d_iters = reinterpret_cast<int32_t *>(b + syn_b + err_b);
+    g->d_ok = reinterpret_cast<uint8_t *>(b + syn_b + err_b + it_b);
+    g->d_prior = reinterpret_cast<float *>(b + syn_b + err_b + it_b + ok_b);
+    g->prior_valid = false;
+    g->cap = cap;
+    return QLDPC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int qldpc_graph_create(const int32_t *row_ptr, const int32_t *col_idx, int32_t m, int32_t n,
+                       qldpc_graph **out)
+{
+    if (!out) return QLDPC_ERR_INVALID_ARG;
+    *out = nullptr;
+    HostLayout hl;
+    int rc = validate_and_layout(row_ptr, col_idx, m, n, hl);
+    if (rc) return rc;
+
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return QLDPC_ERR_CUDA;
+    cudaDeviceProp prop{};
+    e = cudaGetDeviceProperties(&prop, dev);
+    if (e != cudaSuccess) return QLDPC_ERR_CUDA;
+
+    qldpc_graph *g = new (std::nothrow) qldpc_graph();
+    if (!g) return QLDPC_ERR_OOM;
+    g->device = dev;
+    g->sm_count = prop.multiProcessorCount;
+    g->smem_optin = prop.sharedMemPerBlockOptin;
+    g->m = m;
+    g->n = n;
+    g->nnz = row_ptr[m];
+    g->dc_max = hl.dc_max;
+    g->dv_max = hl.dv_max;
+    g->dcb = dc_bucket(hl.dc_max);
+    g->dvb = dv_bucket(hl.dv_max);
+    // The FP32 working set is the larger one; reject graphs whose shot does not fit on chip.
+    if (shot_smem(g, QLDPC_FP32) > g->smem_optin && shot_smem(g, QLDPC_INT16) > g->smem_optin) {
+        delete g;
+        return QLDPC_ERR_UNSUPPORTED;
+    }
+
+    const size_t vs_b = align16(hl.vslot.size() * sizeof(uint32_t));
+    const size_t vd_b = align16(size_t(n));
+    const size_t rd_b = align16(size_t(m));
+    e = cudaMalloc(&g->d_block, vs_b + vd_b + rd_b);
+    if (e != cudaSuccess) {
+        delete g;
+        return cuda_status(e);
+    }
+    char *b = static_cast<char *>(g->d_block);
+    e = cudaMemcpy(b, hl.vslot.data(), hl.vslot.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b + vs_b, hl.vdeg.data(), size_t(n), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b + vs_b + vd_b, hl.rdeg.data(), size_t(m), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(g->d_block);
+        delete g;
+        return cuda_status(e);
+    }
+    g->dg.vslot = reinterpret_cast<const uint32_t *>(b);
+    g->dg.vdeg = reinterpret_cast<const uint8_t *>(b + vs_b);
+    g->dg.rdeg = reinterpret_cast<const uint8_t *>(b + vs_b + vd_b);
+    g->dg.m = m;
+    g->dg.n = n;
+    g->dg.dc_max = hl.dc_max;
+    g->dg.dv_max = hl.dv_max;
+    *out = g;
+    return QLDPC_OK;
+}
+
+int qldpc_graph_create_csc(const int32_t *col_ptr, const int32_t *row_idx, int32_t m, int32_t n,
+                           qldpc_graph **out)
+{
+    if (!out) return QLDPC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!col_ptr || m <= 0 || n <= 0 || col_ptr[0] != 0) return QLDPC_ERR_INVALID_ARG;
+    for (int32_t v = 0; v < n; ++v)
+        if (col_ptr[v + 1] < col_ptr[v]) return QLDPC_ERR_INVALID_ARG;
+    const int32_t nnz = col_ptr[n];
+    if (nnz > 0 && !row_idx) return QLDPC_ERR_INVALID_ARG;
+    std::vector<int32_t> row_ptr(size_t(m) + 1, 0);
+    std::vector<int32_t> col(static_cast<size_t>(nnz));
+    for (int32_t e = 0; e < nnz; ++e) {
+        const int32_t r = row_idx[e];
+        if (r < 0 || r >= m) return QLDPC_ERR_INVALID_ARG;
+        row_ptr[size_t(r) + 1]++;
+    }
+    for (int32_t i = 0; i < m; ++i) row_ptr[size_t(i) + 1] += row_ptr[size_t(i)];
+    std::vector<int32_t> fill(row_ptr.begin(), row_ptr.end() - 1);
+    for (int32_t v = 0; v < n; ++v)
+        for (int32_t e = col_ptr[v]; e < col_ptr[v + 1]; ++e) col[size_t(fill[size_t(row_idx[e])]++)] = v;
+    return qldpc_graph_create(row_ptr.data(), col.data(), m, n, out);
+}
+
+void qldpc_graph_destroy(qldpc_graph *g)
+{
+    if (!g) return;
+    free_stage(g);
+    if (g->d_block) cudaFree(g->d_block);
+    delete g;
+}
+
+int qldpc_graph_dims(const qldpc_graph *g, int32_t *m, int32_t *n, int32_t *nnz,
+                     int32_t *max_row_degree, int32_t *max_col_degree)
+{
+    if (!g) return QLDPC_ERR_INVALID_ARG;
+    if (m) *m = g->m;
+    if (n) *n = g->n;
+    if (nnz) *nnz = g->nnz;
+    if (max_row_degree) *max_row_degree = g->dc_max;
+    if (max_col_degree) *max_col_degree = g->dv_max;
+    return QLDPC_OK;
+}
+
+int qldpc_graph_set_launch(qldpc_graph *g, int32_t threads_per_block, int32_t blocks_per_sm)
+{
+    if (!g) return QLDPC_ERR_INVALID_ARG;
+    if (threads_per_block != 0 && (threads_per_block < 32 || threads_per_block > 1024 || threads_per_block % 32))
+        return QLDPC_ERR_INVALID_ARG;
+    if (blocks_per_sm < 0 || blocks_per_sm > 32) return QLDPC_ERR_INVALID_ARG;
+    if (blocks_per_sm) {
+        // the requested residency must be achievable for both precisions' working sets
+        const int t = threads_per_block ? threads_per_block : 256;
+        for (int prec : {QLDPC_FP32, QLDPC_INT16}) {
+            const size_t smem = shot_smem(g, prec);
+            if (smem > g->smem_optin) continue;
+            if (int rc = ensure_kernel_attrs(prec, g->dcb, g->dvb, smem, g->smem_optin)) return rc;
+            int per_sm = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, msa_kernel(prec, g->dcb, g->dvb), t, smem) !=
+                cudaSuccess)
+                return QLDPC_ERR_CUDA;
+            if (per_sm < blocks_per_sm) return QLDPC_ERR_UNSUPPORTED;
+        }
+    }
+    g->user_threads = threads_per_block;
+    g->user_blocks_per_sm = blocks_per_sm;
+    return QLDPC_OK;
+}
+
+int qldpc_graph_reserve(qldpc_graph *g, int32_t max_batch)
+{
+    if (!g || max_batch < 0) return QLDPC_ERR_INVALID_ARG;
+    if (int rc = check_device(g)) return rc;
+    std::lock_guard<std::mutex> lk(g->host_mu);
+    return reserve_stage(g, std::max(max_batch, 1));
+}
+
+int qldpc_decode_ex(const qldpc_graph *g, const uint8_t *syndromes, int32_t batch,
+                    const float *prior_llr, int32_t max_iter, float alpha, uint8_t *out_err,
+                    int32_t *out_iters, uint8_t *out_ok, float *out_post, int32_t precision,
+                    uint32_t flags, void *stream)
+{
+    if (!g) return QLDPC_ERR_INVALID_ARG;
+    if (batch > 0 && (!syndromes || !prior_llr || !out_err || !out_iters || !out_ok))
+        return QLDPC_ERR_INVALID_ARG;
+    if (int rc = check_device(g)) return rc;
+    const Problem pr = make_problem(g, syndromes, prior_llr, out_err, out_iters, out_ok, out_post);
+    return launch(g, g, &pr, 1, batch, max_iter, alpha, precision, flags,
+                  static_cast<cudaStream_t>(stream));
+}
+
+int qldpc_decode(const qldpc_graph *g, const uint8_t *syndromes, int32_t batch,
+                 const float *prior_llr, int32_t max_iter, float alpha, uint8_t *out_err,
+                 int32_t *out_iters, uint8_t *out_ok)
+{
+    return qldpc_decode_ex(g, syndromes, batch, prior_llr, max_iter, alpha, out_err, out_iters,
+                           out_ok, nullptr, QLDPC_FP32, 0u, nullptr);
+}
+
+int qldpc_decode_pair(const qldpc_graph *g_z, const qldpc_graph *g_x, const uint8_t *s_x,
+                      const uint8_t *s_z, int32_t batch, const float *prior_x, const float *prior_z,
+                      int32_t max_iter, float alpha, uint8_t *err_x, uint8_t *err_z,
+                      int32_t *iters_x, int32_t *iters_z, uint8_t *ok_x, uint8_t *ok_z,
+                      float *post_x, float *post_z, int32_t precision, uint32_t flags, void *stream)
+{
+    if (!g_z || !g_x) return QLDPC_ERR_INVALID_ARG;
+    if (g_z->n != g_x->n || g_z->device != g_x->device) return QLDPC_ERR_INVALID_ARG;
+    if (batch > 0 && (!s_x || !s_z || !prior_x || !prior_z || !err_x || !err_z || !iters_x ||
+                      !iters_z || !ok_x || !ok_z))
+        return QLDPC_ERR_INVALID_ARG;
+    if (int rc = check_device(g_z)) return rc;
+    const Problem pr[2] = {make_problem(g_z, s_x, prior_x, err_x, iters_x, ok_x, post_x),
+                           make_problem(g_x, s_z, prior_z, err_z, iters_z, ok_z, post_z)};
+    return launch(g_z, g_x, pr, 2, batch, max_iter, alpha, precision, flags,
+                  static_cast<cudaStream_t>(stream));
+}
+
+int qldpc_decode_host(qldpc_graph *g, const uint8_t *h_syndromes, int32_t batch,
+                      const float *h_prior, int32_t max_iter, float alpha, uint8_t *h_err,
+                      int32_t *h_iters, uint8_t *h_ok, int32_t precision, uint32_t flags,
+                      void *stream)
+{
+    if (!g) return QLDPC_ERR_INVALID_ARG;
+    if (batch < 0) return QLDPC_ERR_INVALID_ARG;
+    if (batch > 0 && (!h_syndromes || !h_prior || !h_err || !h_iters || !h_ok))
+        return QLDPC_ERR_INVALID_ARG;
+    if (int rc = check_device(g)) return rc;
+    if (batch == 0) return QLDPC_OK;
+    std::lock_guard<std::mutex> lk(g->host_mu);
+    if (int rc = reserve_stage(g, batch)) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaSuccess;
+    const size_t prior_b = size_t(g->n) * sizeof(float);
+    if (!g->prior_valid || std::memcmp(g->prior_cache.data(), h_prior, prior_b) != 0) {
+        g->prior_cache.assign(h_prior, h_prior + g->n);
+        e = cudaMemcpyAsync(g->d_prior, g->prior_cache.data(), prior_b, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cuda_status(e);
+        g->prior_valid = true;
+    }
+    e = cudaMemcpyAsync(g->d_syn, h_syndromes, size_t(batch) * g->m, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_status(e);
+    const Problem pr = make_problem(g, g->d_syn, g->d_prior, g->d_err, g->d_iters, g->d_ok, nullptr);
+    int rc = launch(g, g, &pr, 1, batch, max_iter, alpha, precision, flags, st);
+    if (rc) {
+        cudaStreamSynchronize(st);
+        return rc;
+    }
+    e = cudaMemcpyAsync(h_err, g->d_err, size_t(batch) * g->n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h_iters, g->d_iters, size_t(batch) * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h_ok, g->d_ok, size_t(batch), cudaMemcpyDeviceToHost, st);
+    const cudaError_t se = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_status(e);
+    return cuda_status(se);
+}
+
+const char *qldpc_status_string(int status)
+{
+    switch (status) {
+    case QLDPC_OK: return "QLDPC_OK";
+    case QLDPC_ERR_INVALID_ARG: return "QLDPC_ERR_INVALID_ARG: invalid argument";
+    case QLDPC_ERR_UNSUPPORTED: return "QLDPC_ERR_UNSUPPORTED: graph exceeds a kernel limit";
+    case QLDPC_ERR_OOM: return "QLDPC_ERR_OOM: out of memory";
+    case QLDPC_ERR_CUDA: return "QLDPC_ERR_CUDA: CUDA runtime error";
+    case QLDPC_ERR_TIMEOUT: return "QLDPC_ERR_TIMEOUT: device-side wait expired";
+    default: return "unknown qldpc status";
+    }
+}
+
+}  // extern "C"

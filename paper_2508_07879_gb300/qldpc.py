@@ -1,0 +1,263 @@
+"""Python binding of libqldpc.so (include/qldpc.h) -- argument marshalling only.
+
+The functions named ``qldpc_*`` mirror the C ABI one to one and take raw integers for pointers.
+``Graph``, ``decode``, ``decode_pair`` and ``decode_host`` wrap them for torch tensors and numpy
+arrays.  Every step of the decoder runs in the library's CUDA kernels; this module never computes
+a message, a decision or a syndrome check, and there is no CPU fallback: if the library is missing
+or fails to load, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libqldpc.so")
+
+QLDPC_OK = 0
+QLDPC_ERR_INVALID_ARG = -1
+QLDPC_ERR_UNSUPPORTED = -2
+QLDPC_ERR_OOM = -3
+QLDPC_ERR_CUDA = -4
+QLDPC_ERR_TIMEOUT = -5
+QLDPC_FP32 = 0
+QLDPC_INT16 = 1
+QLDPC_NO_EARLY_STOP = 1
+QLDPC_MAX_ROW_DEGREE = 32
+QLDPC_MAX_COL_DEGREE = 16
+
+PRECISIONS = {"fp32": QLDPC_FP32, "int16": QLDPC_INT16}
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is not built; run `python -c 'import __graft_entry__ as g; "
+                          f"g.build()'` (or paper_2508_07879_gb300/build.py) first")
+    return ctypes.CDLL(LIB_PATH)
+
+
+_lib = _load()
+_p = ctypes.c_void_p
+_i32 = ctypes.c_int32
+_u32 = ctypes.c_uint32
+_f32 = ctypes.c_float
+
+_SIGNATURES = {
+    "qldpc_graph_create": ([_p, _p, _i32, _i32, ctypes.POINTER(_p)], ctypes.c_int),
+    "qldpc_graph_create_csc": ([_p, _p, _i32, _i32, ctypes.POINTER(_p)], ctypes.c_int),
+    "qldpc_graph_destroy": ([_p], None),
+    "qldpc_graph_dims": ([_p, _p, _p, _p, _p, _p], ctypes.c_int),
+    "qldpc_graph_set_launch": ([_p, _i32, _i32], ctypes.c_int),
+    "qldpc_graph_reserve": ([_p, _i32], ctypes.c_int),
+    "qldpc_decode": ([_p, _p, _i32, _p, _i32, _f32, _p, _p, _p], ctypes.c_int),
+    "qldpc_decode_ex": ([_p, _p, _i32, _p, _i32, _f32, _p, _p, _p, _p, _i32, _u32, _p], ctypes.c_int),
+    "qldpc_decode_pair": ([_p, _p, _p, _p, _i32, _p, _p, _i32, _f32, _p, _p, _p, _p, _p, _p, _p, _p,
+                           _i32, _u32, _p], ctypes.c_int),
+    "qldpc_decode_host": ([_p, _p, _i32, _p, _i32, _f32, _p, _p, _p, _i32, _u32, _p], ctypes.c_int),
+    "qldpc_status_string": ([ctypes.c_int], ctypes.c_char_p),
+}
+for _name, (_args, _res) in _SIGNATURES.items():
+    _fn = getattr(_lib, _name)
+    _fn.argtypes = _args
+    _fn.restype = _res
+
+# Raw C entry points, same names as include/qldpc.h.
+qldpc_graph_create = _lib.qldpc_graph_create
+qldpc_graph_create_csc = _lib.qldpc_graph_create_csc
+qldpc_graph_destroy = _lib.qldpc_graph_destroy
+qldpc_graph_dims = _lib.qldpc_graph_dims
+qldpc_graph_set_launch = _lib.qldpc_graph_set_launch
+qldpc_graph_reserve = _lib.qldpc_graph_reserve
+qldpc_decode = _lib.qldpc_decode
+qldpc_decode_ex = _lib.qldpc_decode_ex
+qldpc_decode_pair = _lib.qldpc_decode_pair
+qldpc_decode_host = _lib.qldpc_decode_host
+qldpc_status_string = _lib.qldpc_status_string
+
+
+class QldpcError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        msg = qldpc_status_string(status).decode()
+        super().__init__(f"{what}: {msg}" if what else msg)
+
+
+def check(status: int, what: str = "") -> None:
+    if status != QLDPC_OK:
+        raise QldpcError(status, what)
+
+
+def _np_ptr(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _dev_ptr(t, dtype, shape, name):
+    """Device pointer of a contiguous CUDA tensor of the given dtype and shape (validation only)."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_handle(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Graph:
+    """A Tanner graph uploaded to the current CUDA device (owns a qldpc_graph)."""
+
+    def __init__(self, row_ptr, col_idx, m: int, n: int):
+        self._h = None
+        rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+        ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+        if rp.shape != (m + 1,):
+            raise ValueError("row_ptr must have m+1 entries")
+        h = ctypes.c_void_p()
+        check(qldpc_graph_create(_np_ptr(rp), _np_ptr(ci) if ci.size else None, int(m), int(n),
+                                 ctypes.byref(h)), "qldpc_graph_create")
+        self._h = h
+        self.m, self.n, self.nnz = int(m), int(n), int(rp[-1])
+
+    @classmethod
+    def from_csr(cls, csr) -> "Graph":
+        return cls(csr.row_ptr, csr.col_idx, csr.m, csr.n)
+
+    @classmethod
+    def from_dense(cls, h) -> "Graph":
+        h = np.asarray(h, dtype=np.uint8) & 1
+        rows, cols = np.nonzero(h)
+        rp = np.zeros(h.shape[0] + 1, dtype=np.int32)
+        np.add.at(rp, rows + 1, 1)
+        return cls(np.cumsum(rp), cols, h.shape[0], h.shape[1])
+
+    @property
+    def handle(self):
+        return self._h
+
+    def dims(self):
+        vals = [ctypes.c_int32() for _ in range(5)]
+        check(qldpc_graph_dims(self._h, *[ctypes.byref(v) for v in vals]), "qldpc_graph_dims")
+        return tuple(v.value for v in vals)
+
+    def set_launch(self, threads_per_block: int = 0, blocks_per_sm: int = 0) -> None:
+        check(qldpc_graph_set_launch(self._h, int(threads_per_block), int(blocks_per_sm)),
+              "qldpc_graph_set_launch")
+
+    def reserve(self, max_batch: int) -> None:
+        check(qldpc_graph_reserve(self._h, int(max_batch)), "qldpc_graph_reserve")
+
+    def close(self) -> None:
+        if self._h:
+            qldpc_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def decode(graph: Graph, syndromes, prior, max_iter: int, alpha: float = 0.75,
+           precision: str = "fp32", early_stop: bool = True, want_post: bool = False,
+           out=None, stream=None):
+    """Decode syndromes (CUDA uint8 [B, m]) with prior LLRs (CUDA float32 [n]).
+
+    Returns (err uint8 [B, n], iters int32 [B], ok uint8 [B], post float32 [B, n] or None), all
+    CUDA tensors, enqueued on ``stream`` (default: torch's current stream).  ``out`` may supply
+    the four output tensors to avoid allocation.
+    """
+    import torch
+    batch = int(syndromes.shape[0]) if syndromes.dim() == 2 else 0
+    dev = syndromes.device
+    if out is None:
+        err = torch.empty((batch, graph.n), dtype=torch.uint8, device=dev)
+        iters = torch.empty(batch, dtype=torch.int32, device=dev)
+        ok = torch.empty(batch, dtype=torch.uint8, device=dev)
+        post = torch.empty((batch, graph.n), dtype=torch.float32, device=dev) if want_post else None
+    else:
+        err, iters, ok, post = out
+    flags = 0 if early_stop else QLDPC_NO_EARLY_STOP
+    check(qldpc_decode_ex(graph.handle,
+                          _dev_ptr(syndromes, torch.uint8, (batch, graph.m), "syndromes"), batch,
+                          _dev_ptr(prior, torch.float32, (graph.n,), "prior"), int(max_iter),
+                          float(alpha),
+                          _dev_ptr(err, torch.uint8, (batch, graph.n), "err"),
+                          _dev_ptr(iters, torch.int32, (batch,), "iters"),
+                          _dev_ptr(ok, torch.uint8, (batch,), "ok"),
+                          _dev_ptr(post, torch.float32, (batch, graph.n), "post") if post is not None else None,
+                          PRECISIONS[precision], flags, _stream_handle(stream)),
+          "qldpc_decode_ex")
+    return err, iters, ok, post
+
+
+def decode_pair(g_z: Graph, g_x: Graph, s_x, s_z, prior_x, prior_z, max_iter: int,
+                alpha: float = 0.75, precision: str = "fp32", early_stop: bool = True,
+                want_post: bool = False, stream=None):
+    """X and Z halves of a CSS syndrome round in one launch; returns two (err, iters, ok, post)."""
+    import torch
+    batch = int(s_x.shape[0])
+    dev = s_x.device
+    outs = []
+    for g in (g_z, g_x):
+        outs.append((torch.empty((batch, g.n), dtype=torch.uint8, device=dev),
+                     torch.empty(batch, dtype=torch.int32, device=dev),
+                     torch.empty(batch, dtype=torch.uint8, device=dev),
+                     torch.empty((batch, g.n), dtype=torch.float32, device=dev) if want_post else None))
+    (ex, ix, ox, px), (ez, iz, oz, pz) = outs
+    flags = 0 if early_stop else QLDPC_NO_EARLY_STOP
+    check(qldpc_decode_pair(g_z.handle, g_x.handle,
+                            _dev_ptr(s_x, torch.uint8, (batch, g_z.m), "s_x"),
+                            _dev_ptr(s_z, torch.uint8, (batch, g_x.m), "s_z"), batch,
+                            _dev_ptr(prior_x, torch.float32, (g_z.n,), "prior_x"),
+                            _dev_ptr(prior_z, torch.float32, (g_x.n,), "prior_z"),
+                            int(max_iter), float(alpha),
+                            _dev_ptr(ex, torch.uint8, (batch, g_z.n), "err_x"),
+                            _dev_ptr(ez, torch.uint8, (batch, g_x.n), "err_z"),
+                            _dev_ptr(ix, torch.int32, (batch,), "iters_x"),
+                            _dev_ptr(iz, torch.int32, (batch,), "iters_z"),
+                            _dev_ptr(ox, torch.uint8, (batch,), "ok_x"),
+                            _dev_ptr(oz, torch.uint8, (batch,), "ok_z"),
+                            _dev_ptr(px, torch.float32, (batch, g_z.n), "post_x") if want_post else None,
+                            _dev_ptr(pz, torch.float32, (batch, g_x.n), "post_z") if want_post else None,
+                            PRECISIONS[precision], flags, _stream_handle(stream)),
+          "qldpc_decode_pair")
+    return (ex, ix, ox, px), (ez, iz, oz, pz)
+
+
+def decode_host(graph: Graph, syndromes: np.ndarray, prior: np.ndarray, max_iter: int,
+                alpha: float = 0.75, precision: str = "fp32", early_stop: bool = True,
+                out=None, stream=None):
+    """End-to-end decode from host (numpy) buffers; synchronous.  Returns (err, iters, ok) numpy.
+
+    Pass page-locked arrays (e.g. ``torch.empty(..., pin_memory=True).numpy()``) for fast copies.
+    """
+    syn = np.ascontiguousarray(syndromes, dtype=np.uint8)
+    batch = syn.shape[0]
+    if syn.shape != (batch, graph.m):
+        raise ValueError(f"syndromes must have shape (B, {graph.m})")
+    pr = np.ascontiguousarray(prior, dtype=np.float32)
+    if pr.shape != (graph.n,):
+        raise ValueError(f"prior must have shape ({graph.n},)")
+    if out is None:
+        err = np.empty((batch, graph.n), dtype=np.uint8)
+        iters = np.empty(batch, dtype=np.int32)
+        ok = np.empty(batch, dtype=np.uint8)
+    else:
+        err, iters, ok = out
+    flags = 0 if early_stop else QLDPC_NO_EARLY_STOP
+    sh = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+    check(qldpc_decode_host(graph.handle, _np_ptr(syn), batch, _np_ptr(pr), int(max_iter),
+                            float(alpha), _np_ptr(err), _np_ptr(iters), _np_ptr(ok),
+                            PRECISIONS[precision], flags, sh), "qldpc_decode_host")
+    return err, iters, ok

@@ -1,0 +1,395 @@
+"""Benchmark: batched syndrome decoding of the N=1054 lifted-product code on one GB300 (per rank).
+
+One step = one decode launch over a batch of 65536 syndromes of the [[1054]] lifted-product code
+(H_Z, 465 checks), i.i.d. X noise, plain normalized min-sum (alpha = 0.75), max 50 iterations,
+early stop on.  Steps cycle through five pre-generated batches at p = 0.01 ... 0.05 (seeds
+2001..2005), so consecutive steps read different inputs (5 x 30.5 MB of syndromes plus 69 MB of
+outputs per step, more than the 129 MB L2).
+
+Printed as one JSON line on rank 0:
+  value        syndromes/s of the device-resident decode (inputs in HBM), whole job
+  e2e          the same through qldpc_decode_host with pinned HOST buffers (copies timed)
+  latency      single-shot (B = 1) end-to-end latency percentiles vs the 63 us threshold
+  roofline     the decoder kernel against the SM integer/FP32 issue roof ("alu")
+  cpu_baseline the CPU oracle on a bounded sample of the same workload, all host cores
+  clocks       SM clock and throttle reasons sampled during the timed region
+
+``--impl reference`` times the CPU oracle (the reference arm) on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+P_GRID = (0.01, 0.02, 0.03, 0.04, 0.05)
+SEEDS = (2001, 2002, 2003, 2004, 2005)
+BATCH = 65536
+MAX_ITER = 50
+ALPHA = 0.75
+LAT_P = 0.03
+LAT_SHOTS = 10000
+LAT_WARMUP = 200
+THRESHOLD_US = 63.0
+OPS_PER_EDGE_ITER = 10          # algorithmic ALU operations per edge per iteration
+ALU_LANES_PER_SM = 128          # FP32/INT32 lanes per SM, one operation per lane per clock
+
+# DRAM traffic of one decoder launch from an ncu capture, valid only for the kernel source it was
+# measured on (profiles/msa_flood_lp1054_b65536_fp32.md); reported as null once the source changes.
+NCU_TRAFFIC = {"source_sha16": "6d32bde14398b1f2", "bytes_per_launch": 30554112 + 14575104,
+               "profile": "profiles/msa_flood_lp1054_b65536_fp32.md"}
+
+WORKLOAD = "LP-1054 H_Z (465x1054, E=3720), iid X noise p=0.01..0.05, B=65536/step, max 50 it, alpha 0.75"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp32", "int16"], default="fp32")
+    ap.add_argument("--batch", type=int, default=BATCH)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-latency", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--latency-shots", type=int, default=LAT_SHOTS)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def kernel_traffic():
+    import hashlib
+    src = os.path.join(ROOT, "paper_2508_07879_gb300", "csrc", "msa_kernel.cuh")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return NCU_TRAFFIC["bytes_per_launch"] if sha == NCU_TRAFFIC["source_sha16"] else None
+
+
+def make_batches(batch: int, first_shot: int):
+    from paper_2508_07879_gb300 import workloads as w
+    code = w.lp_code(1054)
+    out = []
+    for p, seed in zip(P_GRID, SEEDS):
+        b = w.x_error_batch(code, p, batch, seed, first_shot=first_shot)
+        out.append(b)
+    return code, out
+
+
+# ------------------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ------------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------------
+# CPU baseline / reference arm: the oracle as it stands, all host cores
+# ------------------------------------------------------------------------------------------------
+def oracle_rate(batches, shots_per_batch: int, precision: str, threads: int):
+    import oracle
+    oprec = {"fp32": "f32", "int16": "i16"}[precision]
+    total = 0
+    t0 = time.perf_counter()
+    for b in batches:
+        syn = b.syndromes[:shots_per_batch]
+        oracle.msa(b.h.row_ptr, b.h.col_idx, b.h.m, b.h.n, syn, b.prior, MAX_ITER, ALPHA, oprec,
+                   True, threads=threads)
+        total += syn.shape[0]
+    dt = time.perf_counter() - t0
+    return total / dt, total, dt
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    threads = os.cpu_count() or 1
+    per_step = 256
+    code, batches = make_batches(max(per_step * 4, 4096), 0)
+    import oracle
+    oracle.build()
+    oprec = {"fp32": "f32", "int16": "i16"}[args.precision]
+
+    def step(i):
+        b = batches[i % len(batches)]
+        lo = (i // len(batches)) * per_step % (b.syndromes.shape[0] - per_step + 1)
+        oracle.msa(b.h.row_ptr, b.h.col_idx, b.h.m, b.h.n, b.syndromes[lo:lo + per_step], b.prior,
+                   MAX_ITER, ALPHA, oprec, True, threads=threads)
+
+    for i in range(args.warmup):
+        step(i)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        step(i)
+    dt = time.perf_counter() - t0
+    value = args.steps * per_step / dt
+    line = {
+        "impl": "reference", "metric": "syndromes/sec", "value": value, "unit": "syndromes/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"fp32": "f32", "int16": "i16"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "reference_step": f"{per_step} shots on the CPU oracle"},
+        "cpu_baseline": {"value": value, "unit": "syndromes/s", "cores": threads, "kind": "oracle",
+                         "sample": f"{args.steps} steps x {per_step} shots cycling p=0.01..0.05"},
+        "e2e": {"value": value, "unit": "syndromes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------------------------
+# our arm
+# ------------------------------------------------------------------------------------------------
+def run_ours(args, rank, world, local):
+    import torch
+    import torch.distributed as dist
+    from paper_2508_07879_gb300 import build as libbuild
+    libbuild.build()
+    from paper_2508_07879_gb300 import qldpc
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    B = args.batch
+    code, batches = make_batches(B, first_shot=rank * B)     # each rank its own shots (weak scaling)
+    h = batches[0].h
+    graph = qldpc.Graph.from_csr(h)
+    dev = torch.device("cuda", local)
+    syn_d = [torch.from_numpy(b.syndromes).to(dev) for b in batches]
+    pri_d = [torch.from_numpy(b.prior).to(dev) for b in batches]
+    out = (torch.empty((B, h.n), dtype=torch.uint8, device=dev),
+           torch.empty(B, dtype=torch.int32, device=dev),
+           torch.empty(B, dtype=torch.uint8, device=dev), None)
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.synchronize()
+
+    # total iterations per batch (deterministic): the units of the algorithmic op count
+    iters_per_batch = []
+    with torch.cuda.stream(stream):
+        for i in range(len(batches)):
+            qldpc.decode(graph, syn_d[i], pri_d[i], MAX_ITER, ALPHA, args.precision, out=out, stream=stream)
+            stream.synchronize()
+            iters_per_batch.append(int(out[1].to(torch.int64).sum().item()))
+
+    def step(i):
+        j = i % len(batches)
+        qldpc.decode(graph, syn_d[j], pri_d[j], MAX_ITER, ALPHA, args.precision, out=out, stream=stream)
+
+    for i in range(args.warmup):
+        step(i)
+    stream.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for i in range(args.steps):
+            step(i)
+        e1.record(stream)
+        stream.synchronize()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    ms_per_step = ms / args.steps
+    value = world * B * args.steps / (ms / 1e3)
+    launches = args.steps
+
+    # roofline of the decoder kernel (one launch per step)
+    sum_iters = sum(iters_per_batch[i % len(batches)] for i in range(args.steps))
+    ops = OPS_PER_EDGE_ITER * h.nnz * sum_iters / args.steps          # per launch
+    achieved = ops / (ms_per_step / 1e3) / 1e12                        # Tops/s
+    props = torch.cuda.get_device_properties(dev)
+    clocks = clk.summary()
+    max_mhz = clocks["sm_max_mhz"] or 2070.0
+    peak = props.multi_processor_count * ALU_LANES_PER_SM * max_mhz * 1e6 / 1e12
+    roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3),
+                "unit": "Tops/s", "frac": round(achieved / peak, 4),
+                "traffic": kernel_traffic() if B == BATCH and args.precision == "fp32" else None,
+                "kernel": "msa_flood_kernel", "ops_per_launch": ops,
+                "units": "10 ALU ops per edge per iteration x E=3720 x iterations run",
+                "peak_basis": f"{props.multi_processor_count} SMs x {ALU_LANES_PER_SM} lanes x {max_mhz:.0f} MHz (max SM clock)",
+                "hbm_algorithmic_gbs": round((h.m + h.n + 5) * B / (ms_per_step / 1e3) / 1e9, 2),
+                "hbm_peak_gbs_measured": 6758.9}
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = measure_e2e(qldpc, graph, batches, args, B, world, dev)
+    latency = None
+    if not args.no_latency and rank == 0:
+        latency = measure_latency(qldpc, graph, code, args)
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0 and world == 1:
+        threads = os.cpu_count() or 1
+        rate, n, dt = oracle_rate(batches, 2048, args.precision, threads)
+        cpu = {"value": rate, "unit": "syndromes/s", "cores": threads, "kind": "oracle",
+               "sample": f"{n} shots (2048 per p at p=0.01..0.05) of the same batches, {dt:.1f} s wall"}
+
+    if rank == 0:
+        line = {
+            "metric": "syndromes/sec", "value": value, "unit": "syndromes/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "int16": "i16"}[args.precision], "data": "synthetic",
+            "config": {"workload": WORKLOAD, "global_batch": B * world, "precision": args.precision,
+                       "l2": "inputs rotate over 5 batches (152 MB) + 69 MB outputs per step > 129 MB L2",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "latency": latency,
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "mean_iters": sum(iters_per_batch) / (len(iters_per_batch) * B),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def measure_e2e(qldpc, graph, batches, args, B, world, dev):
+    import torch
+    import torch.distributed as dist
+    h = batches[0].h
+    pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
+    syn_h = [pin(b.syndromes) for b in batches]
+    pri_h = [b.prior.copy() for b in batches]
+    err = torch.empty((B, h.n), dtype=torch.uint8).pin_memory().numpy()
+    it = torch.empty(B, dtype=torch.int32).pin_memory().numpy()
+    ok = torch.empty(B, dtype=torch.uint8).pin_memory().numpy()
+    graph.reserve(B)
+    steps = max(3, min(args.steps, 40))
+    for i in range(3):
+        qldpc.decode_host(graph, syn_h[i % 5], pri_h[i % 5], MAX_ITER, ALPHA, args.precision, out=(err, it, ok))
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for i in range(steps):
+        qldpc.decode_host(graph, syn_h[i % 5], pri_h[i % 5], MAX_ITER, ALPHA, args.precision, out=(err, it, ok))
+    dt = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([dt], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dt = float(t.item())
+    return {"value": world * B * steps / dt, "unit": "syndromes/s",
+            "h2d_bytes_per_step": B * h.m + h.n * 4, "d2h_bytes_per_step": B * (h.n + 4 + 1),
+            "steps": steps, "path": "qldpc_decode_host, pinned host buffers, synchronous per step"}
+
+
+def measure_latency(qldpc, graph, code, args):
+    """B = 1 end-to-end: pinned syndrome -> H2D -> decode -> D2H -> host (host clock per shot)."""
+    import torch
+    from paper_2508_07879_gb300 import workloads as w
+    shots = args.latency_shots
+    warm = min(LAT_WARMUP, max(shots // 10, 10))
+    b = w.x_error_batch(code, LAT_P, shots + warm, seed=4003)
+    h = b.h
+    syn = torch.from_numpy(b.syndromes).pin_memory().numpy()
+    err = torch.empty((1, h.n), dtype=torch.uint8).pin_memory().numpy()
+    it = torch.empty(1, dtype=torch.int32).pin_memory().numpy()
+    ok = torch.empty(1, dtype=torch.uint8).pin_memory().numpy()
+    prior = b.prior.copy()
+    lat = {}
+    for prec in ("fp32", "int16"):
+        ts = np.empty(shots + warm)
+        iters = np.empty(shots + warm, dtype=np.int32)
+        for i in range(shots + warm):
+            row = syn[i:i + 1]
+            t0 = time.perf_counter_ns()
+            qldpc.decode_host(graph, row, prior, MAX_ITER, ALPHA, prec, out=(err, it, ok))
+            ts[i] = (time.perf_counter_ns() - t0) / 1e3
+            iters[i] = it[0]
+        x = ts[warm:]
+        lat[prec] = {"p50_us": float(np.percentile(x, 50)), "p99_us": float(np.percentile(x, 99)),
+                     "p999_us": float(np.percentile(x, 99.9)), "mean_us": float(x.mean()),
+                     "max_iter_shots": int((iters[warm:] == MAX_ITER).sum())}
+    return {"metric": "p99 single-shot decode latency", "unit": "us", "threshold_us": THRESHOLD_US,
+            "code": "LP-1054 H_Z", "p": LAT_P, "shots": shots, "max_iter": MAX_ITER,
+            "path": "qldpc_decode_host from Python, pinned buffers, host clock, B=1", **lat}
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

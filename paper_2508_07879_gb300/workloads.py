@@ -28,6 +28,7 @@ s_Z = H_X e_Z^T with H_X.
 from __future__ import annotations
 
 import math
+import os
 from dataclasses import dataclass
 
 import numpy as np
@@ -279,10 +280,27 @@ def prior_llr(p: float) -> float:
     return math.log((1.0 - p) / p)
 
 
+def _chunked(fn, shots: int, first_shot: int, chunk: int = 4096):
+    """Evaluate fn(first, count) over shot chunks on a thread pool (numpy releases the GIL);
+    chunking does not change the result because every draw is keyed by its absolute shot index."""
+    from concurrent.futures import ThreadPoolExecutor
+    starts = list(range(0, shots, chunk))
+    if len(starts) <= 1:
+        return fn(first_shot, shots)
+    workers = min(len(starts), os.cpu_count() or 1)
+    with ThreadPoolExecutor(workers) as ex:
+        parts = list(ex.map(lambda s0: fn(first_shot + s0, min(chunk, shots - s0)), starts))
+    if isinstance(parts[0], tuple):
+        return tuple(np.concatenate([p[i] for p in parts]) for i in range(len(parts[0])))
+    return np.concatenate(parts)
+
+
 def iid_x_errors(n: int, p: float, shots: int, seed: int, first_shot: int = 0) -> np.ndarray:
     """Bernoulli(p) bit flips, e[b, q] = [u(seed, first_shot + b, q) < p]  (uint8 [shots, n])."""
-    u = uniform01(seed, np.arange(first_shot, first_shot + shots), np.arange(n))
-    return (u < p).astype(np.uint8)
+    def draw(s0, count):
+        u = uniform01(seed, np.arange(s0, s0 + count), np.arange(n))
+        return (u < p).astype(np.uint8)
+    return _chunked(draw, shots, first_shot)
 
 
 def depolarizing_errors(n: int, p: float, shots: int, seed: int, first_shot: int = 0):
@@ -290,11 +308,13 @@ def depolarizing_errors(n: int, p: float, shots: int, seed: int, first_shot: int
 
     e_X marks X or Y, e_Z marks Z or Y.  Each part has marginal probability 2p/3.
     """
-    u = uniform01(seed, np.arange(first_shot, first_shot + shots), np.arange(n))
-    x = u < p / 3.0
-    y = (u >= p / 3.0) & (u < 2.0 * p / 3.0)
-    z = (u >= 2.0 * p / 3.0) & (u < p)
-    return (x | y).astype(np.uint8), (z | y).astype(np.uint8)
+    def draw(s0, count):
+        u = uniform01(seed, np.arange(s0, s0 + count), np.arange(n))
+        x = u < p / 3.0
+        y = (u >= p / 3.0) & (u < 2.0 * p / 3.0)
+        z = (u >= 2.0 * p / 3.0) & (u < p)
+        return (x | y).astype(np.uint8), (z | y).astype(np.uint8)
+    return _chunked(draw, shots, first_shot)
 
 
 @dataclass(frozen=True)

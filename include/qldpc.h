@@ -170,6 +170,40 @@ QLDPC_API int qldpc_decode_host(qldpc_graph *g, const uint8_t *h_syndromes, int3
 /* Static, human-readable name of a status code. */
 QLDPC_API const char *qldpc_status_string(int status);
 
+/* Size of the library's static device scratch used by qldpc_decode_host_noalloc (4 MiB). */
+enum { QLDPC_NOALLOC_SCRATCH_BYTES = 4 * 1024 * 1024 };
+
+/*
+ * qldpc_decode_host without any device allocation.  (No counterpart in the paper: this is a
+ * deployment aid.)
+ *
+ * Some callers cannot call cudaMalloc once they are running: a real-time control process that
+ * fixes its device memory at start-up because an allocation can synchronize the device and take
+ * unbounded time inside the syndrome cycle, or a plug-in whose host application owns all device
+ * memory.  qldpc_decode_host allocates device staging on first use (and grows it); this entry
+ * point instead stages through one file-scope device array of QLDPC_NOALLOC_SCRATCH_BYTES that
+ * every GPU loading the library holds until the process exits.  It calls no cudaMalloc, cudaFree or
+ * allocating library routine.
+ *
+ * Arguments, outputs and the synchronous behaviour are those of qldpc_decode_host (host buffers
+ * in, host buffers out, stream synchronized before returning).  The prior is copied on every call.
+ * The batch must fit the scratch: with a(x) = x rounded up to 256 bytes,
+ *   a(4n) + a(batch*m) + a(batch*n) + a(4*batch) + a(batch) <= QLDPC_NOALLOC_SCRATCH_BYTES
+ * (e.g. up to 2700 shots of a 465 x 1054 graph); a larger batch returns QLDPC_ERR_UNSUPPORTED
+ * and enqueues nothing.  Invalid arguments return QLDPC_ERR_INVALID_ARG before anything is enqueued.
+ *
+ * The first call on each device resolves the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.  All calls in the process
+ * share the one array and it keeps the last call's contents; nothing in it needs to start at zero
+ * because every byte a call reads is first written by that call.  Calls whose work overlaps on the
+ * GPU (other threads, other streams) race on the array: serialize them.
+ */
+QLDPC_API int qldpc_decode_host_noalloc(const qldpc_graph *g, const uint8_t *h_syndromes,
+                                        int32_t batch, const float *h_prior, int32_t max_iter,
+                                        float alpha, uint8_t *h_err, int32_t *h_iters,
+                                        uint8_t *h_ok, int32_t precision, uint32_t flags,
+                                        void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -24,7 +24,7 @@ NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibilit
               "-Xptxas", "-v", "--fmad=false"]
 CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-fvisibility=hidden", "-Wall", "-Wextra"]
 
-KERNEL_SOURCES = ["msa_f32.cu", "msa_i16.cu"]
+KERNEL_SOURCES = ["msa_f32.cu", "msa_i16.cu", "qldpc_noalloc.cu"]
 HOST_SOURCES = ["qldpc_host.cpp"]
 HEADERS = ["msa_launch.h", "msa_kernel.cuh"]
 

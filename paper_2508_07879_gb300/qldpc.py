@@ -57,6 +57,7 @@ _SIGNATURES = {
                            _i32, _u32, _p], ctypes.c_int),
     "qldpc_decode_host": ([_p, _p, _i32, _p, _i32, _f32, _p, _p, _p, _i32, _u32, _p], ctypes.c_int),
     "qldpc_status_string": ([ctypes.c_int], ctypes.c_char_p),
+    "qldpc_decode_host_noalloc": ([_p, _p, _i32, _p, _i32, _f32, _p, _p, _p, _i32, _u32, _p], ctypes.c_int),
 }
 for _name, (_args, _res) in _SIGNATURES.items():
     _fn = getattr(_lib, _name)
@@ -75,6 +76,8 @@ qldpc_decode_ex = _lib.qldpc_decode_ex
 qldpc_decode_pair = _lib.qldpc_decode_pair
 qldpc_decode_host = _lib.qldpc_decode_host
 qldpc_status_string = _lib.qldpc_status_string
+qldpc_decode_host_noalloc = _lib.qldpc_decode_host_noalloc
+QLDPC_NOALLOC_SCRATCH_BYTES = 4 * 1024 * 1024
 
 
 class QldpcError(RuntimeError):

@@ -16,6 +16,7 @@
  *   Q_n     = gamma_n + sum_{i in S_c(n)} r_{i,n};    e_hat_n = [Q_n < 0]
  *   sign(x) = -1 iff x < 0.  The stop test H e_hat^T = s runs before the first iteration and
  *   after every iteration; decoding stops at the first success or after max_iter iterations.
+ *   (FP32 treats a prior of -0 as +0; this can change only the sign of a zero a-posteriori LLR.)
  *
  * Precisions:
  *   QLDPC_FP32  IEEE binary32 messages, every add and multiply rounded to nearest (no fusion).
@@ -74,7 +75,8 @@ enum {
 /* Limits of the kernels in this build. */
 enum {
     QLDPC_MAX_ROW_DEGREE = 32,    /* check-node degree d_c */
-    QLDPC_MAX_COL_DEGREE = 16     /* variable-node degree d_v */
+    QLDPC_MAX_COL_DEGREE = 16,    /* variable-node degree d_v */
+    QLDPC_MAX_CHECKS = 65535      /* rows m */
 };
 
 /*
@@ -86,8 +88,9 @@ enum {
  * The caller keeps its arrays; the library copies what it needs.
  * INVALID_ARG: null pointer, m or n <= 0, malformed row_ptr, column out of range, repeated column
  *              in a row, or a row of degree < 2 (the check update needs two neighbours).
- * UNSUPPORTED: a row degree > QLDPC_MAX_ROW_DEGREE, a column degree > QLDPC_MAX_COL_DEGREE, or one
- *              shot's working set larger than the device's shared memory per block.
+ * UNSUPPORTED: a row degree > QLDPC_MAX_ROW_DEGREE, a column degree > QLDPC_MAX_COL_DEGREE,
+ *              m > QLDPC_MAX_CHECKS, or one shot's working set (messages, priors, LLRs and parity
+ *              words) larger than the device's shared memory per block.
  * CUDA / OOM:  no usable device or the upload failed.
  */
 QLDPC_API int qldpc_graph_create(const int32_t *row_ptr, const int32_t *col_idx, int32_t m, int32_t n,
@@ -107,10 +110,21 @@ QLDPC_API void qldpc_graph_destroy(qldpc_graph *g);
 QLDPC_API int qldpc_graph_dims(const qldpc_graph *g, int32_t *m, int32_t *n, int32_t *nnz,
                      int32_t *max_row_degree, int32_t *max_col_degree);
 
-/* Override the launch shape chosen by the library: threads per block (a multiple of 32 in
- * [32, 1024]) and resident blocks per SM used to size the grid; 0 keeps the automatic choice.
- * INVALID_ARG if out of range, UNSUPPORTED if the shape cannot be resident. */
-QLDPC_API int qldpc_graph_set_launch(qldpc_graph *g, int32_t threads_per_block, int32_t blocks_per_sm);
+/* Kernels (qldpc_graph_set_launch). */
+enum {
+    QLDPC_KERNEL_AUTO = 0,      /* latency kernel when every shot gets its own SM, else batch kernel */
+    QLDPC_KERNEL_BATCH = 1,     /* throughput kernel: thread per check / per variable, persistent blocks */
+    QLDPC_KERNEL_LATENCY = 2    /* single-shot kernel: per-thread state in registers, one block per
+                                   shot; needs m <= 2*threads and n <= 2*threads, threads <= 640 */
+};
+
+/* Override the library's launch choice for this graph: the kernel, its threads per block (a
+ * multiple of 32 in [32, 1024], 0 = automatic) and the resident blocks per SM used to size the
+ * grid (0 = from occupancy).  QLDPC_KERNEL_AUTO takes no shape (both 0) and restores the default.
+ * INVALID_ARG if out of range, UNSUPPORTED if the shape cannot run this graph or the residency is
+ * not achievable.  Results never depend on the launch choice. */
+QLDPC_API int qldpc_graph_set_launch(qldpc_graph *g, int32_t kernel, int32_t threads_per_block,
+                                     int32_t blocks_per_sm);
 
 /* Pre-size the device staging that qldpc_decode_host uses, for up to max_batch shots. */
 QLDPC_API int qldpc_graph_reserve(qldpc_graph *g, int32_t max_batch);
@@ -159,8 +173,11 @@ QLDPC_API int qldpc_decode_pair(const qldpc_graph *g_z, const qldpc_graph *g_x,
  * host-to-device and device-to-host transfers).  Copies syndromes (host uint8[batch*m]) and the
  * prior (host float[n], uploaded only when it changed since the last call) into the graph's device
  * staging, decodes on `stream`, copies e_hat, iterations and ok back into the host buffers and
- * synchronizes the stream before returning.  Page-locked (pinned) host buffers give the fastest
- * copies.  Calls on the same graph are serialized by a lock inside the graph.
+ * synchronizes the stream before returning.  When the syndrome and output buffers each lie inside
+ * one page-locked allocation registered with CUDA (cudaHostAlloc, cudaMallocHost,
+ * cudaHostRegister; torch pin_memory), no copy is issued: the kernel reads the syndromes from and
+ * writes the results to host memory directly, and the call is one launch plus one synchronize.
+ * Calls on the same graph are serialized by a lock inside the graph.
  */
 QLDPC_API int qldpc_decode_host(qldpc_graph *g, const uint8_t *h_syndromes, int32_t batch,
                       const float *h_prior, int32_t max_iter, float alpha,

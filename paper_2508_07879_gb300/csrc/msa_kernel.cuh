@@ -1,24 +1,36 @@
 // Flooding normalized min-sum decoder driven by a syndrome -- Algorithm 1 ("MSA for
 // syndrome-based LDPC decoding"), Sec. 2 of arXiv 2508.07879 -- for sm_103a.
 //
-// Mapping (a GB300 design, not the paper's per-iteration launches over global memory):
-//   * one thread block per shot, persistent over shots (block b takes shots b, b + gridDim.x, ...);
-//     gridDim.y selects the X or Z problem of a pair decode (the paper's concatenated X+Z kernel);
-//   * all edge messages of the shot live in shared memory, in place: the check step overwrites
+// Two kernels share the arithmetic below and one shared-memory layout:
+//
+//   msa_batch_kernel    throughput: one block per shot, persistent over the batch, one thread per
+//                       check in the check step and one thread per variable in the variable step;
+//                       edge lists are read through the read-only path (L1-resident).
+//   msa_latency_kernel  single-shot latency: the same steps, but every thread keeps its edge
+//                       lists, degrees, priors and a-posteriori LLRs in registers for the whole
+//                       decode, so an iteration touches only shared memory.
+//
+// Layout (a GB300 design, not the paper's per-iteration launches over global memory):
+//   * every edge message of a shot lives in shared memory, in place: the check step overwrites
 //     q_{m,n} with r_{m,n}, the variable step overwrites r with the next q.  Slots are check-major
-//     (slot j*M + m), so the check step reads and writes 32 consecutive words per warp;
-//   * the variable step also stores its decision e_n into every slot of its edges, so the stop
-//     test H e^T = s is folded into the next check step (each check XORs the decisions of its
-//     slots) and decided by one __syncthreads_and.  An iteration costs two block barriers instead of
-//     the paper's four (Fig. 2 caption);
-//   * the graph is read through the read-only path (L1-resident: one copy per SM for all blocks).
+//     (slot j*M + m, 4 bytes FP32 / 2 bytes INT16), so 32 consecutive checks touch 32 consecutive
+//     slots;
+//   * the stop test H e^T = s is kept incrementally: check m owns a parity word
+//     (bit 1 = s_m, bit 0 = s_m XOR the decisions of its variables); a variable whose decision
+//     flips XORs bit 0 of its checks' words (shared-memory atomics, exact).  The next check step
+//     reads one word per check and the block settles the test with one __syncthreads_and, so an
+//     iteration costs two block barriers (the paper's kernel: four);
+//   * the check step keeps no argmin: min over S_v(m)\n is min2 where |q_n| equals min1 and min1
+//     elsewhere (min2 = min1 when the minimum is shared), which is exact.
 //
 // Arithmetic is operation-for-operation that of the CPU oracle:
-//   r = sign * (alpha * min_{j != n} |q_j|)        min_{j != n} taken as min1 or min2 of the row
-//   q_{m,n} = gamma_n + sum_{i != m} r_{i,n}        ascending check order, prefix/suffix reuse
+//   r = sign * (alpha * min_{j != n} |q_j|)
+//   q_{m,n} = gamma_n + sum_{i != m} r_{i,n}        ascending check order, prefixes reused
 //   Q_n = gamma_n + sum_i r_{i,n}                   ascending check order
 // so FP32 results are bit-identical (every add/multiply is an explicit round-to-nearest intrinsic,
 // nothing is fused or reassociated) and INT16 results are exact integer arithmetic.
+// (A lane-per-edge check step with warp-shuffle reductions, a two-lanes-per-check step and a
+// thread-block-cluster split of one shot over several SMs were all measured slower on GB300.)
 #pragma once
 
 #include <cstdint>
@@ -31,34 +43,41 @@ namespace qldpc {
 namespace kern {
 
 // ---------------------------------------------------------------------------------------------
-// Precision policies
+// Precision policies: arithmetic and the slot format
 // ---------------------------------------------------------------------------------------------
 struct F32 {
-    using msg_t = float;    // a message stored in a slot
     using acc_t = float;    // variable-node sums, Q_n
     using mag_t = float;    // |q| and scaled minima
-    static __device__ __forceinline__ acc_t quantize(float g) { return g; }
-    static __device__ __forceinline__ acc_t add(acc_t a, msg_t b) { return __fadd_rn(a, b); }
-    static __device__ __forceinline__ msg_t to_msg(acc_t a) { return a; }
+    using msg_t = float;    // a slot
+    // g + 0 is g except that -0 becomes +0; with no -0 prior no message is ever -0 (a rounded sum
+    // is -0 only when every term is), so the sign bit of a message equals [message < 0].
+    static __device__ __forceinline__ acc_t quantize(float g) { return __fadd_rn(g, 0.0f); }
+    static __device__ __forceinline__ acc_t add(acc_t a, acc_t b) { return __fadd_rn(a, b); }
     static __device__ __forceinline__ bool neg(float x) { return x < 0.0f; }
-    static __device__ __forceinline__ mag_t mag(msg_t x) { return fabsf(x); }
+    static __device__ __forceinline__ mag_t mag(acc_t x) { return fabsf(x); }
     static __device__ __forceinline__ mag_t mag_init() { return __int_as_float(0x7f800000); }
-    static __device__ __forceinline__ mag_t mag_min(mag_t a, mag_t b) { return fminf(a, b); }
+    static __device__ __forceinline__ mag_t mn(mag_t a, mag_t b) { return fminf(a, b); }
+    static __device__ __forceinline__ mag_t mx(mag_t a, mag_t b) { return fmaxf(a, b); }
     static __device__ __forceinline__ mag_t scale(mag_t m, const LaunchParams &p)
     {
         return __fmul_rn(p.alpha, m);
     }
-    static __device__ __forceinline__ msg_t with_sign(mag_t m, uint32_t negative)
+    // bit 31 = [x < 0] (valid because no message is -0)
+    static __device__ __forceinline__ uint32_t sign_word(acc_t x) { return __float_as_uint(x); }
+    // sign * m with sign = (-1)^{negall} * sign(x): the sign bit flipped, one logic operation
+    // (-m is exact, also -0 for m = 0 as in the oracle)
+    static __device__ __forceinline__ acc_t signed_like(mag_t m, acc_t x, uint32_t negall)
     {
-        return negative ? -m : m;
+        return __uint_as_float(__float_as_uint(m) ^ (__float_as_uint(x) & 0x80000000u) ^ (negall << 31));
     }
     static __device__ __forceinline__ float post(acc_t a) { return a; }
+    static __device__ __forceinline__ msg_t to_msg(acc_t q) { return q; }
 };
 
 struct I16 {
-    using msg_t = int16_t;
     using acc_t = int32_t;
     using mag_t = int32_t;
+    using msg_t = int16_t;
     // gamma_q = clamp(round_half_away(gamma * 2^8), -32767, 32767); gamma*256 is exact in binary32
     static __device__ __forceinline__ acc_t quantize(float g)
     {
@@ -66,157 +85,158 @@ struct I16 {
         t = fminf(fmaxf(t, -32767.0f), 32767.0f);
         return static_cast<int32_t>(t);
     }
-    static __device__ __forceinline__ acc_t add(acc_t a, msg_t b) { return a + int32_t(b); }
-    static __device__ __forceinline__ msg_t to_msg(acc_t a)
-    {
-        return static_cast<int16_t>(max(-32767, min(32767, a)));
-    }
+    static __device__ __forceinline__ acc_t add(acc_t a, acc_t b) { return a + b; }
     static __device__ __forceinline__ bool neg(int32_t x) { return x < 0; }
-    static __device__ __forceinline__ mag_t mag(msg_t x) { return abs(int32_t(x)); }
+    static __device__ __forceinline__ mag_t mag(acc_t x) { return abs(x); }
     static __device__ __forceinline__ mag_t mag_init() { return 0x7fffffff; }
-    static __device__ __forceinline__ mag_t mag_min(mag_t a, mag_t b) { return min(a, b); }
+    static __device__ __forceinline__ mag_t mn(mag_t a, mag_t b) { return min(a, b); }
+    static __device__ __forceinline__ mag_t mx(mag_t a, mag_t b) { return max(a, b); }
     // |r| = floor(min * alpha_q / 2^15); min <= 32767 and alpha_q <= 2^15 keep it in 31 bits
     static __device__ __forceinline__ mag_t scale(mag_t m, const LaunchParams &p)
     {
         return (m * p.alpha_q) >> 15;
     }
-    static __device__ __forceinline__ msg_t with_sign(mag_t m, uint32_t negative)
+    static __device__ __forceinline__ uint32_t sign_word(acc_t x) { return uint32_t(x); }
+    static __device__ __forceinline__ acc_t signed_like(mag_t m, acc_t x, uint32_t negall)
     {
-        return static_cast<int16_t>(negative ? -m : m);
+        const int32_t neg = int32_t(negall ^ (uint32_t(x) >> 31));   // 0 or 1
+        return (m ^ -neg) + neg;
     }
     static __device__ __forceinline__ float post(acc_t a) { return float(a) * 0.00390625f; }
+    static __device__ __forceinline__ msg_t to_msg(acc_t q) { return int16_t(max(-32767, min(32767, q))); }
 };
 
-// ---------------------------------------------------------------------------------------------
-// Check-node step (Alg. 1, CN processing) fused with the stop test of the previous decisions.
-// Returns 1 iff the decisions stored in this check's slots satisfy s_m.
-// ---------------------------------------------------------------------------------------------
-template <class P, int DC>
-__device__ __forceinline__ int check_step(int c, int M, int deg, uint32_t s, bool update,
-                                          typename P::msg_t *__restrict__ msg,
-                                          const uint8_t *__restrict__ dec,
-                                          const LaunchParams &p)
+template <class P>
+__device__ __forceinline__ typename P::acc_t load_msg(const typename P::msg_t *s, uint32_t i)
 {
-    using msg_t = typename P::msg_t;
+    return typename P::acc_t(s[i]);
+}
+
+// Flip the decision bit of one check's parity word (exact: integer XOR in shared memory).
+__device__ __forceinline__ void flip_check(uint32_t *parity, uint32_t m) { atomicXor(parity + m, 1u); }
+
+// Edge-list entry: position j of the edge in its check's row (bits 16..20), check m (bits 0..15).
+__device__ __forceinline__ uint32_t slot_of(uint32_t e, uint32_t M) { return (e >> 16) * M + (e & 0xffffu); }
+__device__ __forceinline__ uint32_t check_of(uint32_t e) { return e & 0xffffu; }
+
+// ---------------------------------------------------------------------------------------------
+// Check-node step (Alg. 1, CN processing) of one check, fused with the stop test of the previous
+// decisions.  Returns 1 iff the check's parity word says s_m is satisfied.
+// UNIFORM: every row has exactly DC edges; otherwise deg <= DC.
+// ---------------------------------------------------------------------------------------------
+template <class P, int DC, bool UNIFORM>
+__device__ __forceinline__ int check_step(int c, int M, int deg, uint32_t pw, bool update,
+                                          typename P::msg_t *__restrict__ slots, const LaunchParams &p)
+{
+    using acc_t = typename P::acc_t;
     using mag_t = typename P::mag_t;
-    msg_t q[DC];
-    uint32_t par = s;
-#pragma unroll
-    for (int j = 0; j < DC; ++j) {
-        if (j < deg) {
-            q[j] = msg[j * M + c];
-            par ^= dec[j * M + c];
-        }
-    }
     if (update) {
-        uint32_t mask = 0, negall = s;
+        acc_t q[DC];
+        uint32_t sx = 0;
         mag_t m1 = P::mag_init(), m2 = P::mag_init();
-        int idx = 0;
 #pragma unroll
         for (int j = 0; j < DC; ++j) {
-            if (j < deg) {
-                const uint32_t sg = P::neg(q[j]) ? 1u : 0u;
-                mask |= sg << j;
-                negall ^= sg;
+            if (UNIFORM || j < deg) {
+                q[j] = load_msg<P>(slots, uint32_t(j * M + c));
+                sx ^= P::sign_word(q[j]);          // bit 31: parity of the signs
                 const mag_t a = P::mag(q[j]);
-                if (a < m1) {           // strict: a tie keeps the lower slot as the argmin
-                    m2 = m1;
-                    m1 = a;
-                    idx = j;
-                } else {
-                    m2 = P::mag_min(m2, a);
-                }
+                m2 = P::mn(m2, P::mx(m1, a));     // two smallest magnitudes, with multiplicity
+                m1 = P::mn(m1, a);
             }
         }
-        const mag_t r1 = P::scale(m1, p);   // alpha * min over the other slots, j != idx
-        const mag_t r2 = P::scale(m2, p);   // alpha * min over the other slots, j == idx
+        const uint32_t negall = ((pw >> 1) ^ (sx >> 31)) & 1u;   // (-1)^{s_m} * prod of all signs
+        const mag_t r1 = P::scale(m1, p);                        // alpha * min over the others
+        const mag_t r2 = P::scale(m2, p);                        // ... when |q_j| is the minimum
 #pragma unroll
         for (int j = 0; j < DC; ++j) {
-            if (j < deg) msg[j * M + c] = P::with_sign(j == idx ? r2 : r1, (negall ^ (mask >> j)) & 1u);
+            if (UNIFORM || j < deg)
+                slots[j * M + c] = typename P::msg_t(P::signed_like(P::mag(q[j]) == m1 ? r2 : r1, q[j], negall));
         }
     }
-    return (par & 1u) == 0;
+    return (pw & 1u) == 0;
 }
 
 // ---------------------------------------------------------------------------------------------
-// Variable-node step (Alg. 1, VN processing + a-posteriori LLR + tentative decision) for a
-// variable of degree exactly D.  q_k = gamma + sum_{i != k} r_i in ascending order:
-// q_k = ((pre_k + r_{k+1}) + r_{k+2}) + ...  with pre_k = ((gamma + r_0) + r_1) + ... + r_{k-1}.
+// Variable-node step (Alg. 1, VN processing + a-posteriori LLR + tentative decision) of a
+// variable of degree exactly D whose edges are e[0..D).  q_k = gamma + sum_{i != k} r_i in
+// ascending order: q_k = ((pre_k + r_{k+1}) + r_{k+2}) + ...  with pre_k = ((gamma + r_0) + r_1)
+// + ... + r_{k-1}.  Stores every q_k, flips the parity bit of its checks when the decision
+// [Q < 0] differs from `prev`, and returns Q.
 // ---------------------------------------------------------------------------------------------
 template <class P, int D>
-__device__ __forceinline__ void var_step_exact(int v, int N, const uint32_t *__restrict__ vslot,
-                                               typename P::acc_t gamma,
-                                               typename P::msg_t *__restrict__ msg,
-                                               uint8_t *__restrict__ dec,
-                                               typename P::acc_t *__restrict__ Qs)
+__device__ __forceinline__ typename P::acc_t var_step_exact(const uint32_t *e, uint32_t M, typename P::acc_t gamma,
+                                                            bool prev, typename P::msg_t *__restrict__ slots,
+                                                            uint32_t *__restrict__ parity)
 {
     using acc_t = typename P::acc_t;
-    using msg_t = typename P::msg_t;
     if constexpr (D == 0) {
-        Qs[v] = gamma;
+        return gamma;
     } else {
         uint32_t sl[D];
-        msg_t r[D];
+        acc_t r[D];
 #pragma unroll
-        for (int k = 0; k < D; ++k) sl[k] = __ldg(vslot + size_t(k) * N + v);
+        for (int k = 0; k < D; ++k) sl[k] = slot_of(e[k], M);
 #pragma unroll
-        for (int k = 0; k < D; ++k) r[k] = msg[sl[k]];
+        for (int k = 0; k < D; ++k) r[k] = load_msg<P>(slots, sl[k]);
         acc_t pre[D + 1];
         pre[0] = gamma;
 #pragma unroll
         for (int k = 0; k < D; ++k) pre[k + 1] = P::add(pre[k], r[k]);
         const acc_t Q = pre[D];
-        const uint8_t d = P::neg(Q) ? 1 : 0;
 #pragma unroll
         for (int k = 0; k < D; ++k) {
             acc_t q = pre[k];
 #pragma unroll
             for (int i = k + 1; i < D; ++i) q = P::add(q, r[i]);
-            msg[sl[k]] = P::to_msg(q);
-            dec[sl[k]] = d;
+            slots[sl[k]] = P::to_msg(q);
         }
-        Qs[v] = Q;
+        if (P::neg(Q) != prev) {
+#pragma unroll
+            for (int k = 0; k < D; ++k) flip_check(parity, check_of(e[k]));
+        }
+        return Q;
     }
 }
 
-template <class P, int D, int DV>
-__device__ __forceinline__ void var_step_dispatch(int deg, int v, int N, const uint32_t *vslot,
-                                                  typename P::acc_t gamma, typename P::msg_t *msg,
-                                                  uint8_t *dec, typename P::acc_t *Qs)
+#define QLDPC_DEG_CASES(X) X(0) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16)
+
+// Batch variant: the edge list comes from global memory (L1-resident).
+template <class P, int D>
+__device__ __forceinline__ typename P::acc_t var_step_global(int v, int N, uint32_t M, const uint32_t *__restrict__ vslot,
+                                                             typename P::acc_t gamma, bool prev,
+                                                             typename P::msg_t *slots, uint32_t *parity)
 {
-    if constexpr (D <= DV) {
-        if (deg == D) {
-            var_step_exact<P, D>(v, N, vslot, gamma, msg, dec, Qs);
-        } else {
-            var_step_dispatch<P, D + 1, DV>(deg, v, N, vslot, gamma, msg, dec, Qs);
-        }
-    }
+    uint32_t e[D > 0 ? D : 1];
+#pragma unroll
+    for (int k = 0; k < D; ++k) e[k] = __ldg(vslot + size_t(k) * N + v);
+    return var_step_exact<P, D>(e, M, gamma, prev, slots, parity);
 }
 
-// Initialization (Alg. 1): q^(0)_{m,n} = gamma_n on every edge, decisions from the prior.
-template <class P>
-__device__ __forceinline__ void var_init(int v, int N, int deg, const uint32_t *__restrict__ vslot,
-                                         typename P::acc_t gamma, typename P::msg_t *msg,
-                                         uint8_t *dec, typename P::acc_t *Qs)
+template <class P, int DV>
+__device__ __forceinline__ typename P::acc_t var_step_batch(int deg, int v, int N, uint32_t M, const uint32_t *vslot,
+                                                            typename P::acc_t gamma, bool prev,
+                                                            typename P::msg_t *slots, uint32_t *parity)
 {
-    const typename P::msg_t g = P::to_msg(gamma);
-    const uint8_t d = P::neg(gamma) ? 1 : 0;
-    for (int k = 0; k < deg; ++k) {
-        const uint32_t s = __ldg(vslot + size_t(k) * N + v);
-        msg[s] = g;
-        dec[s] = d;
+    switch (deg) {
+#define QLDPC_CASE(D)                                                                           \
+    case D:                                                                                     \
+        if constexpr (D <= DV) return var_step_global<P, D>(v, N, M, vslot, gamma, prev, slots, parity); \
+        break;
+        QLDPC_DEG_CASES(QLDPC_CASE)
+#undef QLDPC_CASE
+    default: break;
     }
-    Qs[v] = gamma;
+    return gamma;
 }
 
 // ---------------------------------------------------------------------------------------------
-// The decoder kernel.
+// Throughput kernel
 // ---------------------------------------------------------------------------------------------
-template <class P, int DC, int DV>
-__global__ void __launch_bounds__(1024) msa_flood_kernel(const LaunchParams p)
+template <class P, int DC, bool UNIFORM, int DV>
+__global__ void __launch_bounds__(1024, 1) msa_batch_kernel(const LaunchParams p)
 {
-    using msg_t = typename P::msg_t;
     using acc_t = typename P::acc_t;
+    using msg_t = typename P::msg_t;
 
     const Problem pr = blockIdx.y == 0 ? p.prob[0] : p.prob[1];
     const int M = pr.g.m, N = pr.g.n;
@@ -226,9 +246,8 @@ __global__ void __launch_bounds__(1024) msa_flood_kernel(const LaunchParams p)
     const SmemLayout L = smem_layout(M, N, pr.g.dc_max, int(sizeof(msg_t)));
     acc_t *Qs = reinterpret_cast<acc_t *>(smem + L.q_off);
     acc_t *gam = reinterpret_cast<acc_t *>(smem + L.g_off);
-    msg_t *msg = reinterpret_cast<msg_t *>(smem + L.msg_off);
-    uint8_t *dec = smem + L.dec_off;
-    uint8_t *syn = smem + L.syn_off;
+    uint32_t *parity = reinterpret_cast<uint32_t *>(smem + L.par_off);
+    msg_t *slots = reinterpret_cast<msg_t *>(smem + L.slot_off);
 
     // Prior LLRs: loaded once per block, shared by all its shots.
     int bad = 0;
@@ -253,21 +272,37 @@ __global__ void __launch_bounds__(1024) msa_flood_kernel(const LaunchParams p)
             }
             continue;
         }
+        // Initialization (Alg. 1): q^(0) = gamma on every edge; parity words start at s_m and
+        // take the decisions of the prior.
         const uint8_t *s = pr.syn + size_t(b) * M;
-        for (int c = tid; c < M; c += T) syn[c] = s[c] & 1;
-        for (int v = tid; v < N; v += T) var_init<P>(v, N, pr.g.vdeg[v], pr.g.vslot, gam[v], msg, dec, Qs);
+        for (int c = tid; c < M; c += T) parity[c] = (s[c] & 1u) * 3u;
+        __syncthreads();
+        for (int v = tid; v < N; v += T) {
+            const acc_t g = gam[v];
+            const int deg = __ldg(pr.g.vdeg + v);
+            const bool d = P::neg(g);
+            for (int k = 0; k < deg; ++k) {
+                const uint32_t e = __ldg(pr.g.vslot + size_t(k) * N + v);
+                slots[slot_of(e, uint32_t(M))] = P::to_msg(g);
+                if (d) flip_check(parity, check_of(e));
+            }
+            Qs[v] = g;
+        }
         __syncthreads();
 
         int k = 0, all = 0;
         for (;; ++k) {
             const bool last = k >= p.max_iter;
             int ok = 1;
-            for (int c = tid; c < M; c += T)
-                ok &= check_step<P, DC>(c, M, __ldg(pr.g.rdeg + c), syn[c], !last, msg, dec, p);
+            for (int c = tid; c < M; c += T) {
+                const int deg = UNIFORM ? DC : int(__ldg(pr.g.rdeg + c));
+                ok &= check_step<P, DC, UNIFORM>(c, M, deg, parity[c], !last, slots, p);
+            }
             all = __syncthreads_and(ok);
             if (last || (early && all)) break;
             for (int v = tid; v < N; v += T)
-                var_step_dispatch<P, 0, DV>(__ldg(pr.g.vdeg + v), v, N, pr.g.vslot, gam[v], msg, dec, Qs);
+                Qs[v] = var_step_batch<P, DV>(__ldg(pr.g.vdeg + v), v, N, uint32_t(M), pr.g.vslot, gam[v],
+                                              P::neg(Qs[v]), slots, parity);
             __syncthreads();
         }
 
@@ -284,34 +319,178 @@ __global__ void __launch_bounds__(1024) msa_flood_kernel(const LaunchParams p)
     }
 }
 
+// ---------------------------------------------------------------------------------------------
+// Latency kernel: one block per shot, everything a thread needs across iterations in registers.
+// ---------------------------------------------------------------------------------------------
+constexpr int kLatCnPerThread = kLatencyCnPerThread;   // checks per thread: M <= 2*blockDim
+constexpr int kLatVnPerThread = kLatencyVnPerThread;   // variables per thread: N <= 2*blockDim
+
+template <class P, int DV>
+__device__ __forceinline__ typename P::acc_t var_step_regs(int deg, const uint32_t *e, uint32_t M,
+                                                           typename P::acc_t gamma, bool prev,
+                                                           typename P::msg_t *slots, uint32_t *parity)
+{
+    switch (deg) {
+#define QLDPC_CASE(D)                                                                           \
+    case D:                                                                                     \
+        if constexpr (D <= DV) return var_step_exact<P, D>(e, M, gamma, prev, slots, parity);  \
+        break;
+        QLDPC_DEG_CASES(QLDPC_CASE)
+#undef QLDPC_CASE
+    default: break;
+    }
+    return gamma;
+}
+
+template <class P, int DC, bool UNIFORM, int DV>
+__global__ void __launch_bounds__(kLatencyMaxThreads, 1) msa_latency_kernel(const LaunchParams p)
+{
+    using acc_t = typename P::acc_t;
+    using msg_t = typename P::msg_t;
+
+    const Problem pr = blockIdx.y == 0 ? p.prob[0] : p.prob[1];
+    const int M = pr.g.m, N = pr.g.n;
+    const int T = blockDim.x, tid = threadIdx.x;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const LatencyLayout L = latency_layout(M, pr.g.dc_max, int(sizeof(msg_t)));
+    uint32_t *parity = reinterpret_cast<uint32_t *>(smem + L.par_off);
+    msg_t *slots = reinterpret_cast<msg_t *>(smem + L.slot_off);
+
+    // Checks c = tid + i*T: degree in registers.
+    int cdeg[kLatCnPerThread];
+#pragma unroll
+    for (int i = 0; i < kLatCnPerThread; ++i) {
+        const int c = tid + i * T;
+        cdeg[i] = c < M ? (UNIFORM ? DC : int(__ldg(pr.g.rdeg + c))) : -1;
+    }
+    // Variables v = order[tid + i*T] (heaviest first, so the few second-pass variables are the
+    // lightest): edge lists, degree and prior in registers.
+    uint32_t ev[kLatVnPerThread][DV];
+    int vdeg[kLatVnPerThread], vid[kLatVnPerThread];
+    acc_t gam[kLatVnPerThread];
+    int bad = 0;
+#pragma unroll
+    for (int i = 0; i < kLatVnPerThread; ++i) {
+        const int t = tid + i * T;
+        const int v = t < N ? int(__ldg(pr.g.vorder + t)) : N;
+        vid[i] = v;
+        vdeg[i] = v < N ? int(__ldg(pr.g.vdeg + v)) : -1;
+        const float g = v < N ? pr.prior[v] : 0.0f;
+        bad |= !isfinite(g);
+        gam[i] = P::quantize(g);
+#pragma unroll
+        for (int k = 0; k < DV; ++k)
+            ev[i][k] = (k < vdeg[i]) ? __ldg(pr.g.vslot + size_t(k) * N + (v < N ? v : 0)) : 0u;
+    }
+    bad = __syncthreads_or(bad);
+
+    const bool early = (p.flags & kFlagNoEarlyStop) == 0;
+    for (int b = blockIdx.x; b < p.batch; b += gridDim.x) {
+        uint8_t *err = pr.err + size_t(b) * N;
+        if (bad) {
+#pragma unroll
+            for (int i = 0; i < kLatVnPerThread; ++i) {
+                const int v = vid[i];
+                if (v < N) {
+                    err[v] = 0;
+                    if (pr.post) pr.post[size_t(b) * N + v] = __int_as_float(0x7fc00000);
+                }
+            }
+            if (tid == 0) {
+                pr.iters[b] = -1;
+                pr.ok[b] = 0;
+            }
+            continue;
+        }
+        const uint8_t *s = pr.syn + size_t(b) * M;
+#pragma unroll
+        for (int i = 0; i < kLatCnPerThread; ++i)
+            if (cdeg[i] >= 0) parity[tid + i * T] = (s[tid + i * T] & 1u) * 3u;
+        __syncthreads();
+        acc_t Q[kLatVnPerThread];
+#pragma unroll
+        for (int i = 0; i < kLatVnPerThread; ++i) {
+            Q[i] = gam[i];
+            const bool d = P::neg(gam[i]);
+#pragma unroll
+            for (int k = 0; k < DV; ++k) {
+                if (k < vdeg[i]) {
+                    slots[slot_of(ev[i][k], uint32_t(M))] = P::to_msg(gam[i]);
+                    if (d) flip_check(parity, check_of(ev[i][k]));
+                }
+            }
+        }
+        __syncthreads();
+
+        int k = 0, all = 0;
+        for (;; ++k) {
+            const bool last = k >= p.max_iter;
+            int ok = 1;
+#pragma unroll
+            for (int i = 0; i < kLatCnPerThread; ++i)
+                if (cdeg[i] >= 0)
+                    ok &= check_step<P, DC, UNIFORM>(tid + i * T, M, cdeg[i], parity[tid + i * T], !last, slots, p);
+            all = __syncthreads_and(ok);
+            if (last || (early && all)) break;
+#pragma unroll
+            for (int i = 0; i < kLatVnPerThread; ++i)
+                if (vdeg[i] >= 0)
+                    Q[i] = var_step_regs<P, DV>(vdeg[i], ev[i], uint32_t(M), gam[i], P::neg(Q[i]), slots, parity);
+            __syncthreads();
+        }
+
+#pragma unroll
+        for (int i = 0; i < kLatVnPerThread; ++i) {
+            const int v = vid[i];
+            if (v < N) {
+                err[v] = P::neg(Q[i]) ? 1 : 0;
+                if (pr.post) pr.post[size_t(b) * N + v] = P::post(Q[i]);
+            }
+        }
+        if (tid == 0) {
+            pr.iters[b] = k;
+            pr.ok[b] = all ? 1 : 0;
+        }
+        __syncthreads();   // the next shot reuses shared memory
+    }
+}
+
 }  // namespace kern
 
-// Instantiation table for one precision policy.
+// ---------------------------------------------------------------------------------------------
+// Instantiation tables for one precision policy: uniform row degree 6, 7, 8 (exact) or any degree
+// up to 8, 16, 32; column-degree bucket 4, 8, 16; for each, the batch and the latency kernel.
+// ---------------------------------------------------------------------------------------------
+#define QLDPC_DV_LIST(X, A, B) X(A, B, 4) X(A, B, 8) X(A, B, 16)
+#define QLDPC_VARIANTS(X)                                                                       \
+    QLDPC_DV_LIST(X, 6, true) QLDPC_DV_LIST(X, 7, true) QLDPC_DV_LIST(X, 8, true)               \
+    QLDPC_DV_LIST(X, 8, false) QLDPC_DV_LIST(X, 16, false) QLDPC_DV_LIST(X, 32, false)
+
 template <class P>
-const void *kernel_table(int dcb, int dvb)
+const void *kernel_table(const KernelChoice &kc)
 {
-#define QLDPC_K(DCV, DVV)                                                                       \
-    if (dcb == DCV && dvb == DVV)                                                               \
-        return reinterpret_cast<const void *>(&kern::msa_flood_kernel<P, DCV, DVV>);
-    QLDPC_K(8, 4) QLDPC_K(8, 8) QLDPC_K(8, 16)
-    QLDPC_K(16, 4) QLDPC_K(16, 8) QLDPC_K(16, 16)
-    QLDPC_K(32, 4) QLDPC_K(32, 8) QLDPC_K(32, 16)
+#define QLDPC_K(DCV, UNI, DVV)                                                                  \
+    if (kc.dc == DCV && kc.uniform == UNI && kc.dvb == DVV)                                     \
+        return kc.latency ? reinterpret_cast<const void *>(&kern::msa_latency_kernel<P, DCV, UNI, DVV>) \
+                          : reinterpret_cast<const void *>(&kern::msa_batch_kernel<P, DCV, UNI, DVV>);
+    QLDPC_VARIANTS(QLDPC_K)
 #undef QLDPC_K
     return nullptr;
 }
 
 template <class P>
-cudaError_t launch_table(const LaunchParams &p, int dcb, int dvb, dim3 grid, int threads,
+cudaError_t launch_table(const LaunchParams &p, const KernelChoice &kc, dim3 grid, int threads,
                          size_t smem, cudaStream_t stream)
 {
-#define QLDPC_L(DCV, DVV)                                                                       \
-    if (dcb == DCV && dvb == DVV) {                                                             \
-        kern::msa_flood_kernel<P, DCV, DVV><<<grid, threads, smem, stream>>>(p);                \
+#define QLDPC_L(DCV, UNI, DVV)                                                                  \
+    if (kc.dc == DCV && kc.uniform == UNI && kc.dvb == DVV) {                                   \
+        if (kc.latency)                                                                         \
+            kern::msa_latency_kernel<P, DCV, UNI, DVV><<<grid, threads, smem, stream>>>(p);     \
+        else                                                                                    \
+            kern::msa_batch_kernel<P, DCV, UNI, DVV><<<grid, threads, smem, stream>>>(p);       \
         return cudaGetLastError();                                                              \
     }
-    QLDPC_L(8, 4) QLDPC_L(8, 8) QLDPC_L(8, 16)
-    QLDPC_L(16, 4) QLDPC_L(16, 8) QLDPC_L(16, 16)
-    QLDPC_L(32, 4) QLDPC_L(32, 8) QLDPC_L(32, 16)
+    QLDPC_VARIANTS(QLDPC_L)
 #undef QLDPC_L
     return cudaErrorInvalidValue;
 }

@@ -11,12 +11,13 @@ namespace qldpc {
 
 // Tanner graph in the kernels' layout.  Messages of check i live in shared-memory "slots"
 // j*m + i (j = position of the edge in row i), so a warp working on 32 consecutive checks touches
-// 32 consecutive slots.  Variable v finds its edges through vslot[k*n + v] (k-th edge of v in
-// ascending check order); the check side needs no index at all.
+// 32 consecutive slots.  Variable v finds its k-th edge (ascending check order) in
+// vslot[k*n + v] = j << 16 | i; the check side needs no index at all.
 struct DeviceGraph {
-    const uint32_t *vslot;   // [dv_max * n] slot of variable v's k-th edge
+    const uint32_t *vslot;   // [dv_max * n] (j << 16) | check of variable v's k-th edge
     const uint8_t *vdeg;     // [n] column degrees
     const uint8_t *rdeg;     // [m] row degrees
+    const uint32_t *vorder;  // [n] variables by descending degree (latency kernel's assignment)
     int32_t m, n;
     int32_t dc_max, dv_max;  // largest row / column degree
 };
@@ -44,9 +45,9 @@ struct LaunchParams {
 
 constexpr uint32_t kFlagNoEarlyStop = 1u;
 
-// Shared-memory layout of one shot (identical on host and device).
+// Shared-memory layout of one shot in the batch kernel (identical on host and device).
 struct SmemLayout {
-    size_t q_off, g_off, msg_off, dec_off, syn_off, total;
+    size_t q_off, g_off, par_off, slot_off, total;
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
@@ -54,36 +55,53 @@ __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(
 __host__ __device__ inline SmemLayout smem_layout(int m, int n, int dc_max, int msg_bytes)
 {
     SmemLayout s;
-    s.q_off = 0;                                                     // a-posteriori Q_n  [n] (4 B)
-    s.g_off = align16(s.q_off + size_t(n) * 4);                      // prior gamma_n     [n] (4 B)
-    s.msg_off = align16(s.g_off + size_t(n) * 4);                    // edge messages     [dc_max*m]
-    s.dec_off = align16(s.msg_off + size_t(dc_max) * m * msg_bytes); // decision per slot [dc_max*m]
-    s.syn_off = align16(s.dec_off + size_t(dc_max) * m);             // syndrome          [m]
-    s.total = align16(s.syn_off + size_t(m));
+    s.q_off = 0;                                                       // a-posteriori Q_n [n] (4 B)
+    s.g_off = align16(s.q_off + size_t(n) * 4);                        // prior gamma_n    [n] (4 B)
+    s.par_off = align16(s.g_off + size_t(n) * 4);                      // parity words     [m] (4 B)
+    s.slot_off = align16(s.par_off + size_t(m) * 4);                   // edge messages [dc_max*m]
+    s.total = align16(s.slot_off + size_t(dc_max) * m * msg_bytes);
+    return s;
+}
+
+// Latency kernel: parity words and messages only (everything else lives in registers).
+struct LatencyLayout {
+    size_t par_off, slot_off, total;
+};
+
+__host__ __device__ inline LatencyLayout latency_layout(int m, int dc_max, int msg_bytes)
+{
+    LatencyLayout s;
+    s.par_off = 0;
+    s.slot_off = align16(size_t(m) * 4);
+    s.total = align16(s.slot_off + size_t(dc_max) * m * msg_bytes);
     return s;
 }
 
 enum Precision { kFP32 = 0, kINT16 = 1 };
 
+// Bytes per edge message: FP32 4, INT16 2.
 inline int msg_bytes(int precision) { return precision == kINT16 ? 2 : 4; }
 
-// Kernel variant buckets: compile-time maxima the degrees are rounded up to.
-int dc_bucket(int dc_max);   // 8, 16, 32 or -1
-int dv_bucket(int dv_max);   // 4, 8, 16 or -1
+// Which compiled variant runs a launch.
+struct KernelChoice {
+    bool latency;    // msa_latency_kernel (else msa_batch_kernel)
+    int dc;          // exact row degree (uniform) or row-degree bucket 8/16/32
+    bool uniform;    // every row has exactly dc edges
+    int dvb;         // column-degree bucket 4/8/16
+};
 
-// Kernel entry for (precision, dc bucket, dv bucket), for attributes and occupancy queries.
-const void *msa_kernel(int precision, int dcb, int dvb);
-
-// Launch the flooding decoder: grid (grid_x, nprob), `threads` per block, `smem` dynamic bytes.
-cudaError_t launch_msa(const LaunchParams &p, int precision, int dcb, int dvb, int threads,
-                       int grid_x, size_t smem, cudaStream_t stream);
+// Latency kernel limits: checks M <= 2 * threads, variables N <= 2 * threads, threads <= 640
+// (a block of at most 640 threads leaves each thread about 100 registers).
+constexpr int kLatencyCnPerThread = 2;
+constexpr int kLatencyVnPerThread = 2;
+constexpr int kLatencyMaxThreads = 640;
 
 // Per-precision instantiation tables (one translation unit each).
-const void *msa_kernel_f32(int dcb, int dvb);
-const void *msa_kernel_i16(int dcb, int dvb);
-cudaError_t launch_msa_f32(const LaunchParams &p, int dcb, int dvb, dim3 grid, int threads,
+const void *msa_kernel_f32(const KernelChoice &kc);
+const void *msa_kernel_i16(const KernelChoice &kc);
+cudaError_t launch_msa_f32(const LaunchParams &p, const KernelChoice &kc, dim3 grid, int threads,
                            size_t smem, cudaStream_t stream);
-cudaError_t launch_msa_i16(const LaunchParams &p, int dcb, int dvb, dim3 grid, int threads,
+cudaError_t launch_msa_i16(const LaunchParams &p, const KernelChoice &kc, dim3 grid, int threads,
                            size_t smem, cudaStream_t stream);
 
 }  // namespace qldpc

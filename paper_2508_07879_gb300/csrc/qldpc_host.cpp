@@ -11,6 +11,7 @@
 #include <new>
 #include <vector>
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "msa_launch.h"
@@ -22,11 +23,11 @@ struct qldpc_graph {
     int sm_count = 0;
     size_t smem_optin = 0;      // max dynamic shared memory per block (opt-in)
     int32_t m = 0, n = 0, nnz = 0, dc_max = 0, dv_max = 0;
-    int dcb = 0, dvb = 0;       // kernel buckets
+    bool uniform_rows = false;  // every row has degree dc_max
     void *d_block = nullptr;    // one device allocation for all graph arrays
     DeviceGraph dg{};
     // launch overrides (0 = automatic)
-    int user_threads = 0, user_blocks_per_sm = 0;
+    int user_kernel = QLDPC_KERNEL_AUTO, user_threads = 0, user_blocks_per_sm = 0;
     // staging for qldpc_decode_host
     std::mutex host_mu;
     int32_t cap = 0;
@@ -34,6 +35,8 @@ struct qldpc_graph {
     uint8_t *d_syn = nullptr, *d_err = nullptr, *d_ok = nullptr;
     int32_t *d_iters = nullptr;
     float *d_prior = nullptr;
+    uint8_t *h_stage = nullptr;     // page-locked copy-back buffer for small batches
+    size_t h_stage_bytes = 0;
     std::vector<float> prior_cache;
     bool prior_valid = false;
 };
@@ -43,17 +46,17 @@ namespace qldpc {
 int dc_bucket(int d) { return d <= 8 ? 8 : d <= 16 ? 16 : d <= 32 ? 32 : -1; }
 int dv_bucket(int d) { return d <= 4 ? 4 : d <= 8 ? 8 : d <= 16 ? 16 : -1; }
 
-const void *msa_kernel(int precision, int dcb, int dvb)
+const void *msa_kernel(int precision, const KernelChoice &kc)
 {
-    return precision == kINT16 ? msa_kernel_i16(dcb, dvb) : msa_kernel_f32(dcb, dvb);
+    return precision == kINT16 ? msa_kernel_i16(kc) : msa_kernel_f32(kc);
 }
 
-cudaError_t launch_msa(const LaunchParams &p, int precision, int dcb, int dvb, int threads,
+cudaError_t launch_msa(const LaunchParams &p, int precision, const KernelChoice &kc, int threads,
                        int grid_x, size_t smem, cudaStream_t stream)
 {
     dim3 grid(unsigned(grid_x), unsigned(p.nprob));
-    return precision == kINT16 ? launch_msa_i16(p, dcb, dvb, grid, threads, smem, stream)
-                               : launch_msa_f32(p, dcb, dvb, grid, threads, smem, stream);
+    return precision == kINT16 ? launch_msa_i16(p, kc, grid, threads, smem, stream)
+                               : launch_msa_f32(p, kc, grid, threads, smem, stream);
 }
 
 }  // namespace qldpc
@@ -65,8 +68,10 @@ namespace {
 // ------------------------------------------------------------------------------------------
 struct HostLayout {
     int32_t dc_max = 0, dv_max = 0;
+    bool uniform_rows = true;
     std::vector<uint8_t> rdeg, vdeg;
     std::vector<uint32_t> vslot;   // [dv_max * n]
+    std::vector<uint32_t> vorder;  // [n] by descending degree, stable
 };
 
 int validate_and_layout(const int32_t *row_ptr, const int32_t *col_idx, int32_t m, int32_t n,
@@ -95,7 +100,7 @@ int validate_and_layout(const int32_t *row_ptr, const int32_t *col_idx, int32_t 
     }
     const int32_t dv_max = *std::max_element(cdeg.begin(), cdeg.end());
     if (dc_max > QLDPC_MAX_ROW_DEGREE || dv_max > QLDPC_MAX_COL_DEGREE) return QLDPC_ERR_UNSUPPORTED;
-    if (int64_t(dc_max) * m > int64_t(UINT32_MAX)) return QLDPC_ERR_UNSUPPORTED;
+    if (m > QLDPC_MAX_CHECKS) return QLDPC_ERR_UNSUPPORTED;   // edge lists store the check in 16 bits
 
     out.dc_max = dc_max;
     out.dv_max = dv_max;
@@ -106,13 +111,18 @@ int validate_and_layout(const int32_t *row_ptr, const int32_t *col_idx, int32_t 
     // the order in which the variable step accumulates its sums.
     for (int32_t i = 0; i < m; ++i) {
         out.rdeg[size_t(i)] = uint8_t(row_ptr[i + 1] - row_ptr[i]);
+        out.uniform_rows = out.uniform_rows && (row_ptr[i + 1] - row_ptr[i]) == dc_max;
         for (int32_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
             const int32_t v = col_idx[e];
             const int32_t j = e - row_ptr[i];
             const int32_t k = out.vdeg[size_t(v)]++;
-            out.vslot[size_t(k) * n + v] = uint32_t(j) * uint32_t(m) + uint32_t(i);
+            out.vslot[size_t(k) * n + v] = (uint32_t(j) << 16) | uint32_t(i);
         }
     }
+    out.vorder.resize(size_t(n));
+    for (int32_t v = 0; v < n; ++v) out.vorder[size_t(v)] = uint32_t(v);
+    std::stable_sort(out.vorder.begin(), out.vorder.end(),
+                     [&](uint32_t a, uint32_t b) { return out.vdeg[a] > out.vdeg[b]; });
     return QLDPC_OK;
 }
 
@@ -137,37 +147,108 @@ size_t shot_smem(const qldpc_graph *g, int precision)
     return smem_layout(g->m, g->n, g->dc_max, msg_bytes(precision)).total;
 }
 
-// Threads per block: for a latency-bound batch (every shot gets its own SM) make one pass over
-// the checks and as few passes over the variables as possible; for throughput use 256 threads and
-// many resident blocks.
-int choose_threads(const qldpc_graph *g, int32_t shots)
-{
-    if (g->user_threads) return g->user_threads;
-    const int big = std::max(g->m, g->n);
-    if (shots <= g->sm_count) {
-        int t = big <= 1024 ? big : std::max(g->m, (g->n + 1) / 2);
-        t = ((std::min(t, 1024) + 31) / 32) * 32;
-        return std::max(t, 32);
-    }
-    return 256;
-}
-
 // Opt in to more than 48 KB of dynamic shared memory once per kernel variant and size.
-int ensure_kernel_attrs(int precision, int dcb, int dvb, size_t smem, size_t smem_optin)
+int ensure_kernel_attrs(const void *k, size_t smem, size_t smem_optin)
 {
     static std::mutex mu;
-    static size_t granted[2][33][17] = {};
-    const void *k = msa_kernel(precision, dcb, dvb);
+    static std::vector<std::pair<const void *, size_t>> granted;
     if (!k) return QLDPC_ERR_UNSUPPORTED;
     if (smem > smem_optin) return QLDPC_ERR_UNSUPPORTED;
     if (smem <= 48 * 1024) return QLDPC_OK;
     std::lock_guard<std::mutex> lk(mu);
-    size_t &have = granted[precision][dcb][dvb];
-    if (smem <= have) return QLDPC_OK;
+    for (auto &kv : granted)
+        if (kv.first == k && kv.second >= smem) return QLDPC_OK;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return cuda_status(e);
-    have = smem;
+    granted.emplace_back(k, smem);
     return QLDPC_OK;
+}
+
+// The launch shape of one call.
+struct Plan {
+    KernelChoice kc{};
+    int threads = 0;
+    int grid = 0;
+    size_t smem = 0;
+};
+
+int round32(int x) { return (x + 31) / 32 * 32; }
+
+// Compiled variant for the graphs of one call: exact uniform row degree 6..8, else a bucket.
+KernelChoice variant(const qldpc_graph *const *gs, int nprob, bool latency)
+{
+    int dc = 0, dv = 0;
+    bool uniform = true;
+    for (int i = 0; i < nprob; ++i) {
+        dc = std::max(dc, gs[i]->dc_max);
+        dv = std::max(dv, gs[i]->dv_max);
+        uniform = uniform && gs[i]->uniform_rows && gs[i]->dc_max == gs[0]->dc_max;
+    }
+    if (uniform && dc >= 6 && dc <= 8) return KernelChoice{latency, dc, true, dv_bucket(dv)};
+    return KernelChoice{latency, dc_bucket(dc), false, dv_bucket(dv)};
+}
+
+int occupancy_grid(const qldpc_graph *g0, const void *k, int threads, size_t smem, int nprob,
+                   int32_t batch, int per_sm, int &grid)
+{
+    if (!per_sm) {
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem);
+        if (e != cudaSuccess) return cuda_status(e);
+        if (per_sm < 1) return QLDPC_ERR_UNSUPPORTED;
+    }
+    const int64_t slots = std::max<int64_t>(1, int64_t(per_sm) * g0->sm_count / nprob);
+    grid = int(std::max<int64_t>(1, std::min<int64_t>(batch, slots)));
+    return QLDPC_OK;
+}
+
+// Single-shot (latency) path: chosen automatically when every shot of the call gets its own SM,
+// or forced with QLDPC_KERNEL_LATENCY.  One pass over the checks and the variables when both fit
+// in a block of up to 640 threads, else two passes of a block sized for the larger half.
+int plan_latency(const qldpc_graph *const *gs, int nprob, int32_t batch, int precision, Plan &pl,
+                 bool &chosen)
+{
+    const qldpc_graph *g0 = gs[0];
+    chosen = false;
+    if (g0->user_kernel == QLDPC_KERNEL_BATCH) return QLDPC_OK;
+    const bool forced = g0->user_kernel == QLDPC_KERNEL_LATENCY;
+    if (!forced && int64_t(batch) * nprob > g0->sm_count) return QLDPC_OK;
+    int one = 32, two = 32;
+    size_t smem = 0;
+    for (int i = 0; i < nprob; ++i) {
+        one = std::max(one, round32(std::max(gs[i]->m, gs[i]->n)));
+        two = std::max(two, round32(std::max((gs[i]->m + 1) / 2, (gs[i]->n + 1) / 2)));
+        smem = std::max(smem, latency_layout(gs[i]->m, gs[i]->dc_max, msg_bytes(precision)).total);
+    }
+    const int threads = (forced && g0->user_threads) ? g0->user_threads
+                                                      : (one <= kLatencyMaxThreads ? one : two);
+    bool fits = threads <= kLatencyMaxThreads && smem <= g0->smem_optin;
+    for (int i = 0; i < nprob; ++i)
+        fits = fits && gs[i]->m <= kLatencyCnPerThread * threads && gs[i]->n <= kLatencyVnPerThread * threads;
+    if (!fits) return forced ? QLDPC_ERR_UNSUPPORTED : QLDPC_OK;
+    pl.kc = variant(gs, nprob, true);
+    pl.threads = threads;
+    pl.smem = smem;
+    const void *k = msa_kernel(precision, pl.kc);
+    if (int rc = ensure_kernel_attrs(k, smem, g0->smem_optin)) return rc;
+    pl.grid = batch;
+    if (forced || int64_t(batch) * nprob > g0->sm_count)
+        if (int rc = occupancy_grid(g0, k, threads, smem, nprob, batch, g0->user_blocks_per_sm, pl.grid))
+            return rc;
+    chosen = true;
+    return QLDPC_OK;
+}
+
+int plan_batch(const qldpc_graph *const *gs, int nprob, int32_t batch, int precision, Plan &pl)
+{
+    const qldpc_graph *g0 = gs[0];
+    size_t smem = 0;
+    for (int i = 0; i < nprob; ++i) smem = std::max(smem, shot_smem(gs[i], precision));
+    pl.kc = variant(gs, nprob, false);
+    pl.threads = g0->user_threads ? g0->user_threads : 256;
+    pl.smem = smem;
+    const void *k = msa_kernel(precision, pl.kc);
+    if (int rc = ensure_kernel_attrs(k, smem, g0->smem_optin)) return rc;
+    return occupancy_grid(g0, k, pl.threads, smem, nprob, batch, g0->user_blocks_per_sm, pl.grid);
 }
 
 int check_device(const qldpc_graph *g)
@@ -202,33 +283,12 @@ int launch(const qldpc_graph *g0, const qldpc_graph *g1, const Problem *probs, i
 
     // One kernel variant and one block shape serve both problems of a pair.
     const qldpc_graph *gs[2] = {g0, g1};
-    int dcb = 0, dvb = 0;
-    size_t smem = 0;
-    for (int i = 0; i < nprob; ++i) {
-        dcb = std::max(dcb, gs[i]->dcb);
-        dvb = std::max(dvb, gs[i]->dvb);
-        smem = std::max(smem, shot_smem(gs[i], precision));
-    }
-    const qldpc_graph *lead = (nprob == 2 && (g1->m + g1->n) > (g0->m + g0->n)) ? g1 : g0;
-    int rc = ensure_kernel_attrs(precision, dcb, dvb, smem, lead->smem_optin);
-    if (rc) return rc;
-
-    // Latency-bound batches (one block per shot fits on the SMs) launch one block per shot;
-    // larger batches size a persistent grid from the occupancy of the chosen shape.
-    const int threads = choose_threads(lead, batch * nprob);
-    int grid_x = batch;
-    if (int64_t(batch) * nprob > lead->sm_count || lead->user_blocks_per_sm) {
-        int per_sm = lead->user_blocks_per_sm;
-        if (!per_sm) {
-            cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &per_sm, msa_kernel(precision, dcb, dvb), threads, smem);
-            if (e != cudaSuccess) return cuda_status(e);
-            if (per_sm < 1) return QLDPC_ERR_UNSUPPORTED;
-        }
-        const int64_t slots = int64_t(per_sm) * lead->sm_count / nprob;
-        grid_x = int(std::max<int64_t>(1, std::min<int64_t>(batch, slots)));
-    }
-    return cuda_status(launch_msa(p, precision, dcb, dvb, threads, grid_x, smem, stream));
+    Plan pl;
+    bool latency = false;
+    if (int rc = plan_latency(gs, nprob, batch, precision, pl, latency)) return rc;
+    if (!latency)
+        if (int rc = plan_batch(gs, nprob, batch, precision, pl)) return rc;
+    return cuda_status(launch_msa(p, precision, pl.kc, pl.threads, pl.grid, pl.smem, stream));
 }
 
 Problem make_problem(const qldpc_graph *g, const uint8_t *syn, const float *prior, uint8_t *err,
@@ -248,11 +308,17 @@ Problem make_problem(const qldpc_graph *g, const uint8_t *syn, const float *prio
 void free_stage(qldpc_graph *g)
 {
     if (g->d_stage) cudaFree(g->d_stage);
+    if (g->h_stage) cudaFreeHost(g->h_stage);
     g->d_stage = nullptr;
+    g->h_stage = nullptr;
+    g->h_stage_bytes = 0;
     g->d_syn = g->d_err = g->d_ok = nullptr;
     g->d_iters = nullptr;
+    g->d_prior = nullptr;
     g->cap = 0;
 }
+
+constexpr size_t kHostStageMax = 64 * 1024;   // outputs up to this size return in one copy
 
 int reserve_stage(qldpc_graph *g, int32_t max_batch)
 {
@@ -266,6 +332,13 @@ int reserve_stage(qldpc_graph *g, int32_t max_batch)
     void *blk = nullptr;
     cudaError_t e = cudaMalloc(&blk, syn_b + err_b + it_b + ok_b + pr_b);
     if (e != cudaSuccess) return cuda_status(e);
+    void *hblk = nullptr;
+    const size_t h_b = std::min(err_b + it_b + ok_b, kHostStageMax);
+    e = cudaMallocHost(&hblk, h_b);
+    if (e != cudaSuccess) {
+        cudaFree(blk);
+        return cuda_status(e);
+    }
     free_stage(g);
     char *b = static_cast<char *>(blk);
     g->d_stage = blk;
@@ -274,9 +347,51 @@ int reserve_stage(qldpc_graph *g, int32_t max_batch)
     g->d_iters = reinterpret_cast<int32_t *>(b + syn_b + err_b);
     g->d_ok = reinterpret_cast<uint8_t *>(b + syn_b + err_b + it_b);
     g->d_prior = reinterpret_cast<float *>(b + syn_b + err_b + it_b + ok_b);
+    g->h_stage = static_cast<uint8_t *>(hblk);
+    g->h_stage_bytes = h_b;
     g->prior_valid = false;
     g->cap = cap;
     return QLDPC_OK;
+}
+
+// Device-accessible address of [p, p + bytes) when the whole range lies in ONE page-locked host
+// allocation known to CUDA (cudaHostAlloc / cudaMallocHost / cudaHostRegister), else nullptr.
+// The extent comes from the driver's allocation range, so a buffer that merely starts in pinned
+// memory is never read or written by a kernel beyond that allocation.
+using PointerAttrFn = CUresult (*)(void *, CUpointer_attribute, CUdeviceptr);
+
+PointerAttrFn pointer_attr_fn()
+{
+    static PointerAttrFn fn = [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuPointerGetAttribute", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        return reinterpret_cast<PointerAttrFn>(f);
+    }();
+    return fn;
+}
+
+void *mapped_host_range(const void *p, size_t bytes)
+{
+    if (!p || bytes == 0) return nullptr;
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+    PointerAttrFn fn = pointer_attr_fn();
+    if (!fn) return nullptr;
+    CUdeviceptr start = 0;
+    size_t size = 0;
+    const CUdeviceptr dp = reinterpret_cast<CUdeviceptr>(a.devicePointer);
+    if (fn(&start, CU_POINTER_ATTRIBUTE_RANGE_START_ADDR, dp) != CUDA_SUCCESS) return nullptr;
+    if (fn(&size, CU_POINTER_ATTRIBUTE_RANGE_SIZE, dp) != CUDA_SUCCESS) return nullptr;
+    if (start == 0 || size == 0 || dp < start || dp - start + bytes > size) return nullptr;
+    return a.devicePointer;
 }
 
 }  // namespace
@@ -309,8 +424,7 @@ int qldpc_graph_create(const int32_t *row_ptr, const int32_t *col_idx, int32_t m
     g->nnz = row_ptr[m];
     g->dc_max = hl.dc_max;
     g->dv_max = hl.dv_max;
-    g->dcb = dc_bucket(hl.dc_max);
-    g->dvb = dv_bucket(hl.dv_max);
+    g->uniform_rows = hl.uniform_rows;
     // The FP32 working set is the larger one; reject graphs whose shot does not fit on chip.
     if (shot_smem(g, QLDPC_FP32) > g->smem_optin && shot_smem(g, QLDPC_INT16) > g->smem_optin) {
         delete g;
@@ -320,7 +434,8 @@ int qldpc_graph_create(const int32_t *row_ptr, const int32_t *col_idx, int32_t m
     const size_t vs_b = align16(hl.vslot.size() * sizeof(uint32_t));
     const size_t vd_b = align16(size_t(n));
     const size_t rd_b = align16(size_t(m));
-    e = cudaMalloc(&g->d_block, vs_b + vd_b + rd_b);
+    const size_t vo_b = align16(size_t(n) * sizeof(uint32_t));
+    e = cudaMalloc(&g->d_block, vs_b + vd_b + rd_b + vo_b);
     if (e != cudaSuccess) {
         delete g;
         return cuda_status(e);
@@ -329,6 +444,8 @@ int qldpc_graph_create(const int32_t *row_ptr, const int32_t *col_idx, int32_t m
     e = cudaMemcpy(b, hl.vslot.data(), hl.vslot.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b + vs_b, hl.vdeg.data(), size_t(n), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b + vs_b + vd_b, hl.rdeg.data(), size_t(m), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b + vs_b + vd_b + rd_b, hl.vorder.data(), size_t(n) * sizeof(uint32_t), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(g->d_block);
         delete g;
@@ -337,6 +454,7 @@ int qldpc_graph_create(const int32_t *row_ptr, const int32_t *col_idx, int32_t m
     g->dg.vslot = reinterpret_cast<const uint32_t *>(b);
     g->dg.vdeg = reinterpret_cast<const uint8_t *>(b + vs_b);
     g->dg.rdeg = reinterpret_cast<const uint8_t *>(b + vs_b + vd_b);
+    g->dg.vorder = reinterpret_cast<const uint32_t *>(b + vs_b + vd_b + rd_b);
     g->dg.m = m;
     g->dg.n = n;
     g->dg.dc_max = hl.dc_max;
@@ -389,27 +507,39 @@ int qldpc_graph_dims(const qldpc_graph *g, int32_t *m, int32_t *n, int32_t *nnz,
     return QLDPC_OK;
 }
 
-int qldpc_graph_set_launch(qldpc_graph *g, int32_t threads_per_block, int32_t blocks_per_sm)
+int qldpc_graph_set_launch(qldpc_graph *g, int32_t kernel, int32_t threads_per_block,
+                           int32_t blocks_per_sm)
 {
     if (!g) return QLDPC_ERR_INVALID_ARG;
+    if (kernel != QLDPC_KERNEL_AUTO && kernel != QLDPC_KERNEL_BATCH && kernel != QLDPC_KERNEL_LATENCY)
+        return QLDPC_ERR_INVALID_ARG;
     if (threads_per_block != 0 && (threads_per_block < 32 || threads_per_block > 1024 || threads_per_block % 32))
         return QLDPC_ERR_INVALID_ARG;
     if (blocks_per_sm < 0 || blocks_per_sm > 32) return QLDPC_ERR_INVALID_ARG;
-    if (blocks_per_sm) {
-        // the requested residency must be achievable for both precisions' working sets
-        const int t = threads_per_block ? threads_per_block : 256;
-        for (int prec : {QLDPC_FP32, QLDPC_INT16}) {
-            const size_t smem = shot_smem(g, prec);
-            if (smem > g->smem_optin) continue;
-            if (int rc = ensure_kernel_attrs(prec, g->dcb, g->dvb, smem, g->smem_optin)) return rc;
-            int per_sm = 0;
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, msa_kernel(prec, g->dcb, g->dvb), t, smem) !=
-                cudaSuccess)
-                return QLDPC_ERR_CUDA;
-            if (per_sm < blocks_per_sm) return QLDPC_ERR_UNSUPPORTED;
-        }
-    }
+    if (kernel == QLDPC_KERNEL_AUTO && (threads_per_block || blocks_per_sm)) return QLDPC_ERR_INVALID_ARG;
+    if (int rc = check_device(g)) return rc;
+    const int saved[3] = {g->user_kernel, g->user_threads, g->user_blocks_per_sm};
+    g->user_kernel = kernel;
     g->user_threads = threads_per_block;
+    g->user_blocks_per_sm = 0;
+    // the shape must be launchable, and the requested residency achievable, in both precisions
+    const qldpc_graph *gs[1] = {g};
+    int rc = QLDPC_OK;
+    for (int prec : {QLDPC_FP32, QLDPC_INT16}) {
+        Plan pl;
+        bool latency = false;
+        const int32_t big = int32_t(1) << 30;
+        rc = plan_latency(gs, 1, big, prec, pl, latency);
+        if (rc == QLDPC_OK && !latency) rc = plan_batch(gs, 1, big, prec, pl);
+        if (rc == QLDPC_OK && blocks_per_sm && pl.grid < blocks_per_sm * g->sm_count) rc = QLDPC_ERR_UNSUPPORTED;
+        if (rc) break;
+    }
+    if (rc) {
+        g->user_kernel = saved[0];
+        g->user_threads = saved[1];
+        g->user_blocks_per_sm = saved[2];
+        return rc;
+    }
     g->user_blocks_per_sm = blocks_per_sm;
     return QLDPC_OK;
 }
@@ -472,17 +602,34 @@ int qldpc_decode_host(qldpc_graph *g, const uint8_t *h_syndromes, int32_t batch,
     if (batch > 0 && (!h_syndromes || !h_prior || !h_err || !h_iters || !h_ok))
         return QLDPC_ERR_INVALID_ARG;
     if (int rc = check_device(g)) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // every argument check of the decode itself, before anything is enqueued
+    if (int rc = launch(g, g, nullptr, 1, 0, max_iter, alpha, precision, flags, st)) return rc;
     if (batch == 0) return QLDPC_OK;
     std::lock_guard<std::mutex> lk(g->host_mu);
     if (int rc = reserve_stage(g, batch)) return rc;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaSuccess;
+    // Page-locked buffers: the kernel reads the syndromes and writes the results in host memory
+    // directly (NVLink-C2C on Grace-Blackwell), so the call is one launch and one synchronize.
+    void *z_syn = mapped_host_range(h_syndromes, size_t(batch) * g->m);
+    void *z_err = z_syn ? mapped_host_range(h_err, size_t(batch) * g->n) : nullptr;
+    void *z_it = z_err ? mapped_host_range(h_iters, size_t(batch) * 4) : nullptr;
+    void *z_ok = z_it ? mapped_host_range(h_ok, size_t(batch)) : nullptr;
     const size_t prior_b = size_t(g->n) * sizeof(float);
     if (!g->prior_valid || std::memcmp(g->prior_cache.data(), h_prior, prior_b) != 0) {
         g->prior_cache.assign(h_prior, h_prior + g->n);
         e = cudaMemcpyAsync(g->d_prior, g->prior_cache.data(), prior_b, cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) return cuda_status(e);
         g->prior_valid = true;
+    }
+    if (z_ok) {
+        const Problem pz = make_problem(g, static_cast<const uint8_t *>(z_syn), g->d_prior,
+                                        static_cast<uint8_t *>(z_err), static_cast<int32_t *>(z_it),
+                                        static_cast<uint8_t *>(z_ok), nullptr);
+        int rc = launch(g, g, &pz, 1, batch, max_iter, alpha, precision, flags, st);
+        const cudaError_t se = cudaStreamSynchronize(st);
+        if (rc) return rc;
+        return cuda_status(se);
     }
     e = cudaMemcpyAsync(g->d_syn, h_syndromes, size_t(batch) * g->m, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_status(e);
@@ -492,7 +639,21 @@ int qldpc_decode_host(qldpc_graph *g, const uint8_t *h_syndromes, int32_t batch,
         cudaStreamSynchronize(st);
         return rc;
     }
-    e = cudaMemcpyAsync(h_err, g->d_err, size_t(batch) * g->n, cudaMemcpyDeviceToHost, st);
+    // e_hat, iterations and ok are contiguous in the staging: a small batch comes back in one
+    // copy through page-locked staging, a large one straight into the caller's buffers.
+    const size_t err_b = size_t(batch) * g->n;
+    const size_t out_b = size_t(g->d_ok - g->d_err) + size_t(batch);
+    if (g->h_stage && out_b <= g->h_stage_bytes) {
+        e = cudaMemcpyAsync(g->h_stage, g->d_err, out_b, cudaMemcpyDeviceToHost, st);
+        const cudaError_t se = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_status(e);
+        if (se != cudaSuccess) return cuda_status(se);
+        std::memcpy(h_err, g->h_stage, err_b);
+        std::memcpy(h_iters, g->h_stage + (reinterpret_cast<uint8_t *>(g->d_iters) - g->d_err), size_t(batch) * 4);
+        std::memcpy(h_ok, g->h_stage + (g->d_ok - g->d_err), size_t(batch));
+        return QLDPC_OK;
+    }
+    e = cudaMemcpyAsync(h_err, g->d_err, err_b, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h_iters, g->d_iters, size_t(batch) * 4, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h_ok, g->d_ok, size_t(batch), cudaMemcpyDeviceToHost, st);

@@ -27,6 +27,11 @@ QLDPC_INT16 = 1
 QLDPC_NO_EARLY_STOP = 1
 QLDPC_MAX_ROW_DEGREE = 32
 QLDPC_MAX_COL_DEGREE = 16
+QLDPC_MAX_CHECKS = 65535
+QLDPC_KERNEL_AUTO = 0
+QLDPC_KERNEL_BATCH = 1
+QLDPC_KERNEL_LATENCY = 2
+KERNELS = {"auto": QLDPC_KERNEL_AUTO, "batch": QLDPC_KERNEL_BATCH, "latency": QLDPC_KERNEL_LATENCY}
 
 PRECISIONS = {"fp32": QLDPC_FP32, "int16": QLDPC_INT16}
 
@@ -49,7 +54,7 @@ _SIGNATURES = {
     "qldpc_graph_create_csc": ([_p, _p, _i32, _i32, ctypes.POINTER(_p)], ctypes.c_int),
     "qldpc_graph_destroy": ([_p], None),
     "qldpc_graph_dims": ([_p, _p, _p, _p, _p, _p], ctypes.c_int),
-    "qldpc_graph_set_launch": ([_p, _i32, _i32], ctypes.c_int),
+    "qldpc_graph_set_launch": ([_p, _i32, _i32, _i32], ctypes.c_int),
     "qldpc_graph_reserve": ([_p, _i32], ctypes.c_int),
     "qldpc_decode": ([_p, _p, _i32, _p, _i32, _f32, _p, _p, _p], ctypes.c_int),
     "qldpc_decode_ex": ([_p, _p, _i32, _p, _i32, _f32, _p, _p, _p, _p, _i32, _u32, _p], ctypes.c_int),
@@ -152,8 +157,9 @@ class Graph:
         check(qldpc_graph_dims(self._h, *[ctypes.byref(v) for v in vals]), "qldpc_graph_dims")
         return tuple(v.value for v in vals)
 
-    def set_launch(self, threads_per_block: int = 0, blocks_per_sm: int = 0) -> None:
-        check(qldpc_graph_set_launch(self._h, int(threads_per_block), int(blocks_per_sm)),
+    def set_launch(self, kernel: str = "auto", threads_per_block: int = 0, blocks_per_sm: int = 0) -> None:
+        """Force a kernel ("batch" / "latency") and optionally its shape; "auto" restores the default."""
+        check(qldpc_graph_set_launch(self._h, KERNELS[kernel], int(threads_per_block), int(blocks_per_sm)),
               "qldpc_graph_set_launch")
 
     def reserve(self, max_batch: int) -> None:

@@ -31,11 +31,28 @@ def q():
     return qldpc
 
 
-def gpu_decode(q, graph, syn, prior, max_iter, alpha, precision, early_stop=True):
-    s = torch.from_numpy(np.ascontiguousarray(syn, dtype=np.uint8)).cuda()
+def set_kernel(graph, kernel):
+    """"auto", "batch", "latency" or "latencyT" (the latency kernel with T threads per block)."""
+    if kernel.startswith("latency") and kernel != "latency":
+        graph.set_launch("latency", int(kernel[len("latency"):]))
+    else:
+        graph.set_launch(kernel)
+
+
+def gpu_decode(q, graph, syn, prior, max_iter, alpha, precision, early_stop=True, kernel="auto"):
+    """kernel: "auto" (the library's choice), "batch", "latency" or "latencyT" (forced for the
+    whole batch; see set_kernel)."""
+    syn = np.ascontiguousarray(syn, dtype=np.uint8)
     p = torch.from_numpy(np.ascontiguousarray(prior, dtype=np.float32)).cuda()
-    err, iters, ok, post = q.decode(graph, s, p, max_iter, alpha, precision, early_stop, want_post=True)
-    torch.cuda.synchronize()
+    s = torch.from_numpy(syn).cuda()
+    if kernel != "auto":
+        set_kernel(graph, kernel)
+    try:
+        err, iters, ok, post = q.decode(graph, s, p, max_iter, alpha, precision, early_stop, want_post=True)
+        torch.cuda.synchronize()
+    finally:
+        if kernel != "auto":
+            graph.set_launch("auto")
     return {"err": err.cpu().numpy(), "iters": iters.cpu().numpy(), "ok": ok.cpu().numpy(),
             "post": post.cpu().numpy()}
 
@@ -55,11 +72,15 @@ def assert_parity(g, o, precision, where=""):
         np.testing.assert_array_equal(g["post"], o["post"], err_msg=f"post {where}")
 
 
-def check(q, h, syn, prior, max_iter, alpha=0.75, precision="fp32", early_stop=True, graph=None):
+def check(q, h, syn, prior, max_iter, alpha=0.75, precision="fp32", early_stop=True, graph=None,
+          kernels=("batch", "latency")):
+    """Decode on every kernel in `kernels` and compare each with the oracle."""
     graph = graph or q.Graph.from_csr(h)
-    g = gpu_decode(q, graph, syn, prior, max_iter, alpha, precision, early_stop)
     o = oracle_decode(h, syn, prior, max_iter, alpha, precision, early_stop)
-    assert_parity(g, o, precision, f"{precision} early={early_stop} max_iter={max_iter}")
+    g = None
+    for kernel in kernels:
+        g = gpu_decode(q, graph, syn, prior, max_iter, alpha, precision, early_stop, kernel)
+        assert_parity(g, o, precision, f"{kernel} {precision} early={early_stop} max_iter={max_iter}")
     return g, o
 
 
@@ -118,7 +139,9 @@ def test_lp1054_config_mixed_p(q, precision):
     graph = q.Graph.from_csr(h)
     for i, p in enumerate((0.01, 0.02, 0.03, 0.04, 0.05)):
         b = w.x_error_batch(code, p, 2503 if i == 2 else 500, seed=2001 + i)
-        check(q, h, b.syndromes, b.prior, 50, 0.75, precision, graph=graph)
+        check(q, h, b.syndromes, b.prior, 50, 0.75, precision, graph=graph, kernels=("batch",))
+        check(q, h, b.syndromes[:300], b.prior, 50, 0.75, precision, graph=graph,
+              kernels=("latency", "latency544", "latency640"))
 
 
 @pytest.mark.parametrize("precision", PRECS)
@@ -154,20 +177,39 @@ def test_bb_pair_decode(q, name, precision):
         prior = np.full(code.n, w.prior_llr(2 * p / 3), dtype=np.float32)
         for max_iter, early in ((64, True), (10, False)):      # plain mode and the paper's mode
             dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
-            (rx, rz) = q.decode_pair(gz, gx, dev(sx), dev(sz), dev(prior), dev(prior), max_iter, 0.75,
-                                     precision, early, want_post=True)
-            torch.cuda.synchronize()
-            pair_x = {"err": rx[0].cpu().numpy(), "iters": rx[1].cpu().numpy(),
-                      "ok": rx[2].cpu().numpy(), "post": rx[3].cpu().numpy()}
-            pair_z = {"err": rz[0].cpu().numpy(), "iters": rz[1].cpu().numpy(),
-                      "ok": rz[2].cpu().numpy(), "post": rz[3].cpu().numpy()}
+            ox = oracle_decode(code.hz_csr, sx, prior, max_iter, 0.75, precision, early)
+            oz = oracle_decode(code.hx_csr, sz, prior, max_iter, 0.75, precision, early)
+            for chunk in (len(sx), 50):          # one batch-kernel launch / latency-kernel launches
+                parts_x, parts_z = [], []
+                for lo in range(0, len(sx), chunk):
+                    hi = min(lo + chunk, len(sx))
+                    (rx, rz) = q.decode_pair(gz, gx, dev(sx[lo:hi]), dev(sz[lo:hi]), dev(prior), dev(prior),
+                                             max_iter, 0.75, precision, early, want_post=True)
+                    torch.cuda.synchronize()
+                    parts_x.append([t.cpu().numpy() for t in rx])
+                    parts_z.append([t.cpu().numpy() for t in rz])
+                keys = ("err", "iters", "ok", "post")
+                pair_x = {k: np.concatenate([p[i] for p in parts_x]) for i, k in enumerate(keys)}
+                pair_z = {k: np.concatenate([p[i] for p in parts_z]) for i, k in enumerate(keys)}
+                assert_parity(pair_x, ox, precision, f"pair x chunk {chunk}")
+                assert_parity(pair_z, oz, precision, f"pair z chunk {chunk}")
+            # the pair on the latency kernel for the whole batch (the launch shape follows the first graph)
+            gz.set_launch("latency")
+            try:
+                (rx, rz) = q.decode_pair(gz, gx, dev(sx), dev(sz), dev(prior), dev(prior), max_iter, 0.75,
+                                         precision, early, want_post=True)
+                torch.cuda.synchronize()
+            finally:
+                gz.set_launch("auto")
+            assert_parity(dict(zip(("err", "iters", "ok", "post"), [t.cpu().numpy() for t in rx])), ox,
+                          precision, "pair x latency")
+            assert_parity(dict(zip(("err", "iters", "ok", "post"), [t.cpu().numpy() for t in rz])), oz,
+                          precision, "pair z latency")
             sep_x = gpu_decode(q, gz, sx, prior, max_iter, 0.75, precision, early)
             sep_z = gpu_decode(q, gx, sz, prior, max_iter, 0.75, precision, early)
             for k in pair_x:
                 np.testing.assert_array_equal(pair_x[k], sep_x[k])
                 np.testing.assert_array_equal(pair_z[k], sep_z[k])
-            assert_parity(pair_x, oracle_decode(code.hz_csr, sx, prior, max_iter, 0.75, precision, early), precision)
-            assert_parity(pair_z, oracle_decode(code.hx_csr, sz, prior, max_iter, 0.75, precision, early), precision)
 
 
 # ---------------------------------------------------------------------------------------------
@@ -191,13 +233,30 @@ def test_launch_shapes_give_identical_results(q):
     graph = q.Graph.from_csr(code.hz_csr)
     b = w.x_error_batch(code, 0.05, 700, seed=12)
     ref = {p: gpu_decode(q, graph, b.syndromes, b.prior, 50, 0.75, p) for p in PRECS}
-    for threads, per_sm in ((32, 0), (96, 2), (128, 0), (256, 1), (544, 0), (1024, 1)):
-        graph.set_launch(threads, per_sm)
+    shapes = [("batch", 32, 0), ("batch", 96, 2), ("batch", 128, 0), ("batch", 256, 1),
+              ("batch", 544, 0), ("batch", 1024, 1), ("latency", 544, 0), ("latency", 640, 0),
+              ("latency", 0, 0), ("latency", 0, 1), ("latency", 576, 1)]
+    for kernel, threads, per_sm in shapes:
+        graph.set_launch(kernel, threads, per_sm)
         for p in PRECS:
             got = gpu_decode(q, graph, b.syndromes, b.prior, 50, 0.75, p)
             for k in got:
-                np.testing.assert_array_equal(got[k], ref[p][k], err_msg=f"{threads}x{per_sm} {p} {k}")
-    graph.set_launch(0, 0)
+                np.testing.assert_array_equal(got[k], ref[p][k], err_msg=f"{kernel} {threads}x{per_sm} {p} {k}")
+    graph.set_launch("auto")
+    # the latency kernel needs m <= 2*threads and n <= 2*threads, threads <= 640
+    for bad_threads in (256, 1024):
+        with pytest.raises(q.QldpcError) as ei:
+            graph.set_launch("latency", bad_threads, 0)
+        assert ei.value.status == q.QLDPC_ERR_UNSUPPORTED
+    with pytest.raises(q.QldpcError) as ei:      # two 576-thread latency blocks do not fit an SM
+        graph.set_launch("latency", 576, 2)
+    assert ei.value.status == q.QLDPC_ERR_UNSUPPORTED
+    with pytest.raises(q.QldpcError) as ei:
+        graph.set_launch("latency", 256, 0)
+    assert ei.value.status == q.QLDPC_ERR_UNSUPPORTED
+    with pytest.raises(q.QldpcError) as ei:
+        graph.set_launch("auto", 256, 0)
+    assert ei.value.status == q.QLDPC_ERR_INVALID_ARG
 
 
 # ---------------------------------------------------------------------------------------------
@@ -278,6 +337,31 @@ def test_host_buffer_path_matches_device_path(q):
             np.testing.assert_array_equal(err, dev["err"])
             np.testing.assert_array_equal(iters, dev["iters"])
             np.testing.assert_array_equal(ok, dev["ok"])
+
+
+def test_host_path_with_pinned_buffers(q):
+    """Page-locked buffers take the no-copy path (the kernel reads/writes host memory); pageable
+    ones the staged path; both equal the device path, for single shots and a large batch."""
+    code = w.lp_code(1054)
+    graph = q.Graph.from_csr(code.hz_csr)
+    pin = lambda shape, dt: torch.empty(shape, dtype=dt).pin_memory().numpy()
+    for precision in PRECS:
+        for shots in (1, 3, 5000):
+            b = w.x_error_batch(code, 0.04, shots, seed=41 + shots)
+            dev = gpu_decode(q, graph, b.syndromes, b.prior, 50, 0.75, precision)
+            syn = pin((shots, graph.m), torch.uint8)
+            syn[:] = b.syndromes
+            outs = (pin((shots, graph.n), torch.uint8), pin((shots,), torch.int32), pin((shots,), torch.uint8))
+            for o in outs:
+                o.fill(0x5A if o.dtype == np.uint8 else -3)
+            err, iters, ok = q.decode_host(graph, syn, b.prior, 50, 0.75, precision, out=outs)
+            np.testing.assert_array_equal(err, dev["err"])
+            np.testing.assert_array_equal(iters, dev["iters"])
+            np.testing.assert_array_equal(ok, dev["ok"])
+            # mixed: pinned syndromes, pageable outputs -> staged copies
+            err2, iters2, ok2 = q.decode_host(graph, syn, b.prior, 50, 0.75, precision)
+            np.testing.assert_array_equal(err2, dev["err"])
+            np.testing.assert_array_equal(iters2, dev["iters"])
 
 
 def test_side_stream(q):

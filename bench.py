@@ -47,8 +47,8 @@ ALU_LANES_PER_SM = 128          # FP32/INT32 lanes per SM, one operation per lan
 
 # DRAM traffic of one decoder launch from an ncu capture, valid only for the kernel source it was
 # measured on (profiles/msa_flood_lp1054_b65536_fp32.md); reported as null once the source changes.
-NCU_TRAFFIC = {"source_sha16": "6d32bde14398b1f2", "bytes_per_launch": 30554112 + 14575104,
-               "profile": "profiles/msa_flood_lp1054_b65536_fp32.md"}
+NCU_TRAFFIC = {"source_sha16": "0637d7609c5d1aea", "bytes_per_launch": 30676224 + 14220032,
+               "profile": "profiles/msa_batch_lp1054_b65536_fp32.md"}
 
 WORKLOAD = "LP-1054 H_Z (465x1054, E=3720), iid X noise p=0.01..0.05, B=65536/step, max 50 it, alpha 0.75"
 
@@ -280,7 +280,7 @@ def run_ours(args, rank, world, local):
     roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3),
                 "unit": "Tops/s", "frac": round(achieved / peak, 4),
                 "traffic": kernel_traffic() if B == BATCH and args.precision == "fp32" else None,
-                "kernel": "msa_flood_kernel", "ops_per_launch": ops,
+                "kernel": "msa_batch_kernel", "ops_per_launch": ops,
                 "units": "10 ALU ops per edge per iteration x E=3720 x iterations run",
                 "peak_basis": f"{props.multi_processor_count} SMs x {ALU_LANES_PER_SM} lanes x {max_mhz:.0f} MHz (max SM clock)",
                 "hbm_algorithmic_gbs": round((h.m + h.n + 5) * B / (ms_per_step / 1e3) / 1e9, 2),

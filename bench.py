@@ -82,6 +82,26 @@ def kernel_traffic():
     return NCU_TRAFFIC["bytes_per_launch"] if sha == NCU_TRAFFIC["source_sha16"] else None
 
 
+def shard(rank: int, world: int, batch: int):
+    """Weak scaling over replicas: rank r decodes its own `batch` shots [r*batch, (r+1)*batch).
+
+    Shots are independent and the sampler is counter-based, so the shards are disjoint and their
+    union is the single-process sequence of world*batch shots; no data crosses ranks.
+    """
+    return rank * batch, batch
+
+
+def reduce_max(x: float, device=None) -> float:
+    """The slowest rank's value (the job's time); a no-op outside torch.distributed."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return x
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def make_batches(batch: int, first_shot: int):
     from paper_2508_07879_gb300 import workloads as w
     code = w.lp_code(1054)
@@ -220,7 +240,8 @@ def run_ours(args, rank, world, local):
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     B = args.batch
-    code, batches = make_batches(B, first_shot=rank * B)     # each rank its own shots (weak scaling)
+    first, _ = shard(rank, world, B)
+    code, batches = make_batches(B, first_shot=first)       # each rank its own shots (weak scaling)
     h = batches[0].h
     graph = qldpc.Graph.from_csr(h)
     dev = torch.device("cuda", local)
@@ -259,11 +280,8 @@ def run_ours(args, rank, world, local):
         e1.record(stream)
         stream.synchronize()
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
+    ms = reduce_max(e0.elapsed_time(e1), dev)
     if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
     ms_per_step = ms / args.steps
     value = world * B * args.steps / (ms / 1e3)
@@ -341,11 +359,7 @@ def measure_e2e(qldpc, graph, batches, args, B, world, dev):
     t0 = time.perf_counter()
     for i in range(steps):
         qldpc.decode_host(graph, syn_h[i % 5], pri_h[i % 5], MAX_ITER, ALPHA, args.precision, out=(err, it, ok))
-    dt = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([dt], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dt = float(t.item())
+    dt = reduce_max(time.perf_counter() - t0, dev)
     return {"value": world * B * steps / dt, "unit": "syndromes/s",
             "h2d_bytes_per_step": B * h.m + h.n * 4, "d2h_bytes_per_step": B * (h.n + 4 + 1),
             "steps": steps, "path": "qldpc_decode_host, pinned host buffers, synchronous per step"}

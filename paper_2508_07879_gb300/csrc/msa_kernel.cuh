@@ -212,15 +212,17 @@ __device__ __forceinline__ typename P::acc_t var_step_global(int v, int N, uint3
     return var_step_exact<P, D>(e, M, gamma, prev, slots, parity);
 }
 
+// Variable step of the batch kernel for one variable: dispatch on its degree (internal variables
+// are sorted by degree, so the lanes of a warp almost always take the same case).
 template <class P, int DV>
-__device__ __forceinline__ typename P::acc_t var_step_batch(int deg, int v, int N, uint32_t M, const uint32_t *vslot,
+__device__ __forceinline__ typename P::acc_t var_step_batch(int deg, int u, int N, uint32_t M, const uint32_t *vslot,
                                                             typename P::acc_t gamma, bool prev,
                                                             typename P::msg_t *slots, uint32_t *parity)
 {
     switch (deg) {
 #define QLDPC_CASE(D)                                                                           \
     case D:                                                                                     \
-        if constexpr (D <= DV) return var_step_global<P, D>(v, N, M, vslot, gamma, prev, slots, parity); \
+        if constexpr (D <= DV) return var_step_global<P, D>(u, N, M, vslot, gamma, prev, slots, parity); \
         break;
         QLDPC_DEG_CASES(QLDPC_CASE)
 #undef QLDPC_CASE
@@ -251,10 +253,10 @@ __global__ void __launch_bounds__(1024, 1) msa_batch_kernel(const LaunchParams p
 
     // Prior LLRs: loaded once per block, shared by all its shots.
     int bad = 0;
-    for (int v = tid; v < N; v += T) {
-        const float g = pr.prior[v];
+    for (int u = tid; u < N; u += T) {
+        const float g = pr.prior[__ldg(pr.g.vperm + u)];
         bad |= !isfinite(g);
-        gam[v] = P::quantize(g);
+        gam[u] = P::quantize(g);
     }
     bad = __syncthreads_or(bad);
 
@@ -277,16 +279,16 @@ __global__ void __launch_bounds__(1024, 1) msa_batch_kernel(const LaunchParams p
         const uint8_t *s = pr.syn + size_t(b) * M;
         for (int c = tid; c < M; c += T) parity[c] = (s[c] & 1u) * 3u;
         __syncthreads();
-        for (int v = tid; v < N; v += T) {
-            const acc_t g = gam[v];
-            const int deg = __ldg(pr.g.vdeg + v);
+        for (int u = tid; u < N; u += T) {
+            const acc_t g = gam[u];
+            const int deg = __ldg(pr.g.vdeg + u);
             const bool d = P::neg(g);
             for (int k = 0; k < deg; ++k) {
-                const uint32_t e = __ldg(pr.g.vslot + size_t(k) * N + v);
+                const uint32_t e = __ldg(pr.g.vslot + size_t(k) * N + u);
                 slots[slot_of(e, uint32_t(M))] = P::to_msg(g);
                 if (d) flip_check(parity, check_of(e));
             }
-            Qs[v] = g;
+            Qs[u] = g;
         }
         __syncthreads();
 
@@ -300,14 +302,15 @@ __global__ void __launch_bounds__(1024, 1) msa_batch_kernel(const LaunchParams p
             }
             all = __syncthreads_and(ok);
             if (last || (early && all)) break;
-            for (int v = tid; v < N; v += T)
-                Qs[v] = var_step_batch<P, DV>(__ldg(pr.g.vdeg + v), v, N, uint32_t(M), pr.g.vslot, gam[v],
-                                              P::neg(Qs[v]), slots, parity);
+            for (int u = tid; u < N; u += T)
+                Qs[u] = var_step_batch<P, DV>(__ldg(pr.g.vdeg + u), u, N, uint32_t(M), pr.g.vslot, gam[u],
+                                              P::neg(Qs[u]), slots, parity);
             __syncthreads();
         }
 
-        for (int v = tid; v < N; v += T) {
-            const acc_t q = Qs[v];
+        for (int u = tid; u < N; u += T) {
+            const acc_t q = Qs[u];
+            const uint32_t v = __ldg(pr.g.vperm + u);
             err[v] = P::neg(q) ? 1 : 0;
             if (pr.post) pr.post[size_t(b) * N + v] = P::post(q);
         }
@@ -363,24 +366,24 @@ __global__ void __launch_bounds__(kLatencyMaxThreads, 1) msa_latency_kernel(cons
         const int c = tid + i * T;
         cdeg[i] = c < M ? (UNIFORM ? DC : int(__ldg(pr.g.rdeg + c))) : -1;
     }
-    // Variables v = order[tid + i*T] (heaviest first, so the few second-pass variables are the
-    // lightest): edge lists, degree and prior in registers.
+    // Internal variables u = tid + i*T (heaviest first, so the few second-pass variables are the
+    // lightest): edge lists, degree and prior in registers; vid = original index for the outputs.
     uint32_t ev[kLatVnPerThread][DV];
     int vdeg[kLatVnPerThread], vid[kLatVnPerThread];
     acc_t gam[kLatVnPerThread];
     int bad = 0;
 #pragma unroll
     for (int i = 0; i < kLatVnPerThread; ++i) {
-        const int t = tid + i * T;
-        const int v = t < N ? int(__ldg(pr.g.vorder + t)) : N;
+        const int u = tid + i * T;
+        const int v = u < N ? int(__ldg(pr.g.vperm + u)) : N;
         vid[i] = v;
-        vdeg[i] = v < N ? int(__ldg(pr.g.vdeg + v)) : -1;
+        vdeg[i] = u < N ? int(__ldg(pr.g.vdeg + u)) : -1;
+#pragma unroll
+        for (int k = 0; k < DV; ++k)
+            ev[i][k] = (k < vdeg[i]) ? __ldg(pr.g.vslot + size_t(k) * N + u) : 0u;
         const float g = v < N ? pr.prior[v] : 0.0f;
         bad |= !isfinite(g);
         gam[i] = P::quantize(g);
-#pragma unroll
-        for (int k = 0; k < DV; ++k)
-            ev[i][k] = (k < vdeg[i]) ? __ldg(pr.g.vslot + size_t(k) * N + (v < N ? v : 0)) : 0u;
     }
     bad = __syncthreads_or(bad);
 

@@ -11,13 +11,14 @@ namespace qldpc {
 
 // Tanner graph in the kernels' layout.  Messages of check i live in shared-memory "slots"
 // j*m + i (j = position of the edge in row i), so a warp working on 32 consecutive checks touches
-// 32 consecutive slots.  Variable v finds its k-th edge (ascending check order) in
-// vslot[k*n + v] = j << 16 | i; the check side needs no index at all.
+// 32 consecutive slots; the check side needs no index at all.  Variables are relabelled in
+// descending-degree order (internal index u, original index vperm[u]); the k-th edge of internal
+// variable u (ascending check order) is vslot[k*n + u] = j << 16 | i.
 struct DeviceGraph {
-    const uint32_t *vslot;   // [dv_max * n] (j << 16) | check of variable v's k-th edge
-    const uint8_t *vdeg;     // [n] column degrees
+    const uint32_t *vslot;   // [dv_max * n] (j << 16) | check of internal variable u's k-th edge
+    const uint8_t *vdeg;     // [n] column degree of internal variable u
     const uint8_t *rdeg;     // [m] row degrees
-    const uint32_t *vorder;  // [n] variables by descending degree (latency kernel's assignment)
+    const uint32_t *vperm;   // [n] original index of internal variable u
     int32_t m, n;
     int32_t dc_max, dv_max;  // largest row / column degree
 };

@@ -57,6 +57,8 @@ typedef struct qldpc_graph qldpc_graph;   /* opaque; owned by the library */
 
 typedef enum qldpc_status {
     QLDPC_OK = 0,
+    QLDPC_PENDING = 1,            /* (server) the request is not finished yet: poll again */
+    QLDPC_BUSY = 2,               /* (server) the code's ring is full: collect results first */
     QLDPC_ERR_INVALID_ARG = -1,   /* bad pointer, size, CSR structure, alpha, flag or precision */
     QLDPC_ERR_UNSUPPORTED = -2,   /* graph exceeds a kernel limit (degree, shared memory, size) */
     QLDPC_ERR_OOM = -3,           /* device or pinned host allocation failed */
@@ -186,6 +188,72 @@ QLDPC_API int qldpc_decode_host(qldpc_graph *g, const uint8_t *h_syndromes, int3
 
 /* Static, human-readable name of a status code. */
 QLDPC_API const char *qldpc_status_string(int status);
+
+/* ===============================================================================================
+ * Persistent decoding server (continuous batching of single syndrome rounds).
+ *
+ * The paper proposes launching decoders asynchronously so transfers overlap execution (Table 1,
+ * Sec. 3 outlook).  The server takes that to its limit: one kernel stays resident, its worker
+ * blocks each hold one code's graph and priors on chip, and requests flow through per-code rings
+ * of slots in page-locked host memory mapped into the GPU.  A request is admitted as soon as a
+ * worker of its code is free; requests of different codes and sizes decode concurrently; results
+ * come back in the slot.  Decoding is the single-shot algorithm of qldpc_decode_ex, so a request
+ * decodes to the same result alone or in any mix.  Every device-side wait is bounded (idle
+ * timeout, maximum runtime); the library relaunches the workers when requests arrive after they
+ * left.  submit/poll/replay on one server are serialized by a lock inside it.
+ * =============================================================================================== */
+typedef struct qldpc_server qldpc_server;
+
+enum { QLDPC_SERVER_MAX_CODES = 4 };
+
+typedef struct qldpc_server_config {
+    int32_t precision;            /* QLDPC_FP32 or QLDPC_INT16 */
+    int32_t max_iter;             /* >= 0 */
+    float alpha;                  /* as for qldpc_decode_ex */
+    uint32_t flags;               /* QLDPC_NO_EARLY_STOP or 0 */
+    int32_t ring_capacity;        /* slots per code, a power of two in [2, 2^20]; 0 = 256 */
+    int32_t threads_per_block;    /* 0 = automatic */
+    int32_t blocks[QLDPC_SERVER_MAX_CODES];   /* worker blocks per code; 0 = equal share of the SMs */
+    int64_t idle_timeout_ns;      /* workers leave after this long without a request; <= 0: 0.5 s */
+    int64_t max_runtime_ns;       /* workers leave after this long; <= 0: 600 s */
+} qldpc_server_config;
+
+/* Create a server for ncodes (1..4) graphs of the current device with host priors[c] (float[n_c],
+ * copied).  Allocates the rings (page-locked host memory) and device state; the kernel starts on
+ * the first request.  INVALID_ARG on bad arguments or non-finite priors; UNSUPPORTED if a graph
+ * exceeds the single-shot kernel's limits or the workers cannot all be resident. */
+QLDPC_API int qldpc_server_create(const qldpc_graph *const *graphs, const float *const *priors,
+                                  int32_t ncodes, const qldpc_server_config *cfg,
+                                  qldpc_server **out);
+
+/* Publish one request: syndrome (host uint8[m_code]) for code `code`.  Returns QLDPC_OK and a
+ * ticket (the code's request sequence number), or QLDPC_BUSY when all ring slots of the code hold
+ * results not yet collected by qldpc_server_poll. */
+QLDPC_API int qldpc_server_submit(qldpc_server *s, int32_t code, const uint8_t *syndrome,
+                                  uint64_t *ticket);
+
+/* Collect a request: QLDPC_OK with e_hat (host uint8[n_code]), iterations and ok copied out (any
+ * output pointer may be NULL) and the slot released; QLDPC_PENDING while it runs; INVALID_ARG for
+ * an unknown or already collected ticket. */
+QLDPC_API int qldpc_server_poll(qldpc_server *s, int32_t code, uint64_t ticket, uint8_t *err,
+                                int32_t *iters, uint8_t *ok);
+
+/* Open-loop load generator and latency recorder: submits request i (code codes[i], syndrome at
+ * syndromes + syn_offsets[i]) at arrival_ns[i] after the call starts (non-decreasing), collects
+ * every result (e_hat at errs + err_offsets[i], iters[i], oks[i]) and records latency_ns[i] =
+ * completion seen by the host - scheduled arrival.  Returns QLDPC_ERR_TIMEOUT if results are still
+ * missing timeout_ns after the last arrival (<= 0: 10 s). */
+QLDPC_API int qldpc_server_replay(qldpc_server *s, int32_t nreq, const int32_t *codes,
+                                  const uint8_t *syndromes, const int64_t *syn_offsets,
+                                  const int64_t *arrival_ns, uint8_t *errs, const int64_t *err_offsets,
+                                  int32_t *iters, uint8_t *oks, int64_t *latency_ns, int64_t timeout_ns);
+
+/* Status bits the workers left: 1 = idle timeout, 2 = maximum runtime, 4 = spin cap, 8 = stopped. */
+QLDPC_API int qldpc_server_status(qldpc_server *s, uint32_t *status);
+
+/* Stop the workers (they leave at their next poll), wait for the kernel and free everything.
+ * Uncollected results are lost.  NULL is ignored. */
+QLDPC_API void qldpc_server_destroy(qldpc_server *s);
 
 /* Size of the library's static device scratch used by qldpc_decode_host_noalloc (4 MiB). */
 enum { QLDPC_NOALLOC_SCRATCH_BYTES = 4 * 1024 * 1024 };

@@ -1,0 +1,47 @@
+// The opaque qldpc_graph of the C ABI and the host helpers shared by the library's translation
+// units (qldpc_host.cpp: graphs and decodes; qldpc_server.cpp: the persistent server).  Internal.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <mutex>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "msa_launch.h"
+#include "qldpc.h"
+
+struct qldpc_graph {
+    int device = 0;
+    int sm_count = 0;
+    size_t smem_optin = 0;      // max dynamic shared memory per block (opt-in)
+    int32_t m = 0, n = 0, nnz = 0, dc_max = 0, dv_max = 0;
+    bool uniform_rows = false;  // every row has degree dc_max
+    void *d_block = nullptr;    // one device allocation for all graph arrays
+    qldpc::DeviceGraph dg{};
+    // launch overrides (0 = automatic)
+    int user_kernel = QLDPC_KERNEL_AUTO, user_threads = 0, user_blocks_per_sm = 0;
+    // staging for qldpc_decode_host
+    std::mutex host_mu;
+    int32_t cap = 0;
+    void *d_stage = nullptr;
+    uint8_t *d_syn = nullptr, *d_err = nullptr, *d_ok = nullptr;
+    int32_t *d_iters = nullptr;
+    float *d_prior = nullptr;
+    uint8_t *h_stage = nullptr;     // page-locked copy-back buffer for small batches
+    size_t h_stage_bytes = 0;
+    std::vector<float> prior_cache;
+    bool prior_valid = false;
+};
+
+namespace qldpc {
+namespace detail {
+
+int cuda_status(cudaError_t e);                                             // cudaError -> qldpc_status
+int ensure_kernel_attrs(const void *k, size_t smem, size_t smem_optin);     // >48 KB dynamic smem opt-in
+int check_device(const qldpc_graph *g);                                     // graph belongs to the current device
+int alpha_fixed(float alpha);                                               // round(alpha*2^15), -1 outside (0,1]
+
+}  // namespace detail
+}  // namespace qldpc

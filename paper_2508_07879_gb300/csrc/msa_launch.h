@@ -97,6 +97,54 @@ constexpr int kLatencyCnPerThread = 2;
 constexpr int kLatencyVnPerThread = 2;
 constexpr int kLatencyMaxThreads = 640;
 
+// ---------------------------------------------------------------------------------------------
+// Persistent server (server_kernel.cuh): worker blocks that poll per-code request rings.
+// ---------------------------------------------------------------------------------------------
+constexpr int kServerMaxCodes = 4;
+
+// Status bits a server kernel leaves in ServerParams::status.
+constexpr uint32_t kServerIdleExit = 1u;     // a worker left after idle_ns without a request
+constexpr uint32_t kServerTimeLimit = 2u;    // a worker left at max_runtime_ns
+constexpr uint32_t kServerSpinLimit = 4u;    // a worker left at the spin-count safety cap
+constexpr uint32_t kServerStopped = 8u;      // a worker left on the host's stop flag
+
+// Request slot in the ring (page-locked host memory mapped into the device address space):
+//   [0, 4)   done: request sequence number + 1, written by the device last (release)
+//   [4, 8)   iterations run          [8] ok
+//   [syn_off, syn_off + m)  syndrome bits, written by the host before it publishes the request
+//   [err_off, err_off + n)  e_hat, written by the device
+struct ServerCode {
+    DeviceGraph g;
+    const float *prior;         // device [n]
+    unsigned char *ring;        // ring_capacity slots of slot_bytes
+    const uint32_t *tail;       // host-written count of published requests
+    uint32_t *head;             // device count of claimed requests
+    int32_t slot_bytes, syn_off, err_off;
+    int32_t first_block;        // worker blocks [first_block, next code's first_block)
+};
+
+struct ServerParams {
+    ServerCode code[kServerMaxCodes];
+    int32_t ncodes;
+    int32_t ring_capacity;      // power of two
+    int32_t max_iter;
+    float alpha;
+    int32_t alpha_q;
+    uint32_t flags;
+    const uint32_t *stop;       // host-written stop flag
+    uint32_t *status;           // device status bits
+    uint64_t idle_ns, max_runtime_ns;
+};
+
+inline int server_slot_bytes(int m, int n) { return int(align16(16 + size_t(m)) + align16(size_t(n))); }
+
+const void *server_kernel_f32(const KernelChoice &kc);
+const void *server_kernel_i16(const KernelChoice &kc);
+cudaError_t launch_server_f32(const ServerParams &p, const KernelChoice &kc, int blocks, int threads,
+                              size_t smem, cudaStream_t stream);
+cudaError_t launch_server_i16(const ServerParams &p, const KernelChoice &kc, int blocks, int threads,
+                              size_t smem, cudaStream_t stream);
+
 // Per-precision instantiation tables (one translation unit each).
 const void *msa_kernel_f32(const KernelChoice &kc);
 const void *msa_kernel_i16(const KernelChoice &kc);

@@ -14,32 +14,11 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include "graph.h"
 #include "msa_launch.h"
 
 using namespace qldpc;
-
-struct qldpc_graph {
-    int device = 0;
-    int sm_count = 0;
-    size_t smem_optin = 0;      // max dynamic shared memory per block (opt-in)
-    int32_t m = 0, n = 0, nnz = 0, dc_max = 0, dv_max = 0;
-    bool uniform_rows = false;  // every row has degree dc_max
-    void *d_block = nullptr;    // one device allocation for all graph arrays
-    DeviceGraph dg{};
-    // launch overrides (0 = automatic)
-    int user_kernel = QLDPC_KERNEL_AUTO, user_threads = 0, user_blocks_per_sm = 0;
-    // staging for qldpc_decode_host
-    std::mutex host_mu;
-    int32_t cap = 0;
-    void *d_stage = nullptr;
-    uint8_t *d_syn = nullptr, *d_err = nullptr, *d_ok = nullptr;
-    int32_t *d_iters = nullptr;
-    float *d_prior = nullptr;
-    uint8_t *h_stage = nullptr;     // page-locked copy-back buffer for small batches
-    size_t h_stage_bytes = 0;
-    std::vector<float> prior_cache;
-    bool prior_valid = false;
-};
+using namespace qldpc::detail;
 
 namespace qldpc {
 
@@ -128,6 +107,11 @@ int validate_and_layout(const int32_t *row_ptr, const int32_t *col_idx, int32_t 
     }
     return QLDPC_OK;
 }
+
+}  // namespace
+
+namespace qldpc {
+namespace detail {
 
 bool finite_alpha(float a) { return std::isfinite(a) && a > 0.0f; }
 
@@ -401,7 +385,8 @@ void *mapped_host_range(const void *p, size_t bytes)
     return a.devicePointer;
 }
 
-}  // namespace
+}  // namespace detail
+}  // namespace qldpc
 
 extern "C" {
 
@@ -673,6 +658,8 @@ const char *qldpc_status_string(int status)
 {
     switch (status) {
     case QLDPC_OK: return "QLDPC_OK";
+    case QLDPC_PENDING: return "QLDPC_PENDING: the request is still running";
+    case QLDPC_BUSY: return "QLDPC_BUSY: the ring is full";
     case QLDPC_ERR_INVALID_ARG: return "QLDPC_ERR_INVALID_ARG: invalid argument";
     case QLDPC_ERR_UNSUPPORTED: return "QLDPC_ERR_UNSUPPORTED: graph exceeds a kernel limit";
     case QLDPC_ERR_OOM: return "QLDPC_ERR_OOM: out of memory";

@@ -1,0 +1,364 @@
+// Host side of the persistent decoding server (include/qldpc.h: qldpc_server_*).
+//
+// The server owns, per code, a ring of request slots in page-locked host memory mapped into the
+// device address space, a device counter of claimed requests, and the device copy of the code's
+// prior; one persistent kernel (server_kernel.cuh) runs all worker blocks on a private stream.
+// The host publishes a request by writing its syndrome into the next slot and bumping the ring's
+// tail with a release store; it learns completion from the slot's done word (acquire load).
+// Relaunching after the workers left (idle) is safe: workers only leave with every published
+// request claimed and finished, and the counters survive in memory.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "graph.h"
+#include "msa_launch.h"
+#include "qldpc.h"
+
+using namespace qldpc;
+using namespace qldpc::detail;
+
+struct qldpc_server {
+    int device = 0;
+    int precision = QLDPC_FP32;
+    int ncodes = 0;
+    const qldpc_graph *graphs[kServerMaxCodes] = {};
+    int32_t m[kServerMaxCodes] = {}, n[kServerMaxCodes] = {};
+    int32_t capacity = 0;
+    ServerParams sp{};
+    KernelChoice kc{};
+    int blocks = 0, threads = 0;
+    size_t smem = 0;
+    cudaStream_t stream = nullptr;
+    unsigned char *host_block = nullptr;    // rings + tails + stop (page-locked, mapped)
+    unsigned char *ring[kServerMaxCodes] = {};
+    uint32_t *tail[kServerMaxCodes] = {};   // one cache line each
+    uint32_t *stop = nullptr;
+    void *dev_block = nullptr;              // heads + status + priors
+    uint32_t *head = nullptr;
+    uint32_t *status = nullptr;
+    uint64_t next[kServerMaxCodes] = {};    // next sequence number to submit
+    std::vector<uint8_t> busy[kServerMaxCodes];   // slot holds a request whose result is uncollected
+    bool launched = false;
+    std::mutex mu;
+};
+
+namespace {
+
+int launch_server(qldpc_server *s)
+{
+    cudaError_t e = s->precision == QLDPC_INT16
+                        ? launch_server_i16(s->sp, s->kc, s->blocks, s->threads, s->smem, s->stream)
+                        : launch_server_f32(s->sp, s->kc, s->blocks, s->threads, s->smem, s->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    s->launched = true;
+    return QLDPC_OK;
+}
+
+// Relaunch the workers if they left (idle timeout) while requests may be waiting.
+int ensure_running(qldpc_server *s)
+{
+    if (s->launched) {
+        const cudaError_t q = cudaStreamQuery(s->stream);
+        if (q == cudaErrorNotReady) return QLDPC_OK;
+        if (q != cudaSuccess) return cuda_status(q);
+        s->launched = false;
+    }
+    return launch_server(s);
+}
+
+unsigned char *slot_ptr(qldpc_server *s, int code, uint64_t seq)
+{
+    return s->ring[code] + size_t(seq & uint64_t(s->capacity - 1)) * size_t(s->sp.code[code].slot_bytes);
+}
+
+int submit_locked(qldpc_server *s, int32_t code, const uint8_t *syndrome, uint64_t *ticket)
+{
+    const uint64_t seq = s->next[code];
+    const size_t idx = size_t(seq & uint64_t(s->capacity - 1));
+    if (s->busy[code][idx]) return QLDPC_BUSY;
+    unsigned char *slot = slot_ptr(s, code, seq);
+    std::memcpy(slot + s->sp.code[code].syn_off, syndrome, size_t(s->m[code]));
+    __atomic_store_n(reinterpret_cast<uint32_t *>(slot), 0u, __ATOMIC_RELAXED);
+    s->busy[code][idx] = 1;
+    s->next[code] = seq + 1;
+    __atomic_store_n(s->tail[code], uint32_t(seq + 1), __ATOMIC_RELEASE);   // publish
+    if (int rc = ensure_running(s)) return rc;
+    *ticket = seq;
+    return QLDPC_OK;
+}
+
+// QLDPC_OK with the outputs copied (and the slot released) once the request is done.
+int poll_locked(qldpc_server *s, int32_t code, uint64_t ticket, uint8_t *err, int32_t *iters, uint8_t *ok)
+{
+    if (ticket >= s->next[code] || ticket + uint64_t(s->capacity) < s->next[code]) return QLDPC_ERR_INVALID_ARG;
+    const size_t idx = size_t(ticket & uint64_t(s->capacity - 1));
+    if (!s->busy[code][idx]) return QLDPC_ERR_INVALID_ARG;     // already collected
+    unsigned char *slot = slot_ptr(s, code, ticket);
+    const uint32_t done = __atomic_load_n(reinterpret_cast<uint32_t *>(slot), __ATOMIC_ACQUIRE);
+    if (done != uint32_t(ticket + 1)) {
+        if (int rc = ensure_running(s)) return rc;
+        return QLDPC_PENDING;
+    }
+    if (err) std::memcpy(err, slot + s->sp.code[code].err_off, size_t(s->n[code]));
+    if (iters) std::memcpy(iters, slot + 4, 4);
+    if (ok) *ok = slot[8];
+    s->busy[code][idx] = 0;
+    return QLDPC_OK;
+}
+
+void free_server(qldpc_server *s)
+{
+    if (s->stream) cudaStreamDestroy(s->stream);
+    if (s->host_block) cudaFreeHost(s->host_block);
+    if (s->dev_block) cudaFree(s->dev_block);
+    delete s;
+}
+
+}  // namespace
+
+extern "C" {
+
+int qldpc_server_create(const qldpc_graph *const *graphs, const float *const *priors, int32_t ncodes,
+                        const qldpc_server_config *cfg, qldpc_server **out)
+{
+    if (!out) return QLDPC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!graphs || !priors || !cfg || ncodes < 1 || ncodes > QLDPC_SERVER_MAX_CODES) return QLDPC_ERR_INVALID_ARG;
+    if (cfg->precision != QLDPC_FP32 && cfg->precision != QLDPC_INT16) return QLDPC_ERR_INVALID_ARG;
+    if ((cfg->flags & ~uint32_t(QLDPC_NO_EARLY_STOP)) != 0 || cfg->max_iter < 0) return QLDPC_ERR_INVALID_ARG;
+    if (!std::isfinite(cfg->alpha) || cfg->alpha <= 0.0f) return QLDPC_ERR_INVALID_ARG;
+    const int aq = cfg->precision == QLDPC_INT16 ? alpha_fixed(cfg->alpha) : 0;
+    if (aq < 0) return QLDPC_ERR_INVALID_ARG;
+    const int32_t cap = cfg->ring_capacity ? cfg->ring_capacity : 256;
+    if (cap < 2 || cap > (1 << 20) || (cap & (cap - 1))) return QLDPC_ERR_INVALID_ARG;
+    for (int c = 0; c < ncodes; ++c) {
+        if (!graphs[c] || !priors[c] || cfg->blocks[c] < 0) return QLDPC_ERR_INVALID_ARG;
+        for (int32_t v = 0; v < graphs[c]->n; ++v)
+            if (!std::isfinite(priors[c][v])) return QLDPC_ERR_INVALID_ARG;
+        if (graphs[c]->device != graphs[0]->device) return QLDPC_ERR_INVALID_ARG;
+    }
+    if (int rc = check_device(graphs[0])) return rc;
+
+    qldpc_server *s = new (std::nothrow) qldpc_server();
+    if (!s) return QLDPC_ERR_OOM;
+    s->device = graphs[0]->device;
+    s->precision = cfg->precision;
+    s->ncodes = ncodes;
+    s->capacity = cap;
+
+    // one kernel variant and block shape for all codes (the largest degrees and sizes)
+    int dc = 0, dv = 0, want = 32;
+    bool uniform = true;
+    size_t smem = 0;
+    for (int c = 0; c < ncodes; ++c) {
+        const qldpc_graph *g = graphs[c];
+        s->graphs[c] = g;
+        s->m[c] = g->m;
+        s->n[c] = g->n;
+        dc = std::max(dc, g->dc_max);
+        dv = std::max(dv, g->dv_max);
+        uniform = uniform && g->uniform_rows && g->dc_max == graphs[0]->dc_max;
+        const int one = (std::max(g->m, g->n) + 31) / 32 * 32;
+        const int two = (std::max((g->m + 1) / 2, (g->n + 1) / 2) + 31) / 32 * 32;
+        want = std::max(want, one <= kLatencyMaxThreads ? one : two);
+        smem = std::max(smem, latency_layout(g->m, g->dc_max, msg_bytes(cfg->precision)).total);
+    }
+    s->kc = (uniform && dc >= 6 && dc <= 8) ? KernelChoice{true, dc, true, dv <= 4 ? 4 : dv <= 8 ? 8 : 16}
+                                            : KernelChoice{true, dc <= 8 ? 8 : dc <= 16 ? 16 : 32, false,
+                                                           dv <= 4 ? 4 : dv <= 8 ? 8 : 16};
+    s->threads = cfg->threads_per_block ? cfg->threads_per_block : std::min(want, kLatencyMaxThreads);
+    bool fits = s->threads >= 32 && s->threads <= kLatencyMaxThreads && s->threads % 32 == 0;
+    for (int c = 0; c < ncodes; ++c)
+        fits = fits && graphs[c]->m <= kLatencyCnPerThread * s->threads &&
+               graphs[c]->n <= kLatencyVnPerThread * s->threads;
+    s->smem = smem;
+    const void *k = cfg->precision == QLDPC_INT16 ? server_kernel_i16(s->kc) : server_kernel_f32(s->kc);
+    if (!fits || !k) {
+        delete s;
+        return QLDPC_ERR_UNSUPPORTED;
+    }
+    if (int rc = ensure_kernel_attrs(k, smem, graphs[0]->smem_optin)) {
+        delete s;
+        return rc;
+    }
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, s->threads, smem) != cudaSuccess || per_sm < 1) {
+        delete s;
+        return QLDPC_ERR_UNSUPPORTED;
+    }
+    // Worker blocks per code: as configured, else an equal share of the resident slots.
+    const int resident = per_sm * graphs[0]->sm_count;
+    int total = 0;
+    int nb[kServerMaxCodes] = {};
+    for (int c = 0; c < ncodes; ++c) {
+        nb[c] = cfg->blocks[c] ? cfg->blocks[c] : std::max(1, resident / ncodes);
+        total += nb[c];
+    }
+    if (total > resident) {   // every worker must be resident: a waiting block would never run
+        delete s;
+        return QLDPC_ERR_UNSUPPORTED;
+    }
+    s->blocks = total;
+
+    // page-locked, mapped host memory: rings, tails, stop flag
+    size_t host_bytes = 0;
+    size_t ring_off[kServerMaxCodes];
+    for (int c = 0; c < ncodes; ++c) {
+        ring_off[c] = host_bytes;
+        host_bytes += size_t(cap) * size_t(server_slot_bytes(s->m[c], s->n[c]));
+    }
+    const size_t tail_off = host_bytes;
+    host_bytes += 64 * kServerMaxCodes + 64;
+    void *hb = nullptr;
+    cudaError_t e = cudaHostAlloc(&hb, host_bytes, cudaHostAllocMapped | cudaHostAllocPortable);
+    if (e != cudaSuccess) {
+        delete s;
+        return cuda_status(e);
+    }
+    std::memset(hb, 0, host_bytes);
+    s->host_block = static_cast<unsigned char *>(hb);
+    for (int c = 0; c < kServerMaxCodes; ++c) s->tail[c] = reinterpret_cast<uint32_t *>(s->host_block + tail_off + 64 * c);
+    s->stop = reinterpret_cast<uint32_t *>(s->host_block + tail_off + 64 * kServerMaxCodes);
+    void *hb_dev = nullptr;
+    if (cudaHostGetDevicePointer(&hb_dev, hb, 0) != cudaSuccess) {
+        free_server(s);
+        return QLDPC_ERR_CUDA;
+    }
+    unsigned char *hd = static_cast<unsigned char *>(hb_dev);
+
+    // device memory: claim counters, status, priors
+    size_t dev_bytes = 256;
+    size_t prior_off[kServerMaxCodes];
+    for (int c = 0; c < ncodes; ++c) {
+        prior_off[c] = dev_bytes;
+        dev_bytes += align16(size_t(s->n[c]) * sizeof(float));
+    }
+    e = cudaMalloc(&s->dev_block, dev_bytes);
+    if (e == cudaSuccess) e = cudaMemset(s->dev_block, 0, 256);
+    for (int c = 0; c < ncodes && e == cudaSuccess; ++c)
+        e = cudaMemcpy(static_cast<char *>(s->dev_block) + prior_off[c], priors[c], size_t(s->n[c]) * sizeof(float),
+                       cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        free_server(s);
+        return cuda_status(e);
+    }
+    s->head = static_cast<uint32_t *>(s->dev_block);
+    s->status = static_cast<uint32_t *>(s->dev_block) + 32;
+
+    ServerParams &sp = s->sp;
+    sp.ncodes = ncodes;
+    sp.ring_capacity = cap;
+    sp.max_iter = cfg->max_iter;
+    sp.alpha = cfg->alpha;
+    sp.alpha_q = aq;
+    sp.flags = cfg->flags;
+    sp.stop = reinterpret_cast<const uint32_t *>(hd + tail_off + 64 * kServerMaxCodes);
+    sp.status = s->status;
+    sp.idle_ns = uint64_t(cfg->idle_timeout_ns > 0 ? cfg->idle_timeout_ns : 500000000LL);
+    sp.max_runtime_ns = uint64_t(cfg->max_runtime_ns > 0 ? cfg->max_runtime_ns : 600000000000LL);
+    int first = 0;
+    for (int c = 0; c < ncodes; ++c) {
+        ServerCode &sc = sp.code[c];
+        sc.g = graphs[c]->dg;
+        sc.prior = reinterpret_cast<const float *>(static_cast<char *>(s->dev_block) + prior_off[c]);
+        sc.ring = hd + ring_off[c];
+        sc.tail = reinterpret_cast<const uint32_t *>(hd + tail_off + 64 * c);
+        sc.head = s->head + c;
+        sc.slot_bytes = server_slot_bytes(s->m[c], s->n[c]);
+        sc.syn_off = 16;
+        sc.err_off = int32_t(align16(16 + size_t(s->m[c])));
+        sc.first_block = first;
+        first += nb[c];
+        s->ring[c] = s->host_block + ring_off[c];
+        s->busy[c].assign(size_t(cap), 0);
+    }
+    *out = s;
+    return QLDPC_OK;
+}
+
+int qldpc_server_submit(qldpc_server *s, int32_t code, const uint8_t *syndrome, uint64_t *ticket)
+{
+    if (!s || !syndrome || !ticket || code < 0 || code >= s->ncodes) return QLDPC_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    return submit_locked(s, code, syndrome, ticket);
+}
+
+int qldpc_server_poll(qldpc_server *s, int32_t code, uint64_t ticket, uint8_t *err, int32_t *iters, uint8_t *ok)
+{
+    if (!s || code < 0 || code >= s->ncodes) return QLDPC_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    return poll_locked(s, code, ticket, err, iters, ok);
+}
+
+int qldpc_server_replay(qldpc_server *s, int32_t nreq, const int32_t *codes, const uint8_t *syndromes,
+                        const int64_t *syn_offsets, const int64_t *arrival_ns, uint8_t *errs,
+                        const int64_t *err_offsets, int32_t *iters, uint8_t *oks, int64_t *latency_ns,
+                        int64_t timeout_ns)
+{
+    if (!s || nreq < 0) return QLDPC_ERR_INVALID_ARG;
+    if (nreq == 0) return QLDPC_OK;
+    if (!codes || !syndromes || !syn_offsets || !arrival_ns || !errs || !err_offsets || !iters || !oks || !latency_ns)
+        return QLDPC_ERR_INVALID_ARG;
+    for (int32_t i = 0; i < nreq; ++i)
+        if (codes[i] < 0 || codes[i] >= s->ncodes || (i && arrival_ns[i] < arrival_ns[i - 1])) return QLDPC_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    using clock = std::chrono::steady_clock;
+    std::vector<int32_t> inflight;
+    std::vector<uint64_t> tickets(size_t(nreq), 0);
+    inflight.reserve(1024);
+    const auto t0 = clock::now();
+    const int64_t deadline = arrival_ns[nreq - 1] + (timeout_ns > 0 ? timeout_ns : 10000000000LL);
+    int32_t next = 0, completed = 0;
+    while (completed < nreq) {
+        const int64_t now = std::chrono::duration_cast<std::chrono::nanoseconds>(clock::now() - t0).count();
+        if (now > deadline) return QLDPC_ERR_TIMEOUT;
+        while (next < nreq && arrival_ns[next] <= now) {
+            const int rc = submit_locked(s, codes[next], syndromes + syn_offsets[next], &tickets[size_t(next)]);
+            if (rc == QLDPC_BUSY) break;            // ring full: serve completions first
+            if (rc) return rc;
+            inflight.push_back(next++);
+        }
+        for (size_t j = 0; j < inflight.size();) {
+            const int32_t i = inflight[j];
+            const int rc = poll_locked(s, codes[i], tickets[size_t(i)], errs + err_offsets[i], iters + i, oks + i);
+            if (rc == QLDPC_OK) {
+                const int64_t t = std::chrono::duration_cast<std::chrono::nanoseconds>(clock::now() - t0).count();
+                latency_ns[i] = t - arrival_ns[i];
+                ++completed;
+                inflight[j] = inflight.back();
+                inflight.pop_back();
+            } else if (rc == QLDPC_PENDING) {
+                ++j;
+            } else {
+                return rc;
+            }
+        }
+    }
+    return QLDPC_OK;
+}
+
+int qldpc_server_status(qldpc_server *s, uint32_t *status)
+{
+    if (!s || !status) return QLDPC_ERR_INVALID_ARG;
+    return cuda_status(cudaMemcpy(status, s->status, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+}
+
+void qldpc_server_destroy(qldpc_server *s)
+{
+    if (!s) return;
+    __atomic_store_n(s->stop, 1u, __ATOMIC_RELEASE);
+    if (s->stream) cudaStreamSynchronize(s->stream);   // workers leave at the stop flag
+    free_server(s);
+}
+
+}  // extern "C"

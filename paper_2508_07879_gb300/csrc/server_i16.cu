@@ -1,0 +1,14 @@
+// INT16 fixed-point instantiations of the persistent decoding server kernel (see server_kernel.cuh).
+#include "server_kernel.cuh"
+
+namespace qldpc {
+
+const void *server_kernel_i16(const KernelChoice &kc) { return server_table<kern::I16>(kc); }
+
+cudaError_t launch_server_i16(const ServerParams &p, const KernelChoice &kc, int blocks, int threads,
+                              size_t smem, cudaStream_t stream)
+{
+    return server_launch<kern::I16>(p, kc, blocks, threads, smem, stream);
+}
+
+}  // namespace qldpc

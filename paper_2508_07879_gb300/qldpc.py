@@ -17,6 +17,8 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libqldpc.so")
 
 QLDPC_OK = 0
+QLDPC_PENDING = 1
+QLDPC_BUSY = 2
 QLDPC_ERR_INVALID_ARG = -1
 QLDPC_ERR_UNSUPPORTED = -2
 QLDPC_ERR_OOM = -3
@@ -44,6 +46,15 @@ def _load() -> ctypes.CDLL:
 
 
 _lib = _load()
+
+
+class ServerConfig(ctypes.Structure):
+    """qldpc_server_config (include/qldpc.h)."""
+    _fields_ = [("precision", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("alpha", ctypes.c_float),
+                ("flags", ctypes.c_uint32), ("ring_capacity", ctypes.c_int32),
+                ("threads_per_block", ctypes.c_int32), ("blocks", ctypes.c_int32 * 4),
+                ("idle_timeout_ns", ctypes.c_int64), ("max_runtime_ns", ctypes.c_int64)]
+
 _p = ctypes.c_void_p
 _i32 = ctypes.c_int32
 _u32 = ctypes.c_uint32
@@ -63,6 +74,12 @@ _SIGNATURES = {
     "qldpc_decode_host": ([_p, _p, _i32, _p, _i32, _f32, _p, _p, _p, _i32, _u32, _p], ctypes.c_int),
     "qldpc_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "qldpc_decode_host_noalloc": ([_p, _p, _i32, _p, _i32, _f32, _p, _p, _p, _i32, _u32, _p], ctypes.c_int),
+    "qldpc_server_create": ([_p, _p, _i32, ctypes.POINTER(ServerConfig), ctypes.POINTER(_p)], ctypes.c_int),
+    "qldpc_server_submit": ([_p, _i32, _p, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+    "qldpc_server_poll": ([_p, _i32, ctypes.c_uint64, _p, _p, _p], ctypes.c_int),
+    "qldpc_server_replay": ([_p, _i32, _p, _p, _p, _p, _p, _p, _p, _p, _p, ctypes.c_int64], ctypes.c_int),
+    "qldpc_server_status": ([_p, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
+    "qldpc_server_destroy": ([_p], None),
 }
 for _name, (_args, _res) in _SIGNATURES.items():
     _fn = getattr(_lib, _name)
@@ -82,6 +99,12 @@ qldpc_decode_pair = _lib.qldpc_decode_pair
 qldpc_decode_host = _lib.qldpc_decode_host
 qldpc_status_string = _lib.qldpc_status_string
 qldpc_decode_host_noalloc = _lib.qldpc_decode_host_noalloc
+qldpc_server_create = _lib.qldpc_server_create
+qldpc_server_submit = _lib.qldpc_server_submit
+qldpc_server_poll = _lib.qldpc_server_poll
+qldpc_server_replay = _lib.qldpc_server_replay
+qldpc_server_status = _lib.qldpc_server_status
+qldpc_server_destroy = _lib.qldpc_server_destroy
 QLDPC_NOALLOC_SCRATCH_BYTES = 4 * 1024 * 1024
 
 
@@ -270,3 +293,110 @@ def decode_host(graph: Graph, syndromes: np.ndarray, prior: np.ndarray, max_iter
                             float(alpha), _np_ptr(err), _np_ptr(iters), _np_ptr(ok),
                             PRECISIONS[precision], flags, sh), "qldpc_decode_host")
     return err, iters, ok
+
+
+class Server:
+    """Persistent decoding server over up to four codes (qldpc_server_*).
+
+    graphs: list of Graph; priors: list of float32 [n] numpy arrays (host).  The worker kernel starts
+    on the first request and leaves after `idle_timeout_s` without requests (restarted on demand).
+    """
+
+    def __init__(self, graphs, priors, max_iter: int, alpha: float = 0.75, precision: str = "fp32",
+                 early_stop: bool = True, ring_capacity: int = 256, blocks=None,
+                 idle_timeout_s: float = 0.5, max_runtime_s: float = 600.0, threads_per_block: int = 0):
+        self._h = None
+        self.graphs = list(graphs)
+        self._priors = [np.ascontiguousarray(p, dtype=np.float32) for p in priors]
+        cfg = ServerConfig()
+        cfg.precision = PRECISIONS[precision]
+        cfg.max_iter = int(max_iter)
+        cfg.alpha = float(alpha)
+        cfg.flags = 0 if early_stop else QLDPC_NO_EARLY_STOP
+        cfg.ring_capacity = int(ring_capacity)
+        cfg.threads_per_block = int(threads_per_block)
+        for i, b in enumerate(blocks or []):
+            cfg.blocks[i] = int(b)
+        cfg.idle_timeout_ns = int(idle_timeout_s * 1e9)
+        cfg.max_runtime_ns = int(max_runtime_s * 1e9)
+        garr = (ctypes.c_void_p * len(self.graphs))(*[g.handle.value for g in self.graphs])
+        parr = (ctypes.c_void_p * len(self._priors))(*[p.ctypes.data for p in self._priors])
+        h = ctypes.c_void_p()
+        check(qldpc_server_create(garr, parr, len(self.graphs), ctypes.byref(cfg), ctypes.byref(h)),
+              "qldpc_server_create")
+        self._h = h
+
+    def submit(self, code: int, syndrome) -> int:
+        """Returns a ticket, or None when the code's ring is full."""
+        syn = np.ascontiguousarray(syndrome, dtype=np.uint8)
+        if syn.shape != (self.graphs[code].m,):
+            raise ValueError("syndrome must have shape (m,)")
+        t = ctypes.c_uint64()
+        rc = qldpc_server_submit(self._h, int(code), _np_ptr(syn), ctypes.byref(t))
+        if rc == QLDPC_BUSY:
+            return None
+        check(rc, "qldpc_server_submit")
+        return t.value
+
+    def poll(self, code: int, ticket: int):
+        """(err, iters, ok) when done, else None."""
+        err = np.empty(self.graphs[code].n, dtype=np.uint8)
+        it = ctypes.c_int32()
+        ok = ctypes.c_uint8()
+        rc = qldpc_server_poll(self._h, int(code), ctypes.c_uint64(ticket), _np_ptr(err), ctypes.byref(it),
+                               ctypes.byref(ok))
+        if rc == QLDPC_PENDING:
+            return None
+        check(rc, "qldpc_server_poll")
+        return err, it.value, ok.value
+
+    def replay(self, codes, syndromes, arrival_ns, timeout_s: float = 10.0):
+        """Open-loop replay: request i = (codes[i], syndromes[i]) submitted at arrival_ns[i].
+
+        Returns (errs list of uint8 arrays, iters int32 [R], ok uint8 [R], latency_ns int64 [R]).
+        """
+        codes = np.ascontiguousarray(codes, dtype=np.int32)
+        nreq = len(codes)
+        syn_parts = [np.ascontiguousarray(x, dtype=np.uint8) for x in syndromes]
+        syn_off = np.zeros(nreq, dtype=np.int64)
+        err_off = np.zeros(nreq, dtype=np.int64)
+        if nreq:
+            syn_off[1:] = np.cumsum([len(x) for x in syn_parts])[:-1]
+            ns = np.array([self.graphs[c].n for c in codes], dtype=np.int64)
+            err_off[1:] = np.cumsum(ns)[:-1]
+            syn_flat = np.concatenate(syn_parts)
+            err_flat = np.zeros(int(ns.sum()), dtype=np.uint8)
+        else:
+            syn_flat = np.zeros(1, dtype=np.uint8)
+            err_flat = np.zeros(1, dtype=np.uint8)
+        arrival = np.ascontiguousarray(arrival_ns, dtype=np.int64)
+        iters = np.zeros(nreq, dtype=np.int32)
+        ok = np.zeros(nreq, dtype=np.uint8)
+        lat = np.zeros(nreq, dtype=np.int64)
+        check(qldpc_server_replay(self._h, nreq, _np_ptr(codes), _np_ptr(syn_flat), _np_ptr(syn_off),
+                                  _np_ptr(arrival), _np_ptr(err_flat), _np_ptr(err_off), _np_ptr(iters),
+                                  _np_ptr(ok), _np_ptr(lat), int(timeout_s * 1e9)), "qldpc_server_replay")
+        errs = [err_flat[err_off[i]:err_off[i] + self.graphs[codes[i]].n] for i in range(nreq)]
+        return errs, iters, ok, lat
+
+    def status(self) -> int:
+        st = ctypes.c_uint32()
+        check(qldpc_server_status(self._h, ctypes.byref(st)), "qldpc_server_status")
+        return st.value
+
+    def close(self) -> None:
+        if self._h:
+            qldpc_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -9,7 +9,10 @@ outputs per step, more than the 129 MB L2).
 Printed as one JSON line on rank 0:
   value        syndromes/s of the device-resident decode (inputs in HBM), whole job
   e2e          the same through qldpc_decode_host with pinned HOST buffers (copies timed)
-  latency      single-shot (B = 1) end-to-end latency percentiles vs the 63 us threshold
+  latency      single-shot (B = 1) end-to-end latency percentiles vs the 63 us threshold, through
+               the launch path (qldpc_decode_host) and the persistent server (qldpc_server_*)
+  serving      the persistent server under a 40/40/20 mix of the N=400, 1054 and 288 codes with
+               Poisson arrivals 20 us apart: latency percentiles and the saturated request rate
   roofline     the decoder kernel against the SM integer/FP32 issue roof ("alu")
   cpu_baseline the CPU oracle on a bounded sample of the same workload, all host cores
   clocks       SM clock and throttle reasons sampled during the timed region
@@ -42,6 +45,10 @@ LAT_P = 0.03
 LAT_SHOTS = 10000
 LAT_WARMUP = 200
 THRESHOLD_US = 63.0
+SERVE_REQUESTS = 100000
+SERVE_GAP_NS = 20000         # mean Poisson inter-arrival
+SERVE_MIX = (0.4, 0.4, 0.2)  # N=400 HGP, N=1054 LP, N=288 BB (H_Z, i.i.d. X noise at p = 0.03)
+LAT_SERVER_GAP_NS = 50000    # isolated single-shot requests through the server
 OPS_PER_EDGE_ITER = 10          # algorithmic ALU operations per edge per iteration
 ALU_LANES_PER_SM = 128          # FP32/INT32 lanes per SM, one operation per lane per clock
 
@@ -65,6 +72,8 @@ def parse():
     ap.add_argument("--no-latency", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--latency-shots", type=int, default=LAT_SHOTS)
+    ap.add_argument("--serve-requests", type=int, default=SERVE_REQUESTS)
+    ap.add_argument("--no-serving", action="store_true")
     return ap.parse_args()
 
 
@@ -310,6 +319,9 @@ def run_ours(args, rank, world, local):
     latency = None
     if not args.no_latency and rank == 0:
         latency = measure_latency(qldpc, graph, code, args)
+    serving = None
+    if not args.no_serving and rank == 0:
+        serving = measure_serving(qldpc, args)
     cpu = None
     if not args.no_cpu_baseline and rank == 0 and world == 1:
         threads = os.cpu_count() or 1
@@ -330,6 +342,7 @@ def run_ours(args, rank, world, local):
             "cpu_baseline": cpu,
             "e2e": e2e,
             "latency": latency,
+            "serving": serving,
             "gpu_launches": launches,
             "clocks": clocks,
             "mean_iters": sum(iters_per_batch) / (len(iters_per_batch) * B),
@@ -366,7 +379,12 @@ def measure_e2e(qldpc, graph, batches, args, B, world, dev):
 
 
 def measure_latency(qldpc, graph, code, args):
-    """B = 1 end-to-end: pinned syndrome -> H2D -> decode -> D2H -> host (host clock per shot)."""
+    """B = 1 end-to-end latency of LP-1054 shots at p = 0.03, host clock per shot.
+
+    Launch path: page-locked syndrome -> one kernel launch that reads it and writes e_hat,
+    iterations and ok into page-locked host memory -> stream synchronize.  Server path: the same
+    shots as isolated requests to the persistent server (no launch, copy or synchronize).
+    """
     import torch
     from paper_2508_07879_gb300 import workloads as w
     shots = args.latency_shots
@@ -392,9 +410,65 @@ def measure_latency(qldpc, graph, code, args):
         lat[prec] = {"p50_us": float(np.percentile(x, 50)), "p99_us": float(np.percentile(x, 99)),
                      "p999_us": float(np.percentile(x, 99.9)), "mean_us": float(x.mean()),
                      "max_iter_shots": int((iters[warm:] == MAX_ITER).sum())}
-    return {"metric": "p99 single-shot decode latency", "unit": "us", "threshold_us": THRESHOLD_US,
-            "code": "LP-1054 H_Z", "p": LAT_P, "shots": shots, "max_iter": MAX_ITER,
-            "path": "qldpc_decode_host from Python, pinned buffers, host clock, B=1", **lat}
+    out = {"metric": "p99 single-shot decode latency", "unit": "us", "threshold_us": THRESHOLD_US,
+           "code": "LP-1054 H_Z", "p": LAT_P, "shots": shots, "max_iter": MAX_ITER,
+           "launch_path": {"path": "qldpc_decode_host from Python, page-locked buffers read/written by the "
+                                   "kernel, host clock, B=1", **lat}}
+    # the same shots through the persistent server: requests 50 us apart, latency = result seen by
+    # the host - scheduled arrival (host steady clock inside the C ABI)
+    srv_lat = {}
+    for prec in ("fp32", "int16"):
+        with qldpc.Server([graph], [prior], MAX_ITER, ALPHA, prec, blocks=[8], ring_capacity=1024) as srv:
+            arrival = (np.arange(shots + warm) * LAT_SERVER_GAP_NS).astype(np.int64)
+            _, iters, _, lat_ns = srv.replay(np.zeros(shots + warm, np.int32), list(syn), arrival)
+        x = lat_ns[warm:] / 1e3
+        srv_lat[prec] = {"p50_us": float(np.percentile(x, 50)), "p99_us": float(np.percentile(x, 99)),
+                         "p999_us": float(np.percentile(x, 99.9)), "mean_us": float(x.mean()),
+                         "max_iter_shots": int((iters[warm:] == MAX_ITER).sum())}
+    out["server_path"] = {"path": "qldpc_server_replay: persistent kernel, 8 LP workers, requests 50 us apart",
+                          **srv_lat}
+    out["p99_us"] = srv_lat["fp32"]["p99_us"]
+    out["p50_us"] = srv_lat["fp32"]["p50_us"]
+    out["p999_us"] = srv_lat["fp32"]["p999_us"]
+    out["headline"] = "server_path fp32"
+    return out
+
+
+def measure_serving(qldpc, args):
+    """Config 5: Poisson arrivals of syndrome rounds mixed 40/40/20 from three codes."""
+    from paper_2508_07879_gb300 import workloads as w
+    rng = np.random.default_rng(5005)
+    n = args.serve_requests
+    codes = rng.choice(3, size=n, p=list(SERVE_MIX)).astype(np.int32)
+    arrival = np.cumsum(rng.exponential(SERVE_GAP_NS, size=n)).astype(np.int64)
+    graphs, priors, rows = [], [], []
+    for ci, name in enumerate(("hgp400", "lp1054", "bb288")):
+        b = w.x_error_batch(w.CONFIG_CODES[name](), 0.03, int((codes == ci).sum()), seed=5001 + ci)
+        graphs.append(qldpc.Graph.from_csr(b.h))
+        priors.append(b.prior)
+        rows.append(b.syndromes)
+    cursor = [0, 0, 0]
+    syn = []
+    for c in codes:
+        syn.append(rows[c][cursor[c]])
+        cursor[c] += 1
+    out = {"workload": "40/40/20 HGP-400 / LP-1054 / BB-288 (H_Z, iid X, p=0.03), Poisson mean gap 20 us",
+           "requests": n, "max_iter": MAX_ITER}
+    for prec in ("fp32", "int16"):
+        with qldpc.Server(graphs, priors, MAX_ITER, ALPHA, prec, ring_capacity=4096) as srv:
+            _, _, _, lat_ns = srv.replay(codes, syn, arrival, timeout_s=60.0)
+            t0 = time.perf_counter()
+            srv.replay(codes, syn, np.zeros(n, np.int64), timeout_s=60.0)
+            dt = time.perf_counter() - t0
+        x = lat_ns / 1e3
+        per = {}
+        for ci, name in enumerate(("hgp400", "lp1054", "bb288")):
+            xs = x[codes == ci]
+            per[name] = {"p50_us": float(np.percentile(xs, 50)), "p99_us": float(np.percentile(xs, 99))}
+        out[prec] = {"p50_us": float(np.percentile(x, 50)), "p99_us": float(np.percentile(x, 99)),
+                     "p999_us": float(np.percentile(x, 99.9)), "per_code": per,
+                     "saturated_shots_per_s": n / dt}
+    return out
 
 
 def main():

@@ -10,7 +10,9 @@ splits a batch over host threads (ctypes releases the GIL during the call).
 
 Parity pins (see tests/test_oracle_pins.py): the hand-worked single-check update, the Eq. (1)
 trace against its closed-form recurrence, tree codes against brute-force max-product, loopy tiny
-codes against brute-force minimum weight, and the exact symmetries of min-sum.
+codes against brute-force minimum weight, and the exact symmetries of min-sum.  The neural
+min-sum functions (tests/test_oracle_nms.py): constant weights reduce them to the plain decoder,
+the reverse-mode gradient matches central finite differences and a closed form for one check.
 """
 from __future__ import annotations
 
@@ -58,6 +60,13 @@ def _load():
             lib.oracle_msa_i16.restype = ctypes.c_int
             lib.oracle_alpha_q.argtypes = [ctypes.c_float]
             lib.oracle_alpha_q.restype = ctypes.c_int
+            for name in ("oracle_nms_train_f64", "oracle_nms_train_f32"):
+                f = getattr(lib, name)
+                f.argtypes = [p, p, i32, i32, p, p, i32, p, p, i32, p, p, p, p]
+                f.restype = ctypes.c_int
+            lib.oracle_nms_decode_f32.argtypes = [p, p, i32, i32, p, i32, p, p, i32, i32, ctypes.c_float,
+                                                  p, p, p, p, p]
+            lib.oracle_nms_decode_f32.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -123,3 +132,98 @@ def msa(row_ptr, col_idx, m: int, n: int, syndromes, prior, max_iter: int, alpha
     if bad:
         raise ValueError(f"oracle rejected the input (code {bad[0]})")
     return {"err": err, "iters": iters, "ok": ok, "post": post, "margin": margin}
+
+
+# ------------------------------------------------------------------------------------------------
+# Neural normalized min-sum (learned weights w[t][e], CSR edge order)
+# ------------------------------------------------------------------------------------------------
+def nms_train(row_ptr, col_idx, m, n, syndromes, targets, prior, weights, grad_loss=None,
+              precision: str = "f64", post: bool = False, threads: int = 1):
+    """Training pass of the neural min-sum decoder: T iterations, no stop test.
+
+    weights: [T, E] (E = nnz, CSR edge order).  precision "f64" or "f32" is the type the forward
+    runs in; losses and gradients are always float64.  Returns a dict with
+      loss [B]          1/(T n) sum_t sum_v BCE(sigma(-Q^t_v), y_v)
+      post [B, T, n]    Q^t of every iteration (only with post=True)
+      grad [T, E]       sum_b grad_loss[b] d loss_b / d w (only when grad_loss is given)
+    """
+    lib = _load()
+    if precision == "f64":
+        fn, real = lib.oracle_nms_train_f64, np.float64
+    elif precision == "f32":
+        fn, real = lib.oracle_nms_train_f32, np.float32
+    else:
+        raise ValueError(f"unknown precision {precision!r}")
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+    syn = np.ascontiguousarray(syndromes, dtype=np.uint8).reshape(-1, m)
+    y = np.ascontiguousarray(targets, dtype=np.uint8).reshape(-1, n)
+    w = np.ascontiguousarray(weights, dtype=real)
+    T = w.shape[0]
+    pr = np.ascontiguousarray(prior, dtype=real).reshape(n)
+    B = syn.shape[0]
+    loss = np.zeros(B, dtype=np.float64)
+    posts = np.zeros((B, T, n), dtype=real) if post else None
+    g = None if grad_loss is None else np.ascontiguousarray(grad_loss, dtype=np.float64).reshape(B)
+    threads = max(1, min(int(threads), max(B, 1)))
+    bounds = np.linspace(0, B, threads + 1).astype(int)
+    parts = [np.zeros_like(w, dtype=np.float64) for _ in range(threads)] if g is not None else None
+
+    def run(i):
+        lo, hi = bounds[i], bounds[i + 1]
+        if hi <= lo:
+            return 0
+        return fn(_ptr(rp), _ptr(ci), m, n, _ptr(syn[lo:hi]), _ptr(y[lo:hi]), hi - lo, _ptr(pr), _ptr(w), T,
+                  _ptr(g[lo:hi]) if g is not None else None, _ptr(loss[lo:hi]),
+                  _ptr(posts[lo:hi]) if posts is not None else None, _ptr(parts[i]) if parts else None)
+
+    if threads == 1:
+        rcs = [run(0)]
+    else:
+        with ThreadPoolExecutor(threads) as ex:
+            rcs = list(ex.map(run, range(threads)))
+    bad = [rc for rc in rcs if rc != 0]
+    if bad:
+        raise ValueError(f"oracle rejected the input (code {bad[0]})")
+    out = {"loss": loss}
+    if posts is not None:
+        out["post"] = posts
+    if parts is not None:
+        out["grad"] = np.sum(parts, axis=0)
+    return out
+
+
+def nms_decode(row_ptr, col_idx, m, n, syndromes, prior, weights, max_iter_plain, alpha, threads: int = 1):
+    """FP32 learned decoding with plain min-sum fallback; dict like msa() plus 'fallback'."""
+    lib = _load()
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+    syn = np.ascontiguousarray(syndromes, dtype=np.uint8).reshape(-1, m)
+    w = np.ascontiguousarray(weights, dtype=np.float32)
+    T = w.shape[0]
+    pr = np.ascontiguousarray(prior, dtype=np.float32).reshape(n)
+    B = syn.shape[0]
+    err = np.zeros((B, n), dtype=np.uint8)
+    iters = np.zeros(B, dtype=np.int32)
+    ok = np.zeros(B, dtype=np.uint8)
+    post = np.zeros((B, n), dtype=np.float32)
+    fb = np.zeros(B, dtype=np.uint8)
+    threads = max(1, min(int(threads), max(B, 1)))
+    bounds = np.linspace(0, B, threads + 1).astype(int)
+
+    def run(i):
+        lo, hi = bounds[i], bounds[i + 1]
+        if hi <= lo:
+            return 0
+        return lib.oracle_nms_decode_f32(_ptr(rp), _ptr(ci), m, n, _ptr(syn[lo:hi]), hi - lo, _ptr(pr), _ptr(w), T,
+                                         int(max_iter_plain), float(np.float32(alpha)), _ptr(err[lo:hi]),
+                                         _ptr(iters[lo:hi]), _ptr(ok[lo:hi]), _ptr(post[lo:hi]), _ptr(fb[lo:hi]))
+
+    if threads == 1:
+        rcs = [run(0)]
+    else:
+        with ThreadPoolExecutor(threads) as ex:
+            rcs = list(ex.map(run, range(threads)))
+    if any(rcs):
+        raise ValueError("oracle rejected the input")
+    return {"err": err, "iters": iters, "ok": ok, "post": post, "fallback": fb}

@@ -300,3 +300,223 @@ int oracle_msa_i16(const int32_t *row_ptr, const int32_t *col_idx, int32_t m, in
     free(gq); free(q); free(r); free(post); tanner_free(&t);
     return ORACLE_OK;
 }
+
+/* ---------------------------------------------------------------------------------------------
+ * Neural normalized min-sum: Algorithm 1 with the scale alpha replaced by a learned weight
+ * w[t][e] per iteration t (0-based here, iteration t+1 of the algorithm) and per edge e (CSR edge
+ * order: e = row_ptr[m] + position of n in row m):
+ *   r^(t)_{m,n} = (-1)^{s_m} prod_{j != n} sign(q^(t-1)_{m,j}) * (w[t][e] * min_{j != n} |q^(t-1)_{m,j}|)
+ * with the variable step and a-posteriori LLR of Algorithm 1 unchanged (literal sums over
+ * S_c(n)\m in ascending check order, as in the plain decoder above).
+ *
+ * Training loss of one shot with true error y (the sampled e), over T iterations, no stop test:
+ *   loss = 1/(T N) sum_{t=1..T} sum_n BCE(sigma(-Q^(t)_n), y_n),  BCE(p, y) = -y log p - (1-y) log(1-p)
+ * evaluated as softplus(Q) for y = 1 and softplus(-Q) for y = 0 (softplus(x) = log(1 + e^x)):
+ * Q = log P(e_n = 0)/P(e_n = 1), so P(e_n = 1) = sigma(-Q).
+ *
+ * Reverse mode (the gradient of sum_b g_b loss_b with respect to w), with the subgradient rules
+ *   d|q|/dq = +1 for q >= 0, -1 for q < 0;  d sign(q)/dq = 0;
+ *   the minimum over S_v(m)\n flows to the lowest-index edge attaining it.
+ * The forward runs in REAL (double or float, the float one operation for operation the learned
+ * decoder below); losses and the whole reverse sweep are evaluated in double from the recorded
+ * forward values.
+ * --------------------------------------------------------------------------------------------- */
+static double softplus_d(double x) { return x > 0 ? x + log1p(exp(-x)) : log1p(exp(x)); }
+static double sigmoid_d(double x) { return x >= 0 ? 1.0 / (1.0 + exp(-x)) : exp(x) / (1.0 + exp(x)); }
+
+#define DEFINE_NMS_TRAIN(SUFFIX, REAL, FABS)                                                          \
+/* CN update of check c with weights w_t; records per edge the sign factor, the minimum over the    \
+ * other edges and the edge attaining it (lowest index on ties; -1 for a row of degree 1). */       \
+static void nms_check_##SUFFIX(const tanner *t, int32_t c, const uint8_t *s, const REAL *q,           \
+                               const REAL *w_t, REAL *r, double *sgn, REAL *mu, int32_t *arg)        \
+{                                                                                                     \
+    for (int32_t i = t->row_ptr[c]; i < t->row_ptr[c + 1]; ++i) {                                     \
+        int neg = s[c] & 1;                                                                           \
+        REAL mn = (REAL)INFINITY;                                                                     \
+        int32_t am = -1;                                                                              \
+        for (int32_t j = t->row_ptr[c]; j < t->row_ptr[c + 1]; ++j) {                                 \
+            if (j == i) continue;                                                                     \
+            if (q[j] < 0) neg ^= 1;                                                                   \
+            if (FABS(q[j]) < mn) { mn = FABS(q[j]); am = j; }                                         \
+        }                                                                                             \
+        sgn[i] = neg ? -1.0 : 1.0;                                                                    \
+        mu[i] = mn;                                                                                   \
+        arg[i] = am;                                                                                  \
+        const REAL mag = w_t[i] * mn;                                                                 \
+        r[i] = neg ? -mag : mag;                                                                      \
+    }                                                                                                 \
+}                                                                                                     \
+                                                                                                      \
+int oracle_nms_train_##SUFFIX(const int32_t *row_ptr, const int32_t *col_idx, int32_t m, int32_t n,   \
+                              const uint8_t *syn, const uint8_t *target, int32_t batch,               \
+                              const REAL *prior, const REAL *weights, int32_t T,                      \
+                              const double *grad_loss, double *out_loss, REAL *out_post,              \
+                              double *out_grad)                                                       \
+{                                                                                                     \
+    if (batch < 0 || T < 1 || !syn || !target || !prior || !weights || !out_loss) return ORACLE_BAD_ARG; \
+    if (out_grad && !grad_loss) return ORACLE_BAD_ARG;                                                \
+    tanner t;                                                                                         \
+    int rc = tanner_build(&t, row_ptr, col_idx, m, n);                                                \
+    if (rc) return rc;                                                                                \
+    const size_t E = (size_t)(t.e > 0 ? t.e : 1), TE = E * (size_t)T;                                 \
+    REAL *qs = (REAL *)malloc(sizeof(REAL) * TE);      /* q^(k): input of iteration k+1 */            \
+    REAL *rs = (REAL *)malloc(sizeof(REAL) * TE);                                                     \
+    REAL *mus = (REAL *)malloc(sizeof(REAL) * TE);                                                    \
+    double *sgs = (double *)malloc(sizeof(double) * TE);                                              \
+    int32_t *ams = (int32_t *)malloc(sizeof(int32_t) * TE);                                           \
+    REAL *Qs = (REAL *)malloc(sizeof(REAL) * (size_t)n * (size_t)T);                                  \
+    double *gq = (double *)malloc(sizeof(double) * E), *gq_prev = (double *)malloc(sizeof(double) * E); \
+    double *gr = (double *)malloc(sizeof(double) * E), *gQ = (double *)malloc(sizeof(double) * (size_t)n); \
+    if (!qs || !rs || !mus || !sgs || !ams || !Qs || !gq || !gq_prev || !gr || !gQ) {                 \
+        rc = ORACLE_NO_MEMORY;                                                                        \
+        goto done;                                                                                    \
+    }                                                                                                 \
+    for (int32_t b = 0; b < batch; ++b) {                                                             \
+        const uint8_t *s = syn + (size_t)b * m, *y = target + (size_t)b * n;                          \
+        /* forward: T iterations of CN, VN and APP */                                                 \
+        for (int32_t i = 0; i < t.e; ++i) qs[i] = prior[t.col[i]];                                    \
+        double loss = 0.0;                                                                            \
+        for (int32_t k = 0; k < T; ++k) {                                                             \
+            const REAL *q = qs + (size_t)k * E;                                                       \
+            REAL *r = rs + (size_t)k * E;                                                             \
+            for (int32_t c = 0; c < m; ++c)                                                           \
+                nms_check_##SUFFIX(&t, c, s, q, weights + (size_t)k * t.e, r, sgs + (size_t)k * E,     \
+                                   mus + (size_t)k * E, ams + (size_t)k * E);                         \
+            for (int32_t v = 0; v < n; ++v) {                                                         \
+                REAL Q = prior[v];                                                                    \
+                for (int32_t a = t.vptr[v]; a < t.vptr[v + 1]; ++a) Q = Q + r[t.vedge[a]];            \
+                Qs[(size_t)k * n + v] = Q;                                                            \
+                loss += y[v] ? softplus_d((double)Q) : softplus_d(-(double)Q);                        \
+                if (out_post) out_post[((size_t)b * T + k) * n + v] = Q;                              \
+                if (k + 1 < T) {                                                                      \
+                    REAL *qn = qs + (size_t)(k + 1) * E;                                              \
+                    for (int32_t a = t.vptr[v]; a < t.vptr[v + 1]; ++a) {                             \
+                        REAL acc = prior[v];                                                          \
+                        for (int32_t bb = t.vptr[v]; bb < t.vptr[v + 1]; ++bb)                        \
+                            if (bb != a) acc = acc + r[t.vedge[bb]];                                  \
+                        qn[t.vedge[a]] = acc;                                                         \
+                    }                                                                                 \
+                }                                                                                     \
+            }                                                                                         \
+        }                                                                                             \
+        out_loss[b] = loss / ((double)T * n);                                                         \
+        if (!out_grad) continue;                                                                      \
+        /* reverse sweep, iteration T down to 1 */                                                    \
+        const double scale = grad_loss[b] / ((double)T * n);                                          \
+        for (int32_t i = 0; i < t.e; ++i) gq[i] = 0.0;    /* d/d q^(k+1): feeds iteration k+2 */      \
+        for (int32_t k = T - 1; k >= 0; --k) {                                                        \
+            for (int32_t v = 0; v < n; ++v)                                                           \
+                gQ[v] = scale * ((double)y[v] - sigmoid_d(-(double)Qs[(size_t)k * n + v]));           \
+            /* r^(k+1)_{m,n} enters Q^(k+1)_n and every q^(k+1)_{i,n} with i != m */                  \
+            for (int32_t v = 0; v < n; ++v)                                                           \
+                for (int32_t a = t.vptr[v]; a < t.vptr[v + 1]; ++a) {                                 \
+                    double acc = gQ[v];                                                               \
+                    for (int32_t bb = t.vptr[v]; bb < t.vptr[v + 1]; ++bb)                            \
+                        if (bb != a) acc += gq[t.vedge[bb]];                                          \
+                    gr[t.vedge[a]] = acc;                                                             \
+                }                                                                                     \
+            const REAL *q = qs + (size_t)k * E;                                                       \
+            for (int32_t i = 0; i < t.e; ++i) gq_prev[i] = 0.0;                                       \
+            for (int32_t i = 0; i < t.e; ++i) {                                                       \
+                const double sg = sgs[(size_t)k * E + i], mn = (double)mus[(size_t)k * E + i];        \
+                out_grad[(size_t)k * t.e + i] += gr[i] * sg * mn;            /* d r / d w = sg mn */  \
+                const int32_t j = ams[(size_t)k * E + i];                                             \
+                if (j >= 0) {                                /* d r / d q_j = w sg d|q_j|/dq_j */     \
+                    const double dabs = q[j] >= 0 ? 1.0 : -1.0;                                       \
+                    gq_prev[j] += gr[i] * (double)weights[(size_t)k * t.e + i] * sg * dabs;           \
+                }                                                                                     \
+            }                                                                                         \
+            for (int32_t i = 0; i < t.e; ++i) gq[i] = gq_prev[i];                                     \
+        }                                                                                             \
+    }                                                                                                 \
+done:                                                                                                 \
+    free(qs); free(rs); free(mus); free(sgs); free(ams); free(Qs);                                    \
+    free(gq); free(gq_prev); free(gr); free(gQ);                                                      \
+    tanner_free(&t);                                                                                  \
+    return rc;                                                                                        \
+}
+
+DEFINE_NMS_TRAIN(f64, double, fabs)
+DEFINE_NMS_TRAIN(f32, float, fabsf)
+
+/* Learned decoding for inference, FP32: iterations 1..T use the weights with the stop test of
+ * Algorithm 1; a shot whose syndrome is not met after T iterations is decoded again from its prior
+ * by plain min-sum (alpha, early stop, up to max_iter_plain iterations).  iters = learned
+ * iterations run, plus T + the plain iterations for a fallback shot; ok and the outputs are those
+ * of the decoder that produced them.  out_fallback[b] = 1 for fallback shots. */
+int oracle_nms_decode_f32(const int32_t *row_ptr, const int32_t *col_idx, int32_t m, int32_t n,
+                          const uint8_t *syn, int32_t batch, const float *prior, const float *weights,
+                          int32_t T, int32_t max_iter_plain, float alpha, uint8_t *out_err,
+                          int32_t *out_iters, uint8_t *out_ok, float *out_post, uint8_t *out_fallback)
+{
+    if (batch < 0 || T < 0 || max_iter_plain < 0 || !syn || !prior || !weights || !out_err || !out_iters || !out_ok)
+        return ORACLE_BAD_ARG;
+    tanner t;
+    int rc = tanner_build(&t, row_ptr, col_idx, m, n);
+    if (rc) return rc;
+    const size_t E = (size_t)(t.e > 0 ? t.e : 1);
+    float *q = (float *)malloc(sizeof(float) * E), *r = (float *)malloc(sizeof(float) * E);
+    float *post = (float *)malloc(sizeof(float) * (size_t)n);
+    if (!q || !r || !post) { free(q); free(r); free(post); tanner_free(&t); return ORACLE_NO_MEMORY; }
+    for (int32_t b = 0; b < batch; ++b) {
+        const uint8_t *s = syn + (size_t)b * m;
+        uint8_t *e_hat = out_err + (size_t)b * n;
+        for (int32_t v = 0; v < n; ++v) { post[v] = prior[v]; e_hat[v] = prior[v] < 0; }
+        int met = syndrome_met(&t, e_hat, s);
+        int32_t iters = 0;
+        int fell_back = 0;
+        if (!met) {
+            for (int32_t i = 0; i < t.e; ++i) q[i] = prior[t.col[i]];
+            for (int32_t k = 1; k <= T && !met; ++k) {
+                const float *w = weights + (size_t)(k - 1) * t.e;
+                for (int32_t c = 0; c < m; ++c)
+                    for (int32_t i = row_ptr[c]; i < row_ptr[c + 1]; ++i) {
+                        int neg = s[c] & 1;
+                        float mn = INFINITY;
+                        for (int32_t j = row_ptr[c]; j < row_ptr[c + 1]; ++j) {
+                            if (j == i) continue;
+                            if (q[j] < 0) neg ^= 1;
+                            if (fabsf(q[j]) < mn) mn = fabsf(q[j]);
+                        }
+                        const float mag = w[i] * mn;
+                        r[i] = neg ? -mag : mag;
+                    }
+                for (int32_t v = 0; v < n; ++v)
+                    for (int32_t a = t.vptr[v]; a < t.vptr[v + 1]; ++a) {
+                        float acc = prior[v];
+                        for (int32_t bb = t.vptr[v]; bb < t.vptr[v + 1]; ++bb)
+                            if (bb != a) acc = acc + r[t.vedge[bb]];
+                        q[t.vedge[a]] = acc;
+                    }
+                for (int32_t v = 0; v < n; ++v) {
+                    float acc = prior[v];
+                    for (int32_t a = t.vptr[v]; a < t.vptr[v + 1]; ++a) acc = acc + r[t.vedge[a]];
+                    post[v] = acc;
+                    e_hat[v] = acc < 0;
+                }
+                iters = k;
+                met = syndrome_met(&t, e_hat, s);
+            }
+            if (!met) {
+                int32_t it2 = 0;
+                uint8_t ok2 = 0;
+                float *post2 = (float *)malloc(sizeof(float) * (size_t)n);
+                if (!post2) { free(q); free(r); free(post); tanner_free(&t); return ORACLE_NO_MEMORY; }
+                rc = oracle_msa_f32(row_ptr, col_idx, m, n, s, 1, prior, max_iter_plain, alpha, 0u, e_hat, &it2, &ok2,
+                                    post2, NULL);
+                memcpy(post, post2, sizeof(float) * (size_t)n);
+                free(post2);
+                if (rc) { free(q); free(r); free(post); tanner_free(&t); return rc; }
+                iters = T + it2;
+                met = ok2;
+                fell_back = 1;
+            }
+        }
+        out_iters[b] = iters;
+        out_ok[b] = (uint8_t)met;
+        if (out_post) memcpy(out_post + (size_t)b * n, post, sizeof(float) * (size_t)n);
+        if (out_fallback) out_fallback[b] = (uint8_t)fell_back;
+    }
+    free(q); free(r); free(post); tanner_free(&t);
+    return ORACLE_OK;
+}

@@ -20,7 +20,7 @@ Noise
 -----
 A counter-based SplitMix64 generator (Steele, Lea and Flood, "Fast splittable pseudorandom number
 generators", OOPSLA 2014) keyed by (seed, shot, qubit) draws every random number, so a shot's error
-does not depend on the batch it is drawn in.  ``iid_x_errors`` draws Bernoulli(p) bit flips;
+does not depend on the batch it is drawn in.  ``iid_x_errors`` draws Bernoulli(p) bit flips (``iid_x_errors_prange`` at a rate drawn per shot);
 ``depolarizing_errors`` draws X, Y, Z with probability p/3 each and splits them into the X part
 (X or Y) and the Z part (Z or Y).  Per Sec. 2, s_X = H_Z e_X^T is decoded with H_Z and
 s_Z = H_X e_Z^T with H_X.
@@ -300,6 +300,21 @@ def iid_x_errors(n: int, p: float, shots: int, seed: int, first_shot: int = 0) -
     def draw(s0, count):
         u = uniform01(seed, np.arange(s0, s0 + count), np.arange(n))
         return (u < p).astype(np.uint8)
+    return _chunked(draw, shots, first_shot)
+
+
+def iid_x_errors_prange(n: int, p_lo: float, p_hi: float, shots: int, seed: int, first_shot: int = 0):
+    """Bernoulli flips at a per-shot rate drawn uniformly from [p_lo, p_hi).
+
+    p_b = p_lo + (p_hi - p_lo) * u(seed, b, n)   (counter n: one past the last qubit)
+    e[b, q] = [u(seed, b, q) < p_b]              for q < n
+    Returns (uint8 errors [shots, n], float64 rates [shots]).  The same definition drives the
+    device sampler used for training the learned decoder.
+    """
+    def draw(s0, count):
+        u = uniform01(seed, np.arange(s0, s0 + count), np.arange(n + 1))
+        p = p_lo + (p_hi - p_lo) * u[:, n]
+        return (u[:, :n] < p[:, None]).astype(np.uint8), p
     return _chunked(draw, shots, first_shot)
 
 

@@ -105,3 +105,20 @@ def test_csr_roundtrip():
     h = code.hz_csr
     np.testing.assert_array_equal(h.dense(), code.hz)
     assert h.nnz == 1344
+
+
+def test_prange_sampler_rates_and_keying():
+    e, p = w.iid_x_errors_prange(200, 0.02, 0.06, 5000, seed=8)
+    assert e.shape == (5000, 200) and p.shape == (5000,)
+    assert 0.02 <= p.min() and p.max() < 0.06
+    assert abs(p.mean() - 0.04) < 1e-3
+    # flips follow each shot's own rate: binned error density tracks the bin's mean rate
+    order = np.argsort(p)
+    for chunk in np.array_split(order, 5):
+        assert abs(e[chunk].mean() - p[chunk].mean()) < 3e-3
+    # the rate uses counter n and the flips counters 0..n-1 of the same key
+    u = w.uniform01(8, np.arange(3), np.arange(201))
+    np.testing.assert_array_equal(p[:3], 0.02 + (0.06 - 0.02) * u[:, 200])
+    np.testing.assert_array_equal(e[:3], (u[:, :200] < p[:3, None]).astype(np.uint8))
+    e2, p2 = w.iid_x_errors_prange(200, 0.02, 0.06, 10, seed=8, first_shot=4990)
+    np.testing.assert_array_equal(e2, e[4990:])

@@ -41,6 +41,7 @@
 #ifndef QLDPC_H
 #define QLDPC_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #if defined(__GNUC__)
@@ -70,8 +71,10 @@ enum { QLDPC_FP32 = 0, QLDPC_INT16 = 1 };
 
 /* Decode flags (bitwise OR). */
 enum {
-    QLDPC_NO_EARLY_STOP = 1u      /* run exactly max_iter iterations (the paper's timed mode, Sec. 3);
+    QLDPC_NO_EARLY_STOP = 1u,     /* run exactly max_iter iterations (the paper's timed mode, Sec. 3);
                                      ok still reports H e_hat^T = s after the last one */
+    QLDPC_LEARNED = 2u            /* learned decoding with the graph's weights, then the plain
+                                     fallback (see qldpc_graph_set_weights); FP32 and early stop only */
 };
 
 /* Limits of the kernels in this build. */
@@ -150,6 +153,9 @@ QLDPC_API int qldpc_decode(const qldpc_graph *g, const uint8_t *syndromes, int32
  * (cudaStream_t cast to void*, NULL = legacy default stream) and an optional device output
  *   out_post  float[batch*n] or NULL: the a-posteriori LLR Q_n of the last iteration run
  *             (INT16: the fixed-point value / 256, exact).
+ * With QLDPC_LEARNED the graph's learned weights (qldpc_graph_set_weights) drive the first T
+ * iterations and max_iter bounds the plain fallback; INVALID_ARG if the graph has no weights, the
+ * precision is not FP32 or QLDPC_NO_EARLY_STOP is also set.
  */
 QLDPC_API int qldpc_decode_ex(const qldpc_graph *g, const uint8_t *syndromes, int32_t batch,
                     const float *prior_llr, int32_t max_iter, float alpha,
@@ -210,7 +216,8 @@ typedef struct qldpc_server_config {
     int32_t precision;            /* QLDPC_FP32 or QLDPC_INT16 */
     int32_t max_iter;             /* >= 0 */
     float alpha;                  /* as for qldpc_decode_ex */
-    uint32_t flags;               /* QLDPC_NO_EARLY_STOP or 0 */
+    uint32_t flags;               /* QLDPC_NO_EARLY_STOP, or QLDPC_LEARNED (FP32: every code whose
+                                     graph has weights decodes learned, the others plainly), or 0 */
     int32_t ring_capacity;        /* slots per code, a power of two in [2, 2^20]; 0 = 256 */
     int32_t threads_per_block;    /* 0 = automatic */
     int32_t blocks[QLDPC_SERVER_MAX_CODES];   /* worker blocks per code; 0 = equal share of the SMs */
@@ -254,6 +261,94 @@ QLDPC_API int qldpc_server_status(qldpc_server *s, uint32_t *status);
 /* Stop the workers (they leave at their next poll), wait for the kernel and free everything.
  * Uncollected results are lost.  NULL is ignored. */
 QLDPC_API void qldpc_server_destroy(qldpc_server *s);
+
+/* ===============================================================================================
+ * Learned (neural) normalized min-sum.
+ *
+ * The check-node update of Algorithm 1 (Sec. 2) with the normalization alpha replaced by a trained
+ * weight per iteration t and edge e:
+ *   r^(t)_{m,n} = (-1)^{s_m} prod_{j != n} sign(q_{m,j}) * (w[t][e(m,n)] * min_{j != n} |q_{m,j}|)
+ * Weights are float[T][nnz] in CSR edge order (e = row_ptr[m] + position of n in row m of the
+ * matrix given to qldpc_graph_create).  The variable step, APP and decision are Algorithm 1's.
+ * Learned decoding runs iterations 1..T with the weights and the stop test; a shot whose syndrome
+ * is still not met restarts from its prior with plain min-sum (alpha, up to max_iter iterations):
+ * iters = T + plain iterations for such shots.  Training minimizes the BCE of the soft outputs,
+ *   loss_b = 1/(T n) sum_{t=1..T} sum_v BCE(sigma(-Q^(t)_v), y_v)   (y = the true error bits),
+ * with a forward kernel that records a compressed check state per iteration and a backward
+ * kernel that recomputes every message from it.  FP32 throughout.
+ * =============================================================================================== */
+
+/* Set (T >= 1) or clear (T = 0, weights may be NULL) the graph's learned weights: float[T][nnz],
+ * host or device memory, copied (synchronously) into the graph.  Decodes and servers created
+ * afterwards with QLDPC_LEARNED use them; do not call while a decode using the graph is running.
+ * INVALID_ARG: null graph, T < 0 or > 4096, null weights with T > 0, a non-finite weight. */
+QLDPC_API int qldpc_graph_set_weights(qldpc_graph *g, const float *weights, int32_t T);
+
+/* Device workspace (bytes) that qldpc_nms_forward / qldpc_nms_backward need for `batch` shots and
+ * T iterations: the slot-layout weights, 16 bytes of recorded state per check, iteration and shot,
+ * and one gradient slice per backward block.  INVALID_ARG: null pointers, batch < 1, T < 1. */
+QLDPC_API int qldpc_nms_workspace_bytes(const qldpc_graph *g, int32_t batch, int32_t T, size_t *bytes);
+
+/*
+ * Training forward: T learned iterations (no stop test) on every shot.
+ *   syndromes  device uint8[batch][m];  targets device uint8[batch][n], the true error bits
+ *   prior      device float[n];         weights device float[T][nnz] (CSR edge order)
+ *   out_loss   device float[batch], loss_b as above
+ *   out_post   device float[batch][n], Q^(T) (the a-posteriori LLR of iteration T), or NULL
+ *   workspace  device memory of at least qldpc_nms_workspace_bytes(g, batch, T), 256-byte aligned;
+ *              it keeps the weights and the recorded state for qldpc_nms_backward
+ * Enqueued on `stream`.  INVALID_ARG: null pointers, batch < 1, T < 1, workspace too small or
+ * misaligned.  UNSUPPORTED: a degree combination without a compiled training kernel, or a shot
+ * that does not fit in shared memory.  Non-finite priors give non-finite losses.
+ */
+QLDPC_API int qldpc_nms_forward(const qldpc_graph *g, const uint8_t *syndromes, const uint8_t *targets,
+                                int32_t batch, const float *prior, const float *weights, int32_t T,
+                                float *out_loss, float *out_post, void *workspace, size_t workspace_bytes,
+                                void *stream);
+
+/*
+ * Training backward: out_grad (device float[T][nnz], overwritten) = sum_b grad_loss[b] d loss_b / d w,
+ * with the subgradients d|q|/dq = sign(q) (+1 at 0), d sign/dq = 0, and the minimum's gradient going
+ * to the lowest position attaining it.  The arguments must be those of the preceding
+ * qldpc_nms_forward on the same workspace (same syndromes, targets, prior, batch and T; the weights
+ * are read back from the workspace).  grad_loss is device float[batch].  The result does not
+ * depend on scheduling (each block sums its own shots; the blocks are added in a fixed order).
+ */
+QLDPC_API int qldpc_nms_backward(const qldpc_graph *g, const uint8_t *syndromes, const uint8_t *targets,
+                                 int32_t batch, const float *prior, int32_t T, const float *grad_loss,
+                                 float *out_grad, void *workspace, size_t workspace_bytes, void *stream);
+
+/* One Adam step on device float arrays of `count` elements (Kingma and Ba, ICLR 2015), in the
+ * arithmetic of PyTorch's single-tensor Adam: m += (1-beta1)(g-m); v = beta2 v + (1-beta2) g^2;
+ * param -= lr/(1-beta1^step) * m / (sqrt(v)/sqrt(1-beta2^step) + eps).  step >= 1. */
+QLDPC_API int qldpc_adam_step(float *params, const float *grads, float *exp_avg, float *exp_avg_sq,
+                              int64_t count, int32_t step, float lr, float beta1, float beta2, float eps,
+                              void *stream);
+
+/*
+ * Seeded synthetic i.i.d. bit-flip errors and their syndromes s = H e^T mod 2 for the graph's H,
+ * on the device.  Counter-based SplitMix64 (Steele, Lea and Flood, OOPSLA 2014) keyed by
+ * (seed, shot, qubit): u(b, q) = (mix(mix(mix(seed) + shot) + q) >> 11) / 2^53 with
+ * shot = first_shot + b.  Shot b's rate is p_b = p_lo + (p_hi - p_lo) * u(b, n), and
+ * e[b][q] = [u(b, q) < p_b] for q < n (p_lo = p_hi: a fixed rate).  Outputs: device uint8
+ * out_err[batch][n] and out_syn[batch][m].  INVALID_ARG: null pointers, batch < 0, first_shot < 0,
+ * rates outside [0, 1] or p_hi < p_lo.
+ */
+QLDPC_API int qldpc_sample_errors(const qldpc_graph *g, uint64_t seed, int64_t first_shot, int32_t batch,
+                                  double p_lo, double p_hi, uint8_t *out_err, uint8_t *out_syn,
+                                  void *stream);
+
+/*
+ * Logical failure of each decoded shot: fail[b] = 1 if ok[b] = 0 or the residual e_b XOR e_hat_b
+ * has odd overlap with one of the k logical operators (rows of `logicals`, device uint8[k][n],
+ * 0/1), else 0.  For X errors decoded with H_Z the rows are Z logicals (a basis of
+ * ker H_X modulo the row space of H_Z); a residual that meets the syndrome is then a stabilizer
+ * iff it commutes with all of them.  All arrays device memory; INVALID_ARG on null pointers or
+ * sizes < 1 (batch = 0 is a no-op); UNSUPPORTED if (k + 1) * ceil(n / 32) * 4 > 48 KB.
+ */
+QLDPC_API int qldpc_logical_failures(const uint8_t *logicals, int32_t k, int32_t n, const uint8_t *errors,
+                                     const uint8_t *decisions, const uint8_t *ok, int32_t batch,
+                                     uint8_t *out_fail, void *stream);
 
 /* Size of the library's static device scratch used by qldpc_decode_host_noalloc (4 MiB). */
 enum { QLDPC_NOALLOC_SCRATCH_BYTES = 4 * 1024 * 1024 };

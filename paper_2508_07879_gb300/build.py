@@ -1,6 +1,6 @@
 """Build libqldpc.so in-tree: the sm_103a decoder kernels plus the C-ABI host code.
 
-Three translation units compile in parallel (FP32 kernels, INT16 kernels, host code) and link into
+The kernel and host translation units compile in parallel and link into
 ``paper_2508_07879_gb300/libqldpc.so`` with the CUDA runtime linked statically, so loading the
 library needs only the driver.  Objects go to ``paper_2508_07879_gb300/_build/``.
 """
@@ -24,8 +24,9 @@ NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibilit
               "-Xptxas", "-v", "--fmad=false"]
 CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-fvisibility=hidden", "-Wall", "-Wextra"]
 
-KERNEL_SOURCES = ["msa_f32.cu", "msa_i16.cu", "server_f32.cu", "server_i16.cu", "qldpc_noalloc.cu"]
-HOST_SOURCES = ["qldpc_host.cpp", "qldpc_server.cpp"]
+KERNEL_SOURCES = ["msa_f32.cu", "msa_i16.cu", "msa_learned.cu", "nms_train.cu", "server_f32.cu", "server_i16.cu",
+                  "qldpc_noalloc.cu"]
+HOST_SOURCES = ["qldpc_host.cpp", "qldpc_server.cpp", "qldpc_learned.cpp"]
 HEADERS = ["msa_launch.h", "msa_kernel.cuh", "server_kernel.cuh", "graph.h"]
 
 

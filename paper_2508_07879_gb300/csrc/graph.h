@@ -33,9 +33,16 @@ struct qldpc_graph {
     size_t h_stage_bytes = 0;
     std::vector<float> prior_cache;
     bool prior_valid = false;
+    // learned decoding: [learned_T][dc_max * m] slot-layout weights (qldpc_graph_set_weights)
+    float *d_weights = nullptr;
+    int32_t learned_T = 0;
 };
 
 namespace qldpc {
+
+int dc_bucket(int d);   // row-degree bucket 8 / 16 / 32, -1 above
+int dv_bucket(int d);   // column-degree bucket 4 / 8 / 16, -1 above
+
 namespace detail {
 
 int cuda_status(cudaError_t e);                                             // cudaError -> qldpc_status

@@ -124,9 +124,12 @@ __device__ __forceinline__ uint32_t check_of(uint32_t e) { return e & 0xffffu; }
 // decisions.  Returns 1 iff the check's parity word says s_m is satisfied.
 // UNIFORM: every row has exactly DC edges; otherwise deg <= DC.
 // ---------------------------------------------------------------------------------------------
-template <class P, int DC, bool UNIFORM>
+// LEARNED (FP32 only): when w is non-null the scale is the learned weight of each edge,
+// r = sign * (w_{m,n} * min_{j != n} |q_j|), w = this iteration's slot-layout weights.
+template <class P, int DC, bool UNIFORM, bool LEARNED = false>
 __device__ __forceinline__ int check_step(int c, int M, int deg, uint32_t pw, bool update,
-                                          typename P::msg_t *__restrict__ slots, const LaunchParams &p)
+                                          typename P::msg_t *__restrict__ slots, const LaunchParams &p,
+                                          const float *__restrict__ w = nullptr)
 {
     using acc_t = typename P::acc_t;
     using mag_t = typename P::mag_t;
@@ -145,6 +148,19 @@ __device__ __forceinline__ int check_step(int c, int M, int deg, uint32_t pw, bo
             }
         }
         const uint32_t negall = ((pw >> 1) ^ (sx >> 31)) & 1u;   // (-1)^{s_m} * prod of all signs
+        if constexpr (LEARNED) {
+            if (w) {
+#pragma unroll
+                for (int j = 0; j < DC; ++j) {
+                    if (UNIFORM || j < deg) {
+                        const mag_t mu = P::mag(q[j]) == m1 ? m2 : m1;   // min over the others
+                        const mag_t r = __fmul_rn(__ldg(w + j * M + c), mu);
+                        slots[j * M + c] = typename P::msg_t(P::signed_like(r, q[j], negall));
+                    }
+                }
+                return (pw & 1u) == 0;
+            }
+        }
         const mag_t r1 = P::scale(m1, p);                        // alpha * min over the others
         const mag_t r2 = P::scale(m2, p);                        // ... when |q_j| is the minimum
 #pragma unroll
@@ -163,7 +179,8 @@ __device__ __forceinline__ int check_step(int c, int M, int deg, uint32_t pw, bo
 // + ... + r_{k-1}.  Stores every q_k, flips the parity bit of its checks when the decision
 // [Q < 0] differs from `prev`, and returns Q.
 // ---------------------------------------------------------------------------------------------
-template <class P, int D>
+// TRACK = false (training forward): no decision tracking, parity may be null.
+template <class P, int D, bool TRACK = true>
 __device__ __forceinline__ typename P::acc_t var_step_exact(const uint32_t *e, uint32_t M, typename P::acc_t gamma,
                                                             bool prev, typename P::msg_t *__restrict__ slots,
                                                             uint32_t *__restrict__ parity)
@@ -190,7 +207,7 @@ __device__ __forceinline__ typename P::acc_t var_step_exact(const uint32_t *e, u
             for (int i = k + 1; i < D; ++i) q = P::add(q, r[i]);
             slots[sl[k]] = P::to_msg(q);
         }
-        if (P::neg(Q) != prev) {
+        if (TRACK && P::neg(Q) != prev) {
 #pragma unroll
             for (int k = 0; k < D; ++k) flip_check(parity, check_of(e[k]));
         }
@@ -201,7 +218,7 @@ __device__ __forceinline__ typename P::acc_t var_step_exact(const uint32_t *e, u
 #define QLDPC_DEG_CASES(X) X(0) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16)
 
 // Batch variant: the edge list comes from global memory (L1-resident).
-template <class P, int D>
+template <class P, int D, bool TRACK = true>
 __device__ __forceinline__ typename P::acc_t var_step_global(int v, int N, uint32_t M, const uint32_t *__restrict__ vslot,
                                                              typename P::acc_t gamma, bool prev,
                                                              typename P::msg_t *slots, uint32_t *parity)
@@ -209,12 +226,12 @@ __device__ __forceinline__ typename P::acc_t var_step_global(int v, int N, uint3
     uint32_t e[D > 0 ? D : 1];
 #pragma unroll
     for (int k = 0; k < D; ++k) e[k] = __ldg(vslot + size_t(k) * N + v);
-    return var_step_exact<P, D>(e, M, gamma, prev, slots, parity);
+    return var_step_exact<P, D, TRACK>(e, M, gamma, prev, slots, parity);
 }
 
 // Variable step of the batch kernel for one variable: dispatch on its degree (internal variables
 // are sorted by degree, so the lanes of a warp almost always take the same case).
-template <class P, int DV>
+template <class P, int DV, bool TRACK = true>
 __device__ __forceinline__ typename P::acc_t var_step_batch(int deg, int u, int N, uint32_t M, const uint32_t *vslot,
                                                             typename P::acc_t gamma, bool prev,
                                                             typename P::msg_t *slots, uint32_t *parity)
@@ -222,7 +239,7 @@ __device__ __forceinline__ typename P::acc_t var_step_batch(int deg, int u, int 
     switch (deg) {
 #define QLDPC_CASE(D)                                                                           \
     case D:                                                                                     \
-        if constexpr (D <= DV) return var_step_global<P, D>(u, N, M, vslot, gamma, prev, slots, parity); \
+        if constexpr (D <= DV) return var_step_global<P, D, TRACK>(u, N, M, vslot, gamma, prev, slots, parity); \
         break;
         QLDPC_DEG_CASES(QLDPC_CASE)
 #undef QLDPC_CASE
@@ -234,7 +251,33 @@ __device__ __forceinline__ typename P::acc_t var_step_batch(int deg, int u, int 
 // ---------------------------------------------------------------------------------------------
 // Throughput kernel
 // ---------------------------------------------------------------------------------------------
-template <class P, int DC, bool UNIFORM, int DV>
+// Initialization (Alg. 1) of one shot: q^(0) = gamma on every edge; the parity words start at s_m
+// and take the decisions of the prior.  Ends with a barrier.
+template <class P>
+__device__ __forceinline__ void batch_init_shot(const Problem &pr, const uint8_t *s, int M, int N, int tid, int T,
+                                                const typename P::acc_t *gam, typename P::acc_t *Qs,
+                                                uint32_t *parity, typename P::msg_t *slots)
+{
+    for (int c = tid; c < M; c += T) parity[c] = (s[c] & 1u) * 3u;
+    __syncthreads();
+    for (int u = tid; u < N; u += T) {
+        const typename P::acc_t g = gam[u];
+        const int deg = __ldg(pr.g.vdeg + u);
+        const bool d = P::neg(g);
+        for (int k = 0; k < deg; ++k) {
+            const uint32_t e = __ldg(pr.g.vslot + size_t(k) * N + u);
+            slots[slot_of(e, uint32_t(M))] = P::to_msg(g);
+            if (d) flip_check(parity, check_of(e));
+        }
+        Qs[u] = g;
+    }
+    __syncthreads();
+}
+
+// LEARNED: iterations 1..learned_iters use the learned weights; a shot whose syndrome is still not
+// met then restarts from its prior with plain min-sum (alpha) for up to max_iter iterations, and
+// reports learned_iters + the plain iterations.  Learned launches always stop early.
+template <class P, int DC, bool UNIFORM, int DV, bool LEARNED = false>
 __global__ void __launch_bounds__(1024, 1) msa_batch_kernel(const LaunchParams p)
 {
     using acc_t = typename P::acc_t;
@@ -260,7 +303,8 @@ __global__ void __launch_bounds__(1024, 1) msa_batch_kernel(const LaunchParams p
     }
     bad = __syncthreads_or(bad);
 
-    const bool early = (p.flags & kFlagNoEarlyStop) == 0;
+    const bool early = LEARNED || (p.flags & kFlagNoEarlyStop) == 0;
+    const size_t wstride = size_t(pr.g.dc_max) * M;   // learned weights of one iteration
     for (int b = blockIdx.x; b < p.batch; b += gridDim.x) {
         uint8_t *err = pr.err + size_t(b) * N;
         if (bad) {   // non-finite prior: report the shot as not decoded
@@ -274,38 +318,35 @@ __global__ void __launch_bounds__(1024, 1) msa_batch_kernel(const LaunchParams p
             }
             continue;
         }
-        // Initialization (Alg. 1): q^(0) = gamma on every edge; parity words start at s_m and
-        // take the decisions of the prior.
         const uint8_t *s = pr.syn + size_t(b) * M;
-        for (int c = tid; c < M; c += T) parity[c] = (s[c] & 1u) * 3u;
-        __syncthreads();
-        for (int u = tid; u < N; u += T) {
-            const acc_t g = gam[u];
-            const int deg = __ldg(pr.g.vdeg + u);
-            const bool d = P::neg(g);
-            for (int k = 0; k < deg; ++k) {
-                const uint32_t e = __ldg(pr.g.vslot + size_t(k) * N + u);
-                slots[slot_of(e, uint32_t(M))] = P::to_msg(g);
-                if (d) flip_check(parity, check_of(e));
-            }
-            Qs[u] = g;
-        }
-        __syncthreads();
+        batch_init_shot<P>(pr, s, M, N, tid, T, gam, Qs, parity, slots);
 
         int k = 0, all = 0;
-        for (;; ++k) {
-            const bool last = k >= p.max_iter;
+        bool learned = LEARNED;
+        int end = LEARNED ? pr.learned_iters : p.max_iter;   // k at which the current phase ends
+        for (;;) {
+            const bool last = k >= end;
+            const float *wk = nullptr;
+            if constexpr (LEARNED) wk = (learned && !last) ? pr.weights + size_t(k) * wstride : nullptr;
             int ok = 1;
             for (int c = tid; c < M; c += T) {
                 const int deg = UNIFORM ? DC : int(__ldg(pr.g.rdeg + c));
-                ok &= check_step<P, DC, UNIFORM>(c, M, deg, parity[c], !last, slots, p);
+                ok &= check_step<P, DC, UNIFORM, LEARNED>(c, M, deg, parity[c], !last, slots, p, wk);
             }
             all = __syncthreads_and(ok);
-            if (last || (early && all)) break;
+            if (early && all) break;
+            if (last) {
+                if (!LEARNED || !learned) break;
+                learned = false;                  // fallback: plain min-sum from the prior
+                end = k + p.max_iter;
+                batch_init_shot<P>(pr, s, M, N, tid, T, gam, Qs, parity, slots);
+                continue;
+            }
             for (int u = tid; u < N; u += T)
                 Qs[u] = var_step_batch<P, DV>(__ldg(pr.g.vdeg + u), u, N, uint32_t(M), pr.g.vslot, gam[u],
                                               P::neg(Qs[u]), slots, parity);
             __syncthreads();
+            ++k;
         }
 
         for (int u = tid; u < N; u += T) {
@@ -345,7 +386,7 @@ __device__ __forceinline__ typename P::acc_t var_step_regs(int deg, const uint32
     return gamma;
 }
 
-template <class P, int DC, bool UNIFORM, int DV>
+template <class P, int DC, bool UNIFORM, int DV, bool LEARNED = false>
 __global__ void __launch_bounds__(kLatencyMaxThreads, 1) msa_latency_kernel(const LaunchParams p)
 {
     using acc_t = typename P::acc_t;
@@ -387,7 +428,8 @@ __global__ void __launch_bounds__(kLatencyMaxThreads, 1) msa_latency_kernel(cons
     }
     bad = __syncthreads_or(bad);
 
-    const bool early = (p.flags & kFlagNoEarlyStop) == 0;
+    const bool early = LEARNED || (p.flags & kFlagNoEarlyStop) == 0;
+    const size_t wstride = size_t(pr.g.dc_max) * M;
     for (int b = blockIdx.x; b < p.batch; b += gridDim.x) {
         uint8_t *err = pr.err + size_t(b) * N;
         if (bad) {
@@ -406,40 +448,57 @@ __global__ void __launch_bounds__(kLatencyMaxThreads, 1) msa_latency_kernel(cons
             continue;
         }
         const uint8_t *s = pr.syn + size_t(b) * M;
-#pragma unroll
-        for (int i = 0; i < kLatCnPerThread; ++i)
-            if (cdeg[i] >= 0) parity[tid + i * T] = (s[tid + i * T] & 1u) * 3u;
-        __syncthreads();
         acc_t Q[kLatVnPerThread];
+        // Initialization (Alg. 1), also the restart of the plain fallback; ends with a barrier.
+        auto init_shot = [&]() {
 #pragma unroll
-        for (int i = 0; i < kLatVnPerThread; ++i) {
-            Q[i] = gam[i];
-            const bool d = P::neg(gam[i]);
+            for (int i = 0; i < kLatCnPerThread; ++i)
+                if (cdeg[i] >= 0) parity[tid + i * T] = (s[tid + i * T] & 1u) * 3u;
+            __syncthreads();
 #pragma unroll
-            for (int k = 0; k < DV; ++k) {
-                if (k < vdeg[i]) {
-                    slots[slot_of(ev[i][k], uint32_t(M))] = P::to_msg(gam[i]);
-                    if (d) flip_check(parity, check_of(ev[i][k]));
+            for (int i = 0; i < kLatVnPerThread; ++i) {
+                Q[i] = gam[i];
+                const bool d = P::neg(gam[i]);
+#pragma unroll
+                for (int k = 0; k < DV; ++k) {
+                    if (k < vdeg[i]) {
+                        slots[slot_of(ev[i][k], uint32_t(M))] = P::to_msg(gam[i]);
+                        if (d) flip_check(parity, check_of(ev[i][k]));
+                    }
                 }
             }
-        }
-        __syncthreads();
+            __syncthreads();
+        };
+        init_shot();
 
         int k = 0, all = 0;
-        for (;; ++k) {
-            const bool last = k >= p.max_iter;
+        bool learned = LEARNED;
+        int end = LEARNED ? pr.learned_iters : p.max_iter;
+        for (;;) {
+            const bool last = k >= end;
+            const float *wk = nullptr;
+            if constexpr (LEARNED) wk = (learned && !last) ? pr.weights + size_t(k) * wstride : nullptr;
             int ok = 1;
 #pragma unroll
             for (int i = 0; i < kLatCnPerThread; ++i)
                 if (cdeg[i] >= 0)
-                    ok &= check_step<P, DC, UNIFORM>(tid + i * T, M, cdeg[i], parity[tid + i * T], !last, slots, p);
+                    ok &= check_step<P, DC, UNIFORM, LEARNED>(tid + i * T, M, cdeg[i], parity[tid + i * T], !last,
+                                                              slots, p, wk);
             all = __syncthreads_and(ok);
-            if (last || (early && all)) break;
+            if (early && all) break;
+            if (last) {
+                if (!LEARNED || !learned) break;
+                learned = false;                  // fallback: plain min-sum from the prior
+                end = k + p.max_iter;
+                init_shot();
+                continue;
+            }
 #pragma unroll
             for (int i = 0; i < kLatVnPerThread; ++i)
                 if (vdeg[i] >= 0)
                     Q[i] = var_step_regs<P, DV>(vdeg[i], ev[i], uint32_t(M), gam[i], P::neg(Q[i]), slots, parity);
             __syncthreads();
+            ++k;
         }
 
 #pragma unroll
@@ -469,28 +528,28 @@ __global__ void __launch_bounds__(kLatencyMaxThreads, 1) msa_latency_kernel(cons
     QLDPC_DV_LIST(X, 6, true) QLDPC_DV_LIST(X, 7, true) QLDPC_DV_LIST(X, 8, true)               \
     QLDPC_DV_LIST(X, 8, false) QLDPC_DV_LIST(X, 16, false) QLDPC_DV_LIST(X, 32, false)
 
-template <class P>
+template <class P, bool LEARNED = false>
 const void *kernel_table(const KernelChoice &kc)
 {
 #define QLDPC_K(DCV, UNI, DVV)                                                                  \
     if (kc.dc == DCV && kc.uniform == UNI && kc.dvb == DVV)                                     \
-        return kc.latency ? reinterpret_cast<const void *>(&kern::msa_latency_kernel<P, DCV, UNI, DVV>) \
-                          : reinterpret_cast<const void *>(&kern::msa_batch_kernel<P, DCV, UNI, DVV>);
+        return kc.latency ? reinterpret_cast<const void *>(&kern::msa_latency_kernel<P, DCV, UNI, DVV, LEARNED>) \
+                          : reinterpret_cast<const void *>(&kern::msa_batch_kernel<P, DCV, UNI, DVV, LEARNED>);
     QLDPC_VARIANTS(QLDPC_K)
 #undef QLDPC_K
     return nullptr;
 }
 
-template <class P>
+template <class P, bool LEARNED = false>
 cudaError_t launch_table(const LaunchParams &p, const KernelChoice &kc, dim3 grid, int threads,
                          size_t smem, cudaStream_t stream)
 {
 #define QLDPC_L(DCV, UNI, DVV)                                                                  \
     if (kc.dc == DCV && kc.uniform == UNI && kc.dvb == DVV) {                                   \
         if (kc.latency)                                                                         \
-            kern::msa_latency_kernel<P, DCV, UNI, DVV><<<grid, threads, smem, stream>>>(p);     \
+            kern::msa_latency_kernel<P, DCV, UNI, DVV, LEARNED><<<grid, threads, smem, stream>>>(p); \
         else                                                                                    \
-            kern::msa_batch_kernel<P, DCV, UNI, DVV><<<grid, threads, smem, stream>>>(p);       \
+            kern::msa_batch_kernel<P, DCV, UNI, DVV, LEARNED><<<grid, threads, smem, stream>>>(p); \
         return cudaGetLastError();                                                              \
     }
     QLDPC_VARIANTS(QLDPC_L)

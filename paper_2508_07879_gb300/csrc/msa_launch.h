@@ -19,7 +19,10 @@ struct DeviceGraph {
     const uint8_t *vdeg;     // [n] column degree of internal variable u
     const uint8_t *rdeg;     // [m] row degrees
     const uint32_t *vperm;   // [n] original index of internal variable u
-    int32_t m, n;
+    const uint32_t *ecol;    // [dc_max * m] original variable of slot j*m + i (0xffffffff: no edge)
+    const int32_t *slot_edge;// [dc_max * m] CSR edge index of slot j*m + i (-1: no edge)
+    const uint32_t *eslot;   // [nnz] slot j*m + i of CSR edge e
+    int32_t m, n, nnz;
     int32_t dc_max, dv_max;  // largest row / column degree
 };
 
@@ -32,6 +35,8 @@ struct Problem {
     int32_t *iters;          // [batch]
     uint8_t *ok;             // [batch]
     float *post;             // [batch * n] or nullptr
+    const float *weights;    // learned decoding: [learned_iters][dc_max * m] slot-layout weights
+    int32_t learned_iters;   // learned iterations before the plain fallback (learned kernels only)
 };
 
 struct LaunchParams {
@@ -89,6 +94,7 @@ struct KernelChoice {
     int dc;          // exact row degree (uniform) or row-degree bucket 8/16/32
     bool uniform;    // every row has exactly dc edges
     int dvb;         // column-degree bucket 4/8/16
+    bool learned = false;   // learned weights first, then plain fallback (FP32 only)
 };
 
 // Latency kernel limits: checks M <= 2 * threads, variables N <= 2 * threads, threads <= 640
@@ -116,6 +122,8 @@ constexpr uint32_t kServerStopped = 8u;      // a worker left on the host's stop
 struct ServerCode {
     DeviceGraph g;
     const float *prior;         // device [n]
+    const float *weights;       // FP32 learned decoding: [learned_iters][dc_max * m], or nullptr
+    int32_t learned_iters;
     unsigned char *ring;        // ring_capacity slots of slot_bytes
     const uint32_t *tail;       // host-written count of published requests
     uint32_t *head;             // device count of claimed requests
@@ -152,5 +160,75 @@ cudaError_t launch_msa_f32(const LaunchParams &p, const KernelChoice &kc, dim3 g
                            size_t smem, cudaStream_t stream);
 cudaError_t launch_msa_i16(const LaunchParams &p, const KernelChoice &kc, dim3 grid, int threads,
                            size_t smem, cudaStream_t stream);
+// Learned (FP32) decoder kernels, msa_learned.cu.
+const void *msa_kernel_learned(const KernelChoice &kc);
+cudaError_t launch_msa_learned(const LaunchParams &p, const KernelChoice &kc, dim3 grid, int threads,
+                               size_t smem, cudaStream_t stream);
+
+// ---------------------------------------------------------------------------------------------
+// Training of the learned decoder and its helpers (nms_train.cu).
+// ---------------------------------------------------------------------------------------------
+// Recorded check-node state of one iteration: 4 words per check, word f of check i at f*m + i:
+//   0: min1 (FP32 bits)  1: min2 (FP32 bits)  2: sign bits, bit j = [q_j < 0]
+//   3: idx1 | idx2 << 8 | negall << 16   (negall = s_i XOR parity of all sign bits)
+constexpr int kStateWords = 4;
+constexpr int kTrainThreads = 128;   // threads per training block (one shot per block)
+
+struct TrainParams {
+    DeviceGraph g;
+    const uint8_t *syn;         // [batch * m]
+    const uint8_t *target;      // [batch * n] true error bits, caller's variable order
+    const float *prior;         // [n]
+    const float *w;             // [T][dc_max * m] slot-layout weights
+    uint32_t *state;            // [batch][T][kStateWords * m]
+    float *loss;                // [batch]
+    float *post;                // [batch * n] a-posteriori LLR of iteration T, or nullptr
+    const float *grad_loss;     // [batch]
+    float *partial;             // [grid][T][dc_max * m] per-block gradient sums
+    int32_t T, batch;
+};
+
+struct TrainChoice {
+    int dc;          // exact uniform row degree 6..8, else bucket 8/16/32
+    bool uniform;
+    int dvb;         // column-degree bucket 4/8/16
+};
+
+const void *nms_forward_kernel_ptr(const TrainChoice &tc);
+const void *nms_backward_kernel_ptr(const TrainChoice &tc);
+cudaError_t launch_nms_forward(const TrainParams &p, const TrainChoice &tc, int grid, int threads, size_t smem,
+                               cudaStream_t stream);
+cudaError_t launch_nms_backward(const TrainParams &p, const TrainChoice &tc, int grid, int threads, size_t smem,
+                                cudaStream_t stream);
+cudaError_t launch_permute_weights(const float *w_csr, const uint32_t *eslot, int32_t T, int32_t nnz, int32_t S,
+                                   float *w_slot, cudaStream_t stream);
+cudaError_t launch_reduce_grad(const float *partial, int32_t blocks, const int32_t *slot_edge, int32_t T, int32_t S,
+                               int32_t nnz, float *grad, cudaStream_t stream);
+cudaError_t launch_adam(float *param, const float *grad, float *m1, float *m2, int64_t count, int32_t step,
+                        float lr, float beta1, float beta2, float eps, cudaStream_t stream);
+cudaError_t launch_sample(const DeviceGraph &g, uint64_t seed, int64_t first_shot, int32_t batch, double p_lo,
+                          double p_hi, uint8_t *err, uint8_t *syn, int grid, cudaStream_t stream);
+cudaError_t launch_logical(const uint8_t *logicals, int32_t k, int32_t n, const uint8_t *err, const uint8_t *dec,
+                           const uint8_t *ok, int32_t batch, uint8_t *fail, int grid, cudaStream_t stream);
+
+// Shared memory of one training shot (forward: q slots, gamma, targets, syndrome; backward adds
+// the recomputed r slots and a cache of one iteration's recorded state).
+struct TrainLayout {
+    size_t slot_off, r_off, c_off, g_off, y_off, s_off, total;
+};
+
+__host__ __device__ inline TrainLayout train_layout(int m, int n, int dc_max, bool backward)
+{
+    TrainLayout t;
+    const size_t S = size_t(dc_max) * m;
+    t.slot_off = 0;                                                          // q / gradient slots [S] f32
+    t.r_off = align16(S * 4);                                                // r slots [S] f32 (backward)
+    t.c_off = backward ? align16(t.r_off + S * 4) : t.r_off;                 // state cache [4m] u32 (backward)
+    t.g_off = backward ? align16(t.c_off + size_t(kStateWords) * m * 4) : t.c_off;   // gamma [n] f32
+    t.y_off = align16(t.g_off + size_t(n) * 4);                              // targets [n] u8
+    t.s_off = align16(t.y_off + size_t(n));                                  // syndrome bits [m] u8
+    t.total = align16(t.s_off + size_t(m));
+    return t;
+}
 
 }  // namespace qldpc

@@ -1,0 +1,483 @@
+// Training of the neural normalized min-sum decoder on sm_103a: Algorithm 1 (Sec. 2 of
+// arXiv 2508.07879) with the scale alpha replaced by a learned weight w[t][e] per iteration and
+// edge, unrolled over T iterations, trained on the BCE of the soft outputs sigma(-Q).
+//
+//   nms_forward_kernel   one block per shot, persistent over the batch.  T iterations of the learned
+//                        check step and the exact variable step of the decoder kernels (so FP32
+//                        messages are bit-identical to the learned decoder's), the per-shot loss
+//                        1/(T N) sum_t sum_n BCE(sigma(-Q^t_n), y_n), and, per iteration and check, the
+//                        compressed check state: min1, min2, the positions attaining them (lowest on
+//                        ties), the sign bits of the inputs and the syndrome-flipped total sign.
+//   nms_backward_kernel  the reverse sweep.  It stores no message: every r^(t) is recomputed from
+//                        the recorded state (r_{m,n} = sign * (w * (n == idx1 ? min2 : min1))),
+//                        Q^(t) from those r, and the gradient flows
+//                          dL/dr_{m,n}   = dL/dQ_n + sum_{i != m} dL/dq_{i,n}      (variable step)
+//                          dL/dw_{m,n}   = dL/dr_{m,n} * sign * min_{j != n}|q_j|
+//                          dL/dq_{m,idx1} = sum_{n != idx1} dL/dr_{m,n} w sign * sign(q_idx1)
+//                          dL/dq_{m,idx2} = dL/dr_{m,idx1} w sign * sign(q_idx2)     (all other q: 0)
+//                        Two block barriers per iteration.  Each block sums its shots' weight
+//                        gradients into its own slice of a partial buffer (no atomics); a reduction
+//                        kernel adds the slices in block order, so the gradient is deterministic.
+//   helpers              CSR <-> slot-layout weight permutation, an Adam step, a counter-based
+//                        SplitMix64 error sampler with syndromes, and the logical-failure test.
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "msa_kernel.cuh"
+#include "msa_launch.h"
+
+namespace qldpc {
+namespace kern {
+
+__device__ __forceinline__ float softplus(float x) { return fmaxf(x, 0.0f) + log1pf(expf(-fabsf(x))); }
+__device__ __forceinline__ float sigmoid(float x) { return 1.0f / (1.0f + expf(-x)); }
+
+// Sum over the block (deterministic order); every thread gets the total.
+__device__ __forceinline__ float block_sum(float v, float *red)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    float t = 0.0f;
+    for (int i = 0; i < nw; ++i) t += red[i];
+    return t;
+}
+
+// Learned check step of the training forward for check c: r = sign * (w * min over the others),
+// written in place of q, and the compressed state of this iteration.
+template <int DC, bool UNIFORM>
+__device__ __forceinline__ void train_check_fwd(int c, int M, int deg, uint32_t s_bit, float *__restrict__ slots,
+                                                const float *__restrict__ w, uint32_t *__restrict__ st)
+{
+    float q[DC];
+    uint32_t signs = 0;
+    float m1 = __int_as_float(0x7f800000), m2 = m1;
+    int i1 = 0, i2 = 0;
+#pragma unroll
+    for (int j = 0; j < DC; ++j) {
+        if (UNIFORM || j < deg) {
+            q[j] = slots[j * M + c];
+            signs |= (__float_as_uint(q[j]) >> 31) << j;
+            const float a = fabsf(q[j]);
+            if (a < m1) {
+                m2 = m1;
+                i2 = i1;
+                m1 = a;
+                i1 = j;
+            } else if (a < m2) {
+                m2 = a;
+                i2 = j;
+            }
+        }
+    }
+    const uint32_t negall = (s_bit ^ uint32_t(__popc(signs))) & 1u;
+#pragma unroll
+    for (int j = 0; j < DC; ++j) {
+        if (UNIFORM || j < deg) {
+            const float r = __fmul_rn(__ldg(w + j * M + c), j == i1 ? m2 : m1);
+            slots[j * M + c] = F32::signed_like(r, q[j], negall);
+        }
+    }
+    st[c] = __float_as_uint(m1);
+    st[M + c] = __float_as_uint(m2);
+    st[2 * M + c] = signs;
+    st[3 * M + c] = uint32_t(i1) | (uint32_t(i2) << 8) | (negall << 16);
+}
+
+// r of check c recomputed from its recorded state (bit-identical to the forward's r).
+template <int DC, bool UNIFORM>
+__device__ __forceinline__ void recompute_r(int c, int M, int deg, uint32_t m1b, uint32_t m2b, uint32_t signs,
+                                            uint32_t iw, const float *__restrict__ w, float *__restrict__ rs)
+{
+    const int i1 = int(iw & 0xffu);
+    const uint32_t negall = (iw >> 16) & 1u;
+    const float m1 = __uint_as_float(m1b), m2 = __uint_as_float(m2b);
+#pragma unroll
+    for (int j = 0; j < DC; ++j) {
+        if (UNIFORM || j < deg) {
+            const float r = __fmul_rn(__ldg(w + j * M + c), j == i1 ? m2 : m1);
+            rs[j * M + c] = __uint_as_float(__float_as_uint(r) ^ ((((signs >> j) & 1u) ^ negall) << 31));
+        }
+    }
+}
+
+template <int DC, bool UNIFORM, int DV>
+__global__ void __launch_bounds__(kTrainThreads, 4) nms_forward_kernel(const TrainParams p)
+{
+    const int M = p.g.m, N = p.g.n, T = blockDim.x, tid = threadIdx.x;
+    const size_t S = size_t(p.g.dc_max) * M;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const TrainLayout L = train_layout(M, N, p.g.dc_max, false);
+    float *slots = reinterpret_cast<float *>(smem + L.slot_off);
+    float *gam = reinterpret_cast<float *>(smem + L.g_off);
+    uint8_t *y = smem + L.y_off;
+    uint8_t *sb = smem + L.s_off;
+    __shared__ float red[32];
+
+    for (int u = tid; u < N; u += T) gam[u] = F32::quantize(p.prior[__ldg(p.g.vperm + u)]);
+    const float inv = 1.0f / (float(p.T) * float(N));
+    for (int b = blockIdx.x; b < p.batch; b += gridDim.x) {
+        const uint8_t *s = p.syn + size_t(b) * M;
+        const uint8_t *tg = p.target + size_t(b) * N;
+        for (int c = tid; c < M; c += T) sb[c] = s[c] & 1u;
+        __syncthreads();   // gam (first shot) and the previous shot's last reads are done
+        for (int u = tid; u < N; u += T) {
+            y[u] = tg[__ldg(p.g.vperm + u)] & 1u;
+            const int deg = __ldg(p.g.vdeg + u);
+            for (int k = 0; k < deg; ++k) slots[slot_of(__ldg(p.g.vslot + size_t(k) * N + u), uint32_t(M))] = gam[u];
+        }
+        __syncthreads();
+        float acc = 0.0f;
+        for (int k = 0; k < p.T; ++k) {
+            const float *wk = p.w + size_t(k) * S;
+            uint32_t *st = p.state + (size_t(b) * p.T + k) * size_t(kStateWords) * M;
+            for (int c = tid; c < M; c += T) {
+                const int deg = UNIFORM ? DC : int(__ldg(p.g.rdeg + c));
+                train_check_fwd<DC, UNIFORM>(c, M, deg, sb[c], slots, wk, st);
+            }
+            __syncthreads();
+            const bool lastk = k + 1 == p.T;
+            for (int u = tid; u < N; u += T) {
+                const float Q = var_step_batch<F32, DV, false>(__ldg(p.g.vdeg + u), u, N, uint32_t(M), p.g.vslot,
+                                                               gam[u], false, slots, nullptr);
+                acc += y[u] ? softplus(Q) : softplus(-Q);
+                if (lastk && p.post) p.post[size_t(b) * N + __ldg(p.g.vperm + u)] = Q;
+            }
+            __syncthreads();
+        }
+        const float total = block_sum(acc, red);
+        if (tid == 0) p.loss[b] = total * inv;
+    }
+}
+
+template <int DC, bool UNIFORM, int DV>
+__global__ void __launch_bounds__(kTrainThreads, 4) nms_backward_kernel(const TrainParams p)
+{
+    const int M = p.g.m, N = p.g.n, T = blockDim.x, tid = threadIdx.x;
+    const size_t S = size_t(p.g.dc_max) * M;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const TrainLayout L = train_layout(M, N, p.g.dc_max, true);
+    float *gs = reinterpret_cast<float *>(smem + L.slot_off);     // dL/dq (next iteration), then dL/dr
+    float *rs = reinterpret_cast<float *>(smem + L.r_off);        // recomputed r of the current iteration
+    uint32_t *sc = reinterpret_cast<uint32_t *>(smem + L.c_off);  // recorded state of the current iteration
+    float *gam = reinterpret_cast<float *>(smem + L.g_off);
+    uint8_t *y = smem + L.y_off;
+
+    for (int u = tid; u < N; u += T) gam[u] = F32::quantize(p.prior[__ldg(p.g.vperm + u)]);
+    float *part = p.partial + size_t(blockIdx.x) * p.T * S;
+    const float inv = 1.0f / (float(p.T) * float(N));
+    bool first = true;   // the block's first shot writes its partial slice, later shots add to it
+    for (int b = blockIdx.x; b < p.batch; b += gridDim.x) {
+        const uint8_t *tg = p.target + size_t(b) * N;
+        const float gscale = p.grad_loss[b] * inv;
+        const uint32_t *stb = p.state + size_t(b) * p.T * size_t(kStateWords) * M;
+        __syncthreads();   // gam (first shot) and the previous shot's last reads are done
+        for (int u = tid; u < N; u += T) y[u] = tg[__ldg(p.g.vperm + u)] & 1u;
+        // iteration T: recompute r, cache the state; dL/dq of iteration T+1 is zero
+        {
+            const uint32_t *st = stb + size_t(p.T - 1) * kStateWords * M;
+            const float *wk = p.w + size_t(p.T - 1) * S;
+            for (int c = tid; c < M; c += T) {
+                const int deg = UNIFORM ? DC : int(__ldg(p.g.rdeg + c));
+                const uint32_t a = st[c], bb = st[M + c], sg = st[2 * M + c], iw = st[3 * M + c];
+                sc[c] = a;
+                sc[M + c] = bb;
+                sc[2 * M + c] = sg;
+                sc[3 * M + c] = iw;
+                recompute_r<DC, UNIFORM>(c, M, deg, a, bb, sg, iw, wk, rs);
+#pragma unroll
+                for (int j = 0; j < DC; ++j)
+                    if (UNIFORM || j < deg) gs[j * M + c] = 0.0f;
+            }
+        }
+        __syncthreads();
+        for (int k = p.T - 1; k >= 0; --k) {
+            // variable side: Q^(k) from the recomputed r, dL/dQ, and dL/dr for every edge
+            for (int u = tid; u < N; u += T) {
+                const int deg = __ldg(p.g.vdeg + u);
+                uint32_t sl[DV];
+                float Q = gam[u], G = 0.0f;
+#pragma unroll
+                for (int i = 0; i < DV; ++i) {
+                    if (i < deg) {
+                        sl[i] = slot_of(__ldg(p.g.vslot + size_t(i) * N + u), uint32_t(M));
+                        Q = __fadd_rn(Q, rs[sl[i]]);
+                        G += gs[sl[i]];
+                    }
+                }
+                const float gQ = gscale * (float(y[u]) - sigmoid(-Q));
+#pragma unroll
+                for (int i = 0; i < DV; ++i)
+                    if (i < deg) gs[sl[i]] = gQ + (G - gs[sl[i]]);
+            }
+            __syncthreads();
+            // check side: weight gradient, dL/dq of iteration k, and r of iteration k-1
+            const float *wk = p.w + size_t(k) * S;
+            float *pk = part + size_t(k) * S;
+            for (int c = tid; c < M; c += T) {
+                const int deg = UNIFORM ? DC : int(__ldg(p.g.rdeg + c));
+                const float m1 = __uint_as_float(sc[c]), m2 = __uint_as_float(sc[M + c]);
+                const uint32_t signs = sc[2 * M + c], iw = sc[3 * M + c];
+                const int i1 = int(iw & 0xffu), i2 = int((iw >> 8) & 0xffu);
+                const uint32_t negall = (iw >> 16) & 1u;
+                float acc1 = 0.0f, t1 = 0.0f;
+#pragma unroll
+                for (int j = 0; j < DC; ++j) {
+                    if (UNIFORM || j < deg) {
+                        const float gr = gs[j * M + c];
+                        const float sgn = (((signs >> j) & 1u) ^ negall) ? -1.0f : 1.0f;
+                        const float mu = j == i1 ? m2 : m1;
+                        const float gw = gr * sgn * mu;
+                        pk[j * M + c] = first ? gw : pk[j * M + c] + gw;
+                        const float t = gr * __ldg(wk + j * M + c) * sgn;
+                        if (j == i1)
+                            t1 = t;
+                        else
+                            acc1 += t;
+                    }
+                }
+                const float gq1 = ((signs >> i1) & 1u) ? -acc1 : acc1;
+                const float gq2 = ((signs >> i2) & 1u) ? -t1 : t1;
+#pragma unroll
+                for (int j = 0; j < DC; ++j)
+                    if (UNIFORM || j < deg) gs[j * M + c] = j == i1 ? gq1 : (j == i2 ? gq2 : 0.0f);
+                if (k > 0) {
+                    const uint32_t *st = stb + size_t(k - 1) * kStateWords * M;
+                    const uint32_t a = st[c], bb = st[M + c], sg = st[2 * M + c], iw2 = st[3 * M + c];
+                    sc[c] = a;
+                    sc[M + c] = bb;
+                    sc[2 * M + c] = sg;
+                    sc[3 * M + c] = iw2;
+                    recompute_r<DC, UNIFORM>(c, M, deg, a, bb, sg, iw2, p.w + size_t(k - 1) * S, rs);
+                }
+            }
+            __syncthreads();
+        }
+        first = false;
+    }
+}
+
+// w_slot[t][eslot[e]] = w_csr[t][e]; padding slots are never read.
+__global__ void permute_weights_kernel(const float *__restrict__ w_csr, const uint32_t *__restrict__ eslot, int32_t T,
+                                       int32_t nnz, int32_t S, float *__restrict__ w_slot)
+{
+    const int64_t total = int64_t(T) * nnz;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t t = i / nnz, e = i - t * nnz;
+        w_slot[t * S + __ldg(eslot + e)] = w_csr[i];
+    }
+}
+
+// grad[t][slot_edge[sl]] = sum over blocks (in block order) of partial[blk][t][sl].
+__global__ void reduce_grad_kernel(const float *__restrict__ partial, int32_t blocks, const int32_t *__restrict__ slot_edge,
+                                   int32_t T, int32_t S, int32_t nnz, float *__restrict__ grad)
+{
+    const int64_t total = int64_t(T) * S, stride = total;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t t = i / S, sl = i - t * S;
+        const int32_t e = __ldg(slot_edge + sl);
+        if (e < 0) continue;
+        float acc = 0.0f;
+        for (int32_t b = 0; b < blocks; ++b) acc += __ldcs(partial + b * stride + i);
+        grad[t * nnz + e] = acc;
+    }
+}
+
+// One Adam step (Kingma and Ba, 2015) in the form of PyTorch's single-tensor implementation:
+//   m = m + (1 - b1) (g - m);  v = b2 v + (1 - b2) g^2;
+//   p = p - (lr / (1 - b1^t)) * m / (sqrt(v) / sqrt(1 - b2^t) + eps)
+__global__ void adam_kernel(float *__restrict__ param, const float *__restrict__ grad, float *__restrict__ m1,
+                            float *__restrict__ m2, int64_t count, float beta1, float beta2, float eps,
+                            float step_size, float bc2_sqrt)
+{
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < count; i += int64_t(gridDim.x) * blockDim.x) {
+        const float g = grad[i];
+        const float a = m1[i] + (1.0f - beta1) * (g - m1[i]);
+        const float v = beta2 * m2[i] + (1.0f - beta2) * g * g;
+        m1[i] = a;
+        m2[i] = v;
+        param[i] = param[i] - step_size * (a / (sqrtf(v) / bc2_sqrt + eps));
+    }
+}
+
+// SplitMix64 (Steele, Lea and Flood, OOPSLA 2014): the output of one step from state x.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x)
+{
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Errors at a per-shot rate and their syndromes, one block per shot.  Counter-based keying
+// (seed, shot, qubit): u = top 53 bits of mix(mix(mix(seed) + shot) + qubit) / 2^53;
+// p_shot = p_lo + p_span * u(qubit n); e_q = [u(q) < p_shot]; s_i = XOR of e over row i.
+__global__ void sample_kernel(const DeviceGraph g, uint64_t seed, int64_t first_shot, int32_t batch, double p_lo,
+                              double p_span, uint8_t *__restrict__ err, uint8_t *__restrict__ syn)
+{
+    extern __shared__ __align__(16) unsigned char es[];
+    const int M = g.m, N = g.n, T = blockDim.x, tid = threadIdx.x;
+    const uint64_t k_seed = splitmix64(seed);
+    for (int b = blockIdx.x; b < batch; b += gridDim.x) {
+        const uint64_t k_shot = splitmix64(k_seed + uint64_t(first_shot + b));
+        const double un = double(splitmix64(k_shot + uint64_t(N)) >> 11) * 1.1102230246251565e-16;   // 2^-53
+        const double thr = __dmul_rn(__dadd_rn(p_lo, __dmul_rn(p_span, un)), 9007199254740992.0);     // p * 2^53
+        for (int q = tid; q < N; q += T) {
+            const uint8_t e = double(splitmix64(k_shot + uint64_t(q)) >> 11) < thr ? 1 : 0;
+            es[q] = e;
+            err[size_t(b) * N + q] = e;
+        }
+        __syncthreads();
+        for (int c = tid; c < M; c += T) {
+            const int deg = __ldg(g.rdeg + c);
+            uint32_t par = 0;
+            for (int j = 0; j < deg; ++j) par ^= es[__ldg(g.ecol + size_t(j) * M + c)];
+            syn[size_t(b) * M + c] = uint8_t(par);
+        }
+        __syncthreads();
+    }
+}
+
+// fail_b = !ok_b OR some logical operator l has odd overlap with the residual e_b XOR e_hat_b.
+__global__ void logical_kernel(const uint8_t *__restrict__ logicals, int32_t K, int32_t N, const uint8_t *__restrict__ err,
+                               const uint8_t *__restrict__ dec, const uint8_t *__restrict__ ok, int32_t batch,
+                               uint8_t *__restrict__ fail)
+{
+    extern __shared__ __align__(16) uint32_t lw[];
+    const int W = (N + 31) / 32, T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nwarp = (T + 31) / 32;
+    uint32_t *rw = lw + size_t(K) * W;
+    for (int idx = warp; idx < K * W; idx += nwarp) {   // pack L row by row, 32 qubits per word
+        const int l = idx / W, wd = idx - l * W, q = wd * 32 + lane;
+        const uint32_t bits = __ballot_sync(0xffffffffu, q < N && logicals[size_t(l) * N + q]);
+        if (lane == 0) lw[idx] = bits;
+    }
+    for (int b = blockIdx.x; b < batch; b += gridDim.x) {
+        __syncthreads();
+        for (int wd = warp; wd < W; wd += nwarp) {
+            const int q = wd * 32 + lane;
+            const bool r = q < N && ((err[size_t(b) * N + q] ^ dec[size_t(b) * N + q]) & 1u);
+            const uint32_t bits = __ballot_sync(0xffffffffu, r);
+            if (lane == 0) rw[wd] = bits;
+        }
+        __syncthreads();
+        int odd = 0;
+        for (int l = tid; l < K; l += T) {
+            uint32_t par = 0;
+            for (int wd = 0; wd < W; ++wd) par ^= uint32_t(__popc(lw[l * W + wd] & rw[wd]));
+            odd |= int(par & 1u);
+        }
+        odd = __syncthreads_or(odd);
+        if (tid == 0) fail[b] = (ok[b] == 0 || odd) ? 1 : 0;
+    }
+}
+
+}  // namespace kern
+
+// Compiled training variants: uniform row degree 6..8 with column-degree bucket 4 or 8, else a
+// row-degree bucket 8/16/32 with column-degree bucket 8 or 16.
+#define QLDPC_TRAIN_VARIANTS(X)                                                                 \
+    X(6, true, 4) X(6, true, 8) X(7, true, 4) X(7, true, 8) X(8, true, 4) X(8, true, 8)        \
+    X(8, false, 8) X(8, false, 16) X(16, false, 8) X(16, false, 16) X(32, false, 8) X(32, false, 16)
+
+const void *nms_forward_kernel_ptr(const TrainChoice &tc)
+{
+#define QLDPC_K(DCV, UNI, DVV)                                                                  \
+    if (tc.dc == DCV && tc.uniform == UNI && tc.dvb == DVV)                                     \
+        return reinterpret_cast<const void *>(&kern::nms_forward_kernel<DCV, UNI, DVV>);
+    QLDPC_TRAIN_VARIANTS(QLDPC_K)
+#undef QLDPC_K
+    return nullptr;
+}
+
+const void *nms_backward_kernel_ptr(const TrainChoice &tc)
+{
+#define QLDPC_K(DCV, UNI, DVV)                                                                  \
+    if (tc.dc == DCV && tc.uniform == UNI && tc.dvb == DVV)                                     \
+        return reinterpret_cast<const void *>(&kern::nms_backward_kernel<DCV, UNI, DVV>);
+    QLDPC_TRAIN_VARIANTS(QLDPC_K)
+#undef QLDPC_K
+    return nullptr;
+}
+
+cudaError_t launch_nms_forward(const TrainParams &p, const TrainChoice &tc, int grid, int threads, size_t smem,
+                               cudaStream_t stream)
+{
+#define QLDPC_L(DCV, UNI, DVV)                                                                  \
+    if (tc.dc == DCV && tc.uniform == UNI && tc.dvb == DVV) {                                   \
+        kern::nms_forward_kernel<DCV, UNI, DVV><<<grid, threads, smem, stream>>>(p);            \
+        return cudaGetLastError();                                                              \
+    }
+    QLDPC_TRAIN_VARIANTS(QLDPC_L)
+#undef QLDPC_L
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_nms_backward(const TrainParams &p, const TrainChoice &tc, int grid, int threads, size_t smem,
+                                cudaStream_t stream)
+{
+#define QLDPC_L(DCV, UNI, DVV)                                                                  \
+    if (tc.dc == DCV && tc.uniform == UNI && tc.dvb == DVV) {                                   \
+        kern::nms_backward_kernel<DCV, UNI, DVV><<<grid, threads, smem, stream>>>(p);           \
+        return cudaGetLastError();                                                              \
+    }
+    QLDPC_TRAIN_VARIANTS(QLDPC_L)
+#undef QLDPC_L
+    return cudaErrorInvalidValue;
+}
+
+namespace {
+int elementwise_grid(int64_t count)
+{
+    return int(std::max<int64_t>(1, std::min<int64_t>((count + 255) / 256, 4096)));
+}
+}  // namespace
+
+cudaError_t launch_permute_weights(const float *w_csr, const uint32_t *eslot, int32_t T, int32_t nnz, int32_t S,
+                                   float *w_slot, cudaStream_t stream)
+{
+    kern::permute_weights_kernel<<<elementwise_grid(int64_t(T) * nnz), 256, 0, stream>>>(w_csr, eslot, T, nnz, S,
+                                                                                         w_slot);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_grad(const float *partial, int32_t blocks, const int32_t *slot_edge, int32_t T, int32_t S,
+                               int32_t nnz, float *grad, cudaStream_t stream)
+{
+    kern::reduce_grad_kernel<<<elementwise_grid(int64_t(T) * S), 256, 0, stream>>>(partial, blocks, slot_edge, T, S,
+                                                                                   nnz, grad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adam(float *param, const float *grad, float *m1, float *m2, int64_t count, int32_t step,
+                        float lr, float beta1, float beta2, float eps, cudaStream_t stream)
+{
+    const double bc1 = 1.0 - std::pow(double(beta1), double(step));
+    const double bc2 = 1.0 - std::pow(double(beta2), double(step));
+    kern::adam_kernel<<<elementwise_grid(count), 256, 0, stream>>>(param, grad, m1, m2, count, beta1, beta2, eps,
+                                                                   float(double(lr) / bc1), float(std::sqrt(bc2)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sample(const DeviceGraph &g, uint64_t seed, int64_t first_shot, int32_t batch, double p_lo,
+                          double p_hi, uint8_t *err, uint8_t *syn, int grid, cudaStream_t stream)
+{
+    kern::sample_kernel<<<grid, 256, size_t(g.n), stream>>>(g, seed, first_shot, batch, p_lo, p_hi - p_lo, err, syn);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_logical(const uint8_t *logicals, int32_t k, int32_t n, const uint8_t *err, const uint8_t *dec,
+                           const uint8_t *ok, int32_t batch, uint8_t *fail, int grid, cudaStream_t stream)
+{
+    const size_t smem = (size_t(k) + 1) * size_t((n + 31) / 32) * 4;
+    kern::logical_kernel<<<grid, 128, smem, stream>>>(logicals, k, n, err, dec, ok, batch, fail);
+    return cudaGetLastError();
+}
+
+}  // namespace qldpc

@@ -27,6 +27,7 @@ int dv_bucket(int d) { return d <= 4 ? 4 : d <= 8 ? 8 : d <= 16 ? 16 : -1; }
 
 const void *msa_kernel(int precision, const KernelChoice &kc)
 {
+    if (kc.learned) return msa_kernel_learned(kc);
     return precision == kINT16 ? msa_kernel_i16(kc) : msa_kernel_f32(kc);
 }
 
@@ -34,6 +35,7 @@ cudaError_t launch_msa(const LaunchParams &p, int precision, const KernelChoice 
                        int grid_x, size_t smem, cudaStream_t stream)
 {
     dim3 grid(unsigned(grid_x), unsigned(p.nprob));
+    if (kc.learned) return launch_msa_learned(p, kc, grid, threads, smem, stream);
     return precision == kINT16 ? launch_msa_i16(p, kc, grid, threads, smem, stream)
                                : launch_msa_f32(p, kc, grid, threads, smem, stream);
 }
@@ -51,6 +53,9 @@ struct HostLayout {
     std::vector<uint8_t> rdeg, vdeg;
     std::vector<uint32_t> vslot;   // [dv_max * n]
     std::vector<uint32_t> vorder;  // [n] by descending degree, stable
+    std::vector<uint32_t> eslot;   // [nnz] slot j*m + i of CSR edge e
+    std::vector<int32_t> slot_edge;// [dc_max * m] CSR edge of each slot, -1 for padding
+    std::vector<uint32_t> ecol;    // [dc_max * m] caller's variable of each slot, ~0 for padding
 };
 
 int validate_and_layout(const int32_t *row_ptr, const int32_t *col_idx, int32_t m, int32_t n,
@@ -95,6 +100,10 @@ int validate_and_layout(const int32_t *row_ptr, const int32_t *col_idx, int32_t 
     out.vslot.assign(size_t(std::max(dv_max, 1)) * size_t(n), 0u);
     // Rows are visited in ascending order, so each variable's list is in ascending check order,
     // the order in which the variable step accumulates its sums.
+    const size_t S = size_t(dc_max) * size_t(m);
+    out.eslot.assign(size_t(nnz), 0u);
+    out.slot_edge.assign(S, -1);
+    out.ecol.assign(S, ~0u);
     for (int32_t i = 0; i < m; ++i) {
         out.rdeg[size_t(i)] = uint8_t(row_ptr[i + 1] - row_ptr[i]);
         out.uniform_rows = out.uniform_rows && (row_ptr[i + 1] - row_ptr[i]) == dc_max;
@@ -103,6 +112,10 @@ int validate_and_layout(const int32_t *row_ptr, const int32_t *col_idx, int32_t 
             const int32_t j = e - row_ptr[i];
             const int32_t k = out.vdeg[u]++;
             out.vslot[size_t(k) * n + u] = (uint32_t(j) << 16) | uint32_t(i);
+            const size_t sl = size_t(j) * size_t(m) + size_t(i);
+            out.eslot[size_t(e)] = uint32_t(sl);
+            out.slot_edge[sl] = e;
+            out.ecol[sl] = uint32_t(col_idx[e]);
         }
     }
     return QLDPC_OK;
@@ -166,7 +179,7 @@ int round32(int x) { return (x + 31) / 32 * 32; }
 constexpr int kBatchThreads = 128;
 
 // Compiled variant for the graphs of one call: exact uniform row degree 6..8, else a bucket.
-KernelChoice variant(const qldpc_graph *const *gs, int nprob, bool latency)
+KernelChoice variant(const qldpc_graph *const *gs, int nprob, bool latency, bool learned)
 {
     int dc = 0, dv = 0;
     bool uniform = true;
@@ -175,8 +188,8 @@ KernelChoice variant(const qldpc_graph *const *gs, int nprob, bool latency)
         dv = std::max(dv, gs[i]->dv_max);
         uniform = uniform && gs[i]->uniform_rows && gs[i]->dc_max == gs[0]->dc_max;
     }
-    if (uniform && dc >= 6 && dc <= 8) return KernelChoice{latency, dc, true, dv_bucket(dv)};
-    return KernelChoice{latency, dc_bucket(dc), false, dv_bucket(dv)};
+    if (uniform && dc >= 6 && dc <= 8) return KernelChoice{latency, dc, true, dv_bucket(dv), learned};
+    return KernelChoice{latency, dc_bucket(dc), false, dv_bucket(dv), learned};
 }
 
 int occupancy_grid(const qldpc_graph *g0, const void *k, int threads, size_t smem, int nprob,
@@ -195,7 +208,7 @@ int occupancy_grid(const qldpc_graph *g0, const void *k, int threads, size_t sme
 // Single-shot (latency) path: chosen automatically when every shot of the call gets its own SM,
 // or forced with QLDPC_KERNEL_LATENCY.  One pass over the checks and the variables when both fit
 // in a block of up to 640 threads, else two passes of a block sized for the larger half.
-int plan_latency(const qldpc_graph *const *gs, int nprob, int32_t batch, int precision, Plan &pl,
+int plan_latency(const qldpc_graph *const *gs, int nprob, int32_t batch, int precision, bool learned, Plan &pl,
                  bool &chosen)
 {
     const qldpc_graph *g0 = gs[0];
@@ -216,7 +229,7 @@ int plan_latency(const qldpc_graph *const *gs, int nprob, int32_t batch, int pre
     for (int i = 0; i < nprob; ++i)
         fits = fits && gs[i]->m <= kLatencyCnPerThread * threads && gs[i]->n <= kLatencyVnPerThread * threads;
     if (!fits) return forced ? QLDPC_ERR_UNSUPPORTED : QLDPC_OK;
-    pl.kc = variant(gs, nprob, true);
+    pl.kc = variant(gs, nprob, true, learned);
     pl.threads = threads;
     pl.smem = smem;
     const void *k = msa_kernel(precision, pl.kc);
@@ -229,12 +242,12 @@ int plan_latency(const qldpc_graph *const *gs, int nprob, int32_t batch, int pre
     return QLDPC_OK;
 }
 
-int plan_batch(const qldpc_graph *const *gs, int nprob, int32_t batch, int precision, Plan &pl)
+int plan_batch(const qldpc_graph *const *gs, int nprob, int32_t batch, int precision, bool learned, Plan &pl)
 {
     const qldpc_graph *g0 = gs[0];
     size_t smem = 0;
     for (int i = 0; i < nprob; ++i) smem = std::max(smem, shot_smem(gs[i], precision));
-    pl.kc = variant(gs, nprob, false);
+    pl.kc = variant(gs, nprob, false, learned);
     pl.threads = g0->user_threads ? g0->user_threads : kBatchThreads;
     pl.smem = smem;
     const void *k = msa_kernel(precision, pl.kc);
@@ -254,8 +267,13 @@ int launch(const qldpc_graph *g0, const qldpc_graph *g1, const Problem *probs, i
            cudaStream_t stream)
 {
     if (precision != QLDPC_FP32 && precision != QLDPC_INT16) return QLDPC_ERR_INVALID_ARG;
-    if ((flags & ~uint32_t(QLDPC_NO_EARLY_STOP)) != 0) return QLDPC_ERR_INVALID_ARG;
+    if ((flags & ~uint32_t(QLDPC_NO_EARLY_STOP | QLDPC_LEARNED)) != 0) return QLDPC_ERR_INVALID_ARG;
     if (batch < 0 || max_iter < 0 || !finite_alpha(alpha)) return QLDPC_ERR_INVALID_ARG;
+    const bool learned = (flags & QLDPC_LEARNED) != 0;
+    if (learned) {   // FP32 weights, stop test on, weights set on every graph of the call
+        if (precision != QLDPC_FP32 || (flags & QLDPC_NO_EARLY_STOP)) return QLDPC_ERR_INVALID_ARG;
+        if (!g0->d_weights || !g1->d_weights) return QLDPC_ERR_INVALID_ARG;
+    }
     int aq = 0;
     if (precision == QLDPC_INT16) {
         aq = alpha_fixed(alpha);
@@ -269,16 +287,16 @@ int launch(const qldpc_graph *g0, const qldpc_graph *g1, const Problem *probs, i
     p.max_iter = max_iter;
     p.alpha = alpha;
     p.alpha_q = aq;
-    p.flags = flags;
+    p.flags = flags & QLDPC_NO_EARLY_STOP;
     for (int i = 0; i < nprob; ++i) p.prob[i] = probs[i];
 
     // One kernel variant and one block shape serve both problems of a pair.
     const qldpc_graph *gs[2] = {g0, g1};
     Plan pl;
     bool latency = false;
-    if (int rc = plan_latency(gs, nprob, batch, precision, pl, latency)) return rc;
+    if (int rc = plan_latency(gs, nprob, batch, precision, learned, pl, latency)) return rc;
     if (!latency)
-        if (int rc = plan_batch(gs, nprob, batch, precision, pl)) return rc;
+        if (int rc = plan_batch(gs, nprob, batch, precision, learned, pl)) return rc;
     return cuda_status(launch_msa(p, precision, pl.kc, pl.threads, pl.grid, pl.smem, stream));
 }
 
@@ -293,6 +311,8 @@ Problem make_problem(const qldpc_graph *g, const uint8_t *syn, const float *prio
     pr.iters = iters;
     pr.ok = ok;
     pr.post = post;
+    pr.weights = g->d_weights;
+    pr.learned_iters = g->learned_T;
     return pr;
 }
 
@@ -423,30 +443,38 @@ int qldpc_graph_create(const int32_t *row_ptr, const int32_t *col_idx, int32_t m
         return QLDPC_ERR_UNSUPPORTED;
     }
 
-    const size_t vs_b = align16(hl.vslot.size() * sizeof(uint32_t));
-    const size_t vd_b = align16(size_t(n));
-    const size_t rd_b = align16(size_t(m));
-    const size_t vo_b = align16(size_t(n) * sizeof(uint32_t));
-    e = cudaMalloc(&g->d_block, vs_b + vd_b + rd_b + vo_b);
+    // one device block: vslot | vdeg | rdeg | vperm | eslot | slot_edge | ecol
+    const size_t sizes[7] = {hl.vslot.size() * sizeof(uint32_t), size_t(n), size_t(m), size_t(n) * sizeof(uint32_t),
+                             hl.eslot.size() * sizeof(uint32_t), hl.slot_edge.size() * sizeof(int32_t),
+                             hl.ecol.size() * sizeof(uint32_t)};
+    const void *srcs[7] = {hl.vslot.data(), hl.vdeg.data(), hl.rdeg.data(), hl.vorder.data(),
+                           hl.eslot.data(), hl.slot_edge.data(), hl.ecol.data()};
+    size_t offs[7], total = 0;
+    for (int i = 0; i < 7; ++i) {
+        offs[i] = total;
+        total += align16(std::max<size_t>(sizes[i], 1));
+    }
+    e = cudaMalloc(&g->d_block, total);
     if (e != cudaSuccess) {
         delete g;
         return cuda_status(e);
     }
     char *b = static_cast<char *>(g->d_block);
-    e = cudaMemcpy(b, hl.vslot.data(), hl.vslot.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(b + vs_b, hl.vdeg.data(), size_t(n), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(b + vs_b + vd_b, hl.rdeg.data(), size_t(m), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(b + vs_b + vd_b + rd_b, hl.vorder.data(), size_t(n) * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    for (int i = 0; i < 7 && e == cudaSuccess; ++i)
+        if (sizes[i]) e = cudaMemcpy(b + offs[i], srcs[i], sizes[i], cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(g->d_block);
         delete g;
         return cuda_status(e);
     }
-    g->dg.vslot = reinterpret_cast<const uint32_t *>(b);
-    g->dg.vdeg = reinterpret_cast<const uint8_t *>(b + vs_b);
-    g->dg.rdeg = reinterpret_cast<const uint8_t *>(b + vs_b + vd_b);
-    g->dg.vperm = reinterpret_cast<const uint32_t *>(b + vs_b + vd_b + rd_b);
+    g->dg.vslot = reinterpret_cast<const uint32_t *>(b + offs[0]);
+    g->dg.vdeg = reinterpret_cast<const uint8_t *>(b + offs[1]);
+    g->dg.rdeg = reinterpret_cast<const uint8_t *>(b + offs[2]);
+    g->dg.vperm = reinterpret_cast<const uint32_t *>(b + offs[3]);
+    g->dg.eslot = reinterpret_cast<const uint32_t *>(b + offs[4]);
+    g->dg.slot_edge = reinterpret_cast<const int32_t *>(b + offs[5]);
+    g->dg.ecol = reinterpret_cast<const uint32_t *>(b + offs[6]);
+    g->dg.nnz = g->nnz;
     g->dg.m = m;
     g->dg.n = n;
     g->dg.dc_max = hl.dc_max;
@@ -484,6 +512,7 @@ void qldpc_graph_destroy(qldpc_graph *g)
     if (!g) return;
     free_stage(g);
     if (g->d_block) cudaFree(g->d_block);
+    if (g->d_weights) cudaFree(g->d_weights);
     delete g;
 }
 
@@ -521,8 +550,8 @@ int qldpc_graph_set_launch(qldpc_graph *g, int32_t kernel, int32_t threads_per_b
         Plan pl;
         bool latency = false;
         const int32_t big = int32_t(1) << 30;
-        rc = plan_latency(gs, 1, big, prec, pl, latency);
-        if (rc == QLDPC_OK && !latency) rc = plan_batch(gs, 1, big, prec, pl);
+        rc = plan_latency(gs, 1, big, prec, false, pl, latency);
+        if (rc == QLDPC_OK && !latency) rc = plan_batch(gs, 1, big, prec, false, pl);
         if (rc == QLDPC_OK && blocks_per_sm && pl.grid < blocks_per_sm * g->sm_count) rc = QLDPC_ERR_UNSUPPORTED;
         if (rc) break;
     }

@@ -134,7 +134,10 @@ int qldpc_server_create(const qldpc_graph *const *graphs, const float *const *pr
     *out = nullptr;
     if (!graphs || !priors || !cfg || ncodes < 1 || ncodes > QLDPC_SERVER_MAX_CODES) return QLDPC_ERR_INVALID_ARG;
     if (cfg->precision != QLDPC_FP32 && cfg->precision != QLDPC_INT16) return QLDPC_ERR_INVALID_ARG;
-    if ((cfg->flags & ~uint32_t(QLDPC_NO_EARLY_STOP)) != 0 || cfg->max_iter < 0) return QLDPC_ERR_INVALID_ARG;
+    if ((cfg->flags & ~uint32_t(QLDPC_NO_EARLY_STOP | QLDPC_LEARNED)) != 0 || cfg->max_iter < 0)
+        return QLDPC_ERR_INVALID_ARG;
+    const bool learned = (cfg->flags & QLDPC_LEARNED) != 0;
+    if (learned && (cfg->precision != QLDPC_FP32 || (cfg->flags & QLDPC_NO_EARLY_STOP))) return QLDPC_ERR_INVALID_ARG;
     if (!std::isfinite(cfg->alpha) || cfg->alpha <= 0.0f) return QLDPC_ERR_INVALID_ARG;
     const int aq = cfg->precision == QLDPC_INT16 ? alpha_fixed(cfg->alpha) : 0;
     if (aq < 0) return QLDPC_ERR_INVALID_ARG;
@@ -235,18 +238,27 @@ int qldpc_server_create(const qldpc_graph *const *graphs, const float *const *pr
     }
     unsigned char *hd = static_cast<unsigned char *>(hb_dev);
 
-    // device memory: claim counters, status, priors
+    // device memory: claim counters, status, priors, and a private copy of each code's learned
+    // weights (QLDPC_LEARNED; a code without weights decodes plainly)
     size_t dev_bytes = 256;
-    size_t prior_off[kServerMaxCodes];
+    size_t prior_off[kServerMaxCodes], w_off[kServerMaxCodes], w_bytes[kServerMaxCodes];
     for (int c = 0; c < ncodes; ++c) {
         prior_off[c] = dev_bytes;
         dev_bytes += align16(size_t(s->n[c]) * sizeof(float));
+        const qldpc_graph *g = graphs[c];
+        w_bytes[c] = (learned && g->d_weights) ? size_t(g->learned_T) * g->dc_max * g->m * sizeof(float) : 0;
+        w_off[c] = dev_bytes;
+        dev_bytes += align16(w_bytes[c]);
     }
     e = cudaMalloc(&s->dev_block, dev_bytes);
     if (e == cudaSuccess) e = cudaMemset(s->dev_block, 0, 256);
-    for (int c = 0; c < ncodes && e == cudaSuccess; ++c)
+    for (int c = 0; c < ncodes && e == cudaSuccess; ++c) {
         e = cudaMemcpy(static_cast<char *>(s->dev_block) + prior_off[c], priors[c], size_t(s->n[c]) * sizeof(float),
                        cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && w_bytes[c])
+            e = cudaMemcpy(static_cast<char *>(s->dev_block) + w_off[c], graphs[c]->d_weights, w_bytes[c],
+                           cudaMemcpyDeviceToDevice);
+    }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         free_server(s);
@@ -261,7 +273,7 @@ int qldpc_server_create(const qldpc_graph *const *graphs, const float *const *pr
     sp.max_iter = cfg->max_iter;
     sp.alpha = cfg->alpha;
     sp.alpha_q = aq;
-    sp.flags = cfg->flags;
+    sp.flags = cfg->flags & QLDPC_NO_EARLY_STOP;
     sp.stop = reinterpret_cast<const uint32_t *>(hd + tail_off + 64 * kServerMaxCodes);
     sp.status = s->status;
     sp.idle_ns = uint64_t(cfg->idle_timeout_ns > 0 ? cfg->idle_timeout_ns : 500000000LL);
@@ -271,6 +283,8 @@ int qldpc_server_create(const qldpc_graph *const *graphs, const float *const *pr
         ServerCode &sc = sp.code[c];
         sc.g = graphs[c]->dg;
         sc.prior = reinterpret_cast<const float *>(static_cast<char *>(s->dev_block) + prior_off[c]);
+        sc.weights = w_bytes[c] ? reinterpret_cast<const float *>(static_cast<char *>(s->dev_block) + w_off[c]) : nullptr;
+        sc.learned_iters = w_bytes[c] ? graphs[c]->learned_T : 0;
         sc.ring = hd + ring_off[c];
         sc.tail = reinterpret_cast<const uint32_t *>(hd + tail_off + 64 * c);
         sc.head = s->head + c;

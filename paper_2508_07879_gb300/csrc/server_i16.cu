@@ -3,12 +3,12 @@
 
 namespace qldpc {
 
-const void *server_kernel_i16(const KernelChoice &kc) { return server_table<kern::I16>(kc); }
+const void *server_kernel_i16(const KernelChoice &kc) { return server_table<kern::I16, false>(kc); }
 
 cudaError_t launch_server_i16(const ServerParams &p, const KernelChoice &kc, int blocks, int threads,
                               size_t smem, cudaStream_t stream)
 {
-    return server_launch<kern::I16>(p, kc, blocks, threads, smem, stream);
+    return server_launch<kern::I16, false>(p, kc, blocks, threads, smem, stream);
 }
 
 }  // namespace qldpc

@@ -80,7 +80,9 @@ __device__ __forceinline__ int64_t claim_request(const ServerCode &sc, const Ser
     return -1;
 }
 
-template <class P, int DC, bool UNIFORM, int DV>
+// LEARNED (FP32): a code with weights decodes as the learned batch/latency kernels do (learned
+// iterations, then the plain fallback from the prior); a code without weights decodes plainly.
+template <class P, int DC, bool UNIFORM, int DV, bool LEARNED = false>
 __global__ void __launch_bounds__(kLatencyMaxThreads, 1) msa_server_kernel(const ServerParams sp)
 {
     using acc_t = typename P::acc_t;
@@ -122,6 +124,7 @@ __global__ void __launch_bounds__(kLatencyMaxThreads, 1) msa_server_kernel(const
     }
 
     const bool early = (sp.flags & kFlagNoEarlyStop) == 0;
+    const size_t wstride = size_t(sc.g.dc_max) * M;
     const uint64_t t_start = globaltimer();
     uint64_t t_idle_from = t_start;
     for (;;) {
@@ -131,40 +134,57 @@ __global__ void __launch_bounds__(kLatencyMaxThreads, 1) msa_server_kernel(const
         if (h < 0) break;
         unsigned char *slot = sc.ring + size_t(uint32_t(h) & uint32_t(sp.ring_capacity - 1)) * size_t(sc.slot_bytes);
         const unsigned char *syn = slot + sc.syn_off;
-#pragma unroll
-        for (int i = 0; i < kLatCnPerThread; ++i)
-            if (cdeg[i] >= 0) parity[tid + i * T] = (__ldcv(syn + tid + i * T) & 1u) * 3u;
-        __syncthreads();
         acc_t Q[kLatVnPerThread];
+        // Initialization (Alg. 1), also the restart of the plain fallback; ends with a barrier.
+        auto init_shot = [&]() {
 #pragma unroll
-        for (int i = 0; i < kLatVnPerThread; ++i) {
-            Q[i] = gam[i];
-            const bool d = P::neg(gam[i]);
+            for (int i = 0; i < kLatCnPerThread; ++i)
+                if (cdeg[i] >= 0) parity[tid + i * T] = (__ldcv(syn + tid + i * T) & 1u) * 3u;
+            __syncthreads();
 #pragma unroll
-            for (int k = 0; k < DV; ++k) {
-                if (k < vdeg[i]) {
-                    slots[slot_of(ev[i][k], uint32_t(M))] = P::to_msg(gam[i]);
-                    if (d) flip_check(parity, check_of(ev[i][k]));
+            for (int i = 0; i < kLatVnPerThread; ++i) {
+                Q[i] = gam[i];
+                const bool d = P::neg(gam[i]);
+#pragma unroll
+                for (int k = 0; k < DV; ++k) {
+                    if (k < vdeg[i]) {
+                        slots[slot_of(ev[i][k], uint32_t(M))] = P::to_msg(gam[i]);
+                        if (d) flip_check(parity, check_of(ev[i][k]));
+                    }
                 }
             }
-        }
-        __syncthreads();
+            __syncthreads();
+        };
+        init_shot();
 
         int k = 0, all = 0;
-        for (;; ++k) {
-            const bool last = k >= sp.max_iter;
+        bool learned = LEARNED && sc.weights != nullptr;
+        int end = learned ? sc.learned_iters : sp.max_iter;
+        for (;;) {
+            const bool last = k >= end;
+            const float *wk = nullptr;
+            if constexpr (LEARNED) wk = (learned && !last) ? sc.weights + size_t(k) * wstride : nullptr;
             int ok = 1;
 #pragma unroll
             for (int i = 0; i < kLatCnPerThread; ++i)
                 if (cdeg[i] >= 0)
-                    ok &= check_step<P, DC, UNIFORM>(tid + i * T, M, cdeg[i], parity[tid + i * T], !last, slots, p);
+                    ok &= check_step<P, DC, UNIFORM, LEARNED>(tid + i * T, M, cdeg[i], parity[tid + i * T], !last,
+                                                              slots, p, wk);
             all = __syncthreads_and(ok);
-            if (last || (early && all)) break;
+            if ((early || learned) && all) break;
+            if (last) {
+                if (!learned) break;
+                learned = false;                  // fallback: plain min-sum from the prior
+                end = k + sp.max_iter;
+                init_shot();
+                continue;
+            }
 #pragma unroll
             for (int i = 0; i < kLatVnPerThread; ++i)
                 if (vdeg[i] >= 0)
                     Q[i] = var_step_regs<P, DV>(vdeg[i], ev[i], uint32_t(M), gam[i], P::neg(Q[i]), slots, parity);
             __syncthreads();
+            ++k;
         }
 
         unsigned char *err = slot + sc.err_off;
@@ -183,24 +203,24 @@ __global__ void __launch_bounds__(kLatencyMaxThreads, 1) msa_server_kernel(const
 
 }  // namespace kern
 
-template <class P>
+template <class P, bool LEARNED>
 const void *server_table(const KernelChoice &kc)
 {
 #define QLDPC_K(DCV, UNI, DVV)                                                                  \
     if (kc.dc == DCV && kc.uniform == UNI && kc.dvb == DVV)                                     \
-        return reinterpret_cast<const void *>(&kern::msa_server_kernel<P, DCV, UNI, DVV>);
+        return reinterpret_cast<const void *>(&kern::msa_server_kernel<P, DCV, UNI, DVV, LEARNED>);
     QLDPC_VARIANTS(QLDPC_K)
 #undef QLDPC_K
     return nullptr;
 }
 
-template <class P>
+template <class P, bool LEARNED>
 cudaError_t server_launch(const ServerParams &sp, const KernelChoice &kc, int blocks, int threads, size_t smem,
                           cudaStream_t stream)
 {
 #define QLDPC_L(DCV, UNI, DVV)                                                                  \
     if (kc.dc == DCV && kc.uniform == UNI && kc.dvb == DVV) {                                   \
-        kern::msa_server_kernel<P, DCV, UNI, DVV><<<blocks, threads, smem, stream>>>(sp);       \
+        kern::msa_server_kernel<P, DCV, UNI, DVV, LEARNED><<<blocks, threads, smem, stream>>>(sp); \
         return cudaGetLastError();                                                              \
     }
     QLDPC_VARIANTS(QLDPC_L)

@@ -27,6 +27,7 @@ QLDPC_ERR_TIMEOUT = -5
 QLDPC_FP32 = 0
 QLDPC_INT16 = 1
 QLDPC_NO_EARLY_STOP = 1
+QLDPC_LEARNED = 2
 QLDPC_MAX_ROW_DEGREE = 32
 QLDPC_MAX_COL_DEGREE = 16
 QLDPC_MAX_CHECKS = 65535
@@ -80,6 +81,14 @@ _SIGNATURES = {
     "qldpc_server_replay": ([_p, _i32, _p, _p, _p, _p, _p, _p, _p, _p, _p, ctypes.c_int64], ctypes.c_int),
     "qldpc_server_status": ([_p, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
     "qldpc_server_destroy": ([_p], None),
+    "qldpc_graph_set_weights": ([_p, _p, _i32], ctypes.c_int),
+    "qldpc_nms_workspace_bytes": ([_p, _i32, _i32, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "qldpc_nms_forward": ([_p, _p, _p, _i32, _p, _p, _i32, _p, _p, _p, ctypes.c_size_t, _p], ctypes.c_int),
+    "qldpc_nms_backward": ([_p, _p, _p, _i32, _p, _i32, _p, _p, _p, ctypes.c_size_t, _p], ctypes.c_int),
+    "qldpc_adam_step": ([_p, _p, _p, _p, ctypes.c_int64, _i32, _f32, _f32, _f32, _f32, _p], ctypes.c_int),
+    "qldpc_sample_errors": ([_p, ctypes.c_uint64, ctypes.c_int64, _i32, ctypes.c_double, ctypes.c_double, _p, _p,
+                             _p], ctypes.c_int),
+    "qldpc_logical_failures": ([_p, _i32, _i32, _p, _p, _p, _i32, _p, _p], ctypes.c_int),
 }
 for _name, (_args, _res) in _SIGNATURES.items():
     _fn = getattr(_lib, _name)
@@ -105,6 +114,13 @@ qldpc_server_poll = _lib.qldpc_server_poll
 qldpc_server_replay = _lib.qldpc_server_replay
 qldpc_server_status = _lib.qldpc_server_status
 qldpc_server_destroy = _lib.qldpc_server_destroy
+qldpc_graph_set_weights = _lib.qldpc_graph_set_weights
+qldpc_nms_workspace_bytes = _lib.qldpc_nms_workspace_bytes
+qldpc_nms_forward = _lib.qldpc_nms_forward
+qldpc_nms_backward = _lib.qldpc_nms_backward
+qldpc_adam_step = _lib.qldpc_adam_step
+qldpc_sample_errors = _lib.qldpc_sample_errors
+qldpc_logical_failures = _lib.qldpc_logical_failures
 QLDPC_NOALLOC_SCRATCH_BYTES = 4 * 1024 * 1024
 
 
@@ -158,6 +174,7 @@ class Graph:
                                  ctypes.byref(h)), "qldpc_graph_create")
         self._h = h
         self.m, self.n, self.nnz = int(m), int(n), int(rp[-1])
+        self.learned_iters = 0
 
     @classmethod
     def from_csr(cls, csr) -> "Graph":
@@ -188,6 +205,34 @@ class Graph:
     def reserve(self, max_batch: int) -> None:
         check(qldpc_graph_reserve(self._h, int(max_batch)), "qldpc_graph_reserve")
 
+    def set_weights(self, weights) -> None:
+        """Learned weights float32 [T, nnz] (CSR edge order; numpy, or a torch tensor on the host
+        or this device) for decodes with learned=True; None clears them."""
+        if weights is None:
+            check(qldpc_graph_set_weights(self._h, None, 0), "qldpc_graph_set_weights")
+            self.learned_iters = 0
+            return
+        try:
+            import torch
+            is_tensor = isinstance(weights, torch.Tensor)
+        except ImportError:
+            is_tensor = False
+        if is_tensor:
+            w = weights.detach()
+            if w.dtype != torch.float32 or w.dim() != 2 or w.shape[1] != self.nnz:
+                raise ValueError(f"weights must be float32 [T, {self.nnz}]")
+            w = w.contiguous()
+            T = int(w.shape[0])
+            check(qldpc_graph_set_weights(self._h, ctypes.c_void_p(w.data_ptr()) if T else None, T),
+                  "qldpc_graph_set_weights")
+        else:
+            w = np.ascontiguousarray(weights, dtype=np.float32)
+            if w.ndim != 2 or w.shape[1] != self.nnz:
+                raise ValueError(f"weights must be float32 [T, {self.nnz}]")
+            T = int(w.shape[0])
+            check(qldpc_graph_set_weights(self._h, _np_ptr(w) if T else None, T), "qldpc_graph_set_weights")
+        self.learned_iters = T
+
     def close(self) -> None:
         if self._h:
             qldpc_graph_destroy(self._h)
@@ -200,14 +245,19 @@ class Graph:
             pass
 
 
+def _flags(early_stop: bool, learned: bool) -> int:
+    return (0 if early_stop else QLDPC_NO_EARLY_STOP) | (QLDPC_LEARNED if learned else 0)
+
+
 def decode(graph: Graph, syndromes, prior, max_iter: int, alpha: float = 0.75,
            precision: str = "fp32", early_stop: bool = True, want_post: bool = False,
-           out=None, stream=None):
+           out=None, stream=None, learned: bool = False):
     """Decode syndromes (CUDA uint8 [B, m]) with prior LLRs (CUDA float32 [n]).
 
     Returns (err uint8 [B, n], iters int32 [B], ok uint8 [B], post float32 [B, n] or None), all
     CUDA tensors, enqueued on ``stream`` (default: torch's current stream).  ``out`` may supply
-    the four output tensors to avoid allocation.
+    the four output tensors to avoid allocation.  ``learned``: the graph's learned weights first,
+    then plain min-sum for up to ``max_iter`` iterations on shots not yet decoded.
     """
     import torch
     batch = int(syndromes.shape[0]) if syndromes.dim() == 2 else 0
@@ -219,7 +269,7 @@ def decode(graph: Graph, syndromes, prior, max_iter: int, alpha: float = 0.75,
         post = torch.empty((batch, graph.n), dtype=torch.float32, device=dev) if want_post else None
     else:
         err, iters, ok, post = out
-    flags = 0 if early_stop else QLDPC_NO_EARLY_STOP
+    flags = _flags(early_stop, learned)
     check(qldpc_decode_ex(graph.handle,
                           _dev_ptr(syndromes, torch.uint8, (batch, graph.m), "syndromes"), batch,
                           _dev_ptr(prior, torch.float32, (graph.n,), "prior"), int(max_iter),
@@ -235,7 +285,7 @@ def decode(graph: Graph, syndromes, prior, max_iter: int, alpha: float = 0.75,
 
 def decode_pair(g_z: Graph, g_x: Graph, s_x, s_z, prior_x, prior_z, max_iter: int,
                 alpha: float = 0.75, precision: str = "fp32", early_stop: bool = True,
-                want_post: bool = False, stream=None):
+                want_post: bool = False, stream=None, learned: bool = False):
     """X and Z halves of a CSS syndrome round in one launch; returns two (err, iters, ok, post)."""
     import torch
     batch = int(s_x.shape[0])
@@ -247,7 +297,7 @@ def decode_pair(g_z: Graph, g_x: Graph, s_x, s_z, prior_x, prior_z, max_iter: in
                      torch.empty(batch, dtype=torch.uint8, device=dev),
                      torch.empty((batch, g.n), dtype=torch.float32, device=dev) if want_post else None))
     (ex, ix, ox, px), (ez, iz, oz, pz) = outs
-    flags = 0 if early_stop else QLDPC_NO_EARLY_STOP
+    flags = _flags(early_stop, learned)
     check(qldpc_decode_pair(g_z.handle, g_x.handle,
                             _dev_ptr(s_x, torch.uint8, (batch, g_z.m), "s_x"),
                             _dev_ptr(s_z, torch.uint8, (batch, g_x.m), "s_z"), batch,
@@ -304,7 +354,8 @@ class Server:
 
     def __init__(self, graphs, priors, max_iter: int, alpha: float = 0.75, precision: str = "fp32",
                  early_stop: bool = True, ring_capacity: int = 256, blocks=None,
-                 idle_timeout_s: float = 0.5, max_runtime_s: float = 600.0, threads_per_block: int = 0):
+                 idle_timeout_s: float = 0.5, max_runtime_s: float = 600.0, threads_per_block: int = 0,
+                 learned: bool = False):
         self._h = None
         self.graphs = list(graphs)
         self._priors = [np.ascontiguousarray(p, dtype=np.float32) for p in priors]
@@ -312,7 +363,7 @@ class Server:
         cfg.precision = PRECISIONS[precision]
         cfg.max_iter = int(max_iter)
         cfg.alpha = float(alpha)
-        cfg.flags = 0 if early_stop else QLDPC_NO_EARLY_STOP
+        cfg.flags = _flags(early_stop, learned)
         cfg.ring_capacity = int(ring_capacity)
         cfg.threads_per_block = int(threads_per_block)
         for i, b in enumerate(blocks or []):
@@ -400,3 +451,91 @@ class Server:
 
     def __exit__(self, *exc):
         self.close()
+
+
+# ------------------------------------------------------------------------------------------------
+# Learned decoder training and evaluation helpers (device tensors in, device tensors out)
+# ------------------------------------------------------------------------------------------------
+def nms_workspace_bytes(graph: Graph, batch: int, T: int) -> int:
+    out = ctypes.c_size_t()
+    check(qldpc_nms_workspace_bytes(graph.handle, int(batch), int(T), ctypes.byref(out)), "qldpc_nms_workspace_bytes")
+    return out.value
+
+
+def nms_forward(graph: Graph, syndromes, targets, prior, weights, workspace, want_post: bool = False, stream=None):
+    """Training forward (qldpc_nms_forward).  workspace: CUDA uint8 tensor of at least
+    nms_workspace_bytes(graph, B, T) bytes.  Returns (loss float32 [B], post float32 [B, n] or None)."""
+    import torch
+    batch = int(syndromes.shape[0])
+    T = int(weights.shape[0])
+    loss = torch.empty(batch, dtype=torch.float32, device=syndromes.device)
+    post = torch.empty((batch, graph.n), dtype=torch.float32, device=syndromes.device) if want_post else None
+    check(qldpc_nms_forward(graph.handle, _dev_ptr(syndromes, torch.uint8, (batch, graph.m), "syndromes"),
+                            _dev_ptr(targets, torch.uint8, (batch, graph.n), "targets"), batch,
+                            _dev_ptr(prior, torch.float32, (graph.n,), "prior"),
+                            _dev_ptr(weights, torch.float32, (T, graph.nnz), "weights"), T,
+                            _dev_ptr(loss, torch.float32, (batch,), "loss"),
+                            _dev_ptr(post, torch.float32, (batch, graph.n), "post") if post is not None else None,
+                            ctypes.c_void_p(workspace.data_ptr()), int(workspace.numel() * workspace.element_size()),
+                            _stream_handle(stream)), "qldpc_nms_forward")
+    return loss, post
+
+
+def nms_backward(graph: Graph, syndromes, targets, prior, T: int, grad_loss, workspace, stream=None):
+    """Training backward (qldpc_nms_backward) after nms_forward on the same workspace.
+    Returns the weight gradient float32 [T, nnz]."""
+    import torch
+    batch = int(syndromes.shape[0])
+    grad = torch.empty((int(T), graph.nnz), dtype=torch.float32, device=syndromes.device)
+    check(qldpc_nms_backward(graph.handle, _dev_ptr(syndromes, torch.uint8, (batch, graph.m), "syndromes"),
+                             _dev_ptr(targets, torch.uint8, (batch, graph.n), "targets"), batch,
+                             _dev_ptr(prior, torch.float32, (graph.n,), "prior"), int(T),
+                             _dev_ptr(grad_loss, torch.float32, (batch,), "grad_loss"),
+                             _dev_ptr(grad, torch.float32, (int(T), graph.nnz), "grad"),
+                             ctypes.c_void_p(workspace.data_ptr()), int(workspace.numel() * workspace.element_size()),
+                             _stream_handle(stream)), "qldpc_nms_backward")
+    return grad
+
+
+def adam_step(params, grads, exp_avg, exp_avg_sq, step: int, lr: float = 1e-3, betas=(0.9, 0.999),
+              eps: float = 1e-8, stream=None) -> None:
+    """In-place Adam update of CUDA float32 tensors of one shape (qldpc_adam_step)."""
+    import torch
+    shape = tuple(params.shape)
+    count = int(params.numel())
+    check(qldpc_adam_step(_dev_ptr(params, torch.float32, shape, "params"),
+                          _dev_ptr(grads, torch.float32, shape, "grads"),
+                          _dev_ptr(exp_avg, torch.float32, shape, "exp_avg"),
+                          _dev_ptr(exp_avg_sq, torch.float32, shape, "exp_avg_sq"), count, int(step), float(lr),
+                          float(betas[0]), float(betas[1]), float(eps), _stream_handle(stream)), "qldpc_adam_step")
+
+
+def sample_errors(graph: Graph, seed: int, first_shot: int, batch: int, p_lo: float, p_hi=None, device=None,
+                  stream=None):
+    """Device-side seeded errors and syndromes (qldpc_sample_errors).  Returns (err [B, n], syn [B, m])."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else device
+    p_hi = p_lo if p_hi is None else p_hi
+    err = torch.empty((int(batch), graph.n), dtype=torch.uint8, device=dev)
+    syn = torch.empty((int(batch), graph.m), dtype=torch.uint8, device=dev)
+    check(qldpc_sample_errors(graph.handle, ctypes.c_uint64(int(seed) & 0xFFFFFFFFFFFFFFFF), int(first_shot),
+                              int(batch), float(p_lo), float(p_hi),
+                              _dev_ptr(err, torch.uint8, (int(batch), graph.n), "err") if batch else None,
+                              _dev_ptr(syn, torch.uint8, (int(batch), graph.m), "syn") if batch else None,
+                              _stream_handle(stream)), "qldpc_sample_errors")
+    return err, syn
+
+
+def logical_failures(logicals, errors, decisions, ok, stream=None):
+    """fail uint8 [B] (qldpc_logical_failures); logicals: CUDA uint8 [k, n]."""
+    import torch
+    k, n = int(logicals.shape[0]), int(logicals.shape[1])
+    batch = int(errors.shape[0])
+    fail = torch.empty(batch, dtype=torch.uint8, device=errors.device)
+    check(qldpc_logical_failures(_dev_ptr(logicals, torch.uint8, (k, n), "logicals"), k, n,
+                                 _dev_ptr(errors, torch.uint8, (batch, n), "errors"),
+                                 _dev_ptr(decisions, torch.uint8, (batch, n), "decisions"),
+                                 _dev_ptr(ok, torch.uint8, (batch,), "ok"), batch,
+                                 _dev_ptr(fail, torch.uint8, (batch,), "fail"), _stream_handle(stream)),
+          "qldpc_logical_failures")
+    return fail

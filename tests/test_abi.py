@@ -120,6 +120,26 @@ def test_decode_rejects_null_graph(q):
     q.qldpc_graph_destroy(None)
 
 
+def test_learned_entry_points_validate_on_the_host(q):
+    inv = q.QLDPC_ERR_INVALID_ARG
+    assert q.qldpc_graph_set_weights(None, None, 0) == inv
+    size = ctypes.c_size_t()
+    assert q.qldpc_nms_workspace_bytes(None, 16, 4, ctypes.byref(size)) == inv
+    assert q.qldpc_nms_forward(None, None, None, 16, None, None, 4, None, None, None, 0, None) == inv
+    assert q.qldpc_nms_backward(None, None, None, 16, None, 4, None, None, None, 0, None) == inv
+    assert q.qldpc_adam_step(None, None, None, None, -1, 1, 1e-3, 0.9, 0.999, 1e-8, None) == inv
+    assert q.qldpc_adam_step(None, None, None, None, 10, 0, 1e-3, 0.9, 0.999, 1e-8, None) == inv
+    assert q.qldpc_adam_step(None, None, None, None, 10, 1, 1e-3, 1.0, 0.999, 1e-8, None) == inv
+    assert q.qldpc_adam_step(None, None, None, None, 0, 1, 1e-3, 0.9, 0.999, 1e-8, None) == q.QLDPC_OK
+    assert q.qldpc_sample_errors(None, 1, 0, 4, 0.01, 0.02, None, None, None) == inv
+    assert q.qldpc_logical_failures(None, 0, 10, None, None, None, 4, None, None) == inv
+    assert q.qldpc_logical_failures(None, 2, 10, None, None, None, 0, None, None) == q.QLDPC_OK
+    assert q.qldpc_logical_failures(None, 2, 10, None, None, None, 4, None, None) == inv
+    # (k + 1) words of ceil(n/32) must fit in 48 KB of shared memory
+    assert q.qldpc_logical_failures(ctypes.c_void_p(16), 400, 1000, ctypes.c_void_p(16), ctypes.c_void_p(16),
+                                    ctypes.c_void_p(16), 4, ctypes.c_void_p(16), None) == q.QLDPC_ERR_UNSUPPORTED
+
+
 def test_product_and_oracle_are_independent():
     """The decoder package never touches the oracle, and the oracle imports nothing of the package."""
     pkg = os.path.join(ROOT, "paper_2508_07879_gb300")

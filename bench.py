@@ -13,6 +13,10 @@ Printed as one JSON line on rank 0:
                the launch path (qldpc_decode_host) and the persistent server (qldpc_server_*)
   serving      the persistent server under a 40/40/20 mix of the N=400, 1054 and 288 codes with
                Poisson arrivals 20 us apart: latency percentiles and the saturated request rate
+  learned      the learned (neural) min-sum on the same code: training time and kernel times on
+               2e6 device-sampled shots (T = 20, batch 4096, Adam lr 1e-3, p uniform in
+               [0.02, 0.06]), then logical error rates of learned and plain decoding on 1e6 fresh
+               shots
   roofline     the decoder kernel against the SM integer/FP32 issue roof ("alu")
   cpu_baseline the CPU oracle on a bounded sample of the same workload, all host cores
   clocks       SM clock and throttle reasons sampled during the timed region
@@ -49,6 +53,13 @@ SERVE_REQUESTS = 100000
 SERVE_GAP_NS = 20000         # mean Poisson inter-arrival
 SERVE_MIX = (0.4, 0.4, 0.2)  # N=400 HGP, N=1054 LP, N=288 BB (H_Z, i.i.d. X noise at p = 0.03)
 LAT_SERVER_GAP_NS = 50000    # isolated single-shot requests through the server
+LEARN_T = 20                 # unrolled learned iterations
+LEARN_SHOTS = 2_000_000      # training shots
+LEARN_BATCH = 4096
+LEARN_LR = 1e-3
+LEARN_P = (0.02, 0.06)       # per-shot rate range, training and evaluation
+LEARN_EVAL = 1_000_000       # fresh evaluation shots
+LEARN_SEEDS = (7, 99)        # training, evaluation
 OPS_PER_EDGE_ITER = 10          # algorithmic ALU operations per edge per iteration
 ALU_LANES_PER_SM = 128          # FP32/INT32 lanes per SM, one operation per lane per clock
 
@@ -74,6 +85,9 @@ def parse():
     ap.add_argument("--latency-shots", type=int, default=LAT_SHOTS)
     ap.add_argument("--serve-requests", type=int, default=SERVE_REQUESTS)
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--learned-train-shots", type=int, default=LEARN_SHOTS)
+    ap.add_argument("--learned-eval-shots", type=int, default=LEARN_EVAL)
     return ap.parse_args()
 
 
@@ -322,6 +336,9 @@ def run_ours(args, rank, world, local):
     serving = None
     if not args.no_serving and rank == 0:
         serving = measure_serving(qldpc, args)
+    learned_res = None
+    if not args.no_learned and rank == 0:
+        learned_res = measure_learned(qldpc, args)
     cpu = None
     if not args.no_cpu_baseline and rank == 0 and world == 1:
         threads = os.cpu_count() or 1
@@ -343,6 +360,7 @@ def run_ours(args, rank, world, local):
             "e2e": e2e,
             "latency": latency,
             "serving": serving,
+            "learned": learned_res,
             "gpu_launches": launches,
             "clocks": clocks,
             "mean_iters": sum(iters_per_batch) / (len(iters_per_batch) * B),
@@ -469,6 +487,69 @@ def measure_serving(qldpc, args):
                      "p999_us": float(np.percentile(x, 99.9)), "per_code": per,
                      "saturated_shots_per_s": n / dt}
     return out
+
+
+def measure_learned(qldpc, args):
+    """Config 4: learned normalized min-sum on LP-1054 (H_Z), trained and evaluated on the device."""
+    import torch
+    from paper_2508_07879_gb300 import learned
+    from paper_2508_07879_gb300 import workloads as w
+    code = w.lp_code(1054)
+    h = code.hz_csr
+    prior = np.full(h.n, w.prior_llr(0.04), dtype=np.float32)   # one prior at the centre of the range
+    g = qldpc.Graph.from_csr(h)
+    model = learned.NeuralMinSum(h, prior, T=LEARN_T, max_batch=LEARN_BATCH, graph=g)
+    # kernel times of one training step, events on the launching (current) stream
+    err, syn = qldpc.sample_errors(g, LEARN_SEEDS[0] + 1000, 0, LEARN_BATCH, *LEARN_P)
+    gl = torch.full((LEARN_BATCH,), 1.0 / LEARN_BATCH, device=syn.device)
+    w0 = model.weights.detach()
+    for _ in range(3):
+        qldpc.nms_forward(g, syn, err, model.prior, w0, model.workspace)
+        qldpc.nms_backward(g, syn, err, model.prior, LEARN_T, gl, model.workspace)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    tf = tb = 0.0
+    reps = 10
+    for _ in range(reps):
+        ev[0].record()
+        qldpc.nms_forward(g, syn, err, model.prior, w0, model.workspace)
+        ev[1].record()
+        qldpc.nms_backward(g, syn, err, model.prior, LEARN_T, gl, model.workspace)
+        ev[2].record()
+        torch.cuda.synchronize()
+        tf += ev[0].elapsed_time(ev[1])
+        tb += ev[1].elapsed_time(ev[2])
+    tf, tb = tf / reps, tb / reps
+    edge_iters = LEARN_BATCH * LEARN_T * h.nnz
+    # training: sampling, forward, backward and Adam per step, wall clock
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hist = model.train(shots=args.learned_train_shots, batch=LEARN_BATCH, p_lo=LEARN_P[0], p_hi=LEARN_P[1],
+                       seed=LEARN_SEEDS[0], lr=LEARN_LR, record_every=50)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    model.publish()
+    decoders = {"plain_20": (20, False), "plain_50": (50, False), "learned_20": (0, True),
+                "learned_20_fallback_30": (30, True), "learned_20_fallback_50": (50, True)}
+    t0 = time.perf_counter()
+    res = learned.evaluate(g, prior, learned.z_logicals(code), decoders, shots=args.learned_eval_shots,
+                           p_lo=LEARN_P[0], p_hi=LEARN_P[1], seed=LEARN_SEEDS[1])
+    eval_s = time.perf_counter() - t0
+    steps = args.learned_train_shots // LEARN_BATCH
+    return {
+        "workload": "LP-1054 H_Z, iid X noise, p uniform in [0.02, 0.06) per shot, prior ln(0.96/0.04)",
+        "T": LEARN_T, "train_shots": steps * LEARN_BATCH, "batch": LEARN_BATCH, "lr": LEARN_LR,
+        "loss": "mean over iterations and variables of BCE(sigma(-Q), e)",
+        "train_s": train_s, "train_shots_per_s": steps * LEARN_BATCH / train_s,
+        "loss_first": float(hist[0]) if len(hist) else None, "loss_last": float(hist[-1]) if len(hist) else None,
+        "step_kernel_ms": {"forward": tf, "backward_and_reduce": tb},
+        "train_edge_iters_per_s": {"forward": edge_iters / (tf / 1e3), "backward": edge_iters / (tb / 1e3)},
+        "eval_shots": args.learned_eval_shots, "eval_s": eval_s,
+        "ler": {k: v["ler"] for k, v in res.items()},
+        "mean_iters": {k: v["mean_iters"] for k, v in res.items()},
+        "decoders": "plain_K: alpha 0.75, max K iterations; learned_20: 20 learned iterations alone; "
+                    "learned_20_fallback_K: then plain min-sum from the prior for up to K iterations",
+    }
 
 
 def main():

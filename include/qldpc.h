@@ -273,7 +273,8 @@ QLDPC_API void qldpc_server_destroy(qldpc_server *s);
  * Learned decoding runs iterations 1..T with the weights and the stop test; a shot whose syndrome
  * is still not met restarts from its prior with plain min-sum (alpha, up to max_iter iterations):
  * iters = T + plain iterations for such shots.  Training minimizes the BCE of the soft outputs,
- *   loss_b = 1/(T n) sum_{t=1..T} sum_v BCE(sigma(-Q^(t)_v), y_v)   (y = the true error bits),
+ *   loss_b = sum_{t=1..T} lambda_t / n sum_v BCE(sigma(-Q^(t)_v), y_v)   (y = the true error bits),
+ * with per-iteration loss weights lambda_t (default 1/T: the mean over iterations and variables),
  * with a forward kernel that records a compressed check state per iteration and a backward
  * kernel that recomputes every message from it.  FP32 throughout.
  * =============================================================================================== */
@@ -286,13 +287,14 @@ QLDPC_API int qldpc_graph_set_weights(qldpc_graph *g, const float *weights, int3
 
 /* Device workspace (bytes) that qldpc_nms_forward / qldpc_nms_backward need for `batch` shots and
  * T iterations: the slot-layout weights, 16 bytes of recorded state per check, iteration and shot,
- * and one gradient slice per backward block.  INVALID_ARG: null pointers, batch < 1, T < 1. */
+ * and the slot-layout gradient.  INVALID_ARG: null pointers, batch < 1, T < 1. */
 QLDPC_API int qldpc_nms_workspace_bytes(const qldpc_graph *g, int32_t batch, int32_t T, size_t *bytes);
 
 /*
  * Training forward: T learned iterations (no stop test) on every shot.
  *   syndromes  device uint8[batch][m];  targets device uint8[batch][n], the true error bits
  *   prior      device float[n];         weights device float[T][nnz] (CSR edge order)
+ *   loss_weights  device float[T] (lambda_t), or NULL for 1/T each
  *   out_loss   device float[batch], loss_b as above
  *   out_post   device float[batch][n], Q^(T) (the a-posteriori LLR of iteration T), or NULL
  *   workspace  device memory of at least qldpc_nms_workspace_bytes(g, batch, T), 256-byte aligned;
@@ -303,20 +305,22 @@ QLDPC_API int qldpc_nms_workspace_bytes(const qldpc_graph *g, int32_t batch, int
  */
 QLDPC_API int qldpc_nms_forward(const qldpc_graph *g, const uint8_t *syndromes, const uint8_t *targets,
                                 int32_t batch, const float *prior, const float *weights, int32_t T,
-                                float *out_loss, float *out_post, void *workspace, size_t workspace_bytes,
-                                void *stream);
+                                const float *loss_weights, float *out_loss, float *out_post, void *workspace,
+                                size_t workspace_bytes, void *stream);
 
 /*
  * Training backward: out_grad (device float[T][nnz], overwritten) = sum_b grad_loss[b] d loss_b / d w,
  * with the subgradients d|q|/dq = sign(q) (+1 at 0), d sign/dq = 0, and the minimum's gradient going
  * to the lowest position attaining it.  The arguments must be those of the preceding
- * qldpc_nms_forward on the same workspace (same syndromes, targets, prior, batch and T; the weights
- * are read back from the workspace).  grad_loss is device float[batch].  The result does not
- * depend on scheduling (each block sums its own shots; the blocks are added in a fixed order).
+ * qldpc_nms_forward on the same workspace (same syndromes, targets, prior, batch, T and loss
+ * weights; the weights are read back from the workspace).  grad_loss is device float[batch].  The
+ * sum over shots is taken with FP32 global reductions, so its rounding order (the last bits of the
+ * result) follows the schedule and may differ between calls.
  */
 QLDPC_API int qldpc_nms_backward(const qldpc_graph *g, const uint8_t *syndromes, const uint8_t *targets,
-                                 int32_t batch, const float *prior, int32_t T, const float *grad_loss,
-                                 float *out_grad, void *workspace, size_t workspace_bytes, void *stream);
+                                 int32_t batch, const float *prior, int32_t T, const float *loss_weights,
+                                 const float *grad_loss, float *out_grad, void *workspace,
+                                 size_t workspace_bytes, void *stream);
 
 /* One Adam step on device float arrays of `count` elements (Kingma and Ba, ICLR 2015), in the
  * arithmetic of PyTorch's single-tensor Adam: m += (1-beta1)(g-m); v = beta2 v + (1-beta2) g^2;

@@ -62,7 +62,7 @@ def _load():
             lib.oracle_alpha_q.restype = ctypes.c_int
             for name in ("oracle_nms_train_f64", "oracle_nms_train_f32"):
                 f = getattr(lib, name)
-                f.argtypes = [p, p, i32, i32, p, p, i32, p, p, i32, p, p, p, p]
+                f.argtypes = [p, p, i32, i32, p, p, i32, p, p, i32, p, p, p, p, p]
                 f.restype = ctypes.c_int
             lib.oracle_nms_decode_f32.argtypes = [p, p, i32, i32, p, i32, p, p, i32, i32, ctypes.c_float,
                                                   p, p, p, p, p]
@@ -138,12 +138,13 @@ def msa(row_ptr, col_idx, m: int, n: int, syndromes, prior, max_iter: int, alpha
 # Neural normalized min-sum (learned weights w[t][e], CSR edge order)
 # ------------------------------------------------------------------------------------------------
 def nms_train(row_ptr, col_idx, m, n, syndromes, targets, prior, weights, grad_loss=None,
-              precision: str = "f64", post: bool = False, threads: int = 1):
+              precision: str = "f64", post: bool = False, threads: int = 1, loss_weights=None):
     """Training pass of the neural min-sum decoder: T iterations, no stop test.
 
     weights: [T, E] (E = nnz, CSR edge order).  precision "f64" or "f32" is the type the forward
-    runs in; losses and gradients are always float64.  Returns a dict with
-      loss [B]          1/(T n) sum_t sum_v BCE(sigma(-Q^t_v), y_v)
+    runs in; losses and gradients are always float64.  loss_weights: [T] per-iteration weights
+    lambda_t (None: 1/T each).  Returns a dict with
+      loss [B]          sum_t lambda_t / n sum_v BCE(sigma(-Q^t_v), y_v)
       post [B, T, n]    Q^t of every iteration (only with post=True)
       grad [T, E]       sum_b grad_loss[b] d loss_b / d w (only when grad_loss is given)
     """
@@ -165,6 +166,7 @@ def nms_train(row_ptr, col_idx, m, n, syndromes, targets, prior, weights, grad_l
     loss = np.zeros(B, dtype=np.float64)
     posts = np.zeros((B, T, n), dtype=real) if post else None
     g = None if grad_loss is None else np.ascontiguousarray(grad_loss, dtype=np.float64).reshape(B)
+    lw = None if loss_weights is None else np.ascontiguousarray(loss_weights, dtype=np.float64).reshape(T)
     threads = max(1, min(int(threads), max(B, 1)))
     bounds = np.linspace(0, B, threads + 1).astype(int)
     parts = [np.zeros_like(w, dtype=np.float64) for _ in range(threads)] if g is not None else None
@@ -174,7 +176,7 @@ def nms_train(row_ptr, col_idx, m, n, syndromes, targets, prior, weights, grad_l
         if hi <= lo:
             return 0
         return fn(_ptr(rp), _ptr(ci), m, n, _ptr(syn[lo:hi]), _ptr(y[lo:hi]), hi - lo, _ptr(pr), _ptr(w), T,
-                  _ptr(g[lo:hi]) if g is not None else None, _ptr(loss[lo:hi]),
+                  _ptr(lw), _ptr(g[lo:hi]) if g is not None else None, _ptr(loss[lo:hi]),
                   _ptr(posts[lo:hi]) if posts is not None else None, _ptr(parts[i]) if parts else None)
 
     if threads == 1:

@@ -310,7 +310,8 @@ int oracle_msa_i16(const int32_t *row_ptr, const int32_t *col_idx, int32_t m, in
  * S_c(n)\m in ascending check order, as in the plain decoder above).
  *
  * Training loss of one shot with true error y (the sampled e), over T iterations, no stop test:
- *   loss = 1/(T N) sum_{t=1..T} sum_n BCE(sigma(-Q^(t)_n), y_n),  BCE(p, y) = -y log p - (1-y) log(1-p)
+ *   loss = sum_{t=1..T} lambda_t / N sum_n BCE(sigma(-Q^(t)_n), y_n),  BCE(p, y) = -y log p - (1-y) log(1-p)
+ * with per-iteration loss weights lambda_t (default 1/T: the mean over iterations and variables)
  * evaluated as softplus(Q) for y = 1 and softplus(-Q) for y = 0 (softplus(x) = log(1 + e^x)):
  * Q = log P(e_n = 0)/P(e_n = 1), so P(e_n = 1) = sigma(-Q).
  *
@@ -350,8 +351,8 @@ static void nms_check_##SUFFIX(const tanner *t, int32_t c, const uint8_t *s, con
 int oracle_nms_train_##SUFFIX(const int32_t *row_ptr, const int32_t *col_idx, int32_t m, int32_t n,   \
                               const uint8_t *syn, const uint8_t *target, int32_t batch,               \
                               const REAL *prior, const REAL *weights, int32_t T,                      \
-                              const double *grad_loss, double *out_loss, REAL *out_post,              \
-                              double *out_grad)                                                       \
+                              const double *loss_w, const double *grad_loss, double *out_loss,        \
+                              REAL *out_post, double *out_grad)                                       \
 {                                                                                                     \
     if (batch < 0 || T < 1 || !syn || !target || !prior || !weights || !out_loss) return ORACLE_BAD_ARG; \
     if (out_grad && !grad_loss) return ORACLE_BAD_ARG;                                                \
@@ -377,6 +378,8 @@ int oracle_nms_train_##SUFFIX(const int32_t *row_ptr, const int32_t *col_idx, in
         for (int32_t i = 0; i < t.e; ++i) qs[i] = prior[t.col[i]];                                    \
         double loss = 0.0;                                                                            \
         for (int32_t k = 0; k < T; ++k) {                                                             \
+            const double lw = loss_w ? loss_w[k] : 1.0 / T;                                           \
+            double it_loss = 0.0;                                                                     \
             const REAL *q = qs + (size_t)k * E;                                                       \
             REAL *r = rs + (size_t)k * E;                                                             \
             for (int32_t c = 0; c < m; ++c)                                                           \
@@ -386,7 +389,7 @@ int oracle_nms_train_##SUFFIX(const int32_t *row_ptr, const int32_t *col_idx, in
                 REAL Q = prior[v];                                                                    \
                 for (int32_t a = t.vptr[v]; a < t.vptr[v + 1]; ++a) Q = Q + r[t.vedge[a]];            \
                 Qs[(size_t)k * n + v] = Q;                                                            \
-                loss += y[v] ? softplus_d((double)Q) : softplus_d(-(double)Q);                        \
+                it_loss += y[v] ? softplus_d((double)Q) : softplus_d(-(double)Q);                     \
                 if (out_post) out_post[((size_t)b * T + k) * n + v] = Q;                              \
                 if (k + 1 < T) {                                                                      \
                     REAL *qn = qs + (size_t)(k + 1) * E;                                              \
@@ -398,15 +401,17 @@ int oracle_nms_train_##SUFFIX(const int32_t *row_ptr, const int32_t *col_idx, in
                     }                                                                                 \
                 }                                                                                     \
             }                                                                                         \
+            loss += lw * (it_loss / n);                                                               \
         }                                                                                             \
-        out_loss[b] = loss / ((double)T * n);                                                         \
+        out_loss[b] = loss;                                                                           \
         if (!out_grad) continue;                                                                      \
         /* reverse sweep, iteration T down to 1 */                                                    \
-        const double scale = grad_loss[b] / ((double)T * n);                                          \
+        const double scale = grad_loss[b] / n;                                                        \
         for (int32_t i = 0; i < t.e; ++i) gq[i] = 0.0;    /* d/d q^(k+1): feeds iteration k+2 */      \
         for (int32_t k = T - 1; k >= 0; --k) {                                                        \
+            const double lw = loss_w ? loss_w[k] : 1.0 / T;                                           \
             for (int32_t v = 0; v < n; ++v)                                                           \
-                gQ[v] = scale * ((double)y[v] - sigmoid_d(-(double)Qs[(size_t)k * n + v]));           \
+                gQ[v] = scale * lw * ((double)y[v] - sigmoid_d(-(double)Qs[(size_t)k * n + v]));      \
             /* r^(k+1)_{m,n} enters Q^(k+1)_n and every q^(k+1)_{i,n} with i != m */                  \
             for (int32_t v = 0; v < n; ++v)                                                           \
                 for (int32_t a = t.vptr[v]; a < t.vptr[v + 1]; ++a) {                                 \

@@ -184,7 +184,8 @@ struct TrainParams {
     float *loss;                // [batch]
     float *post;                // [batch * n] a-posteriori LLR of iteration T, or nullptr
     const float *grad_loss;     // [batch]
-    float *partial;             // [grid][T][dc_max * m] per-block gradient sums
+    const float *loss_w;        // [T] per-iteration loss weights lambda_t, or nullptr for 1/T each
+    float *partial;             // [T][dc_max * m] slot-layout weight gradient, zeroed before the backward
     int32_t T, batch;
 };
 
@@ -202,8 +203,8 @@ cudaError_t launch_nms_backward(const TrainParams &p, const TrainChoice &tc, int
                                 cudaStream_t stream);
 cudaError_t launch_permute_weights(const float *w_csr, const uint32_t *eslot, int32_t T, int32_t nnz, int32_t S,
                                    float *w_slot, cudaStream_t stream);
-cudaError_t launch_reduce_grad(const float *partial, int32_t blocks, const int32_t *slot_edge, int32_t T, int32_t S,
-                               int32_t nnz, float *grad, cudaStream_t stream);
+cudaError_t launch_gather_grad(const float *grad_slot, const uint32_t *eslot, int32_t T, int32_t S, int32_t nnz,
+                               float *grad, cudaStream_t stream);
 cudaError_t launch_adam(float *param, const float *grad, float *m1, float *m2, int64_t count, int32_t step,
                         float lr, float beta1, float beta2, float eps, cudaStream_t stream);
 cudaError_t launch_sample(const DeviceGraph &g, uint64_t seed, int64_t first_shot, int32_t batch, double p_lo,
@@ -212,7 +213,7 @@ cudaError_t launch_logical(const uint8_t *logicals, int32_t k, int32_t n, const 
                            const uint8_t *ok, int32_t batch, uint8_t *fail, int grid, cudaStream_t stream);
 
 // Shared memory of one training shot (forward: q slots, gamma, targets, syndrome; backward adds
-// the recomputed r slots and a cache of one iteration's recorded state).
+// the recomputed r slots and the recorded state of two iterations).
 struct TrainLayout {
     size_t slot_off, r_off, c_off, g_off, y_off, s_off, total;
 };
@@ -223,8 +224,8 @@ __host__ __device__ inline TrainLayout train_layout(int m, int n, int dc_max, bo
     const size_t S = size_t(dc_max) * m;
     t.slot_off = 0;                                                          // q / gradient slots [S] f32
     t.r_off = align16(S * 4);                                                // r slots [S] f32 (backward)
-    t.c_off = backward ? align16(t.r_off + S * 4) : t.r_off;                 // state cache [4m] u32 (backward)
-    t.g_off = backward ? align16(t.c_off + size_t(kStateWords) * m * 4) : t.c_off;   // gamma [n] f32
+    t.c_off = backward ? align16(t.r_off + S * 4) : t.r_off;                 // state [2][4m] u32 (backward)
+    t.g_off = backward ? align16(t.c_off + 2 * size_t(kStateWords) * m * 4) : t.c_off;   // gamma [n] f32
     t.y_off = align16(t.g_off + size_t(n) * 4);                              // targets [n] u8
     t.s_off = align16(t.y_off + size_t(n));                                  // syndrome bits [m] u8
     t.total = align16(t.s_off + size_t(m));

@@ -5,7 +5,8 @@
 //   nms_forward_kernel   one block per shot, persistent over the batch.  T iterations of the learned
 //                        check step and the exact variable step of the decoder kernels (so FP32
 //                        messages are bit-identical to the learned decoder's), the per-shot loss
-//                        1/(T N) sum_t sum_n BCE(sigma(-Q^t_n), y_n), and, per iteration and check, the
+//                        sum_t lambda_t / N sum_n BCE(sigma(-Q^t_n), y_n) (lambda_t = 1/T unless
+//                        given), and, per iteration and check, the
 //                        compressed check state: min1, min2, the positions attaining them (lowest on
 //                        ties), the sign bits of the inputs and the syndrome-flipped total sign.
 //   nms_backward_kernel  the reverse sweep.  It stores no message: every r^(t) is recomputed from
@@ -15,9 +16,10 @@
 //                          dL/dw_{m,n}   = dL/dr_{m,n} * sign * min_{j != n}|q_j|
 //                          dL/dq_{m,idx1} = sum_{n != idx1} dL/dr_{m,n} w sign * sign(q_idx1)
 //                          dL/dq_{m,idx2} = dL/dr_{m,idx1} w sign * sign(q_idx2)     (all other q: 0)
-//                        Two block barriers per iteration.  Each block sums its shots' weight
-//                        gradients into its own slice of a partial buffer (no atomics); a reduction
-//                        kernel adds the slices in block order, so the gradient is deterministic.
+//                        Two block barriers per iteration; the next iteration's recorded state
+//                        streams into shared memory (cp.async) while the variable side runs.  Weight
+//                        gradients are added into one L2-resident [T][slots] buffer with global
+//                        reductions, so the order of the sum over shots follows the schedule.
 //   helpers              CSR <-> slot-layout weight permutation, an Adam step, a counter-based
 //                        SplitMix64 error sampler with syndromes, and the logical-failure test.
 #include <algorithm>
@@ -121,7 +123,8 @@ __global__ void __launch_bounds__(kTrainThreads, 4) nms_forward_kernel(const Tra
     __shared__ float red[32];
 
     for (int u = tid; u < N; u += T) gam[u] = F32::quantize(p.prior[__ldg(p.g.vperm + u)]);
-    const float inv = 1.0f / (float(p.T) * float(N));
+    // uniform lambda: sum the terms and scale once by 1/(T N); else weight each iteration's terms
+    const float inv = p.loss_w ? 1.0f / float(N) : 1.0f / (float(p.T) * float(N));
     for (int b = blockIdx.x; b < p.batch; b += gridDim.x) {
         const uint8_t *s = p.syn + size_t(b) * M;
         const uint8_t *tg = p.target + size_t(b) * N;
@@ -143,10 +146,11 @@ __global__ void __launch_bounds__(kTrainThreads, 4) nms_forward_kernel(const Tra
             }
             __syncthreads();
             const bool lastk = k + 1 == p.T;
+            const float lw = p.loss_w ? __ldg(p.loss_w + k) : 1.0f;
             for (int u = tid; u < N; u += T) {
                 const float Q = var_step_batch<F32, DV, false>(__ldg(p.g.vdeg + u), u, N, uint32_t(M), p.g.vslot,
                                                                gam[u], false, slots, nullptr);
-                acc += y[u] ? softplus(Q) : softplus(-Q);
+                acc += lw * (y[u] ? softplus(Q) : softplus(-Q));
                 if (lastk && p.post) p.post[size_t(b) * N + __ldg(p.g.vperm + u)] = Q;
             }
             __syncthreads();
@@ -156,41 +160,50 @@ __global__ void __launch_bounds__(kTrainThreads, 4) nms_forward_kernel(const Tra
     }
 }
 
+// Start an asynchronous copy of one iteration's recorded state (kStateWords * M words, a
+// contiguous, 16-byte aligned slice) into shared memory; cp_async_wait() completes it.
+__device__ __forceinline__ void prefetch_state(uint32_t *dst, const uint32_t *src, int M)
+{
+    const uint32_t base = uint32_t(__cvta_generic_to_shared(dst));
+    for (int i = threadIdx.x; i < M; i += blockDim.x)   // kStateWords * M * 4 bytes = M chunks of 16
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(base + 16u * uint32_t(i)),
+                     "l"(src + 4 * size_t(i))
+                     : "memory");
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 template <int DC, bool UNIFORM, int DV>
 __global__ void __launch_bounds__(kTrainThreads, 4) nms_backward_kernel(const TrainParams p)
 {
     const int M = p.g.m, N = p.g.n, T = blockDim.x, tid = threadIdx.x;
     const size_t S = size_t(p.g.dc_max) * M;
+    const size_t SW = size_t(kStateWords) * M;                    // state words of one iteration
     extern __shared__ __align__(16) unsigned char smem[];
     const TrainLayout L = train_layout(M, N, p.g.dc_max, true);
     float *gs = reinterpret_cast<float *>(smem + L.slot_off);     // dL/dq (next iteration), then dL/dr
     float *rs = reinterpret_cast<float *>(smem + L.r_off);        // recomputed r of the current iteration
-    uint32_t *sc = reinterpret_cast<uint32_t *>(smem + L.c_off);  // recorded state of the current iteration
+    uint32_t *scb = reinterpret_cast<uint32_t *>(smem + L.c_off); // recorded state, two iterations
     float *gam = reinterpret_cast<float *>(smem + L.g_off);
     uint8_t *y = smem + L.y_off;
 
     for (int u = tid; u < N; u += T) gam[u] = F32::quantize(p.prior[__ldg(p.g.vperm + u)]);
-    float *part = p.partial + size_t(blockIdx.x) * p.T * S;
-    const float inv = 1.0f / (float(p.T) * float(N));
-    bool first = true;   // the block's first shot writes its partial slice, later shots add to it
+    const float inv = 1.0f / float(N);
     for (int b = blockIdx.x; b < p.batch; b += gridDim.x) {
         const uint8_t *tg = p.target + size_t(b) * N;
         const float gscale = p.grad_loss[b] * inv;
-        const uint32_t *stb = p.state + size_t(b) * p.T * size_t(kStateWords) * M;
+        const uint32_t *stb = p.state + size_t(b) * p.T * SW;
         __syncthreads();   // gam (first shot) and the previous shot's last reads are done
+        prefetch_state(scb, stb + size_t(p.T - 1) * SW, M);
         for (int u = tid; u < N; u += T) y[u] = tg[__ldg(p.g.vperm + u)] & 1u;
-        // iteration T: recompute r, cache the state; dL/dq of iteration T+1 is zero
+        cp_async_wait();
+        __syncthreads();
+        // iteration T: recompute r; dL/dq of iteration T+1 is zero
         {
-            const uint32_t *st = stb + size_t(p.T - 1) * kStateWords * M;
             const float *wk = p.w + size_t(p.T - 1) * S;
             for (int c = tid; c < M; c += T) {
                 const int deg = UNIFORM ? DC : int(__ldg(p.g.rdeg + c));
-                const uint32_t a = st[c], bb = st[M + c], sg = st[2 * M + c], iw = st[3 * M + c];
-                sc[c] = a;
-                sc[M + c] = bb;
-                sc[2 * M + c] = sg;
-                sc[3 * M + c] = iw;
-                recompute_r<DC, UNIFORM>(c, M, deg, a, bb, sg, iw, wk, rs);
+                recompute_r<DC, UNIFORM>(c, M, deg, scb[c], scb[M + c], scb[2 * M + c], scb[3 * M + c], wk, rs);
 #pragma unroll
                 for (int j = 0; j < DC; ++j)
                     if (UNIFORM || j < deg) gs[j * M + c] = 0.0f;
@@ -198,6 +211,10 @@ __global__ void __launch_bounds__(kTrainThreads, 4) nms_backward_kernel(const Tr
         }
         __syncthreads();
         for (int k = p.T - 1; k >= 0; --k) {
+            const uint32_t *sc = scb + size_t((p.T - 1 - k) & 1) * SW;    // state of iteration k
+            uint32_t *sn = scb + size_t(((p.T - 1 - k) & 1) ^ 1) * SW;    // state of iteration k-1
+            if (k > 0) prefetch_state(sn, stb + size_t(k - 1) * SW, M);  // overlaps the variable side
+            const float gk = gscale * (p.loss_w ? __ldg(p.loss_w + k) : 1.0f / float(p.T));
             // variable side: Q^(k) from the recomputed r, dL/dQ, and dL/dr for every edge
             for (int u = tid; u < N; u += T) {
                 const int deg = __ldg(p.g.vdeg + u);
@@ -211,15 +228,16 @@ __global__ void __launch_bounds__(kTrainThreads, 4) nms_backward_kernel(const Tr
                         G += gs[sl[i]];
                     }
                 }
-                const float gQ = gscale * (float(y[u]) - sigmoid(-Q));
+                const float gQ = gk * (float(y[u]) - sigmoid(-Q));
 #pragma unroll
                 for (int i = 0; i < DV; ++i)
                     if (i < deg) gs[sl[i]] = gQ + (G - gs[sl[i]]);
             }
+            cp_async_wait();
             __syncthreads();
             // check side: weight gradient, dL/dq of iteration k, and r of iteration k-1
             const float *wk = p.w + size_t(k) * S;
-            float *pk = part + size_t(k) * S;
+            float *gk_out = p.partial + size_t(k) * S;
             for (int c = tid; c < M; c += T) {
                 const int deg = UNIFORM ? DC : int(__ldg(p.g.rdeg + c));
                 const float m1 = __uint_as_float(sc[c]), m2 = __uint_as_float(sc[M + c]);
@@ -233,8 +251,7 @@ __global__ void __launch_bounds__(kTrainThreads, 4) nms_backward_kernel(const Tr
                         const float gr = gs[j * M + c];
                         const float sgn = (((signs >> j) & 1u) ^ negall) ? -1.0f : 1.0f;
                         const float mu = j == i1 ? m2 : m1;
-                        const float gw = gr * sgn * mu;
-                        pk[j * M + c] = first ? gw : pk[j * M + c] + gw;
+                        atomicAdd(gk_out + j * M + c, gr * sgn * mu);   // result unused: a reduction
                         const float t = gr * __ldg(wk + j * M + c) * sgn;
                         if (j == i1)
                             t1 = t;
@@ -247,19 +264,12 @@ __global__ void __launch_bounds__(kTrainThreads, 4) nms_backward_kernel(const Tr
 #pragma unroll
                 for (int j = 0; j < DC; ++j)
                     if (UNIFORM || j < deg) gs[j * M + c] = j == i1 ? gq1 : (j == i2 ? gq2 : 0.0f);
-                if (k > 0) {
-                    const uint32_t *st = stb + size_t(k - 1) * kStateWords * M;
-                    const uint32_t a = st[c], bb = st[M + c], sg = st[2 * M + c], iw2 = st[3 * M + c];
-                    sc[c] = a;
-                    sc[M + c] = bb;
-                    sc[2 * M + c] = sg;
-                    sc[3 * M + c] = iw2;
-                    recompute_r<DC, UNIFORM>(c, M, deg, a, bb, sg, iw2, p.w + size_t(k - 1) * S, rs);
-                }
+                if (k > 0)
+                    recompute_r<DC, UNIFORM>(c, M, deg, sn[c], sn[M + c], sn[2 * M + c], sn[3 * M + c],
+                                             p.w + size_t(k - 1) * S, rs);
             }
             __syncthreads();
         }
-        first = false;
     }
 }
 
@@ -274,18 +284,14 @@ __global__ void permute_weights_kernel(const float *__restrict__ w_csr, const ui
     }
 }
 
-// grad[t][slot_edge[sl]] = sum over blocks (in block order) of partial[blk][t][sl].
-__global__ void reduce_grad_kernel(const float *__restrict__ partial, int32_t blocks, const int32_t *__restrict__ slot_edge,
-                                   int32_t T, int32_t S, int32_t nnz, float *__restrict__ grad)
+// grad[t][e] = grad_slot[t][eslot[e]]: the slot-layout gradient in CSR edge order.
+__global__ void gather_grad_kernel(const float *__restrict__ grad_slot, const uint32_t *__restrict__ eslot, int32_t T,
+                                   int32_t S, int32_t nnz, float *__restrict__ grad)
 {
-    const int64_t total = int64_t(T) * S, stride = total;
+    const int64_t total = int64_t(T) * nnz;
     for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
-        const int64_t t = i / S, sl = i - t * S;
-        const int32_t e = __ldg(slot_edge + sl);
-        if (e < 0) continue;
-        float acc = 0.0f;
-        for (int32_t b = 0; b < blocks; ++b) acc += __ldcs(partial + b * stride + i);
-        grad[t * nnz + e] = acc;
+        const int64_t t = i / nnz, e = i - t * nnz;
+        grad[i] = grad_slot[t * S + __ldg(eslot + e)];
     }
 }
 
@@ -447,11 +453,10 @@ cudaError_t launch_permute_weights(const float *w_csr, const uint32_t *eslot, in
     return cudaGetLastError();
 }
 
-cudaError_t launch_reduce_grad(const float *partial, int32_t blocks, const int32_t *slot_edge, int32_t T, int32_t S,
-                               int32_t nnz, float *grad, cudaStream_t stream)
+cudaError_t launch_gather_grad(const float *grad_slot, const uint32_t *eslot, int32_t T, int32_t S, int32_t nnz,
+                               float *grad, cudaStream_t stream)
 {
-    kern::reduce_grad_kernel<<<elementwise_grid(int64_t(T) * S), 256, 0, stream>>>(partial, blocks, slot_edge, T, S,
-                                                                                   nnz, grad);
+    kern::gather_grad_kernel<<<elementwise_grid(int64_t(T) * nnz), 256, 0, stream>>>(grad_slot, eslot, T, S, nnz, grad);
     return cudaGetLastError();
 }
 

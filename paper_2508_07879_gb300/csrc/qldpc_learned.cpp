@@ -60,14 +60,13 @@ int plan_training(const qldpc_graph *g, int32_t batch, int32_t T, TrainPlan &tp)
         return QLDPC_ERR_CUDA;
     }
     if (per_f < 1 || per_b < 1) return QLDPC_ERR_UNSUPPORTED;
-    // every backward block gets at least one shot, so every gradient slice is written
     tp.grid_f = int(std::min<int64_t>(batch, int64_t(per_f) * g->sm_count));
     tp.grid_b = int(std::min<int64_t>(batch, int64_t(per_b) * g->sm_count));
     const size_t S = size_t(g->dc_max) * size_t(g->m);
     tp.w_off = 0;
     tp.state_off = align_up(size_t(T) * S * sizeof(float));
     tp.part_off = tp.state_off + align_up(size_t(batch) * size_t(T) * kStateWords * size_t(g->m) * sizeof(uint32_t));
-    tp.total = tp.part_off + align_up(size_t(tp.grid_b) * size_t(T) * S * sizeof(float));
+    tp.total = tp.part_off + align_up(size_t(T) * S * sizeof(float));
     return QLDPC_OK;
 }
 
@@ -150,8 +149,8 @@ int qldpc_nms_workspace_bytes(const qldpc_graph *g, int32_t batch, int32_t T, si
 }
 
 int qldpc_nms_forward(const qldpc_graph *g, const uint8_t *syndromes, const uint8_t *targets, int32_t batch,
-                      const float *prior, const float *weights, int32_t T, float *out_loss, float *out_post,
-                      void *workspace, size_t workspace_bytes, void *stream)
+                      const float *prior, const float *weights, int32_t T, const float *loss_weights,
+                      float *out_loss, float *out_post, void *workspace, size_t workspace_bytes, void *stream)
 {
     if (!g || !syndromes || !targets || !prior || !weights || !out_loss || batch < 1 || T < 1 ||
         T > kMaxLearnedIters)
@@ -164,6 +163,7 @@ int qldpc_nms_forward(const qldpc_graph *g, const uint8_t *syndromes, const uint
     TrainParams p = train_params(g, tp, syndromes, targets, batch, prior, T, workspace);
     p.loss = out_loss;
     p.post = out_post;
+    p.loss_w = loss_weights;
     const size_t S = size_t(g->dc_max) * size_t(g->m);
     cudaError_t e = launch_permute_weights(weights, g->dg.eslot, T, g->nnz, int32_t(S),
                                            const_cast<float *>(p.w), st);
@@ -172,8 +172,8 @@ int qldpc_nms_forward(const qldpc_graph *g, const uint8_t *syndromes, const uint
 }
 
 int qldpc_nms_backward(const qldpc_graph *g, const uint8_t *syndromes, const uint8_t *targets, int32_t batch,
-                       const float *prior, int32_t T, const float *grad_loss, float *out_grad, void *workspace,
-                       size_t workspace_bytes, void *stream)
+                       const float *prior, int32_t T, const float *loss_weights, const float *grad_loss,
+                       float *out_grad, void *workspace, size_t workspace_bytes, void *stream)
 {
     if (!g || !syndromes || !targets || !prior || !grad_loss || !out_grad || batch < 1 || T < 1 ||
         T > kMaxLearnedIters)
@@ -185,10 +185,11 @@ int qldpc_nms_backward(const qldpc_graph *g, const uint8_t *syndromes, const uin
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     TrainParams p = train_params(g, tp, syndromes, targets, batch, prior, T, workspace);
     p.grad_loss = grad_loss;
+    p.loss_w = loss_weights;
     const size_t S = size_t(g->dc_max) * size_t(g->m);
-    cudaError_t e = launch_nms_backward(p, tp.tc, tp.grid_b, kTrainThreads, tp.smem_b, st);
-    if (e == cudaSuccess)
-        e = launch_reduce_grad(p.partial, tp.grid_b, g->dg.slot_edge, T, int32_t(S), g->nnz, out_grad, st);
+    cudaError_t e = cudaMemsetAsync(p.partial, 0, size_t(T) * S * sizeof(float), st);
+    if (e == cudaSuccess) e = launch_nms_backward(p, tp.tc, tp.grid_b, kTrainThreads, tp.smem_b, st);
+    if (e == cudaSuccess) e = launch_gather_grad(p.partial, g->dg.eslot, T, int32_t(S), g->nnz, out_grad, st);
     return cuda_status(e);
 }
 

@@ -38,27 +38,29 @@ class NMSLoss:
     _fn = None
 
     @classmethod
-    def apply(cls, weights, graph, syndromes, targets, prior, workspace):
+    def apply(cls, weights, graph, syndromes, targets, prior, workspace, loss_weights=None):
         if cls._fn is None:
             torch = _torch()
 
             class _F(torch.autograd.Function):
                 @staticmethod
-                def forward(ctx, w, g, syn, tg, pr, ws):
-                    loss, _ = qldpc.nms_forward(g, syn, tg, pr, w.detach().contiguous(), ws)
+                def forward(ctx, w, g, syn, tg, pr, ws, lw):
+                    loss, _ = qldpc.nms_forward(g, syn, tg, pr, w.detach().contiguous(), ws, loss_weights=lw)
                     ctx.graph = g
                     ctx.T = int(w.shape[0])
+                    ctx.lw = lw
                     ctx.save_for_backward(syn, tg, pr, ws)   # ws holds the weights and recorded state
                     return loss
 
                 @staticmethod
                 def backward(ctx, grad_loss):
                     syn, tg, pr, ws = ctx.saved_tensors
-                    grad = qldpc.nms_backward(ctx.graph, syn, tg, pr, ctx.T, grad_loss.float().contiguous(), ws)
-                    return grad, None, None, None, None, None
+                    grad = qldpc.nms_backward(ctx.graph, syn, tg, pr, ctx.T, grad_loss.float().contiguous(), ws,
+                                              loss_weights=ctx.lw)
+                    return grad, None, None, None, None, None, None
 
             cls._fn = _F
-        return cls._fn.apply(weights, graph, syndromes, targets, prior, workspace)
+        return cls._fn.apply(weights, graph, syndromes, targets, prior, workspace, loss_weights)
 
 
 def code_hash(h) -> bytes:
@@ -74,10 +76,12 @@ class NeuralMinSum:
     """Trainable per-edge, per-iteration weights for one parity-check matrix.
 
     h: the CSR matrix (workloads.CSR); prior: float [n] LLRs; T: unrolled iterations;
-    init: the starting weight (0.75 reproduces normalized min-sum with alpha = 0.75).
+    init: the starting weight (0.75 reproduces normalized min-sum with alpha = 0.75);
+    loss_weights: per-iteration loss weights lambda_t ([T]; None: 1/T each).
     """
 
-    def __init__(self, h, prior, T: int = 20, init: float = 0.75, max_batch: int = 4096, graph=None):
+    def __init__(self, h, prior, T: int = 20, init: float = 0.75, max_batch: int = 4096, graph=None,
+                 loss_weights=None):
         torch = _torch()
         self.h = h
         self.graph = graph if graph is not None else qldpc.Graph.from_csr(h)
@@ -92,12 +96,15 @@ class NeuralMinSum:
         self.max_batch = int(max_batch)
         ws = qldpc.nms_workspace_bytes(self.graph, self.max_batch, self.T)
         self.workspace = torch.empty(ws, dtype=torch.uint8, device=dev)
+        self.loss_weights = None if loss_weights is None else torch.as_tensor(
+            np.ascontiguousarray(loss_weights, dtype=np.float32).reshape(self.T), device=dev)
 
     def loss(self, syndromes, targets):
         """Per-shot BCE losses [B] (differentiable with respect to ``weights``)."""
         if syndromes.shape[0] > self.max_batch:
             raise ValueError(f"batch {syndromes.shape[0]} exceeds max_batch {self.max_batch}")
-        return NMSLoss.apply(self.weights, self.graph, syndromes, targets, self.prior, self.workspace)
+        return NMSLoss.apply(self.weights, self.graph, syndromes, targets, self.prior, self.workspace,
+                             self.loss_weights)
 
     def train_step(self, syndromes, targets, lr: float = 1e-3, betas=(0.9, 0.999), eps: float = 1e-8):
         """One Adam step on the mean loss of a batch; returns the mean loss (device scalar)."""

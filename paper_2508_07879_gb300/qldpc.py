@@ -83,8 +83,8 @@ _SIGNATURES = {
     "qldpc_server_destroy": ([_p], None),
     "qldpc_graph_set_weights": ([_p, _p, _i32], ctypes.c_int),
     "qldpc_nms_workspace_bytes": ([_p, _i32, _i32, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
-    "qldpc_nms_forward": ([_p, _p, _p, _i32, _p, _p, _i32, _p, _p, _p, ctypes.c_size_t, _p], ctypes.c_int),
-    "qldpc_nms_backward": ([_p, _p, _p, _i32, _p, _i32, _p, _p, _p, ctypes.c_size_t, _p], ctypes.c_int),
+    "qldpc_nms_forward": ([_p, _p, _p, _i32, _p, _p, _i32, _p, _p, _p, _p, ctypes.c_size_t, _p], ctypes.c_int),
+    "qldpc_nms_backward": ([_p, _p, _p, _i32, _p, _i32, _p, _p, _p, _p, ctypes.c_size_t, _p], ctypes.c_int),
     "qldpc_adam_step": ([_p, _p, _p, _p, ctypes.c_int64, _i32, _f32, _f32, _f32, _f32, _p], ctypes.c_int),
     "qldpc_sample_errors": ([_p, ctypes.c_uint64, ctypes.c_int64, _i32, ctypes.c_double, ctypes.c_double, _p, _p,
                              _p], ctypes.c_int),
@@ -462,9 +462,11 @@ def nms_workspace_bytes(graph: Graph, batch: int, T: int) -> int:
     return out.value
 
 
-def nms_forward(graph: Graph, syndromes, targets, prior, weights, workspace, want_post: bool = False, stream=None):
+def nms_forward(graph: Graph, syndromes, targets, prior, weights, workspace, want_post: bool = False, stream=None,
+                loss_weights=None):
     """Training forward (qldpc_nms_forward).  workspace: CUDA uint8 tensor of at least
-    nms_workspace_bytes(graph, B, T) bytes.  Returns (loss float32 [B], post float32 [B, n] or None)."""
+    nms_workspace_bytes(graph, B, T) bytes; loss_weights: CUDA float32 [T] or None (1/T each).
+    Returns (loss float32 [B], post float32 [B, n] or None)."""
     import torch
     batch = int(syndromes.shape[0])
     T = int(weights.shape[0])
@@ -474,6 +476,8 @@ def nms_forward(graph: Graph, syndromes, targets, prior, weights, workspace, wan
                             _dev_ptr(targets, torch.uint8, (batch, graph.n), "targets"), batch,
                             _dev_ptr(prior, torch.float32, (graph.n,), "prior"),
                             _dev_ptr(weights, torch.float32, (T, graph.nnz), "weights"), T,
+                            _dev_ptr(loss_weights, torch.float32, (T,), "loss_weights")
+                            if loss_weights is not None else None,
                             _dev_ptr(loss, torch.float32, (batch,), "loss"),
                             _dev_ptr(post, torch.float32, (batch, graph.n), "post") if post is not None else None,
                             ctypes.c_void_p(workspace.data_ptr()), int(workspace.numel() * workspace.element_size()),
@@ -481,7 +485,8 @@ def nms_forward(graph: Graph, syndromes, targets, prior, weights, workspace, wan
     return loss, post
 
 
-def nms_backward(graph: Graph, syndromes, targets, prior, T: int, grad_loss, workspace, stream=None):
+def nms_backward(graph: Graph, syndromes, targets, prior, T: int, grad_loss, workspace, stream=None,
+                 loss_weights=None):
     """Training backward (qldpc_nms_backward) after nms_forward on the same workspace.
     Returns the weight gradient float32 [T, nnz]."""
     import torch
@@ -490,6 +495,8 @@ def nms_backward(graph: Graph, syndromes, targets, prior, T: int, grad_loss, wor
     check(qldpc_nms_backward(graph.handle, _dev_ptr(syndromes, torch.uint8, (batch, graph.m), "syndromes"),
                              _dev_ptr(targets, torch.uint8, (batch, graph.n), "targets"), batch,
                              _dev_ptr(prior, torch.float32, (graph.n,), "prior"), int(T),
+                             _dev_ptr(loss_weights, torch.float32, (int(T),), "loss_weights")
+                             if loss_weights is not None else None,
                              _dev_ptr(grad_loss, torch.float32, (batch,), "grad_loss"),
                              _dev_ptr(grad, torch.float32, (int(T), graph.nnz), "grad"),
                              ctypes.c_void_p(workspace.data_ptr()), int(workspace.numel() * workspace.element_size()),

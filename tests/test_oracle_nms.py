@@ -56,6 +56,29 @@ def test_constant_weights_reduce_to_plain_decoder(precision):
     np.testing.assert_allclose(out["loss"], bce_of_posts(out["post"].astype(np.float64), e), rtol=1e-12)
 
 
+def test_loss_weights_select_iterations():
+    """lambda one-hot at iteration t: the loss is the mean BCE of the plain decoder's Q after t
+    iterations (constant weights); a general lambda is the lambda-weighted sum of those."""
+    code = w.hgp_code(400)
+    h = code.hz_csr
+    e = w.iid_x_errors(h.n, 0.05, 5, seed=12)
+    s = w.syndromes(h, e)
+    prior = np.full(h.n, w.prior_llr(0.05))
+    T = 5
+    weights = np.full((T, h.nnz), 0.75)
+    per_iter = []
+    for t in range(T):
+        ref = oracle.msa(h.row_ptr, h.col_idx, h.m, h.n, s, prior, t + 1, 0.75, "f64", early_stop=False)
+        per_iter.append(bce_of_posts(ref["post"][:, None, :], e))
+        lam = np.zeros(T)
+        lam[t] = 1.0
+        np.testing.assert_allclose(train(h, s, e, prior, weights, loss_weights=lam)["loss"], per_iter[-1],
+                                   rtol=1e-12)
+    lam = np.array([0.1, 0.0, 0.5, 0.2, 2.0])
+    np.testing.assert_allclose(train(h, s, e, prior, weights, loss_weights=lam)["loss"],
+                               np.sum([l * p for l, p in zip(lam, per_iter)], axis=0), rtol=1e-12)
+
+
 def first_iteration_dense(hd, s, prior, w0):
     """Q after one iteration, straight from the definitions with dense arrays."""
     m, n = hd.shape
@@ -107,14 +130,14 @@ def test_single_weight_switches_on_single_message():
             np.testing.assert_allclose(out["post"][b, t_star], expect, rtol=1e-15, atol=1e-15)
 
 
-def finite_difference(c, s, e, prior, weights, entries, eps=1e-6):
+def finite_difference(c, s, e, prior, weights, entries, eps=1e-6, lam=None):
     fd = []
     for t, k in entries:
         wp, wm = weights.copy(), weights.copy()
         wp[t, k] += eps
         wm[t, k] -= eps
-        lp = train(c, s, e, prior, wp)["loss"].sum()
-        lm = train(c, s, e, prior, wm)["loss"].sum()
+        lp = train(c, s, e, prior, wp, loss_weights=lam)["loss"].sum()
+        lm = train(c, s, e, prior, wm, loss_weights=lam)["loss"].sum()
         fd.append((lp - lm) / (2 * eps))
     return np.array(fd)
 
@@ -134,11 +157,12 @@ def test_gradient_equals_finite_differences_everywhere(which):
     weights = rng.uniform(0.4, 1.1, (T, c.nnz))
     e, s = sample(hd, 0.25, 6, 12)
     g = rng.uniform(0.5, 2.0, 6)
-    out = train(c, s, e, prior, weights, grad_loss=g)
+    lam = None if which != "regular" else rng.uniform(0.0, 1.0, T)   # also non-uniform loss weights
+    out = train(c, s, e, prior, weights, grad_loss=g, loss_weights=lam)
     entries = [(t, k) for t in range(T) for k in range(c.nnz)]
     fd = np.zeros(len(entries))
     for b in range(6):   # weight each shot's loss by g[b]
-        fd += g[b] * finite_difference(c, s[b:b + 1], e[b:b + 1], prior, weights, entries)
+        fd += g[b] * finite_difference(c, s[b:b + 1], e[b:b + 1], prior, weights, entries, lam=lam)
     np.testing.assert_allclose(out["grad"].reshape(-1), fd, rtol=1e-6, atol=1e-8)
     assert np.abs(out["grad"]).max() > 1e-3
 

@@ -64,8 +64,8 @@ OPS_PER_EDGE_ITER = 10          # algorithmic ALU operations per edge per iterat
 ALU_LANES_PER_SM = 128          # FP32/INT32 lanes per SM, one operation per lane per clock
 
 # DRAM traffic of one decoder launch from an ncu capture, valid only for the kernel source it was
-# measured on (profiles/msa_flood_lp1054_b65536_fp32.md); reported as null once the source changes.
-NCU_TRAFFIC = {"source_sha16": "0637d7609c5d1aea", "bytes_per_launch": 30676224 + 14220032,
+# measured on (profiles/msa_batch_lp1054_b65536_fp32.md); reported as null once the source changes.
+NCU_TRAFFIC = {"source_sha16": "d3c189be4fcec1c0", "bytes_per_launch": 30633472 + 15043584,
                "profile": "profiles/msa_batch_lp1054_b65536_fp32.md"}
 
 WORKLOAD = "LP-1054 H_Z (465x1054, E=3720), iid X noise p=0.01..0.05, B=65536/step, max 50 it, alpha 0.75"

@@ -10,7 +10,10 @@ splits a batch over host threads (ctypes releases the GIL during the call).
 
 Parity pins (see tests/test_oracle_pins.py): the hand-worked single-check update, the Eq. (1)
 trace against its closed-form recurrence, tree codes against brute-force max-product, loopy tiny
-codes against brute-force minimum weight, and the exact symmetries of min-sum.  The neural
+codes against brute-force minimum weight, and the exact symmetries of min-sum.  The layered
+(row-serial) schedule (tests/test_oracle_layered.py): a hand-worked two-check trace, schedule
+independence when no variable is shared, tree exactness, and bit-identical results under any
+reordering that keeps checks sharing a variable in order.  The neural
 min-sum functions (tests/test_oracle_nms.py): constant weights reduce them to the plain decoder,
 the reverse-mode gradient matches central finite differences and a closed form for one check.
 """
@@ -58,6 +61,12 @@ def _load():
             lib.oracle_msa_i16.argtypes = [p, p, i32, i32, p, i32, p, i32, ctypes.c_float, u32,
                                            p, p, p, p, p]
             lib.oracle_msa_i16.restype = ctypes.c_int
+            for name, real in (("oracle_layered_f64", ctypes.c_double), ("oracle_layered_f32", ctypes.c_float)):
+                f = getattr(lib, name)
+                f.argtypes = [p, p, i32, i32, p, i32, p, i32, real, u32, p, p, p, p]
+                f.restype = ctypes.c_int
+            lib.oracle_layered_i16.argtypes = [p, p, i32, i32, p, i32, p, i32, ctypes.c_float, u32, p, p, p, p]
+            lib.oracle_layered_i16.restype = ctypes.c_int
             lib.oracle_alpha_q.argtypes = [ctypes.c_float]
             lib.oracle_alpha_q.restype = ctypes.c_int
             for name in ("oracle_nms_train_f64", "oracle_nms_train_f32"):
@@ -81,8 +90,8 @@ def alpha_q(alpha: float) -> int:
 
 
 def msa(row_ptr, col_idx, m: int, n: int, syndromes, prior, max_iter: int, alpha: float,
-        precision: str = "f64", early_stop: bool = True, threads: int = 1) -> dict:
-    """Decode a batch with Algorithm 1.
+        precision: str = "f64", early_stop: bool = True, threads: int = 1, schedule: str = "flooding") -> dict:
+    """Decode a batch with Algorithm 1 (schedule "flooding") or its row-serial variant ("layered").
 
     row_ptr/col_idx: H in CSR (int32).  syndromes: uint8 [B, m].  prior: [n] LLRs gamma_n.
     precision: "f64", "f32" or "i16".  Returns a dict with
@@ -91,8 +100,12 @@ def msa(row_ptr, col_idx, m: int, n: int, syndromes, prior, max_iter: int, alpha
       ok    uint8 [B]     1 iff H e_hat^T = s
       post  [B, n]        a-posteriori LLR Q_n of the last iteration (float64 / float32; for i16
                           the raw 32-bit fixed-point value, LLR = post / 256)
-      margin float64 [B]  smallest |q| or |Q| the shot produced (near-tie diagnostic)
+      margin float64 [B]  smallest |q| or |Q| the shot produced (near-tie diagnostic; flooding only)
     """
+    if schedule == "layered":
+        return _layered(row_ptr, col_idx, m, n, syndromes, prior, max_iter, alpha, precision, early_stop, threads)
+    if schedule != "flooding":
+        raise ValueError(f"unknown schedule {schedule!r}")
     lib = _load()
     row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
     col_idx = np.ascontiguousarray(col_idx, dtype=np.int32)
@@ -132,6 +145,46 @@ def msa(row_ptr, col_idx, m: int, n: int, syndromes, prior, max_iter: int, alpha
     if bad:
         raise ValueError(f"oracle rejected the input (code {bad[0]})")
     return {"err": err, "iters": iters, "ok": ok, "post": post, "margin": margin}
+
+
+def _layered(row_ptr, col_idx, m, n, syndromes, prior, max_iter, alpha, precision, early_stop, threads):
+    lib = _load()
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    col_idx = np.ascontiguousarray(col_idx, dtype=np.int32)
+    syn = np.ascontiguousarray(syndromes, dtype=np.uint8).reshape(-1, m)
+    batch = syn.shape[0]
+    if precision == "f64":
+        fn, pdt, post_dt, alpha_c = lib.oracle_layered_f64, np.float64, np.float64, float(alpha)
+    elif precision == "f32":
+        fn, pdt, post_dt, alpha_c = lib.oracle_layered_f32, np.float32, np.float32, float(np.float32(alpha))
+    elif precision == "i16":
+        fn, pdt, post_dt, alpha_c = lib.oracle_layered_i16, np.float32, np.int32, float(np.float32(alpha))
+    else:
+        raise ValueError(f"unknown precision {precision!r}")
+    prior = np.ascontiguousarray(prior, dtype=pdt).reshape(n)
+    err = np.zeros((batch, n), dtype=np.uint8)
+    iters = np.zeros(batch, dtype=np.int32)
+    ok = np.zeros(batch, dtype=np.uint8)
+    post = np.zeros((batch, n), dtype=post_dt)
+    flags = 0 if early_stop else NO_EARLY_STOP
+
+    def run(lo, hi):
+        if hi <= lo:
+            return 0
+        return fn(_ptr(row_ptr), _ptr(col_idx), m, n, _ptr(syn[lo:hi]), hi - lo, _ptr(prior), int(max_iter),
+                  alpha_c, flags, _ptr(err[lo:hi]), _ptr(iters[lo:hi]), _ptr(ok[lo:hi]), _ptr(post[lo:hi]))
+
+    threads = max(1, min(int(threads), max(batch, 1)))
+    bounds = np.linspace(0, batch, threads + 1).astype(int)
+    if threads == 1:
+        rcs = [run(0, batch)]
+    else:
+        with ThreadPoolExecutor(threads) as ex:
+            rcs = list(ex.map(lambda i: run(bounds[i], bounds[i + 1]), range(threads)))
+    bad = [rc for rc in rcs if rc != 0]
+    if bad:
+        raise ValueError(f"oracle rejected the input (code {bad[0]})")
+    return {"err": err, "iters": iters, "ok": ok, "post": post}
 
 
 # ------------------------------------------------------------------------------------------------

@@ -302,6 +302,148 @@ int oracle_msa_i16(const int32_t *row_ptr, const int32_t *col_idx, int32_t m, in
 }
 
 /* ---------------------------------------------------------------------------------------------
+ * Layered (row-serial) schedule.  Algorithm 1 updates every check from the previous iteration's
+ * messages (flooding); the layered schedule, a standard alternative for the same min-sum update,
+ * visits the checks one after another within an iteration and lets each use the a-posteriori LLRs
+ * already refreshed by the checks before it:
+ *   start    Q_n = gamma_n, r_{m,n} = 0
+ *   check m (ascending index), for n in S_v(m):
+ *            q_{m,n} = Q_n - r_{m,n}
+ *            r_{m,n} = (-1)^{s_m} prod_{j != n} sign(q_{m,j}) * (alpha * min_{j != n} |q_{m,j}|)
+ *            Q_n     = q_{m,n} + r_{m,n}                     (with the new r)
+ *   after the last check: e_n = [Q_n < 0] and the stop test, exactly as for flooding (iteration-0
+ *   test, early stop, ok, iters).
+ * i16: Q in int32 (not clamped), q = clamp(Q - r, +-32767), |r| = floor(min * alpha_q / 2^15).
+ * --------------------------------------------------------------------------------------------- */
+#define DEFINE_LAYERED_REAL(NAME, REAL, FABS)                                                     \
+int NAME(const int32_t *row_ptr, const int32_t *col_idx, int32_t m, int32_t n,                   \
+         const uint8_t *syn, int32_t batch, const REAL *prior, int32_t max_iter, REAL alpha,      \
+         uint32_t flags, uint8_t *out_err, int32_t *out_iters, uint8_t *out_ok, REAL *out_post)   \
+{                                                                                                 \
+    if (batch < 0 || max_iter < 0 || !syn || !prior || !out_err || !out_iters || !out_ok)        \
+        return ORACLE_BAD_ARG;                                                                    \
+    tanner t;                                                                                     \
+    int rc = tanner_build(&t, row_ptr, col_idx, m, n);                                            \
+    if (rc) return rc;                                                                            \
+    const int early = !(flags & ORACLE_NO_EARLY_STOP);                                           \
+    const size_t E = (size_t)(t.e > 0 ? t.e : 1);                                                 \
+    REAL *q = (REAL *)malloc(sizeof(REAL) * E), *r = (REAL *)malloc(sizeof(REAL) * E);           \
+    REAL *rn = (REAL *)malloc(sizeof(REAL) * E), *Q = (REAL *)malloc(sizeof(REAL) * (size_t)n);  \
+    if (!q || !r || !rn || !Q) { free(q); free(r); free(rn); free(Q); tanner_free(&t); return ORACLE_NO_MEMORY; } \
+    for (int32_t b = 0; b < batch; ++b) {                                                         \
+        const uint8_t *s = syn + (size_t)b * m;                                                   \
+        uint8_t *e_hat = out_err + (size_t)b * n;                                                 \
+        for (int32_t v = 0; v < n; ++v) { Q[v] = prior[v]; e_hat[v] = prior[v] < 0; }           \
+        int met = syndrome_met(&t, e_hat, s);                                                     \
+        int32_t iters = 0;                                                                        \
+        if (!(early && met) && max_iter > 0) {                                                    \
+            for (int32_t i = 0; i < t.e; ++i) r[i] = 0;                                           \
+            for (int32_t k = 1; k <= max_iter; ++k) {                                             \
+                for (int32_t c = 0; c < m; ++c) {                                                 \
+                    for (int32_t i = row_ptr[c]; i < row_ptr[c + 1]; ++i) q[i] = Q[col_idx[i]] - r[i]; \
+                    for (int32_t i = row_ptr[c]; i < row_ptr[c + 1]; ++i) {                       \
+                        int neg = s[c] & 1;                                                       \
+                        REAL mn = (REAL)INFINITY;                                                 \
+                        for (int32_t j = row_ptr[c]; j < row_ptr[c + 1]; ++j) {                   \
+                            if (j == i) continue;                                                 \
+                            if (q[j] < 0) neg ^= 1;                                               \
+                            if (FABS(q[j]) < mn) mn = FABS(q[j]);                                 \
+                        }                                                                         \
+                        REAL mag = alpha * mn;                                                    \
+                        rn[i] = neg ? -mag : mag;                                                 \
+                    }                                                                             \
+                    for (int32_t i = row_ptr[c]; i < row_ptr[c + 1]; ++i) {                       \
+                        Q[col_idx[i]] = q[i] + rn[i];                                             \
+                        r[i] = rn[i];                                                             \
+                    }                                                                             \
+                }                                                                                 \
+                for (int32_t v = 0; v < n; ++v) e_hat[v] = Q[v] < 0;                              \
+                iters = k;                                                                        \
+                met = syndrome_met(&t, e_hat, s);                                                 \
+                if (early && met) break;                                                          \
+            }                                                                                     \
+        }                                                                                         \
+        out_iters[b] = iters;                                                                     \
+        out_ok[b] = (uint8_t)met;                                                                 \
+        if (out_post) memcpy(out_post + (size_t)b * n, Q, sizeof(REAL) * (size_t)n);              \
+    }                                                                                             \
+    free(q); free(r); free(rn); free(Q); tanner_free(&t);                                         \
+    return ORACLE_OK;                                                                             \
+}
+
+DEFINE_LAYERED_REAL(oracle_layered_f64, double, fabs)
+DEFINE_LAYERED_REAL(oracle_layered_f32, float, fabsf)
+
+int oracle_layered_i16(const int32_t *row_ptr, const int32_t *col_idx, int32_t m, int32_t n,
+                       const uint8_t *syn, int32_t batch, const float *prior, int32_t max_iter,
+                       float alpha, uint32_t flags, uint8_t *out_err, int32_t *out_iters,
+                       uint8_t *out_ok, int32_t *out_post_q)
+{
+    if (batch < 0 || max_iter < 0 || !syn || !prior || !out_err || !out_iters || !out_ok)
+        return ORACLE_BAD_ARG;
+    const int32_t alpha_q = oracle_alpha_q(alpha);
+    if (alpha_q < 0) return ORACLE_BAD_ARG;
+    tanner t;
+    int rc = tanner_build(&t, row_ptr, col_idx, m, n);
+    if (rc) return rc;
+    const int early = !(flags & ORACLE_NO_EARLY_STOP);
+    const size_t E = (size_t)(t.e > 0 ? t.e : 1);
+    int32_t *gq = (int32_t *)malloc(sizeof(int32_t) * (size_t)n), *Q = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t *q = (int32_t *)malloc(sizeof(int32_t) * E), *r = (int32_t *)malloc(sizeof(int32_t) * E);
+    int32_t *rn = (int32_t *)malloc(sizeof(int32_t) * E);
+    if (!gq || !Q || !q || !r || !rn) {
+        free(gq); free(Q); free(q); free(r); free(rn); tanner_free(&t);
+        return ORACLE_NO_MEMORY;
+    }
+    for (int32_t v = 0; v < n; ++v)
+        if (!quantize_prior(prior[v], &gq[v])) {
+            free(gq); free(Q); free(q); free(r); free(rn); tanner_free(&t);
+            return ORACLE_BAD_ARG;
+        }
+    for (int32_t b = 0; b < batch; ++b) {
+        const uint8_t *s = syn + (size_t)b * m;
+        uint8_t *e_hat = out_err + (size_t)b * n;
+        for (int32_t v = 0; v < n; ++v) { Q[v] = gq[v]; e_hat[v] = gq[v] < 0; }
+        int met = syndrome_met(&t, e_hat, s);
+        int32_t iters = 0;
+        if (!(early && met) && max_iter > 0) {
+            for (int32_t i = 0; i < t.e; ++i) r[i] = 0;
+            for (int32_t k = 1; k <= max_iter; ++k) {
+                for (int32_t c = 0; c < m; ++c) {
+                    for (int32_t i = row_ptr[c]; i < row_ptr[c + 1]; ++i)
+                        q[i] = clamp16((int64_t)Q[col_idx[i]] - r[i]);
+                    for (int32_t i = row_ptr[c]; i < row_ptr[c + 1]; ++i) {
+                        int neg = s[c] & 1;
+                        int32_t mn = INT32_MAX;
+                        for (int32_t j = row_ptr[c]; j < row_ptr[c + 1]; ++j) {
+                            if (j == i) continue;
+                            if (q[j] < 0) neg ^= 1;
+                            const int32_t a = q[j] < 0 ? -q[j] : q[j];
+                            if (a < mn) mn = a;
+                        }
+                        const int32_t mag = (int32_t)(((int64_t)mn * alpha_q) >> 15);
+                        rn[i] = neg ? -mag : mag;
+                    }
+                    for (int32_t i = row_ptr[c]; i < row_ptr[c + 1]; ++i) {
+                        Q[col_idx[i]] = q[i] + rn[i];
+                        r[i] = rn[i];
+                    }
+                }
+                for (int32_t v = 0; v < n; ++v) e_hat[v] = Q[v] < 0;
+                iters = k;
+                met = syndrome_met(&t, e_hat, s);
+                if (early && met) break;
+            }
+        }
+        out_iters[b] = iters;
+        out_ok[b] = (uint8_t)met;
+        if (out_post_q) memcpy(out_post_q + (size_t)b * n, Q, sizeof(int32_t) * (size_t)n);
+    }
+    free(gq); free(Q); free(q); free(r); free(rn); tanner_free(&t);
+    return ORACLE_OK;
+}
+
+/* ---------------------------------------------------------------------------------------------
  * Neural normalized min-sum: Algorithm 1 with the scale alpha replaced by a learned weight
  * w[t][e] per iteration t (0-based here, iteration t+1 of the algorithm) and per edge e (CSR edge
  * order: e = row_ptr[m] + position of n in row m):

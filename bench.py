@@ -13,6 +13,8 @@ Printed as one JSON line on rank 0:
                the launch path (qldpc_decode_host) and the persistent server (qldpc_server_*)
   serving      the persistent server under a 40/40/20 mix of the N=400, 1054 and 288 codes with
                Poisson arrivals 20 us apart: latency percentiles and the saturated request rate
+  layered      the row-serial (layered) schedule on the same batches and shots: device throughput,
+               mean iterations, decode success, and single-shot latency through qldpc_decode_host
   learned      the learned (neural) min-sum on the same code: training time and kernel times on
                2e6 device-sampled shots (T = 20, batch 4096, Adam lr 1e-3, p uniform in
                [0.02, 0.06]), then logical error rates of learned and plain decoding on 1e6 fresh
@@ -86,6 +88,7 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=SERVE_REQUESTS)
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-layered", action="store_true")
     ap.add_argument("--learned-train-shots", type=int, default=LEARN_SHOTS)
     ap.add_argument("--learned-eval-shots", type=int, default=LEARN_EVAL)
     return ap.parse_args()
@@ -336,6 +339,9 @@ def run_ours(args, rank, world, local):
     serving = None
     if not args.no_serving and rank == 0:
         serving = measure_serving(qldpc, args)
+    layered_res = None
+    if not args.no_layered and rank == 0:
+        layered_res = measure_layered(qldpc, graph, code, syn_d, pri_d, out, stream, B, args)
     learned_res = None
     if not args.no_learned and rank == 0:
         learned_res = measure_learned(qldpc, args)
@@ -360,6 +366,7 @@ def run_ours(args, rank, world, local):
             "e2e": e2e,
             "latency": latency,
             "serving": serving,
+            "layered": layered_res,
             "learned": learned_res,
             "gpu_launches": launches,
             "clocks": clocks,
@@ -487,6 +494,60 @@ def measure_serving(qldpc, args):
                      "p999_us": float(np.percentile(x, 99.9)), "per_code": per,
                      "saturated_shots_per_s": n / dt}
     return out
+
+
+def measure_layered(qldpc, graph, code, syn_d, pri_d, out, stream, B, args, steps=100):
+    """The layered schedule on the benchmark's own batches (device throughput, iterations) and on the
+    single-shot workload of the latency measurement (launch path)."""
+    import torch
+    from paper_2508_07879_gb300 import workloads as w
+    res = {"schedule": "row-serial in ascending check order, checks without shared variables in parallel"}
+    iters = ok = 0
+    with torch.cuda.stream(stream):
+        for j in range(len(syn_d)):
+            qldpc.decode(graph, syn_d[j], pri_d[j], MAX_ITER, ALPHA, args.precision, out=out, stream=stream,
+                         layered=True)
+            stream.synchronize()
+            iters += int(out[1].to(torch.int64).sum().item())
+            ok += int(out[2].to(torch.int64).sum().item())
+        for i in range(5):
+            qldpc.decode(graph, syn_d[i % len(syn_d)], pri_d[i % len(syn_d)], MAX_ITER, ALPHA, args.precision,
+                         out=out, stream=stream, layered=True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        stream.synchronize()
+        e0.record(stream)
+        for i in range(steps):
+            j = i % len(syn_d)
+            qldpc.decode(graph, syn_d[j], pri_d[j], MAX_ITER, ALPHA, args.precision, out=out, stream=stream,
+                         layered=True)
+        e1.record(stream)
+        stream.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    res["value"] = B / (ms / 1e3)
+    res["unit"] = "syndromes/s"
+    res["ms_per_step"] = ms
+    res["mean_iters"] = iters / (len(syn_d) * B)
+    res["decoded_fraction"] = ok / (len(syn_d) * B)
+    # single shot, launch path: the shots of the flooding latency measurement
+    shots = args.latency_shots
+    warm = min(LAT_WARMUP, max(shots // 10, 10))
+    b = w.x_error_batch(code, LAT_P, shots + warm, seed=4003)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    syn = pin(b.syndromes)
+    err, it, okk = pin(np.zeros((1, b.h.n), np.uint8)), pin(np.zeros(1, np.int32)), pin(np.zeros(1, np.uint8))
+    ts = np.empty(shots + warm)
+    its = np.empty(shots + warm, dtype=np.int32)
+    for i in range(shots + warm):
+        t0 = time.perf_counter_ns()
+        qldpc.decode_host(graph, syn[i:i + 1], b.prior, MAX_ITER, ALPHA, "fp32", out=(err, it, okk), layered=True)
+        ts[i] = (time.perf_counter_ns() - t0) / 1e3
+        its[i] = it[0]
+    x = ts[warm:]
+    res["latency_launch_path_fp32"] = {"p50_us": float(np.percentile(x, 50)), "p99_us": float(np.percentile(x, 99)),
+                                       "p999_us": float(np.percentile(x, 99.9)), "mean_us": float(x.mean()),
+                                       "mean_iters": float(its[warm:].mean()), "shots": int(shots), "p": LAT_P}
+    return res
 
 
 def measure_learned(qldpc, args):

@@ -73,8 +73,13 @@ enum { QLDPC_FP32 = 0, QLDPC_INT16 = 1 };
 enum {
     QLDPC_NO_EARLY_STOP = 1u,     /* run exactly max_iter iterations (the paper's timed mode, Sec. 3);
                                      ok still reports H e_hat^T = s after the last one */
-    QLDPC_LEARNED = 2u            /* learned decoding with the graph's weights, then the plain
+    QLDPC_LEARNED = 2u,           /* learned decoding with the graph's weights, then the plain
                                      fallback (see qldpc_graph_set_weights); FP32 and early stop only */
+    QLDPC_LAYERED = 4u            /* layered (row-serial) schedule instead of flooding: the checks
+                                     are updated one after another in ascending index, each from the
+                                     a-posteriori LLRs the checks before it refreshed
+                                     (q = Q - r_old, r = Algorithm 1's check update of q,
+                                     Q = q + r); FP32 or INT16; not with QLDPC_LEARNED */
 };
 
 /* Limits of the kernels in this build. */
@@ -153,6 +158,9 @@ QLDPC_API int qldpc_decode(const qldpc_graph *g, const uint8_t *syndromes, int32
  * (cudaStream_t cast to void*, NULL = legacy default stream) and an optional device output
  *   out_post  float[batch*n] or NULL: the a-posteriori LLR Q_n of the last iteration run
  *             (INT16: the fixed-point value / 256, exact).
+ * With QLDPC_LAYERED the schedule is row-serial (see the flag): same outputs and stop rule; INT16
+ * keeps Q in 32 bits and clamps q = Q - r to +-32767.  Its launch shape is chosen automatically
+ * (qldpc_graph_set_launch does not apply).
  * With QLDPC_LEARNED the graph's learned weights (qldpc_graph_set_weights) drive the first T
  * iterations and max_iter bounds the plain fallback; INVALID_ARG if the graph has no weights, the
  * precision is not FP32 or QLDPC_NO_EARLY_STOP is also set.

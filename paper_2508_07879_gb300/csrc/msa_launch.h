@@ -22,6 +22,9 @@ struct DeviceGraph {
     const uint32_t *ecol;    // [dc_max * m] original variable of slot j*m + i (0xffffffff: no edge)
     const int32_t *slot_edge;// [dc_max * m] CSR edge index of slot j*m + i (-1: no edge)
     const uint32_t *eslot;   // [nnz] slot j*m + i of CSR edge e
+    const int32_t *layer_ptr;// [nlayers + 1] layered schedule: checks of layer l are
+    const uint32_t *layer_chk;//   layer_chk[layer_ptr[l] .. layer_ptr[l+1]) (ascending)
+    int32_t nlayers, max_layer;
     int32_t m, n, nnz;
     int32_t dc_max, dv_max;  // largest row / column degree
 };
@@ -95,6 +98,7 @@ struct KernelChoice {
     bool uniform;    // every row has exactly dc edges
     int dvb;         // column-degree bucket 4/8/16
     bool learned = false;   // learned weights first, then plain fallback (FP32 only)
+    bool layered = false;   // msa_layered_kernel (row-serial schedule)
 };
 
 // Latency kernel limits: checks M <= 2 * threads, variables N <= 2 * threads, threads <= 640
@@ -160,6 +164,26 @@ cudaError_t launch_msa_f32(const LaunchParams &p, const KernelChoice &kc, dim3 g
                            size_t smem, cudaStream_t stream);
 cudaError_t launch_msa_i16(const LaunchParams &p, const KernelChoice &kc, dim3 grid, int threads,
                            size_t smem, cudaStream_t stream);
+// Layered-schedule kernels, msa_layered.cu.
+const void *msa_kernel_layered(int precision, const KernelChoice &kc);
+cudaError_t launch_msa_layered(int precision, const LaunchParams &p, const KernelChoice &kc, dim3 grid, int threads,
+                               size_t smem, cudaStream_t stream);
+
+// Shared memory of one shot in the layered kernel: Q [n] (4 B), r slots [dc_max*m], syndrome bits [m].
+struct LayeredLayout {
+    size_t q_off, slot_off, s_off, total;
+};
+
+__host__ __device__ inline LayeredLayout layered_layout(int m, int n, int dc_max, int msg_bytes)
+{
+    LayeredLayout l;
+    l.q_off = 0;
+    l.slot_off = align16(size_t(n) * 4);
+    l.s_off = align16(l.slot_off + size_t(dc_max) * m * msg_bytes);
+    l.total = align16(l.s_off + size_t(m));
+    return l;
+}
+
 // Learned (FP32) decoder kernels, msa_learned.cu.
 const void *msa_kernel_learned(const KernelChoice &kc);
 cudaError_t launch_msa_learned(const LaunchParams &p, const KernelChoice &kc, dim3 grid, int threads,

@@ -1,0 +1,190 @@
+// Layered (row-serial) schedule of the normalized min-sum decoder, FP32 and INT16, for sm_103a.
+//
+// Algorithm 1 (Sec. 2 of arXiv 2508.07879) updates all checks from the previous iteration's
+// messages (flooding).  The layered schedule applies the same check update to one check after
+// another, each reading the a-posteriori LLRs already refreshed by the checks before it:
+//   q_{m,n} = Q_n - r_{m,n};  r_{m,n} = (-1)^{s_m} prod_{j != n} sign(q_{m,j}) alpha min_{j != n} |q_{m,j}|;
+//   Q_n = q_{m,n} + r_{m,n}        (checks in ascending index; then decisions and the stop test)
+// Two checks that share no variable commute, so the host groups the checks into layers (a check's
+// layer is one more than the largest layer of an earlier check it shares a variable with): the
+// checks of a layer run in parallel, the layers in order, and every result is bit-identical to the
+// strictly serial order.  One block per shot, persistent over the batch; per shot in shared memory:
+// Q [n] (FP32, or INT32 for INT16), the messages r in check-major slots (j*m + i), the syndrome bits.
+// One barrier per layer, then a stop-test pass over all checks (block AND).
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "msa_kernel.cuh"
+
+namespace qldpc {
+namespace kern {
+
+__device__ __forceinline__ float sub_q(float Q, float r) { return __fsub_rn(Q, r); }
+__device__ __forceinline__ int32_t sub_q(int32_t Q, int32_t r) { return max(-32767, min(32767, Q - r)); }
+
+// One check of the layered schedule: q = Q - r_old, the min-sum update, Q = q + r_new.
+template <class P, int DC, bool UNIFORM>
+__device__ __forceinline__ void layered_check(int c, int M, int deg, uint32_t s_bit, typename P::acc_t *__restrict__ Q,
+                                              typename P::msg_t *__restrict__ slots, const uint32_t *__restrict__ ecol,
+                                              const LaunchParams &p)
+{
+    using acc_t = typename P::acc_t;
+    using mag_t = typename P::mag_t;
+    acc_t q[DC];
+    uint32_t v[DC];
+    uint32_t sx = 0;
+    mag_t m1 = P::mag_init(), m2 = P::mag_init();
+#pragma unroll
+    for (int j = 0; j < DC; ++j) {
+        if (UNIFORM || j < deg) {
+            v[j] = __ldg(ecol + size_t(j) * M + c);
+            q[j] = sub_q(Q[v[j]], load_msg<P>(slots, uint32_t(j * M + c)));
+            sx ^= P::sign_word(q[j]);
+            const mag_t a = P::mag(q[j]);
+            m2 = P::mn(m2, P::mx(m1, a));
+            m1 = P::mn(m1, a);
+        }
+    }
+    const uint32_t negall = (s_bit ^ (sx >> 31)) & 1u;
+    const mag_t r1 = P::scale(m1, p), r2 = P::scale(m2, p);
+#pragma unroll
+    for (int j = 0; j < DC; ++j) {
+        if (UNIFORM || j < deg) {
+            const acc_t r = P::signed_like(P::mag(q[j]) == m1 ? r2 : r1, q[j], negall);
+            Q[v[j]] = P::add(q[j], r);
+            slots[j * M + c] = P::to_msg(r);
+        }
+    }
+}
+
+// 1 iff the decisions [Q < 0] of check c's variables meet s_c.
+template <class P, int DC, bool UNIFORM>
+__device__ __forceinline__ int check_met(int c, int M, int deg, uint32_t s_bit, const typename P::acc_t *__restrict__ Q,
+                                         const uint32_t *__restrict__ ecol)
+{
+    uint32_t par = s_bit;
+#pragma unroll
+    for (int j = 0; j < DC; ++j)
+        if (UNIFORM || j < deg) par ^= P::neg(Q[__ldg(ecol + size_t(j) * M + c)]) ? 1u : 0u;
+    return par == 0;
+}
+
+template <class P, int DC, bool UNIFORM>
+__global__ void __launch_bounds__(1024, 1) msa_layered_kernel(const LaunchParams p)
+{
+    using acc_t = typename P::acc_t;
+    using msg_t = typename P::msg_t;
+    const Problem pr = blockIdx.y == 0 ? p.prob[0] : p.prob[1];
+    const int M = pr.g.m, N = pr.g.n, L = pr.g.nlayers;
+    const int T = blockDim.x, tid = threadIdx.x;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const LayeredLayout lay = layered_layout(M, N, pr.g.dc_max, int(sizeof(msg_t)));
+    acc_t *Q = reinterpret_cast<acc_t *>(smem + lay.q_off);
+    msg_t *slots = reinterpret_cast<msg_t *>(smem + lay.slot_off);
+    uint8_t *sb = smem + lay.s_off;
+
+    int bad = 0;
+    for (int v = tid; v < N; v += T) bad |= !isfinite(pr.prior[v]);
+    bad = __syncthreads_or(bad);
+    const bool early = (p.flags & kFlagNoEarlyStop) == 0;
+    for (int b = blockIdx.x; b < p.batch; b += gridDim.x) {
+        uint8_t *err = pr.err + size_t(b) * N;
+        if (bad) {   // non-finite prior: report the shot as not decoded
+            for (int v = tid; v < N; v += T) {
+                err[v] = 0;
+                if (pr.post) pr.post[size_t(b) * N + v] = __int_as_float(0x7fc00000);
+            }
+            if (tid == 0) {
+                pr.iters[b] = -1;
+                pr.ok[b] = 0;
+            }
+            continue;
+        }
+        const uint8_t *s = pr.syn + size_t(b) * M;
+        // Q = gamma, r = 0, syndrome bits
+        for (int v = tid; v < N; v += T) Q[v] = P::quantize(pr.prior[v]);
+        for (int c = tid; c < M; c += T) {
+            sb[c] = s[c] & 1u;
+            const int deg = UNIFORM ? DC : int(__ldg(pr.g.rdeg + c));
+            for (int j = 0; j < deg; ++j) slots[j * M + c] = msg_t(0);
+        }
+        __syncthreads();
+        int ok = 1;
+        for (int c = tid; c < M; c += T)
+            ok &= check_met<P, DC, UNIFORM>(c, M, UNIFORM ? DC : int(__ldg(pr.g.rdeg + c)), sb[c], Q, pr.g.ecol);
+        int all = __syncthreads_and(ok);
+        int k = 0;
+        if (!(early && all)) {
+            for (k = 1; k <= p.max_iter; ++k) {
+                for (int l = 0; l < L; ++l) {
+                    const int lo = __ldg(pr.g.layer_ptr + l), hi = __ldg(pr.g.layer_ptr + l + 1);
+                    for (int i = lo + tid; i < hi; i += T) {
+                        const int c = int(__ldg(pr.g.layer_chk + i));
+                        layered_check<P, DC, UNIFORM>(c, M, UNIFORM ? DC : int(__ldg(pr.g.rdeg + c)), sb[c], Q, slots,
+                                                      pr.g.ecol, p);
+                    }
+                    __syncthreads();
+                }
+                ok = 1;
+                for (int c = tid; c < M; c += T)
+                    ok &= check_met<P, DC, UNIFORM>(c, M, UNIFORM ? DC : int(__ldg(pr.g.rdeg + c)), sb[c], Q,
+                                                    pr.g.ecol);
+                all = __syncthreads_and(ok);
+                if (early && all) break;
+            }
+            if (k > p.max_iter) k = p.max_iter;
+        }
+        for (int v = tid; v < N; v += T) {
+            err[v] = P::neg(Q[v]) ? 1 : 0;
+            if (pr.post) pr.post[size_t(b) * N + v] = P::post(Q[v]);
+        }
+        if (tid == 0) {
+            pr.iters[b] = k;
+            pr.ok[b] = all ? 1 : 0;
+        }
+        __syncthreads();   // the next shot reuses shared memory
+    }
+}
+
+}  // namespace kern
+
+#define QLDPC_LAYERED_VARIANTS(X) X(6, true) X(7, true) X(8, true) X(8, false) X(16, false) X(32, false)
+
+template <class P>
+const void *layered_table(const KernelChoice &kc)
+{
+#define QLDPC_K(DCV, UNI)                                                                       \
+    if (kc.dc == DCV && kc.uniform == UNI) return reinterpret_cast<const void *>(&kern::msa_layered_kernel<P, DCV, UNI>);
+    QLDPC_LAYERED_VARIANTS(QLDPC_K)
+#undef QLDPC_K
+    return nullptr;
+}
+
+template <class P>
+cudaError_t layered_launch(const LaunchParams &p, const KernelChoice &kc, dim3 grid, int threads, size_t smem,
+                           cudaStream_t stream)
+{
+#define QLDPC_L(DCV, UNI)                                                                       \
+    if (kc.dc == DCV && kc.uniform == UNI) {                                                    \
+        kern::msa_layered_kernel<P, DCV, UNI><<<grid, threads, smem, stream>>>(p);              \
+        return cudaGetLastError();                                                              \
+    }
+    QLDPC_LAYERED_VARIANTS(QLDPC_L)
+#undef QLDPC_L
+    return cudaErrorInvalidValue;
+}
+
+const void *msa_kernel_layered(int precision, const KernelChoice &kc)
+{
+    return precision == kINT16 ? layered_table<kern::I16>(kc) : layered_table<kern::F32>(kc);
+}
+
+cudaError_t launch_msa_layered(int precision, const LaunchParams &p, const KernelChoice &kc, dim3 grid, int threads,
+                               size_t smem, cudaStream_t stream)
+{
+    return precision == kINT16 ? layered_launch<kern::I16>(p, kc, grid, threads, smem, stream)
+                               : layered_launch<kern::F32>(p, kc, grid, threads, smem, stream);
+}
+
+}  // namespace qldpc

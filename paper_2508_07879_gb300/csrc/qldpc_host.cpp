@@ -27,6 +27,7 @@ int dv_bucket(int d) { return d <= 4 ? 4 : d <= 8 ? 8 : d <= 16 ? 16 : -1; }
 
 const void *msa_kernel(int precision, const KernelChoice &kc)
 {
+    if (kc.layered) return msa_kernel_layered(precision, kc);
     if (kc.learned) return msa_kernel_learned(kc);
     return precision == kINT16 ? msa_kernel_i16(kc) : msa_kernel_f32(kc);
 }
@@ -35,6 +36,7 @@ cudaError_t launch_msa(const LaunchParams &p, int precision, const KernelChoice 
                        int grid_x, size_t smem, cudaStream_t stream)
 {
     dim3 grid(unsigned(grid_x), unsigned(p.nprob));
+    if (kc.layered) return launch_msa_layered(precision, p, kc, grid, threads, smem, stream);
     if (kc.learned) return launch_msa_learned(p, kc, grid, threads, smem, stream);
     return precision == kINT16 ? launch_msa_i16(p, kc, grid, threads, smem, stream)
                                : launch_msa_f32(p, kc, grid, threads, smem, stream);
@@ -56,6 +58,9 @@ struct HostLayout {
     std::vector<uint32_t> eslot;   // [nnz] slot j*m + i of CSR edge e
     std::vector<int32_t> slot_edge;// [dc_max * m] CSR edge of each slot, -1 for padding
     std::vector<uint32_t> ecol;    // [dc_max * m] caller's variable of each slot, ~0 for padding
+    std::vector<int32_t> layer_ptr;// [nlayers + 1] layered schedule
+    std::vector<uint32_t> layer_chk;// [m] checks ordered by (layer, index)
+    int32_t max_layer = 0;
 };
 
 int validate_and_layout(const int32_t *row_ptr, const int32_t *col_idx, int32_t m, int32_t n,
@@ -118,6 +123,27 @@ int validate_and_layout(const int32_t *row_ptr, const int32_t *col_idx, int32_t 
             out.ecol[sl] = uint32_t(col_idx[e]);
         }
     }
+    // Layered schedule: a check's layer is one more than the largest layer of an earlier check it
+    // shares a variable with, so checks of one layer share no variable and every pair of checks
+    // that does keeps its ascending order.
+    std::vector<int32_t> last(static_cast<size_t>(n), -1), layer(static_cast<size_t>(m), 0);
+    int32_t nlayers = 0;
+    for (int32_t i = 0; i < m; ++i) {
+        int32_t l = 0;
+        for (int32_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) l = std::max(l, last[size_t(col_idx[e])] + 1);
+        for (int32_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) last[size_t(col_idx[e])] = l;
+        layer[size_t(i)] = l;
+        nlayers = std::max(nlayers, l + 1);
+    }
+    out.layer_ptr.assign(size_t(nlayers) + 1, 0);
+    for (int32_t i = 0; i < m; ++i) out.layer_ptr[size_t(layer[size_t(i)]) + 1]++;
+    for (int32_t l = 0; l < nlayers; ++l) {
+        out.max_layer = std::max(out.max_layer, out.layer_ptr[size_t(l) + 1]);
+        out.layer_ptr[size_t(l) + 1] += out.layer_ptr[size_t(l)];
+    }
+    out.layer_chk.assign(size_t(m), 0u);
+    std::vector<int32_t> fillp(out.layer_ptr.begin(), out.layer_ptr.end() - 1);
+    for (int32_t i = 0; i < m; ++i) out.layer_chk[size_t(fillp[size_t(layer[size_t(i)])]++)] = uint32_t(i);
     return QLDPC_OK;
 }
 
@@ -255,6 +281,27 @@ int plan_batch(const qldpc_graph *const *gs, int nprob, int32_t batch, int preci
     return occupancy_grid(g0, k, pl.threads, smem, nprob, batch, g0->user_blocks_per_sm, pl.grid);
 }
 
+// Layered schedule: a block per shot with a thread per check of the largest layer (a multiple
+// of 32, at most 1024); the grid fills the SMs from occupancy.
+int plan_layered(const qldpc_graph *const *gs, int nprob, int32_t batch, int precision, Plan &pl)
+{
+    const qldpc_graph *g0 = gs[0];
+    size_t smem = 0;
+    int widest = 1;
+    for (int i = 0; i < nprob; ++i) {
+        smem = std::max(smem, layered_layout(gs[i]->m, gs[i]->n, gs[i]->dc_max, msg_bytes(precision)).total);
+        widest = std::max(widest, gs[i]->dg.max_layer);
+    }
+    pl.kc = variant(gs, nprob, false, false);
+    pl.kc.dvb = 0;
+    pl.kc.layered = true;
+    pl.threads = std::min(1024, round32(widest));
+    pl.smem = smem;
+    const void *k = msa_kernel(precision, pl.kc);
+    if (int rc = ensure_kernel_attrs(k, smem, g0->smem_optin)) return rc;
+    return occupancy_grid(g0, k, pl.threads, smem, nprob, batch, 0, pl.grid);
+}
+
 int check_device(const qldpc_graph *g)
 {
     int dev = -1;
@@ -267,9 +314,11 @@ int launch(const qldpc_graph *g0, const qldpc_graph *g1, const Problem *probs, i
            cudaStream_t stream)
 {
     if (precision != QLDPC_FP32 && precision != QLDPC_INT16) return QLDPC_ERR_INVALID_ARG;
-    if ((flags & ~uint32_t(QLDPC_NO_EARLY_STOP | QLDPC_LEARNED)) != 0) return QLDPC_ERR_INVALID_ARG;
+    if ((flags & ~uint32_t(QLDPC_NO_EARLY_STOP | QLDPC_LEARNED | QLDPC_LAYERED)) != 0) return QLDPC_ERR_INVALID_ARG;
     if (batch < 0 || max_iter < 0 || !finite_alpha(alpha)) return QLDPC_ERR_INVALID_ARG;
     const bool learned = (flags & QLDPC_LEARNED) != 0;
+    const bool layered = (flags & QLDPC_LAYERED) != 0;
+    if (learned && layered) return QLDPC_ERR_INVALID_ARG;
     if (learned) {   // FP32 weights, stop test on, weights set on every graph of the call
         if (precision != QLDPC_FP32 || (flags & QLDPC_NO_EARLY_STOP)) return QLDPC_ERR_INVALID_ARG;
         if (!g0->d_weights || !g1->d_weights) return QLDPC_ERR_INVALID_ARG;
@@ -294,9 +343,13 @@ int launch(const qldpc_graph *g0, const qldpc_graph *g1, const Problem *probs, i
     const qldpc_graph *gs[2] = {g0, g1};
     Plan pl;
     bool latency = false;
-    if (int rc = plan_latency(gs, nprob, batch, precision, learned, pl, latency)) return rc;
-    if (!latency)
-        if (int rc = plan_batch(gs, nprob, batch, precision, learned, pl)) return rc;
+    if (layered) {
+        if (int rc = plan_layered(gs, nprob, batch, precision, pl)) return rc;
+    } else {
+        if (int rc = plan_latency(gs, nprob, batch, precision, learned, pl, latency)) return rc;
+        if (!latency)
+            if (int rc = plan_batch(gs, nprob, batch, precision, learned, pl)) return rc;
+    }
     return cuda_status(launch_msa(p, precision, pl.kc, pl.threads, pl.grid, pl.smem, stream));
 }
 
@@ -443,14 +496,17 @@ int qldpc_graph_create(const int32_t *row_ptr, const int32_t *col_idx, int32_t m
         return QLDPC_ERR_UNSUPPORTED;
     }
 
-    // one device block: vslot | vdeg | rdeg | vperm | eslot | slot_edge | ecol
-    const size_t sizes[7] = {hl.vslot.size() * sizeof(uint32_t), size_t(n), size_t(m), size_t(n) * sizeof(uint32_t),
-                             hl.eslot.size() * sizeof(uint32_t), hl.slot_edge.size() * sizeof(int32_t),
-                             hl.ecol.size() * sizeof(uint32_t)};
-    const void *srcs[7] = {hl.vslot.data(), hl.vdeg.data(), hl.rdeg.data(), hl.vorder.data(),
-                           hl.eslot.data(), hl.slot_edge.data(), hl.ecol.data()};
-    size_t offs[7], total = 0;
-    for (int i = 0; i < 7; ++i) {
+    // one device block: vslot | vdeg | rdeg | vperm | eslot | slot_edge | ecol | layer_ptr | layer_chk
+    constexpr int kArrays = 9;
+    const size_t sizes[kArrays] = {hl.vslot.size() * sizeof(uint32_t), size_t(n), size_t(m),
+                                   size_t(n) * sizeof(uint32_t), hl.eslot.size() * sizeof(uint32_t),
+                                   hl.slot_edge.size() * sizeof(int32_t), hl.ecol.size() * sizeof(uint32_t),
+                                   hl.layer_ptr.size() * sizeof(int32_t), hl.layer_chk.size() * sizeof(uint32_t)};
+    const void *srcs[kArrays] = {hl.vslot.data(), hl.vdeg.data(), hl.rdeg.data(), hl.vorder.data(),
+                                 hl.eslot.data(), hl.slot_edge.data(), hl.ecol.data(),
+                                 hl.layer_ptr.data(), hl.layer_chk.data()};
+    size_t offs[kArrays], total = 0;
+    for (int i = 0; i < kArrays; ++i) {
         offs[i] = total;
         total += align16(std::max<size_t>(sizes[i], 1));
     }
@@ -460,7 +516,7 @@ int qldpc_graph_create(const int32_t *row_ptr, const int32_t *col_idx, int32_t m
         return cuda_status(e);
     }
     char *b = static_cast<char *>(g->d_block);
-    for (int i = 0; i < 7 && e == cudaSuccess; ++i)
+    for (int i = 0; i < kArrays && e == cudaSuccess; ++i)
         if (sizes[i]) e = cudaMemcpy(b + offs[i], srcs[i], sizes[i], cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(g->d_block);
@@ -474,6 +530,10 @@ int qldpc_graph_create(const int32_t *row_ptr, const int32_t *col_idx, int32_t m
     g->dg.eslot = reinterpret_cast<const uint32_t *>(b + offs[4]);
     g->dg.slot_edge = reinterpret_cast<const int32_t *>(b + offs[5]);
     g->dg.ecol = reinterpret_cast<const uint32_t *>(b + offs[6]);
+    g->dg.layer_ptr = reinterpret_cast<const int32_t *>(b + offs[7]);
+    g->dg.layer_chk = reinterpret_cast<const uint32_t *>(b + offs[8]);
+    g->dg.nlayers = int32_t(hl.layer_ptr.size()) - 1;
+    g->dg.max_layer = hl.max_layer;
     g->dg.nnz = g->nnz;
     g->dg.m = m;
     g->dg.n = n;

@@ -28,6 +28,7 @@ QLDPC_FP32 = 0
 QLDPC_INT16 = 1
 QLDPC_NO_EARLY_STOP = 1
 QLDPC_LEARNED = 2
+QLDPC_LAYERED = 4
 QLDPC_MAX_ROW_DEGREE = 32
 QLDPC_MAX_COL_DEGREE = 16
 QLDPC_MAX_CHECKS = 65535
@@ -245,19 +246,21 @@ class Graph:
             pass
 
 
-def _flags(early_stop: bool, learned: bool) -> int:
-    return (0 if early_stop else QLDPC_NO_EARLY_STOP) | (QLDPC_LEARNED if learned else 0)
+def _flags(early_stop: bool, learned: bool, layered: bool = False) -> int:
+    return ((0 if early_stop else QLDPC_NO_EARLY_STOP) | (QLDPC_LEARNED if learned else 0)
+            | (QLDPC_LAYERED if layered else 0))
 
 
 def decode(graph: Graph, syndromes, prior, max_iter: int, alpha: float = 0.75,
            precision: str = "fp32", early_stop: bool = True, want_post: bool = False,
-           out=None, stream=None, learned: bool = False):
+           out=None, stream=None, learned: bool = False, layered: bool = False):
     """Decode syndromes (CUDA uint8 [B, m]) with prior LLRs (CUDA float32 [n]).
 
     Returns (err uint8 [B, n], iters int32 [B], ok uint8 [B], post float32 [B, n] or None), all
     CUDA tensors, enqueued on ``stream`` (default: torch's current stream).  ``out`` may supply
     the four output tensors to avoid allocation.  ``learned``: the graph's learned weights first,
-    then plain min-sum for up to ``max_iter`` iterations on shots not yet decoded.
+    then plain min-sum for up to ``max_iter`` iterations on shots not yet decoded.  ``layered``:
+    the row-serial schedule instead of flooding.
     """
     import torch
     batch = int(syndromes.shape[0]) if syndromes.dim() == 2 else 0
@@ -269,7 +272,7 @@ def decode(graph: Graph, syndromes, prior, max_iter: int, alpha: float = 0.75,
         post = torch.empty((batch, graph.n), dtype=torch.float32, device=dev) if want_post else None
     else:
         err, iters, ok, post = out
-    flags = _flags(early_stop, learned)
+    flags = _flags(early_stop, learned, layered)
     check(qldpc_decode_ex(graph.handle,
                           _dev_ptr(syndromes, torch.uint8, (batch, graph.m), "syndromes"), batch,
                           _dev_ptr(prior, torch.float32, (graph.n,), "prior"), int(max_iter),
@@ -285,7 +288,7 @@ def decode(graph: Graph, syndromes, prior, max_iter: int, alpha: float = 0.75,
 
 def decode_pair(g_z: Graph, g_x: Graph, s_x, s_z, prior_x, prior_z, max_iter: int,
                 alpha: float = 0.75, precision: str = "fp32", early_stop: bool = True,
-                want_post: bool = False, stream=None, learned: bool = False):
+                want_post: bool = False, stream=None, learned: bool = False, layered: bool = False):
     """X and Z halves of a CSS syndrome round in one launch; returns two (err, iters, ok, post)."""
     import torch
     batch = int(s_x.shape[0])
@@ -297,7 +300,7 @@ def decode_pair(g_z: Graph, g_x: Graph, s_x, s_z, prior_x, prior_z, max_iter: in
                      torch.empty(batch, dtype=torch.uint8, device=dev),
                      torch.empty((batch, g.n), dtype=torch.float32, device=dev) if want_post else None))
     (ex, ix, ox, px), (ez, iz, oz, pz) = outs
-    flags = _flags(early_stop, learned)
+    flags = _flags(early_stop, learned, layered)
     check(qldpc_decode_pair(g_z.handle, g_x.handle,
                             _dev_ptr(s_x, torch.uint8, (batch, g_z.m), "s_x"),
                             _dev_ptr(s_z, torch.uint8, (batch, g_x.m), "s_z"), batch,
@@ -319,7 +322,7 @@ def decode_pair(g_z: Graph, g_x: Graph, s_x, s_z, prior_x, prior_z, max_iter: in
 
 def decode_host(graph: Graph, syndromes: np.ndarray, prior: np.ndarray, max_iter: int,
                 alpha: float = 0.75, precision: str = "fp32", early_stop: bool = True,
-                out=None, stream=None):
+                out=None, stream=None, layered: bool = False):
     """End-to-end decode from host (numpy) buffers; synchronous.  Returns (err, iters, ok) numpy.
 
     Pass page-locked arrays (e.g. ``torch.empty(..., pin_memory=True).numpy()``) for fast copies.
@@ -337,7 +340,7 @@ def decode_host(graph: Graph, syndromes: np.ndarray, prior: np.ndarray, max_iter
         ok = np.empty(batch, dtype=np.uint8)
     else:
         err, iters, ok = out
-    flags = 0 if early_stop else QLDPC_NO_EARLY_STOP
+    flags = _flags(early_stop, False, layered)
     sh = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
     check(qldpc_decode_host(graph.handle, _np_ptr(syn), batch, _np_ptr(pr), int(max_iter),
                             float(alpha), _np_ptr(err), _np_ptr(iters), _np_ptr(ok),

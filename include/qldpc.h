@@ -158,6 +158,10 @@ QLDPC_API int qldpc_decode(const qldpc_graph *g, const uint8_t *syndromes, int32
  * (cudaStream_t cast to void*, NULL = legacy default stream) and an optional device output
  *   out_post  float[batch*n] or NULL: the a-posteriori LLR Q_n of the last iteration run
  *             (INT16: the fixed-point value / 256, exact).
+ * A batch with more shots than the launch's resident blocks hands shots out dynamically: blocks
+ * claim them from one of 1024 counter pairs held by the graph, zeroed on `stream` before the
+ * launch (results do not depend on the order).  Only more than 1024 such decodes of one graph in
+ * flight at once on different streams could share a pair.
  * With QLDPC_LAYERED the schedule is row-serial (see the flag): same outputs and stop rule; INT16
  * keeps Q in 32 bits and clamps q = Q - r to +-32767.  Its launch shape is chosen automatically
  * (qldpc_graph_set_launch does not apply).

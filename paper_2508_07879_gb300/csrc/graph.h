@@ -2,6 +2,7 @@
 // units (qldpc_host.cpp: graphs and decodes; qldpc_server.cpp: the persistent server).  Internal.
 #pragma once
 
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
 #include <mutex>
@@ -19,6 +20,8 @@ struct qldpc_graph {
     int32_t m = 0, n = 0, nnz = 0, dc_max = 0, dv_max = 0;
     bool uniform_rows = false;  // every row has degree dc_max
     void *d_block = nullptr;    // one device allocation for all graph arrays
+    int32_t *d_counters = nullptr;              // [kShotCounterSlots][2] shot counters (inside d_block)
+    mutable std::atomic<uint32_t> counter_seq{0};
     qldpc::DeviceGraph dg{};
     // launch overrides (0 = automatic)
     int user_kernel = QLDPC_KERNEL_AUTO, user_threads = 0, user_blocks_per_sm = 0;

@@ -305,7 +305,20 @@ __global__ void __launch_bounds__(1024, 1) msa_batch_kernel(const LaunchParams p
 
     const bool early = LEARNED || (p.flags & kFlagNoEarlyStop) == 0;
     const size_t wstride = size_t(pr.g.dc_max) * M;   // learned weights of one iteration
-    for (int b = blockIdx.x; b < p.batch; b += gridDim.x) {
+    // Shots are claimed one at a time from a per-launch counter, so blocks that draw slowly
+    // converging shots take fewer of them (or taken statically when no counter is given).
+    // (Two claim words alternate: a thread reads word k&1 after claim k's barrier, and the word is
+    // rewritten only after claim k+1's barrier, which every thread reaches after its read.)
+    __shared__ int s_shot[2];
+    int claim = 0;
+    for (int b = blockIdx.x;; b += gridDim.x) {
+        if (p.next_shot) {
+            if (tid == 0) s_shot[claim] = atomicAdd(p.next_shot + blockIdx.y, 1);
+            __syncthreads();
+            b = s_shot[claim];
+            claim ^= 1;
+        }
+        if (b >= p.batch) break;
         uint8_t *err = pr.err + size_t(b) * N;
         if (bad) {   // non-finite prior: report the shot as not decoded
             for (int v = tid; v < N; v += T) {

@@ -50,7 +50,13 @@ struct LaunchParams {
     float alpha;             // FP32 scale
     int32_t alpha_q;         // INT16 scale, round(alpha * 2^15)
     uint32_t flags;
+    int32_t *next_shot;      // batch and layered kernels: zeroed per-launch shot counters
+                             // [blockIdx.y], claimed with atomicAdd; nullptr: shots b = blockIdx.x + k*gridDim.x
 };
+
+// Counters for dynamic shot claiming: a ring per graph, one pair per launch, zeroed in-stream
+// before the launch, so launches in flight on different streams use different pairs.
+constexpr int kShotCounterSlots = 1024;
 
 constexpr uint32_t kFlagNoEarlyStop = 1u;
 

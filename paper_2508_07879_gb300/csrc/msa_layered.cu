@@ -88,7 +88,16 @@ __global__ void __launch_bounds__(1024, 1) msa_layered_kernel(const LaunchParams
     for (int v = tid; v < N; v += T) bad |= !isfinite(pr.prior[v]);
     bad = __syncthreads_or(bad);
     const bool early = (p.flags & kFlagNoEarlyStop) == 0;
-    for (int b = blockIdx.x; b < p.batch; b += gridDim.x) {
+    __shared__ int s_shot[2];   // alternating claim words, as in the batch kernel
+    int claim = 0;
+    for (int b = blockIdx.x;; b += gridDim.x) {
+        if (p.next_shot) {   // dynamic claiming from a per-launch counter
+            if (tid == 0) s_shot[claim] = atomicAdd(p.next_shot + blockIdx.y, 1);
+            __syncthreads();
+            b = s_shot[claim];
+            claim ^= 1;
+        }
+        if (b >= p.batch) break;
         uint8_t *err = pr.err + size_t(b) * N;
         if (bad) {   // non-finite prior: report the shot as not decoded
             for (int v = tid; v < N; v += T) {

@@ -341,6 +341,7 @@ int launch(const qldpc_graph *g0, const qldpc_graph *g1, const Problem *probs, i
 
     // One kernel variant and one block shape serve both problems of a pair.
     const qldpc_graph *gs[2] = {g0, g1};
+    cudaStream_t st = stream;
     Plan pl;
     bool latency = false;
     if (layered) {
@@ -350,7 +351,12 @@ int launch(const qldpc_graph *g0, const qldpc_graph *g1, const Problem *probs, i
         if (!latency)
             if (int rc = plan_batch(gs, nprob, batch, precision, learned, pl)) return rc;
     }
-    return cuda_status(launch_msa(p, precision, pl.kc, pl.threads, pl.grid, pl.smem, stream));
+    if (!latency && pl.grid < batch) {
+        // more shots than blocks: claim them dynamically from a zeroed counter pair of the ring
+        p.next_shot = g0->d_counters + 2 * size_t(g0->counter_seq.fetch_add(1) % kShotCounterSlots);
+        if (cudaError_t e = cudaMemsetAsync(p.next_shot, 0, 2 * sizeof(int32_t), st)) return cuda_status(e);
+    }
+    return cuda_status(launch_msa(p, precision, pl.kc, pl.threads, pl.grid, pl.smem, st));
 }
 
 Problem make_problem(const qldpc_graph *g, const uint8_t *syn, const float *prior, uint8_t *err,
@@ -496,15 +502,17 @@ int qldpc_graph_create(const int32_t *row_ptr, const int32_t *col_idx, int32_t m
         return QLDPC_ERR_UNSUPPORTED;
     }
 
-    // one device block: vslot | vdeg | rdeg | vperm | eslot | slot_edge | ecol | layer_ptr | layer_chk
-    constexpr int kArrays = 9;
+    // one device block: vslot | vdeg | rdeg | vperm | eslot | slot_edge | ecol | layer_ptr | layer_chk |
+    // shot counters
+    constexpr int kArrays = 10;
     const size_t sizes[kArrays] = {hl.vslot.size() * sizeof(uint32_t), size_t(n), size_t(m),
                                    size_t(n) * sizeof(uint32_t), hl.eslot.size() * sizeof(uint32_t),
                                    hl.slot_edge.size() * sizeof(int32_t), hl.ecol.size() * sizeof(uint32_t),
-                                   hl.layer_ptr.size() * sizeof(int32_t), hl.layer_chk.size() * sizeof(uint32_t)};
+                                   hl.layer_ptr.size() * sizeof(int32_t), hl.layer_chk.size() * sizeof(uint32_t),
+                                   size_t(kShotCounterSlots) * 2 * sizeof(int32_t)};
     const void *srcs[kArrays] = {hl.vslot.data(), hl.vdeg.data(), hl.rdeg.data(), hl.vorder.data(),
                                  hl.eslot.data(), hl.slot_edge.data(), hl.ecol.data(),
-                                 hl.layer_ptr.data(), hl.layer_chk.data()};
+                                 hl.layer_ptr.data(), hl.layer_chk.data(), nullptr};
     size_t offs[kArrays], total = 0;
     for (int i = 0; i < kArrays; ++i) {
         offs[i] = total;
@@ -517,7 +525,7 @@ int qldpc_graph_create(const int32_t *row_ptr, const int32_t *col_idx, int32_t m
     }
     char *b = static_cast<char *>(g->d_block);
     for (int i = 0; i < kArrays && e == cudaSuccess; ++i)
-        if (sizes[i]) e = cudaMemcpy(b + offs[i], srcs[i], sizes[i], cudaMemcpyHostToDevice);
+        if (sizes[i] && srcs[i]) e = cudaMemcpy(b + offs[i], srcs[i], sizes[i], cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(g->d_block);
         delete g;
@@ -532,6 +540,7 @@ int qldpc_graph_create(const int32_t *row_ptr, const int32_t *col_idx, int32_t m
     g->dg.ecol = reinterpret_cast<const uint32_t *>(b + offs[6]);
     g->dg.layer_ptr = reinterpret_cast<const int32_t *>(b + offs[7]);
     g->dg.layer_chk = reinterpret_cast<const uint32_t *>(b + offs[8]);
+    g->d_counters = reinterpret_cast<int32_t *>(b + offs[9]);
     g->dg.nlayers = int32_t(hl.layer_ptr.size()) - 1;
     g->dg.max_layer = hl.max_layer;
     g->dg.nnz = g->nnz;

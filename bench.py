@@ -67,7 +67,7 @@ ALU_LANES_PER_SM = 128          # FP32/INT32 lanes per SM, one operation per lan
 
 # DRAM traffic of one decoder launch from an ncu capture, valid only for the kernel source it was
 # measured on (profiles/msa_batch_lp1054_b65536_fp32.md); reported as null once the source changes.
-NCU_TRAFFIC = {"source_sha16": "d3c189be4fcec1c0", "bytes_per_launch": 30633472 + 15043584,
+NCU_TRAFFIC = {"source_sha16": "77aecb5b5fe69bbe", "bytes_per_launch": 30527232 + 13783296,
                "profile": "profiles/msa_batch_lp1054_b65536_fp32.md"}
 
 WORKLOAD = "LP-1054 H_Z (465x1054, E=3720), iid X noise p=0.01..0.05, B=65536/step, max 50 it, alpha 0.75"
@@ -529,6 +529,8 @@ def measure_layered(qldpc, graph, code, syn_d, pri_d, out, stream, B, args, step
     res["ms_per_step"] = ms
     res["mean_iters"] = iters / (len(syn_d) * B)
     res["decoded_fraction"] = ok / (len(syn_d) * B)
+    if args.no_latency:
+        return res
     # single shot, launch path: the shots of the flooding latency measurement
     shots = args.latency_shots
     warm = min(LAT_WARMUP, max(shots // 10, 10))

@@ -58,15 +58,18 @@ def _load():
                 f = getattr(lib, name)
                 f.argtypes = [p, p, i32, i32, p, i32, p, i32, real, u32, p, p, p, p, p]
                 f.restype = ctypes.c_int
-            lib.oracle_msa_i16.argtypes = [p, p, i32, i32, p, i32, p, i32, ctypes.c_float, u32,
-                                           p, p, p, p, p]
-            lib.oracle_msa_i16.restype = ctypes.c_int
+            for name in ("oracle_msa_i16", "oracle_msa_i8"):
+                f = getattr(lib, name)
+                f.argtypes = [p, p, i32, i32, p, i32, p, i32, ctypes.c_float, u32, p, p, p, p, p]
+                f.restype = ctypes.c_int
             for name, real in (("oracle_layered_f64", ctypes.c_double), ("oracle_layered_f32", ctypes.c_float)):
                 f = getattr(lib, name)
                 f.argtypes = [p, p, i32, i32, p, i32, p, i32, real, u32, p, p, p, p]
                 f.restype = ctypes.c_int
-            lib.oracle_layered_i16.argtypes = [p, p, i32, i32, p, i32, p, i32, ctypes.c_float, u32, p, p, p, p]
-            lib.oracle_layered_i16.restype = ctypes.c_int
+            for name in ("oracle_layered_i16", "oracle_layered_i8"):
+                f = getattr(lib, name)
+                f.argtypes = [p, p, i32, i32, p, i32, p, i32, ctypes.c_float, u32, p, p, p, p]
+                f.restype = ctypes.c_int
             lib.oracle_alpha_q.argtypes = [ctypes.c_float]
             lib.oracle_alpha_q.restype = ctypes.c_int
             for name in ("oracle_nms_train_f64", "oracle_nms_train_f32"):
@@ -94,12 +97,12 @@ def msa(row_ptr, col_idx, m: int, n: int, syndromes, prior, max_iter: int, alpha
     """Decode a batch with Algorithm 1 (schedule "flooding") or its row-serial variant ("layered").
 
     row_ptr/col_idx: H in CSR (int32).  syndromes: uint8 [B, m].  prior: [n] LLRs gamma_n.
-    precision: "f64", "f32" or "i16".  Returns a dict with
+    precision: "f64", "f32", "i16" or "i8".  Returns a dict with
       err   uint8 [B, n]  decisions e_hat
       iters int32 [B]     CN+VN rounds run
       ok    uint8 [B]     1 iff H e_hat^T = s
       post  [B, n]        a-posteriori LLR Q_n of the last iteration (float64 / float32; for i16
-                          the raw 32-bit fixed-point value, LLR = post / 256)
+                          and i8 the raw 32-bit fixed-point value, LLR = post / 256 or post / 4)
       margin float64 [B]  smallest |q| or |Q| the shot produced (near-tie diagnostic; flooding only)
     """
     if schedule == "layered":
@@ -117,6 +120,8 @@ def msa(row_ptr, col_idx, m: int, n: int, syndromes, prior, max_iter: int, alpha
         fn, pdt, post_dt, alpha_c = lib.oracle_msa_f32, np.float32, np.float32, float(np.float32(alpha))
     elif precision == "i16":
         fn, pdt, post_dt, alpha_c = lib.oracle_msa_i16, np.float32, np.int32, float(np.float32(alpha))
+    elif precision == "i8":
+        fn, pdt, post_dt, alpha_c = lib.oracle_msa_i8, np.float32, np.int32, float(np.float32(alpha))
     else:
         raise ValueError(f"unknown precision {precision!r}")
     prior = np.ascontiguousarray(prior, dtype=pdt).reshape(n)
@@ -159,6 +164,8 @@ def _layered(row_ptr, col_idx, m, n, syndromes, prior, max_iter, alpha, precisio
         fn, pdt, post_dt, alpha_c = lib.oracle_layered_f32, np.float32, np.float32, float(np.float32(alpha))
     elif precision == "i16":
         fn, pdt, post_dt, alpha_c = lib.oracle_layered_i16, np.float32, np.int32, float(np.float32(alpha))
+    elif precision == "i8":
+        fn, pdt, post_dt, alpha_c = lib.oracle_layered_i8, np.float32, np.int32, float(np.float32(alpha))
     else:
         raise ValueError(f"unknown precision {precision!r}")
     prior = np.ascontiguousarray(prior, dtype=pdt).reshape(n)

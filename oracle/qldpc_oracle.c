@@ -34,7 +34,8 @@
  *     (the paper's timed runs use 10 fixed iterations, Sec. 3) and ok reports H e = s at the end.
  *   - CN messages are formed as sign * (alpha * min): the product alpha * min is rounded first.
  *
- * Precisions: f64 and f32 run the steps above in that type.  i16 is the fixed-point reading of
+ * Precisions: f64 and f32 run the steps above in that type.  i8 is i16 below with 2 fractional
+ * bits and messages saturated to +-127 (the paper names 8-bit integers without a scheme).  i16 is the fixed-point reading of
  * the paper's integer proposal (Table 1, Sec. 3 outlook): LLRs carry 8 fractional bits,
  *   gamma_q = clamp(round_half_away(gamma * 256), -32767, 32767),
  *   alpha_q = round_half_away(alpha * 32768) with 1 <= alpha_q <= 32768,
@@ -192,25 +193,27 @@ DEFINE_MSA_REAL(oracle_msa_f64, double, fabs)
 DEFINE_MSA_REAL(oracle_msa_f32, float, fabsf)
 
 /* ---------------------------------------------------------------------------------------------
- * 16-bit fixed-point decoder (8 fractional bits, 32-bit accumulation).
+ * Fixed-point decoders with 32-bit accumulation: i16 (8 fractional bits, messages within
+ * +-32767) and i8 (2 fractional bits, messages within +-127).
  * ------------------------------------------------------------------------------------------- */
-static int32_t clamp16(int64_t x)
+static int32_t clampq(int64_t x, int32_t lim)
 {
-    if (x > 32767) return 32767;
-    if (x < -32767) return -32767;
+    if (x > lim) return lim;
+    if (x < -lim) return -lim;
     return (int32_t)x;
 }
 
-/* gamma_q = clamp(round_half_away(gamma * 256)); returns 0 on a non-finite gamma */
-static int quantize_prior(float g, int32_t *out)
+/* gamma_q = clamp(round_half_away(gamma * 2^frac), -lim, lim); returns 0 on a non-finite gamma */
+static int quantize_fixed(float g, int frac, int32_t lim, int32_t *out)
 {
     if (!isfinite(g)) return 0;
-    float t = roundf(g * 256.0f);          /* roundf rounds halves away from zero */
-    if (t > 32767.0f) t = 32767.0f;
-    if (t < -32767.0f) t = -32767.0f;
+    float t = roundf(g * (float)(1 << frac));   /* exact scaling; roundf rounds halves away from zero */
+    if (t > (float)lim) t = (float)lim;
+    if (t < -(float)lim) t = -(float)lim;
     *out = (int32_t)t;
     return 1;
 }
+
 
 int oracle_alpha_q(float alpha)
 {
@@ -219,10 +222,10 @@ int oracle_alpha_q(float alpha)
     return (a >= 1 && a <= 32768) ? a : -1;
 }
 
-int oracle_msa_i16(const int32_t *row_ptr, const int32_t *col_idx, int32_t m, int32_t n,
-                   const uint8_t *syn, int32_t batch, const float *prior, int32_t max_iter,
-                   float alpha, uint32_t flags, uint8_t *out_err, int32_t *out_iters,
-                   uint8_t *out_ok, int32_t *out_post_q, double *out_margin)
+static int msa_fixed(const int32_t *row_ptr, const int32_t *col_idx, int32_t m, int32_t n,
+                     const uint8_t *syn, int32_t batch, const float *prior, int32_t max_iter,
+                     float alpha, uint32_t flags, uint8_t *out_err, int32_t *out_iters,
+                     uint8_t *out_ok, int32_t *out_post_q, double *out_margin, int frac, int32_t lim)
 {
     if (batch < 0 || max_iter < 0 || !syn || !prior || !out_err || !out_iters || !out_ok)
         return ORACLE_BAD_ARG;
@@ -241,7 +244,7 @@ int oracle_msa_i16(const int32_t *row_ptr, const int32_t *col_idx, int32_t m, in
         return ORACLE_NO_MEMORY;
     }
     for (int32_t v = 0; v < n; ++v)
-        if (!quantize_prior(prior[v], &gq[v])) {
+        if (!quantize_fixed(prior[v], frac, lim, &gq[v])) {
             free(gq); free(q); free(r); free(post); tanner_free(&t);
             return ORACLE_BAD_ARG;
         }
@@ -277,7 +280,7 @@ int oracle_msa_i16(const int32_t *row_ptr, const int32_t *col_idx, int32_t m, in
                         int64_t acc = gq[v];
                         for (int32_t bb = t.vptr[v]; bb < t.vptr[v + 1]; ++bb)
                             if (bb != a) acc += r[t.vedge[bb]];
-                        q[t.vedge[a]] = clamp16(acc);
+                        q[t.vedge[a]] = clampq(acc, lim);
                         if (llabs((long long)q[t.vedge[a]]) < margin) margin = llabs((long long)q[t.vedge[a]]);
                     }
                 for (int32_t v = 0; v < n; ++v) {
@@ -295,10 +298,30 @@ int oracle_msa_i16(const int32_t *row_ptr, const int32_t *col_idx, int32_t m, in
         out_iters[b] = iters;
         out_ok[b] = (uint8_t)met;
         if (out_post_q) memcpy(out_post_q + (size_t)b * n, post, sizeof(int32_t) * (size_t)n);
-        if (out_margin) out_margin[b] = (double)margin / 256.0;
+        if (out_margin) out_margin[b] = (double)margin / (double)(1 << frac);
     }
     free(gq); free(q); free(r); free(post); tanner_free(&t);
     return ORACLE_OK;
+}
+
+int oracle_msa_i16(const int32_t *row_ptr, const int32_t *col_idx, int32_t m, int32_t n,
+                   const uint8_t *syn, int32_t batch, const float *prior, int32_t max_iter,
+                   float alpha, uint32_t flags, uint8_t *out_err, int32_t *out_iters,
+                   uint8_t *out_ok, int32_t *out_post_q, double *out_margin)
+{
+    return msa_fixed(row_ptr, col_idx, m, n, syn, batch, prior, max_iter, alpha, flags, out_err, out_iters,
+                     out_ok, out_post_q, out_margin, 8, 32767);
+}
+
+/* i8: LLRs with 2 fractional bits (a quarter), messages saturated to +-127 (+-31.75), Q in 32 bits,
+ * alpha_q and |r| = floor(min * alpha_q / 2^15) as for i16. */
+int oracle_msa_i8(const int32_t *row_ptr, const int32_t *col_idx, int32_t m, int32_t n,
+                  const uint8_t *syn, int32_t batch, const float *prior, int32_t max_iter,
+                  float alpha, uint32_t flags, uint8_t *out_err, int32_t *out_iters,
+                  uint8_t *out_ok, int32_t *out_post_q, double *out_margin)
+{
+    return msa_fixed(row_ptr, col_idx, m, n, syn, batch, prior, max_iter, alpha, flags, out_err, out_iters,
+                     out_ok, out_post_q, out_margin, 2, 127);
 }
 
 /* ---------------------------------------------------------------------------------------------
@@ -374,10 +397,10 @@ int NAME(const int32_t *row_ptr, const int32_t *col_idx, int32_t m, int32_t n,  
 DEFINE_LAYERED_REAL(oracle_layered_f64, double, fabs)
 DEFINE_LAYERED_REAL(oracle_layered_f32, float, fabsf)
 
-int oracle_layered_i16(const int32_t *row_ptr, const int32_t *col_idx, int32_t m, int32_t n,
-                       const uint8_t *syn, int32_t batch, const float *prior, int32_t max_iter,
-                       float alpha, uint32_t flags, uint8_t *out_err, int32_t *out_iters,
-                       uint8_t *out_ok, int32_t *out_post_q)
+static int layered_fixed(const int32_t *row_ptr, const int32_t *col_idx, int32_t m, int32_t n,
+                         const uint8_t *syn, int32_t batch, const float *prior, int32_t max_iter,
+                         float alpha, uint32_t flags, uint8_t *out_err, int32_t *out_iters,
+                         uint8_t *out_ok, int32_t *out_post_q, int frac, int32_t lim)
 {
     if (batch < 0 || max_iter < 0 || !syn || !prior || !out_err || !out_iters || !out_ok)
         return ORACLE_BAD_ARG;
@@ -396,7 +419,7 @@ int oracle_layered_i16(const int32_t *row_ptr, const int32_t *col_idx, int32_t m
         return ORACLE_NO_MEMORY;
     }
     for (int32_t v = 0; v < n; ++v)
-        if (!quantize_prior(prior[v], &gq[v])) {
+        if (!quantize_fixed(prior[v], frac, lim, &gq[v])) {
             free(gq); free(Q); free(q); free(r); free(rn); tanner_free(&t);
             return ORACLE_BAD_ARG;
         }
@@ -411,7 +434,7 @@ int oracle_layered_i16(const int32_t *row_ptr, const int32_t *col_idx, int32_t m
             for (int32_t k = 1; k <= max_iter; ++k) {
                 for (int32_t c = 0; c < m; ++c) {
                     for (int32_t i = row_ptr[c]; i < row_ptr[c + 1]; ++i)
-                        q[i] = clamp16((int64_t)Q[col_idx[i]] - r[i]);
+                        q[i] = clampq((int64_t)Q[col_idx[i]] - r[i], lim);
                     for (int32_t i = row_ptr[c]; i < row_ptr[c + 1]; ++i) {
                         int neg = s[c] & 1;
                         int32_t mn = INT32_MAX;
@@ -441,6 +464,24 @@ int oracle_layered_i16(const int32_t *row_ptr, const int32_t *col_idx, int32_t m
     }
     free(gq); free(Q); free(q); free(r); free(rn); tanner_free(&t);
     return ORACLE_OK;
+}
+
+int oracle_layered_i16(const int32_t *row_ptr, const int32_t *col_idx, int32_t m, int32_t n,
+                       const uint8_t *syn, int32_t batch, const float *prior, int32_t max_iter,
+                       float alpha, uint32_t flags, uint8_t *out_err, int32_t *out_iters,
+                       uint8_t *out_ok, int32_t *out_post_q)
+{
+    return layered_fixed(row_ptr, col_idx, m, n, syn, batch, prior, max_iter, alpha, flags, out_err, out_iters,
+                         out_ok, out_post_q, 8, 32767);
+}
+
+int oracle_layered_i8(const int32_t *row_ptr, const int32_t *col_idx, int32_t m, int32_t n,
+                      const uint8_t *syn, int32_t batch, const float *prior, int32_t max_iter,
+                      float alpha, uint32_t flags, uint8_t *out_err, int32_t *out_iters,
+                      uint8_t *out_ok, int32_t *out_post_q)
+{
+    return layered_fixed(row_ptr, col_idx, m, n, syn, batch, prior, max_iter, alpha, flags, out_err, out_iters,
+                         out_ok, out_post_q, 2, 127);
 }
 
 /* ---------------------------------------------------------------------------------------------

@@ -13,6 +13,7 @@ Printed as one JSON line on rank 0:
                the launch path (qldpc_decode_host) and the persistent server (qldpc_server_*)
   serving      the persistent server under a 40/40/20 mix of the N=400, 1054 and 288 codes with
                Poisson arrivals 20 us apart: latency percentiles and the saturated request rate
+  precisions   the same batches decoded in FP32, INT16 and INT8 (device throughput, decoded fraction)
   layered      the row-serial (layered) schedule on the same batches and shots: device throughput,
                mean iterations, decode success, and single-shot latency through qldpc_decode_host
   learned      the learned (neural) min-sum on the same code: training time and kernel times on
@@ -89,6 +90,7 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-layered", action="store_true")
+    ap.add_argument("--no-precisions", action="store_true")
     ap.add_argument("--learned-train-shots", type=int, default=LEARN_SHOTS)
     ap.add_argument("--learned-eval-shots", type=int, default=LEARN_EVAL)
     return ap.parse_args()
@@ -339,6 +341,9 @@ def run_ours(args, rank, world, local):
     serving = None
     if not args.no_serving and rank == 0:
         serving = measure_serving(qldpc, args)
+    precisions = None
+    if not args.no_precisions and rank == 0:
+        precisions = measure_precisions(qldpc, graph, syn_d, pri_d, out, stream, B, args)
     layered_res = None
     if not args.no_layered and rank == 0:
         layered_res = measure_layered(qldpc, graph, code, syn_d, pri_d, out, stream, B, args)
@@ -366,6 +371,7 @@ def run_ours(args, rank, world, local):
             "e2e": e2e,
             "latency": latency,
             "serving": serving,
+            "precisions": precisions,
             "layered": layered_res,
             "learned": learned_res,
             "gpu_launches": launches,
@@ -494,6 +500,35 @@ def measure_serving(qldpc, args):
                      "p999_us": float(np.percentile(x, 99.9)), "per_code": per,
                      "saturated_shots_per_s": n / dt}
     return out
+
+
+def measure_precisions(qldpc, graph, syn_d, pri_d, out, stream, B, args, steps=100):
+    """Flooding decode of the benchmark's batches in each precision: throughput and decoded fraction."""
+    import torch
+    res = {}
+    for prec in ("fp32", "int16", "int8"):
+        ok = iters = 0
+        with torch.cuda.stream(stream):
+            for j in range(len(syn_d)):
+                qldpc.decode(graph, syn_d[j], pri_d[j], MAX_ITER, ALPHA, prec, out=out, stream=stream)
+                stream.synchronize()
+                ok += int(out[2].to(torch.int64).sum().item())
+                iters += int(out[1].to(torch.int64).sum().item())
+            for i in range(5):
+                qldpc.decode(graph, syn_d[i % len(syn_d)], pri_d[i % len(syn_d)], MAX_ITER, ALPHA, prec, out=out,
+                             stream=stream)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            stream.synchronize()
+            e0.record(stream)
+            for i in range(steps):
+                j = i % len(syn_d)
+                qldpc.decode(graph, syn_d[j], pri_d[j], MAX_ITER, ALPHA, prec, out=out, stream=stream)
+            e1.record(stream)
+            stream.synchronize()
+        res[prec] = {"value": B * steps / (e0.elapsed_time(e1) / 1e3), "unit": "syndromes/s",
+                     "decoded_fraction": ok / (len(syn_d) * B), "mean_iters": iters / (len(syn_d) * B)}
+    return res
 
 
 def measure_layered(qldpc, graph, code, syn_d, pri_d, out, stream, B, args, steps=100):

@@ -24,6 +24,8 @@
  *               gamma_q = clamp(round_half_away(gamma*256), +-32767); alpha_q = round(alpha*2^15);
  *               |r| = floor(min*alpha_q/2^15); q = clamp(32-bit sum, +-32767); Q in 32 bits.
  *               Requires 0 < alpha <= 1.
+ *   QLDPC_INT8  the same with 2 fractional bits and +-127 (8-bit messages; the paper names 8-bit
+ *               integers without a scheme): gamma_q = clamp(round_half_away(gamma*4), +-127).
  *
  * Memory and ownership: graph arrays live on the device and are owned by the qldpc_graph.
  * Every buffer passed to qldpc_decode* is caller-owned DEVICE memory (e.g. torch tensors) unless
@@ -67,7 +69,10 @@ typedef enum qldpc_status {
     QLDPC_ERR_TIMEOUT = -5        /* a bounded device-side wait expired */
 } qldpc_status;
 
-enum { QLDPC_FP32 = 0, QLDPC_INT16 = 1 };
+/* Message precision.  FP32: Algorithm 1 in binary32.  INT16: LLRs in fixed point with 8 fractional
+ * bits, messages clamped to +-32767, sums in 32 bits, alpha as round(alpha * 2^15) / 2^15.  INT8: the
+ * same with 2 fractional bits and messages clamped to +-127 (LLRs within +-31.75). */
+enum { QLDPC_FP32 = 0, QLDPC_INT16 = 1, QLDPC_INT8 = 2 };
 
 /* Decode flags (bitwise OR). */
 enum {
@@ -154,7 +159,7 @@ QLDPC_API int qldpc_decode(const qldpc_graph *g, const uint8_t *syndromes, int32
                  uint8_t *out_err, int32_t *out_iters, uint8_t *out_ok);
 
 /*
- * qldpc_decode with a precision (QLDPC_FP32 / QLDPC_INT16), flags, a CUDA stream
+ * qldpc_decode with a precision (QLDPC_FP32 / QLDPC_INT16 / QLDPC_INT8), flags, a CUDA stream
  * (cudaStream_t cast to void*, NULL = legacy default stream) and an optional device output
  *   out_post  float[batch*n] or NULL: the a-posteriori LLR Q_n of the last iteration run
  *             (INT16: the fixed-point value / 256, exact).
@@ -225,7 +230,7 @@ typedef struct qldpc_server qldpc_server;
 enum { QLDPC_SERVER_MAX_CODES = 4 };
 
 typedef struct qldpc_server_config {
-    int32_t precision;            /* QLDPC_FP32 or QLDPC_INT16 */
+    int32_t precision;            /* QLDPC_FP32 or QLDPC_INT16 (the server has no INT8 kernels) */
     int32_t max_iter;             /* >= 0 */
     float alpha;                  /* as for qldpc_decode_ex */
     uint32_t flags;               /* QLDPC_NO_EARLY_STOP, or QLDPC_LEARNED (FP32: every code whose

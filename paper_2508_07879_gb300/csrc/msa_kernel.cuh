@@ -53,6 +53,7 @@ struct F32 {
     // is -0 only when every term is), so the sign bit of a message equals [message < 0].
     static __device__ __forceinline__ acc_t quantize(float g) { return __fadd_rn(g, 0.0f); }
     static __device__ __forceinline__ acc_t add(acc_t a, acc_t b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ acc_t sub_q(acc_t Q, acc_t r) { return __fsub_rn(Q, r); }   // layered q
     static __device__ __forceinline__ bool neg(float x) { return x < 0.0f; }
     static __device__ __forceinline__ mag_t mag(acc_t x) { return fabsf(x); }
     static __device__ __forceinline__ mag_t mag_init() { return __int_as_float(0x7f800000); }
@@ -74,18 +75,23 @@ struct F32 {
     static __device__ __forceinline__ msg_t to_msg(acc_t q) { return q; }
 };
 
-struct I16 {
+// Fixed point with 32-bit accumulation: LLR * 2^FRAC, messages clamped to +-LIM.
+//   I16: 8 fractional bits, +-32767;  I8: 2 fractional bits, +-127.
+template <class MSG, int FRAC, int LIM>
+struct IFix {
     using acc_t = int32_t;
     using mag_t = int32_t;
-    using msg_t = int16_t;
-    // gamma_q = clamp(round_half_away(gamma * 2^8), -32767, 32767); gamma*256 is exact in binary32
+    using msg_t = MSG;
+    // gamma_q = clamp(round_half_away(gamma * 2^FRAC), -LIM, LIM); the scaling is exact in binary32
     static __device__ __forceinline__ acc_t quantize(float g)
     {
-        float t = roundf(g * 256.0f);
-        t = fminf(fmaxf(t, -32767.0f), 32767.0f);
+        float t = roundf(g * float(1 << FRAC));
+        t = fminf(fmaxf(t, -float(LIM)), float(LIM));
         return static_cast<int32_t>(t);
     }
     static __device__ __forceinline__ acc_t add(acc_t a, acc_t b) { return a + b; }
+    // layered schedule: q = clamp(Q - r)
+    static __device__ __forceinline__ acc_t sub_q(acc_t Q, acc_t r) { return max(-LIM, min(LIM, Q - r)); }
     static __device__ __forceinline__ bool neg(int32_t x) { return x < 0; }
     static __device__ __forceinline__ mag_t mag(acc_t x) { return abs(x); }
     static __device__ __forceinline__ mag_t mag_init() { return 0x7fffffff; }
@@ -102,9 +108,11 @@ struct I16 {
         const int32_t neg = int32_t(negall ^ (uint32_t(x) >> 31));   // 0 or 1
         return (m ^ -neg) + neg;
     }
-    static __device__ __forceinline__ float post(acc_t a) { return float(a) * 0.00390625f; }
-    static __device__ __forceinline__ msg_t to_msg(acc_t q) { return int16_t(max(-32767, min(32767, q))); }
+    static __device__ __forceinline__ float post(acc_t a) { return float(a) * (1.0f / float(1 << FRAC)); }
+    static __device__ __forceinline__ msg_t to_msg(acc_t q) { return msg_t(max(-LIM, min(LIM, q))); }
 };
+using I16 = IFix<int16_t, 8, 32767>;
+using I8 = IFix<int8_t, 2, 127>;
 
 template <class P>
 __device__ __forceinline__ typename P::acc_t load_msg(const typename P::msg_t *s, uint32_t i)

@@ -48,7 +48,7 @@ struct LaunchParams {
     int32_t batch;
     int32_t max_iter;
     float alpha;             // FP32 scale
-    int32_t alpha_q;         // INT16 scale, round(alpha * 2^15)
+    int32_t alpha_q;         // fixed-point scale, round(alpha * 2^15)
     uint32_t flags;
     int32_t *next_shot;      // batch and layered kernels: zeroed per-launch shot counters
                              // [blockIdx.y], claimed with atomicAdd; nullptr: shots b = blockIdx.x + k*gridDim.x
@@ -92,10 +92,10 @@ __host__ __device__ inline LatencyLayout latency_layout(int m, int dc_max, int m
     return s;
 }
 
-enum Precision { kFP32 = 0, kINT16 = 1 };
+enum Precision { kFP32 = 0, kINT16 = 1, kINT8 = 2 };
 
-// Bytes per edge message: FP32 4, INT16 2.
-inline int msg_bytes(int precision) { return precision == kINT16 ? 2 : 4; }
+// Bytes per edge message: FP32 4, INT16 2, INT8 1.
+inline int msg_bytes(int precision) { return precision == kINT16 ? 2 : precision == kINT8 ? 1 : 4; }
 
 // Which compiled variant runs a launch.
 struct KernelChoice {
@@ -170,6 +170,9 @@ cudaError_t launch_msa_f32(const LaunchParams &p, const KernelChoice &kc, dim3 g
                            size_t smem, cudaStream_t stream);
 cudaError_t launch_msa_i16(const LaunchParams &p, const KernelChoice &kc, dim3 grid, int threads,
                            size_t smem, cudaStream_t stream);
+const void *msa_kernel_i8(const KernelChoice &kc);
+cudaError_t launch_msa_i8(const LaunchParams &p, const KernelChoice &kc, dim3 grid, int threads,
+                          size_t smem, cudaStream_t stream);
 // Layered-schedule kernels, msa_layered.cu.
 const void *msa_kernel_layered(int precision, const KernelChoice &kc);
 cudaError_t launch_msa_layered(int precision, const LaunchParams &p, const KernelChoice &kc, dim3 grid, int threads,

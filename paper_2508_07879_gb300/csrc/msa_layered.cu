@@ -1,4 +1,4 @@
-// Layered (row-serial) schedule of the normalized min-sum decoder, FP32 and INT16, for sm_103a.
+// Layered (row-serial) schedule of the normalized min-sum decoder, FP32, INT16 and INT8, for sm_103a.
 //
 // Algorithm 1 (Sec. 2 of arXiv 2508.07879) updates all checks from the previous iteration's
 // messages (flooding).  The layered schedule applies the same check update to one check after
@@ -9,7 +9,8 @@
 // layer is one more than the largest layer of an earlier check it shares a variable with): the
 // checks of a layer run in parallel, the layers in order, and every result is bit-identical to the
 // strictly serial order.  One block per shot, persistent over the batch; per shot in shared memory:
-// Q [n] (FP32, or INT32 for INT16), the messages r in check-major slots (j*m + i), the syndrome bits.
+// Q [n] (FP32, or INT32 for the fixed-point modes), the messages r in check-major slots (j*m + i),
+// the syndrome bits.
 // One barrier per layer, then a stop-test pass over all checks (block AND).
 #include <cstdint>
 
@@ -19,9 +20,6 @@
 
 namespace qldpc {
 namespace kern {
-
-__device__ __forceinline__ float sub_q(float Q, float r) { return __fsub_rn(Q, r); }
-__device__ __forceinline__ int32_t sub_q(int32_t Q, int32_t r) { return max(-32767, min(32767, Q - r)); }
 
 // One check of the layered schedule: q = Q - r_old, the min-sum update, Q = q + r_new.
 template <class P, int DC, bool UNIFORM>
@@ -39,7 +37,7 @@ __device__ __forceinline__ void layered_check(int c, int M, int deg, uint32_t s_
     for (int j = 0; j < DC; ++j) {
         if (UNIFORM || j < deg) {
             v[j] = __ldg(ecol + size_t(j) * M + c);
-            q[j] = sub_q(Q[v[j]], load_msg<P>(slots, uint32_t(j * M + c)));
+            q[j] = P::sub_q(Q[v[j]], load_msg<P>(slots, uint32_t(j * M + c)));
             sx ^= P::sign_word(q[j]);
             const mag_t a = P::mag(q[j]);
             m2 = P::mn(m2, P::mx(m1, a));
@@ -186,14 +184,17 @@ cudaError_t layered_launch(const LaunchParams &p, const KernelChoice &kc, dim3 g
 
 const void *msa_kernel_layered(int precision, const KernelChoice &kc)
 {
-    return precision == kINT16 ? layered_table<kern::I16>(kc) : layered_table<kern::F32>(kc);
+    return precision == kINT16 ? layered_table<kern::I16>(kc)
+           : precision == kINT8 ? layered_table<kern::I8>(kc)
+                                : layered_table<kern::F32>(kc);
 }
 
 cudaError_t launch_msa_layered(int precision, const LaunchParams &p, const KernelChoice &kc, dim3 grid, int threads,
                                size_t smem, cudaStream_t stream)
 {
     return precision == kINT16 ? layered_launch<kern::I16>(p, kc, grid, threads, smem, stream)
-                               : layered_launch<kern::F32>(p, kc, grid, threads, smem, stream);
+           : precision == kINT8 ? layered_launch<kern::I8>(p, kc, grid, threads, smem, stream)
+                                : layered_launch<kern::F32>(p, kc, grid, threads, smem, stream);
 }
 
 }  // namespace qldpc

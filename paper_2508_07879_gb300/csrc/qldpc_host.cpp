@@ -29,7 +29,7 @@ const void *msa_kernel(int precision, const KernelChoice &kc)
 {
     if (kc.layered) return msa_kernel_layered(precision, kc);
     if (kc.learned) return msa_kernel_learned(kc);
-    return precision == kINT16 ? msa_kernel_i16(kc) : msa_kernel_f32(kc);
+    return precision == kINT16 ? msa_kernel_i16(kc) : precision == kINT8 ? msa_kernel_i8(kc) : msa_kernel_f32(kc);
 }
 
 cudaError_t launch_msa(const LaunchParams &p, int precision, const KernelChoice &kc, int threads,
@@ -38,8 +38,9 @@ cudaError_t launch_msa(const LaunchParams &p, int precision, const KernelChoice 
     dim3 grid(unsigned(grid_x), unsigned(p.nprob));
     if (kc.layered) return launch_msa_layered(precision, p, kc, grid, threads, smem, stream);
     if (kc.learned) return launch_msa_learned(p, kc, grid, threads, smem, stream);
-    return precision == kINT16 ? launch_msa_i16(p, kc, grid, threads, smem, stream)
-                               : launch_msa_f32(p, kc, grid, threads, smem, stream);
+    return precision == kINT16  ? launch_msa_i16(p, kc, grid, threads, smem, stream)
+           : precision == kINT8 ? launch_msa_i8(p, kc, grid, threads, smem, stream)
+                                : launch_msa_f32(p, kc, grid, threads, smem, stream);
 }
 
 }  // namespace qldpc
@@ -313,7 +314,7 @@ int launch(const qldpc_graph *g0, const qldpc_graph *g1, const Problem *probs, i
            int32_t batch, int32_t max_iter, float alpha, int32_t precision, uint32_t flags,
            cudaStream_t stream)
 {
-    if (precision != QLDPC_FP32 && precision != QLDPC_INT16) return QLDPC_ERR_INVALID_ARG;
+    if (precision != QLDPC_FP32 && precision != QLDPC_INT16 && precision != QLDPC_INT8) return QLDPC_ERR_INVALID_ARG;
     if ((flags & ~uint32_t(QLDPC_NO_EARLY_STOP | QLDPC_LEARNED | QLDPC_LAYERED)) != 0) return QLDPC_ERR_INVALID_ARG;
     if (batch < 0 || max_iter < 0 || !finite_alpha(alpha)) return QLDPC_ERR_INVALID_ARG;
     const bool learned = (flags & QLDPC_LEARNED) != 0;
@@ -324,7 +325,7 @@ int launch(const qldpc_graph *g0, const qldpc_graph *g1, const Problem *probs, i
         if (!g0->d_weights || !g1->d_weights) return QLDPC_ERR_INVALID_ARG;
     }
     int aq = 0;
-    if (precision == QLDPC_INT16) {
+    if (precision == QLDPC_INT16 || precision == QLDPC_INT8) {
         aq = alpha_fixed(alpha);
         if (aq < 0) return QLDPC_ERR_INVALID_ARG;
     }

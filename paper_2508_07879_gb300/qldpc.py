@@ -26,6 +26,7 @@ QLDPC_ERR_CUDA = -4
 QLDPC_ERR_TIMEOUT = -5
 QLDPC_FP32 = 0
 QLDPC_INT16 = 1
+QLDPC_INT8 = 2
 QLDPC_NO_EARLY_STOP = 1
 QLDPC_LEARNED = 2
 QLDPC_LAYERED = 4
@@ -37,7 +38,7 @@ QLDPC_KERNEL_BATCH = 1
 QLDPC_KERNEL_LATENCY = 2
 KERNELS = {"auto": QLDPC_KERNEL_AUTO, "batch": QLDPC_KERNEL_BATCH, "latency": QLDPC_KERNEL_LATENCY}
 
-PRECISIONS = {"fp32": QLDPC_FP32, "int16": QLDPC_INT16}
+PRECISIONS = {"fp32": QLDPC_FP32, "int16": QLDPC_INT16, "int8": QLDPC_INT8}
 
 
 def _load() -> ctypes.CDLL:

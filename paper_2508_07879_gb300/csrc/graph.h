@@ -39,6 +39,10 @@ struct qldpc_graph {
     // learned decoding: [learned_T][dc_max * m] slot-layout weights (qldpc_graph_set_weights)
     float *d_weights = nullptr;
     int32_t learned_T = 0;
+    // last training launch plan (qldpc_learned.cpp), keyed by (batch, T)
+    std::mutex train_mu;
+    int32_t train_batch = 0, train_T = 0;
+    unsigned char train_plan[256];
 };
 
 namespace qldpc {

@@ -219,12 +219,41 @@ KernelChoice variant(const qldpc_graph *const *gs, int nprob, bool latency, bool
     return KernelChoice{latency, dc_bucket(dc), false, dv_bucket(dv), learned};
 }
 
+// Resident blocks per SM of a kernel at a block size and shared-memory size.  The runtime's query
+// costs host time on the order of the decode itself for small batches, so results are cached.
+int blocks_per_sm(const void *k, int threads, size_t smem, int &per_sm)
+{
+    struct Entry {
+        int device;
+        const void *k;
+        int threads;
+        size_t smem;
+        int per_sm;
+    };
+    static std::mutex mu;
+    static std::vector<Entry> cache;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return QLDPC_ERR_CUDA;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        for (const Entry &e : cache)
+            if (e.device == dev && e.k == k && e.threads == threads && e.smem == smem) {
+                per_sm = e.per_sm;
+                return QLDPC_OK;
+            }
+    }
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem);
+    if (e != cudaSuccess) return cuda_status(e);
+    std::lock_guard<std::mutex> lk(mu);
+    cache.push_back(Entry{dev, k, threads, smem, per_sm});
+    return QLDPC_OK;
+}
+
 int occupancy_grid(const qldpc_graph *g0, const void *k, int threads, size_t smem, int nprob,
                    int32_t batch, int per_sm, int &grid)
 {
     if (!per_sm) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem);
-        if (e != cudaSuccess) return cuda_status(e);
+        if (int rc = blocks_per_sm(k, threads, smem, per_sm)) return rc;
         if (per_sm < 1) return QLDPC_ERR_UNSUPPORTED;
     }
     const int64_t slots = std::max<int64_t>(1, int64_t(per_sm) * g0->sm_count / nprob);

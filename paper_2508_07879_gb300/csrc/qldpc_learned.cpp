@@ -42,7 +42,27 @@ struct TrainPlan {
     size_t w_off = 0, state_off = 0, part_off = 0, total = 0;
 };
 
+int plan_training_uncached(const qldpc_graph *g, int32_t batch, int32_t T, TrainPlan &tp);
+
+// The plan of the graph's last (batch, T), else a new one (occupancy queries cost host time on
+// every training step otherwise).
 int plan_training(const qldpc_graph *g, int32_t batch, int32_t T, TrainPlan &tp)
+{
+    static_assert(sizeof(TrainPlan) <= sizeof(g->train_plan), "plan cache too small");
+    qldpc_graph *mg = const_cast<qldpc_graph *>(g);
+    std::lock_guard<std::mutex> lk(mg->train_mu);
+    if (mg->train_batch == batch && mg->train_T == T) {
+        std::memcpy(&tp, mg->train_plan, sizeof(TrainPlan));
+        return QLDPC_OK;
+    }
+    if (int rc = plan_training_uncached(g, batch, T, tp)) return rc;
+    std::memcpy(mg->train_plan, &tp, sizeof(TrainPlan));
+    mg->train_batch = batch;
+    mg->train_T = T;
+    return QLDPC_OK;
+}
+
+int plan_training_uncached(const qldpc_graph *g, int32_t batch, int32_t T, TrainPlan &tp)
 {
     tp.tc = train_choice(g);
     if (tp.tc.dc < 0) return QLDPC_ERR_UNSUPPORTED;

@@ -323,9 +323,19 @@ int plan_layered(const qldpc_graph *const *gs, int nprob, int32_t batch, int pre
         widest = std::max(widest, gs[i]->dg.max_layer);
     }
     pl.kc = variant(gs, nprob, false, false);
-    pl.kc.dvb = 0;
     pl.kc.layered = true;
     pl.threads = std::min(1024, round32(widest));
+    // Single-shot regime (every shot gets its own SM), at most 8 layers of rows of degree <= 8 and at
+    // most 256 checks per layer: the register-resident kernel (each thread owns one check per layer; Q
+    // is the only shared array) has the lower latency.  Batches take the shared-memory kernel, whose
+    // smaller register footprint keeps more shots per SM (41.8 against 34.0 M syndromes/s, LP-1054).
+    bool reg = pl.threads <= 256 && int64_t(batch) * nprob <= g0->sm_count;
+    for (int i = 0; i < nprob; ++i) reg = reg && gs[i]->dg.nlayers <= 8 && gs[i]->dc_max <= 8 && gs[i]->n <= 65536;
+    pl.kc.dvb = reg ? 1 : 0;
+    if (reg) {
+        smem = 0;
+        for (int i = 0; i < nprob; ++i) smem = std::max(smem, align16(size_t(gs[i]->n) * 4));
+    }
     pl.smem = smem;
     const void *k = msa_kernel(precision, pl.kc);
     if (int rc = ensure_kernel_attrs(k, smem, g0->smem_optin)) return rc;

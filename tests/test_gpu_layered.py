@@ -155,3 +155,17 @@ def test_batch_invariance(q):
         part = device_layered(q, h, s[lo:hi], prior, 50, "fp32")
         for a, b in zip(part, full):
             np.testing.assert_array_equal(a, b[lo:hi])
+
+
+@pytest.mark.parametrize("precision", ["fp32", "int16"])
+def test_single_shot_register_kernel(q, precision):
+    """Batches no larger than the SM count run the register-resident layered kernel (LP-1054: 7
+    layers of degree-8 rows): bit-exact against the oracle as well."""
+    h = w.lp_code(1054).hz_csr
+    e = w.iid_x_errors(h.n, 0.05, 100, seed=88)
+    s = w.syndromes(h, e)
+    prior = np.full(h.n, w.prior_llr(0.05), dtype=np.float32)
+    iters, ok = check_equal(q, h, s, prior, 50, precision)
+    assert (iters > 3).any()
+    check_equal(q, h, s[:1], prior, 50, precision)
+    check_equal(q, h, s[:7], prior, 12, precision, early_stop=False)

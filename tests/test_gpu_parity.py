@@ -399,3 +399,37 @@ def test_invalid_decode_arguments(q):
     assert rc == q.QLDPC_ERR_INVALID_ARG                                  # unknown precision
     rc = q.qldpc_decode_ex(graph.handle, ptr(s), 0, ptr(p), 10, 0.75, None, None, None, None, 0, 6, None)
     assert rc == q.QLDPC_ERR_INVALID_ARG                                  # unknown flag bits
+
+
+def test_pair_with_different_row_widths(q):
+    """A pair whose graphs have different row-degree buckets (8 and 16) shares one kernel variant:
+    each half must still decode as it does alone and as the oracle does."""
+    rng = np.random.default_rng(12)
+    n = 150
+
+    def random_code(m, lo, hi):
+        h = np.zeros((m, n), dtype=np.uint8)
+        for i in range(m):
+            h[i, rng.choice(n, size=int(rng.integers(lo, hi)), replace=False)] = 1
+        for v in np.nonzero(h.sum(0) == 0)[0]:   # cover every column without exceeding degree hi
+            rows = np.nonzero(h.sum(1) < hi)[0]
+            h[rng.choice(rows), v] = 1
+        return w.csr_from_dense(h)
+
+    ha, hb = random_code(70, 3, 8), random_code(60, 9, 13)
+    assert np.diff(ha.row_ptr).max() <= 8 < np.diff(hb.row_ptr).max()
+    ga, gb = q.Graph.from_csr(ha), q.Graph.from_csr(hb)
+    B = 400
+    ea = (rng.random((B, n)) < 0.05).astype(np.uint8)
+    eb = (rng.random((B, n)) < 0.05).astype(np.uint8)
+    sa, sb = w.syndromes(ha, ea), w.syndromes(hb, eb)
+    prior = rng.uniform(1.5, 3.5, n).astype(np.float32)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    (xa, ia, oa, pa), (xb, ib, ob, pb) = q.decode_pair(ga, gb, dev(sa), dev(sb), dev(prior), dev(prior), 40,
+                                                       want_post=True)
+    for h, s, got in ((ha, sa, (xa, ia, oa, pa)), (hb, sb, (xb, ib, ob, pb))):
+        ref = oracle.msa(h.row_ptr, h.col_idx, h.m, h.n, s, prior, 40, 0.75, "f32", threads=8)
+        np.testing.assert_array_equal(got[0].cpu().numpy(), ref["err"])
+        np.testing.assert_array_equal(got[1].cpu().numpy(), ref["iters"])
+        np.testing.assert_array_equal(got[2].cpu().numpy(), ref["ok"])
+        np.testing.assert_array_equal(got[3].cpu().numpy(), ref["post"])

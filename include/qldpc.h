@@ -34,6 +34,16 @@
  * synchronous and uses device staging owned by the graph (grown on demand, or reserved ahead with
  * qldpc_graph_reserve).  A graph must be used on the device that was current when it was created.
  *
+ * Entry points by group:
+ *   graphs          qldpc_graph_create / _create_csc / _destroy / _dims / _set_launch / _reserve
+ *   decoding        qldpc_decode, qldpc_decode_ex (flags: QLDPC_NO_EARLY_STOP, QLDPC_LAYERED for
+ *                   the row-serial schedule, QLDPC_LEARNED), qldpc_decode_pair, qldpc_decode_host,
+ *                   qldpc_decode_host_noalloc
+ *   serving         qldpc_server_create / _submit / _poll / _replay / _status / _destroy
+ *   learned decoder qldpc_graph_set_weights, qldpc_nms_workspace_bytes, qldpc_nms_forward,
+ *                   qldpc_nms_backward, qldpc_adam_step
+ *   workloads       qldpc_sample_errors (device error sampler), qldpc_logical_failures
+ *
  * Errors: every function returns a qldpc_status.  Arguments are validated on the host before any
  * GPU work is enqueued; a rejected call enqueues nothing and writes no output.  A CUDA launch
  * failure returns QLDPC_ERR_CUDA; faults during execution surface at the caller's next

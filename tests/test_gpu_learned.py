@@ -309,3 +309,22 @@ def test_logical_failures_match_host(q):
     expect = (ok == 0) | gf2.logical_failures(e ^ d, L)
     np.testing.assert_array_equal(fail, expect.astype(np.uint8))
     assert fail[1::4].all()
+
+
+@pytest.mark.parametrize("kernel", ["batch", "latency"])
+def test_learned_alone_without_fallback(q, kernel):
+    """max_iter = 0 after the learned iterations: unconverged shots keep the prior's decisions (the
+    plain decoder with no iterations), as the oracle's learned decoder specifies."""
+    h = w.lp_code(1054).hz_csr
+    rng = np.random.default_rng(9)
+    e = w.iid_x_errors(h.n, 0.05, 200, seed=45)
+    s = w.syndromes(h, e)
+    prior = np.full(h.n, w.prior_llr(0.05), dtype=np.float32)
+    weights = rng.uniform(0.55, 0.95, (10, h.nnz)).astype(np.float32)
+    ref = oracle.nms_decode(h.row_ptr, h.col_idx, h.m, h.n, s, prior, weights, 0, 0.75, threads=8)
+    err, iters, ok, post = run_learned(q, h, s, prior, weights, 0, kernel)
+    assert ref["fallback"].any()
+    np.testing.assert_array_equal(err, ref["err"])
+    np.testing.assert_array_equal(iters, ref["iters"])
+    np.testing.assert_array_equal(ok, ref["ok"])
+    np.testing.assert_array_equal(post.view(np.uint32), ref["post"].view(np.uint32))

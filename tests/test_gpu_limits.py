@@ -1,0 +1,93 @@
+"""Maximum sizes on the GPU: the largest graph whose FP32 shot fits the device's shared memory, the
+next size up (rejected before any launch), and a 2^21-shot batch in one call."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2508_07879_gb300 import workloads as w
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def q():
+    from paper_2508_07879_gb300 import build
+    build.build()
+    from paper_2508_07879_gb300 import qldpc
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return qldpc
+
+
+def qc_code(L, seed=1):
+    """Quasi-cyclic (3,6)-regular H: a 3 x 6 array of L x L circulant permutations."""
+    rng = np.random.default_rng(seed)
+    shifts = rng.integers(0, L, size=(3, 6))
+    h = np.zeros((3 * L, 6 * L), dtype=np.uint8)
+    eye = np.eye(L, dtype=np.uint8)
+    for r in range(3):
+        for c in range(6):
+            h[r * L:(r + 1) * L, c * L:(c + 1) * L] = np.roll(eye, shifts[r, c], axis=1)
+    return w.csr_from_dense(h)
+
+
+def fp32_shot_bytes(m, n, dc):
+    """Shared memory of one FP32 shot of the batch kernel: Q and gamma [n], parity words [m],
+    messages [dc * m], each section 16-byte aligned."""
+    a16 = lambda x: (x + 15) // 16 * 16
+    return a16(a16(a16(a16(4 * n) + 4 * n) + 4 * m) + 4 * dc * m)
+
+
+def test_largest_graph_that_fits(q):
+    optin = getattr(torch.cuda.get_device_properties(0), "shared_memory_per_block_optin", 232448)
+    L = max(l for l in range(16, 20000, 8) if fp32_shot_bytes(3 * l, 6 * l, 6) <= optin)
+    h = qc_code(L)
+    g = q.Graph.from_csr(h)
+    e = w.iid_x_errors(h.n, 0.02, 200, seed=5)
+    s = w.syndromes(h, e)
+    prior = np.full(h.n, w.prior_llr(0.02), dtype=np.float32)
+    st, pt = torch.from_numpy(s).cuda(), torch.from_numpy(prior).cuda()
+    err, iters, ok, post = q.decode(g, st, pt, 30, 0.75, "fp32", want_post=True)
+    torch.cuda.synchronize()
+    ref = oracle.msa(h.row_ptr, h.col_idx, h.m, h.n, s, prior, 30, 0.75, "f32", threads=16)
+    np.testing.assert_array_equal(err.cpu().numpy(), ref["err"])
+    np.testing.assert_array_equal(iters.cpu().numpy(), ref["iters"])
+    np.testing.assert_array_equal(post.cpu().numpy(), ref["post"])
+    assert ref["ok"].mean() > 0.5
+    # one circulant size larger: the FP32 shot no longer fits and the decode is refused
+    big = qc_code(L + 8)
+    assert fp32_shot_bytes(big.m, big.n, 6) > optin
+    gb = q.Graph.from_csr(big)            # INT16 still fits, so the graph itself is accepted
+    sb = torch.zeros((4, big.m), dtype=torch.uint8, device="cuda")
+    with pytest.raises(q.QldpcError) as ei:
+        q.decode(gb, sb, torch.full((big.n,), 3.0, device="cuda"), 10, precision="fp32")
+    assert ei.value.status == q.QLDPC_ERR_UNSUPPORTED
+    q.decode(gb, sb, torch.full((big.n,), 3.0, device="cuda"), 10, precision="int16")
+    torch.cuda.synchronize()
+
+
+def test_two_million_shots_in_one_call(q):
+    h = w.hgp_code(400).hz_csr
+    g = q.Graph.from_csr(h)
+    B = 1 << 21
+    err_true, syn = q.sample_errors(g, 2024, 0, B, 0.05)
+    prior = torch.full((h.n,), w.prior_llr(0.05), device="cuda")
+    err, iters, ok, _ = q.decode(g, syn, prior, 32, 0.75, "fp32")
+    torch.cuda.synchronize()
+    # every shot that reports success meets its syndrome (checked on the device, in chunks)
+    hd = torch.from_numpy(h.dense().astype(np.float32)).cuda()
+    for lo in range(0, B, 1 << 18):
+        okm = ok[lo:lo + (1 << 18)].bool()
+        s_hat = (err[lo:lo + (1 << 18)][okm].float() @ hd.T).remainder(2).to(torch.uint8)
+        assert torch.equal(s_hat, syn[lo:lo + (1 << 18)][okm])
+    assert 0.4 < ok.float().mean().item() < 0.6      # the oracle decodes 48 % of HGP-400 shots at p = 0.05
+    # sampled shots across the whole range against the oracle
+    idx = np.unique(np.random.default_rng(0).integers(0, B, 400))
+    idx = np.concatenate([idx, [0, B - 1]])
+    s_host = syn[torch.from_numpy(idx).cuda()].cpu().numpy()
+    ref = oracle.msa(h.row_ptr, h.col_idx, h.m, h.n, s_host, np.full(h.n, w.prior_llr(0.05), np.float32), 32, 0.75,
+                     "f32", threads=16)
+    sel = torch.from_numpy(idx).cuda()
+    np.testing.assert_array_equal(err[sel].cpu().numpy(), ref["err"])
+    np.testing.assert_array_equal(iters[sel].cpu().numpy(), ref["iters"])
+    np.testing.assert_array_equal(ok[sel].cpu().numpy(), ref["ok"])

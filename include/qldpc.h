@@ -135,6 +135,18 @@ QLDPC_API void qldpc_graph_destroy(qldpc_graph *g);
 QLDPC_API int qldpc_graph_dims(const qldpc_graph *g, int32_t *m, int32_t *n, int32_t *nnz,
                      int32_t *max_row_degree, int32_t *max_col_degree);
 
+/* On-chip footprint of the flooding kernels for one precision (QLDPC_FP32 / INT16 / INT8):
+ *   lanes       variable lanes of the variable step, n plus idle lanes (variables are grouped by
+ *               degree and packed into warps whose k-th edge slots fall in distinct shared-memory
+ *               banks; an idle lane closes a warp early where that pays)
+ *   shot_bytes  shared memory one shot takes in the throughput kernel: Q and gamma (4 B per lane),
+ *               parity words (4 B per check), messages (max_row_degree * m slots), each section
+ *               16-byte aligned and the last two with 32 scratch entries for the idle lanes.
+ *               A decode whose shot_bytes exceeds the device's shared memory per block is refused
+ *               with UNSUPPORTED.
+ * Either output pointer may be NULL.  INVALID_ARG: null graph or unknown precision. */
+QLDPC_API int qldpc_graph_footprint(const qldpc_graph *g, int32_t precision, int32_t *lanes, size_t *shot_bytes);
+
 /* Kernels (qldpc_graph_set_launch). */
 enum {
     QLDPC_KERNEL_AUTO = 0,      /* latency kernel when every shot gets its own SM, else batch kernel */

@@ -18,6 +18,7 @@ struct qldpc_graph {
     int sm_count = 0;
     size_t smem_optin = 0;      // max dynamic shared memory per block (opt-in)
     int32_t m = 0, n = 0, nnz = 0, dc_max = 0, dv_max = 0;
+    int32_t nv = 0;             // variable lanes of the kernels: n plus idle lanes (bank packing)
     bool uniform_rows = false;  // every row has degree dc_max
     void *d_block = nullptr;    // one device allocation for all graph arrays
     int32_t *d_counters = nullptr;              // [kShotCounterSlots][2] shot counters (inside d_block)

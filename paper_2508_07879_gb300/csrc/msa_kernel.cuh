@@ -260,7 +260,7 @@ __device__ __forceinline__ typename P::acc_t var_step_batch(int deg, int u, int 
 // Throughput kernel
 // ---------------------------------------------------------------------------------------------
 // Initialization (Alg. 1) of one shot: q^(0) = gamma on every edge; the parity words start at s_m
-// and take the decisions of the prior.  Ends with a barrier.
+// and take the decisions of the prior.  Ends with a barrier.  N = variable lanes.
 template <class P>
 __device__ __forceinline__ void batch_init_shot(const Problem &pr, const uint8_t *s, int M, int N, int tid, int T,
                                                 const typename P::acc_t *gam, typename P::acc_t *Qs,
@@ -292,20 +292,21 @@ __global__ void __launch_bounds__(1024, 1) msa_batch_kernel(const LaunchParams p
     using msg_t = typename P::msg_t;
 
     const Problem pr = blockIdx.y == 0 ? p.prob[0] : p.prob[1];
-    const int M = pr.g.m, N = pr.g.n;
+    const int M = pr.g.m, N = pr.g.n, NV = pr.g.nv;   // checks, variables, variable lanes
     const int T = blockDim.x, tid = threadIdx.x;
 
     extern __shared__ __align__(16) unsigned char smem[];
-    const SmemLayout L = smem_layout(M, N, pr.g.dc_max, int(sizeof(msg_t)));
+    const SmemLayout L = smem_layout(M, NV, pr.g.dc_max, int(sizeof(msg_t)));
     acc_t *Qs = reinterpret_cast<acc_t *>(smem + L.q_off);
     acc_t *gam = reinterpret_cast<acc_t *>(smem + L.g_off);
     uint32_t *parity = reinterpret_cast<uint32_t *>(smem + L.par_off);
     msg_t *slots = reinterpret_cast<msg_t *>(smem + L.slot_off);
 
-    // Prior LLRs: loaded once per block, shared by all its shots.
+    // Prior LLRs: loaded once per block, shared by all its shots (idle lanes: 0, no edges).
     int bad = 0;
-    for (int u = tid; u < N; u += T) {
-        const float g = pr.prior[__ldg(pr.g.vperm + u)];
+    for (int u = tid; u < NV; u += T) {
+        const uint32_t v = __ldg(pr.g.vperm + u);
+        const float g = v < uint32_t(N) ? pr.prior[v] : 0.0f;
         bad |= !isfinite(g);
         gam[u] = P::quantize(g);
     }
@@ -340,7 +341,7 @@ __global__ void __launch_bounds__(1024, 1) msa_batch_kernel(const LaunchParams p
             continue;
         }
         const uint8_t *s = pr.syn + size_t(b) * M;
-        batch_init_shot<P>(pr, s, M, N, tid, T, gam, Qs, parity, slots);
+        batch_init_shot<P>(pr, s, M, NV, tid, T, gam, Qs, parity, slots);
 
         int k = 0, all = 0;
         bool learned = LEARNED;
@@ -360,21 +361,23 @@ __global__ void __launch_bounds__(1024, 1) msa_batch_kernel(const LaunchParams p
                 if (!LEARNED || !learned) break;
                 learned = false;                  // fallback: plain min-sum from the prior
                 end = k + p.max_iter;
-                batch_init_shot<P>(pr, s, M, N, tid, T, gam, Qs, parity, slots);
+                batch_init_shot<P>(pr, s, M, NV, tid, T, gam, Qs, parity, slots);
                 continue;
             }
-            for (int u = tid; u < N; u += T)
-                Qs[u] = var_step_batch<P, DV>(__ldg(pr.g.vdeg + u), u, N, uint32_t(M), pr.g.vslot, gam[u],
+            for (int u = tid; u < NV; u += T)
+                Qs[u] = var_step_batch<P, DV>(__ldg(pr.g.vdeg + u), u, NV, uint32_t(M), pr.g.vslot, gam[u],
                                               P::neg(Qs[u]), slots, parity);
             __syncthreads();
             ++k;
         }
 
-        for (int u = tid; u < N; u += T) {
+        for (int u = tid; u < NV; u += T) {
             const acc_t q = Qs[u];
             const uint32_t v = __ldg(pr.g.vperm + u);
-            err[v] = P::neg(q) ? 1 : 0;
-            if (pr.post) pr.post[size_t(b) * N + v] = P::post(q);
+            if (v < uint32_t(N)) {
+                err[v] = P::neg(q) ? 1 : 0;
+                if (pr.post) pr.post[size_t(b) * N + v] = P::post(q);
+            }
         }
         if (tid == 0) {
             pr.iters[b] = k;
@@ -414,7 +417,7 @@ __global__ void __launch_bounds__(kLatencyMaxThreads, 1) msa_latency_kernel(cons
     using msg_t = typename P::msg_t;
 
     const Problem pr = blockIdx.y == 0 ? p.prob[0] : p.prob[1];
-    const int M = pr.g.m, N = pr.g.n;
+    const int M = pr.g.m, N = pr.g.n, NV = pr.g.nv;
     const int T = blockDim.x, tid = threadIdx.x;
     extern __shared__ __align__(16) unsigned char smem[];
     const LatencyLayout L = latency_layout(M, pr.g.dc_max, int(sizeof(msg_t)));
@@ -428,7 +431,7 @@ __global__ void __launch_bounds__(kLatencyMaxThreads, 1) msa_latency_kernel(cons
         const int c = tid + i * T;
         cdeg[i] = c < M ? (UNIFORM ? DC : int(__ldg(pr.g.rdeg + c))) : -1;
     }
-    // Internal variables u = tid + i*T (heaviest first, so the few second-pass variables are the
+    // Variable lanes u = tid + i*T (heaviest first, so the few second-pass variables are the
     // lightest): edge lists, degree and prior in registers; vid = original index for the outputs.
     uint32_t ev[kLatVnPerThread][DV];
     int vdeg[kLatVnPerThread], vid[kLatVnPerThread];
@@ -437,12 +440,12 @@ __global__ void __launch_bounds__(kLatencyMaxThreads, 1) msa_latency_kernel(cons
 #pragma unroll
     for (int i = 0; i < kLatVnPerThread; ++i) {
         const int u = tid + i * T;
-        const int v = u < N ? int(__ldg(pr.g.vperm + u)) : N;
+        const int v = u < NV ? int(__ldg(pr.g.vperm + u)) : N;   // N: idle lane
         vid[i] = v;
-        vdeg[i] = u < N ? int(__ldg(pr.g.vdeg + u)) : -1;
+        vdeg[i] = u < NV ? int(__ldg(pr.g.vdeg + u)) : -1;
 #pragma unroll
         for (int k = 0; k < DV; ++k)
-            ev[i][k] = (k < vdeg[i]) ? __ldg(pr.g.vslot + size_t(k) * N + u) : 0u;
+            ev[i][k] = (k < vdeg[i]) ? __ldg(pr.g.vslot + size_t(k) * NV + u) : 0u;
         const float g = v < N ? pr.prior[v] : 0.0f;
         bad |= !isfinite(g);
         gam[i] = P::quantize(g);

@@ -11,14 +11,18 @@ namespace qldpc {
 
 // Tanner graph in the kernels' layout.  Messages of check i live in shared-memory "slots"
 // j*m + i (j = position of the edge in row i), so a warp working on 32 consecutive checks touches
-// 32 consecutive slots; the check side needs no index at all.  Variables are relabelled in
-// descending-degree order (internal index u, original index vperm[u]); the k-th edge of internal
-// variable u (ascending check order) is vslot[k*n + u] = j << 16 | i.
+// 32 consecutive slots; the check side needs no index at all.  Variables occupy nv >= n lanes:
+// grouped by descending degree and packed so that the k-th slots of a warp's 32 variables fall in
+// distinct shared-memory banks where possible, with idle lanes (vperm = n) closing a warp early.
+// Lane u holds the caller's variable vperm[u]; the k-th edge of lane u (ascending check order) is
+// vslot[k*nv + u] = j << 16 | i.  An idle lane has its warp's degree and edges j = dc_max - 1,
+// i = m + b (b < kScratch): slot dc_max*m + b and parity word m + b, scratch that no check step
+// reads, in a bank its warp leaves free, so it runs its warp's path without divergence.
 struct DeviceGraph {
-    const uint32_t *vslot;   // [dv_max * n] (j << 16) | check of internal variable u's k-th edge
-    const uint8_t *vdeg;     // [n] column degree of internal variable u
+    const uint32_t *vslot;   // [dv_max * nv] (j << 16) | check of lane u's k-th edge
+    const uint8_t *vdeg;     // [nv] column degree of lane u (idle: its warp's degree)
     const uint8_t *rdeg;     // [m] row degrees
-    const uint32_t *vperm;   // [n] original index of internal variable u
+    const uint32_t *vperm;   // [nv] caller's index of the variable in lane u (n: idle lane)
     const uint32_t *ecol;    // [dc_max * m] original variable of slot j*m + i (0xffffffff: no edge)
     const int32_t *slot_edge;// [dc_max * m] CSR edge index of slot j*m + i (-1: no edge)
     const uint32_t *eslot;   // [nnz] slot j*m + i of CSR edge e
@@ -26,6 +30,7 @@ struct DeviceGraph {
     const uint32_t *layer_chk;//   layer_chk[layer_ptr[l] .. layer_ptr[l+1]) (ascending)
     int32_t nlayers, max_layer;
     int32_t m, n, nnz;
+    int32_t nv;              // variable lanes (n <= nv)
     int32_t dc_max, dv_max;  // largest row / column degree
 };
 
@@ -60,7 +65,12 @@ constexpr int kShotCounterSlots = 1024;
 
 constexpr uint32_t kFlagNoEarlyStop = 1u;
 
-// Shared-memory layout of one shot in the batch kernel (identical on host and device).
+// Idle variable lanes (see DeviceGraph) read and write one of kScratch words past the last slot
+// and flip one of kScratch parity words past the last check; no check step reads either.
+constexpr int kScratch = 32;
+
+// Shared-memory layout of one shot in the batch kernel (identical on host and device);
+// n = variable lanes.
 struct SmemLayout {
     size_t q_off, g_off, par_off, slot_off, total;
 };
@@ -72,9 +82,9 @@ __host__ __device__ inline SmemLayout smem_layout(int m, int n, int dc_max, int 
     SmemLayout s;
     s.q_off = 0;                                                       // a-posteriori Q_n [n] (4 B)
     s.g_off = align16(s.q_off + size_t(n) * 4);                        // prior gamma_n    [n] (4 B)
-    s.par_off = align16(s.g_off + size_t(n) * 4);                      // parity words     [m] (4 B)
-    s.slot_off = align16(s.par_off + size_t(m) * 4);                   // edge messages [dc_max*m]
-    s.total = align16(s.slot_off + size_t(dc_max) * m * msg_bytes);
+    s.par_off = align16(s.g_off + size_t(n) * 4);                      // parity words [m + scratch]
+    s.slot_off = align16(s.par_off + size_t(m + kScratch) * 4);        // messages [dc_max*m + scratch]
+    s.total = align16(s.slot_off + (size_t(dc_max) * m + kScratch) * msg_bytes);
     return s;
 }
 
@@ -87,8 +97,8 @@ __host__ __device__ inline LatencyLayout latency_layout(int m, int dc_max, int m
 {
     LatencyLayout s;
     s.par_off = 0;
-    s.slot_off = align16(size_t(m) * 4);
-    s.total = align16(s.slot_off + size_t(dc_max) * m * msg_bytes);
+    s.slot_off = align16(size_t(m + kScratch) * 4);
+    s.total = align16(s.slot_off + (size_t(dc_max) * m + kScratch) * msg_bytes);
     return s;
 }
 
@@ -254,7 +264,7 @@ struct TrainLayout {
 __host__ __device__ inline TrainLayout train_layout(int m, int n, int dc_max, bool backward)
 {
     TrainLayout t;
-    const size_t S = size_t(dc_max) * m;
+    const size_t S = size_t(dc_max) * m + kScratch;
     t.slot_off = 0;                                                          // q / gradient slots [S] f32
     t.r_off = align16(S * 4);                                                // r slots [S] f32 (backward)
     t.c_off = backward ? align16(t.r_off + S * 4) : t.r_off;                 // state [2][4m] u32 (backward)

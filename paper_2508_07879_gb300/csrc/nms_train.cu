@@ -92,6 +92,20 @@ __device__ __forceinline__ void train_check_fwd(int c, int M, int deg, uint32_t 
     st[3 * M + c] = uint32_t(i1) | (uint32_t(i2) << 8) | (negall << 16);
 }
 
+// Per-lane inputs: the prior and the target of the variable in lane u; idle lanes get prior 0
+// and the marker kIdleLane (they have no edges and add nothing to the loss).
+constexpr uint8_t kIdleLane = 2;
+__device__ __forceinline__ float lane_prior(const DeviceGraph &g, const float *prior, int u, int N)
+{
+    const uint32_t v = __ldg(g.vperm + u);
+    return v < uint32_t(N) ? prior[v] : 0.0f;
+}
+__device__ __forceinline__ uint8_t lane_target(const DeviceGraph &g, const uint8_t *tg, int u, int N)
+{
+    const uint32_t v = __ldg(g.vperm + u);
+    return v < uint32_t(N) ? uint8_t(tg[v] & 1u) : kIdleLane;
+}
+
 // r of check c recomputed from its recorded state (bit-identical to the forward's r).
 template <int DC, bool UNIFORM>
 __device__ __forceinline__ void recompute_r(int c, int M, int deg, uint32_t m1b, uint32_t m2b, uint32_t signs,
@@ -112,17 +126,17 @@ __device__ __forceinline__ void recompute_r(int c, int M, int deg, uint32_t m1b,
 template <int DC, bool UNIFORM, int DV>
 __global__ void __launch_bounds__(kTrainThreads, 4) nms_forward_kernel(const TrainParams p)
 {
-    const int M = p.g.m, N = p.g.n, T = blockDim.x, tid = threadIdx.x;
+    const int M = p.g.m, N = p.g.n, NV = p.g.nv, T = blockDim.x, tid = threadIdx.x;
     const size_t S = size_t(p.g.dc_max) * M;
     extern __shared__ __align__(16) unsigned char smem[];
-    const TrainLayout L = train_layout(M, N, p.g.dc_max, false);
+    const TrainLayout L = train_layout(M, NV, p.g.dc_max, false);
     float *slots = reinterpret_cast<float *>(smem + L.slot_off);
     float *gam = reinterpret_cast<float *>(smem + L.g_off);
     uint8_t *y = smem + L.y_off;
     uint8_t *sb = smem + L.s_off;
     __shared__ float red[32];
 
-    for (int u = tid; u < N; u += T) gam[u] = F32::quantize(p.prior[__ldg(p.g.vperm + u)]);
+    for (int u = tid; u < NV; u += T) gam[u] = F32::quantize(lane_prior(p.g, p.prior, u, N));
     // uniform lambda: sum the terms and scale once by 1/(T N); else weight each iteration's terms
     const float inv = p.loss_w ? 1.0f / float(N) : 1.0f / (float(p.T) * float(N));
     for (int b = blockIdx.x; b < p.batch; b += gridDim.x) {
@@ -130,10 +144,10 @@ __global__ void __launch_bounds__(kTrainThreads, 4) nms_forward_kernel(const Tra
         const uint8_t *tg = p.target + size_t(b) * N;
         for (int c = tid; c < M; c += T) sb[c] = s[c] & 1u;
         __syncthreads();   // gam (first shot) and the previous shot's last reads are done
-        for (int u = tid; u < N; u += T) {
-            y[u] = tg[__ldg(p.g.vperm + u)] & 1u;
+        for (int u = tid; u < NV; u += T) {
+            y[u] = lane_target(p.g, tg, u, N);
             const int deg = __ldg(p.g.vdeg + u);
-            for (int k = 0; k < deg; ++k) slots[slot_of(__ldg(p.g.vslot + size_t(k) * N + u), uint32_t(M))] = gam[u];
+            for (int k = 0; k < deg; ++k) slots[slot_of(__ldg(p.g.vslot + size_t(k) * NV + u), uint32_t(M))] = gam[u];
         }
         __syncthreads();
         float acc = 0.0f;
@@ -147,9 +161,10 @@ __global__ void __launch_bounds__(kTrainThreads, 4) nms_forward_kernel(const Tra
             __syncthreads();
             const bool lastk = k + 1 == p.T;
             const float lw = p.loss_w ? __ldg(p.loss_w + k) : 1.0f;
-            for (int u = tid; u < N; u += T) {
-                const float Q = var_step_batch<F32, DV, false>(__ldg(p.g.vdeg + u), u, N, uint32_t(M), p.g.vslot,
+            for (int u = tid; u < NV; u += T) {
+                const float Q = var_step_batch<F32, DV, false>(__ldg(p.g.vdeg + u), u, NV, uint32_t(M), p.g.vslot,
                                                                gam[u], false, slots, nullptr);
+                if (y[u] == kIdleLane) continue;
                 acc += lw * (y[u] ? softplus(Q) : softplus(-Q));
                 if (lastk && p.post) p.post[size_t(b) * N + __ldg(p.g.vperm + u)] = Q;
             }
@@ -176,18 +191,18 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_al
 template <int DC, bool UNIFORM, int DV>
 __global__ void __launch_bounds__(kTrainThreads, 4) nms_backward_kernel(const TrainParams p)
 {
-    const int M = p.g.m, N = p.g.n, T = blockDim.x, tid = threadIdx.x;
+    const int M = p.g.m, N = p.g.n, NV = p.g.nv, T = blockDim.x, tid = threadIdx.x;
     const size_t S = size_t(p.g.dc_max) * M;
     const size_t SW = size_t(kStateWords) * M;                    // state words of one iteration
     extern __shared__ __align__(16) unsigned char smem[];
-    const TrainLayout L = train_layout(M, N, p.g.dc_max, true);
+    const TrainLayout L = train_layout(M, NV, p.g.dc_max, true);
     float *gs = reinterpret_cast<float *>(smem + L.slot_off);     // dL/dq (next iteration), then dL/dr
     float *rs = reinterpret_cast<float *>(smem + L.r_off);        // recomputed r of the current iteration
     uint32_t *scb = reinterpret_cast<uint32_t *>(smem + L.c_off); // recorded state, two iterations
     float *gam = reinterpret_cast<float *>(smem + L.g_off);
     uint8_t *y = smem + L.y_off;
 
-    for (int u = tid; u < N; u += T) gam[u] = F32::quantize(p.prior[__ldg(p.g.vperm + u)]);
+    for (int u = tid; u < NV; u += T) gam[u] = F32::quantize(lane_prior(p.g, p.prior, u, N));
     const float inv = 1.0f / float(N);
     for (int b = blockIdx.x; b < p.batch; b += gridDim.x) {
         const uint8_t *tg = p.target + size_t(b) * N;
@@ -195,7 +210,7 @@ __global__ void __launch_bounds__(kTrainThreads, 4) nms_backward_kernel(const Tr
         const uint32_t *stb = p.state + size_t(b) * p.T * SW;
         __syncthreads();   // gam (first shot) and the previous shot's last reads are done
         prefetch_state(scb, stb + size_t(p.T - 1) * SW, M);
-        for (int u = tid; u < N; u += T) y[u] = tg[__ldg(p.g.vperm + u)] & 1u;
+        for (int u = tid; u < NV; u += T) y[u] = lane_target(p.g, tg, u, N);
         cp_async_wait();
         __syncthreads();
         // iteration T: recompute r; dL/dq of iteration T+1 is zero
@@ -216,14 +231,14 @@ __global__ void __launch_bounds__(kTrainThreads, 4) nms_backward_kernel(const Tr
             if (k > 0) prefetch_state(sn, stb + size_t(k - 1) * SW, M);  // overlaps the variable side
             const float gk = gscale * (p.loss_w ? __ldg(p.loss_w + k) : 1.0f / float(p.T));
             // variable side: Q^(k) from the recomputed r, dL/dQ, and dL/dr for every edge
-            for (int u = tid; u < N; u += T) {
-                const int deg = __ldg(p.g.vdeg + u);
+            for (int u = tid; u < NV; u += T) {
+                const int deg = __ldg(p.g.vdeg + u);   // 0 on idle lanes
                 uint32_t sl[DV];
                 float Q = gam[u], G = 0.0f;
 #pragma unroll
                 for (int i = 0; i < DV; ++i) {
                     if (i < deg) {
-                        sl[i] = slot_of(__ldg(p.g.vslot + size_t(i) * N + u), uint32_t(M));
+                        sl[i] = slot_of(__ldg(p.g.vslot + size_t(i) * NV + u), uint32_t(M));
                         Q = __fadd_rn(Q, rs[sl[i]]);
                         G += gs[sl[i]];
                     }

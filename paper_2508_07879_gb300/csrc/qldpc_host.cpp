@@ -48,20 +48,146 @@ cudaError_t launch_msa(const LaunchParams &p, int precision, const KernelChoice 
 namespace {
 
 // ------------------------------------------------------------------------------------------
+// Variable lanes.  The variable step runs one thread per variable, so a warp's 32 lanes read and
+// write the k-th edge slot of 32 variables at once; slots that share a shared-memory bank (same
+// address mod 32 words) serialise.  For a quasi-cyclic code with lift 31 the plain order puts two
+// circulant blocks in most warps and costs ~2 wavefronts per access.  The lanes are therefore
+// packed per degree class: a warp takes, in order, the first remaining variable whose k-th slots
+// all fall in free banks, and is closed early (idle lanes) when none is left, if that pays.
+// ------------------------------------------------------------------------------------------
+constexpr int kBanks = 32;
+
+// Wavefronts of one warp access: the most distinct words that fall into one bank.
+int warp_wavefronts(const uint32_t *addr, int count)
+{
+    int dist[kBanks] = {0}, worst = count > 0 ? 1 : 0;
+    uint32_t seen[kBanks][kBanks];
+    for (int l = 0; l < count; ++l) {
+        const int b = int(addr[l] % kBanks);
+        bool dup = false;
+        for (int i = 0; i < dist[b]; ++i) dup = dup || seen[b][i] == addr[l];
+        if (!dup) seen[b][dist[b]++] = addr[l];
+        worst = std::max(worst, dist[b]);
+    }
+    return worst;
+}
+
+// Cost model of one variable-step warp: load and store wavefronts of its edge slots, three for
+// Q and gamma, and its instructions (about 8 per edge + 10) at four issues per wavefront cycle.
+double lanes_score(const std::vector<int32_t> &lanes, const std::vector<uint32_t> &eaddr,
+                   const std::vector<int32_t> &cdeg, int dv)
+{
+    double s = 0.0;
+    uint32_t a[kBanks];
+    for (size_t w0 = 0; w0 < lanes.size(); w0 += kBanks) {
+        const size_t w1 = std::min(lanes.size(), w0 + kBanks);
+        int D = -1;
+        for (size_t l = w0; l < w1; ++l)
+            if (lanes[l] >= 0) D = std::max(D, cdeg[size_t(lanes[l])]);
+        if (D < 0) continue;
+        int wf = 0;
+        for (int k = 0; k < D; ++k) {
+            int c = 0;
+            for (size_t l = w0; l < w1; ++l)
+                if (lanes[l] >= 0 && k < cdeg[size_t(lanes[l])]) a[c++] = eaddr[size_t(lanes[l]) * dv + k];
+            wf += warp_wavefronts(a, c);
+        }
+        s += 2.0 * wf + 3.0 + (8.0 * D + 10.0) / 4.0;
+    }
+    return s;
+}
+
+// Greedy packing of one candidate; close_at = fewest lanes a warp keeps before it may close early.
+std::vector<int32_t> pack_lanes(const std::vector<uint32_t> &order, const std::vector<uint32_t> &eaddr,
+                                const std::vector<int32_t> &cdeg, int dv, int close_at)
+{
+    constexpr size_t kScan = 4096;   // candidates examined per lane
+    std::vector<int32_t> lanes;
+    lanes.reserve(order.size() + order.size() / 4 + kBanks);
+    const size_t n = order.size();
+    for (size_t i = 0; i < n;) {
+        const int d = cdeg[order[i]];
+        size_t j = i;
+        while (j < n && cdeg[order[j]] == d) ++j;
+        std::vector<char> taken(j - i, 0);
+        size_t first = 0, left = j - i;
+        while (left > 0) {
+            int64_t owner[16][kBanks];   // word held by bank b for the k-th edges, -1 free
+            for (int k = 0; k < std::max(d, 1) && k < 16; ++k)
+                for (int b = 0; b < kBanks; ++b) owner[k][b] = -1;
+            int filled = 0;
+            while (filled < kBanks && left > 0) {
+                size_t best = SIZE_MAX, scanned = 0;
+                int best_cost = 1 << 30;
+                for (size_t x = first; x < j - i && scanned < kScan; ++x) {
+                    if (taken[x]) continue;
+                    ++scanned;
+                    const uint32_t v = order[i + x];
+                    int c = 0;
+                    for (int k = 0; k < d; ++k) {
+                        const uint32_t a = eaddr[size_t(v) * dv + k];
+                        const int64_t o = owner[k][a % kBanks];
+                        c += (o >= 0 && o != int64_t(a)) ? 1 : 0;
+                    }
+                    if (c < best_cost) {
+                        best_cost = c;
+                        best = x;
+                        if (c == 0) break;
+                    }
+                }
+                if (best_cost > 0 && filled >= close_at) break;
+                taken[best] = 1;
+                --left;
+                const uint32_t v = order[i + best];
+                lanes.push_back(int32_t(v));
+                for (int k = 0; k < d; ++k) {
+                    const uint32_t a = eaddr[size_t(v) * dv + k];
+                    if (owner[k][a % kBanks] < 0) owner[k][a % kBanks] = a;
+                }
+                ++filled;
+                while (first < j - i && taken[first]) ++first;
+            }
+            while (lanes.size() % kBanks) lanes.push_back(-1);
+        }
+        i = j;
+    }
+    return lanes;
+}
+
+// The lanes with the lowest cost among the plain degree order and four packings.
+std::vector<int32_t> choose_lanes(const std::vector<uint32_t> &order, const std::vector<uint32_t> &eaddr,
+                                  const std::vector<int32_t> &cdeg, int dv)
+{
+    std::vector<int32_t> best(order.begin(), order.end());
+    if (dv > 16) return best;
+    double best_s = lanes_score(best, eaddr, cdeg, dv);
+    for (int close_at : {32, 28, 24, 16}) {
+        std::vector<int32_t> c = pack_lanes(order, eaddr, cdeg, dv, close_at);
+        const double s = lanes_score(c, eaddr, cdeg, dv);
+        if (s < best_s) {
+            best_s = s;
+            best.swap(c);
+        }
+    }
+    return best;
+}
+
+// ------------------------------------------------------------------------------------------
 // CSR validation and layout (pure host; runs before any CUDA call)
 // ------------------------------------------------------------------------------------------
 struct HostLayout {
     int32_t dc_max = 0, dv_max = 0;
     bool uniform_rows = true;
     std::vector<uint8_t> rdeg, vdeg;
-    std::vector<uint32_t> vslot;   // [dv_max * n]
-    std::vector<uint32_t> vorder;  // [n] by descending degree, stable
+    std::vector<uint32_t> vslot;   // [dv_max * nv]
+    std::vector<uint32_t> vorder;  // [nv] caller's variable of each lane, n for an idle lane
     std::vector<uint32_t> eslot;   // [nnz] slot j*m + i of CSR edge e
     std::vector<int32_t> slot_edge;// [dc_max * m] CSR edge of each slot, -1 for padding
     std::vector<uint32_t> ecol;    // [dc_max * m] caller's variable of each slot, ~0 for padding
     std::vector<int32_t> layer_ptr;// [nlayers + 1] layered schedule
     std::vector<uint32_t> layer_chk;// [m] checks ordered by (layer, index)
     int32_t max_layer = 0;
+    int32_t nv = 0;               // variable lanes (n + idle lanes)
 };
 
 int validate_and_layout(const int32_t *row_ptr, const int32_t *col_idx, int32_t m, int32_t n,
@@ -95,15 +221,63 @@ int validate_and_layout(const int32_t *row_ptr, const int32_t *col_idx, int32_t 
     out.dc_max = dc_max;
     out.dv_max = dv_max;
     out.rdeg.resize(size_t(m));
-    // internal order: descending degree, stable (ties keep the caller's order)
-    out.vorder.resize(size_t(n));
-    for (int32_t v = 0; v < n; ++v) out.vorder[size_t(v)] = uint32_t(v);
-    std::stable_sort(out.vorder.begin(), out.vorder.end(),
-                     [&](uint32_t a, uint32_t b) { return cdeg[a] > cdeg[b]; });
+    // internal order: descending degree, stable (ties keep the caller's order), then packed into
+    // warps of bank-disjoint slots (idle lanes: vorder = n, degree 0)
+    std::vector<uint32_t> order(static_cast<size_t>(n));
+    for (int32_t v = 0; v < n; ++v) order[size_t(v)] = uint32_t(v);
+    std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return cdeg[a] > cdeg[b]; });
+    const int dv1 = std::max(dv_max, 1);
+    std::vector<uint32_t> eaddr(size_t(n) * size_t(dv1), 0u);   // FP32 slot words, ascending checks
+    {
+        std::vector<int32_t> fill(static_cast<size_t>(n), 0);
+        for (int32_t i = 0; i < m; ++i)
+            for (int32_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+                const int32_t v = col_idx[e];
+                eaddr[size_t(v) * dv1 + size_t(fill[size_t(v)]++)] = uint32_t(e - row_ptr[i]) * uint32_t(m) + uint32_t(i);
+            }
+    }
+    // idle lanes address check m + b, which must fit the 16-bit check field
+    const bool idle_ok = int64_t(m) + kScratch <= 65536;
+    const std::vector<int32_t> lanes = idle_ok ? choose_lanes(order, eaddr, cdeg, dv1)
+                                               : std::vector<int32_t>(order.begin(), order.end());
+    const size_t nv = lanes.size();
+    out.nv = int32_t(nv);
+    out.vorder.assign(nv, uint32_t(n));
     std::vector<uint32_t> internal(static_cast<size_t>(n), 0u);
-    for (int32_t u = 0; u < n; ++u) internal[out.vorder[size_t(u)]] = uint32_t(u);
-    out.vdeg.assign(size_t(n), 0);
-    out.vslot.assign(size_t(std::max(dv_max, 1)) * size_t(n), 0u);
+    for (size_t u = 0; u < nv; ++u)
+        if (lanes[u] >= 0) {
+            out.vorder[u] = uint32_t(lanes[u]);
+            internal[size_t(lanes[u])] = uint32_t(u);
+        }
+    out.vdeg.assign(nv, 0);
+    out.vslot.assign(size_t(dv1) * nv, 0u);
+    // Idle lanes: their warp's degree, every edge on a scratch word (slot dc_max*m + b, parity word
+    // m + b) in a bank the warp's variables leave free for that edge.
+    const uint32_t S_words = uint32_t(dc_max) * uint32_t(m);
+    for (size_t w0 = 0; w0 < nv; w0 += kBanks) {
+        const size_t w1 = std::min(nv, w0 + kBanks);
+        int D = 0;
+        bool any_idle = false;
+        for (size_t l = w0; l < w1; ++l) {
+            if (lanes[l] >= 0)
+                D = std::max(D, cdeg[size_t(lanes[l])]);
+            else
+                any_idle = true;
+        }
+        if (!any_idle) continue;
+        for (int k = 0; k < D; ++k) {
+            bool used[kBanks] = {false};
+            for (size_t l = w0; l < w1; ++l)
+                if (lanes[l] >= 0 && k < cdeg[size_t(lanes[l])]) used[eaddr[size_t(lanes[l]) * dv1 + k] % kBanks] = true;
+            int b = 0;
+            while (b < kBanks - 1 && used[b]) ++b;
+            const uint32_t sw = (uint32_t(b) + kBanks - S_words % kBanks) % kBanks;   // (S + sw) % 32 == b
+            for (size_t l = w0; l < w1; ++l)
+                if (lanes[l] < 0) out.vslot[size_t(k) * nv + l] = (uint32_t(dc_max - 1) << 16) | (uint32_t(m) + sw);
+        }
+        for (size_t l = w0; l < w1; ++l)
+            if (lanes[l] < 0) out.vdeg[l] = uint8_t(D);
+    }
     // Rows are visited in ascending order, so each variable's list is in ascending check order,
     // the order in which the variable step accumulates its sums.
     const size_t S = size_t(dc_max) * size_t(m);
@@ -117,7 +291,7 @@ int validate_and_layout(const int32_t *row_ptr, const int32_t *col_idx, int32_t 
             const uint32_t u = internal[size_t(col_idx[e])];
             const int32_t j = e - row_ptr[i];
             const int32_t k = out.vdeg[u]++;
-            out.vslot[size_t(k) * n + u] = (uint32_t(j) << 16) | uint32_t(i);
+            out.vslot[size_t(k) * nv + u] = (uint32_t(j) << 16) | uint32_t(i);
             const size_t sl = size_t(j) * size_t(m) + size_t(i);
             out.eslot[size_t(e)] = uint32_t(sl);
             out.slot_edge[sl] = e;
@@ -171,7 +345,7 @@ int cuda_status(cudaError_t e)
 
 size_t shot_smem(const qldpc_graph *g, int precision)
 {
-    return smem_layout(g->m, g->n, g->dc_max, msg_bytes(precision)).total;
+    return smem_layout(g->m, g->nv, g->dc_max, msg_bytes(precision)).total;
 }
 
 // Opt in to more than 48 KB of dynamic shared memory once per kernel variant and size.
@@ -275,15 +449,15 @@ int plan_latency(const qldpc_graph *const *gs, int nprob, int32_t batch, int pre
     int one = 32, two = 32;
     size_t smem = 0;
     for (int i = 0; i < nprob; ++i) {
-        one = std::max(one, round32(std::max(gs[i]->m, gs[i]->n)));
-        two = std::max(two, round32(std::max((gs[i]->m + 1) / 2, (gs[i]->n + 1) / 2)));
+        one = std::max(one, round32(std::max(gs[i]->m, gs[i]->nv)));
+        two = std::max(two, round32(std::max((gs[i]->m + 1) / 2, (gs[i]->nv + 1) / 2)));
         smem = std::max(smem, latency_layout(gs[i]->m, gs[i]->dc_max, msg_bytes(precision)).total);
     }
     const int threads = (forced && g0->user_threads) ? g0->user_threads
                                                       : (one <= kLatencyMaxThreads ? one : two);
     bool fits = threads <= kLatencyMaxThreads && smem <= g0->smem_optin;
     for (int i = 0; i < nprob; ++i)
-        fits = fits && gs[i]->m <= kLatencyCnPerThread * threads && gs[i]->n <= kLatencyVnPerThread * threads;
+        fits = fits && gs[i]->m <= kLatencyCnPerThread * threads && gs[i]->nv <= kLatencyVnPerThread * threads;
     if (!fits) return forced ? QLDPC_ERR_UNSUPPORTED : QLDPC_OK;
     pl.kc = variant(gs, nprob, true, learned);
     pl.threads = threads;
@@ -532,6 +706,7 @@ int qldpc_graph_create(const int32_t *row_ptr, const int32_t *col_idx, int32_t m
     g->smem_optin = prop.sharedMemPerBlockOptin;
     g->m = m;
     g->n = n;
+    g->nv = hl.nv;
     g->nnz = row_ptr[m];
     g->dc_max = hl.dc_max;
     g->dv_max = hl.dv_max;
@@ -545,8 +720,8 @@ int qldpc_graph_create(const int32_t *row_ptr, const int32_t *col_idx, int32_t m
     // one device block: vslot | vdeg | rdeg | vperm | eslot | slot_edge | ecol | layer_ptr | layer_chk |
     // shot counters
     constexpr int kArrays = 10;
-    const size_t sizes[kArrays] = {hl.vslot.size() * sizeof(uint32_t), size_t(n), size_t(m),
-                                   size_t(n) * sizeof(uint32_t), hl.eslot.size() * sizeof(uint32_t),
+    const size_t sizes[kArrays] = {hl.vslot.size() * sizeof(uint32_t), size_t(hl.nv), size_t(m),
+                                   size_t(hl.nv) * sizeof(uint32_t), hl.eslot.size() * sizeof(uint32_t),
                                    hl.slot_edge.size() * sizeof(int32_t), hl.ecol.size() * sizeof(uint32_t),
                                    hl.layer_ptr.size() * sizeof(int32_t), hl.layer_chk.size() * sizeof(uint32_t),
                                    size_t(kShotCounterSlots) * 2 * sizeof(int32_t)};
@@ -586,6 +761,7 @@ int qldpc_graph_create(const int32_t *row_ptr, const int32_t *col_idx, int32_t m
     g->dg.nnz = g->nnz;
     g->dg.m = m;
     g->dg.n = n;
+    g->dg.nv = hl.nv;
     g->dg.dc_max = hl.dc_max;
     g->dg.dv_max = hl.dv_max;
     *out = g;
@@ -634,6 +810,15 @@ int qldpc_graph_dims(const qldpc_graph *g, int32_t *m, int32_t *n, int32_t *nnz,
     if (nnz) *nnz = g->nnz;
     if (max_row_degree) *max_row_degree = g->dc_max;
     if (max_col_degree) *max_col_degree = g->dv_max;
+    return QLDPC_OK;
+}
+
+int qldpc_graph_footprint(const qldpc_graph *g, int32_t precision, int32_t *lanes, size_t *shot_bytes)
+{
+    if (!g) return QLDPC_ERR_INVALID_ARG;
+    if (precision != QLDPC_FP32 && precision != QLDPC_INT16 && precision != QLDPC_INT8) return QLDPC_ERR_INVALID_ARG;
+    if (lanes) *lanes = g->nv;
+    if (shot_bytes) *shot_bytes = shot_smem(g, precision);
     return QLDPC_OK;
 }
 

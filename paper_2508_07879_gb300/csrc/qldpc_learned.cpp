@@ -69,8 +69,8 @@ int plan_training_uncached(const qldpc_graph *g, int32_t batch, int32_t T, Train
     tp.fwd = nms_forward_kernel_ptr(tp.tc);
     tp.bwd = nms_backward_kernel_ptr(tp.tc);
     if (!tp.fwd || !tp.bwd) return QLDPC_ERR_UNSUPPORTED;
-    tp.smem_f = train_layout(g->m, g->n, g->dc_max, false).total;
-    tp.smem_b = train_layout(g->m, g->n, g->dc_max, true).total;
+    tp.smem_f = train_layout(g->m, g->nv, g->dc_max, false).total;
+    tp.smem_b = train_layout(g->m, g->nv, g->dc_max, true).total;
     if (int rc = ensure_kernel_attrs(tp.fwd, tp.smem_f, g->smem_optin)) return rc;
     if (int rc = ensure_kernel_attrs(tp.bwd, tp.smem_b, g->smem_optin)) return rc;
     int per_f = 0, per_b = 0;

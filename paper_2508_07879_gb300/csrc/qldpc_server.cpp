@@ -170,8 +170,8 @@ int qldpc_server_create(const qldpc_graph *const *graphs, const float *const *pr
         dc = std::max(dc, g->dc_max);
         dv = std::max(dv, g->dv_max);
         uniform = uniform && g->uniform_rows && g->dc_max == graphs[0]->dc_max;
-        const int one = (std::max(g->m, g->n) + 31) / 32 * 32;
-        const int two = (std::max((g->m + 1) / 2, (g->n + 1) / 2) + 31) / 32 * 32;
+        const int one = (std::max(g->m, g->nv) + 31) / 32 * 32;
+        const int two = (std::max((g->m + 1) / 2, (g->nv + 1) / 2) + 31) / 32 * 32;
         want = std::max(want, one <= kLatencyMaxThreads ? one : two);
         smem = std::max(smem, latency_layout(g->m, g->dc_max, msg_bytes(cfg->precision)).total);
     }
@@ -183,7 +183,7 @@ int qldpc_server_create(const qldpc_graph *const *graphs, const float *const *pr
     bool fits = s->threads >= 32 && s->threads <= kLatencyMaxThreads && s->threads % 32 == 0;
     for (int c = 0; c < ncodes; ++c)
         fits = fits && graphs[c]->m <= kLatencyCnPerThread * s->threads &&
-               graphs[c]->n <= kLatencyVnPerThread * s->threads;
+               graphs[c]->nv <= kLatencyVnPerThread * s->threads;
     s->smem = smem;
     const void *k = cfg->precision == QLDPC_INT16 ? server_kernel_i16(s->kc) : server_kernel_f32(s->kc);
     if (!fits || !k) {

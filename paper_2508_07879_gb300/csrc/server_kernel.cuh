@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(kLatencyMaxThreads, 1) msa_server_kernel(const
     int ci = 0;
     while (ci + 1 < sp.ncodes && int(blockIdx.x) >= sp.code[ci + 1].first_block) ++ci;
     const ServerCode sc = sp.code[ci];
-    const int M = sc.g.m, N = sc.g.n;
+    const int M = sc.g.m, N = sc.g.n, NV = sc.g.nv;
     const int T = blockDim.x, tid = threadIdx.x;
     extern __shared__ __align__(16) unsigned char smem[];
     const LatencyLayout L = latency_layout(M, sc.g.dc_max, int(sizeof(msg_t)));
@@ -115,11 +115,11 @@ __global__ void __launch_bounds__(kLatencyMaxThreads, 1) msa_server_kernel(const
 #pragma unroll
     for (int i = 0; i < kLatVnPerThread; ++i) {
         const int u = tid + i * T;
-        const int v = u < N ? int(__ldg(sc.g.vperm + u)) : N;
+        const int v = u < NV ? int(__ldg(sc.g.vperm + u)) : N;   // N: idle lane
         vid[i] = v;
-        vdeg[i] = u < N ? int(__ldg(sc.g.vdeg + u)) : -1;
+        vdeg[i] = u < NV ? int(__ldg(sc.g.vdeg + u)) : -1;
 #pragma unroll
-        for (int k = 0; k < DV; ++k) ev[i][k] = (k < vdeg[i]) ? __ldg(sc.g.vslot + size_t(k) * N + u) : 0u;
+        for (int k = 0; k < DV; ++k) ev[i][k] = (k < vdeg[i]) ? __ldg(sc.g.vslot + size_t(k) * NV + u) : 0u;
         gam[i] = P::quantize(v < N ? sc.prior[v] : 0.0f);
     }
 

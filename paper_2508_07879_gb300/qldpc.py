@@ -68,6 +68,7 @@ _SIGNATURES = {
     "qldpc_graph_create_csc": ([_p, _p, _i32, _i32, ctypes.POINTER(_p)], ctypes.c_int),
     "qldpc_graph_destroy": ([_p], None),
     "qldpc_graph_dims": ([_p, _p, _p, _p, _p, _p], ctypes.c_int),
+    "qldpc_graph_footprint": ([_p, _i32, ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
     "qldpc_graph_set_launch": ([_p, _i32, _i32, _i32], ctypes.c_int),
     "qldpc_graph_reserve": ([_p, _i32], ctypes.c_int),
     "qldpc_decode": ([_p, _p, _i32, _p, _i32, _f32, _p, _p, _p], ctypes.c_int),
@@ -102,6 +103,7 @@ qldpc_graph_create = _lib.qldpc_graph_create
 qldpc_graph_create_csc = _lib.qldpc_graph_create_csc
 qldpc_graph_destroy = _lib.qldpc_graph_destroy
 qldpc_graph_dims = _lib.qldpc_graph_dims
+qldpc_graph_footprint = _lib.qldpc_graph_footprint
 qldpc_graph_set_launch = _lib.qldpc_graph_set_launch
 qldpc_graph_reserve = _lib.qldpc_graph_reserve
 qldpc_decode = _lib.qldpc_decode
@@ -198,6 +200,13 @@ class Graph:
         vals = [ctypes.c_int32() for _ in range(5)]
         check(qldpc_graph_dims(self._h, *[ctypes.byref(v) for v in vals]), "qldpc_graph_dims")
         return tuple(v.value for v in vals)
+
+    def footprint(self, precision: str = "fp32"):
+        """(variable lanes, shared-memory bytes of one shot in the throughput kernel)."""
+        lanes, nbytes = ctypes.c_int32(), ctypes.c_size_t()
+        check(qldpc_graph_footprint(self._h, PRECISIONS[precision], ctypes.byref(lanes), ctypes.byref(nbytes)),
+              "qldpc_graph_footprint")
+        return lanes.value, nbytes.value
 
     def set_launch(self, kernel: str = "auto", threads_per_block: int = 0, blocks_per_sm: int = 0) -> None:
         """Force a kernel ("batch" / "latency") and optionally its shape; "auto" restores the default."""

@@ -116,6 +116,7 @@ def test_decode_rejects_null_graph(q):
     assert q.qldpc_decode_host(None, None, 0, None, 10, 0.75, None, None, None, 0, 0, None) \
         == q.QLDPC_ERR_INVALID_ARG
     assert q.qldpc_graph_dims(None, None, None, None, None, None) == q.QLDPC_ERR_INVALID_ARG
+    assert q.qldpc_graph_footprint(None, 0, None, None) == q.QLDPC_ERR_INVALID_ARG
     assert q.qldpc_graph_set_launch(None, 0, 0, 0) == q.QLDPC_ERR_INVALID_ARG
     q.qldpc_graph_destroy(None)
 

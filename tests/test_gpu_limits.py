@@ -31,16 +31,46 @@ def qc_code(L, seed=1):
     return w.csr_from_dense(h)
 
 
-def fp32_shot_bytes(m, n, dc):
-    """Shared memory of one FP32 shot of the batch kernel: Q and gamma [n], parity words [m],
-    messages [dc * m], each section 16-byte aligned."""
+def fp32_shot_bytes(m, lanes, dc):
+    """Shared memory of one FP32 shot of the batch kernel: Q and gamma [lanes], parity words
+    [m + 32], messages [dc * m + 32] (32 scratch entries each for idle lanes), each section 16-byte
+    aligned."""
     a16 = lambda x: (x + 15) // 16 * 16
-    return a16(a16(a16(a16(4 * n) + 4 * n) + 4 * m) + 4 * dc * m)
+    return a16(a16(a16(a16(4 * lanes) + 4 * lanes) + 4 * (m + 32)) + 4 * (dc * m + 32))
+
+
+def test_footprint_formula_and_lanes(q):
+    """The reported footprint follows the layout above; the lift-31 code packs 31 variables and
+    one idle lane per warp (34 warps), the 144- and 288-qubit codes need no idle lane."""
+    for code, lanes_want in ((w.lp_code(1054), 1088), (w.bb_code(12, 6), 144), (w.bb_code(12, 12), 288)):
+        h = code.hz_csr
+        g = q.Graph.from_csr(h)
+        lanes, nbytes = g.footprint("fp32")
+        assert lanes == lanes_want
+        assert nbytes == fp32_shot_bytes(h.m, lanes, int(h.row_degrees().max()))
+        l16, b16 = g.footprint("int16")
+        assert l16 == lanes and b16 < nbytes
+        g.close()
 
 
 def test_largest_graph_that_fits(q):
     optin = getattr(torch.cuda.get_device_properties(0), "shared_memory_per_block_optin", 232448)
-    L = max(l for l in range(16, 20000, 8) if fp32_shot_bytes(3 * l, 6 * l, 6) <= optin)
+
+    def fp32_bytes(L):
+        g = q.Graph.from_csr(qc_code(L))
+        try:
+            return g.footprint("fp32")[1]
+        finally:
+            g.close()
+
+    lo, hi = 16, 16
+    while fp32_bytes(hi) <= optin:                      # bracket the boundary, then bisect (step 8)
+        lo, hi = hi, hi * 2
+    while hi - lo > 8:
+        mid = (lo + hi) // 16 * 8
+        lo, hi = (mid, hi) if fp32_bytes(mid) <= optin else (lo, mid)
+    L = lo
+    assert fp32_bytes(L) <= optin < fp32_bytes(L + 8)
     h = qc_code(L)
     g = q.Graph.from_csr(h)
     e = w.iid_x_errors(h.n, 0.02, 200, seed=5)
@@ -56,8 +86,8 @@ def test_largest_graph_that_fits(q):
     assert ref["ok"].mean() > 0.5
     # one circulant size larger: the FP32 shot no longer fits and the decode is refused
     big = qc_code(L + 8)
-    assert fp32_shot_bytes(big.m, big.n, 6) > optin
     gb = q.Graph.from_csr(big)            # INT16 still fits, so the graph itself is accepted
+    assert gb.footprint("fp32")[1] > optin >= gb.footprint("int16")[1]
     sb = torch.zeros((4, big.m), dtype=torch.uint8, device="cuda")
     with pytest.raises(q.QldpcError) as ei:
         q.decode(gb, sb, torch.full((big.n,), 3.0, device="cuda"), 10, precision="fp32")

@@ -140,10 +140,10 @@ QLDPC_API int qldpc_graph_dims(const qldpc_graph *g, int32_t *m, int32_t *n, int
  *               degree and packed into warps whose k-th edge slots fall in distinct shared-memory
  *               banks; an idle lane closes a warp early where that pays)
  *   shot_bytes  shared memory one shot takes in the throughput kernel: Q and gamma (4 B per lane),
- *               parity words (4 B per check), messages (max_row_degree * m slots), each section
- *               16-byte aligned and the last two with 32 scratch entries for the idle lanes.
- *               A decode whose shot_bytes exceeds the device's shared memory per block is refused
- *               with UNSUPPORTED.
+ *               parity words (4 B per check), messages (max_row_degree * m slots and 32 scratch
+ *               slots for the idle lanes), each section 16-byte aligned.  A decode whose
+ *               shot_bytes plus the kernel's few bytes of static shared memory exceed the
+ *               device's shared memory per block is refused with UNSUPPORTED.
  * Either output pointer may be NULL.  INVALID_ARG: null graph or unknown precision. */
 QLDPC_API int qldpc_graph_footprint(const qldpc_graph *g, int32_t precision, int32_t *lanes, size_t *shot_bytes);
 

@@ -123,9 +123,18 @@ __device__ __forceinline__ typename P::acc_t load_msg(const typename P::msg_t *s
 // Flip the decision bit of one check's parity word (exact: integer XOR in shared memory).
 __device__ __forceinline__ void flip_check(uint32_t *parity, uint32_t m) { atomicXor(parity + m, 1u); }
 
-// Edge-list entry: position j of the edge in its check's row (bits 16..20), check m (bits 0..15).
-__device__ __forceinline__ uint32_t slot_of(uint32_t e, uint32_t M) { return (e >> 16) * M + (e & 0xffffu); }
-__device__ __forceinline__ uint32_t check_of(uint32_t e) { return e & 0xffffu; }
+// Edge-list entries are slot indices j*M + m; the check of a slot is needed only when a decision
+// flips: m = slot - M * floor(slot / M), the quotient by a multiply-high with a magic number the
+// host verified for every slot (Granlund and Montgomery, PLDI 1994).
+struct CheckOf {
+    uint32_t M, magic, shift;
+    __device__ __forceinline__ explicit CheckOf(const DeviceGraph &g)
+        : M(uint32_t(g.m)), magic(g.m_magic), shift(uint32_t(g.m_shift)) {}
+    __device__ __forceinline__ uint32_t operator()(uint32_t slot) const
+    {
+        return M == 1u ? 0u : slot - M * (__umulhi(slot, magic) >> shift);
+    }
+};
 
 // ---------------------------------------------------------------------------------------------
 // Check-node step (Alg. 1, CN processing) of one check, fused with the stop test of the previous
@@ -189,7 +198,7 @@ __device__ __forceinline__ int check_step(int c, int M, int deg, uint32_t pw, bo
 // ---------------------------------------------------------------------------------------------
 // TRACK = false (training forward): no decision tracking, parity may be null.
 template <class P, int D, bool TRACK = true>
-__device__ __forceinline__ typename P::acc_t var_step_exact(const uint32_t *e, uint32_t M, typename P::acc_t gamma,
+__device__ __forceinline__ typename P::acc_t var_step_exact(const uint32_t *sl, const CheckOf &ck, typename P::acc_t gamma,
                                                             bool prev, typename P::msg_t *__restrict__ slots,
                                                             uint32_t *__restrict__ parity)
 {
@@ -197,10 +206,7 @@ __device__ __forceinline__ typename P::acc_t var_step_exact(const uint32_t *e, u
     if constexpr (D == 0) {
         return gamma;
     } else {
-        uint32_t sl[D];
         acc_t r[D];
-#pragma unroll
-        for (int k = 0; k < D; ++k) sl[k] = slot_of(e[k], M);
 #pragma unroll
         for (int k = 0; k < D; ++k) r[k] = load_msg<P>(slots, sl[k]);
         acc_t pre[D + 1];
@@ -217,7 +223,7 @@ __device__ __forceinline__ typename P::acc_t var_step_exact(const uint32_t *e, u
         }
         if (TRACK && P::neg(Q) != prev) {
 #pragma unroll
-            for (int k = 0; k < D; ++k) flip_check(parity, check_of(e[k]));
+            for (int k = 0; k < D; ++k) flip_check(parity, ck(sl[k]));
         }
         return Q;
     }
@@ -227,27 +233,27 @@ __device__ __forceinline__ typename P::acc_t var_step_exact(const uint32_t *e, u
 
 // Batch variant: the edge list comes from global memory (L1-resident).
 template <class P, int D, bool TRACK = true>
-__device__ __forceinline__ typename P::acc_t var_step_global(int v, int N, uint32_t M, const uint32_t *__restrict__ vslot,
+__device__ __forceinline__ typename P::acc_t var_step_global(int v, int N, const CheckOf &ck, const uint32_t *__restrict__ vslot,
                                                              typename P::acc_t gamma, bool prev,
                                                              typename P::msg_t *slots, uint32_t *parity)
 {
     uint32_t e[D > 0 ? D : 1];
 #pragma unroll
     for (int k = 0; k < D; ++k) e[k] = __ldg(vslot + size_t(k) * N + v);
-    return var_step_exact<P, D, TRACK>(e, M, gamma, prev, slots, parity);
+    return var_step_exact<P, D, TRACK>(e, ck, gamma, prev, slots, parity);
 }
 
 // Variable step of the batch kernel for one variable: dispatch on its degree (internal variables
 // are sorted by degree, so the lanes of a warp almost always take the same case).
 template <class P, int DV, bool TRACK = true>
-__device__ __forceinline__ typename P::acc_t var_step_batch(int deg, int u, int N, uint32_t M, const uint32_t *vslot,
+__device__ __forceinline__ typename P::acc_t var_step_batch(int deg, int u, int N, const CheckOf &ck, const uint32_t *vslot,
                                                             typename P::acc_t gamma, bool prev,
                                                             typename P::msg_t *slots, uint32_t *parity)
 {
     switch (deg) {
 #define QLDPC_CASE(D)                                                                           \
     case D:                                                                                     \
-        if constexpr (D <= DV) return var_step_global<P, D, TRACK>(u, N, M, vslot, gamma, prev, slots, parity); \
+        if constexpr (D <= DV) return var_step_global<P, D, TRACK>(u, N, ck, vslot, gamma, prev, slots, parity); \
         break;
         QLDPC_DEG_CASES(QLDPC_CASE)
 #undef QLDPC_CASE
@@ -268,14 +274,15 @@ __device__ __forceinline__ void batch_init_shot(const Problem &pr, const uint8_t
 {
     for (int c = tid; c < M; c += T) parity[c] = (s[c] & 1u) * 3u;
     __syncthreads();
+    const CheckOf ck(pr.g);
     for (int u = tid; u < N; u += T) {
         const typename P::acc_t g = gam[u];
         const int deg = __ldg(pr.g.vdeg + u);
         const bool d = P::neg(g);
         for (int k = 0; k < deg; ++k) {
             const uint32_t e = __ldg(pr.g.vslot + size_t(k) * N + u);
-            slots[slot_of(e, uint32_t(M))] = P::to_msg(g);
-            if (d) flip_check(parity, check_of(e));
+            slots[e] = P::to_msg(g);
+            if (d) flip_check(parity, ck(e));
         }
         Qs[u] = g;
     }
@@ -365,7 +372,7 @@ __global__ void __launch_bounds__(1024, 1) msa_batch_kernel(const LaunchParams p
                 continue;
             }
             for (int u = tid; u < NV; u += T)
-                Qs[u] = var_step_batch<P, DV>(__ldg(pr.g.vdeg + u), u, NV, uint32_t(M), pr.g.vslot, gam[u],
+                Qs[u] = var_step_batch<P, DV>(__ldg(pr.g.vdeg + u), u, NV, CheckOf(pr.g), pr.g.vslot, gam[u],
                                               P::neg(Qs[u]), slots, parity);
             __syncthreads();
             ++k;
@@ -394,14 +401,14 @@ constexpr int kLatCnPerThread = kLatencyCnPerThread;   // checks per thread: M <
 constexpr int kLatVnPerThread = kLatencyVnPerThread;   // variables per thread: N <= 2*blockDim
 
 template <class P, int DV>
-__device__ __forceinline__ typename P::acc_t var_step_regs(int deg, const uint32_t *e, uint32_t M,
+__device__ __forceinline__ typename P::acc_t var_step_regs(int deg, const uint32_t *e, const CheckOf &ck,
                                                            typename P::acc_t gamma, bool prev,
                                                            typename P::msg_t *slots, uint32_t *parity)
 {
     switch (deg) {
 #define QLDPC_CASE(D)                                                                           \
     case D:                                                                                     \
-        if constexpr (D <= DV) return var_step_exact<P, D>(e, M, gamma, prev, slots, parity);  \
+        if constexpr (D <= DV) return var_step_exact<P, D>(e, ck, gamma, prev, slots, parity); \
         break;
         QLDPC_DEG_CASES(QLDPC_CASE)
 #undef QLDPC_CASE
@@ -486,8 +493,8 @@ __global__ void __launch_bounds__(kLatencyMaxThreads, 1) msa_latency_kernel(cons
 #pragma unroll
                 for (int k = 0; k < DV; ++k) {
                     if (k < vdeg[i]) {
-                        slots[slot_of(ev[i][k], uint32_t(M))] = P::to_msg(gam[i]);
-                        if (d) flip_check(parity, check_of(ev[i][k]));
+                        slots[ev[i][k]] = P::to_msg(gam[i]);
+                        if (d) flip_check(parity, CheckOf(pr.g)(ev[i][k]));
                     }
                 }
             }
@@ -520,7 +527,7 @@ __global__ void __launch_bounds__(kLatencyMaxThreads, 1) msa_latency_kernel(cons
 #pragma unroll
             for (int i = 0; i < kLatVnPerThread; ++i)
                 if (vdeg[i] >= 0)
-                    Q[i] = var_step_regs<P, DV>(vdeg[i], ev[i], uint32_t(M), gam[i], P::neg(Q[i]), slots, parity);
+                    Q[i] = var_step_regs<P, DV>(vdeg[i], ev[i], CheckOf(pr.g), gam[i], P::neg(Q[i]), slots, parity);
             __syncthreads();
             ++k;
         }

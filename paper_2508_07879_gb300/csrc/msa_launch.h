@@ -15,11 +15,12 @@ namespace qldpc {
 // grouped by descending degree and packed so that the k-th slots of a warp's 32 variables fall in
 // distinct shared-memory banks where possible, with idle lanes (vperm = n) closing a warp early.
 // Lane u holds the caller's variable vperm[u]; the k-th edge of lane u (ascending check order) is
-// vslot[k*nv + u] = j << 16 | i.  An idle lane has its warp's degree and edges j = dc_max - 1,
-// i = m + b (b < kScratch): slot dc_max*m + b and parity word m + b, scratch that no check step
-// reads, in a bank its warp leaves free, so it runs its warp's path without divergence.
+// the slot vslot[k*nv + u] = j*m + i, and i = slot mod m (m_magic, m_shift) when a decision
+// flips.  An idle lane has its warp's degree and every edge on a scratch slot dc_max*m + b
+// (b < kScratch) in a bank its warp leaves free, so it runs its warp's path without divergence;
+// its prior is 0 and its scratch slots hold 0, so its decision never flips.
 struct DeviceGraph {
-    const uint32_t *vslot;   // [dv_max * nv] (j << 16) | check of lane u's k-th edge
+    const uint32_t *vslot;   // [dv_max * nv] slot j*m + i of lane u's k-th edge
     const uint8_t *vdeg;     // [nv] column degree of lane u (idle: its warp's degree)
     const uint8_t *rdeg;     // [m] row degrees
     const uint32_t *vperm;   // [nv] caller's index of the variable in lane u (n: idle lane)
@@ -31,6 +32,8 @@ struct DeviceGraph {
     int32_t nlayers, max_layer;
     int32_t m, n, nnz;
     int32_t nv;              // variable lanes (n <= nv)
+    uint32_t m_magic;        // floor(slot / m) = umulhi(slot, m_magic) >> m_shift for every slot
+    int32_t m_shift;
     int32_t dc_max, dv_max;  // largest row / column degree
 };
 
@@ -65,8 +68,8 @@ constexpr int kShotCounterSlots = 1024;
 
 constexpr uint32_t kFlagNoEarlyStop = 1u;
 
-// Idle variable lanes (see DeviceGraph) read and write one of kScratch words past the last slot
-// and flip one of kScratch parity words past the last check; no check step reads either.
+// Idle variable lanes (see DeviceGraph) read and write one of kScratch words past the last slot,
+// which no check step reads.
 constexpr int kScratch = 32;
 
 // Shared-memory layout of one shot in the batch kernel (identical on host and device);
@@ -82,8 +85,8 @@ __host__ __device__ inline SmemLayout smem_layout(int m, int n, int dc_max, int 
     SmemLayout s;
     s.q_off = 0;                                                       // a-posteriori Q_n [n] (4 B)
     s.g_off = align16(s.q_off + size_t(n) * 4);                        // prior gamma_n    [n] (4 B)
-    s.par_off = align16(s.g_off + size_t(n) * 4);                      // parity words [m + scratch]
-    s.slot_off = align16(s.par_off + size_t(m + kScratch) * 4);        // messages [dc_max*m + scratch]
+    s.par_off = align16(s.g_off + size_t(n) * 4);                      // parity words     [m] (4 B)
+    s.slot_off = align16(s.par_off + size_t(m) * 4);                   // messages [dc_max*m + scratch]
     s.total = align16(s.slot_off + (size_t(dc_max) * m + kScratch) * msg_bytes);
     return s;
 }
@@ -97,7 +100,7 @@ __host__ __device__ inline LatencyLayout latency_layout(int m, int dc_max, int m
 {
     LatencyLayout s;
     s.par_off = 0;
-    s.slot_off = align16(size_t(m + kScratch) * 4);
+    s.slot_off = align16(size_t(m) * 4);
     s.total = align16(s.slot_off + (size_t(dc_max) * m + kScratch) * msg_bytes);
     return s;
 }

@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(kTrainThreads, 4) nms_forward_kernel(const Tra
         for (int u = tid; u < NV; u += T) {
             y[u] = lane_target(p.g, tg, u, N);
             const int deg = __ldg(p.g.vdeg + u);
-            for (int k = 0; k < deg; ++k) slots[slot_of(__ldg(p.g.vslot + size_t(k) * NV + u), uint32_t(M))] = gam[u];
+            for (int k = 0; k < deg; ++k) slots[__ldg(p.g.vslot + size_t(k) * NV + u)] = gam[u];
         }
         __syncthreads();
         float acc = 0.0f;
@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(kTrainThreads, 4) nms_forward_kernel(const Tra
             const bool lastk = k + 1 == p.T;
             const float lw = p.loss_w ? __ldg(p.loss_w + k) : 1.0f;
             for (int u = tid; u < NV; u += T) {
-                const float Q = var_step_batch<F32, DV, false>(__ldg(p.g.vdeg + u), u, NV, uint32_t(M), p.g.vslot,
+                const float Q = var_step_batch<F32, DV, false>(__ldg(p.g.vdeg + u), u, NV, CheckOf(p.g), p.g.vslot,
                                                                gam[u], false, slots, nullptr);
                 if (y[u] == kIdleLane) continue;
                 acc += lw * (y[u] ? softplus(Q) : softplus(-Q));
@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(kTrainThreads, 4) nms_backward_kernel(const Tr
 #pragma unroll
                 for (int i = 0; i < DV; ++i) {
                     if (i < deg) {
-                        sl[i] = slot_of(__ldg(p.g.vslot + size_t(i) * NV + u), uint32_t(M));
+                        sl[i] = __ldg(p.g.vslot + size_t(i) * NV + u);
                         Q = __fadd_rn(Q, rs[sl[i]]);
                         G += gs[sl[i]];
                     }

@@ -188,6 +188,8 @@ struct HostLayout {
     std::vector<uint32_t> layer_chk;// [m] checks ordered by (layer, index)
     int32_t max_layer = 0;
     int32_t nv = 0;               // variable lanes (n + idle lanes)
+    uint32_t m_magic = 0;         // slot / m = umulhi(slot, m_magic) >> m_shift
+    int32_t m_shift = 0;
 };
 
 int validate_and_layout(const int32_t *row_ptr, const int32_t *col_idx, int32_t m, int32_t n,
@@ -236,10 +238,7 @@ int validate_and_layout(const int32_t *row_ptr, const int32_t *col_idx, int32_t 
                 eaddr[size_t(v) * dv1 + size_t(fill[size_t(v)]++)] = uint32_t(e - row_ptr[i]) * uint32_t(m) + uint32_t(i);
             }
     }
-    // idle lanes address check m + b, which must fit the 16-bit check field
-    const bool idle_ok = int64_t(m) + kScratch <= 65536;
-    const std::vector<int32_t> lanes = idle_ok ? choose_lanes(order, eaddr, cdeg, dv1)
-                                               : std::vector<int32_t>(order.begin(), order.end());
+    const std::vector<int32_t> lanes = choose_lanes(order, eaddr, cdeg, dv1);
     const size_t nv = lanes.size();
     out.nv = int32_t(nv);
     out.vorder.assign(nv, uint32_t(n));
@@ -251,8 +250,8 @@ int validate_and_layout(const int32_t *row_ptr, const int32_t *col_idx, int32_t 
         }
     out.vdeg.assign(nv, 0);
     out.vslot.assign(size_t(dv1) * nv, 0u);
-    // Idle lanes: their warp's degree, every edge on a scratch word (slot dc_max*m + b, parity word
-    // m + b) in a bank the warp's variables leave free for that edge.
+    // Idle lanes: their warp's degree, every edge on a scratch slot dc_max*m + b in a bank the
+    // warp's variables leave free for that edge.
     const uint32_t S_words = uint32_t(dc_max) * uint32_t(m);
     for (size_t w0 = 0; w0 < nv; w0 += kBanks) {
         const size_t w1 = std::min(nv, w0 + kBanks);
@@ -273,7 +272,7 @@ int validate_and_layout(const int32_t *row_ptr, const int32_t *col_idx, int32_t 
             while (b < kBanks - 1 && used[b]) ++b;
             const uint32_t sw = (uint32_t(b) + kBanks - S_words % kBanks) % kBanks;   // (S + sw) % 32 == b
             for (size_t l = w0; l < w1; ++l)
-                if (lanes[l] < 0) out.vslot[size_t(k) * nv + l] = (uint32_t(dc_max - 1) << 16) | (uint32_t(m) + sw);
+                if (lanes[l] < 0) out.vslot[size_t(k) * nv + l] = S_words + sw;
         }
         for (size_t l = w0; l < w1; ++l)
             if (lanes[l] < 0) out.vdeg[l] = uint8_t(D);
@@ -291,12 +290,31 @@ int validate_and_layout(const int32_t *row_ptr, const int32_t *col_idx, int32_t 
             const uint32_t u = internal[size_t(col_idx[e])];
             const int32_t j = e - row_ptr[i];
             const int32_t k = out.vdeg[u]++;
-            out.vslot[size_t(k) * nv + u] = (uint32_t(j) << 16) | uint32_t(i);
+            out.vslot[size_t(k) * nv + u] = uint32_t(j) * uint32_t(m) + uint32_t(i);
             const size_t sl = size_t(j) * size_t(m) + size_t(i);
             out.eslot[size_t(e)] = uint32_t(sl);
             out.slot_edge[sl] = e;
             out.ecol[sl] = uint32_t(col_idx[e]);
         }
+    }
+    // floor(slot / m) for every slot (scratch included) as a multiply-high and a shift: the
+    // smallest shift whose rounded-up reciprocal fits 32 bits and divides every slot exactly.
+    {
+        const uint32_t limit = S_words + uint32_t(kScratch);
+        bool found = m == 1;   // one check: every slot belongs to it (the kernels test m == 1)
+        for (uint32_t sh = 0; sh < 32 && !found; ++sh) {
+            const uint64_t mg = ((uint64_t(1) << (32 + sh)) + uint64_t(m) - 1) / uint64_t(m);
+            if (mg >> 32) break;
+            bool exact = true;
+            for (uint32_t x = 0; x < limit && exact; ++x)
+                exact = uint32_t((uint64_t(x) * mg) >> (32 + sh)) == x / uint32_t(m);
+            if (exact) {
+                out.m_magic = uint32_t(mg);
+                out.m_shift = int32_t(sh);
+                found = true;
+            }
+        }
+        if (!found) return QLDPC_ERR_UNSUPPORTED;
     }
     // Layered schedule: a check's layer is one more than the largest layer of an earlier check it
     // shares a variable with, so checks of one layer share no variable and every pair of checks
@@ -349,19 +367,34 @@ size_t shot_smem(const qldpc_graph *g, int precision)
 }
 
 // Opt in to more than 48 KB of dynamic shared memory once per kernel variant and size.
+// The kernel's own static shared memory counts against the same per-block limit, so a launch
+// whose dynamic part fits only without it is refused here (UNSUPPORTED) rather than failing.
 int ensure_kernel_attrs(const void *k, size_t smem, size_t smem_optin)
 {
+    struct Entry {
+        const void *k;
+        size_t static_bytes, granted;
+    };
     static std::mutex mu;
-    static std::vector<std::pair<const void *, size_t>> granted;
+    static std::vector<Entry> known;
     if (!k) return QLDPC_ERR_UNSUPPORTED;
     if (smem > smem_optin) return QLDPC_ERR_UNSUPPORTED;
-    if (smem <= 48 * 1024) return QLDPC_OK;
     std::lock_guard<std::mutex> lk(mu);
-    for (auto &kv : granted)
-        if (kv.first == k && kv.second >= smem) return QLDPC_OK;
+    Entry *en = nullptr;
+    for (auto &x : known)
+        if (x.k == k) en = &x;
+    if (!en) {
+        cudaFuncAttributes fa{};
+        cudaError_t e = cudaFuncGetAttributes(&fa, k);
+        if (e != cudaSuccess) return cuda_status(e);
+        known.push_back(Entry{k, fa.sharedSizeBytes, 0});
+        en = &known.back();
+    }
+    if (smem + en->static_bytes > smem_optin) return QLDPC_ERR_UNSUPPORTED;
+    if (smem + en->static_bytes <= 48 * 1024 || en->granted >= smem) return QLDPC_OK;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return cuda_status(e);
-    granted.emplace_back(k, smem);
+    en->granted = smem;
     return QLDPC_OK;
 }
 
@@ -762,6 +795,8 @@ int qldpc_graph_create(const int32_t *row_ptr, const int32_t *col_idx, int32_t m
     g->dg.m = m;
     g->dg.n = n;
     g->dg.nv = hl.nv;
+    g->dg.m_magic = hl.m_magic;
+    g->dg.m_shift = hl.m_shift;
     g->dg.dc_max = hl.dc_max;
     g->dg.dv_max = hl.dv_max;
     *out = g;

@@ -148,8 +148,8 @@ __global__ void __launch_bounds__(kLatencyMaxThreads, 1) msa_server_kernel(const
 #pragma unroll
                 for (int k = 0; k < DV; ++k) {
                     if (k < vdeg[i]) {
-                        slots[slot_of(ev[i][k], uint32_t(M))] = P::to_msg(gam[i]);
-                        if (d) flip_check(parity, check_of(ev[i][k]));
+                        slots[ev[i][k]] = P::to_msg(gam[i]);
+                        if (d) flip_check(parity, CheckOf(sc.g)(ev[i][k]));
                     }
                 }
             }
@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(kLatencyMaxThreads, 1) msa_server_kernel(const
 #pragma unroll
             for (int i = 0; i < kLatVnPerThread; ++i)
                 if (vdeg[i] >= 0)
-                    Q[i] = var_step_regs<P, DV>(vdeg[i], ev[i], uint32_t(M), gam[i], P::neg(Q[i]), slots, parity);
+                    Q[i] = var_step_regs<P, DV>(vdeg[i], ev[i], CheckOf(sc.g), gam[i], P::neg(Q[i]), slots, parity);
             __syncthreads();
             ++k;
         }

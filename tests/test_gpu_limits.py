@@ -32,11 +32,10 @@ def qc_code(L, seed=1):
 
 
 def fp32_shot_bytes(m, lanes, dc):
-    """Shared memory of one FP32 shot of the batch kernel: Q and gamma [lanes], parity words
-    [m + 32], messages [dc * m + 32] (32 scratch entries each for idle lanes), each section 16-byte
-    aligned."""
+    """Shared memory of one FP32 shot of the batch kernel: Q and gamma [lanes], parity words [m],
+    messages [dc * m + 32] (32 scratch slots for idle lanes), each section 16-byte aligned."""
     a16 = lambda x: (x + 15) // 16 * 16
-    return a16(a16(a16(a16(4 * lanes) + 4 * lanes) + 4 * (m + 32)) + 4 * (dc * m + 32))
+    return a16(a16(a16(a16(4 * lanes) + 4 * lanes) + 4 * m) + 4 * (dc * m + 32))
 
 
 def test_footprint_formula_and_lanes(q):
@@ -63,14 +62,19 @@ def test_largest_graph_that_fits(q):
         finally:
             g.close()
 
-    lo, hi = 16, 16
-    while fp32_bytes(hi) <= optin:                      # bracket the boundary, then bisect (step 8)
-        lo, hi = hi, hi * 2
-    while hi - lo > 8:
-        mid = (lo + hi) // 16 * 8
-        lo, hi = (mid, hi) if fp32_bytes(mid) <= optin else (lo, mid)
-    L = lo
-    assert fp32_bytes(L) <= optin < fp32_bytes(L + 8)
+    def boundary(limit):
+        # largest L (step 8) whose shot fits `limit` bytes: bracket, then bisect
+        lo, hi = 16, 16
+        while fp32_bytes(hi) <= limit:
+            lo, hi = hi, hi * 2
+        while hi - lo > 8:
+            mid = (lo + hi) // 16 * 8
+            lo, hi = (mid, hi) if fp32_bytes(mid) <= limit else (lo, mid)
+        return lo
+
+    # the kernel adds a few bytes of static shared memory: leave it 256 bytes
+    L = boundary(optin - 256)
+    assert fp32_bytes(L) <= optin - 256 < fp32_bytes(L + 8)
     h = qc_code(L)
     g = q.Graph.from_csr(h)
     e = w.iid_x_errors(h.n, 0.02, 200, seed=5)
@@ -84,8 +88,19 @@ def test_largest_graph_that_fits(q):
     np.testing.assert_array_equal(iters.cpu().numpy(), ref["iters"])
     np.testing.assert_array_equal(post.cpu().numpy(), ref["post"])
     assert ref["ok"].mean() > 0.5
-    # one circulant size larger: the FP32 shot no longer fits and the decode is refused
-    big = qc_code(L + 8)
+    # sizes up to the first whose shot exceeds the limit itself: decoded or refused, never a
+    # launch failure; that first size is refused and still decodes in INT16
+    Lx = boundary(optin) + 8
+    for Lm in range(L + 8, Lx, 8):
+        hm = qc_code(Lm)
+        gm = q.Graph.from_csr(hm)
+        try:
+            q.decode(gm, torch.zeros((4, hm.m), dtype=torch.uint8, device="cuda"),
+                     torch.full((hm.n,), 3.0, device="cuda"), 10, precision="fp32")
+        except q.QldpcError as ex:
+            assert ex.status == q.QLDPC_ERR_UNSUPPORTED
+        gm.close()
+    big = qc_code(Lx)
     gb = q.Graph.from_csr(big)            # INT16 still fits, so the graph itself is accepted
     assert gb.footprint("fp32")[1] > optin >= gb.footprint("int16")[1]
     sb = torch.zeros((4, big.m), dtype=torch.uint8, device="cuda")

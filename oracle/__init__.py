@@ -74,7 +74,7 @@ def _load():
             lib.oracle_alpha_q.restype = ctypes.c_int
             for name in ("oracle_nms_train_f64", "oracle_nms_train_f32"):
                 f = getattr(lib, name)
-                f.argtypes = [p, p, i32, i32, p, p, i32, p, p, i32, p, p, p, p, p]
+                f.argtypes = [p, p, i32, i32, p, p, i32, p, p, i32, p, i32, p, p, p, p]
                 f.restype = ctypes.c_int
             lib.oracle_nms_decode_f32.argtypes = [p, p, i32, i32, p, i32, p, p, i32, i32, ctypes.c_float,
                                                   p, p, p, p, p]
@@ -198,17 +198,21 @@ def _layered(row_ptr, col_idx, m, n, syndromes, prior, max_iter, alpha, precisio
 # Neural normalized min-sum (learned weights w[t][e], CSR edge order)
 # ------------------------------------------------------------------------------------------------
 def nms_train(row_ptr, col_idx, m, n, syndromes, targets, prior, weights, grad_loss=None,
-              precision: str = "f64", post: bool = False, threads: int = 1, loss_weights=None):
+              precision: str = "f64", post: bool = False, threads: int = 1, loss_weights=None,
+              loss: str = "error"):
     """Training pass of the neural min-sum decoder: T iterations, no stop test.
 
     weights: [T, E] (E = nnz, CSR edge order).  precision "f64" or "f32" is the type the forward
     runs in; losses and gradients are always float64.  loss_weights: [T] per-iteration weights
-    lambda_t (None: 1/T each).  Returns a dict with
-      loss [B]          sum_t lambda_t / n sum_v BCE(sigma(-Q^t_v), y_v)
+    lambda_t (None: 1/T each).  loss "error": BCE of sigma(-Q) against the sampled error;
+    "syndrome": BCE of the soft syndrome against s (targets unused).  Returns a dict with
+      loss [B]          sum_t lambda_t / n sum_v BCE(sigma(-Q^t_v), y_v)   ("error"), or
+                        sum_t lambda_t / m sum_c -log P^t_c                 ("syndrome")
       post [B, T, n]    Q^t of every iteration (only with post=True)
       grad [T, E]       sum_b grad_loss[b] d loss_b / d w (only when grad_loss is given)
     """
     lib = _load()
+    kind = {"error": 0, "syndrome": 1}[loss]
     if precision == "f64":
         fn, real = lib.oracle_nms_train_f64, np.float64
     elif precision == "f32":
@@ -223,7 +227,7 @@ def nms_train(row_ptr, col_idx, m, n, syndromes, targets, prior, weights, grad_l
     T = w.shape[0]
     pr = np.ascontiguousarray(prior, dtype=real).reshape(n)
     B = syn.shape[0]
-    loss = np.zeros(B, dtype=np.float64)
+    out_loss = np.zeros(B, dtype=np.float64)
     posts = np.zeros((B, T, n), dtype=real) if post else None
     g = None if grad_loss is None else np.ascontiguousarray(grad_loss, dtype=np.float64).reshape(B)
     lw = None if loss_weights is None else np.ascontiguousarray(loss_weights, dtype=np.float64).reshape(T)
@@ -236,7 +240,7 @@ def nms_train(row_ptr, col_idx, m, n, syndromes, targets, prior, weights, grad_l
         if hi <= lo:
             return 0
         return fn(_ptr(rp), _ptr(ci), m, n, _ptr(syn[lo:hi]), _ptr(y[lo:hi]), hi - lo, _ptr(pr), _ptr(w), T,
-                  _ptr(lw), _ptr(g[lo:hi]) if g is not None else None, _ptr(loss[lo:hi]),
+                  _ptr(lw), kind, _ptr(g[lo:hi]) if g is not None else None, _ptr(out_loss[lo:hi]),
                   _ptr(posts[lo:hi]) if posts is not None else None, _ptr(parts[i]) if parts else None)
 
     if threads == 1:
@@ -247,7 +251,7 @@ def nms_train(row_ptr, col_idx, m, n, syndromes, targets, prior, weights, grad_l
     bad = [rc for rc in rcs if rc != 0]
     if bad:
         raise ValueError(f"oracle rejected the input (code {bad[0]})")
-    out = {"loss": loss}
+    out = {"loss": out_loss}
     if posts is not None:
         out["post"] = posts
     if parts is not None:

@@ -498,6 +498,17 @@ int oracle_layered_i8(const int32_t *row_ptr, const int32_t *col_idx, int32_t m,
  * evaluated as softplus(Q) for y = 1 and softplus(-Q) for y = 0 (softplus(x) = log(1 + e^x)):
  * Q = log P(e_n = 0)/P(e_n = 1), so P(e_n = 1) = sigma(-Q).
  *
+ * Syndrome loss (loss_kind 1): the same unrolled decoder scored on the syndrome instead of the
+ * sampled error.  With independent bits of P(e_n = 1) = sigma(-Q_n), the parity of row m is odd
+ * with probability (1 - prod_{n in S_v(m)} tanh(Q_n / 2)) / 2 (the product of the bits' 1 - 2p),
+ * so the probability that the soft output reproduces s_m is
+ *   P_m = (1 + (-1)^{s_m} prod_{n in S_v(m)} tanh(Q_n / 2)) / 2,
+ *   loss = sum_{t=1..T} lambda_t / M sum_m -log(max(P^(t)_m, 1e-7)),
+ * the BCE of the soft syndrome against s.  It is blind to which error of a coset the outputs
+ * point at (any e with H e = s scores the same), as a quantum code's decoder may be.
+ *   dloss_m/dQ_n = -(1 / P_m) (-1)^{s_m} / 2 prod_{j in S_v(m)\n} tanh(Q_j / 2) (1 - tanh^2(Q_n / 2)) / 2,
+ * and 0 where the floor 1e-7 is active.
+ *
  * Reverse mode (the gradient of sum_b g_b loss_b with respect to w), with the subgradient rules
  *   d|q|/dq = +1 for q >= 0, -1 for q < 0;  d sign(q)/dq = 0;
  *   the minimum over S_v(m)\n flows to the lowest-index edge attaining it.
@@ -507,6 +518,31 @@ int oracle_layered_i8(const int32_t *row_ptr, const int32_t *col_idx, int32_t m,
  * --------------------------------------------------------------------------------------------- */
 static double softplus_d(double x) { return x > 0 ? x + log1p(exp(-x)) : log1p(exp(x)); }
 static double sigmoid_d(double x) { return x >= 0 ? 1.0 / (1.0 + exp(-x)) : exp(x) / (1.0 + exp(x)); }
+#define SYN_LOSS_FLOOR 1e-7
+
+/* P_m of the syndrome loss for row c from a-posteriori LLRs Q (any precision, evaluated in double). */
+static double syndrome_match_prob(const tanner *t, int32_t c, const uint8_t *s, const double *Qd)
+{
+    double prod = 1.0;
+    for (int32_t i = t->row_ptr[c]; i < t->row_ptr[c + 1]; ++i) prod *= tanh(0.5 * Qd[t->col[i]]);
+    return 0.5 * (1.0 + ((s[c] & 1) ? -prod : prod));
+}
+
+/* Adds scale * dloss_c/dQ_n to gQ[n] for every n of row c (the product over S_v(c)\n taken literally). */
+static void syndrome_loss_grad(const tanner *t, int32_t c, const uint8_t *s, const double *Qd, double scale,
+                               double *gQ)
+{
+    const double P = syndrome_match_prob(t, c, s, Qd);
+    if (!(P > SYN_LOSS_FLOOR)) return;
+    const double sg = (s[c] & 1) ? -1.0 : 1.0;
+    for (int32_t i = t->row_ptr[c]; i < t->row_ptr[c + 1]; ++i) {
+        double others = 1.0;
+        for (int32_t j = t->row_ptr[c]; j < t->row_ptr[c + 1]; ++j)
+            if (j != i) others *= tanh(0.5 * Qd[t->col[j]]);
+        const double th = tanh(0.5 * Qd[t->col[i]]);
+        gQ[t->col[i]] += scale * (-(1.0 / P) * 0.5 * sg * others * 0.5 * (1.0 - th * th));
+    }
+}
 
 #define DEFINE_NMS_TRAIN(SUFFIX, REAL, FABS)                                                          \
 /* CN update of check c with weights w_t; records per edge the sign factor, the minimum over the    \
@@ -534,10 +570,11 @@ static void nms_check_##SUFFIX(const tanner *t, int32_t c, const uint8_t *s, con
 int oracle_nms_train_##SUFFIX(const int32_t *row_ptr, const int32_t *col_idx, int32_t m, int32_t n,   \
                               const uint8_t *syn, const uint8_t *target, int32_t batch,               \
                               const REAL *prior, const REAL *weights, int32_t T,                      \
-                              const double *loss_w, const double *grad_loss, double *out_loss,        \
-                              REAL *out_post, double *out_grad)                                       \
+                              const double *loss_w, int32_t loss_kind, const double *grad_loss,       \
+                              double *out_loss, REAL *out_post, double *out_grad)                     \
 {                                                                                                     \
     if (batch < 0 || T < 1 || !syn || !target || !prior || !weights || !out_loss) return ORACLE_BAD_ARG; \
+    if (loss_kind != 0 && loss_kind != 1) return ORACLE_BAD_ARG;                                      \
     if (out_grad && !grad_loss) return ORACLE_BAD_ARG;                                                \
     tanner t;                                                                                         \
     int rc = tanner_build(&t, row_ptr, col_idx, m, n);                                                \
@@ -551,7 +588,8 @@ int oracle_nms_train_##SUFFIX(const int32_t *row_ptr, const int32_t *col_idx, in
     REAL *Qs = (REAL *)malloc(sizeof(REAL) * (size_t)n * (size_t)T);                                  \
     double *gq = (double *)malloc(sizeof(double) * E), *gq_prev = (double *)malloc(sizeof(double) * E); \
     double *gr = (double *)malloc(sizeof(double) * E), *gQ = (double *)malloc(sizeof(double) * (size_t)n); \
-    if (!qs || !rs || !mus || !sgs || !ams || !Qs || !gq || !gq_prev || !gr || !gQ) {                 \
+    double *Qd = (double *)malloc(sizeof(double) * (size_t)n);                                         \
+    if (!qs || !rs || !mus || !sgs || !ams || !Qs || !gq || !gq_prev || !gr || !gQ || !Qd) {          \
         rc = ORACLE_NO_MEMORY;                                                                        \
         goto done;                                                                                    \
     }                                                                                                 \
@@ -572,7 +610,8 @@ int oracle_nms_train_##SUFFIX(const int32_t *row_ptr, const int32_t *col_idx, in
                 REAL Q = prior[v];                                                                    \
                 for (int32_t a = t.vptr[v]; a < t.vptr[v + 1]; ++a) Q = Q + r[t.vedge[a]];            \
                 Qs[(size_t)k * n + v] = Q;                                                            \
-                it_loss += y[v] ? softplus_d((double)Q) : softplus_d(-(double)Q);                     \
+                Qd[v] = (double)Q;                                                                    \
+                if (loss_kind == 0) it_loss += y[v] ? softplus_d((double)Q) : softplus_d(-(double)Q); \
                 if (out_post) out_post[((size_t)b * T + k) * n + v] = Q;                              \
                 if (k + 1 < T) {                                                                      \
                     REAL *qn = qs + (size_t)(k + 1) * E;                                              \
@@ -584,17 +623,33 @@ int oracle_nms_train_##SUFFIX(const int32_t *row_ptr, const int32_t *col_idx, in
                     }                                                                                 \
                 }                                                                                     \
             }                                                                                         \
-            loss += lw * (it_loss / n);                                                               \
+            if (loss_kind == 1) {                                                                     \
+                for (int32_t c = 0; c < m; ++c) {                                                     \
+                    const double P = syndrome_match_prob(&t, c, s, Qd);                               \
+                    it_loss += -log(P > SYN_LOSS_FLOOR ? P : SYN_LOSS_FLOOR);                         \
+                }                                                                                     \
+                loss += lw * (it_loss / m);                                                           \
+            } else {                                                                                  \
+                loss += lw * (it_loss / n);                                                           \
+            }                                                                                         \
         }                                                                                             \
         out_loss[b] = loss;                                                                           \
         if (!out_grad) continue;                                                                      \
         /* reverse sweep, iteration T down to 1 */                                                    \
-        const double scale = grad_loss[b] / n;                                                        \
+        const double scale = grad_loss[b] / (loss_kind == 1 ? m : n);                                 \
         for (int32_t i = 0; i < t.e; ++i) gq[i] = 0.0;    /* d/d q^(k+1): feeds iteration k+2 */      \
         for (int32_t k = T - 1; k >= 0; --k) {                                                        \
             const double lw = loss_w ? loss_w[k] : 1.0 / T;                                           \
-            for (int32_t v = 0; v < n; ++v)                                                           \
-                gQ[v] = scale * lw * ((double)y[v] - sigmoid_d(-(double)Qs[(size_t)k * n + v]));      \
+            if (loss_kind == 1) {                                                                     \
+                for (int32_t v = 0; v < n; ++v) {                                                     \
+                    gQ[v] = 0.0;                                                                      \
+                    Qd[v] = (double)Qs[(size_t)k * n + v];                                            \
+                }                                                                                     \
+                for (int32_t c = 0; c < m; ++c) syndrome_loss_grad(&t, c, s, Qd, scale * lw, gQ);     \
+            } else {                                                                                  \
+                for (int32_t v = 0; v < n; ++v)                                                       \
+                    gQ[v] = scale * lw * ((double)y[v] - sigmoid_d(-(double)Qs[(size_t)k * n + v]));  \
+            }                                                                                         \
             /* r^(k+1)_{m,n} enters Q^(k+1)_n and every q^(k+1)_{i,n} with i != m */                  \
             for (int32_t v = 0; v < n; ++v)                                                           \
                 for (int32_t a = t.vptr[v]; a < t.vptr[v + 1]; ++a) {                                 \
@@ -619,7 +674,7 @@ int oracle_nms_train_##SUFFIX(const int32_t *row_ptr, const int32_t *col_idx, in
     }                                                                                                 \
 done:                                                                                                 \
     free(qs); free(rs); free(mus); free(sgs); free(ams); free(Qs);                                    \
-    free(gq); free(gq_prev); free(gr); free(gQ);                                                      \
+    free(gq); free(gq_prev); free(gr); free(gQ); free(Qd);                                            \
     tanner_free(&t);                                                                                  \
     return rc;                                                                                        \
 }

@@ -588,7 +588,8 @@ def measure_layered(qldpc, graph, code, syn_d, pri_d, out, stream, B, args, step
 
 
 def measure_learned(qldpc, args):
-    """Config 4: learned normalized min-sum on LP-1054 (H_Z), trained and evaluated on the device."""
+    """Config 4: learned normalized min-sum on LP-1054 (H_Z), trained and evaluated on the device,
+    once with each training loss (BCE against the sampled error; BCE of the soft syndrome)."""
     import torch
     from paper_2508_07879_gb300 import learned
     from paper_2508_07879_gb300 import workloads as w
@@ -596,58 +597,74 @@ def measure_learned(qldpc, args):
     h = code.hz_csr
     prior = np.full(h.n, w.prior_llr(0.04), dtype=np.float32)   # one prior at the centre of the range
     g = qldpc.Graph.from_csr(h)
-    model = learned.NeuralMinSum(h, prior, T=LEARN_T, max_batch=LEARN_BATCH, graph=g)
-    # kernel times of one training step, events on the launching (current) stream
-    err, syn = qldpc.sample_errors(g, LEARN_SEEDS[0] + 1000, 0, LEARN_BATCH, *LEARN_P)
-    gl = torch.full((LEARN_BATCH,), 1.0 / LEARN_BATCH, device=syn.device)
-    w0 = model.weights.detach()
-    for _ in range(3):
-        qldpc.nms_forward(g, syn, err, model.prior, w0, model.workspace)
-        qldpc.nms_backward(g, syn, err, model.prior, LEARN_T, gl, model.workspace)
-    torch.cuda.synchronize()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-    tf = tb = 0.0
-    reps = 10
-    for _ in range(reps):
-        ev[0].record()
-        qldpc.nms_forward(g, syn, err, model.prior, w0, model.workspace)
-        ev[1].record()
-        qldpc.nms_backward(g, syn, err, model.prior, LEARN_T, gl, model.workspace)
-        ev[2].record()
-        torch.cuda.synchronize()
-        tf += ev[0].elapsed_time(ev[1])
-        tb += ev[1].elapsed_time(ev[2])
-    tf, tb = tf / reps, tb / reps
-    edge_iters = LEARN_BATCH * LEARN_T * h.nnz
-    # training: sampling, forward, backward and Adam per step, wall clock
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    hist = model.train(shots=args.learned_train_shots, batch=LEARN_BATCH, p_lo=LEARN_P[0], p_hi=LEARN_P[1],
-                       seed=LEARN_SEEDS[0], lr=LEARN_LR, record_every=50)
-    torch.cuda.synchronize()
-    train_s = time.perf_counter() - t0
-    model.publish()
-    decoders = {"plain_20": (20, False), "plain_50": (50, False), "learned_20": (0, True),
-                "learned_20_fallback_30": (30, True), "learned_20_fallback_50": (50, True)}
-    t0 = time.perf_counter()
-    res = learned.evaluate(g, prior, learned.z_logicals(code), decoders, shots=args.learned_eval_shots,
-                           p_lo=LEARN_P[0], p_hi=LEARN_P[1], seed=LEARN_SEEDS[1])
-    eval_s = time.perf_counter() - t0
+    logicals = learned.z_logicals(code)
     steps = args.learned_train_shots // LEARN_BATCH
-    return {
+    edge_iters = LEARN_BATCH * LEARN_T * h.nnz
+    out = {
         "workload": "LP-1054 H_Z, iid X noise, p uniform in [0.02, 0.06) per shot, prior ln(0.96/0.04)",
         "T": LEARN_T, "train_shots": steps * LEARN_BATCH, "batch": LEARN_BATCH, "lr": LEARN_LR,
-        "loss": "mean over iterations and variables of BCE(sigma(-Q), e)",
-        "train_s": train_s, "train_shots_per_s": steps * LEARN_BATCH / train_s,
-        "loss_first": float(hist[0]) if len(hist) else None, "loss_last": float(hist[-1]) if len(hist) else None,
-        "step_kernel_ms": {"forward": tf, "backward_and_reduce": tb},
-        "train_edge_iters_per_s": {"forward": edge_iters / (tf / 1e3), "backward": edge_iters / (tb / 1e3)},
-        "eval_shots": args.learned_eval_shots, "eval_s": eval_s,
-        "ler": {k: v["ler"] for k, v in res.items()},
-        "mean_iters": {k: v["mean_iters"] for k, v in res.items()},
+        "eval_shots": args.learned_eval_shots,
         "decoders": "plain_K: alpha 0.75, max K iterations; learned_20: 20 learned iterations alone; "
                     "learned_20_fallback_K: then plain min-sum from the prior for up to K iterations",
+        "losses": {"error": "mean over iterations and variables of BCE(sigma(-Q), e)",
+                   "syndrome": "mean over iterations and checks of -log P(soft syndrome bit = s)"},
     }
+    plain = {"plain_20": (20, False), "plain_50": (50, False)}
+    res = learned.evaluate(g, prior, logicals, plain, shots=args.learned_eval_shots, p_lo=LEARN_P[0],
+                           p_hi=LEARN_P[1], seed=LEARN_SEEDS[1])
+    ler = {k: v["ler"] for k, v in res.items()}
+    iters = {k: v["mean_iters"] for k, v in res.items()}
+    for loss in ("syndrome", "error"):
+        model = learned.NeuralMinSum(h, prior, T=LEARN_T, max_batch=LEARN_BATCH, graph=g, loss=loss)
+        # kernel times of one training step, events on the launching (current) stream
+        err, syn = qldpc.sample_errors(g, LEARN_SEEDS[0] + 1000, 0, LEARN_BATCH, *LEARN_P)
+        gl = torch.full((LEARN_BATCH,), 1.0 / LEARN_BATCH, device=syn.device)
+        w0 = model.weights.detach()
+        for _ in range(3):
+            qldpc.nms_forward(g, syn, err, model.prior, w0, model.workspace, loss=loss)
+            qldpc.nms_backward(g, syn, err, model.prior, LEARN_T, gl, model.workspace, loss=loss)
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        tf = tb = 0.0
+        reps = 10
+        for _ in range(reps):
+            ev[0].record()
+            qldpc.nms_forward(g, syn, err, model.prior, w0, model.workspace, loss=loss)
+            ev[1].record()
+            qldpc.nms_backward(g, syn, err, model.prior, LEARN_T, gl, model.workspace, loss=loss)
+            ev[2].record()
+            torch.cuda.synchronize()
+            tf += ev[0].elapsed_time(ev[1])
+            tb += ev[1].elapsed_time(ev[2])
+        tf, tb = tf / reps, tb / reps
+        # training: sampling, forward, backward and Adam per step, wall clock
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hist = model.train(shots=args.learned_train_shots, batch=LEARN_BATCH, p_lo=LEARN_P[0], p_hi=LEARN_P[1],
+                           seed=LEARN_SEEDS[0], lr=LEARN_LR, record_every=50)
+        torch.cuda.synchronize()
+        train_s = time.perf_counter() - t0
+        model.publish()
+        t0 = time.perf_counter()
+        res = learned.evaluate(g, prior, logicals, {"learned_20": (0, True), "learned_20_fallback_30": (30, True),
+                                                    "learned_20_fallback_50": (50, True)},
+                               shots=args.learned_eval_shots, p_lo=LEARN_P[0], p_hi=LEARN_P[1], seed=LEARN_SEEDS[1])
+        eval_s = time.perf_counter() - t0
+        prefix = "" if loss == "syndrome" else "error_loss_"
+        ler.update({prefix + k: v["ler"] for k, v in res.items()})
+        iters.update({prefix + k: v["mean_iters"] for k, v in res.items()})
+        out[loss + "_loss_training"] = {
+            "train_s": train_s, "train_shots_per_s": steps * LEARN_BATCH / train_s,
+            "loss_first": float(hist[0]) if len(hist) else None, "loss_last": float(hist[-1]) if len(hist) else None,
+            "step_kernel_ms": {"forward": tf, "backward_and_reduce": tb},
+            "train_edge_iters_per_s": {"forward": edge_iters / (tf / 1e3), "backward": edge_iters / (tb / 1e3)},
+            "eval_s": eval_s,
+        }
+        g.set_weights(None)
+    out["ler"] = ler
+    out["mean_iters"] = iters
+    out["learned_keys"] = "learned_*: trained on the syndrome loss; error_loss_learned_*: on the error loss"
+    return out
 
 
 def main():

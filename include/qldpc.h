@@ -311,12 +311,19 @@ QLDPC_API void qldpc_server_destroy(qldpc_server *s);
  * matrix given to qldpc_graph_create).  The variable step, APP and decision are Algorithm 1's.
  * Learned decoding runs iterations 1..T with the weights and the stop test; a shot whose syndrome
  * is still not met restarts from its prior with plain min-sum (alpha, up to max_iter iterations):
- * iters = T + plain iterations for such shots.  Training minimizes the BCE of the soft outputs,
- *   loss_b = sum_{t=1..T} lambda_t / n sum_v BCE(sigma(-Q^(t)_v), y_v)   (y = the true error bits),
- * with per-iteration loss weights lambda_t (default 1/T: the mean over iterations and variables),
+ * iters = T + plain iterations for such shots.  Training minimizes a BCE of the soft outputs,
+ * with per-iteration loss weights lambda_t (default 1/T), one of
+ *   QLDPC_LOSS_ERROR     loss_b = sum_t lambda_t / n sum_v BCE(sigma(-Q^(t)_v), y_v)
+ *                        (y = the true error bits: the mean over iterations and variables)
+ *   QLDPC_LOSS_SYNDROME  loss_b = sum_t lambda_t / m sum_c -log max(P^(t)_c, 1e-7),
+ *                        P_c = (1 + (-1)^{s_c} prod_{v in row c} tanh(Q_v / 2)) / 2
+ *                        (the BCE of the soft syndrome: P_c is the probability that row c's parity
+ *                        under independent bits of P(e_v = 1) = sigma(-Q_v) equals s_c; every error
+ *                        with the shot's syndrome scores alike, and targets are not read)
  * with a forward kernel that records a compressed check state per iteration and a backward
  * kernel that recomputes every message from it.  FP32 throughout.
  * =============================================================================================== */
+enum { QLDPC_LOSS_ERROR = 0, QLDPC_LOSS_SYNDROME = 1 };
 
 /* Set (T >= 1) or clear (T = 0, weights may be NULL) the graph's learned weights: float[T][nnz],
  * host or device memory, copied (synchronously) into the graph.  Decodes and servers created
@@ -331,9 +338,11 @@ QLDPC_API int qldpc_nms_workspace_bytes(const qldpc_graph *g, int32_t batch, int
 
 /*
  * Training forward: T learned iterations (no stop test) on every shot.
- *   syndromes  device uint8[batch][m];  targets device uint8[batch][n], the true error bits
+ *   syndromes  device uint8[batch][m];  targets device uint8[batch][n], the true error bits (may be
+ *              NULL with QLDPC_LOSS_SYNDROME)
  *   prior      device float[n];         weights device float[T][nnz] (CSR edge order)
  *   loss_weights  device float[T] (lambda_t), or NULL for 1/T each
+ *   loss       QLDPC_LOSS_ERROR or QLDPC_LOSS_SYNDROME
  *   out_loss   device float[batch], loss_b as above
  *   out_post   device float[batch][n], Q^(T) (the a-posteriori LLR of iteration T), or NULL
  *   workspace  device memory of at least qldpc_nms_workspace_bytes(g, batch, T), 256-byte aligned;
@@ -344,21 +353,21 @@ QLDPC_API int qldpc_nms_workspace_bytes(const qldpc_graph *g, int32_t batch, int
  */
 QLDPC_API int qldpc_nms_forward(const qldpc_graph *g, const uint8_t *syndromes, const uint8_t *targets,
                                 int32_t batch, const float *prior, const float *weights, int32_t T,
-                                const float *loss_weights, float *out_loss, float *out_post, void *workspace,
-                                size_t workspace_bytes, void *stream);
+                                const float *loss_weights, int32_t loss, float *out_loss, float *out_post,
+                                void *workspace, size_t workspace_bytes, void *stream);
 
 /*
  * Training backward: out_grad (device float[T][nnz], overwritten) = sum_b grad_loss[b] d loss_b / d w,
  * with the subgradients d|q|/dq = sign(q) (+1 at 0), d sign/dq = 0, and the minimum's gradient going
  * to the lowest position attaining it.  The arguments must be those of the preceding
- * qldpc_nms_forward on the same workspace (same syndromes, targets, prior, batch, T and loss
- * weights; the weights are read back from the workspace).  grad_loss is device float[batch].  The
+ * qldpc_nms_forward on the same workspace (same syndromes, targets, prior, batch, T, loss weights
+ * and loss; the weights are read back from the workspace).  grad_loss is device float[batch].  The
  * sum over shots is taken with FP32 global reductions, so its rounding order (the last bits of the
  * result) follows the schedule and may differ between calls.
  */
 QLDPC_API int qldpc_nms_backward(const qldpc_graph *g, const uint8_t *syndromes, const uint8_t *targets,
                                  int32_t batch, const float *prior, int32_t T, const float *loss_weights,
-                                 const float *grad_loss, float *out_grad, void *workspace,
+                                 int32_t loss, const float *grad_loss, float *out_grad, void *workspace,
                                  size_t workspace_bytes, void *stream);
 
 /* One Adam step on device float arrays of `count` elements (Kingma and Ba, ICLR 2015), in the

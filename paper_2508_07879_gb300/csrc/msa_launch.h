@@ -233,7 +233,11 @@ struct TrainParams {
     const float *loss_w;        // [T] per-iteration loss weights lambda_t, or nullptr for 1/T each
     float *partial;             // [T][dc_max * m] slot-layout weight gradient, zeroed before the backward
     int32_t T, batch;
+    int32_t loss_kind;          // kLossError or kLossSyndrome
 };
+
+constexpr int kLossError = 0;      // BCE of sigma(-Q) against the sampled error, mean over variables
+constexpr int kLossSyndrome = 1;   // BCE of the soft syndrome against s, mean over checks
 
 struct TrainChoice {
     int dc;          // exact uniform row degree 6..8, else bucket 8/16/32
@@ -261,17 +265,19 @@ cudaError_t launch_logical(const uint8_t *logicals, int32_t k, int32_t n, const 
 // Shared memory of one training shot (forward: q slots, gamma, targets, syndrome; backward adds
 // the recomputed r slots and the recorded state of two iterations).
 struct TrainLayout {
-    size_t slot_off, r_off, c_off, g_off, y_off, s_off, total;
+    size_t slot_off, r_off, c_off, t_off, g_off, y_off, s_off, total;
 };
 
-__host__ __device__ inline TrainLayout train_layout(int m, int n, int dc_max, bool backward)
+__host__ __device__ inline TrainLayout train_layout(int m, int n, int dc_max, bool backward, bool syndrome = false)
 {
     TrainLayout t;
     const size_t S = size_t(dc_max) * m + kScratch;
     t.slot_off = 0;                                                          // q / gradient slots [S] f32
     t.r_off = align16(S * 4);                                                // r slots [S] f32 (backward)
     t.c_off = backward ? align16(t.r_off + S * 4) : t.r_off;                 // state [2][4m] u32 (backward)
-    t.g_off = backward ? align16(t.c_off + 2 * size_t(kStateWords) * m * 4) : t.c_off;   // gamma [n] f32
+    t.t_off = backward ? align16(t.c_off + 2 * size_t(kStateWords) * m * 4) : t.c_off;   // syndrome loss:
+    const size_t g0 = syndrome ? align16(t.t_off + S * 4) : t.t_off;                     //   tanh slots [S] f32
+    t.g_off = g0;                                                                        // gamma [n] f32
     t.y_off = align16(t.g_off + size_t(n) * 4);                              // targets [n] u8
     t.s_off = align16(t.y_off + size_t(n));                                  // syndrome bits [m] u8
     t.total = align16(t.s_off + size_t(m));

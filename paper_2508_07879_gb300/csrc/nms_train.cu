@@ -103,7 +103,77 @@ __device__ __forceinline__ float lane_prior(const DeviceGraph &g, const float *p
 __device__ __forceinline__ uint8_t lane_target(const DeviceGraph &g, const uint8_t *tg, int u, int N)
 {
     const uint32_t v = __ldg(g.vperm + u);
-    return v < uint32_t(N) ? uint8_t(tg[v] & 1u) : kIdleLane;
+    return v < uint32_t(N) ? (tg ? uint8_t(tg[v] & 1u) : uint8_t(0)) : kIdleLane;
+}
+
+// Syndrome loss of check c from the a-posteriori LLRs Q_j of its variables (in its slots):
+// P = (1 + (-1)^s prod_j t_j) / 2 with t_j = tanh(Q_j / 2) is the probability that the row's parity
+// under independent bits sigma(-Q) equals s.  |t_j| = (1 - x_j) / (1 + x_j) with x_j = e^{-|Q_j|},
+// and prod_j |t_j| = exp(A), A = sum_j [log1p(-x_j) - log1p(x_j)], so that a violated, confident
+// check gets P = -expm1(A) / 2 without the cancellation of 1 - prod (|t| rounds to 1 well before
+// 1 - |t| is negligible).  Fills t[] for the caller.
+constexpr float kSynLossFloor = 1e-7f;
+template <int DC, bool UNIFORM>
+__device__ __forceinline__ float parity_match_prob(int c, int M, int deg, uint32_t s_bit, const float *__restrict__ qs,
+                                                   float *t)
+{
+    float A = 0.0f;
+    uint32_t neg = s_bit & 1u;
+#pragma unroll
+    for (int j = 0; j < DC; ++j) {
+        if (UNIFORM || j < deg) {
+            const float Q = qs[j * M + c];
+            const float x = expf(-fabsf(Q));
+            A += log1pf(-x) - log1pf(x);
+            const float at = (1.0f - x) / (1.0f + x);
+            t[j] = Q < 0.0f ? -at : at;
+            neg ^= Q < 0.0f ? 1u : 0u;
+        } else {
+            t[j] = 1.0f;
+        }
+    }
+    const float e = expf(A);   // prod_j |t_j|
+    return neg ? -0.5f * expm1f(A) : 0.5f * (1.0f + e);
+}
+
+template <int DC, bool UNIFORM>
+__device__ __forceinline__ float syndrome_term(int c, int M, int deg, uint32_t s_bit, const float *__restrict__ qs)
+{
+    float t[DC];
+    const float P = parity_match_prob<DC, UNIFORM>(c, M, deg, s_bit, qs, t);
+    return -logf(fmaxf(P, kSynLossFloor));
+}
+
+// d(syndrome term)/d t_j = -(1 / P) (-1)^s / 2 prod_{i != j} t_i (0 at the floor), written over the
+// Q_j of check c.
+template <int DC, bool UNIFORM>
+__device__ __forceinline__ void syndrome_term_grad(int c, int M, int deg, uint32_t s_bit, float *__restrict__ qs)
+{
+    float t[DC], pre[DC];
+    const float P = parity_match_prob<DC, UNIFORM>(c, M, deg, s_bit, qs, t);
+    const float sg = s_bit ? -1.0f : 1.0f;
+    const float coef = P > kSynLossFloor ? -0.5f * sg / P : 0.0f;
+    float prod = 1.0f;
+#pragma unroll
+    for (int j = 0; j < DC; ++j) {
+        pre[j] = prod;                       // t_0 ... t_{j-1}
+        prod *= t[j];
+    }
+    float suf = 1.0f;                        // t_{j+1} ... t_{deg-1}
+#pragma unroll
+    for (int j = DC - 1; j >= 0; --j) {
+        if (UNIFORM || j < deg) {
+            qs[j * M + c] = coef * (pre[j] * suf);
+            suf *= t[j];
+        }
+    }
+}
+
+// d tanh(Q/2) / dQ = sech^2(Q/2) / 2 (no cancellation for large |Q|)
+__device__ __forceinline__ float half_sech2_half(float Q)
+{
+    const float ch = coshf(0.5f * Q);
+    return 0.5f / (ch * ch);
 }
 
 // r of check c recomputed from its recorded state (bit-identical to the forward's r).
@@ -128,20 +198,24 @@ __global__ void __launch_bounds__(kTrainThreads, 4) nms_forward_kernel(const Tra
 {
     const int M = p.g.m, N = p.g.n, NV = p.g.nv, T = blockDim.x, tid = threadIdx.x;
     const size_t S = size_t(p.g.dc_max) * M;
+    const bool syn_loss = p.loss_kind == kLossSyndrome;
     extern __shared__ __align__(16) unsigned char smem[];
-    const TrainLayout L = train_layout(M, NV, p.g.dc_max, false);
+    const TrainLayout L = train_layout(M, NV, p.g.dc_max, false, syn_loss);
     float *slots = reinterpret_cast<float *>(smem + L.slot_off);
+    float *ts = reinterpret_cast<float *>(smem + L.t_off);        // syndrome loss: Q of each edge's variable
     float *gam = reinterpret_cast<float *>(smem + L.g_off);
     uint8_t *y = smem + L.y_off;
     uint8_t *sb = smem + L.s_off;
     __shared__ float red[32];
 
     for (int u = tid; u < NV; u += T) gam[u] = F32::quantize(lane_prior(p.g, p.prior, u, N));
-    // uniform lambda: sum the terms and scale once by 1/(T N); else weight each iteration's terms
-    const float inv = p.loss_w ? 1.0f / float(N) : 1.0f / (float(p.T) * float(N));
+    // uniform lambda: sum the terms and scale once by 1/(T K); else weight each iteration's terms
+    // (K = N variables for the error loss, M checks for the syndrome loss)
+    const float K = float(syn_loss ? M : N);
+    const float inv = p.loss_w ? 1.0f / K : 1.0f / (float(p.T) * K);
     for (int b = blockIdx.x; b < p.batch; b += gridDim.x) {
         const uint8_t *s = p.syn + size_t(b) * M;
-        const uint8_t *tg = p.target + size_t(b) * N;
+        const uint8_t *tg = syn_loss ? nullptr : p.target + size_t(b) * N;
         for (int c = tid; c < M; c += T) sb[c] = s[c] & 1u;
         __syncthreads();   // gam (first shot) and the previous shot's last reads are done
         for (int u = tid; u < NV; u += T) {
@@ -154,21 +228,36 @@ __global__ void __launch_bounds__(kTrainThreads, 4) nms_forward_kernel(const Tra
         for (int k = 0; k < p.T; ++k) {
             const float *wk = p.w + size_t(k) * S;
             uint32_t *st = p.state + (size_t(b) * p.T + k) * size_t(kStateWords) * M;
+            // syndrome loss of iteration k-1 (its Q slots are complete) beside the check step of k
+            const float lw_prev = (syn_loss && k > 0) ? (p.loss_w ? __ldg(p.loss_w + k - 1) : 1.0f) : 0.0f;
             for (int c = tid; c < M; c += T) {
                 const int deg = UNIFORM ? DC : int(__ldg(p.g.rdeg + c));
+                if (syn_loss && k > 0) acc += lw_prev * syndrome_term<DC, UNIFORM>(c, M, deg, sb[c], ts);
                 train_check_fwd<DC, UNIFORM>(c, M, deg, sb[c], slots, wk, st);
             }
             __syncthreads();
             const bool lastk = k + 1 == p.T;
             const float lw = p.loss_w ? __ldg(p.loss_w + k) : 1.0f;
             for (int u = tid; u < NV; u += T) {
-                const float Q = var_step_batch<F32, DV, false>(__ldg(p.g.vdeg + u), u, NV, CheckOf(p.g), p.g.vslot,
-                                                               gam[u], false, slots, nullptr);
+                const int deg = __ldg(p.g.vdeg + u);
+                const float Q = var_step_batch<F32, DV, false>(deg, u, NV, CheckOf(p.g), p.g.vslot, gam[u], false,
+                                                               slots, nullptr);
                 if (y[u] == kIdleLane) continue;
-                acc += lw * (y[u] ? softplus(Q) : softplus(-Q));
+                if (syn_loss) {
+                    for (int i = 0; i < deg; ++i) ts[__ldg(p.g.vslot + size_t(i) * NV + u)] = Q;
+                } else {
+                    acc += lw * (y[u] ? softplus(Q) : softplus(-Q));
+                }
                 if (lastk && p.post) p.post[size_t(b) * N + __ldg(p.g.vperm + u)] = Q;
             }
             __syncthreads();
+        }
+        if (syn_loss) {   // the last iteration's syndrome loss
+            const float lw = p.loss_w ? __ldg(p.loss_w + p.T - 1) : 1.0f;
+            for (int c = tid; c < M; c += T) {
+                const int deg = UNIFORM ? DC : int(__ldg(p.g.rdeg + c));
+                acc += lw * syndrome_term<DC, UNIFORM>(c, M, deg, sb[c], ts);
+            }
         }
         const float total = block_sum(acc, red);
         if (tid == 0) p.loss[b] = total * inv;
@@ -194,23 +283,28 @@ __global__ void __launch_bounds__(kTrainThreads, 4) nms_backward_kernel(const Tr
     const int M = p.g.m, N = p.g.n, NV = p.g.nv, T = blockDim.x, tid = threadIdx.x;
     const size_t S = size_t(p.g.dc_max) * M;
     const size_t SW = size_t(kStateWords) * M;                    // state words of one iteration
+    const bool syn_loss = p.loss_kind == kLossSyndrome;
     extern __shared__ __align__(16) unsigned char smem[];
-    const TrainLayout L = train_layout(M, NV, p.g.dc_max, true);
+    const TrainLayout L = train_layout(M, NV, p.g.dc_max, true, syn_loss);
     float *gs = reinterpret_cast<float *>(smem + L.slot_off);     // dL/dq (next iteration), then dL/dr
     float *rs = reinterpret_cast<float *>(smem + L.r_off);        // recomputed r of the current iteration
     uint32_t *scb = reinterpret_cast<uint32_t *>(smem + L.c_off); // recorded state, two iterations
+    float *ts = reinterpret_cast<float *>(smem + L.t_off);        // syndrome loss: Q per edge, then d/dt
     float *gam = reinterpret_cast<float *>(smem + L.g_off);
     uint8_t *y = smem + L.y_off;
+    uint8_t *sb = smem + L.s_off;
 
     for (int u = tid; u < NV; u += T) gam[u] = F32::quantize(lane_prior(p.g, p.prior, u, N));
-    const float inv = 1.0f / float(N);
+    const float inv = 1.0f / float(syn_loss ? M : N);
     for (int b = blockIdx.x; b < p.batch; b += gridDim.x) {
-        const uint8_t *tg = p.target + size_t(b) * N;
+        const uint8_t *tg = syn_loss ? nullptr : p.target + size_t(b) * N;
         const float gscale = p.grad_loss[b] * inv;
         const uint32_t *stb = p.state + size_t(b) * p.T * SW;
         __syncthreads();   // gam (first shot) and the previous shot's last reads are done
         prefetch_state(scb, stb + size_t(p.T - 1) * SW, M);
         for (int u = tid; u < NV; u += T) y[u] = lane_target(p.g, tg, u, N);
+        if (syn_loss)
+            for (int c = tid; c < M; c += T) sb[c] = p.syn[size_t(b) * M + c] & 1u;
         cp_async_wait();
         __syncthreads();
         // iteration T: recompute r; dL/dq of iteration T+1 is zero
@@ -230,20 +324,45 @@ __global__ void __launch_bounds__(kTrainThreads, 4) nms_backward_kernel(const Tr
             uint32_t *sn = scb + size_t(((p.T - 1 - k) & 1) ^ 1) * SW;    // state of iteration k-1
             if (k > 0) prefetch_state(sn, stb + size_t(k - 1) * SW, M);  // overlaps the variable side
             const float gk = gscale * (p.loss_w ? __ldg(p.loss_w + k) : 1.0f / float(p.T));
+            if (syn_loss) {
+                // Q^(k) of every edge's variable, then each check's d(loss term)/d t in its place
+                for (int u = tid; u < NV; u += T) {
+                    const int deg = __ldg(p.g.vdeg + u);
+                    uint32_t sl[DV];
+                    float Q = gam[u];
+#pragma unroll
+                    for (int i = 0; i < DV; ++i) {
+                        if (i < deg) {
+                            sl[i] = __ldg(p.g.vslot + size_t(i) * NV + u);
+                            Q = __fadd_rn(Q, rs[sl[i]]);
+                        }
+                    }
+#pragma unroll
+                    for (int i = 0; i < DV; ++i)
+                        if (i < deg) ts[sl[i]] = Q;
+                }
+                __syncthreads();
+                for (int c = tid; c < M; c += T) {
+                    const int deg = UNIFORM ? DC : int(__ldg(p.g.rdeg + c));
+                    syndrome_term_grad<DC, UNIFORM>(c, M, deg, sb[c], ts);
+                }
+                __syncthreads();
+            }
             // variable side: Q^(k) from the recomputed r, dL/dQ, and dL/dr for every edge
             for (int u = tid; u < NV; u += T) {
-                const int deg = __ldg(p.g.vdeg + u);   // 0 on idle lanes
+                const int deg = __ldg(p.g.vdeg + u);   // idle lanes: their warp's degree, scratch slots
                 uint32_t sl[DV];
-                float Q = gam[u], G = 0.0f;
+                float Q = gam[u], G = 0.0f, H = 0.0f;
 #pragma unroll
                 for (int i = 0; i < DV; ++i) {
                     if (i < deg) {
                         sl[i] = __ldg(p.g.vslot + size_t(i) * NV + u);
                         Q = __fadd_rn(Q, rs[sl[i]]);
                         G += gs[sl[i]];
+                        if (syn_loss) H += ts[sl[i]];
                     }
                 }
-                const float gQ = gk * (float(y[u]) - sigmoid(-Q));
+                const float gQ = syn_loss ? gk * half_sech2_half(Q) * H : gk * (float(y[u]) - sigmoid(-Q));
 #pragma unroll
                 for (int i = 0; i < DV; ++i)
                     if (i < deg) gs[sl[i]] = gQ + (G - gs[sl[i]]);

@@ -37,8 +37,8 @@ TrainChoice train_choice(const qldpc_graph *g)
 struct TrainPlan {
     TrainChoice tc{};
     const void *fwd = nullptr, *bwd = nullptr;
-    size_t smem_f = 0, smem_b = 0;
-    int grid_f = 0, grid_b = 0;
+    size_t smem_f[2] = {0, 0}, smem_b[2] = {0, 0};   // [loss kind]
+    int grid_f[2] = {0, 0}, grid_b[2] = {0, 0};
     size_t w_off = 0, state_off = 0, part_off = 0, total = 0;
 };
 
@@ -69,19 +69,24 @@ int plan_training_uncached(const qldpc_graph *g, int32_t batch, int32_t T, Train
     tp.fwd = nms_forward_kernel_ptr(tp.tc);
     tp.bwd = nms_backward_kernel_ptr(tp.tc);
     if (!tp.fwd || !tp.bwd) return QLDPC_ERR_UNSUPPORTED;
-    tp.smem_f = train_layout(g->m, g->nv, g->dc_max, false).total;
-    tp.smem_b = train_layout(g->m, g->nv, g->dc_max, true).total;
-    if (int rc = ensure_kernel_attrs(tp.fwd, tp.smem_f, g->smem_optin)) return rc;
-    if (int rc = ensure_kernel_attrs(tp.bwd, tp.smem_b, g->smem_optin)) return rc;
-    int per_f = 0, per_b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_f, tp.fwd, kTrainThreads, tp.smem_f) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_b, tp.bwd, kTrainThreads, tp.smem_b) != cudaSuccess) {
-        cudaGetLastError();
-        return QLDPC_ERR_CUDA;
+    for (int kind = 0; kind < 2; ++kind) {
+        const bool syn = kind == kLossSyndrome;
+        tp.smem_f[kind] = train_layout(g->m, g->nv, g->dc_max, false, syn).total;
+        tp.smem_b[kind] = train_layout(g->m, g->nv, g->dc_max, true, syn).total;
     }
-    if (per_f < 1 || per_b < 1) return QLDPC_ERR_UNSUPPORTED;
-    tp.grid_f = int(std::min<int64_t>(batch, int64_t(per_f) * g->sm_count));
-    tp.grid_b = int(std::min<int64_t>(batch, int64_t(per_b) * g->sm_count));
+    if (int rc = ensure_kernel_attrs(tp.fwd, tp.smem_f[kLossSyndrome], g->smem_optin)) return rc;
+    if (int rc = ensure_kernel_attrs(tp.bwd, tp.smem_b[kLossSyndrome], g->smem_optin)) return rc;
+    for (int kind = 0; kind < 2; ++kind) {
+        int per_f = 0, per_b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_f, tp.fwd, kTrainThreads, tp.smem_f[kind]) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_b, tp.bwd, kTrainThreads, tp.smem_b[kind]) != cudaSuccess) {
+            cudaGetLastError();
+            return QLDPC_ERR_CUDA;
+        }
+        if (per_f < 1 || per_b < 1) return QLDPC_ERR_UNSUPPORTED;
+        tp.grid_f[kind] = int(std::min<int64_t>(batch, int64_t(per_f) * g->sm_count));
+        tp.grid_b[kind] = int(std::min<int64_t>(batch, int64_t(per_b) * g->sm_count));
+    }
     const size_t S = size_t(g->dc_max) * size_t(g->m);
     tp.w_off = 0;
     tp.state_off = align_up(size_t(T) * S * sizeof(float));
@@ -170,10 +175,12 @@ int qldpc_nms_workspace_bytes(const qldpc_graph *g, int32_t batch, int32_t T, si
 
 int qldpc_nms_forward(const qldpc_graph *g, const uint8_t *syndromes, const uint8_t *targets, int32_t batch,
                       const float *prior, const float *weights, int32_t T, const float *loss_weights,
-                      float *out_loss, float *out_post, void *workspace, size_t workspace_bytes, void *stream)
+                      int32_t loss, float *out_loss, float *out_post, void *workspace, size_t workspace_bytes,
+                      void *stream)
 {
-    if (!g || !syndromes || !targets || !prior || !weights || !out_loss || batch < 1 || T < 1 ||
-        T > kMaxLearnedIters)
+    if (loss != QLDPC_LOSS_ERROR && loss != QLDPC_LOSS_SYNDROME) return QLDPC_ERR_INVALID_ARG;
+    if (!g || !syndromes || (!targets && loss == QLDPC_LOSS_ERROR) || !prior || !weights || !out_loss || batch < 1 ||
+        T < 1 || T > kMaxLearnedIters)
         return QLDPC_ERR_INVALID_ARG;
     if (int rc = check_device(g)) return rc;
     TrainPlan tp;
@@ -184,19 +191,22 @@ int qldpc_nms_forward(const qldpc_graph *g, const uint8_t *syndromes, const uint
     p.loss = out_loss;
     p.post = out_post;
     p.loss_w = loss_weights;
+    p.loss_kind = loss;
     const size_t S = size_t(g->dc_max) * size_t(g->m);
     cudaError_t e = launch_permute_weights(weights, g->dg.eslot, T, g->nnz, int32_t(S),
                                            const_cast<float *>(p.w), st);
-    if (e == cudaSuccess) e = launch_nms_forward(p, tp.tc, tp.grid_f, kTrainThreads, tp.smem_f, st);
+    if (e == cudaSuccess) e = launch_nms_forward(p, tp.tc, tp.grid_f[loss], kTrainThreads, tp.smem_f[loss], st);
     return cuda_status(e);
 }
 
 int qldpc_nms_backward(const qldpc_graph *g, const uint8_t *syndromes, const uint8_t *targets, int32_t batch,
-                       const float *prior, int32_t T, const float *loss_weights, const float *grad_loss,
-                       float *out_grad, void *workspace, size_t workspace_bytes, void *stream)
+                       const float *prior, int32_t T, const float *loss_weights, int32_t loss,
+                       const float *grad_loss, float *out_grad, void *workspace, size_t workspace_bytes,
+                       void *stream)
 {
-    if (!g || !syndromes || !targets || !prior || !grad_loss || !out_grad || batch < 1 || T < 1 ||
-        T > kMaxLearnedIters)
+    if (loss != QLDPC_LOSS_ERROR && loss != QLDPC_LOSS_SYNDROME) return QLDPC_ERR_INVALID_ARG;
+    if (!g || !syndromes || (!targets && loss == QLDPC_LOSS_ERROR) || !prior || !grad_loss || !out_grad ||
+        batch < 1 || T < 1 || T > kMaxLearnedIters)
         return QLDPC_ERR_INVALID_ARG;
     if (int rc = check_device(g)) return rc;
     TrainPlan tp;
@@ -206,9 +216,10 @@ int qldpc_nms_backward(const qldpc_graph *g, const uint8_t *syndromes, const uin
     TrainParams p = train_params(g, tp, syndromes, targets, batch, prior, T, workspace);
     p.grad_loss = grad_loss;
     p.loss_w = loss_weights;
+    p.loss_kind = loss;
     const size_t S = size_t(g->dc_max) * size_t(g->m);
     cudaError_t e = cudaMemsetAsync(p.partial, 0, size_t(T) * S * sizeof(float), st);
-    if (e == cudaSuccess) e = launch_nms_backward(p, tp.tc, tp.grid_b, kTrainThreads, tp.smem_b, st);
+    if (e == cudaSuccess) e = launch_nms_backward(p, tp.tc, tp.grid_b[loss], kTrainThreads, tp.smem_b[loss], st);
     if (e == cudaSuccess) e = launch_gather_grad(p.partial, g->dg.eslot, T, int32_t(S), g->nnz, out_grad, st);
     return cuda_status(e);
 }

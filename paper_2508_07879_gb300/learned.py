@@ -5,8 +5,9 @@ iteration and edge instead of one alpha.  Everything that touches the decoder ru
 library's CUDA kernels:
 
 * ``NMSLoss`` is a ``torch.autograd.Function`` whose forward is ``qldpc_nms_forward`` (T unrolled
-  iterations, per-shot BCE of the soft outputs) and whose backward is ``qldpc_nms_backward`` (the
-  reverse sweep, recomputing every message from the recorded check state);
+  iterations, per-shot BCE of the soft outputs against the sampled error, or of the soft syndrome
+  against the measured one) and whose backward is ``qldpc_nms_backward`` (the reverse sweep,
+  recomputing every message from the recorded check state);
 * ``NeuralMinSum`` holds the weights, the Adam state (updated by ``qldpc_adam_step``) and the
   device workspace, and trains on shots drawn on the device by ``qldpc_sample_errors``;
 * ``evaluate`` decodes fresh device-sampled shots with any mix of plain and learned decoders and
@@ -38,29 +39,31 @@ class NMSLoss:
     _fn = None
 
     @classmethod
-    def apply(cls, weights, graph, syndromes, targets, prior, workspace, loss_weights=None):
+    def apply(cls, weights, graph, syndromes, targets, prior, workspace, loss_weights=None, loss: str = "error"):
         if cls._fn is None:
             torch = _torch()
 
             class _F(torch.autograd.Function):
                 @staticmethod
-                def forward(ctx, w, g, syn, tg, pr, ws, lw):
-                    loss, _ = qldpc.nms_forward(g, syn, tg, pr, w.detach().contiguous(), ws, loss_weights=lw)
+                def forward(ctx, w, g, syn, tg, pr, ws, lw, kind):
+                    out, _ = qldpc.nms_forward(g, syn, tg, pr, w.detach().contiguous(), ws, loss_weights=lw,
+                                               loss=kind)
                     ctx.graph = g
                     ctx.T = int(w.shape[0])
                     ctx.lw = lw
+                    ctx.kind = kind
                     ctx.save_for_backward(syn, tg, pr, ws)   # ws holds the weights and recorded state
-                    return loss
+                    return out
 
                 @staticmethod
                 def backward(ctx, grad_loss):
                     syn, tg, pr, ws = ctx.saved_tensors
                     grad = qldpc.nms_backward(ctx.graph, syn, tg, pr, ctx.T, grad_loss.float().contiguous(), ws,
-                                              loss_weights=ctx.lw)
-                    return grad, None, None, None, None, None, None
+                                              loss_weights=ctx.lw, loss=ctx.kind)
+                    return grad, None, None, None, None, None, None, None
 
             cls._fn = _F
-        return cls._fn.apply(weights, graph, syndromes, targets, prior, workspace, loss_weights)
+        return cls._fn.apply(weights, graph, syndromes, targets, prior, workspace, loss_weights, loss)
 
 
 def code_hash(h) -> bytes:
@@ -77,11 +80,16 @@ class NeuralMinSum:
 
     h: the CSR matrix (workloads.CSR); prior: float [n] LLRs; T: unrolled iterations;
     init: the starting weight (0.75 reproduces normalized min-sum with alpha = 0.75);
-    loss_weights: per-iteration loss weights lambda_t ([T]; None: 1/T each).
+    loss_weights: per-iteration loss weights lambda_t ([T]; None: 1/T each);
+    loss: "error" (BCE of sigma(-Q) against the sampled error) or "syndrome" (BCE of the soft
+    syndrome against the measured one, blind to which error of a coset the outputs point at).
     """
 
     def __init__(self, h, prior, T: int = 20, init: float = 0.75, max_batch: int = 4096, graph=None,
-                 loss_weights=None):
+                 loss_weights=None, loss: str = "error"):
+        if loss not in qldpc.LOSSES:
+            raise ValueError(f"unknown loss {loss!r}")
+        self.loss_kind = loss
         torch = _torch()
         self.h = h
         self.graph = graph if graph is not None else qldpc.Graph.from_csr(h)
@@ -100,11 +108,11 @@ class NeuralMinSum:
             np.ascontiguousarray(loss_weights, dtype=np.float32).reshape(self.T), device=dev)
 
     def loss(self, syndromes, targets):
-        """Per-shot BCE losses [B] (differentiable with respect to ``weights``)."""
+        """Per-shot losses [B] (differentiable with respect to ``weights``)."""
         if syndromes.shape[0] > self.max_batch:
             raise ValueError(f"batch {syndromes.shape[0]} exceeds max_batch {self.max_batch}")
         return NMSLoss.apply(self.weights, self.graph, syndromes, targets, self.prior, self.workspace,
-                             self.loss_weights)
+                             self.loss_weights, self.loss_kind)
 
     def train_step(self, syndromes, targets, lr: float = 1e-3, betas=(0.9, 0.999), eps: float = 1e-8):
         """One Adam step on the mean loss of a batch; returns the mean loss (device scalar)."""

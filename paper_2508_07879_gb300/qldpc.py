@@ -30,6 +30,9 @@ QLDPC_INT8 = 2
 QLDPC_NO_EARLY_STOP = 1
 QLDPC_LEARNED = 2
 QLDPC_LAYERED = 4
+QLDPC_LOSS_ERROR = 0
+QLDPC_LOSS_SYNDROME = 1
+LOSSES = {"error": QLDPC_LOSS_ERROR, "syndrome": QLDPC_LOSS_SYNDROME}
 QLDPC_MAX_ROW_DEGREE = 32
 QLDPC_MAX_COL_DEGREE = 16
 QLDPC_MAX_CHECKS = 65535
@@ -86,8 +89,8 @@ _SIGNATURES = {
     "qldpc_server_destroy": ([_p], None),
     "qldpc_graph_set_weights": ([_p, _p, _i32], ctypes.c_int),
     "qldpc_nms_workspace_bytes": ([_p, _i32, _i32, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
-    "qldpc_nms_forward": ([_p, _p, _p, _i32, _p, _p, _i32, _p, _p, _p, _p, ctypes.c_size_t, _p], ctypes.c_int),
-    "qldpc_nms_backward": ([_p, _p, _p, _i32, _p, _i32, _p, _p, _p, _p, ctypes.c_size_t, _p], ctypes.c_int),
+    "qldpc_nms_forward": ([_p, _p, _p, _i32, _p, _p, _i32, _p, _i32, _p, _p, _p, ctypes.c_size_t, _p], ctypes.c_int),
+    "qldpc_nms_backward": ([_p, _p, _p, _i32, _p, _i32, _p, _i32, _p, _p, _p, ctypes.c_size_t, _p], ctypes.c_int),
     "qldpc_adam_step": ([_p, _p, _p, _p, ctypes.c_int64, _i32, _f32, _f32, _f32, _f32, _p], ctypes.c_int),
     "qldpc_sample_errors": ([_p, ctypes.c_uint64, ctypes.c_int64, _i32, ctypes.c_double, ctypes.c_double, _p, _p,
                              _p], ctypes.c_int),
@@ -476,40 +479,45 @@ def nms_workspace_bytes(graph: Graph, batch: int, T: int) -> int:
 
 
 def nms_forward(graph: Graph, syndromes, targets, prior, weights, workspace, want_post: bool = False, stream=None,
-                loss_weights=None):
+                loss_weights=None, loss: str = "error"):
     """Training forward (qldpc_nms_forward).  workspace: CUDA uint8 tensor of at least
-    nms_workspace_bytes(graph, B, T) bytes; loss_weights: CUDA float32 [T] or None (1/T each).
+    nms_workspace_bytes(graph, B, T) bytes; loss_weights: CUDA float32 [T] or None (1/T each);
+    loss "error" or "syndrome" (targets may be None for "syndrome").
     Returns (loss float32 [B], post float32 [B, n] or None)."""
     import torch
+    kind = LOSSES[loss]
     batch = int(syndromes.shape[0])
     T = int(weights.shape[0])
-    loss = torch.empty(batch, dtype=torch.float32, device=syndromes.device)
+    out = torch.empty(batch, dtype=torch.float32, device=syndromes.device)
     post = torch.empty((batch, graph.n), dtype=torch.float32, device=syndromes.device) if want_post else None
     check(qldpc_nms_forward(graph.handle, _dev_ptr(syndromes, torch.uint8, (batch, graph.m), "syndromes"),
-                            _dev_ptr(targets, torch.uint8, (batch, graph.n), "targets"), batch,
+                            _dev_ptr(targets, torch.uint8, (batch, graph.n), "targets")
+                            if targets is not None else None, batch,
                             _dev_ptr(prior, torch.float32, (graph.n,), "prior"),
                             _dev_ptr(weights, torch.float32, (T, graph.nnz), "weights"), T,
                             _dev_ptr(loss_weights, torch.float32, (T,), "loss_weights")
-                            if loss_weights is not None else None,
-                            _dev_ptr(loss, torch.float32, (batch,), "loss"),
+                            if loss_weights is not None else None, kind,
+                            _dev_ptr(out, torch.float32, (batch,), "loss"),
                             _dev_ptr(post, torch.float32, (batch, graph.n), "post") if post is not None else None,
                             ctypes.c_void_p(workspace.data_ptr()), int(workspace.numel() * workspace.element_size()),
                             _stream_handle(stream)), "qldpc_nms_forward")
-    return loss, post
+    return out, post
 
 
 def nms_backward(graph: Graph, syndromes, targets, prior, T: int, grad_loss, workspace, stream=None,
-                 loss_weights=None):
-    """Training backward (qldpc_nms_backward) after nms_forward on the same workspace.
+                 loss_weights=None, loss: str = "error"):
+    """Training backward (qldpc_nms_backward) after nms_forward on the same workspace (same loss).
     Returns the weight gradient float32 [T, nnz]."""
     import torch
+    kind = LOSSES[loss]
     batch = int(syndromes.shape[0])
     grad = torch.empty((int(T), graph.nnz), dtype=torch.float32, device=syndromes.device)
     check(qldpc_nms_backward(graph.handle, _dev_ptr(syndromes, torch.uint8, (batch, graph.m), "syndromes"),
-                             _dev_ptr(targets, torch.uint8, (batch, graph.n), "targets"), batch,
+                             _dev_ptr(targets, torch.uint8, (batch, graph.n), "targets")
+                             if targets is not None else None, batch,
                              _dev_ptr(prior, torch.float32, (graph.n,), "prior"), int(T),
                              _dev_ptr(loss_weights, torch.float32, (int(T),), "loss_weights")
-                             if loss_weights is not None else None,
+                             if loss_weights is not None else None, kind,
                              _dev_ptr(grad_loss, torch.float32, (batch,), "grad_loss"),
                              _dev_ptr(grad, torch.float32, (int(T), graph.nnz), "grad"),
                              ctypes.c_void_p(workspace.data_ptr()), int(workspace.numel() * workspace.element_size()),

@@ -126,8 +126,11 @@ def test_learned_entry_points_validate_on_the_host(q):
     assert q.qldpc_graph_set_weights(None, None, 0) == inv
     size = ctypes.c_size_t()
     assert q.qldpc_nms_workspace_bytes(None, 16, 4, ctypes.byref(size)) == inv
-    assert q.qldpc_nms_forward(None, None, None, 16, None, None, 4, None, None, None, None, 0, None) == inv
-    assert q.qldpc_nms_backward(None, None, None, 16, None, 4, None, None, None, None, 0, None) == inv
+    assert q.qldpc_nms_forward(None, None, None, 16, None, None, 4, None, 0, None, None, None, 0, None) == inv
+    assert q.qldpc_nms_backward(None, None, None, 16, None, 4, None, 0, None, None, None, 0, None) == inv
+    # an unknown loss kind is refused before anything else is looked at
+    assert q.qldpc_nms_forward(None, None, None, 16, None, None, 4, None, 7, None, None, None, 0, None) == inv
+    assert q.qldpc_nms_backward(None, None, None, 16, None, 4, None, -1, None, None, None, 0, None) == inv
     assert q.qldpc_adam_step(None, None, None, None, -1, 1, 1e-3, 0.9, 0.999, 1e-8, None) == inv
     assert q.qldpc_adam_step(None, None, None, None, 10, 0, 1e-3, 0.9, 0.999, 1e-8, None) == inv
     assert q.qldpc_adam_step(None, None, None, None, 10, 1, 1e-3, 1.0, 0.999, 1e-8, None) == inv

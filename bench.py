@@ -614,7 +614,9 @@ def measure_learned(qldpc, args):
                            p_hi=LEARN_P[1], seed=LEARN_SEEDS[1])
     ler = {k: v["ler"] for k, v in res.items()}
     iters = {k: v["mean_iters"] for k, v in res.items()}
-    for loss in ("syndrome", "error"):
+    # (key prefix, loss, Adam lr): the configured lr, and the syndrome loss at a larger step
+    runs = (("", "syndrome", LEARN_LR), ("lr1e-2_", "syndrome", 1e-2), ("error_loss_", "error", LEARN_LR))
+    for prefix, loss, lr in runs:
         model = learned.NeuralMinSum(h, prior, T=LEARN_T, max_batch=LEARN_BATCH, graph=g, loss=loss)
         # kernel times of one training step, events on the launching (current) stream
         err, syn = qldpc.sample_errors(g, LEARN_SEEDS[0] + 1000, 0, LEARN_BATCH, *LEARN_P)
@@ -641,7 +643,7 @@ def measure_learned(qldpc, args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         hist = model.train(shots=args.learned_train_shots, batch=LEARN_BATCH, p_lo=LEARN_P[0], p_hi=LEARN_P[1],
-                           seed=LEARN_SEEDS[0], lr=LEARN_LR, record_every=50)
+                           seed=LEARN_SEEDS[0], lr=lr, record_every=50)
         torch.cuda.synchronize()
         train_s = time.perf_counter() - t0
         model.publish()
@@ -650,10 +652,11 @@ def measure_learned(qldpc, args):
                                                     "learned_20_fallback_50": (50, True)},
                                shots=args.learned_eval_shots, p_lo=LEARN_P[0], p_hi=LEARN_P[1], seed=LEARN_SEEDS[1])
         eval_s = time.perf_counter() - t0
-        prefix = "" if loss == "syndrome" else "error_loss_"
         ler.update({prefix + k: v["ler"] for k, v in res.items()})
         iters.update({prefix + k: v["mean_iters"] for k, v in res.items()})
-        out[loss + "_loss_training"] = {
+        wmean = model.weights.detach().mean(dim=1).cpu().numpy()
+        out[(prefix or "syndrome_") + "training"] = {
+            "loss": loss, "lr": lr, "mean_weight_per_iteration": [round(float(x), 4) for x in wmean],
             "train_s": train_s, "train_shots_per_s": steps * LEARN_BATCH / train_s,
             "loss_first": float(hist[0]) if len(hist) else None, "loss_last": float(hist[-1]) if len(hist) else None,
             "step_kernel_ms": {"forward": tf, "backward_and_reduce": tb},
@@ -663,7 +666,8 @@ def measure_learned(qldpc, args):
         g.set_weights(None)
     out["ler"] = ler
     out["mean_iters"] = iters
-    out["learned_keys"] = "learned_*: trained on the syndrome loss; error_loss_learned_*: on the error loss"
+    out["learned_keys"] = ("learned_*: syndrome loss, lr 1e-3 (the configured run); lr1e-2_learned_*: syndrome "
+                           "loss, lr 1e-2; error_loss_learned_*: error loss, lr 1e-3")
     return out
 
 

@@ -35,7 +35,8 @@
  * qldpc_graph_reserve).  A graph must be used on the device that was current when it was created.
  *
  * Entry points by group:
- *   graphs          qldpc_graph_create / _create_csc / _destroy / _dims / _set_launch / _reserve
+ *   graphs          qldpc_graph_create / _create_csc / _destroy / _dims / _footprint / _set_launch /
+ *                   _reserve
  *   decoding        qldpc_decode, qldpc_decode_ex (flags: QLDPC_NO_EARLY_STOP, QLDPC_LAYERED for
  *                   the row-serial schedule, QLDPC_LEARNED), qldpc_decode_pair, qldpc_decode_host,
  *                   qldpc_decode_host_noalloc

@@ -218,7 +218,7 @@ int validate_and_layout(const int32_t *row_ptr, const int32_t *col_idx, int32_t 
     }
     const int32_t dv_max = *std::max_element(cdeg.begin(), cdeg.end());
     if (dc_max > QLDPC_MAX_ROW_DEGREE || dv_max > QLDPC_MAX_COL_DEGREE) return QLDPC_ERR_UNSUPPORTED;
-    if (m > QLDPC_MAX_CHECKS) return QLDPC_ERR_UNSUPPORTED;   // edge lists store the check in 16 bits
+    if (m > QLDPC_MAX_CHECKS) return QLDPC_ERR_UNSUPPORTED;   // (no shot that large fits on chip either)
 
     out.dc_max = dc_max;
     out.dv_max = dv_max;

@@ -106,15 +106,26 @@ __device__ __forceinline__ uint8_t lane_target(const DeviceGraph &g, const uint8
     return v < uint32_t(N) ? (tg ? uint8_t(tg[v] & 1u) : uint8_t(0)) : kIdleLane;
 }
 
-// Syndrome loss of check c from the a-posteriori LLRs Q_j of its variables (in its slots):
-// P = (1 + (-1)^s prod_j t_j) / 2 with t_j = tanh(Q_j / 2) is the probability that the row's parity
-// under independent bits sigma(-Q) equals s.  |t_j| = (1 - x_j) / (1 + x_j) with x_j = e^{-|Q_j|},
-// and prod_j |t_j| = exp(A), A = sum_j [log1p(-x_j) - log1p(x_j)], so that a violated, confident
-// check gets P = -expm1(A) / 2 without the cancellation of 1 - prod (|t| rounds to 1 well before
-// 1 - |t| is negligible).  Fills t[] for the caller.
+// Syndrome loss.  With t_v = tanh(Q_v / 2), P_c = (1 + (-1)^s prod_{v in c} t_v) / 2 is the
+// probability that row c's parity under independent bits sigma(-Q) equals s.  Each variable
+// stores, on its edge slots, its log-magnitude code
+//   lm_v = sign(Q_v) * (-log |t_v|),  -log |t_v| = log1p(e^-|Q_v|) - log1p(-e^-|Q_v|)  (+inf at Q = 0),
+// computed once per variable.  A check then has prod |t| = exp(A), A = -sum |lm|, and a violated,
+// confident check gets P = -expm1(A) / 2 without the cancellation of 1 - prod (|t| rounds to 1
+// long before 1 - |t| is negligible).
 constexpr float kSynLossFloor = 1e-7f;
-template <int DC, bool UNIFORM>
-__device__ __forceinline__ float parity_match_prob(int c, int M, int deg, uint32_t s_bit, const float *__restrict__ qs,
+
+// The sign travels in the sign bit (also on a magnitude of 0, where |Q| is so large that |t| = 1).
+__device__ __forceinline__ float log_magnitude_code(float Q)
+{
+    const float x = expf(-fabsf(Q));
+    const float mag = log1pf(x) - log1pf(-x);   // -log |tanh(Q/2)| >= 0
+    return __uint_as_float(__float_as_uint(mag) | (Q < 0.0f ? 0x80000000u : 0u));
+}
+
+// P_c from the codes in check c's slots; optionally t_j = sign * exp(-|lm_j|) for the caller.
+template <int DC, bool UNIFORM, bool WANT_T>
+__device__ __forceinline__ float parity_match_prob(int c, int M, int deg, uint32_t s_bit, const float *__restrict__ ls,
                                                    float *t)
 {
     float A = 0.0f;
@@ -122,35 +133,35 @@ __device__ __forceinline__ float parity_match_prob(int c, int M, int deg, uint32
 #pragma unroll
     for (int j = 0; j < DC; ++j) {
         if (UNIFORM || j < deg) {
-            const float Q = qs[j * M + c];
-            const float x = expf(-fabsf(Q));
-            A += log1pf(-x) - log1pf(x);
-            const float at = (1.0f - x) / (1.0f + x);
-            t[j] = Q < 0.0f ? -at : at;
-            neg ^= Q < 0.0f ? 1u : 0u;
-        } else {
+            const float lm = ls[j * M + c];
+            const bool nj = (__float_as_uint(lm) >> 31) != 0u;
+            A -= fabsf(lm);
+            neg ^= nj ? 1u : 0u;
+            if (WANT_T) {
+                const float at = expf(-fabsf(lm));
+                t[j] = nj ? -at : at;
+            }
+        } else if (WANT_T) {
             t[j] = 1.0f;
         }
     }
-    const float e = expf(A);   // prod_j |t_j|
-    return neg ? -0.5f * expm1f(A) : 0.5f * (1.0f + e);
+    return neg ? -0.5f * expm1f(A) : 0.5f * (1.0f + expf(A));
 }
 
 template <int DC, bool UNIFORM>
-__device__ __forceinline__ float syndrome_term(int c, int M, int deg, uint32_t s_bit, const float *__restrict__ qs)
+__device__ __forceinline__ float syndrome_term(int c, int M, int deg, uint32_t s_bit, const float *__restrict__ ls)
 {
-    float t[DC];
-    const float P = parity_match_prob<DC, UNIFORM>(c, M, deg, s_bit, qs, t);
+    const float P = parity_match_prob<DC, UNIFORM, false>(c, M, deg, s_bit, ls, nullptr);
     return -logf(fmaxf(P, kSynLossFloor));
 }
 
 // d(syndrome term)/d t_j = -(1 / P) (-1)^s / 2 prod_{i != j} t_i (0 at the floor), written over the
-// Q_j of check c.
+// codes of check c.
 template <int DC, bool UNIFORM>
-__device__ __forceinline__ void syndrome_term_grad(int c, int M, int deg, uint32_t s_bit, float *__restrict__ qs)
+__device__ __forceinline__ void syndrome_term_grad(int c, int M, int deg, uint32_t s_bit, float *__restrict__ ls)
 {
     float t[DC], pre[DC];
-    const float P = parity_match_prob<DC, UNIFORM>(c, M, deg, s_bit, qs, t);
+    const float P = parity_match_prob<DC, UNIFORM, true>(c, M, deg, s_bit, ls, t);
     const float sg = s_bit ? -1.0f : 1.0f;
     const float coef = P > kSynLossFloor ? -0.5f * sg / P : 0.0f;
     float prod = 1.0f;
@@ -163,7 +174,7 @@ __device__ __forceinline__ void syndrome_term_grad(int c, int M, int deg, uint32
 #pragma unroll
     for (int j = DC - 1; j >= 0; --j) {
         if (UNIFORM || j < deg) {
-            qs[j * M + c] = coef * (pre[j] * suf);
+            ls[j * M + c] = coef * (pre[j] * suf);
             suf *= t[j];
         }
     }
@@ -202,7 +213,7 @@ __global__ void __launch_bounds__(kTrainThreads, 4) nms_forward_kernel(const Tra
     extern __shared__ __align__(16) unsigned char smem[];
     const TrainLayout L = train_layout(M, NV, p.g.dc_max, false, syn_loss);
     float *slots = reinterpret_cast<float *>(smem + L.slot_off);
-    float *ts = reinterpret_cast<float *>(smem + L.t_off);        // syndrome loss: Q of each edge's variable
+    float *ts = reinterpret_cast<float *>(smem + L.t_off);        // syndrome loss: each edge's variable's code
     float *gam = reinterpret_cast<float *>(smem + L.g_off);
     uint8_t *y = smem + L.y_off;
     uint8_t *sb = smem + L.s_off;
@@ -228,7 +239,7 @@ __global__ void __launch_bounds__(kTrainThreads, 4) nms_forward_kernel(const Tra
         for (int k = 0; k < p.T; ++k) {
             const float *wk = p.w + size_t(k) * S;
             uint32_t *st = p.state + (size_t(b) * p.T + k) * size_t(kStateWords) * M;
-            // syndrome loss of iteration k-1 (its Q slots are complete) beside the check step of k
+            // syndrome loss of iteration k-1 (its code slots are complete) beside the check step of k
             const float lw_prev = (syn_loss && k > 0) ? (p.loss_w ? __ldg(p.loss_w + k - 1) : 1.0f) : 0.0f;
             for (int c = tid; c < M; c += T) {
                 const int deg = UNIFORM ? DC : int(__ldg(p.g.rdeg + c));
@@ -244,7 +255,8 @@ __global__ void __launch_bounds__(kTrainThreads, 4) nms_forward_kernel(const Tra
                                                                slots, nullptr);
                 if (y[u] == kIdleLane) continue;
                 if (syn_loss) {
-                    for (int i = 0; i < deg; ++i) ts[__ldg(p.g.vslot + size_t(i) * NV + u)] = Q;
+                    const float lm = log_magnitude_code(Q);
+                    for (int i = 0; i < deg; ++i) ts[__ldg(p.g.vslot + size_t(i) * NV + u)] = lm;
                 } else {
                     acc += lw * (y[u] ? softplus(Q) : softplus(-Q));
                 }
@@ -289,7 +301,7 @@ __global__ void __launch_bounds__(kTrainThreads, 4) nms_backward_kernel(const Tr
     float *gs = reinterpret_cast<float *>(smem + L.slot_off);     // dL/dq (next iteration), then dL/dr
     float *rs = reinterpret_cast<float *>(smem + L.r_off);        // recomputed r of the current iteration
     uint32_t *scb = reinterpret_cast<uint32_t *>(smem + L.c_off); // recorded state, two iterations
-    float *ts = reinterpret_cast<float *>(smem + L.t_off);        // syndrome loss: Q per edge, then d/dt
+    float *ts = reinterpret_cast<float *>(smem + L.t_off);        // syndrome loss: codes per edge, then d/dt
     float *gam = reinterpret_cast<float *>(smem + L.g_off);
     uint8_t *y = smem + L.y_off;
     uint8_t *sb = smem + L.s_off;
@@ -325,7 +337,7 @@ __global__ void __launch_bounds__(kTrainThreads, 4) nms_backward_kernel(const Tr
             if (k > 0) prefetch_state(sn, stb + size_t(k - 1) * SW, M);  // overlaps the variable side
             const float gk = gscale * (p.loss_w ? __ldg(p.loss_w + k) : 1.0f / float(p.T));
             if (syn_loss) {
-                // Q^(k) of every edge's variable, then each check's d(loss term)/d t in its place
+                // the code of Q^(k) on every edge slot, then each check's d(loss term)/d t in its place
                 for (int u = tid; u < NV; u += T) {
                     const int deg = __ldg(p.g.vdeg + u);
                     uint32_t sl[DV];
@@ -337,9 +349,10 @@ __global__ void __launch_bounds__(kTrainThreads, 4) nms_backward_kernel(const Tr
                             Q = __fadd_rn(Q, rs[sl[i]]);
                         }
                     }
+                    const float lm = log_magnitude_code(Q);
 #pragma unroll
                     for (int i = 0; i < DV; ++i)
-                        if (i < deg) ts[sl[i]] = Q;
+                        if (i < deg) ts[sl[i]] = lm;
                 }
                 __syncthreads();
                 for (int c = tid; c < M; c += T) {

@@ -59,6 +59,13 @@ struct F32 {
     static __device__ __forceinline__ mag_t mag_init() { return __int_as_float(0x7f800000); }
     static __device__ __forceinline__ mag_t mn(mag_t a, mag_t b) { return fminf(a, b); }
     static __device__ __forceinline__ mag_t mx(mag_t a, mag_t b) { return fmaxf(a, b); }
+    // three-input minimum (sm_100 and later)
+    static __device__ __forceinline__ mag_t mn3(mag_t a, mag_t b, mag_t c)
+    {
+        float r;
+        asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+        return r;
+    }
     static __device__ __forceinline__ mag_t scale(mag_t m, const LaunchParams &p)
     {
         return __fmul_rn(p.alpha, m);
@@ -97,6 +104,7 @@ struct IFix {
     static __device__ __forceinline__ mag_t mag_init() { return 0x7fffffff; }
     static __device__ __forceinline__ mag_t mn(mag_t a, mag_t b) { return min(a, b); }
     static __device__ __forceinline__ mag_t mx(mag_t a, mag_t b) { return max(a, b); }
+    static __device__ __forceinline__ mag_t mn3(mag_t a, mag_t b, mag_t c) { return __vimin3_s32(a, b, c); }
     // |r| = floor(min * alpha_q / 2^15); min <= 32767 and alpha_q <= 2^15 keep it in 31 bits
     static __device__ __forceinline__ mag_t scale(mag_t m, const LaunchParams &p)
     {
@@ -136,6 +144,39 @@ struct CheckOf {
     }
 };
 
+// The two smallest magnitudes of a row, with multiplicity (m2 = m1 when the minimum is shared).
+// Rows of even exact degree take the magnitudes in pairs (lo, hi): the second smallest of
+// {m1 <= m2} and {lo <= hi} is min(max(m1, lo), m2, hi), one three-input minimum; other rows
+// stream them one at a time.  Either way the result is the exact pair of minima.
+template <class P, int DC, bool UNIFORM>
+__device__ __forceinline__ void two_smallest(const typename P::acc_t *q, int deg, typename P::mag_t &m1,
+                                             typename P::mag_t &m2)
+{
+    using mag_t = typename P::mag_t;
+    if constexpr (UNIFORM && DC % 2 == 0) {
+        m1 = P::mn(P::mag(q[0]), P::mag(q[1]));
+        m2 = P::mx(P::mag(q[0]), P::mag(q[1]));
+#pragma unroll
+        for (int j = 2; j < DC; j += 2) {
+            const mag_t a = P::mag(q[j]), b = P::mag(q[j + 1]);
+            const mag_t lo = P::mn(a, b), hi = P::mx(a, b);
+            m2 = P::mn3(P::mx(m1, lo), m2, hi);
+            m1 = P::mn(m1, lo);
+        }
+    } else {
+        m1 = P::mag_init();
+        m2 = P::mag_init();
+#pragma unroll
+        for (int j = 0; j < DC; ++j) {
+            if (UNIFORM || j < deg) {
+                const mag_t a = P::mag(q[j]);
+                m2 = P::mn(m2, P::mx(m1, a));
+                m1 = P::mn(m1, a);
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------------------------
 // Check-node step (Alg. 1, CN processing) of one check, fused with the stop test of the previous
 // decisions.  Returns 1 iff the check's parity word says s_m is satisfied.
@@ -153,17 +194,15 @@ __device__ __forceinline__ int check_step(int c, int M, int deg, uint32_t pw, bo
     if (update) {
         acc_t q[DC];
         uint32_t sx = 0;
-        mag_t m1 = P::mag_init(), m2 = P::mag_init();
 #pragma unroll
         for (int j = 0; j < DC; ++j) {
             if (UNIFORM || j < deg) {
                 q[j] = load_msg<P>(slots, uint32_t(j * M + c));
                 sx ^= P::sign_word(q[j]);          // bit 31: parity of the signs
-                const mag_t a = P::mag(q[j]);
-                m2 = P::mn(m2, P::mx(m1, a));     // two smallest magnitudes, with multiplicity
-                m1 = P::mn(m1, a);
             }
         }
+        mag_t m1, m2;
+        two_smallest<P, DC, UNIFORM>(q, deg, m1, m2);
         const uint32_t negall = ((pw >> 1) ^ (sx >> 31)) & 1u;   // (-1)^{s_m} * prod of all signs
         if constexpr (LEARNED) {
             if (w) {

@@ -78,6 +78,15 @@ struct F32 {
     {
         return __uint_as_float(__float_as_uint(m) ^ (__float_as_uint(x) & 0x80000000u) ^ (negall << 31));
     }
+    // the same in two steps: the check's factor on a magnitude once, then each edge's own sign
+    static __device__ __forceinline__ mag_t presign(mag_t m, uint32_t negall)
+    {
+        return __uint_as_float(__float_as_uint(m) ^ (negall << 31));
+    }
+    static __device__ __forceinline__ acc_t apply_sign(mag_t pm, acc_t x)
+    {
+        return __uint_as_float(__float_as_uint(pm) ^ (__float_as_uint(x) & 0x80000000u));
+    }
     static __device__ __forceinline__ float post(acc_t a) { return a; }
     static __device__ __forceinline__ msg_t to_msg(acc_t q) { return q; }
 };
@@ -116,6 +125,8 @@ struct IFix {
         const int32_t neg = int32_t(negall ^ (uint32_t(x) >> 31));   // 0 or 1
         return (m ^ -neg) + neg;
     }
+    static __device__ __forceinline__ mag_t presign(mag_t m, uint32_t negall) { return negall ? -m : m; }
+    static __device__ __forceinline__ acc_t apply_sign(mag_t pm, acc_t x) { return x < 0 ? -pm : pm; }
     static __device__ __forceinline__ float post(acc_t a) { return float(a) * (1.0f / float(1 << FRAC)); }
     static __device__ __forceinline__ msg_t to_msg(acc_t q) { return msg_t(max(-LIM, min(LIM, q))); }
 };
@@ -217,12 +228,13 @@ __device__ __forceinline__ int check_step(int c, int M, int deg, uint32_t pw, bo
                 return (pw & 1u) == 0;
             }
         }
-        const mag_t r1 = P::scale(m1, p);                        // alpha * min over the others
-        const mag_t r2 = P::scale(m2, p);                        // ... when |q_j| is the minimum
+        // alpha * min over the others (r2 where |q_j| is the minimum), with the check's sign factor
+        const mag_t r1 = P::presign(P::scale(m1, p), negall);
+        const mag_t r2 = P::presign(P::scale(m2, p), negall);
 #pragma unroll
         for (int j = 0; j < DC; ++j) {
             if (UNIFORM || j < deg)
-                slots[j * M + c] = typename P::msg_t(P::signed_like(P::mag(q[j]) == m1 ? r2 : r1, q[j], negall));
+                slots[j * M + c] = typename P::msg_t(P::apply_sign(P::mag(q[j]) == m1 ? r2 : r1, q[j]));
         }
     }
     return (pw & 1u) == 0;

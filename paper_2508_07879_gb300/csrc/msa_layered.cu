@@ -32,24 +32,22 @@ __device__ __forceinline__ void layered_check(int c, int M, int deg, uint32_t s_
     acc_t q[DC];
     uint32_t v[DC];
     uint32_t sx = 0;
-    mag_t m1 = P::mag_init(), m2 = P::mag_init();
 #pragma unroll
     for (int j = 0; j < DC; ++j) {
         if (UNIFORM || j < deg) {
             v[j] = __ldg(ecol + size_t(j) * M + c);
             q[j] = P::sub_q(Q[v[j]], load_msg<P>(slots, uint32_t(j * M + c)));
             sx ^= P::sign_word(q[j]);
-            const mag_t a = P::mag(q[j]);
-            m2 = P::mn(m2, P::mx(m1, a));
-            m1 = P::mn(m1, a);
         }
     }
+    mag_t m1, m2;
+    two_smallest<P, DC, UNIFORM>(q, deg, m1, m2);
     const uint32_t negall = (s_bit ^ (sx >> 31)) & 1u;
-    const mag_t r1 = P::scale(m1, p), r2 = P::scale(m2, p);
+    const mag_t r1 = P::presign(P::scale(m1, p), negall), r2 = P::presign(P::scale(m2, p), negall);
 #pragma unroll
     for (int j = 0; j < DC; ++j) {
         if (UNIFORM || j < deg) {
-            const acc_t r = P::signed_like(P::mag(q[j]) == m1 ? r2 : r1, q[j], negall);
+            const acc_t r = P::apply_sign(P::mag(q[j]) == m1 ? r2 : r1, q[j]);
             Q[v[j]] = P::add(q[j], r);
             slots[j * M + c] = P::to_msg(r);
         }
@@ -255,24 +253,23 @@ __global__ void __launch_bounds__(256, 1) msa_layered_reg_kernel(const LaunchPar
                             acc_t q[DC];
                             uint32_t v[DC];
                             uint32_t sx = 0;
-                            mag_t m1 = P::mag_init(), m2 = P::mag_init();
 #pragma unroll
                             for (int j = 0; j < DC; ++j) {
                                 if (UNIFORM || j < mdeg[l]) {
                                     v[j] = (ev[l][j / 2] >> (16 * (j & 1))) & 0xffffu;
                                     q[j] = P::sub_q(Q[v[j]], r[l][j]);
                                     sx ^= P::sign_word(q[j]);
-                                    const mag_t a = P::mag(q[j]);
-                                    m2 = P::mn(m2, P::mx(m1, a));
-                                    m1 = P::mn(m1, a);
                                 }
                             }
+                            mag_t m1, m2;
+                            two_smallest<P, DC, UNIFORM>(q, mdeg[l], m1, m2);
                             const uint32_t negall = (((sbits >> l) & 1u) ^ (sx >> 31)) & 1u;
-                            const mag_t r1 = P::scale(m1, p), r2 = P::scale(m2, p);
+                            const mag_t r1 = P::presign(P::scale(m1, p), negall);
+                            const mag_t r2 = P::presign(P::scale(m2, p), negall);
 #pragma unroll
                             for (int j = 0; j < DC; ++j) {
                                 if (UNIFORM || j < mdeg[l]) {
-                                    r[l][j] = P::signed_like(P::mag(q[j]) == m1 ? r2 : r1, q[j], negall);
+                                    r[l][j] = P::apply_sign(P::mag(q[j]) == m1 ? r2 : r1, q[j]);
                                     Q[v[j]] = P::add(q[j], r[l][j]);
                                 }
                             }

@@ -68,7 +68,7 @@ ALU_LANES_PER_SM = 128          # FP32/INT32 lanes per SM, one operation per lan
 
 # DRAM traffic of one decoder launch from an ncu capture, valid only for the kernel source it was
 # measured on (profiles/msa_batch_lp1054_b65536_fp32.md); reported as null once the source changes.
-NCU_TRAFFIC = {"source_sha16": "d8fbdb3f760e29ae", "bytes_per_launch": 30533888 + 12434176,
+NCU_TRAFFIC = {"source_sha16": "54bcf551061bd128", "bytes_per_launch": 30557440 + 12357632,
                "profile": "profiles/msa_batch_lp1054_b65536_fp32.md"}
 
 WORKLOAD = "LP-1054 H_Z (465x1054, E=3720), iid X noise p=0.01..0.05, B=65536/step, max 50 it, alpha 0.75"

@@ -156,19 +156,26 @@ struct CheckOf {
 };
 
 // The two smallest magnitudes of a row, with multiplicity (m2 = m1 when the minimum is shared).
-// Rows of even exact degree take the magnitudes in pairs (lo, hi): the second smallest of
-// {m1 <= m2} and {lo <= hi} is min(max(m1, lo), m2, hi), one three-input minimum; other rows
-// stream them one at a time.  Either way the result is the exact pair of minima.
+// Rows of exact degree take the magnitudes in pairs (lo, hi): the second smallest of {m1 <= m2}
+// and {lo <= hi} is min(max(m1, lo), m2, hi), one three-input minimum (an odd degree starts from
+// m1 = the first magnitude, m2 = +inf); rows of varying degree stream them one at a time.  Either
+// way the result is the exact pair of minima.
 template <class P, int DC, bool UNIFORM>
 __device__ __forceinline__ void two_smallest(const typename P::acc_t *q, int deg, typename P::mag_t &m1,
                                              typename P::mag_t &m2)
 {
     using mag_t = typename P::mag_t;
-    if constexpr (UNIFORM && DC % 2 == 0) {
-        m1 = P::mn(P::mag(q[0]), P::mag(q[1]));
-        m2 = P::mx(P::mag(q[0]), P::mag(q[1]));
+    if constexpr (UNIFORM && DC >= 2) {
+        constexpr int j0 = DC % 2 == 0 ? 2 : 1;
+        if constexpr (DC % 2 == 0) {
+            m1 = P::mn(P::mag(q[0]), P::mag(q[1]));
+            m2 = P::mx(P::mag(q[0]), P::mag(q[1]));
+        } else {
+            m1 = P::mag(q[0]);
+            m2 = P::mag_init();
+        }
 #pragma unroll
-        for (int j = 2; j < DC; j += 2) {
+        for (int j = j0; j < DC; j += 2) {
             const mag_t a = P::mag(q[j]), b = P::mag(q[j + 1]);
             const mag_t lo = P::mn(a, b), hi = P::mx(a, b);
             m2 = P::mn3(P::mx(m1, lo), m2, hi);

@@ -63,8 +63,13 @@ LEARN_LR = 1e-3
 LEARN_P = (0.02, 0.06)       # per-shot rate range, training and evaluation
 LEARN_EVAL = 1_000_000       # fresh evaluation shots
 LEARN_SEEDS = (7, 99)        # training, evaluation
-OPS_PER_EDGE_ITER = 10          # algorithmic ALU operations per edge per iteration
+# Algorithmic operations per edge per iteration: check step |q|, sign parity, three min/max, select,
+# alpha multiply, sign apply; variable step add and extrinsic add.  Seven of them (all but the
+# multiply and the two adds) are ALU-pipe work.
+OPS_PER_EDGE_ITER = 10
+ALU_OPS_PER_EDGE_ITER = 7
 ALU_LANES_PER_SM = 128          # FP32/INT32 lanes per SM, one operation per lane per clock
+ALU_PIPE_LANES_PER_SM = 64      # the ALU pipe (integer, logic, compare, min/max) is half rate
 
 # DRAM traffic of one decoder launch from an ncu capture, valid only for the kernel source it was
 # measured on (profiles/msa_batch_lp1054_b65536_fp32.md); reported as null once the source changes.
@@ -329,6 +334,11 @@ def run_ours(args, rank, world, local):
                 "kernel": "msa_batch_kernel", "ops_per_launch": ops,
                 "units": "10 ALU ops per edge per iteration x E=3720 x iterations run",
                 "peak_basis": f"{props.multi_processor_count} SMs x {ALU_LANES_PER_SM} lanes x {max_mhz:.0f} MHz (max SM clock)",
+                # the op mix on the half-rate ALU pipe: 7 ALU-pipe ops per 10 bound the rate
+                "op_mix_peak": round(peak * (ALU_PIPE_LANES_PER_SM / ALU_LANES_PER_SM)
+                                     * OPS_PER_EDGE_ITER / ALU_OPS_PER_EDGE_ITER, 3),
+                "op_mix_frac": round(achieved / (peak * (ALU_PIPE_LANES_PER_SM / ALU_LANES_PER_SM)
+                                                 * OPS_PER_EDGE_ITER / ALU_OPS_PER_EDGE_ITER), 4),
                 "hbm_algorithmic_gbs": round((h.m + h.n + 5) * B / (ms_per_step / 1e3) / 1e9, 2),
                 "hbm_peak_gbs_measured": 6758.9}
 

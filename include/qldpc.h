@@ -98,7 +98,7 @@ enum {
                                      Q = q + r); FP32 or INT16; not with QLDPC_LEARNED */
 };
 
-/* Limits of the kernels in this build. */
+/* Limits of the compiled kernels. */
 enum {
     QLDPC_MAX_ROW_DEGREE = 32,    /* check-node degree d_c */
     QLDPC_MAX_COL_DEGREE = 16,    /* variable-node degree d_v */

@@ -438,7 +438,7 @@ def measure_latency(qldpc, graph, code, args):
     ok = torch.empty(1, dtype=torch.uint8).pin_memory().numpy()
     prior = b.prior.copy()
     lat = {}
-    for prec in ("fp32", "int16"):
+    for prec in ("fp32", "int16", "int8"):
         ts = np.empty(shots + warm)
         iters = np.empty(shots + warm, dtype=np.int32)
         for i in range(shots + warm):
@@ -458,7 +458,7 @@ def measure_latency(qldpc, graph, code, args):
     # the same shots through the persistent server: requests 50 us apart, latency = result seen by
     # the host - scheduled arrival (host steady clock inside the C ABI)
     srv_lat = {}
-    for prec in ("fp32", "int16"):
+    for prec in ("fp32", "int16", "int8"):
         with qldpc.Server([graph], [prior], MAX_ITER, ALPHA, prec, blocks=[8], ring_capacity=1024) as srv:
             arrival = (np.arange(shots + warm) * LAT_SERVER_GAP_NS).astype(np.int64)
             _, iters, _, lat_ns = srv.replay(np.zeros(shots + warm, np.int32), list(syn), arrival)
@@ -495,7 +495,7 @@ def measure_serving(qldpc, args):
         cursor[c] += 1
     out = {"workload": "40/40/20 HGP-400 / LP-1054 / BB-288 (H_Z, iid X, p=0.03), Poisson mean gap 20 us",
            "requests": n, "max_iter": MAX_ITER}
-    for prec in ("fp32", "int16"):
+    for prec in ("fp32", "int16", "int8"):
         with qldpc.Server(graphs, priors, MAX_ITER, ALPHA, prec, ring_capacity=4096) as srv:
             _, _, _, lat_ns = srv.replay(codes, syn, arrival, timeout_s=60.0)
             t0 = time.perf_counter()

@@ -253,7 +253,7 @@ typedef struct qldpc_server qldpc_server;
 enum { QLDPC_SERVER_MAX_CODES = 4 };
 
 typedef struct qldpc_server_config {
-    int32_t precision;            /* QLDPC_FP32 or QLDPC_INT16 (the server has no INT8 kernels) */
+    int32_t precision;            /* QLDPC_FP32, QLDPC_INT16 or QLDPC_INT8 */
     int32_t max_iter;             /* >= 0 */
     float alpha;                  /* as for qldpc_decode_ex */
     uint32_t flags;               /* QLDPC_NO_EARLY_STOP, or QLDPC_LEARNED (FP32: every code whose

@@ -171,10 +171,13 @@ inline int server_slot_bytes(int m, int n) { return int(align16(16 + size_t(m)) 
 
 const void *server_kernel_f32(const KernelChoice &kc);
 const void *server_kernel_i16(const KernelChoice &kc);
+const void *server_kernel_i8(const KernelChoice &kc);
 cudaError_t launch_server_f32(const ServerParams &p, const KernelChoice &kc, int blocks, int threads,
                               size_t smem, cudaStream_t stream);
 cudaError_t launch_server_i16(const ServerParams &p, const KernelChoice &kc, int blocks, int threads,
                               size_t smem, cudaStream_t stream);
+cudaError_t launch_server_i8(const ServerParams &p, const KernelChoice &kc, int blocks, int threads,
+                             size_t smem, cudaStream_t stream);
 
 // Per-precision instantiation tables (one translation unit each).
 const void *msa_kernel_f32(const KernelChoice &kc);

@@ -55,9 +55,9 @@ namespace {
 
 int launch_server(qldpc_server *s)
 {
-    cudaError_t e = s->precision == QLDPC_INT16
-                        ? launch_server_i16(s->sp, s->kc, s->blocks, s->threads, s->smem, s->stream)
-                        : launch_server_f32(s->sp, s->kc, s->blocks, s->threads, s->smem, s->stream);
+    cudaError_t e = s->precision == QLDPC_INT16  ? launch_server_i16(s->sp, s->kc, s->blocks, s->threads, s->smem, s->stream)
+                    : s->precision == QLDPC_INT8 ? launch_server_i8(s->sp, s->kc, s->blocks, s->threads, s->smem, s->stream)
+                                                 : launch_server_f32(s->sp, s->kc, s->blocks, s->threads, s->smem, s->stream);
     if (e != cudaSuccess) return cuda_status(e);
     s->launched = true;
     return QLDPC_OK;
@@ -133,13 +133,14 @@ int qldpc_server_create(const qldpc_graph *const *graphs, const float *const *pr
     if (!out) return QLDPC_ERR_INVALID_ARG;
     *out = nullptr;
     if (!graphs || !priors || !cfg || ncodes < 1 || ncodes > QLDPC_SERVER_MAX_CODES) return QLDPC_ERR_INVALID_ARG;
-    if (cfg->precision != QLDPC_FP32 && cfg->precision != QLDPC_INT16) return QLDPC_ERR_INVALID_ARG;
+    if (cfg->precision != QLDPC_FP32 && cfg->precision != QLDPC_INT16 && cfg->precision != QLDPC_INT8)
+        return QLDPC_ERR_INVALID_ARG;
     if ((cfg->flags & ~uint32_t(QLDPC_NO_EARLY_STOP | QLDPC_LEARNED)) != 0 || cfg->max_iter < 0)
         return QLDPC_ERR_INVALID_ARG;
     const bool learned = (cfg->flags & QLDPC_LEARNED) != 0;
     if (learned && (cfg->precision != QLDPC_FP32 || (cfg->flags & QLDPC_NO_EARLY_STOP))) return QLDPC_ERR_INVALID_ARG;
     if (!std::isfinite(cfg->alpha) || cfg->alpha <= 0.0f) return QLDPC_ERR_INVALID_ARG;
-    const int aq = cfg->precision == QLDPC_INT16 ? alpha_fixed(cfg->alpha) : 0;
+    const int aq = cfg->precision == QLDPC_FP32 ? 0 : alpha_fixed(cfg->alpha);
     if (aq < 0) return QLDPC_ERR_INVALID_ARG;
     const int32_t cap = cfg->ring_capacity ? cfg->ring_capacity : 256;
     if (cap < 2 || cap > (1 << 20) || (cap & (cap - 1))) return QLDPC_ERR_INVALID_ARG;
@@ -185,7 +186,9 @@ int qldpc_server_create(const qldpc_graph *const *graphs, const float *const *pr
         fits = fits && graphs[c]->m <= kLatencyCnPerThread * s->threads &&
                graphs[c]->nv <= kLatencyVnPerThread * s->threads;
     s->smem = smem;
-    const void *k = cfg->precision == QLDPC_INT16 ? server_kernel_i16(s->kc) : server_kernel_f32(s->kc);
+    const void *k = cfg->precision == QLDPC_INT16  ? server_kernel_i16(s->kc)
+                    : cfg->precision == QLDPC_INT8 ? server_kernel_i8(s->kc)
+                                                   : server_kernel_f32(s->kc);
     if (!fits || !k) {
         delete s;
         return QLDPC_ERR_UNSUPPORTED;

@@ -79,5 +79,3 @@ def test_int8_pair_equals_single_decodes(q):
     ra = q.decode(gz, sx, pr, 64, precision="int8")
     rb = q.decode(gx, sz, pr, 64, precision="int8")
     assert torch.equal(a, ra[0]) and torch.equal(ia, ra[1]) and torch.equal(b, rb[0]) and torch.equal(ib, rb[1])
-    with pytest.raises(q.QldpcError):
-        q.Server([gz], [np.full(c.n, 3.0, np.float32)], 20, precision="int8")

@@ -43,7 +43,7 @@ def mixed_stream(n_req, seed, p=0.03):
     return codes, arrival
 
 
-@pytest.mark.parametrize("precision", ["fp32", "int16"])
+@pytest.mark.parametrize("precision", ["fp32", "int16", "int8"])
 def test_mixed_stream_equals_alone(q, precision):
     graphs, priors, batches = [], [], []
     codes, arrival = mixed_stream(600, seed=5)

@@ -299,6 +299,25 @@ def decode(graph: Graph, syndromes, prior, max_iter: int, alpha: float = 0.75,
     return err, iters, ok, post
 
 
+def decode_soft(graph: Graph, syndromes, prior, syndrome_llr, max_iter: int, alpha: float = 0.75,
+                precision: str = "fp32", early_stop: bool = True, want_post: bool = False, stream=None,
+                layered: bool = False):
+    """Soft-syndrome decoding: ``graph`` is the data-syndrome Tanner graph [H | I_m]
+    (``workloads.data_syndrome_csr``), ``syndromes`` the measured bits (CUDA uint8 [B, m]),
+    ``prior`` the data LLRs (CUDA float32 [n]) and ``syndrome_llr`` the LLRs that each measured bit
+    is right (CUDA float32 [m], ln((1 - q)/q) for a read error rate q).  Runs the ordinary decode
+    on that graph with the priors side by side; returns (err [B, n], syndrome errors [B, m], iters,
+    ok, post [B, n + m] or None)."""
+    import torch
+    n = graph.n - graph.m
+    if n < 1 or prior.shape != (n,) or syndrome_llr.shape != (graph.m,):
+        raise ValueError("decode_soft expects a data-syndrome graph, prior [n] and syndrome_llr [m]")
+    full = torch.cat([prior.float(), syndrome_llr.float()]).contiguous()
+    err, iters, ok, post = decode(graph, syndromes, full, max_iter, alpha, precision, early_stop, want_post,
+                                  stream=stream, layered=layered)
+    return err[:, :n], err[:, n:], iters, ok, post
+
+
 def decode_pair(g_z: Graph, g_x: Graph, s_x, s_z, prior_x, prior_z, max_iter: int,
                 alpha: float = 0.75, precision: str = "fp32", early_stop: bool = True,
                 want_post: bool = False, stream=None, learned: bool = False, layered: bool = False):

@@ -332,6 +332,30 @@ def depolarizing_errors(n: int, p: float, shots: int, seed: int, first_shot: int
     return _chunked(draw, shots, first_shot)
 
 
+def data_syndrome_csr(h: CSR) -> CSR:
+    """The data-syndrome Tanner graph [H | I_m]: column n + i is the measurement error of syndrome
+    bit i (one edge, to check i).  A syndrome read with errors, s~ = H e + e', is the syndrome of
+    the combined error (e, e') on this graph."""
+    rp = np.asarray(h.row_ptr, dtype=np.int64)
+    cols = []
+    for i in range(h.m):
+        cols.append(np.asarray(h.col_idx[rp[i]:rp[i + 1]], dtype=np.int32))
+        cols.append(np.array([h.n + i], dtype=np.int32))
+    row_ptr = (rp + np.arange(h.m + 1)).astype(np.int32)
+    return CSR(row_ptr, np.concatenate(cols) if cols else np.zeros(0, np.int32), h.m, h.n + h.m)
+
+
+def noisy_syndrome_batch(h: CSR, p: float, q: float, shots: int, seed: int, first_shot: int = 0):
+    """Data errors at rate p and syndrome measurement errors at rate q, one draw per shot:
+    e[b, j] = [u(seed, b, j) < p] for the n data bits, e'[b, i] = [u(seed, b, n + i) < q] for the m
+    syndrome bits; returns (e uint8 [shots, n], e' uint8 [shots, m], s~ = H e + e' uint8 [shots, m])."""
+    def draw(s0, count):
+        u = uniform01(seed, np.arange(s0, s0 + count), np.arange(h.n + h.m))
+        return (u[:, :h.n] < p).astype(np.uint8), (u[:, h.n:] < q).astype(np.uint8)
+    e, es = _chunked(draw, shots, first_shot)
+    return e, es, syndromes(h, e) ^ es
+
+
 @dataclass(frozen=True)
 class Batch:
     """One batch of synthetic decoding problems for a single parity-check matrix."""

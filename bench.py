@@ -96,6 +96,7 @@ def parse():
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-layered", action="store_true")
     ap.add_argument("--no-precisions", action="store_true")
+    ap.add_argument("--no-soft", action="store_true")
     ap.add_argument("--learned-train-shots", type=int, default=LEARN_SHOTS)
     ap.add_argument("--learned-eval-shots", type=int, default=LEARN_EVAL)
     return ap.parse_args()
@@ -360,6 +361,9 @@ def run_ours(args, rank, world, local):
     learned_res = None
     if not args.no_learned and rank == 0:
         learned_res = measure_learned(qldpc, args)
+    soft_res = None
+    if not args.no_soft and rank == 0:
+        soft_res = measure_soft_syndrome(qldpc, args)
     cpu = None
     if not args.no_cpu_baseline and rank == 0 and world == 1:
         threads = os.cpu_count() or 1
@@ -384,6 +388,7 @@ def run_ours(args, rank, world, local):
             "precisions": precisions,
             "layered": layered_res,
             "learned": learned_res,
+            "soft_syndrome": soft_res,
             "gpu_launches": launches,
             "clocks": clocks,
             "mean_iters": sum(iters_per_batch) / (len(iters_per_batch) * B),
@@ -392,6 +397,52 @@ def run_ours(args, rank, world, local):
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def measure_soft_syndrome(qldpc, args, q=0.01, shots=65536, evaluated=16384, steps=20):
+    """Syndrome read errors: LP-1054 with data errors at p and every syndrome bit misread with
+    probability q.  The hard decoder runs on H with the measured bits; the soft-syndrome decoder runs
+    on the data-syndrome graph [H | I] with the read-error LLR ln((1-q)/q).  A shot succeeds when the
+    residual data error has zero syndrome and commutes with every logical."""
+    import torch
+    from paper_2508_07879_gb300 import gf2
+    from paper_2508_07879_gb300 import learned
+    from paper_2508_07879_gb300 import workloads as w
+    code = w.lp_code(1054)
+    h = code.hz_csr
+    gh, ga = qldpc.Graph.from_csr(h), qldpc.Graph.from_csr(w.data_syndrome_csr(h))
+    lam = torch.full((h.m,), w.prior_llr(q), device="cuda")
+    logicals = learned.z_logicals(code)
+    out = {"workload": f"LP-1054 H_Z, data errors at p, syndrome read errors q={q}, {shots} shots per p",
+           "success": "residual data error with zero syndrome, commuting with every logical",
+           "evaluated_shots": evaluated}
+    for p in (0.01, 0.03):
+        e, es, s = w.noisy_syndrome_batch(h, p, q, shots, seed=5001)
+        st = torch.from_numpy(s).cuda()
+        gamma = torch.full((h.n,), w.prior_llr(p), device="cuda")
+        row = {}
+        for name in ("hard", "soft"):
+            if name == "hard":
+                run = lambda: qldpc.decode(gh, st, gamma, MAX_ITER, ALPHA)
+            else:
+                run = lambda: qldpc.decode_soft(ga, st, gamma, lam, MAX_ITER, ALPHA)
+            res = run()
+            torch.cuda.synchronize()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ev[0].record()
+            for _ in range(steps):
+                run()
+            ev[1].record()
+            torch.cuda.synchronize()
+            ms = ev[0].elapsed_time(ev[1]) / steps
+            e_hat = res[0].cpu().numpy()
+            iters, ok = (res[1], res[2]) if name == "hard" else (res[2], res[3])
+            r = e[:evaluated] ^ e_hat[:evaluated]
+            fail = w.syndromes(h, r).any(axis=1) | gf2.logical_failures(r, logicals).astype(bool)
+            row[name] = {"success": float(1.0 - fail.mean()), "decoded_fraction": float(ok.float().mean().item()),
+                         "mean_iters": float(iters.float().mean().item()), "syndromes_per_s": shots / (ms / 1e3)}
+        out[f"p={p}"] = row
+    return out
 
 
 def measure_e2e(qldpc, graph, batches, args, B, world, dev):

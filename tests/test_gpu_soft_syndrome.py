@@ -46,7 +46,7 @@ def test_lp1054_noisy_syndromes_match_oracle(q, precision, layered):
     np.testing.assert_array_equal(ok.cpu().numpy(), ref["ok"])
     np.testing.assert_array_equal(post.cpu().numpy().astype(np.float64) * SCALE[precision],
                                   ref["post"].astype(np.float64))
-    assert ref["ok"].mean() > 0.8 and esd.cpu().numpy().any()
+    assert 0.25 < ref["ok"].mean() < 0.6 and esd.cpu().numpy().any()   # the oracle: 36 % of these shots decode
 
 
 def test_reliable_bits_reproduce_the_hard_decode(q):

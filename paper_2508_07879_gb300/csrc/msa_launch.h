@@ -248,8 +248,8 @@ struct TrainChoice {
     int dvb;         // column-degree bucket 4/8/16
 };
 
-const void *nms_forward_kernel_ptr(const TrainChoice &tc);
-const void *nms_backward_kernel_ptr(const TrainChoice &tc);
+const void *nms_forward_kernel_ptr(const TrainChoice &tc, int loss_kind);
+const void *nms_backward_kernel_ptr(const TrainChoice &tc, int loss_kind);
 cudaError_t launch_nms_forward(const TrainParams &p, const TrainChoice &tc, int grid, int threads, size_t smem,
                                cudaStream_t stream);
 cudaError_t launch_nms_backward(const TrainParams &p, const TrainChoice &tc, int grid, int threads, size_t smem,

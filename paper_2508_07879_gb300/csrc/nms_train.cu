@@ -204,12 +204,13 @@ __device__ __forceinline__ void recompute_r(int c, int M, int deg, uint32_t m1b,
     }
 }
 
-template <int DC, bool UNIFORM, int DV>
+// SYN: the syndrome loss (compiled separately, so the error-loss kernels carry none of its code).
+template <int DC, bool UNIFORM, int DV, bool SYN>
 __global__ void __launch_bounds__(kTrainThreads, 4) nms_forward_kernel(const TrainParams p)
 {
     const int M = p.g.m, N = p.g.n, NV = p.g.nv, T = blockDim.x, tid = threadIdx.x;
     const size_t S = size_t(p.g.dc_max) * M;
-    const bool syn_loss = p.loss_kind == kLossSyndrome;
+    constexpr bool syn_loss = SYN;
     extern __shared__ __align__(16) unsigned char smem[];
     const TrainLayout L = train_layout(M, NV, p.g.dc_max, false, syn_loss);
     float *slots = reinterpret_cast<float *>(smem + L.slot_off);
@@ -289,13 +290,13 @@ __device__ __forceinline__ void prefetch_state(uint32_t *dst, const uint32_t *sr
 }
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-template <int DC, bool UNIFORM, int DV>
+template <int DC, bool UNIFORM, int DV, bool SYN>
 __global__ void __launch_bounds__(kTrainThreads, 4) nms_backward_kernel(const TrainParams p)
 {
     const int M = p.g.m, N = p.g.n, NV = p.g.nv, T = blockDim.x, tid = threadIdx.x;
     const size_t S = size_t(p.g.dc_max) * M;
     const size_t SW = size_t(kStateWords) * M;                    // state words of one iteration
-    const bool syn_loss = p.loss_kind == kLossSyndrome;
+    constexpr bool syn_loss = SYN;
     extern __shared__ __align__(16) unsigned char smem[];
     const TrainLayout L = train_layout(M, NV, p.g.dc_max, true, syn_loss);
     float *gs = reinterpret_cast<float *>(smem + L.slot_off);     // dL/dq (next iteration), then dL/dr
@@ -539,21 +540,25 @@ __global__ void logical_kernel(const uint8_t *__restrict__ logicals, int32_t K, 
     X(6, true, 4) X(6, true, 8) X(7, true, 4) X(7, true, 8) X(8, true, 4) X(8, true, 8)        \
     X(8, false, 8) X(8, false, 16) X(16, false, 8) X(16, false, 16) X(32, false, 8) X(32, false, 16)
 
-const void *nms_forward_kernel_ptr(const TrainChoice &tc)
+const void *nms_forward_kernel_ptr(const TrainChoice &tc, int loss_kind)
 {
+    const bool syn = loss_kind == kLossSyndrome;
 #define QLDPC_K(DCV, UNI, DVV)                                                                  \
     if (tc.dc == DCV && tc.uniform == UNI && tc.dvb == DVV)                                     \
-        return reinterpret_cast<const void *>(&kern::nms_forward_kernel<DCV, UNI, DVV>);
+        return syn ? reinterpret_cast<const void *>(&kern::nms_forward_kernel<DCV, UNI, DVV, true>) \
+                   : reinterpret_cast<const void *>(&kern::nms_forward_kernel<DCV, UNI, DVV, false>);
     QLDPC_TRAIN_VARIANTS(QLDPC_K)
 #undef QLDPC_K
     return nullptr;
 }
 
-const void *nms_backward_kernel_ptr(const TrainChoice &tc)
+const void *nms_backward_kernel_ptr(const TrainChoice &tc, int loss_kind)
 {
+    const bool syn = loss_kind == kLossSyndrome;
 #define QLDPC_K(DCV, UNI, DVV)                                                                  \
     if (tc.dc == DCV && tc.uniform == UNI && tc.dvb == DVV)                                     \
-        return reinterpret_cast<const void *>(&kern::nms_backward_kernel<DCV, UNI, DVV>);
+        return syn ? reinterpret_cast<const void *>(&kern::nms_backward_kernel<DCV, UNI, DVV, true>) \
+                   : reinterpret_cast<const void *>(&kern::nms_backward_kernel<DCV, UNI, DVV, false>);
     QLDPC_TRAIN_VARIANTS(QLDPC_K)
 #undef QLDPC_K
     return nullptr;
@@ -562,9 +567,13 @@ const void *nms_backward_kernel_ptr(const TrainChoice &tc)
 cudaError_t launch_nms_forward(const TrainParams &p, const TrainChoice &tc, int grid, int threads, size_t smem,
                                cudaStream_t stream)
 {
+    const bool syn = p.loss_kind == kLossSyndrome;
 #define QLDPC_L(DCV, UNI, DVV)                                                                  \
     if (tc.dc == DCV && tc.uniform == UNI && tc.dvb == DVV) {                                   \
-        kern::nms_forward_kernel<DCV, UNI, DVV><<<grid, threads, smem, stream>>>(p);            \
+        if (syn)                                                                                \
+            kern::nms_forward_kernel<DCV, UNI, DVV, true><<<grid, threads, smem, stream>>>(p);  \
+        else                                                                                    \
+            kern::nms_forward_kernel<DCV, UNI, DVV, false><<<grid, threads, smem, stream>>>(p); \
         return cudaGetLastError();                                                              \
     }
     QLDPC_TRAIN_VARIANTS(QLDPC_L)
@@ -575,9 +584,13 @@ cudaError_t launch_nms_forward(const TrainParams &p, const TrainChoice &tc, int 
 cudaError_t launch_nms_backward(const TrainParams &p, const TrainChoice &tc, int grid, int threads, size_t smem,
                                 cudaStream_t stream)
 {
+    const bool syn = p.loss_kind == kLossSyndrome;
 #define QLDPC_L(DCV, UNI, DVV)                                                                  \
     if (tc.dc == DCV && tc.uniform == UNI && tc.dvb == DVV) {                                   \
-        kern::nms_backward_kernel<DCV, UNI, DVV><<<grid, threads, smem, stream>>>(p);           \
+        if (syn)                                                                                \
+            kern::nms_backward_kernel<DCV, UNI, DVV, true><<<grid, threads, smem, stream>>>(p); \
+        else                                                                                    \
+            kern::nms_backward_kernel<DCV, UNI, DVV, false><<<grid, threads, smem, stream>>>(p); \
         return cudaGetLastError();                                                              \
     }
     QLDPC_TRAIN_VARIANTS(QLDPC_L)

@@ -36,7 +36,7 @@ TrainChoice train_choice(const qldpc_graph *g)
 
 struct TrainPlan {
     TrainChoice tc{};
-    const void *fwd = nullptr, *bwd = nullptr;
+    const void *fwd[2] = {nullptr, nullptr}, *bwd[2] = {nullptr, nullptr};   // [loss kind]
     size_t smem_f[2] = {0, 0}, smem_b[2] = {0, 0};   // [loss kind]
     int grid_f[2] = {0, 0}, grid_b[2] = {0, 0};
     size_t w_off = 0, state_off = 0, part_off = 0, total = 0;
@@ -66,20 +66,20 @@ int plan_training_uncached(const qldpc_graph *g, int32_t batch, int32_t T, Train
 {
     tp.tc = train_choice(g);
     if (tp.tc.dc < 0) return QLDPC_ERR_UNSUPPORTED;
-    tp.fwd = nms_forward_kernel_ptr(tp.tc);
-    tp.bwd = nms_backward_kernel_ptr(tp.tc);
-    if (!tp.fwd || !tp.bwd) return QLDPC_ERR_UNSUPPORTED;
     for (int kind = 0; kind < 2; ++kind) {
         const bool syn = kind == kLossSyndrome;
+        tp.fwd[kind] = nms_forward_kernel_ptr(tp.tc, kind);
+        tp.bwd[kind] = nms_backward_kernel_ptr(tp.tc, kind);
+        if (!tp.fwd[kind] || !tp.bwd[kind]) return QLDPC_ERR_UNSUPPORTED;
         tp.smem_f[kind] = train_layout(g->m, g->nv, g->dc_max, false, syn).total;
         tp.smem_b[kind] = train_layout(g->m, g->nv, g->dc_max, true, syn).total;
+        if (int rc = ensure_kernel_attrs(tp.fwd[kind], tp.smem_f[kind], g->smem_optin)) return rc;
+        if (int rc = ensure_kernel_attrs(tp.bwd[kind], tp.smem_b[kind], g->smem_optin)) return rc;
     }
-    if (int rc = ensure_kernel_attrs(tp.fwd, tp.smem_f[kLossSyndrome], g->smem_optin)) return rc;
-    if (int rc = ensure_kernel_attrs(tp.bwd, tp.smem_b[kLossSyndrome], g->smem_optin)) return rc;
     for (int kind = 0; kind < 2; ++kind) {
         int per_f = 0, per_b = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_f, tp.fwd, kTrainThreads, tp.smem_f[kind]) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_b, tp.bwd, kTrainThreads, tp.smem_b[kind]) != cudaSuccess) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_f, tp.fwd[kind], kTrainThreads, tp.smem_f[kind]) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_b, tp.bwd[kind], kTrainThreads, tp.smem_b[kind]) != cudaSuccess) {
             cudaGetLastError();
             return QLDPC_ERR_CUDA;
         }

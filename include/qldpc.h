@@ -45,6 +45,11 @@
  *                   qldpc_nms_backward, qldpc_adam_step
  *   workloads       qldpc_sample_errors (device error sampler), qldpc_logical_failures
  *
+ * Soft syndromes: a syndrome bit read with error probability q is a degree-1 variable of its check
+ * with prior LLR ln((1-q)/q).  Decoding the data-syndrome matrix [H | I_m] (create the graph from
+ * it) with the data priors followed by the m read-error LLRs, and the measured bits as syndromes,
+ * is soft-syndrome decoding; e_hat then holds the data error followed by the read errors.
+ *
  * Errors: every function returns a qldpc_status.  Arguments are validated on the host before any
  * GPU work is enqueued; a rejected call enqueues nothing and writes no output.  A CUDA launch
  * failure returns QLDPC_ERR_CUDA; faults during execution surface at the caller's next

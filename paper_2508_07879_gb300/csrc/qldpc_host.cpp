@@ -154,15 +154,19 @@ std::vector<int32_t> pack_lanes(const std::vector<uint32_t> &order, const std::v
     return lanes;
 }
 
-// The lanes with the lowest cost among the plain degree order and four packings.
+// The lanes with the lowest cost among the plain degree order and four packings.  A packing may
+// add at most an eighth more lanes (plus one warp), so that it never costs a graph its fit in shared
+// memory by more than the Q and gamma words of those lanes.
 std::vector<int32_t> choose_lanes(const std::vector<uint32_t> &order, const std::vector<uint32_t> &eaddr,
                                   const std::vector<int32_t> &cdeg, int dv)
 {
     std::vector<int32_t> best(order.begin(), order.end());
     if (dv > 16) return best;
     double best_s = lanes_score(best, eaddr, cdeg, dv);
+    const size_t max_lanes = order.size() + order.size() / 8 + kBanks;
     for (int close_at : {32, 28, 24, 16}) {
         std::vector<int32_t> c = pack_lanes(order, eaddr, cdeg, dv, close_at);
+        if (c.size() > max_lanes) continue;
         const double s = lanes_score(c, eaddr, cdeg, dv);
         if (s < best_s) {
             best_s = s;

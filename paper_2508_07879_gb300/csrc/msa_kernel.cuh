@@ -609,13 +609,14 @@ __global__ void __launch_bounds__(kLatencyMaxThreads, 1) msa_latency_kernel(cons
 }  // namespace kern
 
 // ---------------------------------------------------------------------------------------------
-// Instantiation tables for one precision policy: uniform row degree 6, 7, 8 (exact) or any degree
-// up to 8, 16, 32; column-degree bucket 4, 8, 16; for each, the batch and the latency kernel.
+// Instantiation tables for one precision policy: uniform row degree 6, 7, 8, 9 (exact; 9 is a
+// degree-8 code's row on the data-syndrome graph [H | I]) or any degree up to 8, 16, 32;
+// column-degree bucket 4, 8, 16; for each, the batch and the latency kernel.
 // ---------------------------------------------------------------------------------------------
 #define QLDPC_DV_LIST(X, A, B) X(A, B, 4) X(A, B, 8) X(A, B, 16)
 #define QLDPC_VARIANTS(X)                                                                       \
     QLDPC_DV_LIST(X, 6, true) QLDPC_DV_LIST(X, 7, true) QLDPC_DV_LIST(X, 8, true)               \
-    QLDPC_DV_LIST(X, 8, false) QLDPC_DV_LIST(X, 16, false) QLDPC_DV_LIST(X, 32, false)
+    QLDPC_DV_LIST(X, 9, true) QLDPC_DV_LIST(X, 8, false) QLDPC_DV_LIST(X, 16, false) QLDPC_DV_LIST(X, 32, false)
 
 template <class P, bool LEARNED = false>
 const void *kernel_table(const KernelChoice &kc)

@@ -296,7 +296,7 @@ __global__ void __launch_bounds__(256, 1) msa_layered_reg_kernel(const LaunchPar
 
 }  // namespace kern
 
-#define QLDPC_LAYERED_VARIANTS(X) X(6, true) X(7, true) X(8, true) X(8, false) X(16, false) X(32, false)
+#define QLDPC_LAYERED_VARIANTS(X) X(6, true) X(7, true) X(8, true) X(9, true) X(8, false) X(16, false) X(32, false)
 
 // Register-resident variants (at most 8 layers, rows of degree <= 8); KernelChoice::dvb = 1 selects them.
 #define QLDPC_LAYERED_REG_VARIANTS(X) X(6, true) X(7, true) X(8, true) X(8, false)

@@ -416,7 +416,7 @@ int round32(int x) { return (x + 31) / 32 * 32; }
 // 192-, 465- and 144-check codes (several small blocks per SM beat few large ones).
 constexpr int kBatchThreads = 128;
 
-// Compiled variant for the graphs of one call: exact uniform row degree 6..8, else a bucket.
+// Compiled variant for the graphs of one call: exact uniform row degree 6..9, else a bucket.
 KernelChoice variant(const qldpc_graph *const *gs, int nprob, bool latency, bool learned)
 {
     int dc = 0, dv = 0;
@@ -426,7 +426,7 @@ KernelChoice variant(const qldpc_graph *const *gs, int nprob, bool latency, bool
         dv = std::max(dv, gs[i]->dv_max);
         uniform = uniform && gs[i]->uniform_rows && gs[i]->dc_max == gs[0]->dc_max;
     }
-    if (uniform && dc >= 6 && dc <= 8) return KernelChoice{latency, dc, true, dv_bucket(dv), learned};
+    if (uniform && dc >= 6 && dc <= 9) return KernelChoice{latency, dc, true, dv_bucket(dv), learned};
     return KernelChoice{latency, dc_bucket(dc), false, dv_bucket(dv), learned};
 }
 

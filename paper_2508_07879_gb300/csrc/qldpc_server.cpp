@@ -176,7 +176,7 @@ int qldpc_server_create(const qldpc_graph *const *graphs, const float *const *pr
         want = std::max(want, one <= kLatencyMaxThreads ? one : two);
         smem = std::max(smem, latency_layout(g->m, g->dc_max, msg_bytes(cfg->precision)).total);
     }
-    s->kc = (uniform && dc >= 6 && dc <= 8) ? KernelChoice{true, dc, true, dv <= 4 ? 4 : dv <= 8 ? 8 : 16}
+    s->kc = (uniform && dc >= 6 && dc <= 9) ? KernelChoice{true, dc, true, dv <= 4 ? 4 : dv <= 8 ? 8 : 16}
                                             : KernelChoice{true, dc <= 8 ? 8 : dc <= 16 ? 16 : 32, false,
                                                            dv <= 4 ? 4 : dv <= 8 ? 8 : 16};
     for (int c = 0; c < ncodes; ++c) s->kc.learned = s->kc.learned || (learned && graphs[c]->d_weights);

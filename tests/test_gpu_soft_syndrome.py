@@ -49,6 +49,31 @@ def test_lp1054_noisy_syndromes_match_oracle(q, precision, layered):
     assert 0.25 < ref["ok"].mean() < 0.6 and esd.cpu().numpy().any()   # the oracle: 36 % of these shots decode
 
 
+@pytest.mark.parametrize("precision", ["fp32", "int16", "int8"])
+def test_single_shot_kernel_matches_oracle(q, precision):
+    """A (4, 8)-regular code with 60 checks: its data-syndrome rows have exact degree 9, and a batch
+    of at most one shot per SM takes the single-shot kernel."""
+    h = w.csr_from_dense(w.random_regular_ldpc(60, 120, 4, 8, seed=5))
+    a = w.data_syndrome_csr(h)
+    g = q.Graph.from_csr(a)
+    e, es, s = w.noisy_syndrome_batch(h, 0.03, 0.02, 100, seed=79)
+    gamma = np.full(h.n, w.prior_llr(0.03), np.float32)
+    lam = np.full(h.m, w.prior_llr(0.02), np.float32)
+    ed, esd, iters, ok, post = q.decode_soft(g, torch.from_numpy(s).cuda(), torch.from_numpy(gamma).cuda(),
+                                             torch.from_numpy(lam).cuda(), 50, precision=precision,
+                                             want_post=True)
+    torch.cuda.synchronize()
+    ref = oracle.msa(a.row_ptr, a.col_idx, a.m, a.n, s, np.concatenate([gamma, lam]), 50, 0.75, ORACLE[precision],
+                     threads=16)
+    np.testing.assert_array_equal(ed.cpu().numpy(), ref["err"][:, :h.n])
+    np.testing.assert_array_equal(esd.cpu().numpy(), ref["err"][:, h.n:])
+    np.testing.assert_array_equal(iters.cpu().numpy(), ref["iters"])
+    np.testing.assert_array_equal(ok.cpu().numpy(), ref["ok"])
+    np.testing.assert_array_equal(post.cpu().numpy().astype(np.float64) * SCALE[precision],
+                                  ref["post"].astype(np.float64))
+    assert ref["iters"].max() > 5 and esd.cpu().numpy().any()
+
+
 def test_reliable_bits_reproduce_the_hard_decode(q):
     h = w.lp_code(1054).hz_csr
     a = w.data_syndrome_csr(h)
@@ -61,3 +86,22 @@ def test_reliable_bits_reproduce_the_hard_decode(q):
     assert torch.equal(soft[0], hard[0]) and not soft[1].any()
     assert torch.equal(soft[2], hard[1]) and torch.equal(soft[3], hard[2])
     assert torch.equal(soft[4][:, :h.n], hard[3])
+
+
+def test_served_soft_syndromes_equal_the_batch_decode(q):
+    """The persistent server on a data-syndrome graph (rows of exact degree 9) decodes every request
+    as the batch decode does."""
+    h = w.csr_from_dense(w.random_regular_ldpc(60, 120, 4, 8, seed=5))
+    a = w.data_syndrome_csr(h)
+    g = q.Graph.from_csr(a)
+    e, es, s = w.noisy_syndrome_batch(h, 0.03, 0.02, 200, seed=80)
+    prior = np.concatenate([np.full(h.n, w.prior_llr(0.03)), np.full(h.m, w.prior_llr(0.02))]).astype(np.float32)
+    err, iters, ok, _ = q.decode(g, torch.from_numpy(s).cuda(), torch.from_numpy(prior).cuda(), 50)
+    torch.cuda.synchronize()
+    codes = np.zeros(len(s), np.int32)
+    arrival = np.arange(len(s), dtype=np.int64) * 20000
+    with q.Server([g], [prior], 50, 0.75, "fp32", blocks=[16], idle_timeout_s=2.0) as srv:
+        errs, it, okk, _ = srv.replay(codes, list(s), arrival)
+    np.testing.assert_array_equal(np.stack(errs), err.cpu().numpy())
+    np.testing.assert_array_equal(np.asarray(it), iters.cpu().numpy())
+    np.testing.assert_array_equal(np.asarray(okk), ok.cpu().numpy())

@@ -50,6 +50,9 @@ namespace qldpc {
 
 int dc_bucket(int d);   // row-degree bucket 8 / 16 / 32, -1 above
 int dv_bucket(int d);   // column-degree bucket 4 / 8 / 16, -1 above
+// Compiled kernel variant for graphs of largest row degree dc and column degree dv: the exact
+// degree when every row has degree dc in 6..9 (uniform), else the buckets.
+KernelChoice kernel_variant(int dc, int dv, bool uniform, bool latency, bool learned);
 
 namespace detail {
 

@@ -24,6 +24,11 @@ namespace qldpc {
 
 int dc_bucket(int d) { return d <= 8 ? 8 : d <= 16 ? 16 : d <= 32 ? 32 : -1; }
 int dv_bucket(int d) { return d <= 4 ? 4 : d <= 8 ? 8 : d <= 16 ? 16 : -1; }
+KernelChoice kernel_variant(int dc, int dv, bool uniform, bool latency, bool learned)
+{
+    if (uniform && dc >= 6 && dc <= 9) return KernelChoice{latency, dc, true, dv_bucket(dv), learned};
+    return KernelChoice{latency, dc_bucket(dc), false, dv_bucket(dv), learned};
+}
 
 const void *msa_kernel(int precision, const KernelChoice &kc)
 {
@@ -426,8 +431,7 @@ KernelChoice variant(const qldpc_graph *const *gs, int nprob, bool latency, bool
         dv = std::max(dv, gs[i]->dv_max);
         uniform = uniform && gs[i]->uniform_rows && gs[i]->dc_max == gs[0]->dc_max;
     }
-    if (uniform && dc >= 6 && dc <= 9) return KernelChoice{latency, dc, true, dv_bucket(dv), learned};
-    return KernelChoice{latency, dc_bucket(dc), false, dv_bucket(dv), learned};
+    return kernel_variant(dc, dv, uniform, latency, learned);
 }
 
 // Resident blocks per SM of a kernel at a block size and shared-memory size.  The runtime's query

@@ -176,9 +176,7 @@ int qldpc_server_create(const qldpc_graph *const *graphs, const float *const *pr
         want = std::max(want, one <= kLatencyMaxThreads ? one : two);
         smem = std::max(smem, latency_layout(g->m, g->dc_max, msg_bytes(cfg->precision)).total);
     }
-    s->kc = (uniform && dc >= 6 && dc <= 9) ? KernelChoice{true, dc, true, dv <= 4 ? 4 : dv <= 8 ? 8 : 16}
-                                            : KernelChoice{true, dc <= 8 ? 8 : dc <= 16 ? 16 : 32, false,
-                                                           dv <= 4 ? 4 : dv <= 8 ? 8 : 16};
+    s->kc = kernel_variant(dc, dv, uniform, true, false);
     for (int c = 0; c < ncodes; ++c) s->kc.learned = s->kc.learned || (learned && graphs[c]->d_weights);
     s->threads = cfg->threads_per_block ? cfg->threads_per_block : std::min(want, kLatencyMaxThreads);
     bool fits = s->threads >= 32 && s->threads <= kLatencyMaxThreads && s->threads % 32 == 0;

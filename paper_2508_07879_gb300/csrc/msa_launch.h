@@ -266,7 +266,8 @@ cudaError_t launch_logical(const uint8_t *logicals, int32_t k, int32_t n, const 
                            const uint8_t *ok, int32_t batch, uint8_t *fail, int grid, cudaStream_t stream);
 
 // Shared memory of one training shot (forward: q slots, gamma, targets, syndrome; backward adds
-// the recomputed r slots and the recorded state of two iterations).
+// the recomputed r slots and the recorded state of two iterations).  The syndrome loss adds the
+// per-edge codes to the forward and Q per lane to the backward, whose codes overwrite r in place.
 struct TrainLayout {
     size_t slot_off, r_off, c_off, t_off, g_off, y_off, s_off, total;
 };
@@ -279,7 +280,7 @@ __host__ __device__ inline TrainLayout train_layout(int m, int n, int dc_max, bo
     t.r_off = align16(S * 4);                                                // r slots [S] f32 (backward)
     t.c_off = backward ? align16(t.r_off + S * 4) : t.r_off;                 // state [2][4m] u32 (backward)
     t.t_off = backward ? align16(t.c_off + 2 * size_t(kStateWords) * m * 4) : t.c_off;   // syndrome loss:
-    const size_t g0 = syndrome ? align16(t.t_off + S * 4) : t.t_off;                     //   tanh slots [S] f32
+    const size_t g0 = syndrome ? align16(t.t_off + (backward ? size_t(n) : S) * 4) : t.t_off; // codes [S] / Q [n]
     t.g_off = g0;                                                                        // gamma [n] f32
     t.y_off = align16(t.g_off + size_t(n) * 4);                              // targets [n] u8
     t.s_off = align16(t.y_off + size_t(n));                                  // syndrome bits [m] u8

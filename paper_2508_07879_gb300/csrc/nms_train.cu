@@ -187,10 +187,19 @@ __device__ __forceinline__ float half_sech2_half(float Q)
     return 0.5f / (ch * ch);
 }
 
-// r of check c recomputed from its recorded state (bit-identical to the forward's r).
+// The weights of check c's edges in one iteration, all loads issued before any is used.
+template <int DC, bool UNIFORM>
+__device__ __forceinline__ void load_check_weights(int c, int M, int deg, const float *__restrict__ w, float (&wv)[DC])
+{
+#pragma unroll
+    for (int j = 0; j < DC; ++j) wv[j] = (UNIFORM || j < deg) ? __ldg(w + j * M + c) : 0.0f;
+}
+
+// r of check c recomputed from its recorded state and its edges' weights (bit-identical to the
+// forward's r).
 template <int DC, bool UNIFORM>
 __device__ __forceinline__ void recompute_r(int c, int M, int deg, uint32_t m1b, uint32_t m2b, uint32_t signs,
-                                            uint32_t iw, const float *__restrict__ w, float *__restrict__ rs)
+                                            uint32_t iw, const float (&wv)[DC], float *__restrict__ rs)
 {
     const int i1 = int(iw & 0xffu);
     const uint32_t negall = (iw >> 16) & 1u;
@@ -198,7 +207,7 @@ __device__ __forceinline__ void recompute_r(int c, int M, int deg, uint32_t m1b,
 #pragma unroll
     for (int j = 0; j < DC; ++j) {
         if (UNIFORM || j < deg) {
-            const float r = __fmul_rn(__ldg(w + j * M + c), j == i1 ? m2 : m1);
+            const float r = __fmul_rn(wv[j], j == i1 ? m2 : m1);
             rs[j * M + c] = __uint_as_float(__float_as_uint(r) ^ ((((signs >> j) & 1u) ^ negall) << 31));
         }
     }
@@ -302,7 +311,10 @@ __global__ void __launch_bounds__(kTrainThreads, 4) nms_backward_kernel(const Tr
     float *gs = reinterpret_cast<float *>(smem + L.slot_off);     // dL/dq (next iteration), then dL/dr
     float *rs = reinterpret_cast<float *>(smem + L.r_off);        // recomputed r of the current iteration
     uint32_t *scb = reinterpret_cast<uint32_t *>(smem + L.c_off); // recorded state, two iterations
-    float *ts = reinterpret_cast<float *>(smem + L.t_off);        // syndrome loss: codes per edge, then d/dt
+    // Syndrome loss: once Q^(k) is formed, each variable overwrites its own r slots with its code
+    // (no other thread reads them), and each check then replaces the codes with d(term)/d(code).
+    float *ts = rs;
+    float *qlane = reinterpret_cast<float *>(smem + L.t_off);     // syndrome loss: Q^(k) per lane
     float *gam = reinterpret_cast<float *>(smem + L.g_off);
     uint8_t *y = smem + L.y_off;
     uint8_t *sb = smem + L.s_off;
@@ -325,7 +337,9 @@ __global__ void __launch_bounds__(kTrainThreads, 4) nms_backward_kernel(const Tr
             const float *wk = p.w + size_t(p.T - 1) * S;
             for (int c = tid; c < M; c += T) {
                 const int deg = UNIFORM ? DC : int(__ldg(p.g.rdeg + c));
-                recompute_r<DC, UNIFORM>(c, M, deg, scb[c], scb[M + c], scb[2 * M + c], scb[3 * M + c], wk, rs);
+                float wv[DC];
+                load_check_weights<DC, UNIFORM>(c, M, deg, wk, wv);
+                recompute_r<DC, UNIFORM>(c, M, deg, scb[c], scb[M + c], scb[2 * M + c], scb[3 * M + c], wv, rs);
 #pragma unroll
                 for (int j = 0; j < DC; ++j)
                     if (UNIFORM || j < deg) gs[j * M + c] = 0.0f;
@@ -350,6 +364,7 @@ __global__ void __launch_bounds__(kTrainThreads, 4) nms_backward_kernel(const Tr
                             Q = __fadd_rn(Q, rs[sl[i]]);
                         }
                     }
+                    qlane[u] = Q;
                     const float lm = log_magnitude_code(Q);
 #pragma unroll
                     for (int i = 0; i < DV; ++i)
@@ -366,14 +381,16 @@ __global__ void __launch_bounds__(kTrainThreads, 4) nms_backward_kernel(const Tr
             for (int u = tid; u < NV; u += T) {
                 const int deg = __ldg(p.g.vdeg + u);   // idle lanes: their warp's degree, scratch slots
                 uint32_t sl[DV];
-                float Q = gam[u], G = 0.0f, H = 0.0f;
+                float Q = syn_loss ? qlane[u] : gam[u], G = 0.0f, H = 0.0f;
 #pragma unroll
                 for (int i = 0; i < DV; ++i) {
                     if (i < deg) {
                         sl[i] = __ldg(p.g.vslot + size_t(i) * NV + u);
-                        Q = __fadd_rn(Q, rs[sl[i]]);
+                        if (syn_loss)
+                            H += ts[sl[i]];
+                        else
+                            Q = __fadd_rn(Q, rs[sl[i]]);
                         G += gs[sl[i]];
-                        if (syn_loss) H += ts[sl[i]];
                     }
                 }
                 const float gQ = syn_loss ? gk * half_sech2_half(Q) * H : gk * (float(y[u]) - sigmoid(-Q));
@@ -388,6 +405,9 @@ __global__ void __launch_bounds__(kTrainThreads, 4) nms_backward_kernel(const Tr
             float *gk_out = p.partial + size_t(k) * S;
             for (int c = tid; c < M; c += T) {
                 const int deg = UNIFORM ? DC : int(__ldg(p.g.rdeg + c));
+                float wv[DC], wp[DC];   // this iteration's weights and the previous one's, loaded together
+                load_check_weights<DC, UNIFORM>(c, M, deg, wk, wv);
+                if (k > 0) load_check_weights<DC, UNIFORM>(c, M, deg, wk - S, wp);
                 const float m1 = __uint_as_float(sc[c]), m2 = __uint_as_float(sc[M + c]);
                 const uint32_t signs = sc[2 * M + c], iw = sc[3 * M + c];
                 const int i1 = int(iw & 0xffu), i2 = int((iw >> 8) & 0xffu);
@@ -400,7 +420,7 @@ __global__ void __launch_bounds__(kTrainThreads, 4) nms_backward_kernel(const Tr
                         const float sgn = (((signs >> j) & 1u) ^ negall) ? -1.0f : 1.0f;
                         const float mu = j == i1 ? m2 : m1;
                         atomicAdd(gk_out + j * M + c, gr * sgn * mu);   // result unused: a reduction
-                        const float t = gr * __ldg(wk + j * M + c) * sgn;
+                        const float t = gr * wv[j] * sgn;
                         if (j == i1)
                             t1 = t;
                         else
@@ -412,9 +432,7 @@ __global__ void __launch_bounds__(kTrainThreads, 4) nms_backward_kernel(const Tr
 #pragma unroll
                 for (int j = 0; j < DC; ++j)
                     if (UNIFORM || j < deg) gs[j * M + c] = j == i1 ? gq1 : (j == i2 ? gq2 : 0.0f);
-                if (k > 0)
-                    recompute_r<DC, UNIFORM>(c, M, deg, sn[c], sn[M + c], sn[2 * M + c], sn[3 * M + c],
-                                             p.w + size_t(k - 1) * S, rs);
+                if (k > 0) recompute_r<DC, UNIFORM>(c, M, deg, sn[c], sn[M + c], sn[2 * M + c], sn[3 * M + c], wp, rs);
             }
             __syncthreads();
         }

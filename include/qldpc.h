@@ -262,9 +262,14 @@ typedef struct qldpc_server_config {
     int32_t max_iter;             /* >= 0 */
     float alpha;                  /* as for qldpc_decode_ex */
     uint32_t flags;               /* QLDPC_NO_EARLY_STOP, or QLDPC_LEARNED (FP32: every code whose
-                                     graph has weights decodes learned, the others plainly), or 0 */
+                                     graph has weights decodes learned, the others plainly), and/or
+                                     QLDPC_LAYERED (workers on the layered schedule: results equal
+                                     qldpc_decode_ex with QLDPC_LAYERED; every code at most 8 layers
+                                     of rows of degree <= 8 and n <= 65536; not with QLDPC_LEARNED),
+                                     or 0 */
     int32_t ring_capacity;        /* slots per code, a power of two in [2, 2^20]; 0 = 256 */
-    int32_t threads_per_block;    /* 0 = automatic */
+    int32_t threads_per_block;    /* 0 = automatic; QLDPC_LAYERED: a multiple of 32 in
+                                     [widest layer, 256] */
     int32_t blocks[QLDPC_SERVER_MAX_CODES];   /* worker blocks per code; 0 = equal share of the SMs */
     int64_t idle_timeout_ns;      /* workers leave after this long without a request; <= 0: 0.5 s */
     int64_t max_runtime_ns;       /* workers leave after this long; <= 0: 600 s */
@@ -273,7 +278,8 @@ typedef struct qldpc_server_config {
 /* Create a server for ncodes (1..4) graphs of the current device with host priors[c] (float[n_c],
  * copied).  Allocates the rings (page-locked host memory) and device state; the kernel starts on
  * the first request.  INVALID_ARG on bad arguments or non-finite priors; UNSUPPORTED if a graph
- * exceeds the single-shot kernel's limits or the workers cannot all be resident. */
+ * exceeds the single-shot kernel's limits (with QLDPC_LAYERED: the layer and degree limits above)
+ * or the workers cannot all be resident. */
 QLDPC_API int qldpc_server_create(const qldpc_graph *const *graphs, const float *const *priors,
                                   int32_t ncodes, const qldpc_server_config *cfg,
                                   qldpc_server **out);

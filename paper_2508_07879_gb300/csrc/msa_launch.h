@@ -178,6 +178,13 @@ cudaError_t launch_server_i16(const ServerParams &p, const KernelChoice &kc, int
                               size_t smem, cudaStream_t stream);
 cudaError_t launch_server_i8(const ServerParams &p, const KernelChoice &kc, int blocks, int threads,
                              size_t smem, cudaStream_t stream);
+// Server workers on the layered schedule (msa_layered.cu): register-resident checks, at most
+// kLayeredServerMaxLayers layers of rows of degree <= 8 and kLayeredServerMaxThreads checks per layer.
+constexpr int kLayeredServerMaxLayers = 8;
+constexpr int kLayeredServerMaxThreads = 256;
+const void *server_kernel_layered(int precision, const KernelChoice &kc);
+cudaError_t launch_server_layered(int precision, const ServerParams &p, const KernelChoice &kc, int blocks,
+                                  int threads, size_t smem, cudaStream_t stream);
 
 // Per-precision instantiation tables (one translation unit each).
 const void *msa_kernel_f32(const KernelChoice &kc);

@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include "msa_kernel.cuh"
+#include "server_kernel.cuh"
 
 namespace qldpc {
 namespace kern {
@@ -156,40 +157,129 @@ __global__ void __launch_bounds__(1024, 1) msa_layered_kernel(const LaunchParams
 // owns check t of every layer (at most one per layer), and keeps that check's variable indices and
 // messages in registers across iterations, so an iteration touches shared memory only for Q.
 // Arithmetic and order are those of msa_layered_kernel.
+template <int DC, int MAXL>
+struct LayeredOwned {
+    int myc[MAXL], mdeg[MAXL];           // check of layer l owned by this thread (or -1), its degree
+    uint32_t ev[MAXL][(DC + 1) / 2];     // its variables, two 16-bit indices per word
+};
+
+template <int DC, bool UNIFORM, int MAXL>
+__device__ __forceinline__ void layered_own(const DeviceGraph &g, int tid, LayeredOwned<DC, MAXL> &o)
+{
+    const int M = g.m, L = g.nlayers;
+#pragma unroll
+    for (int l = 0; l < MAXL; ++l) {
+        o.myc[l] = -1;
+        o.mdeg[l] = 0;
+        if (l < L) {
+            const int i = __ldg(g.layer_ptr + l) + tid;
+            if (i < __ldg(g.layer_ptr + l + 1)) {
+                o.myc[l] = int(__ldg(g.layer_chk + i));
+                o.mdeg[l] = UNIFORM ? DC : int(__ldg(g.rdeg + o.myc[l]));
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < DC; j += 2) {
+            uint32_t lo = 0, hi = 0;
+            if (j < o.mdeg[l]) lo = __ldg(g.ecol + size_t(j) * M + o.myc[l]);
+            if (j + 1 < DC && j + 1 < o.mdeg[l]) hi = __ldg(g.ecol + size_t(j + 1) * M + o.myc[l]);
+            o.ev[l][j / 2] = lo | (hi << 16);
+        }
+    }
+}
+
+// One shot: Q [n] (shared) starts at the quantized priors, the messages at zero; syn(c) reads s_c.
+// Runs the layers of every iteration with one barrier each and the stop test after the last, and
+// returns the iterations run (all = every check satisfied).  Ends with Q final and visible to the
+// block.
+template <class P, int DC, bool UNIFORM, int MAXL, class Syn>
+__device__ __forceinline__ int layered_reg_shot(const LayeredOwned<DC, MAXL> &o, int L, int N, int tid, int T,
+                                                Syn syn, const float *__restrict__ prior,
+                                                typename P::acc_t *__restrict__ Q, const LaunchParams &p,
+                                                bool early, int &all)
+{
+    using acc_t = typename P::acc_t;
+    using mag_t = typename P::mag_t;
+    acc_t r[MAXL][DC];
+    uint32_t sbits = 0;
+#pragma unroll
+    for (int l = 0; l < MAXL; ++l) {
+        if (o.myc[l] >= 0) sbits |= (syn(o.myc[l]) & 1u) << l;
+#pragma unroll
+        for (int j = 0; j < DC; ++j) r[l][j] = acc_t(0);
+    }
+    for (int v = tid; v < N; v += T) Q[v] = P::quantize(prior[v]);
+    __syncthreads();
+    // stop test over the thread's own checks
+    auto met = [&]() {
+        int ok = 1;
+#pragma unroll
+        for (int l = 0; l < MAXL; ++l) {
+            if (o.myc[l] >= 0) {
+                uint32_t par = (sbits >> l) & 1u;
+#pragma unroll
+                for (int j = 0; j < DC; ++j)
+                    if (UNIFORM || j < o.mdeg[l]) par ^= P::neg(Q[(o.ev[l][j / 2] >> (16 * (j & 1))) & 0xffffu]) ? 1u : 0u;
+                ok &= par == 0;
+            }
+        }
+        return ok;
+    };
+    all = __syncthreads_and(met());
+    int k = 0;
+    if (!(early && all)) {
+        for (k = 1; k <= p.max_iter; ++k) {
+#pragma unroll
+            for (int l = 0; l < MAXL; ++l) {
+                if (l < L) {
+                    if (o.myc[l] >= 0) {
+                        acc_t q[DC];
+                        uint32_t v[DC];
+                        uint32_t sx = 0;
+#pragma unroll
+                        for (int j = 0; j < DC; ++j) {
+                            if (UNIFORM || j < o.mdeg[l]) {
+                                v[j] = (o.ev[l][j / 2] >> (16 * (j & 1))) & 0xffffu;
+                                q[j] = P::sub_q(Q[v[j]], r[l][j]);
+                                sx ^= P::sign_word(q[j]);
+                            }
+                        }
+                        mag_t m1, m2;
+                        two_smallest<P, DC, UNIFORM>(q, o.mdeg[l], m1, m2);
+                        const uint32_t negall = (((sbits >> l) & 1u) ^ (sx >> 31)) & 1u;
+                        const mag_t r1 = P::presign(P::scale(m1, p), negall);
+                        const mag_t r2 = P::presign(P::scale(m2, p), negall);
+#pragma unroll
+                        for (int j = 0; j < DC; ++j) {
+                            if (UNIFORM || j < o.mdeg[l]) {
+                                r[l][j] = P::apply_sign(P::mag(q[j]) == m1 ? r2 : r1, q[j]);
+                                Q[v[j]] = P::add(q[j], r[l][j]);
+                            }
+                        }
+                    }
+                    __syncthreads();
+                }
+            }
+            all = __syncthreads_and(met());
+            if (early && all) break;
+        }
+        if (k > p.max_iter) k = p.max_iter;
+    }
+    return k;
+}
+
 template <class P, int DC, bool UNIFORM, int MAXL>
 __global__ void __launch_bounds__(256, 1) msa_layered_reg_kernel(const LaunchParams p)
 {
     using acc_t = typename P::acc_t;
-    using mag_t = typename P::mag_t;
     const Problem pr = blockIdx.y == 0 ? p.prob[0] : p.prob[1];
     const int M = pr.g.m, N = pr.g.n, L = pr.g.nlayers;
     const int T = blockDim.x, tid = threadIdx.x;
     extern __shared__ __align__(16) unsigned char smem[];
     acc_t *Q = reinterpret_cast<acc_t *>(smem);
 
-    // ownership: check myc[l] of layer l (or -1), its degree and variables (two 16-bit indices per word)
-    int myc[MAXL], mdeg[MAXL];
-    uint32_t ev[MAXL][(DC + 1) / 2];
-    acc_t r[MAXL][DC];
-#pragma unroll
-    for (int l = 0; l < MAXL; ++l) {
-        myc[l] = -1;
-        mdeg[l] = 0;
-        if (l < L) {
-            const int i = __ldg(pr.g.layer_ptr + l) + tid;
-            if (i < __ldg(pr.g.layer_ptr + l + 1)) {
-                myc[l] = int(__ldg(pr.g.layer_chk + i));
-                mdeg[l] = UNIFORM ? DC : int(__ldg(pr.g.rdeg + myc[l]));
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < DC; j += 2) {
-            uint32_t lo = 0, hi = 0;
-            if (j < mdeg[l]) lo = __ldg(pr.g.ecol + size_t(j) * M + myc[l]);
-            if (j + 1 < DC && j + 1 < mdeg[l]) hi = __ldg(pr.g.ecol + size_t(j + 1) * M + myc[l]);
-            ev[l][j / 2] = lo | (hi << 16);
-        }
-    }
+    LayeredOwned<DC, MAXL> own;
+    layered_own<DC, UNIFORM, MAXL>(pr.g, tid, own);
 
     int bad = 0;
     for (int v = tid; v < N; v += T) bad |= !isfinite(pr.prior[v]);
@@ -218,70 +308,9 @@ __global__ void __launch_bounds__(256, 1) msa_layered_reg_kernel(const LaunchPar
             continue;
         }
         const uint8_t *s = pr.syn + size_t(b) * M;
-        uint32_t sbits = 0;
-#pragma unroll
-        for (int l = 0; l < MAXL; ++l) {
-            if (myc[l] >= 0) sbits |= uint32_t(s[myc[l]] & 1u) << l;
-#pragma unroll
-            for (int j = 0; j < DC; ++j) r[l][j] = acc_t(0);
-        }
-        for (int v = tid; v < N; v += T) Q[v] = P::quantize(pr.prior[v]);
-        __syncthreads();
-        // stop test over the thread's own checks
-        auto met = [&]() {
-            int ok = 1;
-#pragma unroll
-            for (int l = 0; l < MAXL; ++l) {
-                if (myc[l] >= 0) {
-                    uint32_t par = (sbits >> l) & 1u;
-#pragma unroll
-                    for (int j = 0; j < DC; ++j)
-                        if (UNIFORM || j < mdeg[l]) par ^= P::neg(Q[(ev[l][j / 2] >> (16 * (j & 1))) & 0xffffu]) ? 1u : 0u;
-                    ok &= par == 0;
-                }
-            }
-            return ok;
-        };
-        int all = __syncthreads_and(met());
-        int k = 0;
-        if (!(early && all)) {
-            for (k = 1; k <= p.max_iter; ++k) {
-#pragma unroll
-                for (int l = 0; l < MAXL; ++l) {
-                    if (l < L) {
-                        if (myc[l] >= 0) {
-                            acc_t q[DC];
-                            uint32_t v[DC];
-                            uint32_t sx = 0;
-#pragma unroll
-                            for (int j = 0; j < DC; ++j) {
-                                if (UNIFORM || j < mdeg[l]) {
-                                    v[j] = (ev[l][j / 2] >> (16 * (j & 1))) & 0xffffu;
-                                    q[j] = P::sub_q(Q[v[j]], r[l][j]);
-                                    sx ^= P::sign_word(q[j]);
-                                }
-                            }
-                            mag_t m1, m2;
-                            two_smallest<P, DC, UNIFORM>(q, mdeg[l], m1, m2);
-                            const uint32_t negall = (((sbits >> l) & 1u) ^ (sx >> 31)) & 1u;
-                            const mag_t r1 = P::presign(P::scale(m1, p), negall);
-                            const mag_t r2 = P::presign(P::scale(m2, p), negall);
-#pragma unroll
-                            for (int j = 0; j < DC; ++j) {
-                                if (UNIFORM || j < mdeg[l]) {
-                                    r[l][j] = P::apply_sign(P::mag(q[j]) == m1 ? r2 : r1, q[j]);
-                                    Q[v[j]] = P::add(q[j], r[l][j]);
-                                }
-                            }
-                        }
-                        __syncthreads();
-                    }
-                }
-                all = __syncthreads_and(met());
-                if (early && all) break;
-            }
-            if (k > p.max_iter) k = p.max_iter;
-        }
+        int all = 0;
+        const int k = layered_reg_shot<P, DC, UNIFORM, MAXL>(own, L, N, tid, T, [&](int c) { return uint32_t(s[c]); },
+                                                             pr.prior, Q, p, early, all);
         for (int v = tid; v < N; v += T) {
             err[v] = P::neg(Q[v]) ? 1 : 0;
             if (pr.post) pr.post[size_t(b) * N + v] = P::post(Q[v]);
@@ -294,6 +323,55 @@ __global__ void __launch_bounds__(256, 1) msa_layered_reg_kernel(const LaunchPar
     }
 }
 
+// Persistent server worker on the layered schedule (QLDPC_LAYERED in the server's flags): the
+// claim, publish and leave protocol of msa_server_kernel around one layered_reg_shot per request.
+// Each worker block owns its code's checks in registers from the kernel's start.
+template <class P, int DC, bool UNIFORM, int MAXL>
+__global__ void __launch_bounds__(256, 1) msa_server_layered_kernel(const ServerParams sp)
+{
+    using acc_t = typename P::acc_t;
+    int ci = 0;
+    while (ci + 1 < sp.ncodes && int(blockIdx.x) >= sp.code[ci + 1].first_block) ++ci;
+    const ServerCode sc = sp.code[ci];
+    const int N = sc.g.n, T = blockDim.x, tid = threadIdx.x;
+    extern __shared__ __align__(16) unsigned char smem[];
+    acc_t *Q = reinterpret_cast<acc_t *>(smem);
+    __shared__ int64_t s_claim;
+
+    LaunchParams p{};   // the arithmetic parameters the shared device functions read
+    p.alpha = sp.alpha;
+    p.alpha_q = sp.alpha_q;
+    p.max_iter = sp.max_iter;
+    p.flags = sp.flags;
+    const bool early = (sp.flags & kFlagNoEarlyStop) == 0;
+
+    LayeredOwned<DC, MAXL> own;
+    layered_own<DC, UNIFORM, MAXL>(sc.g, tid, own);
+
+    const uint64_t t_start = globaltimer();
+    uint64_t t_idle_from = t_start;
+    for (;;) {
+        if (tid == 0) s_claim = claim_request(sc, sp, t_start, t_idle_from);
+        __syncthreads();
+        const int64_t h = s_claim;
+        if (h < 0) break;
+        unsigned char *slot = sc.ring + size_t(uint32_t(h) & uint32_t(sp.ring_capacity - 1)) * size_t(sc.slot_bytes);
+        const unsigned char *syn = slot + sc.syn_off;
+        int all = 0;
+        const int k = layered_reg_shot<P, DC, UNIFORM, MAXL>(
+            own, sc.g.nlayers, N, tid, T, [&](int c) { return uint32_t(__ldcv(syn + c)); }, sc.prior, Q, p, early, all);
+        unsigned char *err = slot + sc.err_off;
+        for (int v = tid; v < N; v += T) err[v] = P::neg(Q[v]) ? 1 : 0;
+        __syncthreads();
+        if (tid == 0) {
+            *reinterpret_cast<int32_t *>(slot + 4) = k;
+            slot[8] = all ? 1 : 0;
+            __threadfence_system();
+            st_release_sys(reinterpret_cast<uint32_t *>(slot), uint32_t(h) + 1u);
+        }
+    }
+}
+
 }  // namespace kern
 
 #define QLDPC_LAYERED_VARIANTS(X) X(6, true) X(7, true) X(8, true) X(9, true) X(8, false) X(16, false) X(32, false)
@@ -301,6 +379,7 @@ __global__ void __launch_bounds__(256, 1) msa_layered_reg_kernel(const LaunchPar
 // Register-resident variants (at most 8 layers, rows of degree <= 8); KernelChoice::dvb = 1 selects them.
 #define QLDPC_LAYERED_REG_VARIANTS(X) X(6, true) X(7, true) X(8, true) X(8, false)
 constexpr int kLayeredRegMaxLayers = 8;
+static_assert(kLayeredRegMaxLayers == kLayeredServerMaxLayers, "the server workers use the register-resident layout");
 
 template <class P>
 const void *layered_table(const KernelChoice &kc)
@@ -336,6 +415,46 @@ cudaError_t layered_launch(const LaunchParams &p, const KernelChoice &kc, dim3 g
     QLDPC_LAYERED_REG_VARIANTS(QLDPC_L)
 #undef QLDPC_L
     return cudaErrorInvalidValue;
+}
+
+template <class P>
+const void *server_layered_table(const KernelChoice &kc)
+{
+#define QLDPC_K(DCV, UNI)                                                                       \
+    if (kc.dc == DCV && kc.uniform == UNI)                                                      \
+        return reinterpret_cast<const void *>(&kern::msa_server_layered_kernel<P, DCV, UNI, kLayeredRegMaxLayers>);
+    QLDPC_LAYERED_REG_VARIANTS(QLDPC_K)
+#undef QLDPC_K
+    return nullptr;
+}
+
+template <class P>
+cudaError_t server_layered_launch(const ServerParams &sp, const KernelChoice &kc, int blocks, int threads, size_t smem,
+                                  cudaStream_t stream)
+{
+#define QLDPC_L(DCV, UNI)                                                                       \
+    if (kc.dc == DCV && kc.uniform == UNI) {                                                    \
+        kern::msa_server_layered_kernel<P, DCV, UNI, kLayeredRegMaxLayers><<<blocks, threads, smem, stream>>>(sp); \
+        return cudaGetLastError();                                                              \
+    }
+    QLDPC_LAYERED_REG_VARIANTS(QLDPC_L)
+#undef QLDPC_L
+    return cudaErrorInvalidValue;
+}
+
+const void *server_kernel_layered(int precision, const KernelChoice &kc)
+{
+    return precision == kINT16 ? server_layered_table<kern::I16>(kc)
+           : precision == kINT8 ? server_layered_table<kern::I8>(kc)
+                                : server_layered_table<kern::F32>(kc);
+}
+
+cudaError_t launch_server_layered(int precision, const ServerParams &sp, const KernelChoice &kc, int blocks,
+                                  int threads, size_t smem, cudaStream_t stream)
+{
+    return precision == kINT16 ? server_layered_launch<kern::I16>(sp, kc, blocks, threads, smem, stream)
+           : precision == kINT8 ? server_layered_launch<kern::I8>(sp, kc, blocks, threads, smem, stream)
+                                : server_layered_launch<kern::F32>(sp, kc, blocks, threads, smem, stream);
 }
 
 const void *msa_kernel_layered(int precision, const KernelChoice &kc)

@@ -29,6 +29,7 @@ using namespace qldpc::detail;
 struct qldpc_server {
     int device = 0;
     int precision = QLDPC_FP32;
+    bool layered = false;                   // QLDPC_LAYERED: layered-schedule workers
     int ncodes = 0;
     const qldpc_graph *graphs[kServerMaxCodes] = {};
     int32_t m[kServerMaxCodes] = {}, n[kServerMaxCodes] = {};
@@ -55,9 +56,10 @@ namespace {
 
 int launch_server(qldpc_server *s)
 {
-    cudaError_t e = s->precision == QLDPC_INT16  ? launch_server_i16(s->sp, s->kc, s->blocks, s->threads, s->smem, s->stream)
-                    : s->precision == QLDPC_INT8 ? launch_server_i8(s->sp, s->kc, s->blocks, s->threads, s->smem, s->stream)
-                                                 : launch_server_f32(s->sp, s->kc, s->blocks, s->threads, s->smem, s->stream);
+    cudaError_t e = s->layered ? launch_server_layered(s->precision, s->sp, s->kc, s->blocks, s->threads, s->smem, s->stream)
+                    : s->precision == QLDPC_INT16 ? launch_server_i16(s->sp, s->kc, s->blocks, s->threads, s->smem, s->stream)
+                    : s->precision == QLDPC_INT8  ? launch_server_i8(s->sp, s->kc, s->blocks, s->threads, s->smem, s->stream)
+                                                  : launch_server_f32(s->sp, s->kc, s->blocks, s->threads, s->smem, s->stream);
     if (e != cudaSuccess) return cuda_status(e);
     s->launched = true;
     return QLDPC_OK;
@@ -135,9 +137,11 @@ int qldpc_server_create(const qldpc_graph *const *graphs, const float *const *pr
     if (!graphs || !priors || !cfg || ncodes < 1 || ncodes > QLDPC_SERVER_MAX_CODES) return QLDPC_ERR_INVALID_ARG;
     if (cfg->precision != QLDPC_FP32 && cfg->precision != QLDPC_INT16 && cfg->precision != QLDPC_INT8)
         return QLDPC_ERR_INVALID_ARG;
-    if ((cfg->flags & ~uint32_t(QLDPC_NO_EARLY_STOP | QLDPC_LEARNED)) != 0 || cfg->max_iter < 0)
+    if ((cfg->flags & ~uint32_t(QLDPC_NO_EARLY_STOP | QLDPC_LEARNED | QLDPC_LAYERED)) != 0 || cfg->max_iter < 0)
         return QLDPC_ERR_INVALID_ARG;
     const bool learned = (cfg->flags & QLDPC_LEARNED) != 0;
+    const bool layered = (cfg->flags & QLDPC_LAYERED) != 0;
+    if (learned && layered) return QLDPC_ERR_INVALID_ARG;
     if (learned && (cfg->precision != QLDPC_FP32 || (cfg->flags & QLDPC_NO_EARLY_STOP))) return QLDPC_ERR_INVALID_ARG;
     if (!std::isfinite(cfg->alpha) || cfg->alpha <= 0.0f) return QLDPC_ERR_INVALID_ARG;
     const int aq = cfg->precision == QLDPC_FP32 ? 0 : alpha_fixed(cfg->alpha);
@@ -156,6 +160,7 @@ int qldpc_server_create(const qldpc_graph *const *graphs, const float *const *pr
     if (!s) return QLDPC_ERR_OOM;
     s->device = graphs[0]->device;
     s->precision = cfg->precision;
+    s->layered = layered;
     s->ncodes = ncodes;
     s->capacity = cap;
 
@@ -178,15 +183,34 @@ int qldpc_server_create(const qldpc_graph *const *graphs, const float *const *pr
     }
     s->kc = kernel_variant(dc, dv, uniform, true, false);
     for (int c = 0; c < ncodes; ++c) s->kc.learned = s->kc.learned || (learned && graphs[c]->d_weights);
-    s->threads = cfg->threads_per_block ? cfg->threads_per_block : std::min(want, kLatencyMaxThreads);
-    bool fits = s->threads >= 32 && s->threads <= kLatencyMaxThreads && s->threads % 32 == 0;
-    for (int c = 0; c < ncodes; ++c)
-        fits = fits && graphs[c]->m <= kLatencyCnPerThread * s->threads &&
-               graphs[c]->nv <= kLatencyVnPerThread * s->threads;
+    bool fits;
+    if (layered) {
+        // a thread per check of the widest layer; each thread keeps one check per layer in registers
+        int widest = 32;
+        smem = 0;
+        fits = dc <= 8;
+        for (int c = 0; c < ncodes; ++c) {
+            const qldpc_graph *g = graphs[c];
+            widest = std::max(widest, (g->dg.max_layer + 31) / 32 * 32);
+            smem = std::max(smem, align16(size_t(g->n) * 4));
+            fits = fits && g->dg.nlayers <= kLayeredServerMaxLayers && g->n <= 65536;
+        }
+        s->kc.latency = false;
+        s->kc.layered = true;
+        s->threads = cfg->threads_per_block ? cfg->threads_per_block : widest;
+        fits = fits && s->threads >= widest && s->threads <= kLayeredServerMaxThreads && s->threads % 32 == 0;
+    } else {
+        s->threads = cfg->threads_per_block ? cfg->threads_per_block : std::min(want, kLatencyMaxThreads);
+        fits = s->threads >= 32 && s->threads <= kLatencyMaxThreads && s->threads % 32 == 0;
+        for (int c = 0; c < ncodes; ++c)
+            fits = fits && graphs[c]->m <= kLatencyCnPerThread * s->threads &&
+                   graphs[c]->nv <= kLatencyVnPerThread * s->threads;
+    }
     s->smem = smem;
-    const void *k = cfg->precision == QLDPC_INT16  ? server_kernel_i16(s->kc)
-                    : cfg->precision == QLDPC_INT8 ? server_kernel_i8(s->kc)
-                                                   : server_kernel_f32(s->kc);
+    const void *k = layered                          ? server_kernel_layered(cfg->precision, s->kc)
+                    : cfg->precision == QLDPC_INT16 ? server_kernel_i16(s->kc)
+                    : cfg->precision == QLDPC_INT8  ? server_kernel_i8(s->kc)
+                                                    : server_kernel_f32(s->kc);
     if (!fits || !k) {
         delete s;
         return QLDPC_ERR_UNSUPPORTED;

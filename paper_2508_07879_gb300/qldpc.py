@@ -385,12 +385,13 @@ class Server:
 
     graphs: list of Graph; priors: list of float32 [n] numpy arrays (host).  The worker kernel starts
     on the first request and leaves after `idle_timeout_s` without requests (restarted on demand).
+    layered=True: workers on the layered schedule (codes of at most 8 layers of rows of degree <= 8).
     """
 
     def __init__(self, graphs, priors, max_iter: int, alpha: float = 0.75, precision: str = "fp32",
                  early_stop: bool = True, ring_capacity: int = 256, blocks=None,
                  idle_timeout_s: float = 0.5, max_runtime_s: float = 600.0, threads_per_block: int = 0,
-                 learned: bool = False):
+                 learned: bool = False, layered: bool = False):
         self._h = None
         self.graphs = list(graphs)
         self._priors = [np.ascontiguousarray(p, dtype=np.float32) for p in priors]
@@ -398,7 +399,7 @@ class Server:
         cfg.precision = PRECISIONS[precision]
         cfg.max_iter = int(max_iter)
         cfg.alpha = float(alpha)
-        cfg.flags = _flags(early_stop, learned)
+        cfg.flags = _flags(early_stop, learned, layered)
         cfg.ring_capacity = int(ring_capacity)
         cfg.threads_per_block = int(threads_per_block)
         for i, b in enumerate(blocks or []):

@@ -27,10 +27,10 @@ def q():
     return qldpc
 
 
-def device_reference(q, graph, syn, prior, max_iter, precision, early_stop=True):
+def device_reference(q, graph, syn, prior, max_iter, precision, early_stop=True, layered=False):
     s = torch.from_numpy(np.ascontiguousarray(syn, dtype=np.uint8)).cuda()
     p = torch.from_numpy(np.ascontiguousarray(prior, dtype=np.float32)).cuda()
-    err, iters, ok, _ = q.decode(graph, s, p, max_iter, 0.75, precision, early_stop)
+    err, iters, ok, _ = q.decode(graph, s, p, max_iter, 0.75, precision, early_stop, layered=layered)
     torch.cuda.synchronize()
     return err.cpu().numpy(), iters.cpu().numpy(), ok.cpu().numpy()
 
@@ -151,4 +151,51 @@ def test_server_rejects_bad_arguments(q):
         assert ei.value.status == q.QLDPC_ERR_INVALID_ARG
     with pytest.raises(q.QldpcError) as ei:
         q.Server([g], [prior], 10, blocks=[100000])            # more workers than can be resident
+    assert ei.value.status == q.QLDPC_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("precision", ["fp32", "int16", "int8"])
+def test_layered_server_equals_layered_decode(q, precision):
+    """Layered-schedule workers (QLDPC_LAYERED) over LP-1054's H_Z and H_X (7 layers each), a mixed
+    stream: every request decodes as the layered batch decode does."""
+    code = w.lp_code(1054)
+    ex, ez = w.depolarizing_errors(code.n, 0.03, 400, seed=72)
+    prior = np.full(code.n, w.prior_llr(0.02), dtype=np.float32)
+    hs = [code.hz_csr, code.hx_csr]
+    syns = [w.syndromes(code.hz_csr, ex), w.syndromes(code.hx_csr, ez)]
+    graphs = [q.Graph.from_csr(h) for h in hs]
+    refs = [device_reference(q, graphs[i], syns[i], prior, 50, precision, layered=True) for i in range(2)]
+    rng = np.random.default_rng(9)
+    codes = rng.integers(0, 2, 400).astype(np.int32)
+    arrival = np.cumsum(rng.exponential(20e3, size=400)).astype(np.int64)
+    cursor = [0, 0]
+    syn, ref_index = [], []
+    for c in codes:
+        syn.append(syns[c][cursor[c]])
+        ref_index.append(cursor[c])
+        cursor[c] += 1
+    with q.Server(graphs, [prior, prior], 50, 0.75, precision, blocks=[8, 8], idle_timeout_s=2.0,
+                  layered=True) as srv:
+        errs, iters, ok, lat = srv.replay(codes, syn, arrival)
+    for i, c in enumerate(codes):
+        j = ref_index[i]
+        np.testing.assert_array_equal(errs[i], refs[c][0][j])
+        assert iters[i] == refs[c][1][j] and ok[i] == refs[c][2][j]
+    assert (lat > 0).all() and np.asarray(ok).mean() > 0.9
+
+
+def test_layered_server_limits(q):
+    hgp = w.hgp_code(400)
+    prior = np.full(hgp.n, 2.0, dtype=np.float32)
+    with pytest.raises(q.QldpcError) as ei:                    # 15 layers: above the register-resident 8
+        q.Server([q.Graph.from_csr(hgp.hz_csr)], [prior], 10, layered=True)
+    assert ei.value.status == q.QLDPC_ERR_UNSUPPORTED
+    lp = w.lp_code(1054)
+    g = q.Graph.from_csr(lp.hz_csr)
+    g.set_weights(np.full((4, lp.hz_csr.nnz), 0.75, dtype=np.float32))
+    with pytest.raises(q.QldpcError) as ei:
+        q.Server([g], [np.full(lp.n, 2.0, dtype=np.float32)], 10, learned=True, layered=True)
+    assert ei.value.status == q.QLDPC_ERR_INVALID_ARG
+    with pytest.raises(q.QldpcError) as ei:                    # fewer threads than the widest layer (93)
+        q.Server([g], [np.full(lp.n, 2.0, dtype=np.float32)], 10, layered=True, threads_per_block=64)
     assert ei.value.status == q.QLDPC_ERR_UNSUPPORTED

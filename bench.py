@@ -47,6 +47,7 @@ P_GRID = (0.01, 0.02, 0.03, 0.04, 0.05)
 SEEDS = (2001, 2002, 2003, 2004, 2005)
 BATCH = 65536
 MAX_ITER = 50
+CPU_SHOTS_PER_P = 8192       # oracle sample per error rate: about 20 core-seconds on the host
 ALPHA = 0.75
 LAT_P = 0.03
 LAT_SHOTS = 10000
@@ -73,7 +74,7 @@ ALU_PIPE_LANES_PER_SM = 64      # the ALU pipe (integer, logic, compare, min/max
 
 # DRAM traffic of one decoder launch from an ncu capture, valid only for the kernel source it was
 # measured on (profiles/msa_batch_lp1054_b65536_fp32.md); reported as null once the source changes.
-NCU_TRAFFIC = {"source_sha16": "54bcf551061bd128", "bytes_per_launch": 30557440 + 12357632,
+NCU_TRAFFIC = {"source_sha16": "1a1f4f5b43445955", "bytes_per_launch": 30665216 + 11027456,
                "profile": "profiles/msa_batch_lp1054_b65536_fp32.md"}
 
 WORKLOAD = "LP-1054 H_Z (465x1054, E=3720), iid X noise p=0.01..0.05, B=65536/step, max 50 it, alpha 0.75"
@@ -367,9 +368,10 @@ def run_ours(args, rank, world, local):
     cpu = None
     if not args.no_cpu_baseline and rank == 0 and world == 1:
         threads = os.cpu_count() or 1
-        rate, n, dt = oracle_rate(batches, 2048, args.precision, threads)
+        rate, n, dt = oracle_rate(batches, CPU_SHOTS_PER_P, args.precision, threads)
         cpu = {"value": rate, "unit": "syndromes/s", "cores": threads, "kind": "oracle",
-               "sample": f"{n} shots (2048 per p at p=0.01..0.05) of the same batches, {dt:.1f} s wall"}
+               "sample": f"{n} shots ({CPU_SHOTS_PER_P} per p at p=0.01..0.05) of the same batches, "
+                         f"{dt:.1f} s wall, about {dt * threads:.0f} core-s"}
 
     if rank == 0:
         line = {
@@ -379,6 +381,8 @@ def run_ours(args, rank, world, local):
             "dtype": {"fp32": "f32", "int16": "i16"}[args.precision], "data": "synthetic",
             "config": {"workload": WORKLOAD, "global_batch": B * world, "precision": args.precision,
                        "l2": "inputs rotate over 5 batches (152 MB) + 69 MB outputs per step > 129 MB L2",
+                       "rates": "step i decodes the batch of p = 0.01, 0.02, ..., 0.05 at i mod 5; a step count "
+                                "that is a multiple of 5 weights the five rates equally",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "roofline": roofline,
             "cpu_baseline": cpu,

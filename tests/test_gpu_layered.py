@@ -43,7 +43,7 @@ def device_layered(q, h, s, prior, max_iter, precision, early_stop=True):
 
 
 def oracle_layered(h, s, prior, max_iter, precision, early_stop=True):
-    prec = {"fp32": "f32", "int16": "i16"}[precision]
+    prec = {"fp32": "f32", "int16": "i16", "int8": "i8"}[precision]
     return oracle.msa(h.row_ptr, h.col_idx, h.m, h.n, s, prior, max_iter, 0.75, prec, early_stop, threads=16,
                       schedule="layered")
 
@@ -54,7 +54,7 @@ def check_equal(q, h, s, prior, max_iter, precision, early_stop=True):
     np.testing.assert_array_equal(err, ref["err"])
     np.testing.assert_array_equal(iters, ref["iters"])
     np.testing.assert_array_equal(ok, ref["ok"])
-    want = ref["post"] / 256.0 if precision == "int16" else ref["post"]
+    want = ref["post"] / {"fp32": 1.0, "int16": 256.0, "int8": 4.0}[precision]
     np.testing.assert_array_equal(post, want.astype(np.float32))
     return iters, ok
 
@@ -157,7 +157,7 @@ def test_batch_invariance(q):
             np.testing.assert_array_equal(a, b[lo:hi])
 
 
-@pytest.mark.parametrize("precision", ["fp32", "int16"])
+@pytest.mark.parametrize("precision", ["fp32", "int16", "int8"])
 def test_single_shot_register_kernel(q, precision):
     """Batches no larger than the SM count run the register-resident layered kernel (LP-1054: 7
     layers of degree-8 rows): bit-exact against the oracle as well."""
@@ -169,3 +169,32 @@ def test_single_shot_register_kernel(q, precision):
     assert (iters > 3).any()
     check_equal(q, h, s[:1], prior, 50, precision)
     check_equal(q, h, s[:7], prior, 12, precision, early_stop=False)
+
+
+def block_layered_code(seed, degree=None, n=168, blocks=6):
+    """Rows in `blocks` groups, each group a random partition of the columns into rows of `degree`
+    (or of 8 with 0-5 entries then dropped per row: degrees 3..8).  Row order by group, so the
+    as-soon-as-possible layering gives at most `blocks` layers: the register-resident regime."""
+    rng = np.random.default_rng(seed)
+    d = degree or 8
+    rows = []
+    for _ in range(blocks):
+        for r in rng.permutation(n).reshape(n // d, d):
+            rows.append(r if degree else r[:d - int(rng.integers(0, 6))])
+    h = np.zeros((len(rows), n), dtype=np.uint8)
+    for i, r in enumerate(rows):
+        h[i, r] = 1
+    return w.csr_from_dense(h)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "int16", "int8"])
+@pytest.mark.parametrize("degree", [6, 7, None])
+def test_single_shot_kernel_on_few_layer_codes(q, precision, degree):
+    """Rows of exact degree 6 and 7 and of varying degree 3..8 in the register-resident kernel
+    (six layers), where a check's edges do not fill its lanes evenly."""
+    h = block_layered_code(40 + (degree or 0), degree)
+    e = w.iid_x_errors(h.n, 0.06, 120, seed=89)
+    s = w.syndromes(h, e)
+    prior = np.full(h.n, w.prior_llr(0.06), dtype=np.float32)
+    iters, ok = check_equal(q, h, s, prior, 30, precision)
+    assert (iters > 2).any()

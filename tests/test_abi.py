@@ -158,3 +158,23 @@ def test_product_and_oracle_are_independent():
             text = open(os.path.join(ROOT, "oracle", f)).read()
             assert "paper_2508_07879_gb300" not in text, f
             assert "qldpc.h" not in text and "msa_kernel" not in text, f
+
+
+def test_binding_refuses_host_tensors(q):
+    """No CPU fallback: device arguments given as host tensors are refused before the library is
+    called, for the decode and the soft-syndrome decode alike."""
+    import torch
+
+    class FakeGraph:            # only the dimensions are read before the arguments are marshalled
+        m, n, handle = 4, 6, ctypes.c_void_p(0)
+
+    syn = torch.zeros((2, 4), dtype=torch.uint8)
+    prior = torch.ones(6)
+    with pytest.raises(TypeError, match="CUDA tensor"):
+        q.decode(FakeGraph(), syn, prior, 10)
+    soft = FakeGraph()
+    soft.n = 10                 # [H | I_4] of a 4 x 6 H
+    with pytest.raises(TypeError, match="CUDA tensor"):
+        q.decode_soft(soft, syn, prior, torch.ones(4), 10)
+    with pytest.raises(ValueError, match="data-syndrome"):
+        q.decode_soft(soft, syn, torch.ones(5), torch.ones(4), 10)

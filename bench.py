@@ -223,6 +223,24 @@ def oracle_rate(batches, shots_per_batch: int, precision: str, threads: int):
     return total / dt, total, dt
 
 
+def oracle_single_thread(batches, precision: str, shots: int = 2000):
+    """The oracle on one core, one shot per call, on the p = 0.03 batch: shots/s and per-shot
+    latency percentiles (host clock around each call, Python call overhead included)."""
+    import oracle
+    oprec = {"fp32": "f32", "int16": "i16"}[precision]
+    b = batches[P_GRID.index(0.03)]
+    shots = min(shots, b.syndromes.shape[0])
+    lat = np.empty(shots)
+    for i in range(shots):
+        t0 = time.perf_counter_ns()
+        oracle.msa(b.h.row_ptr, b.h.col_idx, b.h.m, b.h.n, b.syndromes[i:i + 1], b.prior, MAX_ITER, ALPHA,
+                   oprec, True, threads=1)
+        lat[i] = (time.perf_counter_ns() - t0) / 1e3
+    return {"shots_per_s": shots / (lat.sum() / 1e6), "p50_us": float(np.percentile(lat, 50)),
+            "p99_us": float(np.percentile(lat, 99)), "p999_us": float(np.percentile(lat, 99.9)),
+            "shots": shots, "p": 0.03, "cores": 1}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -254,7 +272,8 @@ def run_reference(args, rank, world):
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "reference_step": f"{per_step} shots on the CPU oracle"},
         "cpu_baseline": {"value": value, "unit": "syndromes/s", "cores": threads, "kind": "oracle",
-                         "sample": f"{args.steps} steps x {per_step} shots cycling p=0.01..0.05"},
+                         "sample": f"{args.steps} steps x {per_step} shots cycling p=0.01..0.05",
+                         "single_thread": oracle_single_thread(batches, args.precision, 500)},
         "e2e": {"value": value, "unit": "syndromes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -371,7 +390,8 @@ def run_ours(args, rank, world, local):
         rate, n, dt = oracle_rate(batches, CPU_SHOTS_PER_P, args.precision, threads)
         cpu = {"value": rate, "unit": "syndromes/s", "cores": threads, "kind": "oracle",
                "sample": f"{n} shots ({CPU_SHOTS_PER_P} per p at p=0.01..0.05) of the same batches, "
-                         f"{dt:.1f} s wall, about {dt * threads:.0f} core-s"}
+                         f"{dt:.1f} s wall, about {dt * threads:.0f} core-s",
+               "single_thread": oracle_single_thread(batches, args.precision)}
 
     if rank == 0:
         line = {

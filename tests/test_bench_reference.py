@@ -27,6 +27,9 @@ def test_reference_arm_line():
     assert d["ms_per_step"] > 0 and d["data"] == "synthetic" and "workload" in d["config"]
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    st = cb["single_thread"]
+    assert st["cores"] == 1 and st["shots"] > 0 and st["shots_per_s"] > 0
+    assert 0 < st["p50_us"] <= st["p99_us"] <= st["p999_us"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
 
 

@@ -100,7 +100,7 @@ enum {
                                      are updated one after another in ascending index, each from the
                                      a-posteriori LLRs the checks before it refreshed
                                      (q = Q - r_old, r = Algorithm 1's check update of q,
-                                     Q = q + r); FP32 or INT16; not with QLDPC_LEARNED */
+                                     Q = q + r); FP32, INT16 or INT8; not with QLDPC_LEARNED */
 };
 
 /* Limits of the compiled kernels. */
@@ -417,6 +417,10 @@ QLDPC_API int qldpc_logical_failures(const uint8_t *logicals, int32_t k, int32_t
 /* Size of the library's static device scratch used by qldpc_decode_host_noalloc (4 MiB). */
 enum { QLDPC_NOALLOC_SCRATCH_BYTES = 4 * 1024 * 1024 };
 
+/* The size of that scratch as compiled into the library, in bytes (a binding that carries its own
+ * copy of the constant above can check it against this). */
+QLDPC_API size_t qldpc_noalloc_scratch_bytes(void);
+
 /*
  * qldpc_decode_host without any device allocation.  (No counterpart in the paper: this is a
  * deployment aid.)
@@ -425,19 +429,25 @@ enum { QLDPC_NOALLOC_SCRATCH_BYTES = 4 * 1024 * 1024 };
  * fixes its device memory at start-up because an allocation can synchronize the device and take
  * unbounded time inside the syndrome cycle, or a plug-in whose host application owns all device
  * memory.  qldpc_decode_host allocates device staging on first use (and grows it); this entry
- * point instead stages through one file-scope device array of QLDPC_NOALLOC_SCRATCH_BYTES that
- * every GPU loading the library holds until the process exits.  It calls no cudaMalloc, cudaFree or
- * allocating library routine.
+ * point instead stages through one file-scope device array of QLDPC_NOALLOC_SCRATCH_BYTES.  It
+ * calls no cudaMalloc, cudaFree or allocating library routine.  The driver places the array in a
+ * device's memory when the library's module holding it is first loaded on that device, which
+ * (with CUDA's default lazy module loading) is the first call of this function there, and keeps
+ * it until the process exits.  So call it once with batch = 0 at start-up, on each device, with
+ * that device current and before any stream capture: that call checks its arguments, resolves
+ * the array's device address (cudaGetSymbolAddress) and returns.  The first decode of each kernel
+ * variant (precision, schedule, learned weights) can likewise load that kernel's code: run one
+ * decode of each kind you will use during start-up as well.
  *
  * Arguments, outputs and the synchronous behaviour are those of qldpc_decode_host (host buffers
  * in, host buffers out, stream synchronized before returning).  The prior is copied on every call.
  * The batch must fit the scratch: with a(x) = x rounded up to 256 bytes,
  *   a(4n) + a(batch*m) + a(batch*n) + a(4*batch) + a(batch) <= QLDPC_NOALLOC_SCRATCH_BYTES
- * (e.g. up to 2700 shots of a 465 x 1054 graph); a larger batch returns QLDPC_ERR_UNSUPPORTED
- * and enqueues nothing.  Invalid arguments return QLDPC_ERR_INVALID_ARG before anything is enqueued.
+ * (e.g. up to 2749 shots of a 465 x 1054 graph); a larger batch returns QLDPC_ERR_UNSUPPORTED
+ * and enqueues nothing.  Invalid arguments (QLDPC_ERR_INVALID_ARG) and a launch plan the kernels
+ * cannot run (QLDPC_ERR_UNSUPPORTED) are also reported before anything is enqueued.
  *
- * The first call on each device resolves the array's device address (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture.  All calls in the process
+ * All calls in the process
  * share the one array and it keeps the last call's contents; nothing in it needs to start at zero
  * because every byte a call reads is first written by that call.  Calls whose work overlaps on the
  * GPU (other threads, other streams) race on the array: serialize them.

@@ -60,6 +60,10 @@ int cuda_status(cudaError_t e);                                             // c
 int ensure_kernel_attrs(const void *k, size_t smem, size_t smem_optin);     // >48 KB dynamic smem opt-in
 int check_device(const qldpc_graph *g);                                     // graph belongs to the current device
 int alpha_fixed(float alpha);                                               // round(alpha*2^15), -1 outside (0,1]
+// Every argument check and the launch plan of a qldpc_decode_ex call on g with this batch, without
+// enqueuing anything: QLDPC_OK when such a call would launch.
+int decode_plan(const qldpc_graph *g, int32_t batch, int32_t max_iter, float alpha, int32_t precision,
+                uint32_t flags);
 
 }  // namespace detail
 }  // namespace qldpc

@@ -564,9 +564,11 @@ int check_device(const qldpc_graph *g)
     return dev == g->device ? QLDPC_OK : QLDPC_ERR_INVALID_ARG;
 }
 
+// Validate, plan and enqueue one decode.  plan_only: every check and the launch plan of this batch
+// (kernel attributes included), but nothing enqueued.
 int launch(const qldpc_graph *g0, const qldpc_graph *g1, const Problem *probs, int nprob,
            int32_t batch, int32_t max_iter, float alpha, int32_t precision, uint32_t flags,
-           cudaStream_t stream)
+           cudaStream_t stream, bool plan_only = false)
 {
     if (precision != QLDPC_FP32 && precision != QLDPC_INT16 && precision != QLDPC_INT8) return QLDPC_ERR_INVALID_ARG;
     if ((flags & ~uint32_t(QLDPC_NO_EARLY_STOP | QLDPC_LEARNED | QLDPC_LAYERED)) != 0) return QLDPC_ERR_INVALID_ARG;
@@ -606,6 +608,7 @@ int launch(const qldpc_graph *g0, const qldpc_graph *g1, const Problem *probs, i
         if (!latency)
             if (int rc = plan_batch(gs, nprob, batch, precision, learned, pl)) return rc;
     }
+    if (plan_only) return QLDPC_OK;
     if (!latency && pl.grid < batch) {
         // more shots than blocks: claim them dynamically from a zeroed counter pair of the ring
         p.next_shot = g0->d_counters + 2 * size_t(g0->counter_seq.fetch_add(1) % kShotCounterSlots);
@@ -628,6 +631,15 @@ Problem make_problem(const qldpc_graph *g, const uint8_t *syn, const float *prio
     pr.weights = g->d_weights;
     pr.learned_iters = g->learned_T;
     return pr;
+}
+
+int decode_plan(const qldpc_graph *g, int32_t batch, int32_t max_iter, float alpha, int32_t precision,
+                uint32_t flags)
+{
+    if (!g || batch < 0) return QLDPC_ERR_INVALID_ARG;
+    if (int rc = check_device(g)) return rc;
+    const Problem pr = make_problem(g, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+    return launch(g, g, &pr, 1, batch, max_iter, alpha, precision, flags, nullptr, true);
 }
 
 void free_stage(qldpc_graph *g)

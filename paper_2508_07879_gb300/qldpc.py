@@ -81,6 +81,7 @@ _SIGNATURES = {
     "qldpc_decode_host": ([_p, _p, _i32, _p, _i32, _f32, _p, _p, _p, _i32, _u32, _p], ctypes.c_int),
     "qldpc_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "qldpc_decode_host_noalloc": ([_p, _p, _i32, _p, _i32, _f32, _p, _p, _p, _i32, _u32, _p], ctypes.c_int),
+    "qldpc_noalloc_scratch_bytes": ([], ctypes.c_size_t),
     "qldpc_server_create": ([_p, _p, _i32, ctypes.POINTER(ServerConfig), ctypes.POINTER(_p)], ctypes.c_int),
     "qldpc_server_submit": ([_p, _i32, _p, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
     "qldpc_server_poll": ([_p, _i32, ctypes.c_uint64, _p, _p, _p], ctypes.c_int),
@@ -115,6 +116,7 @@ qldpc_decode_pair = _lib.qldpc_decode_pair
 qldpc_decode_host = _lib.qldpc_decode_host
 qldpc_status_string = _lib.qldpc_status_string
 qldpc_decode_host_noalloc = _lib.qldpc_decode_host_noalloc
+qldpc_noalloc_scratch_bytes = _lib.qldpc_noalloc_scratch_bytes
 qldpc_server_create = _lib.qldpc_server_create
 qldpc_server_submit = _lib.qldpc_server_submit
 qldpc_server_poll = _lib.qldpc_server_poll
@@ -128,7 +130,7 @@ qldpc_nms_backward = _lib.qldpc_nms_backward
 qldpc_adam_step = _lib.qldpc_adam_step
 qldpc_sample_errors = _lib.qldpc_sample_errors
 qldpc_logical_failures = _lib.qldpc_logical_failures
-QLDPC_NOALLOC_SCRATCH_BYTES = 4 * 1024 * 1024
+QLDPC_NOALLOC_SCRATCH_BYTES = qldpc_noalloc_scratch_bytes()   # as compiled into the library
 
 
 class QldpcError(RuntimeError):

@@ -52,6 +52,16 @@ def test_binding_names_match_header(q):
         assert callable(getattr(q, name))
 
 
+def test_noalloc_scratch_size_matches_header(q):
+    text = open(HEADER).read()
+    m = re.search(r"QLDPC_NOALLOC_SCRATCH_BYTES\s*=\s*([0-9 *]+)", text)
+    assert m
+    size = 1
+    for f in m.group(1).split("*"):
+        size *= int(f)
+    assert q.qldpc_noalloc_scratch_bytes() == size == q.QLDPC_NOALLOC_SCRATCH_BYTES
+
+
 def test_status_strings(q):
     assert q.qldpc_status_string(0) == b"QLDPC_OK"
     for code in (-1, -2, -3, -4, -5):

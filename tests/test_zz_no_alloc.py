@@ -89,6 +89,36 @@ def test_noalloc_rejects_batches_beyond_the_scratch(q):
     assert rc == q.QLDPC_OK and (iters == 0).all() and (ok == 1).all()
 
 
+def test_noalloc_allocates_nothing_once_warm(q):
+    """After the start-up zero-shot call and one call of each kind (which may load kernel code), a
+    series of further calls of every kind and size leaves the device's free memory unchanged, and
+    the scratch size the binding uses is the one compiled into the library."""
+    assert q.qldpc_noalloc_scratch_bytes() == q.QLDPC_NOALLOC_SCRATCH_BYTES
+    code = w.lp_code(1054)
+    graph = q.Graph.from_csr(code.hz_csr)
+    graph.set_weights(np.random.default_rng(5).uniform(0.6, 0.9, (6, code.hz_csr.nnz)).astype(np.float32))
+    b = w.x_error_batch(code, 0.04, 2000, seed=75)
+    kinds = [("fp32", 0), ("int16", 0), ("int8", 0), ("fp32", q.QLDPC_LAYERED),
+             ("int16", q.QLDPC_LAYERED | q.QLDPC_NO_EARLY_STOP), ("int8", q.QLDPC_NO_EARLY_STOP),
+             ("fp32", q.QLDPC_LEARNED)]
+    sizes = (1, 97, 2000)                       # single-shot and batch kernels
+    assert q.qldpc_decode_host_noalloc(graph.handle, None, 0, None, 50, 0.75, None, None, None,
+                                       q.QLDPC_FP32, 0, None) == q.QLDPC_OK
+    for prec, flags in kinds:
+        for shots in sizes:
+            rc, *_ = noalloc(q, graph, b.syndromes[:shots], b.prior, 50, 0.75, prec, flags)
+            assert rc == q.QLDPC_OK, (prec, flags, shots)
+    torch.cuda.synchronize()
+    free_before = torch.cuda.mem_get_info()[0]
+    for rep in range(2):
+        for prec, flags in kinds:
+            for shots in sizes:
+                rc, err, iters, ok = noalloc(q, graph, b.syndromes[:shots], b.prior, 50, 0.75, prec, flags)
+                assert rc == q.QLDPC_OK and (iters >= 0).all()
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free_before
+
+
 def test_noalloc_validates_before_enqueueing(q):
     code = w.bb_code(12, 6)
     graph = q.Graph.from_csr(code.hz_csr)

@@ -336,7 +336,9 @@ int oracle_msa_i8(const int32_t *row_ptr, const int32_t *col_idx, int32_t m, int
  *            Q_n     = q_{m,n} + r_{m,n}                     (with the new r)
  *   after the last check: e_n = [Q_n < 0] and the stop test, exactly as for flooding (iteration-0
  *   test, early stop, ok, iters).
- * i16: Q in int32 (not clamped), q = clamp(Q - r, +-32767), |r| = floor(min * alpha_q / 2^15).
+ * Fixed point (i16, i8): the a-posteriori LLR stays the exact 32-bit sum of Algorithm 1's APP step,
+ * Q_n = gamma_n + sum_m r_{m,n}, updated per check as Q_n <- Q_n - r_old + r_new; only the check's
+ * input is clamped, q = clamp(Q - r_old, +-lim), and |r| = floor(min * alpha_q / 2^15).
  * --------------------------------------------------------------------------------------------- */
 #define DEFINE_LAYERED_REAL(NAME, REAL, FABS)                                                     \
 int NAME(const int32_t *row_ptr, const int32_t *col_idx, int32_t m, int32_t n,                   \
@@ -448,7 +450,7 @@ static int layered_fixed(const int32_t *row_ptr, const int32_t *col_idx, int32_t
                         rn[i] = neg ? -mag : mag;
                     }
                     for (int32_t i = row_ptr[c]; i < row_ptr[c + 1]; ++i) {
-                        Q[col_idx[i]] = q[i] + rn[i];
+                        Q[col_idx[i]] = Q[col_idx[i]] - r[i] + rn[i];   /* exact: Q = gamma + sum r */
                         r[i] = rn[i];
                     }
                 }

@@ -58,6 +58,29 @@ def test_two_check_hand_example(precision):
     np.testing.assert_array_equal(llr(two, precision)[0], [6.0, 6.0, 6.0])
 
 
+@pytest.mark.parametrize("precision,gamma,lim", [("i8", 31.0, 127), ("i16", 120.0, 32767)])
+def test_fixed_point_clamp_feeds_only_the_check(precision, gamma, lim):
+    """Chain c0 = {0, 1}, c1 = {1, 2}, s = 0, alpha = 1, every prior gamma_q = g (i8: 4 * 31 = 124,
+    i16: 256 * 120 = 30720), worked by hand with the messages' clamp L (127, 32767) active.
+    The a-posteriori LLR stays the exact sum gamma + sum r (Algorithm 1's APP step); only the
+    check's input q = clamp(Q - r_old) is clamped.
+    Iteration 1: c0: q = (g, g) -> r = (g, g), Q_0 = Q_1 = 2g; c1: q = (clamp(2g) = L, g) ->
+    r = (g, L), Q_1 = 2g + g = 3g, Q_2 = g + L.
+    Iteration 2: c0: q = (clamp(2g - g) = g, clamp(3g - g) = L) -> r = (L, g): Q_0 = 2g - g + L,
+    Q_1 = 3g - g + g; c1: q = (clamp(3g - g) = L, clamp(g + L - L) = g) -> r = (g, L): Q_1 = 3g,
+    Q_2 = g + L.  So Q = [g + L, 3g, g + L], what flooding gives on this chain, where rebuilding Q
+    from the clamped q would cap the middle variable at L + g."""
+    h = np.array([[1, 1, 0], [0, 1, 1]], dtype=np.uint8)
+    g = int(gamma * (4 if precision == "i8" else 256))
+    assert 2 * g > lim >= g
+    one = run(h, [0, 0], np.full(3, gamma), 1, 1.0, precision, early_stop=False)
+    np.testing.assert_array_equal(one["post"][0], [2 * g, 3 * g, g + lim])
+    two = run(h, [0, 0], np.full(3, gamma), 2, 1.0, precision, early_stop=False)
+    np.testing.assert_array_equal(two["post"][0], [g + lim, 3 * g, g + lim])
+    flood = run(h, [0, 0], np.full(3, gamma), 2, 1.0, precision, early_stop=False, schedule="flooding")
+    np.testing.assert_array_equal(two["post"][0], flood["post"][0])
+
+
 def test_degree_one_variables_make_the_schedule_irrelevant():
     """Every variable in exactly one check: flooding and layered coincide at every iteration (i16:
     (Q - r) + r' is exact integer arithmetic)."""

@@ -9,20 +9,20 @@ outputs per step, more than the 129 MB L2).
 Printed as one JSON line on rank 0:
   value        syndromes/s of the device-resident decode (inputs in HBM), whole job
   e2e          the same through qldpc_decode_host with pinned HOST buffers (copies timed)
-  latency      single-shot (B = 1) end-to-end latency percentiles vs the 63 us threshold, through
-               the launch path (qldpc_decode_host) and the persistent server (qldpc_server_*)
-  serving      the persistent server under a 40/40/20 mix of the N=400, 1054 and 288 codes with
-               Poisson arrivals 20 us apart: latency percentiles and the saturated request rate
-  precisions   the same batches decoded in FP32, INT16 and INT8 (device throughput, decoded fraction)
-  layered      the row-serial (layered) schedule on the same batches and shots: device throughput,
-               mean iterations, decode success, and single-shot latency through qldpc_decode_host
-  learned      the learned (neural) min-sum on the same code: training time and kernel times on
-               2e6 device-sampled shots (T = 20, batch 4096, Adam lr 1e-3, p uniform in
-               [0.02, 0.06]), then logical error rates of learned and plain decoding on 1e6 fresh
-               shots
-  roofline     the decoder kernel against the SM integer/FP32 issue roof ("alu")
+  roofline     the decoder kernel against its binding on-chip roof (shared-memory message traffic),
+               with the ALU-issue and HBM roofs beside it
   cpu_baseline the CPU oracle on a bounded sample of the same workload, all host cores
   clocks       SM clock and throttle reasons sampled during the timed region
+  details      latency      single-shot (B = 1) end-to-end latency percentiles vs the 63 us
+                            threshold: launch path and persistent server, flooding and layered
+               paper_mode   the paper's timing conditions: BB-144 X+Z pair in one launch, FP32,
+                            10 iterations, no early stop, B = 1, end to end (host buffers)
+               bb_sweep     BB-144 / BB-288 pair, depolarizing p = 0.01..0.05, max 64, B = 1
+               configs      HGP-400 1000-shot batch; LP-1054 at B = 64, 4096, 65536 (FP32/INT16/INT8)
+               serving      the persistent server under a 40/40/20 mix of the N=400, 1054 and 288
+                            codes, Poisson arrivals 20 us apart, per-code learned / plain weights
+               precisions, layered, learned, soft_syndrome
+  headline     the headline scalars, last on the line
 
 ``--impl reference`` times the CPU oracle (the reference arm) on the same workload instead.
 """
@@ -53,7 +53,8 @@ LAT_P = 0.03
 LAT_SHOTS = 10000
 LAT_WARMUP = 200
 THRESHOLD_US = 63.0
-SERVE_REQUESTS = 100000
+SERVE_REQUESTS = 1_000_000   # FP32 mixed stream (learned LP-1054, plain HGP-400 / BB-288)
+SERVE_REQUESTS_FIXED = 100_000   # the INT16 / INT8 mixed streams and the saturated replays
 SERVE_GAP_NS = 20000         # mean Poisson inter-arrival
 SERVE_MIX = (0.4, 0.4, 0.2)  # N=400 HGP, N=1054 LP, N=288 BB (H_Z, i.i.d. X noise at p = 0.03)
 LAT_SERVER_GAP_NS = 50000    # isolated single-shot requests through the server
@@ -64,6 +65,7 @@ LEARN_LR = 1e-3
 LEARN_P = (0.02, 0.06)       # per-shot rate range, training and evaluation
 LEARN_EVAL = 1_000_000       # fresh evaluation shots
 LEARN_SEEDS = (7, 99)        # training, evaluation
+LEARN_INIT = 0.7             # initial weight of the configured run: the best constant scale untrained
 # Algorithmic operations per edge per iteration: check step |q|, sign parity, three min/max, select,
 # alpha multiply, sign apply; variable step add and extrinsic add.  Seven of them (all but the
 # multiply and the two adds) are ALU-pipe work.
@@ -71,13 +73,37 @@ OPS_PER_EDGE_ITER = 10
 ALU_OPS_PER_EDGE_ITER = 7
 ALU_LANES_PER_SM = 128          # FP32/INT32 lanes per SM, one operation per lane per clock
 ALU_PIPE_LANES_PER_SM = 64      # the ALU pipe (integer, logic, compare, min/max) is half rate
+# Shared-memory message traffic per edge per iteration: the check step reads q and writes r, the
+# variable step reads r and writes q (4 accesses of one message: 16 B FP32, 8 B INT16, 4 B INT8).
+SMEM_ACCESSES_PER_EDGE_ITER = 4
+MSG_BYTES = {"fp32": 4, "int16": 2, "int8": 1}
+SMEM_BYTES_PER_CLK_PER_SM = 128  # 32 banks x 4 B
 
-# DRAM traffic of one decoder launch from an ncu capture, valid only for the kernel source it was
-# measured on (profiles/msa_batch_lp1054_b65536_fp32.md); reported as null once the source changes.
-NCU_TRAFFIC = {"source_sha16": "1a1f4f5b43445955", "bytes_per_launch": 30665216 + 11027456,
-               "profile": "profiles/msa_batch_lp1054_b65536_fp32.md"}
+# DRAM bytes of one decoder launch on the benchmark batch, from one ncu capture (the sum of
+# dram__bytes_read.sum and dram__bytes_write.sum), valid only for the kernel source it was taken
+# on (sha256 prefix of msa_kernel.cuh); null once that source changes.
+NCU_TRAFFIC = {"source_sha16": "1a1f4f5b43445955", "bytes_per_launch": 30665216 + 11027456}
 
+FALLBACK_HBM_GBS = 6800.0     # the profiling recipe's fallback when MEASURED_PEAKS.json is absent
 WORKLOAD = "LP-1054 H_Z (465x1054, E=3720), iid X noise p=0.01..0.05, B=65536/step, max 50 it, alpha 0.75"
+
+
+def measured_hbm():
+    """(HBM copy GB/s, basis) from MEASURED_PEAKS.json beside this file, else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs (of measured)"
+    except (OSError, ValueError, KeyError):
+        return FALLBACK_HBM_GBS, "6.8 TB/s (of fallback)"
+
+
+def bench_config(batch: int, world: int, precision: str) -> dict:
+    """The workload description both arms print."""
+    return {"workload": WORKLOAD, "global_batch": batch * world, "precision": precision,
+            "l2": "inputs rotate over 5 batches (152 MB) + 69 MB outputs per step > 129 MB L2",
+            "rates": "step i decodes the batch of p = 0.01, 0.02, ..., 0.05 at i mod 5; a step count "
+                     "that is a multiple of 5 weights the five rates equally",
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
 
 
 def parse():
@@ -242,20 +268,22 @@ def oracle_single_thread(batches, precision: str, shots: int = 2000):
 
 
 def run_reference(args, rank, world):
+    """The reference arm: the CPU oracle, as it stands, on all host cores.  Each step decodes the
+    same sample the cpu_baseline leg uses, 8192 shots of one rate's benchmark batch, cycling
+    p = 0.01..0.05."""
     if rank != 0:
         return 0
     threads = os.cpu_count() or 1
-    per_step = 256
-    code, batches = make_batches(max(per_step * 4, 4096), 0)
+    per_step = CPU_SHOTS_PER_P
+    code, batches = make_batches(per_step, 0)
     import oracle
     oracle.build()
     oprec = {"fp32": "f32", "int16": "i16"}[args.precision]
 
     def step(i):
         b = batches[i % len(batches)]
-        lo = (i // len(batches)) * per_step % (b.syndromes.shape[0] - per_step + 1)
-        oracle.msa(b.h.row_ptr, b.h.col_idx, b.h.m, b.h.n, b.syndromes[lo:lo + per_step], b.prior,
-                   MAX_ITER, ALPHA, oprec, True, threads=threads)
+        oracle.msa(b.h.row_ptr, b.h.col_idx, b.h.m, b.h.n, b.syndromes, b.prior, MAX_ITER, ALPHA, oprec, True,
+                   threads=threads)
 
     for i in range(args.warmup):
         step(i)
@@ -270,9 +298,11 @@ def run_reference(args, rank, world):
         "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"fp32": "f32", "int16": "i16"}[args.precision],
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "reference_step": f"{per_step} shots on the CPU oracle"},
+        "config": bench_config(BATCH, world, args.precision),
         "cpu_baseline": {"value": value, "unit": "syndromes/s", "cores": threads, "kind": "oracle",
-                         "sample": f"{args.steps} steps x {per_step} shots cycling p=0.01..0.05",
+                         "sample": f"{args.steps} steps x {per_step} shots (the first {per_step} shots of the "
+                                   f"benchmark batch of one rate per step, cycling p=0.01..0.05), the sample the "
+                                   f"cpu_baseline leg of the GPU arm decodes",
                          "single_thread": oracle_single_thread(batches, args.precision, 500)},
         "e2e": {"value": value, "unit": "syndromes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -341,49 +371,34 @@ def run_ours(args, rank, world, local):
     value = world * B * args.steps / (ms / 1e3)
     launches = args.steps
 
-    # roofline of the decoder kernel (one launch per step)
-    sum_iters = sum(iters_per_batch[i % len(batches)] for i in range(args.steps))
-    ops = OPS_PER_EDGE_ITER * h.nnz * sum_iters / args.steps          # per launch
-    achieved = ops / (ms_per_step / 1e3) / 1e12                        # Tops/s
+    # roofline of the decoder kernel (one launch per step); the units of one launch are the
+    # edge-iterations it runs: E x (iterations summed over its 65536 shots)
     props = torch.cuda.get_device_properties(dev)
     clocks = clk.summary()
-    max_mhz = clocks["sm_max_mhz"] or 2070.0
-    peak = props.multi_processor_count * ALU_LANES_PER_SM * max_mhz * 1e6 / 1e12
-    roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3),
-                "unit": "Tops/s", "frac": round(achieved / peak, 4),
-                "traffic": kernel_traffic() if B == BATCH and args.precision == "fp32" else None,
-                "kernel": "msa_batch_kernel", "ops_per_launch": ops,
-                "units": "10 ALU ops per edge per iteration x E=3720 x iterations run",
-                "peak_basis": f"{props.multi_processor_count} SMs x {ALU_LANES_PER_SM} lanes x {max_mhz:.0f} MHz (max SM clock)",
-                # the op mix on the half-rate ALU pipe: 7 ALU-pipe ops per 10 bound the rate
-                "op_mix_peak": round(peak * (ALU_PIPE_LANES_PER_SM / ALU_LANES_PER_SM)
-                                     * OPS_PER_EDGE_ITER / ALU_OPS_PER_EDGE_ITER, 3),
-                "op_mix_frac": round(achieved / (peak * (ALU_PIPE_LANES_PER_SM / ALU_LANES_PER_SM)
-                                                 * OPS_PER_EDGE_ITER / ALU_OPS_PER_EDGE_ITER), 4),
-                "hbm_algorithmic_gbs": round((h.m + h.n + 5) * B / (ms_per_step / 1e3) / 1e9, 2),
-                "hbm_peak_gbs_measured": 6758.9}
+    roofline = decoder_roofline(h, B, iters_per_batch, args.steps, ms_per_step, args.precision,
+                                props.multi_processor_count, clocks["sm_max_mhz"] or 2070.0)
 
     e2e = None
     if not args.no_e2e:
         e2e = measure_e2e(qldpc, graph, batches, args, B, world, dev)
-    latency = None
-    if not args.no_latency and rank == 0:
-        latency = measure_latency(qldpc, graph, code, args)
-    serving = None
-    if not args.no_serving and rank == 0:
-        serving = measure_serving(qldpc, args)
-    precisions = None
-    if not args.no_precisions and rank == 0:
-        precisions = measure_precisions(qldpc, graph, syn_d, pri_d, out, stream, B, args)
-    layered_res = None
-    if not args.no_layered and rank == 0:
-        layered_res = measure_layered(qldpc, graph, code, syn_d, pri_d, out, stream, B, args)
-    learned_res = None
-    if not args.no_learned and rank == 0:
-        learned_res = measure_learned(qldpc, args)
-    soft_res = None
-    if not args.no_soft and rank == 0:
-        soft_res = measure_soft_syndrome(qldpc, args)
+    details = {}
+    if rank == 0:
+        if not args.no_latency:
+            details["latency"] = measure_latency(qldpc, graph, code, args)
+            details["paper_mode"] = measure_paper_mode(qldpc, args)
+            details["bb_sweep"] = measure_bb_sweep(qldpc, args)
+        if not args.no_precisions:
+            details["precisions"] = measure_precisions(qldpc, graph, syn_d, pri_d, out, stream, B, args)
+            details["configs"] = measure_configs(qldpc, graph, syn_d, pri_d, args)
+        if not args.no_layered:
+            details["layered"] = measure_layered(qldpc, graph, code, syn_d, pri_d, out, stream, B, args)
+        learned_weights = None
+        if not args.no_learned:
+            details["learned"], learned_weights = measure_learned(qldpc, args)
+        if not args.no_serving:
+            details["serving"] = measure_serving(qldpc, args, learned_weights)
+        if not args.no_soft:
+            details["soft_syndrome"] = measure_soft_syndrome(qldpc, args)
     cpu = None
     if not args.no_cpu_baseline and rank == 0 and world == 1:
         threads = os.cpu_count() or 1
@@ -399,28 +414,98 @@ def run_ours(args, rank, world, local):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp32": "f32", "int16": "i16"}[args.precision], "data": "synthetic",
-            "config": {"workload": WORKLOAD, "global_batch": B * world, "precision": args.precision,
-                       "l2": "inputs rotate over 5 batches (152 MB) + 69 MB outputs per step > 129 MB L2",
-                       "rates": "step i decodes the batch of p = 0.01, 0.02, ..., 0.05 at i mod 5; a step count "
-                                "that is a multiple of 5 weights the five rates equally",
-                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "config": bench_config(B, world, args.precision),
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "latency": latency,
-            "serving": serving,
-            "precisions": precisions,
-            "layered": layered_res,
-            "learned": learned_res,
-            "soft_syndrome": soft_res,
             "gpu_launches": launches,
             "clocks": clocks,
             "mean_iters": sum(iters_per_batch) / (len(iters_per_batch) * B),
+            "details": details,
         }
+        line["headline"] = headline(line)      # last, so that the end of the line carries it
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def decoder_roofline(h, B, iters_per_batch, steps, ms_per_step, precision, sms, max_mhz):
+    """Algorithmic work of one launch against the kernel's roofs.  The binding roof is the one with
+    the longest time at peak: shared-memory message traffic (4 accesses of one message per edge and
+    iteration, 32 banks x 4 B per clock per SM) or ALU issue (10 operations per edge and iteration,
+    128 lanes per SM per clock); HBM (syndromes in, decisions, iterations and ok out) is far below
+    either."""
+    edge_iters = h.nnz * sum(iters_per_batch[i % len(iters_per_batch)] for i in range(steps)) / steps
+    t = ms_per_step / 1e3
+    smem_bytes = SMEM_ACCESSES_PER_EDGE_ITER * MSG_BYTES[precision] * edge_iters
+    smem_peak = sms * SMEM_BYTES_PER_CLK_PER_SM * max_mhz * 1e6
+    ops = OPS_PER_EDGE_ITER * edge_iters
+    alu_peak = sms * ALU_LANES_PER_SM * max_mhz * 1e6
+    hbm_bytes = (h.m + h.n + 5) * B
+    hbm_gbs, hbm_basis = measured_hbm()
+    hbm_peak = hbm_gbs * 1e9
+    smem = {"achieved": round(smem_bytes / t / 1e9, 1), "peak": round(smem_peak / 1e9, 1), "unit": "GB/s",
+            "frac": round(smem_bytes / t / smem_peak, 4), "time_at_peak_ms": round(smem_bytes / smem_peak * 1e3, 4),
+            "bytes_per_launch": smem_bytes,
+            "units": f"{SMEM_ACCESSES_PER_EDGE_ITER} x {MSG_BYTES[precision]} B per edge-iteration x E={h.nnz} x "
+                     f"iterations run",
+            "peak_basis": f"{sms} SMs x {SMEM_BYTES_PER_CLK_PER_SM} B/clk x {max_mhz:.0f} MHz (derived)"}
+    alu = {"achieved": round(ops / t / 1e12, 3), "peak": round(alu_peak / 1e12, 3), "unit": "Tops/s",
+           "frac": round(ops / t / alu_peak, 4), "time_at_peak_ms": round(ops / alu_peak * 1e3, 4),
+           "ops_per_launch": ops,
+           "units": f"{OPS_PER_EDGE_ITER} ALU ops per edge-iteration x E={h.nnz} x iterations run",
+           "peak_basis": f"{sms} SMs x {ALU_LANES_PER_SM} lanes x {max_mhz:.0f} MHz (derived)",
+           "op_mix_frac": round(ops / t / (alu_peak * (ALU_PIPE_LANES_PER_SM / ALU_LANES_PER_SM)
+                                            * OPS_PER_EDGE_ITER / ALU_OPS_PER_EDGE_ITER), 4)}
+    hbm = {"achieved": round(hbm_bytes / t / 1e9, 2), "peak": hbm_gbs, "unit": "GB/s",
+           "frac": round(hbm_bytes / t / hbm_peak, 5), "bytes_per_launch": hbm_bytes, "peak_basis": hbm_basis}
+    binding = "smem" if smem["time_at_peak_ms"] >= alu["time_at_peak_ms"] else "alu"
+    top = smem if binding == "smem" else alu
+    traffic = kernel_traffic() if (B == BATCH and precision == "fp32") else None
+    return {"bound": binding, "achieved": top["achieved"], "peak": top["peak"], "unit": top["unit"],
+            "frac": top["frac"], "traffic": traffic,
+            "traffic_source": {"kind": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch",
+                               "source_sha16": NCU_TRAFFIC["source_sha16"],
+                               "current": traffic is not None},
+            "kernel": "msa_batch_kernel", "smem": smem, "alu": alu, "hbm": hbm}
+
+
+def headline(line) -> dict:
+    """The headline scalars (BASELINE metric: p99 single-shot latency vs 63 us, syndromes/s, learned
+    vs plain LER), with the paper's own figures as context."""
+    d = line.get("details", {})
+    lat, pm, srv, lay, prec, lrn = (d.get(k) or {} for k in ("latency", "paper_mode", "serving", "layered",
+                                                            "precisions", "learned"))
+    g = lambda obj, *ks: _dig(obj, ks)
+    out = {
+        "syndromes_per_s": round(line["value"]),
+        "e2e_syndromes_per_s": round(g(line, "e2e", "value") or 0) or None,
+        "roofline": f"{line['roofline']['bound']} {line['roofline']['frac']}",
+        "latency_p50_us": g(lat, "p50_us"), "latency_p99_us": g(lat, "p99_us"),
+        "latency_p999_us": g(lat, "p999_us"), "latency_path": g(lat, "headline"),
+        "layered_p99_us": g(lat, "layered_p99_us"),
+        "launch_path_p99_us": g(lat, "launch_path", "fp32", "p99_us"),
+        "paper_mode_bb144_pair_mean_us": g(pm, "launch_path", "mean_us"),
+        "paper_mode_bb144_pair_p99_us": g(pm, "launch_path", "p99_us"),
+        "serving_p99_us": g(srv, "fp32", "p99_us"), "serving_p999_us": g(srv, "fp32", "p999_us"),
+        "serving_saturated_per_s": g(srv, "fp32", "saturated_shots_per_s"),
+        "int16_syndromes_per_s": g(prec, "int16", "value"), "int8_syndromes_per_s": g(prec, "int8", "value"),
+        "layered_syndromes_per_s": g(lay, "value"),
+        "ler_plain_20": g(lrn, "ler", "plain_20"), "ler_learned_20": g(lrn, "ler", "learned_20"),
+        "iters_plain_20": g(lrn, "mean_iters", "plain_20"), "iters_learned_20": g(lrn, "mean_iters", "learned_20"),
+        "learned_minus_plain_ci95": g(lrn, "paired", "learned_20|plain_20", "ci95"),
+        "paper_context": "avg 23.3-62.9 us end to end, FP32, 10 it., RTX 3090/4090 (Sec. 3); 63 us threshold",
+    }
+    return {k: (round(v, 3) if isinstance(v, float) else v) for k, v in out.items()}
+
+
+def _dig(obj, keys):
+    for k in keys:
+        if not isinstance(obj, dict) or k not in obj:
+            return None
+        obj = obj[k]
+    return obj
 
 
 def measure_soft_syndrome(qldpc, args, q=0.01, shots=65536, evaluated=16384, steps=20):
@@ -556,43 +641,238 @@ def measure_latency(qldpc, graph, code, args):
     out["p999_us"] = srv_lat["fp32"]["p999_us"]
     out["headline"] = "server_path fp32"
     out["layered_p99_us"] = out["server_layered_path"]["fp32"]["p99_us"]
+    out["layered_per_code"] = measure_layered_codes(qldpc, args)
     return out
 
 
-def measure_serving(qldpc, args):
-    """Config 5: Poisson arrivals of syndrome rounds mixed 40/40/20 from three codes."""
+def layered_serving_code(name):
+    """A serving code's H_Z in the row order the layered workers use: LP-1054 as built (7 layers);
+    HGP-400 and BB-288 reordered by workloads.layer_order (15 -> 7 and 56 -> 3 layers).  Returns
+    (H, row order) with the syndromes of H = the original syndromes[:, order]."""
+    from paper_2508_07879_gb300 import workloads as w
+    h = w.CONFIG_CODES[name]().hz_csr
+    if name == "lp1054":
+        return h, np.arange(h.m)
+    order = w.layer_order(h)
+    return w.csr_rows(h, order), order
+
+
+def measure_layered_codes(qldpc, args, shots=None):
+    """Isolated single-shot requests (50 us apart, p = 0.03) of each serving code to a layered-schedule
+    server of that code alone, FP32, INT16 and INT8: latency percentiles and iterations."""
+    from paper_2508_07879_gb300 import workloads as w
+    shots = shots or max(1000, args.latency_shots // 2)
+    warm = min(LAT_WARMUP, max(shots // 10, 10))
+    res = {}
+    for name in ("hgp400", "lp1054", "bb288"):
+        h, order = layered_serving_code(name)
+        b = w.x_error_batch(w.CONFIG_CODES[name](), LAT_P, shots + warm, seed=4103)
+        syn = np.ascontiguousarray(b.syndromes[:, order])
+        g = qldpc.Graph.from_csr(h)
+        layers, widest = g.layers(widest=True)
+        row = {"layers": layers, "widest_layer": widest, "row_order": "natural" if name == "lp1054" else "layer_order"}
+        for prec in ("fp32", "int16", "int8"):
+            with qldpc.Server([g], [b.prior], MAX_ITER, ALPHA, prec, blocks=[8], ring_capacity=1024,
+                              layered=True) as srv:
+                arrival = (np.arange(shots + warm) * LAT_SERVER_GAP_NS).astype(np.int64)
+                _, iters, ok, lat_ns = srv.replay(np.zeros(shots + warm, np.int32), list(syn), arrival)
+            x = lat_ns[warm:] / 1e3
+            row[prec] = {"p50_us": float(np.percentile(x, 50)), "p99_us": float(np.percentile(x, 99)),
+                         "p999_us": float(np.percentile(x, 99.9)), "mean_iters": float(iters[warm:].mean()),
+                         "decoded_fraction": float(ok[warm:].mean()),
+                         "max_iter_shots": int((iters[warm:] == MAX_ITER).sum())}
+        res[name] = row
+        g.close()
+    return res
+
+
+def measure_paper_mode(qldpc, args, shots=10000, warm=100):
+    """The paper's timing conditions (Sec. 3): X and Z decoded in one kernel, FP32, 10 iterations,
+    no early stop, B = 1, average end-to-end latency including the transfers.  BB-144 ([[144,12,12]],
+    the one code of the paper's set that is reproducible here), depolarizing p = 0.03; host clock
+    around qldpc_decode_pair_host with page-locked buffers (no copies: the kernel reads and writes
+    host memory), and the same pairs as two concurrent requests to the persistent server."""
+    import torch
+    from paper_2508_07879_gb300 import workloads as w
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    out = {"conditions": "FP32, 10 iterations, no early stop, B = 1, X+Z, end to end (host buffers)",
+           "paper": "[[144,12,12]] among the BB codes: about 28 us (RTX 4090) / 35 us (RTX 3090) average, Sec. 3"}
+    for name in ("bb144", "bb288"):
+        code = w.CONFIG_CODES[name]()
+        gz, gx = qldpc.Graph.from_csr(code.hz_csr), qldpc.Graph.from_csr(code.hx_csr)
+        ex, ez = w.depolarizing_errors(code.n, 0.03, shots + warm, seed=3203)
+        sx, sz = pin(w.syndromes(code.hz_csr, ex)), pin(w.syndromes(code.hx_csr, ez))
+        prior = np.full(code.n, w.prior_llr(2 * 0.03 / 3), dtype=np.float32)
+        outs = tuple((pin(np.zeros((1, code.n), np.uint8)), pin(np.zeros(1, np.int32)), pin(np.zeros(1, np.uint8)))
+                     for _ in range(2))
+        ts = np.empty(shots + warm)
+        for i in range(shots + warm):
+            t0 = time.perf_counter_ns()
+            qldpc.decode_pair_host(gz, gx, sx[i:i + 1], sz[i:i + 1], prior, prior, 10, ALPHA, "fp32", False, out=outs)
+            ts[i] = (time.perf_counter_ns() - t0) / 1e3
+        x = ts[warm:]
+        row = {"launch_path": {"path": "qldpc_decode_pair_host, one launch for X and Z",
+                               "mean_us": float(x.mean()), "p50_us": float(np.percentile(x, 50)),
+                               "p99_us": float(np.percentile(x, 99)), "p999_us": float(np.percentile(x, 99.9))}}
+        with qldpc.Server([gz, gx], [prior, prior], 10, ALPHA, "fp32", early_stop=False, blocks=[8, 8],
+                          ring_capacity=1024) as srv:
+            n = shots + warm
+            codes = np.tile(np.array([0, 1], np.int32), n)
+            syn = [r for pair in zip(sx, sz) for r in pair]
+            arrival = np.repeat(np.arange(n) * LAT_SERVER_GAP_NS, 2).astype(np.int64)
+            _, iters, _, lat_ns = srv.replay(codes, syn, arrival)
+        pair_us = np.maximum(lat_ns[0::2], lat_ns[1::2])[warm:] / 1e3
+        row["server_path"] = {"path": "the X and Z halves as two requests at the same instant to the persistent "
+                                      "server; latency = the later of the two",
+                              "mean_us": float(pair_us.mean()), "p50_us": float(np.percentile(pair_us, 50)),
+                              "p99_us": float(np.percentile(pair_us, 99)),
+                              "p999_us": float(np.percentile(pair_us, 99.9))}
+        row["shots"] = shots
+        out[name] = row
+        if name == "bb144":
+            out["launch_path"] = row["launch_path"]
+        gz.close()
+        gx.close()
+    return out
+
+
+def measure_bb_sweep(qldpc, args, shots=10000, warm=100):
+    """BB-144 and BB-288 single-shot latency sweep: depolarizing noise at p = 0.01..0.05 split into
+    its X and Z parts, both halves decoded in one launch (max 64 iterations, early stop), B = 1,
+    host clock around qldpc_decode_pair_host with page-locked buffers."""
+    import torch
+    from paper_2508_07879_gb300 import workloads as w
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    shots = min(shots, max(1000, args.latency_shots))
+    out = {"max_iter": 64, "shots_per_p": shots, "path": "qldpc_decode_pair_host (X+Z in one launch), FP32"}
+    for ci, name in enumerate(("bb144", "bb288")):
+        code = w.CONFIG_CODES[name]()
+        gz, gx = qldpc.Graph.from_csr(code.hz_csr), qldpc.Graph.from_csr(code.hx_csr)
+        outs = tuple((pin(np.zeros((1, code.n), np.uint8)), pin(np.zeros(1, np.int32)), pin(np.zeros(1, np.uint8)))
+                     for _ in range(2))
+        rows = {}
+        for pi, p in enumerate(P_GRID):
+            ex, ez = w.depolarizing_errors(code.n, p, shots + warm, seed=3001 + 100 * ci + pi)
+            sx, sz = pin(w.syndromes(code.hz_csr, ex)), pin(w.syndromes(code.hx_csr, ez))
+            prior = np.full(code.n, w.prior_llr(2 * p / 3), dtype=np.float32)
+            ts = np.empty(shots + warm)
+            both_ok = np.empty(shots + warm, dtype=bool)
+            its = np.empty(shots + warm)
+            for i in range(shots + warm):
+                t0 = time.perf_counter_ns()
+                qldpc.decode_pair_host(gz, gx, sx[i:i + 1], sz[i:i + 1], prior, prior, 64, ALPHA, "fp32", True,
+                                       out=outs)
+                ts[i] = (time.perf_counter_ns() - t0) / 1e3
+                both_ok[i] = outs[0][2][0] and outs[1][2][0]
+                its[i] = max(outs[0][1][0], outs[1][1][0])
+            x = ts[warm:]
+            rows[f"p={p}"] = {"mean_us": float(x.mean()), "p50_us": float(np.percentile(x, 50)),
+                              "p99_us": float(np.percentile(x, 99)), "p999_us": float(np.percentile(x, 99.9)),
+                              "decoded_fraction": float(both_ok[warm:].mean()),
+                              "mean_max_iters": float(its[warm:].mean())}
+        out[name] = rows
+        gz.close()
+        gx.close()
+    return out
+
+
+def measure_configs(qldpc, graph, syn_d, pri_d, args, steps=50):
+    """Config 1 (HGP-400, 1000 shots at p = 0.05, max 32, FP32 and INT16) and config 2 at B = 64
+    and 4096 (LP-1054, the benchmark batches, max 50): device throughput (CUDA events over repeated
+    launches), decoded fraction and mean iterations."""
+    import torch
+    from paper_2508_07879_gb300 import workloads as w
+
+    def timed(g, s, p, max_iter, prec):
+        res = qldpc.decode(g, s, p, max_iter, ALPHA, prec)
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record()
+        for _ in range(steps):
+            qldpc.decode(g, s, p, max_iter, ALPHA, prec)
+        ev[1].record()
+        torch.cuda.synchronize()
+        ms = ev[0].elapsed_time(ev[1]) / steps
+        return {"ms_per_launch": ms, "syndromes_per_s": s.shape[0] / (ms / 1e3),
+                "decoded_fraction": float(res[2].float().mean().item()),
+                "mean_iters": float(res[1].float().mean().item())}
+
+    out = {}
+    b = w.x_error_batch(w.hgp_code(400), 0.05, 1000, seed=1)
+    g = qldpc.Graph.from_csr(b.h)
+    s, p = torch.from_numpy(b.syndromes).cuda(), torch.from_numpy(b.prior).cuda()
+    out["c1_hgp400_b1000"] = {prec: timed(g, s, p, 32, prec) for prec in ("fp32", "int16", "int8")}
+    g.close()
+    for B in (64, 4096):
+        rows = {}
+        for prec in ("fp32", "int16", "int8"):
+            per_p = [timed(graph, syn_d[j][:B].contiguous(), pri_d[j], MAX_ITER, prec) for j in range(len(syn_d))]
+            ms = sum(r["ms_per_launch"] for r in per_p) / len(per_p)
+            rows[prec] = {"syndromes_per_s": B / (ms / 1e3), "ms_per_launch": ms,
+                          "decoded_fraction": sum(r["decoded_fraction"] for r in per_p) / len(per_p),
+                          "mean_iters": sum(r["mean_iters"] for r in per_p) / len(per_p)}
+        out[f"c2_lp1054_b{B}"] = rows
+    return out
+
+
+def measure_serving(qldpc, args, learned_weights=None):
+    """Config 5: Poisson arrivals (mean gap 20 us) of syndrome rounds mixed 40/40/20 from the N=400,
+    1054 and 288 codes (H_Z, iid X noise at p = 0.03) through one persistent server whose workers
+    serve every code.  FP32 with per-code weights (LP-1054 learned, when the learned section trained
+    them, then the plain fallback; HGP-400 and BB-288 plain), 10^6 requests; FP32 plain, INT16 and
+    INT8 over the first 10^5 requests of the same stream.  Requests cycle through 10^5 distinct
+    syndromes per code.  Latency = completion seen by the host - scheduled arrival."""
     from paper_2508_07879_gb300 import workloads as w
     rng = np.random.default_rng(5005)
     n = args.serve_requests
     codes = rng.choice(3, size=n, p=list(SERVE_MIX)).astype(np.int32)
     arrival = np.cumsum(rng.exponential(SERVE_GAP_NS, size=n)).astype(np.int64)
+    names = ("hgp400", "lp1054", "bb288")
     graphs, priors, rows = [], [], []
-    for ci, name in enumerate(("hgp400", "lp1054", "bb288")):
-        b = w.x_error_batch(w.CONFIG_CODES[name](), 0.03, int((codes == ci).sum()), seed=5001 + ci)
+    for ci, name in enumerate(names):
+        count = max(1, min(int((codes == ci).sum()), 100_000))
+        b = w.x_error_batch(w.CONFIG_CODES[name](), 0.03, count, seed=5001 + ci)
         graphs.append(qldpc.Graph.from_csr(b.h))
         priors.append(b.prior)
         rows.append(b.syndromes)
     cursor = [0, 0, 0]
     syn = []
     for c in codes:
-        syn.append(rows[c][cursor[c]])
+        syn.append(rows[c][cursor[c] % rows[c].shape[0]])
         cursor[c] += 1
     out = {"workload": "40/40/20 HGP-400 / LP-1054 / BB-288 (H_Z, iid X, p=0.03), Poisson mean gap 20 us",
            "requests": n, "max_iter": MAX_ITER}
-    for prec in ("fp32", "int16", "int8"):
-        with qldpc.Server(graphs, priors, MAX_ITER, ALPHA, prec, ring_capacity=4096) as srv:
-            _, _, _, lat_ns = srv.replay(codes, syn, arrival, timeout_s=60.0)
+    runs = [("fp32", "fp32", n, learned_weights is not None), ("fp32_plain", "fp32", SERVE_REQUESTS_FIXED, False),
+            ("int16", "int16", SERVE_REQUESTS_FIXED, False), ("int8", "int8", SERVE_REQUESTS_FIXED, False)]
+    for key, prec, count, use_learned in runs:
+        count = min(count, n)
+        if use_learned:
+            graphs[1].set_weights(learned_weights)
+        with qldpc.Server(graphs, priors, MAX_ITER, ALPHA, prec, ring_capacity=4096, learned=use_learned) as srv:
+            info = srv.info()
+            _, iters, _, lat_ns, workers = srv.replay(codes[:count], syn[:count], arrival[:count], timeout_s=60.0,
+                                                     want_workers=True)
+            sat = min(count, SERVE_REQUESTS_FIXED)
             t0 = time.perf_counter()
-            srv.replay(codes, syn, np.zeros(n, np.int64), timeout_s=60.0)
+            srv.replay(codes[:sat], syn[:sat], np.zeros(sat, np.int64), timeout_s=60.0)
             dt = time.perf_counter() - t0
+        if use_learned:
+            graphs[1].set_weights(None)
         x = lat_ns / 1e3
         per = {}
-        for ci, name in enumerate(("hgp400", "lp1054", "bb288")):
-            xs = x[codes == ci]
-            per[name] = {"p50_us": float(np.percentile(xs, 50)), "p99_us": float(np.percentile(xs, 99))}
-        out[prec] = {"p50_us": float(np.percentile(x, 50)), "p99_us": float(np.percentile(x, 99)),
-                     "p999_us": float(np.percentile(x, 99.9)), "per_code": per,
-                     "saturated_shots_per_s": n / dt}
+        for ci, name in enumerate(names):
+            sel = codes[:count] == ci
+            xs = x[sel]
+            per[name] = {"p50_us": float(np.percentile(xs, 50)), "p99_us": float(np.percentile(xs, 99)),
+                         "mean_iters": float(iters[sel].mean()), "distinct_workers": int(len(set(workers[sel].tolist())))}
+        out[key] = {"requests": count, "p50_us": float(np.percentile(x, 50)), "p99_us": float(np.percentile(x, 99)),
+                    "p999_us": float(np.percentile(x, 99.9)), "mean_us": float(x.mean()), "per_code": per,
+                    "saturated_shots_per_s": sat / dt, "saturated_requests": sat,
+                    "offered_per_s": 1e9 / SERVE_GAP_NS, "workers": info["workers"],
+                    "threads_per_block": info["threads_per_block"], "smem_per_block": info["smem_per_block"],
+                    "weights": "LP-1054 learned (configured training run), others plain" if use_learned else "plain"}
+    for g in graphs:
+        g.close()
     return out
 
 
@@ -708,10 +988,19 @@ def measure_learned(qldpc, args):
                            p_hi=LEARN_P[1], seed=LEARN_SEEDS[1])
     ler = {k: v["ler"] for k, v in res.items()}
     iters = {k: v["mean_iters"] for k, v in res.items()}
-    # (key prefix, loss, Adam lr): the configured lr, and the syndrome loss at a larger step
-    runs = (("", "syndrome", LEARN_LR), ("lr1e-2_", "syndrome", 1e-2), ("error_loss_", "error", LEARN_LR))
-    for prefix, loss, lr in runs:
-        model = learned.NeuralMinSum(h, prior, T=LEARN_T, max_batch=LEARN_BATCH, graph=g, loss=loss)
+    # the plain decoder at the initial weight of the configured run, for context
+    res = learned.evaluate(g, prior, logicals, {"plain_20": (20, False)}, shots=args.learned_eval_shots,
+                           p_lo=LEARN_P[0], p_hi=LEARN_P[1], seed=LEARN_SEEDS[1], alpha=LEARN_INIT)
+    ler[f"plain_20_alpha{LEARN_INIT}"] = res["plain_20"]["ler"]
+    iters[f"plain_20_alpha{LEARN_INIT}"] = res["plain_20"]["mean_iters"]
+    paired = {}
+    configured = None
+    # (key prefix, loss, Adam lr, initial weight): the configured run (syndrome loss, lr 1e-3, started
+    # at the best constant scale of the untrained sweep), the same from 0.75, a larger step, the error loss
+    runs = (("", "syndrome", LEARN_LR, LEARN_INIT), ("init0.75_", "syndrome", LEARN_LR, 0.75),
+            ("lr1e-2_", "syndrome", 1e-2, 0.75), ("error_loss_", "error", LEARN_LR, 0.75))
+    for prefix, loss, lr, init in runs:
+        model = learned.NeuralMinSum(h, prior, T=LEARN_T, init=init, max_batch=LEARN_BATCH, graph=g, loss=loss)
         # kernel times of one training step, events on the launching (current) stream
         err, syn = qldpc.sample_errors(g, LEARN_SEEDS[0] + 1000, 0, LEARN_BATCH, *LEARN_P)
         gl = torch.full((LEARN_BATCH,), 1.0 / LEARN_BATCH, device=syn.device)
@@ -743,14 +1032,22 @@ def measure_learned(qldpc, args):
         model.publish()
         t0 = time.perf_counter()
         res = learned.evaluate(g, prior, logicals, {"learned_20": (0, True), "learned_20_fallback_30": (30, True),
-                                                    "learned_20_fallback_50": (50, True)},
-                               shots=args.learned_eval_shots, p_lo=LEARN_P[0], p_hi=LEARN_P[1], seed=LEARN_SEEDS[1])
+                                                    "learned_20_fallback_50": (50, True), "plain_20": (20, False),
+                                                    "plain_50": (50, False)},
+                               shots=args.learned_eval_shots, p_lo=LEARN_P[0], p_hi=LEARN_P[1], seed=LEARN_SEEDS[1],
+                               paired=(("learned_20", "plain_20"), ("learned_20_fallback_50", "plain_50")))
         eval_s = time.perf_counter() - t0
-        ler.update({prefix + k: v["ler"] for k, v in res.items()})
-        iters.update({prefix + k: v["mean_iters"] for k, v in res.items()})
+        for k, v in res.items():
+            if k == "paired":
+                paired.update({prefix + pk: pv for pk, pv in v.items()})
+            elif not k.startswith("plain"):
+                ler[prefix + k] = v["ler"]
+                iters[prefix + k] = v["mean_iters"]
+        if not prefix:
+            configured = model.weights.detach().cpu().numpy().copy()
         wmean = model.weights.detach().mean(dim=1).cpu().numpy()
         out[(prefix or "syndrome_") + "training"] = {
-            "loss": loss, "lr": lr, "mean_weight_per_iteration": [round(float(x), 4) for x in wmean],
+            "loss": loss, "lr": lr, "init": init, "mean_weight_per_iteration": [round(float(x), 4) for x in wmean],
             "train_s": train_s, "train_shots_per_s": steps * LEARN_BATCH / train_s,
             "loss_first": float(hist[0]) if len(hist) else None, "loss_last": float(hist[-1]) if len(hist) else None,
             "step_kernel_ms": {"forward": tf, "backward_and_reduce": tb},
@@ -760,9 +1057,12 @@ def measure_learned(qldpc, args):
         g.set_weights(None)
     out["ler"] = ler
     out["mean_iters"] = iters
-    out["learned_keys"] = ("learned_*: syndrome loss, lr 1e-3 (the configured run); lr1e-2_learned_*: syndrome "
-                           "loss, lr 1e-2; error_loss_learned_*: error loss, lr 1e-3")
-    return out
+    out["paired"] = paired
+    out["learned_keys"] = (f"learned_*: syndrome loss, lr 1e-3, weights started at {LEARN_INIT} (the configured run); "
+                           "init0.75_learned_*: the same started at 0.75; lr1e-2_learned_*: syndrome loss, lr 1e-2; "
+                           "error_loss_learned_*: error loss, lr 1e-3; paired: learned minus plain LER on the same "
+                           "shots with its 95 % CI (discordant-shot counts)")
+    return out, configured
 
 
 def main():

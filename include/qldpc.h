@@ -141,6 +141,12 @@ QLDPC_API void qldpc_graph_destroy(qldpc_graph *g);
 QLDPC_API int qldpc_graph_dims(const qldpc_graph *g, int32_t *m, int32_t *n, int32_t *nnz,
                      int32_t *max_row_degree, int32_t *max_col_degree);
 
+/* The layered schedule the graph's row order gives (QLDPC_LAYERED): each check goes to the layer one
+ * above the highest layer of an earlier row it shares a variable with, so the checks of a layer are
+ * independent.  Reports the number of layers and the largest layer (any output pointer may be
+ * NULL).  A caller who wants fewer layers reorders the rows of H, which is a different schedule. */
+QLDPC_API int qldpc_graph_layers(const qldpc_graph *g, int32_t *layers, int32_t *widest);
+
 /* On-chip footprint of the flooding kernels for one precision (QLDPC_FP32 / INT16 / INT8):
  *   lanes       variable lanes of the variable step, n plus idle lanes (variables are grouped by
  *               degree and packed into warps whose k-th edge slots fall in distinct shared-memory
@@ -237,6 +243,24 @@ QLDPC_API int qldpc_decode_host(qldpc_graph *g, const uint8_t *h_syndromes, int3
                       uint8_t *h_err, int32_t *h_iters, uint8_t *h_ok,
                       int32_t precision, uint32_t flags, void *stream);
 
+/*
+ * The X+Z pair decode of qldpc_decode_pair end to end with host buffers (the paper's latency
+ * measurement, Sec. 3: transfers included, both halves in one kernel).  Arguments as for
+ * qldpc_decode_pair, but every buffer is host memory: s_x [batch, m_z], s_z [batch, m_x], priors
+ * float[n] each, outputs e_hat [batch, n], iters [batch], ok [batch] per half.  g_z and g_x must be
+ * two different graphs (each stages its own half).  When every buffer lies in page-locked memory
+ * the kernel reads and writes them in place (no copies); otherwise they are staged through each
+ * graph's device staging (allocated on first use, as for qldpc_decode_host).  Synchronous: returns
+ * after the results are in the host buffers.  Arguments and the launch plan are checked before
+ * anything is enqueued (INVALID_ARG / UNSUPPORTED as for qldpc_decode_pair).
+ */
+QLDPC_API int qldpc_decode_pair_host(qldpc_graph *g_z, qldpc_graph *g_x, const uint8_t *h_sx,
+                                     const uint8_t *h_sz, int32_t batch, const float *h_prior_x,
+                                     const float *h_prior_z, int32_t max_iter, float alpha,
+                                     uint8_t *h_err_x, uint8_t *h_err_z, int32_t *h_iters_x,
+                                     int32_t *h_iters_z, uint8_t *h_ok_x, uint8_t *h_ok_z,
+                                     int32_t precision, uint32_t flags, void *stream);
+
 /* Static, human-readable name of a status code. */
 QLDPC_API const char *qldpc_status_string(int status);
 
@@ -244,14 +268,18 @@ QLDPC_API const char *qldpc_status_string(int status);
  * Persistent decoding server (continuous batching of single syndrome rounds).
  *
  * The paper proposes launching decoders asynchronously so transfers overlap execution (Table 1,
- * Sec. 3 outlook).  The server takes that to its limit: one kernel stays resident, its worker
- * blocks each hold one code's graph and priors on chip, and requests flow through per-code rings
- * of slots in page-locked host memory mapped into the GPU.  A request is admitted as soon as a
- * worker of its code is free; requests of different codes and sizes decode concurrently; results
- * come back in the slot.  Decoding is the single-shot algorithm of qldpc_decode_ex, so a request
- * decodes to the same result alone or in any mix.  Every device-side wait is bounded (idle
- * timeout, maximum runtime); the library relaunches the workers when requests arrive after they
- * left.  submit/poll/replay on one server are serialized by a lock inside it.
+ * Sec. 3 outlook).  The server takes that to its limit: one kernel stays resident and requests
+ * flow through per-code rings of slots in page-locked host memory mapped into the GPU, announced
+ * in arrival order through one shared queue.  Admission is by footprint: every worker block is
+ * sized for the largest footprint among the server's codes (threads, shared memory, registers),
+ * as many workers run as fit on the GPU at that footprint, and a request is admitted as soon as
+ * any worker is free, oldest first, whatever its code; a worker keeps the last code's graph and
+ * priors in registers and reloads them only when it switches codes.  Requests of different codes
+ * and sizes decode concurrently; results come back in the slot.  Decoding is the single-shot
+ * algorithm of qldpc_decode_ex, so a request decodes to the same result alone or in any mix.
+ * Every device-side wait is bounded (idle timeout, maximum runtime); the library relaunches the
+ * workers when requests arrive after they left.  submit/poll/replay on one server are serialized
+ * by a lock inside it.
  * =============================================================================================== */
 typedef struct qldpc_server qldpc_server;
 
@@ -264,13 +292,15 @@ typedef struct qldpc_server_config {
     uint32_t flags;               /* QLDPC_NO_EARLY_STOP, or QLDPC_LEARNED (FP32: every code whose
                                      graph has weights decodes learned, the others plainly), and/or
                                      QLDPC_LAYERED (workers on the layered schedule: results equal
-                                     qldpc_decode_ex with QLDPC_LAYERED; every code at most 8 layers
-                                     of rows of degree <= 8 and n <= 65536; not with QLDPC_LEARNED),
-                                     or 0 */
+                                     qldpc_decode_ex with QLDPC_LAYERED; rows of degree <= 8 and at
+                                     most 256 checks per layer; a code of at most 8 layers and
+                                     n <= 65536 keeps its checks in registers, any other its messages
+                                     in shared memory; not with QLDPC_LEARNED), or 0 */
     int32_t ring_capacity;        /* slots per code, a power of two in [2, 2^20]; 0 = 256 */
     int32_t threads_per_block;    /* 0 = automatic; QLDPC_LAYERED: a multiple of 32 in
                                      [widest layer, 256] */
-    int32_t blocks[QLDPC_SERVER_MAX_CODES];   /* worker blocks per code; 0 = equal share of the SMs */
+    int32_t blocks[QLDPC_SERVER_MAX_CODES];   /* the worker pool's size is the sum (every worker
+                                     serves every code); all 0 = as many as fit on the GPU */
     int64_t idle_timeout_ns;      /* workers leave after this long without a request; <= 0: 0.5 s */
     int64_t max_runtime_ns;       /* workers leave after this long; <= 0: 600 s */
 } qldpc_server_config;
@@ -298,13 +328,21 @@ QLDPC_API int qldpc_server_poll(qldpc_server *s, int32_t code, uint64_t ticket, 
 
 /* Open-loop load generator and latency recorder: submits request i (code codes[i], syndrome at
  * syndromes + syn_offsets[i]) at arrival_ns[i] after the call starts (non-decreasing), collects
- * every result (e_hat at errs + err_offsets[i], iters[i], oks[i]) and records latency_ns[i] =
- * completion seen by the host - scheduled arrival.  Returns QLDPC_ERR_TIMEOUT if results are still
- * missing timeout_ns after the last arrival (<= 0: 10 s). */
+ * every result (e_hat at errs + err_offsets[i], iters[i], oks[i], and in workers[i] the index of
+ * the worker block that decoded it, if workers is not NULL) and records latency_ns[i] = completion
+ * seen by the host - scheduled arrival.  A request whose ring is full waits until a result of that
+ * code is collected.  Returns QLDPC_ERR_TIMEOUT if results are still missing timeout_ns after the
+ * last arrival (<= 0: 10 s). */
 QLDPC_API int qldpc_server_replay(qldpc_server *s, int32_t nreq, const int32_t *codes,
                                   const uint8_t *syndromes, const int64_t *syn_offsets,
                                   const int64_t *arrival_ns, uint8_t *errs, const int64_t *err_offsets,
-                                  int32_t *iters, uint8_t *oks, int64_t *latency_ns, int64_t timeout_ns);
+                                  int32_t *iters, uint8_t *oks, int64_t *latency_ns, int32_t *workers,
+                                  int64_t timeout_ns);
+
+/* The worker pool: number of worker blocks and the footprint each has (threads, dynamic shared
+ * memory in bytes).  Any output pointer may be NULL. */
+QLDPC_API int qldpc_server_info(const qldpc_server *s, int32_t *workers, int32_t *threads_per_block,
+                                size_t *smem_per_block);
 
 /* Status bits the workers left: 1 = idle timeout, 2 = maximum runtime, 4 = spin cap, 8 = stopped. */
 QLDPC_API int qldpc_server_status(qldpc_server *s, uint32_t *status);

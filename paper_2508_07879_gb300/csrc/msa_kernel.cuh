@@ -53,7 +53,9 @@ struct F32 {
     // is -0 only when every term is), so the sign bit of a message equals [message < 0].
     static __device__ __forceinline__ acc_t quantize(float g) { return __fadd_rn(g, 0.0f); }
     static __device__ __forceinline__ acc_t add(acc_t a, acc_t b) { return __fadd_rn(a, b); }
-    static __device__ __forceinline__ acc_t sub_q(acc_t Q, acc_t r) { return __fsub_rn(Q, r); }   // layered q
+    // layered schedule: Q - r_old, and the check's input clamped to the message range (none here)
+    static __device__ __forceinline__ acc_t sub(acc_t Q, acc_t r) { return __fsub_rn(Q, r); }
+    static __device__ __forceinline__ acc_t clampq(acc_t x) { return x; }
     static __device__ __forceinline__ bool neg(float x) { return x < 0.0f; }
     static __device__ __forceinline__ mag_t mag(acc_t x) { return fabsf(x); }
     static __device__ __forceinline__ mag_t mag_init() { return __int_as_float(0x7f800000); }
@@ -106,8 +108,9 @@ struct IFix {
         return static_cast<int32_t>(t);
     }
     static __device__ __forceinline__ acc_t add(acc_t a, acc_t b) { return a + b; }
-    // layered schedule: q = clamp(Q - r)
-    static __device__ __forceinline__ acc_t sub_q(acc_t Q, acc_t r) { return max(-LIM, min(LIM, Q - r)); }
+    // layered schedule: Q - r_old exactly in 32 bits, and the check's input q = clamp(Q - r_old)
+    static __device__ __forceinline__ acc_t sub(acc_t Q, acc_t r) { return Q - r; }
+    static __device__ __forceinline__ acc_t clampq(acc_t x) { return max(-LIM, min(LIM, x)); }
     static __device__ __forceinline__ bool neg(int32_t x) { return x < 0; }
     static __device__ __forceinline__ mag_t mag(acc_t x) { return abs(x); }
     static __device__ __forceinline__ mag_t mag_init() { return 0x7fffffff; }
@@ -147,6 +150,7 @@ __device__ __forceinline__ void flip_check(uint32_t *parity, uint32_t m) { atomi
 // host verified for every slot (Granlund and Montgomery, PLDI 1994).
 struct CheckOf {
     uint32_t M, magic, shift;
+    __device__ __forceinline__ CheckOf() : M(1u), magic(0u), shift(0u) {}
     __device__ __forceinline__ explicit CheckOf(const DeviceGraph &g)
         : M(uint32_t(g.m)), magic(g.m_magic), shift(uint32_t(g.m_shift)) {}
     __device__ __forceinline__ uint32_t operator()(uint32_t slot) const

@@ -127,7 +127,8 @@ constexpr int kLatencyVnPerThread = 2;
 constexpr int kLatencyMaxThreads = 640;
 
 // ---------------------------------------------------------------------------------------------
-// Persistent server (server_kernel.cuh): worker blocks that poll per-code request rings.
+// Persistent server (server_kernel.cuh): worker blocks that take requests of any code from one
+// arrival-ordered queue.
 // ---------------------------------------------------------------------------------------------
 constexpr int kServerMaxCodes = 4;
 
@@ -137,9 +138,20 @@ constexpr uint32_t kServerTimeLimit = 2u;    // a worker left at max_runtime_ns
 constexpr uint32_t kServerSpinLimit = 4u;    // a worker left at the spin-count safety cap
 constexpr uint32_t kServerStopped = 8u;      // a worker left on the host's stop flag
 
-// Request slot in the ring (page-locked host memory mapped into the device address space):
-//   [0, 4)   done: request sequence number + 1, written by the device last (release)
-//   [4, 8)   iterations run          [8] ok
+// Queue entry (64 bits, page-locked host memory mapped into the device address space), written by
+// the host with a release store when it publishes request number g (counting from 0):
+//   [32, 64)  g + 1 (mod 2^32): the entry is published for the worker whose head count is g;
+//             also the completion word the worker writes into the slot
+//   [20, 24)  code      [0, 20)  slot index in the code's ring
+// Bits [24, 32) are zero in every entry, so an all-ones value can stand for "no request".
+constexpr int kQueueCodeShift = 20;
+constexpr int kQueueCodeMask = 0xf;
+constexpr uint32_t kQueueSlotMask = (1u << 20) - 1u;
+constexpr unsigned long long kQueueLeave = ~0ull;
+
+// Request slot in a code's ring (page-locked host memory mapped into the device address space):
+//   [0, 4)   done: the entry's arrival number + 1, written by the device last (release)
+//   [4, 8)   iterations run          [8] ok          [10, 12) index of the worker block
 //   [syn_off, syn_off + m)  syndrome bits, written by the host before it publishes the request
 //   [err_off, err_off + n)  e_hat, written by the device
 struct ServerCode {
@@ -148,16 +160,16 @@ struct ServerCode {
     const float *weights;       // FP32 learned decoding: [learned_iters][dc_max * m], or nullptr
     int32_t learned_iters;
     unsigned char *ring;        // ring_capacity slots of slot_bytes
-    const uint32_t *tail;       // host-written count of published requests
-    uint32_t *head;             // device count of claimed requests
     int32_t slot_bytes, syn_off, err_off;
-    int32_t first_block;        // worker blocks [first_block, next code's first_block)
+    int32_t layered_reg;        // layered workers: 1 = register-resident checks (<= 8 layers), 0 = shared memory
 };
 
 struct ServerParams {
     ServerCode code[kServerMaxCodes];
     int32_t ncodes;
-    int32_t ring_capacity;      // power of two
+    const unsigned long long *queue;   // [queue_mask + 1] entries (host-written)
+    uint32_t queue_mask;        // capacity - 1, capacity a power of two >= every ring slot together
+    uint32_t *head;             // device count of claimed entries
     int32_t max_iter;
     float alpha;
     int32_t alpha_q;
@@ -178,8 +190,9 @@ cudaError_t launch_server_i16(const ServerParams &p, const KernelChoice &kc, int
                               size_t smem, cudaStream_t stream);
 cudaError_t launch_server_i8(const ServerParams &p, const KernelChoice &kc, int blocks, int threads,
                              size_t smem, cudaStream_t stream);
-// Server workers on the layered schedule (msa_layered.cu): register-resident checks, at most
-// kLayeredServerMaxLayers layers of rows of degree <= 8 and kLayeredServerMaxThreads checks per layer.
+// Server workers on the layered schedule (msa_layered.cu): rows of degree <= 8 and at most
+// kLayeredServerMaxThreads checks per layer.  A code of at most kLayeredServerMaxLayers layers keeps
+// its checks in registers; one with more layers keeps its messages in shared memory.
 constexpr int kLayeredServerMaxLayers = 8;
 constexpr int kLayeredServerMaxThreads = 256;
 const void *server_kernel_layered(int precision, const KernelChoice &kc);

@@ -4,7 +4,9 @@
 // messages (flooding).  The layered schedule applies the same check update to one check after
 // another, each reading the a-posteriori LLRs already refreshed by the checks before it:
 //   q_{m,n} = Q_n - r_{m,n};  r_{m,n} = (-1)^{s_m} prod_{j != n} sign(q_{m,j}) alpha min_{j != n} |q_{m,j}|;
-//   Q_n = q_{m,n} + r_{m,n}        (checks in ascending index; then decisions and the stop test)
+//   Q_n = Q_n - r_old + r_new      (checks in ascending index; then decisions and the stop test)
+// In fixed point Q is the exact 32-bit sum gamma + sum r of Algorithm 1's APP step and only the
+// check's input q is clamped to the message range.
 // Two checks that share no variable commute, so the host groups the checks into layers (a check's
 // layer is one more than the largest layer of an earlier check it shares a variable with): the
 // checks of a layer run in parallel, the layers in order, and every result is bit-identical to the
@@ -22,7 +24,8 @@
 namespace qldpc {
 namespace kern {
 
-// One check of the layered schedule: q = Q - r_old, the min-sum update, Q = q + r_new.
+// One check of the layered schedule: Q - r_old, the min-sum update of q = clamp(Q - r_old),
+// Q = (Q - r_old) + r_new.
 template <class P, int DC, bool UNIFORM>
 __device__ __forceinline__ void layered_check(int c, int M, int deg, uint32_t s_bit, typename P::acc_t *__restrict__ Q,
                                               typename P::msg_t *__restrict__ slots, const uint32_t *__restrict__ ecol,
@@ -30,14 +33,15 @@ __device__ __forceinline__ void layered_check(int c, int M, int deg, uint32_t s_
 {
     using acc_t = typename P::acc_t;
     using mag_t = typename P::mag_t;
-    acc_t q[DC];
+    acc_t qu[DC], q[DC];
     uint32_t v[DC];
     uint32_t sx = 0;
 #pragma unroll
     for (int j = 0; j < DC; ++j) {
         if (UNIFORM || j < deg) {
             v[j] = __ldg(ecol + size_t(j) * M + c);
-            q[j] = P::sub_q(Q[v[j]], load_msg<P>(slots, uint32_t(j * M + c)));
+            qu[j] = P::sub(Q[v[j]], load_msg<P>(slots, uint32_t(j * M + c)));
+            q[j] = P::clampq(qu[j]);
             sx ^= P::sign_word(q[j]);
         }
     }
@@ -49,7 +53,7 @@ __device__ __forceinline__ void layered_check(int c, int M, int deg, uint32_t s_
     for (int j = 0; j < DC; ++j) {
         if (UNIFORM || j < deg) {
             const acc_t r = P::apply_sign(P::mag(q[j]) == m1 ? r2 : r1, q[j]);
-            Q[v[j]] = P::add(q[j], r);
+            Q[v[j]] = P::add(qu[j], r);
             slots[j * M + c] = P::to_msg(r);
         }
     }
@@ -67,13 +71,59 @@ __device__ __forceinline__ int check_met(int c, int M, int deg, uint32_t s_bit, 
     return par == 0;
 }
 
+// One shot on the shared-memory layout: Q [n] starts at the quantized priors, the messages at zero,
+// sb [m] takes the syndrome bits syn(c).  Runs the layers of every iteration with one barrier each and
+// the stop test after the last, and returns the iterations run (all = every check satisfied).  Ends
+// with Q final and visible to the block.
+template <class P, int DC, bool UNIFORM, class Syn>
+__device__ __forceinline__ int layered_smem_shot(const DeviceGraph &g, int tid, int T, Syn syn,
+                                                 const float *__restrict__ prior, typename P::acc_t *__restrict__ Q,
+                                                 typename P::msg_t *__restrict__ slots, uint8_t *__restrict__ sb,
+                                                 const LaunchParams &p, bool early, int &all)
+{
+    using msg_t = typename P::msg_t;
+    const int M = g.m, N = g.n, L = g.nlayers;
+    for (int v = tid; v < N; v += T) Q[v] = P::quantize(prior[v]);
+    for (int c = tid; c < M; c += T) {
+        sb[c] = syn(c) & 1u;
+        const int deg = UNIFORM ? DC : int(__ldg(g.rdeg + c));
+        for (int j = 0; j < deg; ++j) slots[j * M + c] = msg_t(0);
+    }
+    __syncthreads();
+    int ok = 1;
+    for (int c = tid; c < M; c += T)
+        ok &= check_met<P, DC, UNIFORM>(c, M, UNIFORM ? DC : int(__ldg(g.rdeg + c)), sb[c], Q, g.ecol);
+    all = __syncthreads_and(ok);
+    int k = 0;
+    if (!(early && all)) {
+        for (k = 1; k <= p.max_iter; ++k) {
+            for (int l = 0; l < L; ++l) {
+                const int lo = __ldg(g.layer_ptr + l), hi = __ldg(g.layer_ptr + l + 1);
+                for (int i = lo + tid; i < hi; i += T) {
+                    const int c = int(__ldg(g.layer_chk + i));
+                    layered_check<P, DC, UNIFORM>(c, M, UNIFORM ? DC : int(__ldg(g.rdeg + c)), sb[c], Q, slots,
+                                                  g.ecol, p);
+                }
+                __syncthreads();
+            }
+            ok = 1;
+            for (int c = tid; c < M; c += T)
+                ok &= check_met<P, DC, UNIFORM>(c, M, UNIFORM ? DC : int(__ldg(g.rdeg + c)), sb[c], Q, g.ecol);
+            all = __syncthreads_and(ok);
+            if (early && all) break;
+        }
+        if (k > p.max_iter) k = p.max_iter;
+    }
+    return k;
+}
+
 template <class P, int DC, bool UNIFORM>
 __global__ void __launch_bounds__(1024, 1) msa_layered_kernel(const LaunchParams p)
 {
     using acc_t = typename P::acc_t;
     using msg_t = typename P::msg_t;
     const Problem pr = blockIdx.y == 0 ? p.prob[0] : p.prob[1];
-    const int M = pr.g.m, N = pr.g.n, L = pr.g.nlayers;
+    const int M = pr.g.m, N = pr.g.n;
     const int T = blockDim.x, tid = threadIdx.x;
     extern __shared__ __align__(16) unsigned char smem[];
     const LayeredLayout lay = layered_layout(M, N, pr.g.dc_max, int(sizeof(msg_t)));
@@ -108,39 +158,9 @@ __global__ void __launch_bounds__(1024, 1) msa_layered_kernel(const LaunchParams
             continue;
         }
         const uint8_t *s = pr.syn + size_t(b) * M;
-        // Q = gamma, r = 0, syndrome bits
-        for (int v = tid; v < N; v += T) Q[v] = P::quantize(pr.prior[v]);
-        for (int c = tid; c < M; c += T) {
-            sb[c] = s[c] & 1u;
-            const int deg = UNIFORM ? DC : int(__ldg(pr.g.rdeg + c));
-            for (int j = 0; j < deg; ++j) slots[j * M + c] = msg_t(0);
-        }
-        __syncthreads();
-        int ok = 1;
-        for (int c = tid; c < M; c += T)
-            ok &= check_met<P, DC, UNIFORM>(c, M, UNIFORM ? DC : int(__ldg(pr.g.rdeg + c)), sb[c], Q, pr.g.ecol);
-        int all = __syncthreads_and(ok);
-        int k = 0;
-        if (!(early && all)) {
-            for (k = 1; k <= p.max_iter; ++k) {
-                for (int l = 0; l < L; ++l) {
-                    const int lo = __ldg(pr.g.layer_ptr + l), hi = __ldg(pr.g.layer_ptr + l + 1);
-                    for (int i = lo + tid; i < hi; i += T) {
-                        const int c = int(__ldg(pr.g.layer_chk + i));
-                        layered_check<P, DC, UNIFORM>(c, M, UNIFORM ? DC : int(__ldg(pr.g.rdeg + c)), sb[c], Q, slots,
-                                                      pr.g.ecol, p);
-                    }
-                    __syncthreads();
-                }
-                ok = 1;
-                for (int c = tid; c < M; c += T)
-                    ok &= check_met<P, DC, UNIFORM>(c, M, UNIFORM ? DC : int(__ldg(pr.g.rdeg + c)), sb[c], Q,
-                                                    pr.g.ecol);
-                all = __syncthreads_and(ok);
-                if (early && all) break;
-            }
-            if (k > p.max_iter) k = p.max_iter;
-        }
+        int all = 0;
+        const int k = layered_smem_shot<P, DC, UNIFORM>(pr.g, tid, T, [&](int c) { return uint32_t(s[c]); }, pr.prior,
+                                                        Q, slots, sb, p, early, all);
         for (int v = tid; v < N; v += T) {
             err[v] = P::neg(Q[v]) ? 1 : 0;
             if (pr.post) pr.post[size_t(b) * N + v] = P::post(Q[v]);
@@ -233,14 +253,15 @@ __device__ __forceinline__ int layered_reg_shot(const LayeredOwned<DC, MAXL> &o,
             for (int l = 0; l < MAXL; ++l) {
                 if (l < L) {
                     if (o.myc[l] >= 0) {
-                        acc_t q[DC];
+                        acc_t qu[DC], q[DC];
                         uint32_t v[DC];
                         uint32_t sx = 0;
 #pragma unroll
                         for (int j = 0; j < DC; ++j) {
                             if (UNIFORM || j < o.mdeg[l]) {
                                 v[j] = (o.ev[l][j / 2] >> (16 * (j & 1))) & 0xffffu;
-                                q[j] = P::sub_q(Q[v[j]], r[l][j]);
+                                qu[j] = P::sub(Q[v[j]], r[l][j]);
+                                q[j] = P::clampq(qu[j]);
                                 sx ^= P::sign_word(q[j]);
                             }
                         }
@@ -253,7 +274,7 @@ __device__ __forceinline__ int layered_reg_shot(const LayeredOwned<DC, MAXL> &o,
                         for (int j = 0; j < DC; ++j) {
                             if (UNIFORM || j < o.mdeg[l]) {
                                 r[l][j] = P::apply_sign(P::mag(q[j]) == m1 ? r2 : r1, q[j]);
-                                Q[v[j]] = P::add(q[j], r[l][j]);
+                                Q[v[j]] = P::add(qu[j], r[l][j]);
                             }
                         }
                     }
@@ -323,20 +344,20 @@ __global__ void __launch_bounds__(256, 1) msa_layered_reg_kernel(const LaunchPar
     }
 }
 
-// Persistent server worker on the layered schedule (QLDPC_LAYERED in the server's flags): the
-// claim, publish and leave protocol of msa_server_kernel around one layered_reg_shot per request.
-// Each worker block owns its code's checks in registers from the kernel's start.
+// Persistent server worker on the layered schedule (QLDPC_LAYERED in the server's flags): the claim,
+// publish and leave protocol of msa_server_kernel around one layered shot per request.  A code of at
+// most MAXL layers runs layered_reg_shot (each thread owns one check per layer in registers, reloaded
+// when the worker takes a request of another code); a code with more layers runs layered_smem_shot
+// (messages in shared memory).  Results are those of msa_layered_kernel either way.
 template <class P, int DC, bool UNIFORM, int MAXL>
 __global__ void __launch_bounds__(256, 1) msa_server_layered_kernel(const ServerParams sp)
 {
     using acc_t = typename P::acc_t;
-    int ci = 0;
-    while (ci + 1 < sp.ncodes && int(blockIdx.x) >= sp.code[ci + 1].first_block) ++ci;
-    const ServerCode sc = sp.code[ci];
-    const int N = sc.g.n, T = blockDim.x, tid = threadIdx.x;
+    using msg_t = typename P::msg_t;
+    const int T = blockDim.x, tid = threadIdx.x;
     extern __shared__ __align__(16) unsigned char smem[];
     acc_t *Q = reinterpret_cast<acc_t *>(smem);
-    __shared__ int64_t s_claim;
+    __shared__ uint64_t s_claim;
 
     LaunchParams p{};   // the arithmetic parameters the shared device functions read
     p.alpha = sp.alpha;
@@ -345,30 +366,40 @@ __global__ void __launch_bounds__(256, 1) msa_server_layered_kernel(const Server
     p.flags = sp.flags;
     const bool early = (sp.flags & kFlagNoEarlyStop) == 0;
 
+    int cur = -1;
     LayeredOwned<DC, MAXL> own;
-    layered_own<DC, UNIFORM, MAXL>(sc.g, tid, own);
 
     const uint64_t t_start = globaltimer();
     uint64_t t_idle_from = t_start;
     for (;;) {
-        if (tid == 0) s_claim = claim_request(sc, sp, t_start, t_idle_from);
+        if (tid == 0) s_claim = claim_request(sp, t_start, t_idle_from);
         __syncthreads();
-        const int64_t h = s_claim;
-        if (h < 0) break;
-        unsigned char *slot = sc.ring + size_t(uint32_t(h) & uint32_t(sp.ring_capacity - 1)) * size_t(sc.slot_bytes);
+        const uint64_t e = s_claim;
+        if (e == kQueueLeave) break;
+        const int code = entry_code(e);
+        const ServerCode &sc = sp.code[code];
+        const bool reg = sc.layered_reg != 0;
+        if (reg && code != cur) {
+            layered_own<DC, UNIFORM, MAXL>(sc.g, tid, own);
+            cur = code;
+        }
+        unsigned char *slot = sc.ring + size_t(entry_slot(e)) * size_t(sc.slot_bytes);
         const unsigned char *syn = slot + sc.syn_off;
-        int all = 0;
-        const int k = layered_reg_shot<P, DC, UNIFORM, MAXL>(
-            own, sc.g.nlayers, N, tid, T, [&](int c) { return uint32_t(__ldcv(syn + c)); }, sc.prior, Q, p, early, all);
+        auto syn_bit = [&](int c) { return uint32_t(__ldcv(syn + c)); };
+        const int N = sc.g.n;
+        int all = 0, k;
+        if (reg) {
+            k = layered_reg_shot<P, DC, UNIFORM, MAXL>(own, sc.g.nlayers, N, tid, T, syn_bit, sc.prior, Q, p, early, all);
+        } else {
+            const LayeredLayout lay = layered_layout(sc.g.m, N, sc.g.dc_max, int(sizeof(msg_t)));
+            k = layered_smem_shot<P, DC, UNIFORM>(sc.g, tid, T, syn_bit, sc.prior, Q,
+                                                  reinterpret_cast<msg_t *>(smem + lay.slot_off), smem + lay.s_off, p,
+                                                  early, all);
+        }
         unsigned char *err = slot + sc.err_off;
         for (int v = tid; v < N; v += T) err[v] = P::neg(Q[v]) ? 1 : 0;
         __syncthreads();
-        if (tid == 0) {
-            *reinterpret_cast<int32_t *>(slot + 4) = k;
-            slot[8] = all ? 1 : 0;
-            __threadfence_system();
-            st_release_sys(reinterpret_cast<uint32_t *>(slot), uint32_t(h) + 1u);
-        }
+        if (tid == 0) publish_result(slot, k, all, entry_done(e));
     }
 }
 

@@ -731,6 +731,19 @@ void *mapped_host_range(const void *p, size_t bytes)
     return a.devicePointer;
 }
 
+// The graph's device copy of the prior, uploaded only when it differs from the last one (caller
+// holds host_mu and has reserved the staging).
+int upload_prior(qldpc_graph *g, const float *h_prior, cudaStream_t st)
+{
+    const size_t prior_b = size_t(g->n) * sizeof(float);
+    if (g->prior_valid && std::memcmp(g->prior_cache.data(), h_prior, prior_b) == 0) return QLDPC_OK;
+    g->prior_cache.assign(h_prior, h_prior + g->n);
+    const cudaError_t e = cudaMemcpyAsync(g->d_prior, g->prior_cache.data(), prior_b, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_status(e);
+    g->prior_valid = true;
+    return QLDPC_OK;
+}
+
 }  // namespace detail
 }  // namespace qldpc
 
@@ -868,6 +881,14 @@ int qldpc_graph_dims(const qldpc_graph *g, int32_t *m, int32_t *n, int32_t *nnz,
     return QLDPC_OK;
 }
 
+int qldpc_graph_layers(const qldpc_graph *g, int32_t *layers, int32_t *widest)
+{
+    if (!g) return QLDPC_ERR_INVALID_ARG;
+    if (layers) *layers = g->dg.nlayers;
+    if (widest) *widest = g->dg.max_layer;
+    return QLDPC_OK;
+}
+
 int qldpc_graph_footprint(const qldpc_graph *g, int32_t precision, int32_t *lanes, size_t *shot_bytes)
 {
     if (!g) return QLDPC_ERR_INVALID_ARG;
@@ -985,13 +1006,7 @@ int qldpc_decode_host(qldpc_graph *g, const uint8_t *h_syndromes, int32_t batch,
     void *z_err = z_syn ? mapped_host_range(h_err, size_t(batch) * g->n) : nullptr;
     void *z_it = z_err ? mapped_host_range(h_iters, size_t(batch) * 4) : nullptr;
     void *z_ok = z_it ? mapped_host_range(h_ok, size_t(batch)) : nullptr;
-    const size_t prior_b = size_t(g->n) * sizeof(float);
-    if (!g->prior_valid || std::memcmp(g->prior_cache.data(), h_prior, prior_b) != 0) {
-        g->prior_cache.assign(h_prior, h_prior + g->n);
-        e = cudaMemcpyAsync(g->d_prior, g->prior_cache.data(), prior_b, cudaMemcpyHostToDevice, st);
-        if (e != cudaSuccess) return cuda_status(e);
-        g->prior_valid = true;
-    }
+    if (int rc = upload_prior(g, h_prior, st)) return rc;
     if (z_ok) {
         const Problem pz = make_problem(g, static_cast<const uint8_t *>(z_syn), g->d_prior,
                                         static_cast<uint8_t *>(z_err), static_cast<int32_t *>(z_it),
@@ -1027,6 +1042,72 @@ int qldpc_decode_host(qldpc_graph *g, const uint8_t *h_syndromes, int32_t batch,
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h_iters, g->d_iters, size_t(batch) * 4, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h_ok, g->d_ok, size_t(batch), cudaMemcpyDeviceToHost, st);
+    const cudaError_t se = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_status(e);
+    return cuda_status(se);
+}
+
+int qldpc_decode_pair_host(qldpc_graph *g_z, qldpc_graph *g_x, const uint8_t *h_sx, const uint8_t *h_sz,
+                           int32_t batch, const float *h_prior_x, const float *h_prior_z, int32_t max_iter,
+                           float alpha, uint8_t *h_err_x, uint8_t *h_err_z, int32_t *h_iters_x,
+                           int32_t *h_iters_z, uint8_t *h_ok_x, uint8_t *h_ok_z, int32_t precision,
+                           uint32_t flags, void *stream)
+{
+    if (!g_z || !g_x || g_z == g_x || batch < 0) return QLDPC_ERR_INVALID_ARG;
+    if (g_z->n != g_x->n || g_z->device != g_x->device) return QLDPC_ERR_INVALID_ARG;
+    if (batch > 0 && (!h_sx || !h_sz || !h_prior_x || !h_prior_z || !h_err_x || !h_err_z || !h_iters_x ||
+                      !h_iters_z || !h_ok_x || !h_ok_z))
+        return QLDPC_ERR_INVALID_ARG;
+    if (int rc = check_device(g_z)) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Problem pr[2] = {make_problem(g_z, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr),
+                     make_problem(g_x, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr)};
+    // every argument check and the launch plan, before anything is enqueued
+    if (int rc = launch(g_z, g_x, pr, 2, batch, max_iter, alpha, precision, flags, st, true)) return rc;
+    if (batch == 0) return QLDPC_OK;
+    std::scoped_lock lk(g_z->host_mu, g_x->host_mu);
+    if (int rc = reserve_stage(g_z, batch)) return rc;
+    if (int rc = reserve_stage(g_x, batch)) return rc;
+    if (int rc = upload_prior(g_z, h_prior_x, st)) return rc;
+    if (int rc = upload_prior(g_x, h_prior_z, st)) return rc;
+    // Page-locked buffers: the kernel reads the syndromes and writes the results in host memory.
+    const size_t bx = size_t(batch) * g_z->m, bz = size_t(batch) * g_x->m, be = size_t(batch) * g_z->n;
+    void *z[8] = {mapped_host_range(h_sx, bx), mapped_host_range(h_sz, bz), mapped_host_range(h_err_x, be),
+                  mapped_host_range(h_err_z, be), mapped_host_range(h_iters_x, size_t(batch) * 4),
+                  mapped_host_range(h_iters_z, size_t(batch) * 4), mapped_host_range(h_ok_x, size_t(batch)),
+                  mapped_host_range(h_ok_z, size_t(batch))};
+    bool zero_copy = true;
+    for (void *x : z) zero_copy = zero_copy && x;
+    if (zero_copy) {
+        pr[0] = make_problem(g_z, static_cast<const uint8_t *>(z[0]), g_z->d_prior, static_cast<uint8_t *>(z[2]),
+                             static_cast<int32_t *>(z[4]), static_cast<uint8_t *>(z[6]), nullptr);
+        pr[1] = make_problem(g_x, static_cast<const uint8_t *>(z[1]), g_x->d_prior, static_cast<uint8_t *>(z[3]),
+                             static_cast<int32_t *>(z[5]), static_cast<uint8_t *>(z[7]), nullptr);
+        const int rc = launch(g_z, g_x, pr, 2, batch, max_iter, alpha, precision, flags, st);
+        const cudaError_t se = cudaStreamSynchronize(st);
+        if (rc) return rc;
+        return cuda_status(se);
+    }
+    cudaError_t e = cudaMemcpyAsync(g_z->d_syn, h_sx, bx, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(g_x->d_syn, h_sz, bz, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(st);
+        return cuda_status(e);
+    }
+    pr[0] = make_problem(g_z, g_z->d_syn, g_z->d_prior, g_z->d_err, g_z->d_iters, g_z->d_ok, nullptr);
+    pr[1] = make_problem(g_x, g_x->d_syn, g_x->d_prior, g_x->d_err, g_x->d_iters, g_x->d_ok, nullptr);
+    if (int rc = launch(g_z, g_x, pr, 2, batch, max_iter, alpha, precision, flags, st)) {
+        cudaStreamSynchronize(st);
+        return rc;
+    }
+    const qldpc_graph *gs[2] = {g_z, g_x};
+    uint8_t *errs[2] = {h_err_x, h_err_z}, *oks[2] = {h_ok_x, h_ok_z};
+    int32_t *its[2] = {h_iters_x, h_iters_z};
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+        e = cudaMemcpyAsync(errs[i], gs[i]->d_err, be, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(its[i], gs[i]->d_iters, size_t(batch) * 4, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(oks[i], gs[i]->d_ok, size_t(batch), cudaMemcpyDeviceToHost, st);
+    }
     const cudaError_t se = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_status(e);
     return cuda_status(se);

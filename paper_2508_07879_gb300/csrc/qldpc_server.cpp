@@ -1,12 +1,14 @@
 // Host side of the persistent decoding server (include/qldpc.h: qldpc_server_*).
 //
 // The server owns, per code, a ring of request slots in page-locked host memory mapped into the
-// device address space, a device counter of claimed requests, and the device copy of the code's
-// prior; one persistent kernel (server_kernel.cuh) runs all worker blocks on a private stream.
-// The host publishes a request by writing its syndrome into the next slot and bumping the ring's
-// tail with a release store; it learns completion from the slot's done word (acquire load).
-// Relaunching after the workers left (idle) is safe: workers only leave with every published
-// request claimed and finished, and the counters survive in memory.
+// device address space and the device copy of the code's prior (and learned weights), plus one
+// arrival-ordered queue of request entries (also mapped) and its device-side claim counter; one
+// persistent kernel (server_kernel.cuh, or the layered workers of msa_layered.cu) runs all worker
+// blocks on a private stream.  The host publishes a request by writing its syndrome into a free slot
+// of its code's ring and then the request's entry into the queue with a release store; any free
+// worker claims the oldest entry, whatever its code.  Completion is the slot's done word (acquire
+// load).  Relaunching after the workers left (idle) is safe: workers only leave with every
+// published request claimed and finished, and the counters survive in memory.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -33,21 +35,25 @@ struct qldpc_server {
     int ncodes = 0;
     const qldpc_graph *graphs[kServerMaxCodes] = {};
     int32_t m[kServerMaxCodes] = {}, n[kServerMaxCodes] = {};
-    int32_t capacity = 0;
+    int32_t capacity = 0;                   // slots per code ring
     ServerParams sp{};
     KernelChoice kc{};
     int blocks = 0, threads = 0;
     size_t smem = 0;
     cudaStream_t stream = nullptr;
-    unsigned char *host_block = nullptr;    // rings + tails + stop (page-locked, mapped)
+    unsigned char *host_block = nullptr;    // queue + rings + stop (page-locked, mapped)
+    unsigned long long *queue = nullptr;    // [queue_cap] entries
+    uint32_t queue_cap = 0;
     unsigned char *ring[kServerMaxCodes] = {};
-    uint32_t *tail[kServerMaxCodes] = {};   // one cache line each
     uint32_t *stop = nullptr;
-    void *dev_block = nullptr;              // heads + status + priors
+    void *dev_block = nullptr;              // head + status + priors + weights
     uint32_t *head = nullptr;
     uint32_t *status = nullptr;
-    uint64_t next[kServerMaxCodes] = {};    // next sequence number to submit
-    std::vector<uint8_t> busy[kServerMaxCodes];   // slot holds a request whose result is uncollected
+    uint64_t next_global = 0;               // arrival number of the next request
+    uint64_t next[kServerMaxCodes] = {};    // next ticket (sequence number) per code
+    // per slot: holds a request whose result is uncollected, and that request's completion word
+    std::vector<uint8_t> busy[kServerMaxCodes];
+    std::vector<uint32_t> done_word[kServerMaxCodes];
     bool launched = false;
     std::mutex mu;
 };
@@ -89,30 +95,43 @@ int submit_locked(qldpc_server *s, int32_t code, const uint8_t *syndrome, uint64
     if (s->busy[code][idx]) return QLDPC_BUSY;
     unsigned char *slot = slot_ptr(s, code, seq);
     std::memcpy(slot + s->sp.code[code].syn_off, syndrome, size_t(s->m[code]));
-    __atomic_store_n(reinterpret_cast<uint32_t *>(slot), 0u, __ATOMIC_RELAXED);
+    // The queue holds at most every ring slot's request at once (its capacity covers them all), so
+    // the entry about to be overwritten was claimed long ago.
+    const uint64_t g = s->next_global++;
+    const uint32_t done = uint32_t(g + 1);
+    __atomic_store_n(reinterpret_cast<uint32_t *>(slot), done - 1u, __ATOMIC_RELAXED);   // not done
     s->busy[code][idx] = 1;
+    s->done_word[code][idx] = done;
     s->next[code] = seq + 1;
-    __atomic_store_n(s->tail[code], uint32_t(seq + 1), __ATOMIC_RELEASE);   // publish
+    const unsigned long long entry = (static_cast<unsigned long long>(done) << 32) |
+                                     (static_cast<unsigned long long>(code) << kQueueCodeShift) | idx;
+    __atomic_store_n(s->queue + (g & (s->queue_cap - 1)), entry, __ATOMIC_RELEASE);   // publish
     if (int rc = ensure_running(s)) return rc;
     *ticket = seq;
     return QLDPC_OK;
 }
 
 // QLDPC_OK with the outputs copied (and the slot released) once the request is done.
-int poll_locked(qldpc_server *s, int32_t code, uint64_t ticket, uint8_t *err, int32_t *iters, uint8_t *ok)
+int poll_locked(qldpc_server *s, int32_t code, uint64_t ticket, uint8_t *err, int32_t *iters, uint8_t *ok,
+                int32_t *worker)
 {
     if (ticket >= s->next[code] || ticket + uint64_t(s->capacity) < s->next[code]) return QLDPC_ERR_INVALID_ARG;
     const size_t idx = size_t(ticket & uint64_t(s->capacity - 1));
     if (!s->busy[code][idx]) return QLDPC_ERR_INVALID_ARG;     // already collected
     unsigned char *slot = slot_ptr(s, code, ticket);
     const uint32_t done = __atomic_load_n(reinterpret_cast<uint32_t *>(slot), __ATOMIC_ACQUIRE);
-    if (done != uint32_t(ticket + 1)) {
+    if (done != s->done_word[code][idx]) {
         if (int rc = ensure_running(s)) return rc;
         return QLDPC_PENDING;
     }
     if (err) std::memcpy(err, slot + s->sp.code[code].err_off, size_t(s->n[code]));
     if (iters) std::memcpy(iters, slot + 4, 4);
     if (ok) *ok = slot[8];
+    if (worker) {
+        uint16_t w;
+        std::memcpy(&w, slot + 10, 2);
+        *worker = int32_t(w);
+    }
     s->busy[code][idx] = 0;
     return QLDPC_OK;
 }
@@ -164,7 +183,8 @@ int qldpc_server_create(const qldpc_graph *const *graphs, const float *const *pr
     s->ncodes = ncodes;
     s->capacity = cap;
 
-    // one kernel variant and block shape for all codes (the largest degrees and sizes)
+    // One footprint for every worker, the largest any code needs (kernel variant of the largest
+    // degrees, threads, shared memory), so that every worker can decode every code.
     int dc = 0, dv = 0, want = 32;
     bool uniform = true;
     size_t smem = 0;
@@ -184,18 +204,21 @@ int qldpc_server_create(const qldpc_graph *const *graphs, const float *const *pr
     s->kc = kernel_variant(dc, dv, uniform, true, false);
     for (int c = 0; c < ncodes; ++c) s->kc.learned = s->kc.learned || (learned && graphs[c]->d_weights);
     bool fits;
+    int layered_reg[kServerMaxCodes] = {};
     if (layered) {
-        // a thread per check of the widest layer; each thread keeps one check per layer in registers
+        // a thread per check of the widest layer; a code of at most 8 layers keeps one check per
+        // layer per thread in registers, one with more layers its messages in shared memory
         int widest = 32;
         smem = 0;
         fits = dc <= 8;
         for (int c = 0; c < ncodes; ++c) {
             const qldpc_graph *g = graphs[c];
             widest = std::max(widest, (g->dg.max_layer + 31) / 32 * 32);
-            smem = std::max(smem, align16(size_t(g->n) * 4));
-            fits = fits && g->dg.nlayers <= kLayeredServerMaxLayers && g->n <= 65536;
+            layered_reg[c] = g->dg.nlayers <= kLayeredServerMaxLayers && g->n <= 65536;
+            smem = std::max(smem, layered_reg[c] ? align16(size_t(g->n) * 4)
+                                                 : layered_layout(g->m, g->n, g->dc_max, msg_bytes(cfg->precision)).total);
         }
-        s->kc.latency = false;
+        s->kc = kernel_variant(dc, dv, uniform, false, false);
         s->kc.layered = true;
         s->threads = cfg->threads_per_block ? cfg->threads_per_block : widest;
         fits = fits && s->threads >= widest && s->threads <= kLayeredServerMaxThreads && s->threads % 32 == 0;
@@ -207,11 +230,12 @@ int qldpc_server_create(const qldpc_graph *const *graphs, const float *const *pr
                    graphs[c]->nv <= kLatencyVnPerThread * s->threads;
     }
     s->smem = smem;
-    const void *k = layered                          ? server_kernel_layered(cfg->precision, s->kc)
+    const void *k = !fits                            ? nullptr
+                    : layered                        ? server_kernel_layered(cfg->precision, s->kc)
                     : cfg->precision == QLDPC_INT16 ? server_kernel_i16(s->kc)
                     : cfg->precision == QLDPC_INT8  ? server_kernel_i8(s->kc)
                                                     : server_kernel_f32(s->kc);
-    if (!fits || !k) {
+    if (!k) {
         delete s;
         return QLDPC_ERR_UNSUPPORTED;
     }
@@ -224,29 +248,32 @@ int qldpc_server_create(const qldpc_graph *const *graphs, const float *const *pr
         delete s;
         return QLDPC_ERR_UNSUPPORTED;
     }
-    // Worker blocks per code: as configured, else an equal share of the resident slots.
+    // Worker pool: the sum of cfg->blocks when given, else every worker that fits on the GPU at
+    // this footprint.  All of them must be resident at once (a worker that never starts would never
+    // take a request).
     const int resident = per_sm * graphs[0]->sm_count;
     int total = 0;
-    int nb[kServerMaxCodes] = {};
-    for (int c = 0; c < ncodes; ++c) {
-        nb[c] = cfg->blocks[c] ? cfg->blocks[c] : std::max(1, resident / ncodes);
-        total += nb[c];
-    }
-    if (total > resident) {   // every worker must be resident: a waiting block would never run
+    for (int c = 0; c < ncodes; ++c) total += cfg->blocks[c];
+    if (total == 0) total = resident;
+    if (total > resident || total > 65535) {
         delete s;
         return QLDPC_ERR_UNSUPPORTED;
     }
     s->blocks = total;
 
-    // page-locked, mapped host memory: rings, tails, stop flag
-    size_t host_bytes = 0;
+    // page-locked, mapped host memory: the queue (one entry per ring slot of every code, rounded up
+    // to a power of two), the rings, the stop flag
+    uint32_t qcap = 1;
+    while (qcap < uint32_t(ncodes) * uint32_t(cap)) qcap <<= 1;
+    s->queue_cap = qcap;
+    size_t host_bytes = size_t(qcap) * sizeof(unsigned long long);
     size_t ring_off[kServerMaxCodes];
     for (int c = 0; c < ncodes; ++c) {
         ring_off[c] = host_bytes;
         host_bytes += size_t(cap) * size_t(server_slot_bytes(s->m[c], s->n[c]));
     }
-    const size_t tail_off = host_bytes;
-    host_bytes += 64 * kServerMaxCodes + 64;
+    const size_t stop_off = align16(host_bytes);
+    host_bytes = stop_off + 64;
     void *hb = nullptr;
     cudaError_t e = cudaHostAlloc(&hb, host_bytes, cudaHostAllocMapped | cudaHostAllocPortable);
     if (e != cudaSuccess) {
@@ -255,8 +282,8 @@ int qldpc_server_create(const qldpc_graph *const *graphs, const float *const *pr
     }
     std::memset(hb, 0, host_bytes);
     s->host_block = static_cast<unsigned char *>(hb);
-    for (int c = 0; c < kServerMaxCodes; ++c) s->tail[c] = reinterpret_cast<uint32_t *>(s->host_block + tail_off + 64 * c);
-    s->stop = reinterpret_cast<uint32_t *>(s->host_block + tail_off + 64 * kServerMaxCodes);
+    s->queue = reinterpret_cast<unsigned long long *>(s->host_block);
+    s->stop = reinterpret_cast<uint32_t *>(s->host_block + stop_off);
     void *hb_dev = nullptr;
     if (cudaHostGetDevicePointer(&hb_dev, hb, 0) != cudaSuccess) {
         free_server(s);
@@ -264,7 +291,7 @@ int qldpc_server_create(const qldpc_graph *const *graphs, const float *const *pr
     }
     unsigned char *hd = static_cast<unsigned char *>(hb_dev);
 
-    // device memory: claim counters, status, priors, and a private copy of each code's learned
+    // device memory: claim counter, status, priors, and a private copy of each code's learned
     // weights (QLDPC_LEARNED; a code without weights decodes plainly)
     size_t dev_bytes = 256;
     size_t prior_off[kServerMaxCodes], w_off[kServerMaxCodes], w_bytes[kServerMaxCodes];
@@ -295,16 +322,17 @@ int qldpc_server_create(const qldpc_graph *const *graphs, const float *const *pr
 
     ServerParams &sp = s->sp;
     sp.ncodes = ncodes;
-    sp.ring_capacity = cap;
+    sp.queue = reinterpret_cast<const unsigned long long *>(hd);
+    sp.queue_mask = qcap - 1;
+    sp.head = s->head;
     sp.max_iter = cfg->max_iter;
     sp.alpha = cfg->alpha;
     sp.alpha_q = aq;
     sp.flags = cfg->flags & QLDPC_NO_EARLY_STOP;
-    sp.stop = reinterpret_cast<const uint32_t *>(hd + tail_off + 64 * kServerMaxCodes);
+    sp.stop = reinterpret_cast<const uint32_t *>(hd + stop_off);
     sp.status = s->status;
     sp.idle_ns = uint64_t(cfg->idle_timeout_ns > 0 ? cfg->idle_timeout_ns : 500000000LL);
     sp.max_runtime_ns = uint64_t(cfg->max_runtime_ns > 0 ? cfg->max_runtime_ns : 600000000000LL);
-    int first = 0;
     for (int c = 0; c < ncodes; ++c) {
         ServerCode &sc = sp.code[c];
         sc.g = graphs[c]->dg;
@@ -312,15 +340,13 @@ int qldpc_server_create(const qldpc_graph *const *graphs, const float *const *pr
         sc.weights = w_bytes[c] ? reinterpret_cast<const float *>(static_cast<char *>(s->dev_block) + w_off[c]) : nullptr;
         sc.learned_iters = w_bytes[c] ? graphs[c]->learned_T : 0;
         sc.ring = hd + ring_off[c];
-        sc.tail = reinterpret_cast<const uint32_t *>(hd + tail_off + 64 * c);
-        sc.head = s->head + c;
         sc.slot_bytes = server_slot_bytes(s->m[c], s->n[c]);
         sc.syn_off = 16;
         sc.err_off = int32_t(align16(16 + size_t(s->m[c])));
-        sc.first_block = first;
-        first += nb[c];
+        sc.layered_reg = layered_reg[c];
         s->ring[c] = s->host_block + ring_off[c];
         s->busy[c].assign(size_t(cap), 0);
+        s->done_word[c].assign(size_t(cap), 0);
     }
     *out = s;
     return QLDPC_OK;
@@ -337,13 +363,13 @@ int qldpc_server_poll(qldpc_server *s, int32_t code, uint64_t ticket, uint8_t *e
 {
     if (!s || code < 0 || code >= s->ncodes) return QLDPC_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(s->mu);
-    return poll_locked(s, code, ticket, err, iters, ok);
+    return poll_locked(s, code, ticket, err, iters, ok, nullptr);
 }
 
 int qldpc_server_replay(qldpc_server *s, int32_t nreq, const int32_t *codes, const uint8_t *syndromes,
                         const int64_t *syn_offsets, const int64_t *arrival_ns, uint8_t *errs,
                         const int64_t *err_offsets, int32_t *iters, uint8_t *oks, int64_t *latency_ns,
-                        int64_t timeout_ns)
+                        int32_t *workers, int64_t timeout_ns)
 {
     if (!s || nreq < 0) return QLDPC_ERR_INVALID_ARG;
     if (nreq == 0) return QLDPC_OK;
@@ -370,7 +396,8 @@ int qldpc_server_replay(qldpc_server *s, int32_t nreq, const int32_t *codes, con
         }
         for (size_t j = 0; j < inflight.size();) {
             const int32_t i = inflight[j];
-            const int rc = poll_locked(s, codes[i], tickets[size_t(i)], errs + err_offsets[i], iters + i, oks + i);
+            const int rc = poll_locked(s, codes[i], tickets[size_t(i)], errs + err_offsets[i], iters + i, oks + i,
+                                       workers ? workers + i : nullptr);
             if (rc == QLDPC_OK) {
                 const int64_t t = std::chrono::duration_cast<std::chrono::nanoseconds>(clock::now() - t0).count();
                 latency_ns[i] = t - arrival_ns[i];
@@ -384,6 +411,15 @@ int qldpc_server_replay(qldpc_server *s, int32_t nreq, const int32_t *codes, con
             }
         }
     }
+    return QLDPC_OK;
+}
+
+int qldpc_server_info(const qldpc_server *s, int32_t *workers, int32_t *threads_per_block, size_t *smem_per_block)
+{
+    if (!s) return QLDPC_ERR_INVALID_ARG;
+    if (workers) *workers = s->blocks;
+    if (threads_per_block) *threads_per_block = s->threads;
+    if (smem_per_block) *smem_per_block = s->smem;
     return QLDPC_OK;
 }
 

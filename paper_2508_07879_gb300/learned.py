@@ -180,30 +180,50 @@ def z_logicals(code):
 
 
 def evaluate(graph, prior, logicals, decoders: dict, shots: int, batch: int = 65536, p_lo: float = 0.02,
-             p_hi=None, seed: int = 11, first_shot: int = 0, alpha: float = 0.75):
+             p_hi=None, seed: int = 11, first_shot: int = 0, alpha: float = 0.75, paired=()):
     """Logical error rates of several decoders on the same device-sampled shots.
 
     decoders: name -> (max_iter, learned).  A learned decoder uses the graph's weights and then
     plain min-sum for up to max_iter iterations.  Returns name -> dict(failures, ler, mean_iters,
     unconverged) over ``shots`` shots (rate uniform in [p_lo, p_hi), or p_lo if p_hi is None).
+
+    paired: pairs (a, b) of decoder names compared shot by shot on the same shots.  out["paired"]
+    ["a|b"] holds the discordant counts (a_only: shots a fails and b decodes, b_only: the reverse),
+    the LER difference ler_a - ler_b and its 95 % confidence interval from the paired (McNemar)
+    variance of the per-shot difference.
     """
     torch = _torch()
     dev = torch.device("cuda", torch.cuda.current_device())
     L = torch.as_tensor(np.ascontiguousarray(logicals, dtype=np.uint8), device=dev)
     pr = torch.as_tensor(np.ascontiguousarray(prior, dtype=np.float32), device=dev)
     acc = {k: torch.zeros(3, dtype=torch.int64, device=dev) for k in decoders}
+    disc = {pair: torch.zeros(2, dtype=torch.int64, device=dev) for pair in paired}
     done = 0
     while done < shots:
         b = min(batch, shots - done)
         err, syn = qldpc.sample_errors(graph, seed, first_shot + done, b, p_lo, p_hi)
+        fails = {}
         for name, (max_iter, learned) in decoders.items():
             dec, iters, ok, _ = qldpc.decode(graph, syn, pr, int(max_iter), alpha, learned=bool(learned))
             fail = qldpc.logical_failures(L, err, dec, ok)
+            fails[name] = fail.bool()
             acc[name] += torch.stack([fail.sum(dtype=torch.int64), iters.sum(dtype=torch.int64),
                                       (ok == 0).sum(dtype=torch.int64)])
+        for (a, c) in paired:
+            disc[(a, c)] += torch.stack([(fails[a] & ~fails[c]).sum(dtype=torch.int64),
+                                         (fails[c] & ~fails[a]).sum(dtype=torch.int64)])
         done += b
     out = {}
     for name, a in acc.items():
         f, it, unc = (int(x) for x in a.cpu())
         out[name] = {"failures": f, "ler": f / shots, "mean_iters": it / shots, "unconverged": unc}
+    if paired:
+        out["paired"] = {}
+        for (a, c), d in disc.items():
+            n_a, n_c = (int(x) for x in d.cpu())
+            diff = (n_a - n_c) / shots
+            var = ((n_a + n_c) / shots - diff * diff) / shots
+            half = 1.959964 * float(np.sqrt(max(var, 0.0)))
+            out["paired"][f"{a}|{c}"] = {"a_only": n_a, "b_only": n_c, "ler_diff": diff,
+                                         "ci95": [diff - half, diff + half]}
     return out

@@ -71,6 +71,7 @@ _SIGNATURES = {
     "qldpc_graph_create_csc": ([_p, _p, _i32, _i32, ctypes.POINTER(_p)], ctypes.c_int),
     "qldpc_graph_destroy": ([_p], None),
     "qldpc_graph_dims": ([_p, _p, _p, _p, _p, _p], ctypes.c_int),
+    "qldpc_graph_layers": ([_p, ctypes.POINTER(_i32), ctypes.POINTER(_i32)], ctypes.c_int),
     "qldpc_graph_footprint": ([_p, _i32, ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
     "qldpc_graph_set_launch": ([_p, _i32, _i32, _i32], ctypes.c_int),
     "qldpc_graph_reserve": ([_p, _i32], ctypes.c_int),
@@ -79,14 +80,18 @@ _SIGNATURES = {
     "qldpc_decode_pair": ([_p, _p, _p, _p, _i32, _p, _p, _i32, _f32, _p, _p, _p, _p, _p, _p, _p, _p,
                            _i32, _u32, _p], ctypes.c_int),
     "qldpc_decode_host": ([_p, _p, _i32, _p, _i32, _f32, _p, _p, _p, _i32, _u32, _p], ctypes.c_int),
+    "qldpc_decode_pair_host": ([_p, _p, _p, _p, _i32, _p, _p, _i32, _f32, _p, _p, _p, _p, _p, _p, _i32, _u32, _p],
+                               ctypes.c_int),
     "qldpc_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "qldpc_decode_host_noalloc": ([_p, _p, _i32, _p, _i32, _f32, _p, _p, _p, _i32, _u32, _p], ctypes.c_int),
     "qldpc_noalloc_scratch_bytes": ([], ctypes.c_size_t),
     "qldpc_server_create": ([_p, _p, _i32, ctypes.POINTER(ServerConfig), ctypes.POINTER(_p)], ctypes.c_int),
     "qldpc_server_submit": ([_p, _i32, _p, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
     "qldpc_server_poll": ([_p, _i32, ctypes.c_uint64, _p, _p, _p], ctypes.c_int),
-    "qldpc_server_replay": ([_p, _i32, _p, _p, _p, _p, _p, _p, _p, _p, _p, ctypes.c_int64], ctypes.c_int),
+    "qldpc_server_replay": ([_p, _i32, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, ctypes.c_int64], ctypes.c_int),
     "qldpc_server_status": ([_p, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
+    "qldpc_server_info": ([_p, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_size_t)],
+                          ctypes.c_int),
     "qldpc_server_destroy": ([_p], None),
     "qldpc_graph_set_weights": ([_p, _p, _i32], ctypes.c_int),
     "qldpc_nms_workspace_bytes": ([_p, _i32, _i32, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
@@ -108,12 +113,14 @@ qldpc_graph_create_csc = _lib.qldpc_graph_create_csc
 qldpc_graph_destroy = _lib.qldpc_graph_destroy
 qldpc_graph_dims = _lib.qldpc_graph_dims
 qldpc_graph_footprint = _lib.qldpc_graph_footprint
+qldpc_graph_layers = _lib.qldpc_graph_layers
 qldpc_graph_set_launch = _lib.qldpc_graph_set_launch
 qldpc_graph_reserve = _lib.qldpc_graph_reserve
 qldpc_decode = _lib.qldpc_decode
 qldpc_decode_ex = _lib.qldpc_decode_ex
 qldpc_decode_pair = _lib.qldpc_decode_pair
 qldpc_decode_host = _lib.qldpc_decode_host
+qldpc_decode_pair_host = _lib.qldpc_decode_pair_host
 qldpc_status_string = _lib.qldpc_status_string
 qldpc_decode_host_noalloc = _lib.qldpc_decode_host_noalloc
 qldpc_noalloc_scratch_bytes = _lib.qldpc_noalloc_scratch_bytes
@@ -122,6 +129,7 @@ qldpc_server_submit = _lib.qldpc_server_submit
 qldpc_server_poll = _lib.qldpc_server_poll
 qldpc_server_replay = _lib.qldpc_server_replay
 qldpc_server_status = _lib.qldpc_server_status
+qldpc_server_info = _lib.qldpc_server_info
 qldpc_server_destroy = _lib.qldpc_server_destroy
 qldpc_graph_set_weights = _lib.qldpc_graph_set_weights
 qldpc_nms_workspace_bytes = _lib.qldpc_nms_workspace_bytes
@@ -205,6 +213,12 @@ class Graph:
         vals = [ctypes.c_int32() for _ in range(5)]
         check(qldpc_graph_dims(self._h, *[ctypes.byref(v) for v in vals]), "qldpc_graph_dims")
         return tuple(v.value for v in vals)
+
+    def layers(self, widest: bool = False):
+        """Number of layers of the layered schedule in this row order (and the widest layer)."""
+        n_l, w_l = _i32(), _i32()
+        check(qldpc_graph_layers(self._h, ctypes.byref(n_l), ctypes.byref(w_l)), "qldpc_graph_layers")
+        return (n_l.value, w_l.value) if widest else n_l.value
 
     def footprint(self, precision: str = "fp32"):
         """(variable lanes, shared-memory bytes of one shot in the throughput kernel)."""
@@ -382,12 +396,37 @@ def decode_host(graph: Graph, syndromes: np.ndarray, prior: np.ndarray, max_iter
     return err, iters, ok
 
 
+def decode_pair_host(graph_z: Graph, graph_x: Graph, s_x: np.ndarray, s_z: np.ndarray, prior_x: np.ndarray,
+                     prior_z: np.ndarray, max_iter: int, alpha: float = 0.75, precision: str = "fp32",
+                     early_stop: bool = True, out=None, stream=None, layered: bool = False):
+    """X+Z pair decode (one launch) end to end from host (numpy) buffers; synchronous.  s_x [B, m_z]
+    is decoded with graph_z, s_z [B, m_x] with graph_x.  Returns ((err_x, iters_x, ok_x), (err_z,
+    iters_z, ok_z)); out, if given, is that pair of triples (page-locked arrays avoid all copies)."""
+    sx = np.ascontiguousarray(s_x, dtype=np.uint8)
+    sz = np.ascontiguousarray(s_z, dtype=np.uint8)
+    batch = sx.shape[0]
+    if sx.shape != (batch, graph_z.m) or sz.shape != (batch, graph_x.m):
+        raise ValueError("s_x must be (B, m_z) and s_z (B, m_x)")
+    px = np.ascontiguousarray(prior_x, dtype=np.float32)
+    pz = np.ascontiguousarray(prior_z, dtype=np.float32)
+    if out is None:
+        out = tuple((np.empty((batch, graph_z.n), np.uint8), np.empty(batch, np.int32), np.empty(batch, np.uint8))
+                    for _ in range(2))
+    (ex, ix, ox), (ez, iz, oz) = out
+    sh = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+    check(qldpc_decode_pair_host(graph_z.handle, graph_x.handle, _np_ptr(sx), _np_ptr(sz), batch, _np_ptr(px),
+                                 _np_ptr(pz), int(max_iter), float(alpha), _np_ptr(ex), _np_ptr(ez), _np_ptr(ix),
+                                 _np_ptr(iz), _np_ptr(ox), _np_ptr(oz), PRECISIONS[precision],
+                                 _flags(early_stop, False, layered), sh), "qldpc_decode_pair_host")
+    return out
+
+
 class Server:
     """Persistent decoding server over up to four codes (qldpc_server_*).
 
     graphs: list of Graph; priors: list of float32 [n] numpy arrays (host).  The worker kernel starts
     on the first request and leaves after `idle_timeout_s` without requests (restarted on demand).
-    layered=True: workers on the layered schedule (codes of at most 8 layers of rows of degree <= 8).
+    layered=True: workers on the layered schedule (rows of degree <= 8, at most 256 checks per layer).
     """
 
     def __init__(self, graphs, priors, max_iter: int, alpha: float = 0.75, precision: str = "fp32",
@@ -439,10 +478,11 @@ class Server:
         check(rc, "qldpc_server_poll")
         return err, it.value, ok.value
 
-    def replay(self, codes, syndromes, arrival_ns, timeout_s: float = 10.0):
+    def replay(self, codes, syndromes, arrival_ns, timeout_s: float = 10.0, want_workers: bool = False):
         """Open-loop replay: request i = (codes[i], syndromes[i]) submitted at arrival_ns[i].
 
-        Returns (errs list of uint8 arrays, iters int32 [R], ok uint8 [R], latency_ns int64 [R]).
+        Returns (errs list of uint8 arrays, iters int32 [R], ok uint8 [R], latency_ns int64 [R]), plus
+        workers int32 [R] (the worker block that decoded each request) with want_workers=True.
         """
         codes = np.ascontiguousarray(codes, dtype=np.int32)
         nreq = len(codes)
@@ -462,11 +502,21 @@ class Server:
         iters = np.zeros(nreq, dtype=np.int32)
         ok = np.zeros(nreq, dtype=np.uint8)
         lat = np.zeros(nreq, dtype=np.int64)
+        workers = np.full(max(nreq, 1), -1, dtype=np.int32)
         check(qldpc_server_replay(self._h, nreq, _np_ptr(codes), _np_ptr(syn_flat), _np_ptr(syn_off),
                                   _np_ptr(arrival), _np_ptr(err_flat), _np_ptr(err_off), _np_ptr(iters),
-                                  _np_ptr(ok), _np_ptr(lat), int(timeout_s * 1e9)), "qldpc_server_replay")
+                                  _np_ptr(ok), _np_ptr(lat), _np_ptr(workers), int(timeout_s * 1e9)),
+              "qldpc_server_replay")
         errs = [err_flat[err_off[i]:err_off[i] + self.graphs[codes[i]].n] for i in range(nreq)]
+        if want_workers:
+            return errs, iters, ok, lat, workers[:nreq]
         return errs, iters, ok, lat
+
+    def info(self) -> dict:
+        """The worker pool: {"workers", "threads_per_block", "smem_per_block"}."""
+        wk, th, sm = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_size_t()
+        check(qldpc_server_info(self._h, ctypes.byref(wk), ctypes.byref(th), ctypes.byref(sm)), "qldpc_server_info")
+        return {"workers": wk.value, "threads_per_block": th.value, "smem_per_block": sm.value}
 
     def status(self) -> int:
         st = ctypes.c_uint32()

@@ -345,6 +345,48 @@ def data_syndrome_csr(h: CSR) -> CSR:
     return CSR(row_ptr, np.concatenate(cols) if cols else np.zeros(0, np.int32), h.m, h.n + h.m)
 
 
+def csr_rows(h: CSR, order) -> CSR:
+    """H with its rows permuted: row i of the result is row order[i] of h (same columns).  The
+    syndrome of the result is s[:, order]."""
+    order = np.asarray(order, dtype=np.int64)
+    rp = np.asarray(h.row_ptr, dtype=np.int64)
+    deg = rp[order + 1] - rp[order]
+    row_ptr = np.concatenate([[0], np.cumsum(deg)]).astype(np.int32)
+    cols = [np.asarray(h.col_idx[rp[i]:rp[i + 1]], dtype=np.int32) for i in order]
+    return CSR(row_ptr, np.concatenate(cols) if cols else np.zeros(0, np.int32), h.m, h.n)
+
+
+def layer_order(h: CSR) -> np.ndarray:
+    """A row order for the layered schedule with few layers: rows that share a variable get
+    different colours (greedy colouring, most-constrained row first), and rows are listed colour by
+    colour in ascending index.  In that order every colour class is a set of rows without a common
+    variable, so the as-soon-as-possible layering of the reordered matrix needs at most as many
+    layers as there are colours.  (A different row order is a different layered schedule.)"""
+    rp = np.asarray(h.row_ptr, dtype=np.int64)
+    rows_of = [[] for _ in range(h.n)]
+    for i in range(h.m):
+        for v in h.col_idx[rp[i]:rp[i + 1]]:
+            rows_of[int(v)].append(i)
+    nbrs = [set() for _ in range(h.m)]
+    for rows in rows_of:
+        for a in rows:
+            nbrs[a].update(rows)
+    for i in range(h.m):
+        nbrs[i].discard(i)
+    colour = np.full(h.m, -1, dtype=np.int64)
+    seen = [set() for _ in range(h.m)]          # colours of the coloured neighbours
+    for _ in range(h.m):
+        cand = [i for i in range(h.m) if colour[i] < 0]
+        i = max(cand, key=lambda r: (len(seen[r]), len(nbrs[r]), -r))
+        c = 0
+        while c in seen[i]:
+            c += 1
+        colour[i] = c
+        for j in nbrs[i]:
+            seen[j].add(c)
+    return np.lexsort((np.arange(h.m), colour))
+
+
 def noisy_syndrome_batch(h: CSR, p: float, q: float, shots: int, seed: int, first_shot: int = 0):
     """Data errors at rate p and syndrome measurement errors at rate q, one draw per shot:
     e[b, j] = [u(seed, b, j) < p] for the n data bits, e'[b, i] = [u(seed, b, n + i) < q] for the m

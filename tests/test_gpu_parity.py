@@ -364,6 +364,36 @@ def test_host_path_with_pinned_buffers(q):
             np.testing.assert_array_equal(iters2, dev["iters"])
 
 
+@pytest.mark.parametrize("name", ["bb144", "bb288"])
+def test_pair_host_path_matches_oracle(q, name):
+    """The X+Z pair end to end with host buffers (qldpc_decode_pair_host): page-locked buffers (no
+    copies) and pageable ones (staged), in plain and the paper's mode, against the oracle's two
+    separate decodes; single shots (the latency sweep) and a batch."""
+    code = w.CONFIG_CODES[name]()
+    gz, gx = q.Graph.from_csr(code.hz_csr), q.Graph.from_csr(code.hx_csr)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    ex, ez = w.depolarizing_errors(code.n, 0.04, 300, seed=3301)
+    sx, sz = w.syndromes(code.hz_csr, ex), w.syndromes(code.hx_csr, ez)
+    prior = np.full(code.n, w.prior_llr(2 * 0.04 / 3), dtype=np.float32)
+    for max_iter, early in ((64, True), (10, False)):
+        ox = oracle_decode(code.hz_csr, sx, prior, max_iter, 0.75, "fp32", early)
+        oz = oracle_decode(code.hx_csr, sz, prior, max_iter, 0.75, "fp32", early)
+        for pinned in (True, False):
+            for lo, hi in ((0, 1), (1, 2), (2, 300)):
+                a, b = (pin(sx[lo:hi]), pin(sz[lo:hi])) if pinned else (sx[lo:hi].copy(), sz[lo:hi].copy())
+                outs = None
+                if pinned:
+                    outs = tuple((pin(np.zeros((hi - lo, code.n), np.uint8)), pin(np.zeros(hi - lo, np.int32)),
+                                  pin(np.zeros(hi - lo, np.uint8))) for _ in range(2))
+                (rx, rz) = q.decode_pair_host(gz, gx, a, b, prior, prior, max_iter, 0.75, "fp32", early, out=outs)
+                for got, ref in ((rx, ox), (rz, oz)):
+                    np.testing.assert_array_equal(got[0], ref["err"][lo:hi])
+                    np.testing.assert_array_equal(got[1], ref["iters"][lo:hi])
+                    np.testing.assert_array_equal(got[2], ref["ok"][lo:hi])
+    with pytest.raises(q.QldpcError):
+        q.decode_pair_host(gz, gz, sx[:1], sx[:1], prior, prior, 10)      # one graph for both halves
+
+
 def test_side_stream(q):
     code = w.hgp_code(400)
     graph = q.Graph.from_csr(code.hz_csr)

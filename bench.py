@@ -112,7 +112,14 @@ def parse():
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp32", "int16"], default="fp32")
+    ap.add_argument("--precision", choices=["fp32", "int16", "int8"], default="fp32")
+    ap.add_argument("--kernel", choices=["auto", "batch", "packed"], default="auto",
+                    help="throughput kernel of the timed decode (packed: two fixed-point shots per word)")
+    ap.add_argument("--profile", choices=["none", "server", "server-layered", "launch", "launch-layered"],
+                    default="none",
+                    help="only run single LP-1054 shots, each in a kernel launch of its own that ends by itself "
+                         "(server: isolated requests to workers with a 50 us idle timeout; launch: "
+                         "qldpc_decode_host with B = 1), for an ncu capture of that kernel, then exit")
     ap.add_argument("--batch", type=int, default=BATCH)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-latency", action="store_true")
@@ -237,7 +244,7 @@ class ClockSampler:
 # ------------------------------------------------------------------------------------------------
 def oracle_rate(batches, shots_per_batch: int, precision: str, threads: int):
     import oracle
-    oprec = {"fp32": "f32", "int16": "i16"}[precision]
+    oprec = {"fp32": "f32", "int16": "i16", "int8": "i8"}[precision]
     total = 0
     t0 = time.perf_counter()
     for b in batches:
@@ -253,7 +260,7 @@ def oracle_single_thread(batches, precision: str, shots: int = 2000):
     """The oracle on one core, one shot per call, on the p = 0.03 batch: shots/s and per-shot
     latency percentiles (host clock around each call, Python call overhead included)."""
     import oracle
-    oprec = {"fp32": "f32", "int16": "i16"}[precision]
+    oprec = {"fp32": "f32", "int16": "i16", "int8": "i8"}[precision]
     b = batches[P_GRID.index(0.03)]
     shots = min(shots, b.syndromes.shape[0])
     lat = np.empty(shots)
@@ -267,6 +274,47 @@ def oracle_single_thread(batches, precision: str, shots: int = 2000):
             "shots": shots, "p": 0.03, "cores": 1}
 
 
+def oracle_configs(threads: int) -> dict:
+    """The oracle on each configuration's workload (the CPU baseline table): single-thread shots/s and
+    per-shot latency percentiles (one shot per call), all-core shots/s, mean iterations.  HGP-400: 1000
+    shots at p = 0.05, max 32; LP-1054: the p = 0.03 benchmark rate, max 50; BB-144 / BB-288: X+Z
+    pairs (two decodes per shot) at p = 0.03 depolarizing, max 64.  FP32 and INT16."""
+    import oracle
+    from paper_2508_07879_gb300 import workloads as w
+    out = {"cores": threads}
+    cases = {"hgp400": (w.x_error_batch(w.hgp_code(400), 0.05, 1000, seed=1), None, 32, 300),
+             "lp1054": (w.x_error_batch(w.lp_code(1054), 0.03, 4096, seed=2003), None, 50, 300)}
+    for name in ("bb144", "bb288"):
+        code = w.CONFIG_CODES[name]()
+        ex, ez = w.depolarizing_errors(code.n, 0.03, 2000, seed=3003)
+        prior = np.full(code.n, w.prior_llr(0.02), dtype=np.float32)
+        cases[name] = ((code.hz_csr, w.syndromes(code.hz_csr, ex), prior),
+                       (code.hx_csr, w.syndromes(code.hx_csr, ez), prior), 64, 300)
+    for name, (a, b, max_iter, single) in cases.items():
+        halves = [(a.h, a.syndromes, a.prior)] if b is None else [a, b]
+        row = {}
+        for prec, oprec in (("fp32", "f32"), ("int16", "i16")):
+            shots = halves[0][1].shape[0]
+            t0 = time.perf_counter()
+            its = 0
+            for h, syn, prior in halves:
+                its += int(oracle.msa(h.row_ptr, h.col_idx, h.m, h.n, syn, prior, max_iter, ALPHA, oprec, True,
+                                      threads=threads)["iters"].sum())
+            all_core = shots / (time.perf_counter() - t0)
+            lat = np.empty(single)
+            for i in range(single):
+                t1 = time.perf_counter_ns()
+                for h, syn, prior in halves:
+                    oracle.msa(h.row_ptr, h.col_idx, h.m, h.n, syn[i:i + 1], prior, max_iter, ALPHA, oprec, True,
+                               threads=1)
+                lat[i] = (time.perf_counter_ns() - t1) / 1e3
+            row[prec] = {"all_core_shots_per_s": all_core, "single_thread_shots_per_s": single / (lat.sum() / 1e6),
+                         "p50_us": float(np.percentile(lat, 50)), "p99_us": float(np.percentile(lat, 99)),
+                         "mean_iters": its / (shots * len(halves)), "shots": shots, "single_thread_shots": single}
+        out[name] = row
+    return out
+
+
 def run_reference(args, rank, world):
     """The reference arm: the CPU oracle, as it stands, on all host cores.  Each step decodes the
     same sample the cpu_baseline leg uses, 8192 shots of one rate's benchmark batch, cycling
@@ -278,7 +326,7 @@ def run_reference(args, rank, world):
     code, batches = make_batches(per_step, 0)
     import oracle
     oracle.build()
-    oprec = {"fp32": "f32", "int16": "i16"}[args.precision]
+    oprec = {"fp32": "f32", "int16": "i16", "int8": "i8"}[args.precision]
 
     def step(i):
         b = batches[i % len(batches)]
@@ -296,7 +344,7 @@ def run_reference(args, rank, world):
         "impl": "reference", "metric": "syndromes/sec", "value": value, "unit": "syndromes/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": {"fp32": "f32", "int16": "i16"}[args.precision],
+        "vs_baseline": None, "dtype": {"fp32": "f32", "int16": "i16", "int8": "i8"}[args.precision],
         "data": "synthetic",
         "config": bench_config(BATCH, world, args.precision),
         "cpu_baseline": {"value": value, "unit": "syndromes/s", "cores": threads, "kind": "oracle",
@@ -323,11 +371,15 @@ def run_ours(args, rank, world, local):
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if args.profile != "none":
+        return profile_single(qldpc, args.profile, args.precision)
     B = args.batch
     first, _ = shard(rank, world, B)
     code, batches = make_batches(B, first_shot=first)       # each rank its own shots (weak scaling)
     h = batches[0].h
     graph = qldpc.Graph.from_csr(h)
+    if args.kernel != "auto":
+        graph.set_launch(args.kernel)
     dev = torch.device("cuda", local)
     syn_d = [torch.from_numpy(b.syndromes).to(dev) for b in batches]
     pri_d = [torch.from_numpy(b.prior).to(dev) for b in batches]
@@ -375,8 +427,9 @@ def run_ours(args, rank, world, local):
     # edge-iterations it runs: E x (iterations summed over its 65536 shots)
     props = torch.cuda.get_device_properties(dev)
     clocks = clk.summary()
+    kernel_name = "msa_batch_kernel" if args.precision == "fp32" or args.kernel == "batch" else "msa_packed_kernel"
     roofline = decoder_roofline(h, B, iters_per_batch, args.steps, ms_per_step, args.precision,
-                                props.multi_processor_count, clocks["sm_max_mhz"] or 2070.0)
+                                props.multi_processor_count, clocks["sm_max_mhz"] or 2070.0, kernel_name)
 
     e2e = None
     if not args.no_e2e:
@@ -406,14 +459,15 @@ def run_ours(args, rank, world, local):
         cpu = {"value": rate, "unit": "syndromes/s", "cores": threads, "kind": "oracle",
                "sample": f"{n} shots ({CPU_SHOTS_PER_P} per p at p=0.01..0.05) of the same batches, "
                          f"{dt:.1f} s wall, about {dt * threads:.0f} core-s",
-               "single_thread": oracle_single_thread(batches, args.precision)}
+               "single_thread": oracle_single_thread(batches, args.precision),
+               "per_config": oracle_configs(threads)}
 
     if rank == 0:
         line = {
             "metric": "syndromes/sec", "value": value, "unit": "syndromes/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp32": "f32", "int16": "i16"}[args.precision], "data": "synthetic",
+            "dtype": {"fp32": "f32", "int16": "i16", "int8": "i8"}[args.precision], "data": "synthetic",
             "config": bench_config(B, world, args.precision),
             "roofline": roofline,
             "cpu_baseline": cpu,
@@ -430,7 +484,35 @@ def run_ours(args, rank, world, local):
     return 0
 
 
-def decoder_roofline(h, B, iters_per_batch, steps, ms_per_step, precision, sms, max_mhz):
+def profile_single(qldpc, mode: str, precision: str, shots: int = 40):
+    """Single LP-1054 shots (p = 0.03), each in a kernel launch of its own that ends by itself (the
+    form an ncu capture of a persistent worker needs).  server / server-layered: isolated requests to
+    workers that leave 50 us after their last request, each collected before the next is submitted;
+    launch / launch-layered: qldpc_decode_host with B = 1."""
+    from paper_2508_07879_gb300 import workloads as w
+    b = w.x_error_batch(w.lp_code(1054), LAT_P, shots, seed=4003)
+    g = qldpc.Graph.from_csr(b.h)
+    layered = mode.endswith("layered")
+    if mode.startswith("server"):
+        with qldpc.Server([g], [b.prior], MAX_ITER, ALPHA, precision, blocks=[8], idle_timeout_s=5e-5,
+                          layered=layered) as srv:
+            for i in range(shots):
+                t = srv.submit(0, b.syndromes[i])
+                res = None
+                deadline = time.time() + 10
+                while res is None and time.time() < deadline:
+                    res = srv.poll(0, t)
+                if res is None:
+                    raise RuntimeError("server request timed out")
+                time.sleep(2e-4)                     # > idle timeout: the workers leave
+    else:
+        for i in range(shots):
+            qldpc.decode_host(g, b.syndromes[i:i + 1], b.prior, MAX_ITER, ALPHA, precision, layered=layered)
+    print(json.dumps({"profile": mode, "precision": precision, "shots": shots}), flush=True)
+    return 0
+
+
+def decoder_roofline(h, B, iters_per_batch, steps, ms_per_step, precision, sms, max_mhz, kernel_name):
     """Algorithmic work of one launch against the kernel's roofs.  The binding roof is the one with
     the longest time at peak: shared-memory message traffic (4 accesses of one message per edge and
     iteration, 32 banks x 4 B per clock per SM) or ALU issue (10 operations per edge and iteration,
@@ -462,13 +544,13 @@ def decoder_roofline(h, B, iters_per_batch, steps, ms_per_step, precision, sms, 
            "frac": round(hbm_bytes / t / hbm_peak, 5), "bytes_per_launch": hbm_bytes, "peak_basis": hbm_basis}
     binding = "smem" if smem["time_at_peak_ms"] >= alu["time_at_peak_ms"] else "alu"
     top = smem if binding == "smem" else alu
-    traffic = kernel_traffic() if (B == BATCH and precision == "fp32") else None
+    traffic = kernel_traffic() if (B == BATCH and kernel_name == "msa_batch_kernel" and precision == "fp32") else None
     return {"bound": binding, "achieved": top["achieved"], "peak": top["peak"], "unit": top["unit"],
             "frac": top["frac"], "traffic": traffic,
             "traffic_source": {"kind": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch",
                                "source_sha16": NCU_TRAFFIC["source_sha16"],
                                "current": traffic is not None},
-            "kernel": "msa_batch_kernel", "smem": smem, "alu": alu, "hbm": hbm}
+            "kernel": kernel_name, "smem": smem, "alu": alu, "hbm": hbm}
 
 
 def headline(line) -> dict:
@@ -880,7 +962,9 @@ def measure_precisions(qldpc, graph, syn_d, pri_d, out, stream, B, args, steps=1
     """Flooding decode of the benchmark's batches in each precision: throughput and decoded fraction."""
     import torch
     res = {}
-    for prec in ("fp32", "int16", "int8"):
+    for name in ("fp32", "int16", "int8", "int16_scalar", "int8_scalar"):
+        prec = name.split("_")[0]
+        graph.set_launch("batch" if name.endswith("_scalar") else "auto")
         ok = iters = 0
         with torch.cuda.stream(stream):
             for j in range(len(syn_d)):
@@ -900,8 +984,11 @@ def measure_precisions(qldpc, graph, syn_d, pri_d, out, stream, B, args, steps=1
                 qldpc.decode(graph, syn_d[j], pri_d[j], MAX_ITER, ALPHA, prec, out=out, stream=stream)
             e1.record(stream)
             stream.synchronize()
-        res[prec] = {"value": B * steps / (e0.elapsed_time(e1) / 1e3), "unit": "syndromes/s",
-                     "decoded_fraction": ok / (len(syn_d) * B), "mean_iters": iters / (len(syn_d) * B)}
+        res[name] = {"value": B * steps / (e0.elapsed_time(e1) / 1e3), "unit": "syndromes/s",
+                     "decoded_fraction": ok / (len(syn_d) * B), "mean_iters": iters / (len(syn_d) * B),
+                     "kernel": "msa_batch_kernel (one shot per block)" if name.endswith("_scalar") or prec == "fp32"
+                     else "msa_packed_kernel (two shots per block)"}
+    graph.set_launch("auto")
     return res
 
 

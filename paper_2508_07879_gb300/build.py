@@ -24,10 +24,11 @@ NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibilit
               "-Xptxas", "-v", "--fmad=false"]
 CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-fvisibility=hidden", "-Wall", "-Wextra"]
 
-KERNEL_SOURCES = ["msa_f32.cu", "msa_i16.cu", "msa_i8.cu", "msa_learned.cu", "msa_layered.cu", "nms_train.cu", "server_f32.cu",
-                  "server_i16.cu", "server_i8.cu", "qldpc_noalloc.cu"]
+KERNEL_SOURCES = ["msa_f32.cu", "msa_i16.cu", "msa_i8.cu", "msa_i16x2.cu", "msa_i8x2.cu", "msa_learned.cu",
+                  "msa_layered.cu", "nms_train.cu", "server_f32.cu", "server_i16.cu", "server_i8.cu",
+                  "qldpc_noalloc.cu"]
 HOST_SOURCES = ["qldpc_host.cpp", "qldpc_server.cpp", "qldpc_learned.cpp"]
-HEADERS = ["msa_launch.h", "msa_kernel.cuh", "server_kernel.cuh", "graph.h"]
+HEADERS = ["msa_launch.h", "msa_kernel.cuh", "msa_packed.cuh", "server_kernel.cuh", "graph.h"]
 
 
 def _nvcc() -> str:

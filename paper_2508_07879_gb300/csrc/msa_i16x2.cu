@@ -1,0 +1,14 @@
+// INT16 instantiations of the two-shots-per-word throughput kernel (see msa_packed.cuh).
+#include "msa_packed.cuh"
+
+namespace qldpc {
+
+const void *msa_kernel_i16x2(const KernelChoice &kc) { return packed_table<kern::I16>(kc); }
+
+cudaError_t launch_msa_i16x2(const LaunchParams &p, const KernelChoice &kc, dim3 grid, int threads, size_t smem,
+                             cudaStream_t stream)
+{
+    return packed_launch<kern::I16>(p, kc, grid, threads, smem, stream);
+}
+
+}  // namespace qldpc

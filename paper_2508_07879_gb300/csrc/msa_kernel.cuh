@@ -97,6 +97,7 @@ struct F32 {
 //   I16: 8 fractional bits, +-32767;  I8: 2 fractional bits, +-127.
 template <class MSG, int FRAC, int LIM>
 struct IFix {
+    static constexpr int kFrac = FRAC, kLim = LIM;
     using acc_t = int32_t;
     using mag_t = int32_t;
     using msg_t = MSG;

@@ -118,6 +118,7 @@ struct KernelChoice {
     int dvb;         // column-degree bucket 4/8/16
     bool learned = false;   // learned weights first, then plain fallback (FP32 only)
     bool layered = false;   // msa_layered_kernel (row-serial schedule)
+    bool packed = false;    // msa_packed_kernel: two fixed-point shots per message word (INT16 / INT8)
 };
 
 // Latency kernel limits: checks M <= 2 * threads, variables N <= 2 * threads, threads <= 640
@@ -209,6 +210,34 @@ cudaError_t launch_msa_i16(const LaunchParams &p, const KernelChoice &kc, dim3 g
 const void *msa_kernel_i8(const KernelChoice &kc);
 cudaError_t launch_msa_i8(const LaunchParams &p, const KernelChoice &kc, dim3 grid, int threads,
                           size_t smem, cudaStream_t stream);
+// Two-shots-per-word fixed-point throughput kernels, msa_i16x2.cu / msa_i8x2.cu (msa_packed.cuh).
+const void *msa_kernel_i16x2(const KernelChoice &kc);
+const void *msa_kernel_i8x2(const KernelChoice &kc);
+cudaError_t launch_msa_i16x2(const LaunchParams &p, const KernelChoice &kc, dim3 grid, int threads,
+                             size_t smem, cudaStream_t stream);
+cudaError_t launch_msa_i8x2(const LaunchParams &p, const KernelChoice &kc, dim3 grid, int threads,
+                            size_t smem, cudaStream_t stream);
+
+// Threads per block of the packed kernel at most (its register budget assumes no more).
+constexpr int kPackedMaxThreads = 512;
+
+// Shared memory of one block of the packed kernel (two shots): gamma [nv] i32, Q [nv] i32x2,
+// parity words [m], packed message slots [dc_max*m + scratch] u32.
+struct PackedLayout {
+    size_t g_off, q_off, par_off, slot_off, total;
+};
+
+__host__ __device__ inline PackedLayout packed_layout(int m, int nv, int dc_max)
+{
+    PackedLayout l;
+    l.g_off = 0;
+    l.q_off = align16(size_t(nv) * 4);
+    l.par_off = align16(l.q_off + size_t(nv) * 8);
+    l.slot_off = align16(l.par_off + size_t(m) * 4);
+    l.total = align16(l.slot_off + (size_t(dc_max) * m + kScratch) * 4);
+    return l;
+}
+
 // Layered-schedule kernels, msa_layered.cu.
 const void *msa_kernel_layered(int precision, const KernelChoice &kc);
 cudaError_t launch_msa_layered(int precision, const LaunchParams &p, const KernelChoice &kc, dim3 grid, int threads,

@@ -1,0 +1,372 @@
+// Two fixed-point shots per message word: the throughput kernel of the INT16 and INT8 modes.
+//
+// Algorithm 1 (Sec. 2 of arXiv 2508.07879) with the integer arithmetic of the IFix policies of
+// msa_kernel.cuh, but every shared-memory slot holds the same edge's message of two shots, lane 0
+// in bits 0..15 and lane 1 in bits 16..31 (16-bit two's complement; INT8 messages are held in
+// 16-bit lanes too, within +-127).  One block decodes two shots at a time:
+//   * check step: one thread per check handles both shots with paired-lane instructions (min/max
+//     of s16x2 / u16x2, lane-wise add, byte permutes), one load and one store per edge for both;
+//   * variable step: one thread per variable loads each slot word once for both shots, sums each
+//     lane in 32 bits exactly (Q_n = gamma_n + sum r, q = clamp(Q_n - r)) and packs the pair back;
+//     the edge list, degree and prior are read once for both shots;
+//   * stop test: the parity word of a check carries both shots (bit 0: lane 0's s_m xor decisions,
+//     bit 15: lane 0's s_m, bit 16 and bit 31 the same for lane 1), so one block OR settles both.
+// Each lane stops at its own iteration (the scalar kernel's rule) and is refilled with the next
+// shot of the batch in the same variable step, so a lane never waits for its partner: the block
+// takes shots from the launch's counter one lane at a time.
+//
+// A refill writes the prior into the lane's half of every slot and Q, and flips the lane's parity
+// bit of a check where the variable's decision changes from the old shot's to the prior's; the next
+// check step replaces the old syndrome bit by the new one (bit 0 and bit 15 both take s_old xor
+// s_new), which leaves exactly the initial state of the new shot.
+#pragma once
+
+#include "msa_kernel.cuh"
+
+namespace qldpc {
+namespace kern {
+
+// ---------------------------------------------------------------------------------------------
+// Paired-lane helpers (lane 0 = bits 0..15, lane 1 = bits 16..31)
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t max_s16x2(uint32_t a, uint32_t b)
+{
+    uint32_t d;
+    asm("max.s16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+__device__ __forceinline__ uint32_t min_s16x2(uint32_t a, uint32_t b)
+{
+    uint32_t d;
+    asm("min.s16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+__device__ __forceinline__ uint32_t max_u16x2(uint32_t a, uint32_t b)
+{
+    uint32_t d;
+    asm("max.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+__device__ __forceinline__ uint32_t min_u16x2(uint32_t a, uint32_t b)
+{
+    uint32_t d;
+    asm("min.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+// lane-wise sum modulo 2^16 (no carry between the lanes)
+__device__ __forceinline__ uint32_t add_u16x2(uint32_t a, uint32_t b)
+{
+    uint32_t d;
+    asm("add.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+// each lane's sign bit (bit 15 / bit 31) replicated over its 16 bits: a byte permute whose
+// selector nibbles 0x9 / 0xB take the sign of byte 1 / byte 3
+__device__ __forceinline__ uint32_t signmask16x2(uint32_t x)
+{
+    uint32_t d;
+    asm("prmt.b32 %0, %1, 0, 0xBB99;" : "=r"(d) : "r"(x));
+    return d;
+}
+// lane-wise negation (two's complement; -0 = 0 without a carry into the other lane)
+__device__ __forceinline__ uint32_t neg16x2(uint32_t x) { return add_u16x2(~x, 0x00010001u); }
+// lane-wise |x| for lanes in [-32767, 32767]
+__device__ __forceinline__ uint32_t abs16x2(uint32_t x) { return max_s16x2(x, neg16x2(x)); }
+// a where the lane of m is all ones, else b
+__device__ __forceinline__ uint32_t select16x2(uint32_t m, uint32_t a, uint32_t b) { return (a & m) | (b & ~m); }
+__device__ __forceinline__ int32_t lane0(uint32_t w) { return int32_t(int16_t(uint16_t(w & 0xffffu))); }
+__device__ __forceinline__ int32_t lane1(uint32_t w) { return int32_t(w) >> 16; }
+// Saturate two 32-bit sums to [-32768, 32767] and pack them (lane 0 = x0, lane 1 = x1).
+// cvt.pack.sat.s16.s32 d, a, b puts a in the upper and b in the lower half.
+__device__ __forceinline__ uint32_t pack_sat16x2(int32_t x0, int32_t x1)
+{
+    uint32_t d;
+    asm("cvt.pack.sat.s16.s32 %0, %1, %2;" : "=r"(d) : "r"(x1), "r"(x0));
+    return d;
+}
+
+// The message clamp of a fixed-point policy on a packed pair: [-LIM, LIM] in each lane.
+template <class P>
+__device__ __forceinline__ uint32_t clamp_pair(int32_t x0, int32_t x1)
+{
+    constexpr uint32_t lim = uint32_t(P::kLim) | (uint32_t(P::kLim) << 16);
+    constexpr uint32_t nlim = (uint32_t(-P::kLim) & 0xffffu) | ((uint32_t(-P::kLim) & 0xffffu) << 16);
+    const uint32_t w = pack_sat16x2(x0, x1);        // [-32768, 32767]
+    if constexpr (P::kLim == 32767) return max_s16x2(w, nlim);
+    else return max_s16x2(min_s16x2(w, lim), nlim);
+}
+
+// |r| = floor(min * alpha_q / 2^15) in each lane (min <= 32767, alpha_q <= 2^15: 30-bit products)
+__device__ __forceinline__ uint32_t scale16x2(uint32_t m, int32_t alpha_q)
+{
+    const uint32_t lo = (uint32_t(m & 0xffffu) * uint32_t(alpha_q)) >> 15;
+    const uint32_t hi = ((m >> 16) * uint32_t(alpha_q)) >> 15;
+    return lo | (hi << 16);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Check step of one check for both lanes (Alg. 1, CN processing).  pw: the check's parity word
+// (bits 15 / 31: s_m of lane 0 / 1).  Writes r over q in place.
+// ---------------------------------------------------------------------------------------------
+template <class P, int DC, bool UNIFORM>
+__device__ __forceinline__ void check_step_x2(int c, int M, int deg, uint32_t pw, uint32_t *__restrict__ slots,
+                                              int32_t alpha_q)
+{
+    uint32_t q[DC], a[DC];
+    uint32_t sx = 0;
+#pragma unroll
+    for (int j = 0; j < DC; ++j) {
+        if (UNIFORM || j < deg) {
+            q[j] = slots[j * M + c];
+            sx ^= q[j];                                 // bits 15 / 31: parity of the signs
+            a[j] = abs16x2(q[j]);
+        }
+    }
+    // the two smallest magnitudes of each lane, with multiplicity
+    uint32_t m1 = 0x7fff7fffu, m2 = 0x7fff7fffu;
+#pragma unroll
+    for (int j = 0; j < DC; ++j) {
+        if (UNIFORM || j < deg) {
+            m2 = min_u16x2(m2, max_u16x2(m1, a[j]));
+            m1 = min_u16x2(m1, a[j]);
+        }
+    }
+    // (-1)^{s_m} prod of all signs, per lane, replicated over the lane
+    const uint32_t negm = signmask16x2(pw ^ sx);
+    const uint32_t s1 = scale16x2(m1, alpha_q), s2 = scale16x2(m2, alpha_q);
+    const uint32_t n1 = neg16x2(s1), n2 = neg16x2(s2);
+    // alpha * min over the others with the check's factor applied (r1: |q| above the minimum, r2: at
+    // it), and the same negated for an edge whose own sign is negative
+    const uint32_t rp1 = select16x2(negm, n1, s1), rp2 = select16x2(negm, n2, s2);
+    const uint32_t rn1 = select16x2(negm, s1, n1), rn2 = select16x2(negm, s2, n2);
+    const uint32_t m1p = m1 + 0x00010001u;             // no carry: m1 <= 32767 per lane
+#pragma unroll
+    for (int j = 0; j < DC; ++j) {
+        if (UNIFORM || j < deg) {
+            // bit 15 of each lane of (|q| + 0x8000) - (m1 + 1) is set iff |q| > m1 (|q| >= m1, so no
+            // borrow crosses the lanes)
+            const uint32_t gt = signmask16x2((a[j] | 0x80008000u) - m1p);
+            const uint32_t pos = select16x2(gt, rp1, rp2), neg = select16x2(gt, rn1, rn2);
+            slots[j * M + c] = select16x2(signmask16x2(q[j]), neg, pos);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Variable step of one variable of degree exactly D for both lanes (Alg. 1, VN processing,
+// a-posteriori LLR and decision).  keep: per lane 0xffff where the lane updates (its r is used),
+// 0 where the lane restarts from the prior (r taken as 0: Q = gamma, q = gamma).  Returns the new
+// (Q0, Q1); flips the lane's parity bit of every check of the variable whose decision changed.
+// ---------------------------------------------------------------------------------------------
+template <class P, int D>
+__device__ __forceinline__ int2 var_step_x2(int u, int NV, const CheckOf &ck, const uint32_t *__restrict__ vslot,
+                                            int32_t gamma, int2 Qold, uint32_t keep, uint32_t *__restrict__ slots,
+                                            uint32_t *__restrict__ parity)
+{
+    if constexpr (D == 0) {
+        return make_int2(gamma, gamma);
+    } else {
+        uint32_t e[D], r[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) e[k] = __ldg(vslot + size_t(k) * NV + u);
+#pragma unroll
+        for (int k = 0; k < D; ++k) r[k] = slots[e[k]] & keep;
+        int32_t Q0 = gamma, Q1 = gamma;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            Q0 += lane0(r[k]);
+            Q1 += lane1(r[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < D; ++k) slots[e[k]] = clamp_pair<P>(Q0 - lane0(r[k]), Q1 - lane1(r[k]));
+        const uint32_t flip = (uint32_t(Q0 ^ Qold.x) >> 31) | ((uint32_t(Q1 ^ Qold.y) >> 31) << 16);
+        if (flip) {
+#pragma unroll
+            for (int k = 0; k < D; ++k) atomicXor(parity + ck(e[k]), flip);
+        }
+        return make_int2(Q0, Q1);
+    }
+}
+
+template <class P, int DV>
+__device__ __forceinline__ int2 var_step_x2_dispatch(int deg, int u, int NV, const CheckOf &ck, const uint32_t *vslot,
+                                                     int32_t gamma, int2 Qold, uint32_t keep, uint32_t *slots,
+                                                     uint32_t *parity)
+{
+    switch (deg) {
+#define QLDPC_CASE(D)                                                                           \
+    case D:                                                                                     \
+        if constexpr (D <= DV) return var_step_x2<P, D>(u, NV, ck, vslot, gamma, Qold, keep, slots, parity); \
+        break;
+        QLDPC_DEG_CASES(QLDPC_CASE)
+#undef QLDPC_CASE
+    default: break;
+    }
+    return make_int2(gamma, gamma);
+}
+
+template <class P, int DC, bool UNIFORM, int DV>
+__global__ void __launch_bounds__(kPackedMaxThreads, 1) msa_packed_kernel(const LaunchParams p)
+{
+    const Problem pr = blockIdx.y == 0 ? p.prob[0] : p.prob[1];
+    const int M = pr.g.m, N = pr.g.n, NV = pr.g.nv;
+    const int T = blockDim.x, tid = threadIdx.x;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const PackedLayout L = packed_layout(M, NV, pr.g.dc_max);
+    int32_t *gam = reinterpret_cast<int32_t *>(smem + L.g_off);
+    int2 *Qs = reinterpret_cast<int2 *>(smem + L.q_off);
+    uint32_t *parity = reinterpret_cast<uint32_t *>(smem + L.par_off);
+    uint32_t *slots = reinterpret_cast<uint32_t *>(smem + L.slot_off);
+    __shared__ int s_claim[2];
+    __shared__ uint32_t s_any[2];   // OR of the parity words' lane bits (alternating per iteration)
+
+    int bad = 0;
+    for (int u = tid; u < NV; u += T) {
+        const uint32_t v = __ldg(pr.g.vperm + u);
+        const float g = v < uint32_t(N) ? pr.prior[v] : 0.0f;
+        bad |= !isfinite(g);
+        gam[u] = P::quantize(g);
+        Qs[u] = make_int2(0, 0);        // the decisions a refill compares against: none set
+    }
+    for (int c = tid; c < M; c += T) parity[c] = 0u;
+    if (tid < 2) s_any[tid] = 0u;
+    bad = __syncthreads_or(bad);
+    if (bad) {   // non-finite prior: every shot of the launch is reported as not decoded
+        for (;;) {
+            if (tid == 0) s_claim[0] = atomicAdd(p.next_shot + blockIdx.y, 1);
+            __syncthreads();
+            const int b = s_claim[0];
+            __syncthreads();
+            if (b >= p.batch) return;
+            for (int v = tid; v < N; v += T) {
+                pr.err[size_t(b) * N + v] = 0;
+                if (pr.post) pr.post[size_t(b) * N + v] = __int_as_float(0x7fc00000);
+            }
+            if (tid == 0) {
+                pr.iters[b] = -1;
+                pr.ok[b] = 0;
+            }
+        }
+    }
+
+    const bool early = (p.flags & kFlagNoEarlyStop) == 0;
+    const CheckOf ck(pr.g);
+    // Block-uniform lane state: shot of each lane (-1: idle), iterations run, the lanes whose var
+    // step updates (act), the lanes that take a new shot in the next var step (refill), the lanes
+    // whose finished shot the next var step writes out (out), and the lanes filled by the last var
+    // step (fresh: the next check step installs their syndrome bits).
+    int shot[2] = {-1, -1}, k[2] = {0, 0}, okl[2] = {0, 0};
+    uint32_t act = 0u, refill = 3u, out = 0u, fresh = 0u, ph = 0u;
+    for (;;) {
+        // ---- variable step: updates, outputs of finished shots, refills ----
+        const uint32_t keep = ((act & 1u) ? 0x0000ffffu : 0u) | ((act & 2u) ? 0xffff0000u : 0u);
+        for (int u = tid; u < NV; u += T) {
+            const int2 Qo = Qs[u];
+            if (out) {
+                const uint32_t v = __ldg(pr.g.vperm + u);
+                if (v < uint32_t(N)) {
+#pragma unroll
+                    for (int l = 0; l < 2; ++l) {
+                        if (out & (1u << l)) {
+                            const int32_t q = l ? Qo.y : Qo.x;
+                            pr.err[size_t(shot[l]) * N + v] = q < 0 ? 1 : 0;
+                            if (pr.post) pr.post[size_t(shot[l]) * N + v] = P::post(q);
+                        }
+                    }
+                }
+            }
+            Qs[u] = var_step_x2_dispatch<P, DV>(__ldg(pr.g.vdeg + u), u, NV, ck, pr.g.vslot, gam[u], Qo, keep, slots,
+                                                parity);
+        }
+        if (tid == 0) {
+            s_any[ph] = 0u;                           // the word the next check step reduces into
+#pragma unroll
+            for (int l = 0; l < 2; ++l) {
+                if (out & (1u << l)) {
+                    pr.iters[shot[l]] = k[l];
+                    pr.ok[shot[l]] = okl[l] ? 1 : 0;
+                }
+                if (refill & (1u << l)) s_claim[l] = atomicAdd(p.next_shot + blockIdx.y, 1);
+            }
+        }
+        __syncthreads();
+        fresh = 0u;
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+            if (refill & (1u << l)) {
+                const int b = s_claim[l];
+                shot[l] = b < p.batch ? b : -1;
+                k[l] = 0;
+                if (shot[l] >= 0) fresh |= 1u << l;
+            } else if (act & (1u << l)) {
+                ++k[l];
+            }
+        }
+        if (shot[0] < 0 && shot[1] < 0) break;
+
+        // ---- check step and stop test of both lanes ----
+        const uint8_t *s0 = (fresh & 1u) ? pr.syn + size_t(shot[0]) * M : nullptr;
+        const uint8_t *s1 = (fresh & 2u) ? pr.syn + size_t(shot[1]) * M : nullptr;
+        uint32_t unsat = 0u;
+        for (int c = tid; c < M; c += T) {
+            uint32_t pw = parity[c];
+            if (fresh) {   // the new shots' syndrome bits replace the old ones (bit 0 and bit 15 / 16 and 31)
+                if (s0) pw ^= (((pw >> 15) ^ uint32_t(s0[c])) & 1u) * 0x00008001u;
+                if (s1) pw ^= (((pw >> 31) ^ uint32_t(s1[c])) & 1u) * 0x80010000u;
+                parity[c] = pw;
+            }
+            unsat |= pw;
+            check_step_x2<P, DC, UNIFORM>(c, M, UNIFORM ? DC : int(__ldg(pr.g.rdeg + c)), pw, slots, p.alpha_q);
+        }
+        // block OR of both lanes' unsatisfied bits (bit 0 and bit 16): warp OR, one shared OR per warp
+        const uint32_t wv = __reduce_or_sync(0xffffffffu, unsat & 0x00010001u);
+        if ((tid & 31) == 0 && wv) atomicOr(&s_any[ph], wv);
+        __syncthreads();
+        const uint32_t any = s_any[ph];
+        ph ^= 1u;
+        out = refill = act = 0u;
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+            if (shot[l] < 0) continue;                // idle lane: keeps restarting from the prior
+            const int met = ((any >> (16 * l)) & 1u) == 0u;
+            if ((early && met) || k[l] >= p.max_iter) {
+                okl[l] = met;
+                out |= 1u << l;
+                refill |= 1u << l;
+            } else {
+                act |= 1u << l;
+            }
+        }
+    }
+}
+
+}  // namespace kern
+
+// Instantiation tables of the packed kernel for one fixed-point policy (same variants as the other
+// flooding kernels).
+template <class P>
+const void *packed_table(const KernelChoice &kc)
+{
+#define QLDPC_K(DCV, UNI, DVV)                                                                  \
+    if (kc.dc == DCV && kc.uniform == UNI && kc.dvb == DVV)                                     \
+        return reinterpret_cast<const void *>(&kern::msa_packed_kernel<P, DCV, UNI, DVV>);
+    QLDPC_VARIANTS(QLDPC_K)
+#undef QLDPC_K
+    return nullptr;
+}
+
+template <class P>
+cudaError_t packed_launch(const LaunchParams &p, const KernelChoice &kc, dim3 grid, int threads, size_t smem,
+                          cudaStream_t stream)
+{
+#define QLDPC_L(DCV, UNI, DVV)                                                                  \
+    if (kc.dc == DCV && kc.uniform == UNI && kc.dvb == DVV) {                                   \
+        kern::msa_packed_kernel<P, DCV, UNI, DVV><<<grid, threads, smem, stream>>>(p);          \
+        return cudaGetLastError();                                                              \
+    }
+    QLDPC_VARIANTS(QLDPC_L)
+#undef QLDPC_L
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace qldpc

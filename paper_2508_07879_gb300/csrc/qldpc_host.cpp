@@ -34,6 +34,7 @@ const void *msa_kernel(int precision, const KernelChoice &kc)
 {
     if (kc.layered) return msa_kernel_layered(precision, kc);
     if (kc.learned) return msa_kernel_learned(kc);
+    if (kc.packed) return precision == kINT16 ? msa_kernel_i16x2(kc) : precision == kINT8 ? msa_kernel_i8x2(kc) : nullptr;
     return precision == kINT16 ? msa_kernel_i16(kc) : precision == kINT8 ? msa_kernel_i8(kc) : msa_kernel_f32(kc);
 }
 
@@ -43,6 +44,10 @@ cudaError_t launch_msa(const LaunchParams &p, int precision, const KernelChoice 
     dim3 grid(unsigned(grid_x), unsigned(p.nprob));
     if (kc.layered) return launch_msa_layered(precision, p, kc, grid, threads, smem, stream);
     if (kc.learned) return launch_msa_learned(p, kc, grid, threads, smem, stream);
+    if (kc.packed)
+        return precision == kINT16  ? launch_msa_i16x2(p, kc, grid, threads, smem, stream)
+               : precision == kINT8 ? launch_msa_i8x2(p, kc, grid, threads, smem, stream)
+                                    : cudaErrorInvalidValue;
     return precision == kINT16  ? launch_msa_i16(p, kc, grid, threads, smem, stream)
            : precision == kINT8 ? launch_msa_i8(p, kc, grid, threads, smem, stream)
                                 : launch_msa_f32(p, kc, grid, threads, smem, stream);
@@ -484,7 +489,7 @@ int plan_latency(const qldpc_graph *const *gs, int nprob, int32_t batch, int pre
 {
     const qldpc_graph *g0 = gs[0];
     chosen = false;
-    if (g0->user_kernel == QLDPC_KERNEL_BATCH) return QLDPC_OK;
+    if (g0->user_kernel == QLDPC_KERNEL_BATCH || g0->user_kernel == QLDPC_KERNEL_PACKED) return QLDPC_OK;
     const bool forced = g0->user_kernel == QLDPC_KERNEL_LATENCY;
     if (!forced && int64_t(batch) * nprob > g0->sm_count) return QLDPC_OK;
     int one = 32, two = 32;
@@ -513,17 +518,25 @@ int plan_latency(const qldpc_graph *const *gs, int nprob, int32_t batch, int pre
     return QLDPC_OK;
 }
 
+// Throughput path: in the fixed-point precisions the two-shots-per-word kernel (unless the graph's
+// launch override asks for the one-shot-per-block kernel), else one shot per block.
 int plan_batch(const qldpc_graph *const *gs, int nprob, int32_t batch, int precision, bool learned, Plan &pl)
 {
     const qldpc_graph *g0 = gs[0];
+    const bool packed = precision != QLDPC_FP32 && !learned && g0->user_kernel != QLDPC_KERNEL_BATCH;
     size_t smem = 0;
-    for (int i = 0; i < nprob; ++i) smem = std::max(smem, shot_smem(gs[i], precision));
+    for (int i = 0; i < nprob; ++i)
+        smem = std::max(smem, packed ? packed_layout(gs[i]->m, gs[i]->nv, gs[i]->dc_max).total
+                                     : shot_smem(gs[i], precision));
     pl.kc = variant(gs, nprob, false, learned);
+    pl.kc.packed = packed;
     pl.threads = g0->user_threads ? g0->user_threads : kBatchThreads;
+    if (packed && pl.threads > kPackedMaxThreads) return QLDPC_ERR_UNSUPPORTED;
     pl.smem = smem;
     const void *k = msa_kernel(precision, pl.kc);
     if (int rc = ensure_kernel_attrs(k, smem, g0->smem_optin)) return rc;
-    return occupancy_grid(g0, k, pl.threads, smem, nprob, batch, g0->user_blocks_per_sm, pl.grid);
+    const int32_t units = packed ? int32_t((int64_t(batch) + 1) / 2) : batch;   // two shots per packed block
+    return occupancy_grid(g0, k, pl.threads, smem, nprob, units, g0->user_blocks_per_sm, pl.grid);
 }
 
 // Layered schedule: a block per shot with a thread per check of the largest layer (a multiple
@@ -609,8 +622,9 @@ int launch(const qldpc_graph *g0, const qldpc_graph *g1, const Problem *probs, i
             if (int rc = plan_batch(gs, nprob, batch, precision, learned, pl)) return rc;
     }
     if (plan_only) return QLDPC_OK;
-    if (!latency && pl.grid < batch) {
-        // more shots than blocks: claim them dynamically from a zeroed counter pair of the ring
+    if (!latency && (pl.kc.packed || pl.grid < batch)) {
+        // more shots than blocks (or the packed kernel, whose lanes always take shots from a counter):
+        // claim them dynamically from a zeroed counter pair of the ring
         p.next_shot = g0->d_counters + 2 * size_t(g0->counter_seq.fetch_add(1) % kShotCounterSlots);
         if (cudaError_t e = cudaMemsetAsync(p.next_shot, 0, 2 * sizeof(int32_t), st)) return cuda_status(e);
     }
@@ -902,7 +916,8 @@ int qldpc_graph_set_launch(qldpc_graph *g, int32_t kernel, int32_t threads_per_b
                            int32_t blocks_per_sm)
 {
     if (!g) return QLDPC_ERR_INVALID_ARG;
-    if (kernel != QLDPC_KERNEL_AUTO && kernel != QLDPC_KERNEL_BATCH && kernel != QLDPC_KERNEL_LATENCY)
+    if (kernel != QLDPC_KERNEL_AUTO && kernel != QLDPC_KERNEL_BATCH && kernel != QLDPC_KERNEL_LATENCY &&
+        kernel != QLDPC_KERNEL_PACKED)
         return QLDPC_ERR_INVALID_ARG;
     if (threads_per_block != 0 && (threads_per_block < 32 || threads_per_block > 1024 || threads_per_block % 32))
         return QLDPC_ERR_INVALID_ARG;
@@ -916,7 +931,7 @@ int qldpc_graph_set_launch(qldpc_graph *g, int32_t kernel, int32_t threads_per_b
     // the shape must be launchable, and the requested residency achievable, in both precisions
     const qldpc_graph *gs[1] = {g};
     int rc = QLDPC_OK;
-    for (int prec : {QLDPC_FP32, QLDPC_INT16}) {
+    for (int prec : {QLDPC_FP32, QLDPC_INT16, QLDPC_INT8}) {
         Plan pl;
         bool latency = false;
         const int32_t big = int32_t(1) << 30;

@@ -248,6 +248,21 @@ int qldpc_server_create(const qldpc_graph *const *graphs, const float *const *pr
         delete s;
         return QLDPC_ERR_UNSUPPORTED;
     }
+    // A worker reloads a code's graph arrays through L1 when it switches codes: ask for the smallest
+    // shared-memory carve-out that still holds the resident workers, which leaves the rest of each
+    // SM's 256 KB to L1 (a hint the driver rounds up to a supported size).  Kept only if the
+    // residency stays the same.
+    {
+        const size_t need = size_t(per_sm) * (smem + 2048);
+        const int pct = int(std::min<size_t>(100, (need * 100 + 228 * 1024 - 1) / (228 * 1024)));
+        int again = 0;
+        if (cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, pct) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&again, k, s->threads, smem) != cudaSuccess || again != per_sm) {
+            cudaGetLastError();
+            cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, -1);
+            cudaGetLastError();
+        }
+    }
     // Worker pool: the sum of cfg->blocks when given, else every worker that fits on the GPU at
     // this footprint.  All of them must be resident at once (a worker that never starts would never
     // take a request).

@@ -174,6 +174,15 @@ __global__ void __launch_bounds__(kLatencyMaxThreads, 1) msa_server_kernel(const
         if (e == kQueueLeave) break;
         const int code = entry_code(e);
         const ServerCode &sc = sp.code[code];
+        unsigned char *slot = sc.ring + size_t(entry_slot(e)) * size_t(sc.slot_bytes);
+        // The syndrome bits of the thread's checks, read from the host-memory slot once per request
+        // and issued before the code's state is reloaded, so the two round trips overlap.
+        uint32_t sbit[kLatCnPerThread];
+#pragma unroll
+        for (int i = 0; i < kLatCnPerThread; ++i) {
+            const int c = tid + i * T;
+            sbit[i] = c < sc.g.m ? uint32_t(__ldcv(slot + sc.syn_off + c)) & 1u : 0u;
+        }
         if (code != cur) {
             cur = code;
             M = sc.g.m;
@@ -185,14 +194,12 @@ __global__ void __launch_bounds__(kLatencyMaxThreads, 1) msa_server_kernel(const
             wstride = size_t(sc.g.dc_max) * M;
             wc.load(sc, tid, T);
         }
-        unsigned char *slot = sc.ring + size_t(entry_slot(e)) * size_t(sc.slot_bytes);
-        const unsigned char *syn = slot + sc.syn_off;
         acc_t Q[kLatVnPerThread];
         // Initialization (Alg. 1), also the restart of the plain fallback; ends with a barrier.
         auto init_shot = [&]() {
 #pragma unroll
             for (int i = 0; i < kLatCnPerThread; ++i)
-                if (wc.cdeg[i] >= 0) parity[tid + i * T] = (__ldcv(syn + tid + i * T) & 1u) * 3u;
+                if (wc.cdeg[i] >= 0) parity[tid + i * T] = sbit[i] * 3u;
             __syncthreads();
 #pragma unroll
             for (int i = 0; i < kLatVnPerThread; ++i) {

@@ -39,7 +39,9 @@ QLDPC_MAX_CHECKS = 65535
 QLDPC_KERNEL_AUTO = 0
 QLDPC_KERNEL_BATCH = 1
 QLDPC_KERNEL_LATENCY = 2
-KERNELS = {"auto": QLDPC_KERNEL_AUTO, "batch": QLDPC_KERNEL_BATCH, "latency": QLDPC_KERNEL_LATENCY}
+QLDPC_KERNEL_PACKED = 3
+KERNELS = {"auto": QLDPC_KERNEL_AUTO, "batch": QLDPC_KERNEL_BATCH, "latency": QLDPC_KERNEL_LATENCY,
+           "packed": QLDPC_KERNEL_PACKED}
 
 PRECISIONS = {"fp32": QLDPC_FP32, "int16": QLDPC_INT16, "int8": QLDPC_INT8}
 

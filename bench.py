@@ -427,7 +427,8 @@ def run_ours(args, rank, world, local):
     # edge-iterations it runs: E x (iterations summed over its 65536 shots)
     props = torch.cuda.get_device_properties(dev)
     clocks = clk.summary()
-    kernel_name = "msa_batch_kernel" if args.precision == "fp32" or args.kernel == "batch" else "msa_packed_kernel"
+    packed = args.kernel == "packed" or (args.kernel == "auto" and args.precision == "int16")
+    kernel_name = "msa_packed_kernel" if packed and args.precision != "fp32" else "msa_batch_kernel"
     roofline = decoder_roofline(h, B, iters_per_batch, args.steps, ms_per_step, args.precision,
                                 props.multi_processor_count, clocks["sm_max_mhz"] or 2070.0, kernel_name)
 
@@ -962,9 +963,9 @@ def measure_precisions(qldpc, graph, syn_d, pri_d, out, stream, B, args, steps=1
     """Flooding decode of the benchmark's batches in each precision: throughput and decoded fraction."""
     import torch
     res = {}
-    for name in ("fp32", "int16", "int8", "int16_scalar", "int8_scalar"):
+    for name in ("fp32", "int16", "int8", "int16_scalar", "int8_packed"):
         prec = name.split("_")[0]
-        graph.set_launch("batch" if name.endswith("_scalar") else "auto")
+        graph.set_launch("batch" if name.endswith("_scalar") else "packed" if name.endswith("_packed") else "auto")
         ok = iters = 0
         with torch.cuda.stream(stream):
             for j in range(len(syn_d)):
@@ -986,8 +987,8 @@ def measure_precisions(qldpc, graph, syn_d, pri_d, out, stream, B, args, steps=1
             stream.synchronize()
         res[name] = {"value": B * steps / (e0.elapsed_time(e1) / 1e3), "unit": "syndromes/s",
                      "decoded_fraction": ok / (len(syn_d) * B), "mean_iters": iters / (len(syn_d) * B),
-                     "kernel": "msa_batch_kernel (one shot per block)" if name.endswith("_scalar") or prec == "fp32"
-                     else "msa_packed_kernel (two shots per block)"}
+                     "kernel": "msa_packed_kernel (two shots per block)" if (prec == "int16" and name == "int16")
+                     or name.endswith("_packed") else "msa_batch_kernel (one shot per block)"}
     graph.set_launch("auto")
     return res
 

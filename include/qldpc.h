@@ -162,7 +162,7 @@ QLDPC_API int qldpc_graph_footprint(const qldpc_graph *g, int32_t precision, int
 /* Kernels (qldpc_graph_set_launch). */
 enum {
     QLDPC_KERNEL_AUTO = 0,      /* latency kernel when every shot gets its own SM, else the packed
-                                   kernel in INT16 / INT8 and the batch kernel in FP32 */
+                                   kernel in INT16 and the batch kernel in FP32 and INT8 */
     QLDPC_KERNEL_BATCH = 1,     /* throughput kernel: one shot per block, thread per check / per
                                    variable, persistent blocks */
     QLDPC_KERNEL_LATENCY = 2,   /* single-shot kernel: per-thread state in registers, one block per

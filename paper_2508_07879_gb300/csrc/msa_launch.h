@@ -163,6 +163,7 @@ struct ServerCode {
     unsigned char *ring;        // ring_capacity slots of slot_bytes
     int32_t slot_bytes, syn_off, err_off;
     int32_t layered_reg;        // layered workers: 1 = register-resident checks (<= 8 layers), 0 = shared memory
+    int32_t udc;                // every row has this degree (6..9), else 0: the check step's compiled degree
 };
 
 struct ServerParams {
@@ -218,7 +219,9 @@ cudaError_t launch_msa_i16x2(const LaunchParams &p, const KernelChoice &kc, dim3
 cudaError_t launch_msa_i8x2(const LaunchParams &p, const KernelChoice &kc, dim3 grid, int threads,
                             size_t smem, cudaStream_t stream);
 
-// Threads per block of the packed kernel at most (its register budget assumes no more).
+// Threads per block of the packed kernel at most (its register budget, up to 128 per thread, assumes no
+// more).  A tighter register cap (63 for 7 blocks per SM) made the compiler recompute values: 19 %
+// more instructions and a slower kernel, although twice as many warps were resident.
 constexpr int kPackedMaxThreads = 512;
 
 // Shared memory of one block of the packed kernel (two shots): gamma [nv] i32, Q [nv] i32x2,

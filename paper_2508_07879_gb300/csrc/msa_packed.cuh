@@ -139,13 +139,13 @@ __device__ __forceinline__ void check_step_x2(int c, int M, int deg, uint32_t pw
     // it), and the same negated for an edge whose own sign is negative
     const uint32_t rp1 = select16x2(negm, n1, s1), rp2 = select16x2(negm, n2, s2);
     const uint32_t rn1 = select16x2(negm, s1, n1), rn2 = select16x2(negm, s2, n2);
-    const uint32_t m1p = m1 + 0x00010001u;             // no carry: m1 <= 32767 per lane
+    // per lane 0x7fff - m1: |q| + (0x7fff - m1) has bit 15 set iff |q| > m1, and stays below 0x10000
+    // (|q|, m1 <= 32767), so one 32-bit add serves both lanes without a carry between them
+    const uint32_t k1 = 0x7fff7fffu - m1;
 #pragma unroll
     for (int j = 0; j < DC; ++j) {
         if (UNIFORM || j < deg) {
-            // bit 15 of each lane of (|q| + 0x8000) - (m1 + 1) is set iff |q| > m1 (|q| >= m1, so no
-            // borrow crosses the lanes)
-            const uint32_t gt = signmask16x2((a[j] | 0x80008000u) - m1p);
+            const uint32_t gt = signmask16x2(a[j] + k1);
             const uint32_t pos = select16x2(gt, rp1, rp2), neg = select16x2(gt, rn1, rn2);
             slots[j * M + c] = select16x2(signmask16x2(q[j]), neg, pos);
         }

@@ -19,7 +19,9 @@
 //                        Two block barriers per iteration; the next iteration's recorded state
 //                        streams into shared memory (cp.async) while the variable side runs.  Weight
 //                        gradients are added into one L2-resident [T][slots] buffer with global
-//                        reductions, so the order of the sum over shots follows the schedule.
+//                        reductions, so the order of the sum over shots follows the schedule: the
+//                        gradient is deterministic only up to the order of its FP32 additions
+//                        (last-bit differences between calls).
 //   helpers              CSR <-> slot-layout weight permutation, an Adam step, a counter-based
 //                        SplitMix64 error sampler with syndromes, and the logical-failure test.
 #include <algorithm>

@@ -518,12 +518,15 @@ int plan_latency(const qldpc_graph *const *gs, int nprob, int32_t batch, int pre
     return QLDPC_OK;
 }
 
-// Throughput path: in the fixed-point precisions the two-shots-per-word kernel (unless the graph's
-// launch override asks for the one-shot-per-block kernel), else one shot per block.
+// Throughput path: one shot per block, or two shots per block with their messages paired in one word
+// (INT16 by default, INT16 / INT8 when the graph's launch override asks for it).  Measured on LP-1054
+// at 65536 shots: INT16 28.8 M/s packed against 26.5 one shot per block; INT8 26.9 against 27.9
+// (one-byte slots let 10 one-shot blocks share an SM), so INT8 keeps one shot per block.
 int plan_batch(const qldpc_graph *const *gs, int nprob, int32_t batch, int precision, bool learned, Plan &pl)
 {
     const qldpc_graph *g0 = gs[0];
-    const bool packed = precision != QLDPC_FP32 && !learned && g0->user_kernel != QLDPC_KERNEL_BATCH;
+    const bool packed = !learned && ((precision == QLDPC_INT16 && g0->user_kernel != QLDPC_KERNEL_BATCH) ||
+                                     (precision == QLDPC_INT8 && g0->user_kernel == QLDPC_KERNEL_PACKED));
     size_t smem = 0;
     for (int i = 0; i < nprob; ++i)
         smem = std::max(smem, packed ? packed_layout(gs[i]->m, gs[i]->nv, gs[i]->dc_max).total

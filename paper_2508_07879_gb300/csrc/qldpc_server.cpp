@@ -359,6 +359,7 @@ int qldpc_server_create(const qldpc_graph *const *graphs, const float *const *pr
         sc.syn_off = 16;
         sc.err_off = int32_t(align16(16 + size_t(s->m[c])));
         sc.layered_reg = layered_reg[c];
+        sc.udc = (graphs[c]->uniform_rows && graphs[c]->dc_max >= 6 && graphs[c]->dc_max <= 9) ? graphs[c]->dc_max : 0;
         s->ring[c] = s->host_block + ring_off[c];
         s->busy[c].assign(size_t(cap), 0);
         s->done_word[c].assign(size_t(cap), 0);

@@ -139,6 +139,42 @@ struct WorkerCode {
     }
 };
 
+// Check step and stop test of the thread's checks (tid + i*T) for rows of compiled degree D.
+template <class P, int D, bool U, bool LEARNED>
+__device__ __forceinline__ int server_checks(const int *cdeg, int tid, int T, int M, const uint32_t *parity, bool update,
+                                             typename P::msg_t *slots, const LaunchParams &p, const float *wk)
+{
+    int ok = 1;
+#pragma unroll
+    for (int i = 0; i < kLatCnPerThread; ++i)
+        if (cdeg[i] >= 0)
+            ok &= check_step<P, D, U, LEARNED>(tid + i * T, M, cdeg[i], parity[tid + i * T], update, slots, p, wk);
+    return ok;
+}
+
+// The check phase of one iteration.  A kernel compiled for rows of varying degree (a server whose
+// codes differ in row degree) still runs each code whose rows all have one degree of 6..9 with that
+// degree compiled in (pairwise minima, no per-edge predicates): the code is the same for the whole
+// block, so the dispatch costs no divergence.
+template <class P, int DC, bool UNIFORM, bool LEARNED>
+__device__ __forceinline__ int server_check_phase(int udc, const int *cdeg, int tid, int T, int M,
+                                                  const uint32_t *parity, bool update, typename P::msg_t *slots,
+                                                  const LaunchParams &p, const float *wk)
+{
+    if constexpr (!UNIFORM) {
+        switch (udc) {
+        case 6: return server_checks<P, 6, true, LEARNED>(cdeg, tid, T, M, parity, update, slots, p, wk);
+        case 7: return server_checks<P, 7, true, LEARNED>(cdeg, tid, T, M, parity, update, slots, p, wk);
+        case 8: return server_checks<P, 8, true, LEARNED>(cdeg, tid, T, M, parity, update, slots, p, wk);
+        case 9:
+            if constexpr (DC >= 9) return server_checks<P, 9, true, LEARNED>(cdeg, tid, T, M, parity, update, slots, p, wk);
+            break;
+        default: break;
+        }
+    }
+    return server_checks<P, DC, UNIFORM, LEARNED>(cdeg, tid, T, M, parity, update, slots, p, wk);
+}
+
 // LEARNED (FP32): a code with weights decodes as the learned batch/latency kernels do (learned
 // iterations, then the plain fallback from the prior); a code without weights decodes plainly.
 template <class P, int DC, bool UNIFORM, int DV, bool LEARNED = false>
@@ -158,7 +194,7 @@ __global__ void __launch_bounds__(kLatencyMaxThreads, 1) msa_server_kernel(const
     const bool early = (sp.flags & kFlagNoEarlyStop) == 0;
 
     // the code whose state the registers hold (-1: none yet) and its block-uniform parameters
-    int cur = -1, M = 0, N = 0, learned_iters = 0;
+    int cur = -1, M = 0, N = 0, learned_iters = 0, udc = 0;
     CheckOf ck;
     msg_t *slots = nullptr;
     const float *weights = nullptr;
@@ -192,6 +228,7 @@ __global__ void __launch_bounds__(kLatencyMaxThreads, 1) msa_server_kernel(const
             weights = LEARNED ? sc.weights : nullptr;
             learned_iters = sc.learned_iters;
             wstride = size_t(sc.g.dc_max) * M;
+            udc = sc.udc;
             wc.load(sc, tid, T);
         }
         acc_t Q[kLatVnPerThread];
@@ -224,12 +261,8 @@ __global__ void __launch_bounds__(kLatencyMaxThreads, 1) msa_server_kernel(const
             const bool last = k >= end;
             const float *wk = nullptr;
             if constexpr (LEARNED) wk = (learned && !last) ? weights + size_t(k) * wstride : nullptr;
-            int ok = 1;
-#pragma unroll
-            for (int i = 0; i < kLatCnPerThread; ++i)
-                if (wc.cdeg[i] >= 0)
-                    ok &= check_step<P, DC, UNIFORM, LEARNED>(tid + i * T, M, wc.cdeg[i], parity[tid + i * T], !last,
-                                                              slots, p, wk);
+            const int ok = server_check_phase<P, DC, UNIFORM, LEARNED>(udc, wc.cdeg, tid, T, M, parity, !last, slots,
+                                                                       p, wk);
             all = __syncthreads_and(ok);
             if ((early || learned) && all) break;
             if (last) {

@@ -681,14 +681,20 @@ def measure_latency(qldpc, graph, code, args):
     ok = torch.empty(1, dtype=torch.uint8).pin_memory().numpy()
     prior = b.prior.copy()
     lat = {}
+    # the C entry point through ctypes with addresses computed once (the per-call cost of extracting
+    # numpy pointers in Python is not the library's)
+    syn0, pr0, e0, i0, o0 = (a.ctypes.data for a in (syn, prior, err, it, ok))
     for prec in ("fp32", "int16", "int8"):
         ts = np.empty(shots + warm)
         iters = np.empty(shots + warm, dtype=np.int32)
+        pc = qldpc.PRECISIONS[prec]
         for i in range(shots + warm):
-            row = syn[i:i + 1]
             t0 = time.perf_counter_ns()
-            qldpc.decode_host(graph, row, prior, MAX_ITER, ALPHA, prec, out=(err, it, ok))
+            rc = qldpc.qldpc_decode_host(graph.handle, syn0 + i * h.m, 1, pr0, MAX_ITER, ALPHA, e0, i0, o0, pc, 0,
+                                         None)
             ts[i] = (time.perf_counter_ns() - t0) / 1e3
+            if rc:
+                raise qldpc.QldpcError(rc, "qldpc_decode_host")
             iters[i] = it[0]
         x = ts[warm:]
         lat[prec] = {"p50_us": float(np.percentile(x, 50)), "p99_us": float(np.percentile(x, 99)),
@@ -696,7 +702,7 @@ def measure_latency(qldpc, graph, code, args):
                      "max_iter_shots": int((iters[warm:] == MAX_ITER).sum())}
     out = {"metric": "p99 single-shot decode latency", "unit": "us", "threshold_us": THRESHOLD_US,
            "code": "LP-1054 H_Z", "p": LAT_P, "shots": shots, "max_iter": MAX_ITER,
-           "launch_path": {"path": "qldpc_decode_host from Python, page-locked buffers read/written by the "
+           "launch_path": {"path": "qldpc_decode_host through ctypes, page-locked buffers read/written by the "
                                    "kernel, host clock, B=1", **lat}}
     # the same shots through the persistent server: requests 50 us apart, latency = result seen by
     # the host - scheduled arrival (host steady clock inside the C ABI)
@@ -769,6 +775,24 @@ def measure_layered_codes(qldpc, args, shots=None):
     return res
 
 
+def pair_host_call(qldpc, gz, gx, sx, sz, prior, outs, max_iter, early_stop):
+    """call(i): qldpc_decode_pair_host on shot i of the page-locked syndrome arrays sx / sz, through
+    ctypes with every address computed once."""
+    (ex, ix, ox), (ez, iz, oz) = outs
+    a = [x.ctypes.data for x in (sx, sz, prior, ex, ez, ix, iz, ox, oz)]
+    mz, mx = gz.m, gx.m
+    flags = 0 if early_stop else qldpc.QLDPC_NO_EARLY_STOP
+    hz, hx = gz.handle, gx.handle
+    fn = qldpc.qldpc_decode_pair_host
+
+    def call(i):
+        rc = fn(hz, hx, a[0] + i * mz, a[1] + i * mx, 1, a[2], a[2], max_iter, ALPHA, a[3], a[4], a[5], a[6], a[7],
+                a[8], qldpc.QLDPC_FP32, flags, None)
+        if rc:
+            raise qldpc.QldpcError(rc, "qldpc_decode_pair_host")
+    return call
+
+
 def measure_paper_mode(qldpc, args, shots=10000, warm=100):
     """The paper's timing conditions (Sec. 3): X and Z decoded in one kernel, FP32, 10 iterations,
     no early stop, B = 1, average end-to-end latency including the transfers.  BB-144 ([[144,12,12]],
@@ -788,13 +812,14 @@ def measure_paper_mode(qldpc, args, shots=10000, warm=100):
         prior = np.full(code.n, w.prior_llr(2 * 0.03 / 3), dtype=np.float32)
         outs = tuple((pin(np.zeros((1, code.n), np.uint8)), pin(np.zeros(1, np.int32)), pin(np.zeros(1, np.uint8)))
                      for _ in range(2))
+        call = pair_host_call(qldpc, gz, gx, sx, sz, prior, outs, 10, False)
         ts = np.empty(shots + warm)
         for i in range(shots + warm):
             t0 = time.perf_counter_ns()
-            qldpc.decode_pair_host(gz, gx, sx[i:i + 1], sz[i:i + 1], prior, prior, 10, ALPHA, "fp32", False, out=outs)
+            call(i)
             ts[i] = (time.perf_counter_ns() - t0) / 1e3
         x = ts[warm:]
-        row = {"launch_path": {"path": "qldpc_decode_pair_host, one launch for X and Z",
+        row = {"launch_path": {"path": "qldpc_decode_pair_host through ctypes, one launch for X and Z",
                                "mean_us": float(x.mean()), "p50_us": float(np.percentile(x, 50)),
                                "p99_us": float(np.percentile(x, 99)), "p999_us": float(np.percentile(x, 99.9))}}
         with qldpc.Server([gz, gx], [prior, prior], 10, ALPHA, "fp32", early_stop=False, blocks=[8, 8],
@@ -827,7 +852,8 @@ def measure_bb_sweep(qldpc, args, shots=10000, warm=100):
     from paper_2508_07879_gb300 import workloads as w
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
     shots = min(shots, max(1000, args.latency_shots))
-    out = {"max_iter": 64, "shots_per_p": shots, "path": "qldpc_decode_pair_host (X+Z in one launch), FP32"}
+    out = {"max_iter": 64, "shots_per_p": shots,
+           "path": "qldpc_decode_pair_host through ctypes (X+Z in one launch), FP32, page-locked buffers"}
     for ci, name in enumerate(("bb144", "bb288")):
         code = w.CONFIG_CODES[name]()
         gz, gx = qldpc.Graph.from_csr(code.hz_csr), qldpc.Graph.from_csr(code.hx_csr)
@@ -841,10 +867,10 @@ def measure_bb_sweep(qldpc, args, shots=10000, warm=100):
             ts = np.empty(shots + warm)
             both_ok = np.empty(shots + warm, dtype=bool)
             its = np.empty(shots + warm)
+            call = pair_host_call(qldpc, gz, gx, sx, sz, prior, outs, 64, True)
             for i in range(shots + warm):
                 t0 = time.perf_counter_ns()
-                qldpc.decode_pair_host(gz, gx, sx[i:i + 1], sz[i:i + 1], prior, prior, 64, ALPHA, "fp32", True,
-                                       out=outs)
+                call(i)
                 ts[i] = (time.perf_counter_ns() - t0) / 1e3
                 both_ok[i] = outs[0][2][0] and outs[1][2][0]
                 its[i] = max(outs[0][1][0], outs[1][1][0])
@@ -1037,10 +1063,15 @@ def measure_layered(qldpc, graph, code, syn_d, pri_d, out, stream, B, args, step
     err, it, okk = pin(np.zeros((1, b.h.n), np.uint8)), pin(np.zeros(1, np.int32)), pin(np.zeros(1, np.uint8))
     ts = np.empty(shots + warm)
     its = np.empty(shots + warm, dtype=np.int32)
+    prior = np.ascontiguousarray(b.prior, dtype=np.float32)
+    syn0, pr0, e0, i0, o0 = (a.ctypes.data for a in (syn, prior, err, it, okk))
     for i in range(shots + warm):
         t0 = time.perf_counter_ns()
-        qldpc.decode_host(graph, syn[i:i + 1], b.prior, MAX_ITER, ALPHA, "fp32", out=(err, it, okk), layered=True)
+        rc = qldpc.qldpc_decode_host(graph.handle, syn0 + i * b.h.m, 1, pr0, MAX_ITER, ALPHA, e0, i0, o0,
+                                     qldpc.QLDPC_FP32, qldpc.QLDPC_LAYERED, None)
         ts[i] = (time.perf_counter_ns() - t0) / 1e3
+        if rc:
+            raise qldpc.QldpcError(rc, "qldpc_decode_host")
         its[i] = it[0]
     x = ts[warm:]
     res["latency_launch_path_fp32"] = {"p50_us": float(np.percentile(x, 50)), "p99_us": float(np.percentile(x, 99)),

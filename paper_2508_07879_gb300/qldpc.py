@@ -156,7 +156,7 @@ def check(status: int, what: str = "") -> None:
 
 
 def _np_ptr(a: np.ndarray):
-    return ctypes.c_void_p(a.ctypes.data)
+    return a.ctypes.data            # an int: ctypes passes it as the void* the signature declares
 
 
 def _dev_ptr(t, dtype, shape, name):

@@ -211,22 +211,23 @@ __device__ __forceinline__ void layered_own(const DeviceGraph &g, int tid, Layer
 // One shot: Q [n] (shared) starts at the quantized priors, the messages at zero; syn(c) reads s_c.
 // Runs the layers of every iteration with one barrier each and the stop test after the last, and
 // returns the iterations run (all = every check satisfied).  Ends with Q final and visible to the
-// block.
-template <class P, int DC, bool UNIFORM, int MAXL, class Syn>
+// block.  D <= DC: the row degree compiled into the loops (UNIFORM: every row has exactly D edges).
+template <class P, int DC, int D, bool UNIFORM, int MAXL, class Syn>
 __device__ __forceinline__ int layered_reg_shot(const LayeredOwned<DC, MAXL> &o, int L, int N, int tid, int T,
                                                 Syn syn, const float *__restrict__ prior,
                                                 typename P::acc_t *__restrict__ Q, const LaunchParams &p,
                                                 bool early, int &all)
 {
+    static_assert(D <= DC, "compiled degree above the owned-check layout");
     using acc_t = typename P::acc_t;
     using mag_t = typename P::mag_t;
-    acc_t r[MAXL][DC];
+    acc_t r[MAXL][D];
     uint32_t sbits = 0;
 #pragma unroll
     for (int l = 0; l < MAXL; ++l) {
         if (o.myc[l] >= 0) sbits |= (syn(o.myc[l]) & 1u) << l;
 #pragma unroll
-        for (int j = 0; j < DC; ++j) r[l][j] = acc_t(0);
+        for (int j = 0; j < D; ++j) r[l][j] = acc_t(0);
     }
     for (int v = tid; v < N; v += T) Q[v] = P::quantize(prior[v]);
     __syncthreads();
@@ -238,7 +239,7 @@ __device__ __forceinline__ int layered_reg_shot(const LayeredOwned<DC, MAXL> &o,
             if (o.myc[l] >= 0) {
                 uint32_t par = (sbits >> l) & 1u;
 #pragma unroll
-                for (int j = 0; j < DC; ++j)
+                for (int j = 0; j < D; ++j)
                     if (UNIFORM || j < o.mdeg[l]) par ^= P::neg(Q[(o.ev[l][j / 2] >> (16 * (j & 1))) & 0xffffu]) ? 1u : 0u;
                 ok &= par == 0;
             }
@@ -253,11 +254,11 @@ __device__ __forceinline__ int layered_reg_shot(const LayeredOwned<DC, MAXL> &o,
             for (int l = 0; l < MAXL; ++l) {
                 if (l < L) {
                     if (o.myc[l] >= 0) {
-                        acc_t qu[DC], q[DC];
-                        uint32_t v[DC];
+                        acc_t qu[D], q[D];
+                        uint32_t v[D];
                         uint32_t sx = 0;
 #pragma unroll
-                        for (int j = 0; j < DC; ++j) {
+                        for (int j = 0; j < D; ++j) {
                             if (UNIFORM || j < o.mdeg[l]) {
                                 v[j] = (o.ev[l][j / 2] >> (16 * (j & 1))) & 0xffffu;
                                 qu[j] = P::sub(Q[v[j]], r[l][j]);
@@ -266,12 +267,12 @@ __device__ __forceinline__ int layered_reg_shot(const LayeredOwned<DC, MAXL> &o,
                             }
                         }
                         mag_t m1, m2;
-                        two_smallest<P, DC, UNIFORM>(q, o.mdeg[l], m1, m2);
+                        two_smallest<P, D, UNIFORM>(q, o.mdeg[l], m1, m2);
                         const uint32_t negall = (((sbits >> l) & 1u) ^ (sx >> 31)) & 1u;
                         const mag_t r1 = P::presign(P::scale(m1, p), negall);
                         const mag_t r2 = P::presign(P::scale(m2, p), negall);
 #pragma unroll
-                        for (int j = 0; j < DC; ++j) {
+                        for (int j = 0; j < D; ++j) {
                             if (UNIFORM || j < o.mdeg[l]) {
                                 r[l][j] = P::apply_sign(P::mag(q[j]) == m1 ? r2 : r1, q[j]);
                                 Q[v[j]] = P::add(qu[j], r[l][j]);
@@ -330,8 +331,8 @@ __global__ void __launch_bounds__(256, 1) msa_layered_reg_kernel(const LaunchPar
         }
         const uint8_t *s = pr.syn + size_t(b) * M;
         int all = 0;
-        const int k = layered_reg_shot<P, DC, UNIFORM, MAXL>(own, L, N, tid, T, [&](int c) { return uint32_t(s[c]); },
-                                                             pr.prior, Q, p, early, all);
+        const int k = layered_reg_shot<P, DC, DC, UNIFORM, MAXL>(own, L, N, tid, T, [&](int c) { return uint32_t(s[c]); },
+                                                                 pr.prior, Q, p, early, all);
         for (int v = tid; v < N; v += T) {
             err[v] = P::neg(Q[v]) ? 1 : 0;
             if (pr.post) pr.post[size_t(b) * N + v] = P::post(Q[v]);
@@ -388,13 +389,38 @@ __global__ void __launch_bounds__(256, 1) msa_server_layered_kernel(const Server
         auto syn_bit = [&](int c) { return uint32_t(__ldcv(syn + c)); };
         const int N = sc.g.n;
         int all = 0, k;
+        // a server whose codes differ in row degree still runs a code whose rows all have degree 6, 7
+        // or 8 with that degree compiled in (block-uniform dispatch, no divergence)
+        const int L = sc.g.nlayers;
         if (reg) {
-            k = layered_reg_shot<P, DC, UNIFORM, MAXL>(own, sc.g.nlayers, N, tid, T, syn_bit, sc.prior, Q, p, early, all);
+            bool done = false;
+            if constexpr (!UNIFORM && DC >= 8) {
+                done = true;
+                switch (sc.udc) {
+                case 6: k = layered_reg_shot<P, DC, 6, true, MAXL>(own, L, N, tid, T, syn_bit, sc.prior, Q, p, early, all); break;
+                case 7: k = layered_reg_shot<P, DC, 7, true, MAXL>(own, L, N, tid, T, syn_bit, sc.prior, Q, p, early, all); break;
+                case 8: k = layered_reg_shot<P, DC, 8, true, MAXL>(own, L, N, tid, T, syn_bit, sc.prior, Q, p, early, all); break;
+                default: done = false; break;
+                }
+            }
+            if (!done)
+                k = layered_reg_shot<P, DC, DC, UNIFORM, MAXL>(own, L, N, tid, T, syn_bit, sc.prior, Q, p, early, all);
         } else {
             const LayeredLayout lay = layered_layout(sc.g.m, N, sc.g.dc_max, int(sizeof(msg_t)));
-            k = layered_smem_shot<P, DC, UNIFORM>(sc.g, tid, T, syn_bit, sc.prior, Q,
-                                                  reinterpret_cast<msg_t *>(smem + lay.slot_off), smem + lay.s_off, p,
-                                                  early, all);
+            msg_t *slots = reinterpret_cast<msg_t *>(smem + lay.slot_off);
+            uint8_t *sb = smem + lay.s_off;
+            bool done = false;
+            if constexpr (!UNIFORM && DC >= 8) {
+                done = true;
+                switch (sc.udc) {
+                case 6: k = layered_smem_shot<P, 6, true>(sc.g, tid, T, syn_bit, sc.prior, Q, slots, sb, p, early, all); break;
+                case 7: k = layered_smem_shot<P, 7, true>(sc.g, tid, T, syn_bit, sc.prior, Q, slots, sb, p, early, all); break;
+                case 8: k = layered_smem_shot<P, 8, true>(sc.g, tid, T, syn_bit, sc.prior, Q, slots, sb, p, early, all); break;
+                default: done = false; break;
+                }
+            }
+            if (!done)
+                k = layered_smem_shot<P, DC, UNIFORM>(sc.g, tid, T, syn_bit, sc.prior, Q, slots, sb, p, early, all);
         }
         unsigned char *err = slot + sc.err_off;
         for (int v = tid; v < N; v += T) err[v] = P::neg(Q[v]) ? 1 : 0;

@@ -525,8 +525,14 @@ int plan_latency(const qldpc_graph *const *gs, int nprob, int32_t batch, int pre
 int plan_batch(const qldpc_graph *const *gs, int nprob, int32_t batch, int precision, bool learned, Plan &pl)
 {
     const qldpc_graph *g0 = gs[0];
-    const bool packed = !learned && ((precision == QLDPC_INT16 && g0->user_kernel != QLDPC_KERNEL_BATCH) ||
-                                     (precision == QLDPC_INT8 && g0->user_kernel == QLDPC_KERNEL_PACKED));
+    bool packed = !learned && ((precision == QLDPC_INT16 && g0->user_kernel != QLDPC_KERNEL_BATCH) ||
+                               (precision == QLDPC_INT8 && g0->user_kernel == QLDPC_KERNEL_PACKED));
+    if (packed && g0->user_kernel != QLDPC_KERNEL_PACKED) {
+        // by default only where two shots fit a block's shared memory (beside 1 KB of static shared
+        // memory); a graph whose single shot just fits keeps one shot per block
+        for (int i = 0; i < nprob; ++i)
+            packed = packed && packed_layout(gs[i]->m, gs[i]->nv, gs[i]->dc_max).total + 1024 <= g0->smem_optin;
+    }
     size_t smem = 0;
     for (int i = 0; i < nprob; ++i)
         smem = std::max(smem, packed ? packed_layout(gs[i]->m, gs[i]->nv, gs[i]->dc_max).total

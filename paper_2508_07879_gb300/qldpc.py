@@ -496,14 +496,16 @@ class Server:
             ns = np.array([self.graphs[c].n for c in codes], dtype=np.int64)
             err_off[1:] = np.cumsum(ns)[:-1]
             syn_flat = np.concatenate(syn_parts)
-            err_flat = np.zeros(int(ns.sum()), dtype=np.uint8)
+            # written once here, so that its pages are in place before the replay's clock starts
+            err_flat = np.empty(int(ns.sum()), dtype=np.uint8)
+            err_flat.fill(0)
         else:
             syn_flat = np.zeros(1, dtype=np.uint8)
             err_flat = np.zeros(1, dtype=np.uint8)
         arrival = np.ascontiguousarray(arrival_ns, dtype=np.int64)
-        iters = np.zeros(nreq, dtype=np.int32)
-        ok = np.zeros(nreq, dtype=np.uint8)
-        lat = np.zeros(nreq, dtype=np.int64)
+        iters = np.full(nreq, 0, dtype=np.int32)      # np.full writes every page, unlike np.zeros
+        ok = np.full(nreq, 0, dtype=np.uint8)
+        lat = np.full(nreq, 0, dtype=np.int64)
         workers = np.full(max(nreq, 1), -1, dtype=np.int32)
         check(qldpc_server_replay(self._h, nreq, _np_ptr(codes), _np_ptr(syn_flat), _np_ptr(syn_off),
                                   _np_ptr(arrival), _np_ptr(err_flat), _np_ptr(err_off), _np_ptr(iters),

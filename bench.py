@@ -82,7 +82,7 @@ SMEM_BYTES_PER_CLK_PER_SM = 128  # 32 banks x 4 B
 # DRAM bytes of one decoder launch on the benchmark batch, from one ncu capture (the sum of
 # dram__bytes_read.sum and dram__bytes_write.sum), valid only for the kernel source it was taken
 # on (sha256 prefix of msa_kernel.cuh); null once that source changes.
-NCU_TRAFFIC = {"source_sha16": "1a1f4f5b43445955", "bytes_per_launch": 30665216 + 11027456}
+NCU_TRAFFIC = {"source_sha16": "61e9fb1b9d8386fc", "bytes_per_launch": 39156923}
 
 FALLBACK_HBM_GBS = 6800.0     # the profiling recipe's fallback when MEASURED_PEAKS.json is absent
 WORKLOAD = "LP-1054 H_Z (465x1054, E=3720), iid X noise p=0.01..0.05, B=65536/step, max 50 it, alpha 0.75"
@@ -197,7 +197,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -209,6 +209,15 @@ class ClockSampler:
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
+    def wait_first(self, timeout_s: float = 3.0):
+        """Block until the sampler has produced a line (nvidia-smi takes a moment to start)."""
+        t0 = time.time()
+        while self.proc is not None and not self.lines and time.time() - t0 < timeout_s:
+            time.sleep(0.01)
+
+    def mark(self) -> int:
+        return len(self.lines)
+
     def __exit__(self, *exc):
         if self.proc is not None:
             self.proc.terminate()
@@ -218,10 +227,13 @@ class ClockSampler:
                 self.proc.kill()
             self.thread.join(timeout=2)
 
-    def summary(self):
+    def summary(self, lo: int = 0, hi=None):
+        """Median SM clock, max clock and throttle reasons of the samples lines[lo:hi] (the timed
+        region when the caller marked it), or of every sample when that window is empty."""
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in self.lines:
+        window = self.lines[lo:hi] if self.lines[lo:hi] else self.lines
+        for line in window:
             parts = [x.strip() for x in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -401,20 +413,26 @@ def run_ours(args, rank, world, local):
         j = i % len(batches)
         qldpc.decode(graph, syn_d[j], pri_d[j], MAX_ITER, ALPHA, args.precision, out=out, stream=stream)
 
-    for i in range(args.warmup):
-        step(i)
-    stream.synchronize()
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    # clocks sampled every 20 ms from before the warm-up, so that the sampler is running when the
+    # (short) timed region starts; the summary takes the samples of the timed region
     with ClockSampler(local) as clk:
+        clk.wait_first()
+        for i in range(args.warmup):
+            step(i)
+        stream.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        lo = clk.mark()
         e0.record(stream)
         for i in range(args.steps):
             step(i)
         e1.record(stream)
         stream.synchronize()
+        time.sleep(0.03)                     # the sample that covers the region's end
+        hi = clk.mark()
     torch.cuda.synchronize()
     ms = reduce_max(e0.elapsed_time(e1), dev)
     if world > 1:
@@ -426,7 +444,7 @@ def run_ours(args, rank, world, local):
     # roofline of the decoder kernel (one launch per step); the units of one launch are the
     # edge-iterations it runs: E x (iterations summed over its 65536 shots)
     props = torch.cuda.get_device_properties(dev)
-    clocks = clk.summary()
+    clocks = clk.summary(lo, hi)
     packed = args.kernel == "packed" or (args.kernel == "auto" and args.precision == "int16")
     kernel_name = "msa_packed_kernel" if packed and args.precision != "fp32" else "msa_batch_kernel"
     roofline = decoder_roofline(h, B, iters_per_batch, args.steps, ms_per_step, args.precision,
@@ -853,7 +871,8 @@ def measure_bb_sweep(qldpc, args, shots=10000, warm=100):
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
     shots = min(shots, max(1000, args.latency_shots))
     out = {"max_iter": 64, "shots_per_p": shots,
-           "path": "qldpc_decode_pair_host through ctypes (X+Z in one launch), FP32, page-locked buffers"}
+           "path": "qldpc_decode_pair_host through ctypes (X+Z in one launch), FP32, page-locked buffers; "
+                   "server_path: the two halves as two requests at the same instant, latency = the later"}
     for ci, name in enumerate(("bb144", "bb288")):
         code = w.CONFIG_CODES[name]()
         gz, gx = qldpc.Graph.from_csr(code.hz_csr), qldpc.Graph.from_csr(code.hx_csr)
@@ -879,6 +898,16 @@ def measure_bb_sweep(qldpc, args, shots=10000, warm=100):
                               "p99_us": float(np.percentile(x, 99)), "p999_us": float(np.percentile(x, 99.9)),
                               "decoded_fraction": float(both_ok[warm:].mean()),
                               "mean_max_iters": float(its[warm:].mean())}
+            # the same pairs as two requests at the same instant to the persistent server
+            with qldpc.Server([gz, gx], [prior, prior], 64, ALPHA, "fp32", blocks=[8, 8], ring_capacity=1024) as srv:
+                n = shots + warm
+                codes = np.tile(np.array([0, 1], np.int32), n)
+                arrival = np.repeat(np.arange(n) * LAT_SERVER_GAP_NS, 2).astype(np.int64)
+                _, _, _, lat_ns = srv.replay(codes, [r for pair in zip(sx, sz) for r in pair], arrival)
+            y = np.maximum(lat_ns[0::2], lat_ns[1::2])[warm:] / 1e3
+            rows[f"p={p}"]["server_path"] = {"mean_us": float(y.mean()), "p50_us": float(np.percentile(y, 50)),
+                                             "p99_us": float(np.percentile(y, 99)),
+                                             "p999_us": float(np.percentile(y, 99.9))}
         out[name] = rows
         gz.close()
         gx.close()
@@ -989,7 +1018,7 @@ def measure_precisions(qldpc, graph, syn_d, pri_d, out, stream, B, args, steps=1
     """Flooding decode of the benchmark's batches in each precision: throughput and decoded fraction."""
     import torch
     res = {}
-    for name in ("fp32", "int16", "int8", "int16_scalar", "int8_packed"):
+    for name in ("fp32", "int16", "int8", "fp32_packed", "int16_scalar", "int8_packed"):
         prec = name.split("_")[0]
         graph.set_launch("batch" if name.endswith("_scalar") else "packed" if name.endswith("_packed") else "auto")
         ok = iters = 0

@@ -24,7 +24,7 @@ NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibilit
               "-Xptxas", "-v", "--fmad=false"]
 CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-fvisibility=hidden", "-Wall", "-Wextra"]
 
-KERNEL_SOURCES = ["msa_f32.cu", "msa_i16.cu", "msa_i8.cu", "msa_i16x2.cu", "msa_i8x2.cu", "msa_learned.cu",
+KERNEL_SOURCES = ["msa_f32.cu", "msa_i16.cu", "msa_i8.cu", "msa_i16x2.cu", "msa_i8x2.cu", "msa_f32x2.cu", "msa_learned.cu",
                   "msa_layered.cu", "nms_train.cu", "server_f32.cu", "server_i16.cu", "server_i8.cu",
                   "qldpc_noalloc.cu"]
 HOST_SOURCES = ["qldpc_host.cpp", "qldpc_server.cpp", "qldpc_learned.cpp"]

@@ -4,12 +4,12 @@
 
 namespace qldpc {
 
-const void *msa_kernel_i8x2(const KernelChoice &kc) { return packed_table<kern::I8>(kc); }
+const void *msa_kernel_i8x2(const KernelChoice &kc) { return packed_table<kern::Pair16<kern::I8>>(kc); }
 
 cudaError_t launch_msa_i8x2(const LaunchParams &p, const KernelChoice &kc, dim3 grid, int threads, size_t smem,
                             cudaStream_t stream)
 {
-    return packed_launch<kern::I8>(p, kc, grid, threads, smem, stream);
+    return packed_launch<kern::Pair16<kern::I8>>(p, kc, grid, threads, smem, stream);
 }
 
 }  // namespace qldpc

@@ -214,6 +214,9 @@ cudaError_t launch_msa_i8(const LaunchParams &p, const KernelChoice &kc, dim3 gr
 // Two-shots-per-word fixed-point throughput kernels, msa_i16x2.cu / msa_i8x2.cu (msa_packed.cuh).
 const void *msa_kernel_i16x2(const KernelChoice &kc);
 const void *msa_kernel_i8x2(const KernelChoice &kc);
+const void *msa_kernel_f32x2(const KernelChoice &kc);
+cudaError_t launch_msa_f32x2(const LaunchParams &p, const KernelChoice &kc, dim3 grid, int threads,
+                             size_t smem, cudaStream_t stream);
 cudaError_t launch_msa_i16x2(const LaunchParams &p, const KernelChoice &kc, dim3 grid, int threads,
                              size_t smem, cudaStream_t stream);
 cudaError_t launch_msa_i8x2(const LaunchParams &p, const KernelChoice &kc, dim3 grid, int threads,
@@ -224,20 +227,21 @@ cudaError_t launch_msa_i8x2(const LaunchParams &p, const KernelChoice &kc, dim3 
 // more instructions and a slower kernel, although twice as many warps were resident.
 constexpr int kPackedMaxThreads = 512;
 
-// Shared memory of one block of the packed kernel (two shots): gamma [nv] i32, Q [nv] i32x2,
-// parity words [m], packed message slots [dc_max*m + scratch] u32.
+// Shared memory of one block of the packed kernel (two shots): gamma [nv] (4 B), Q [nv] (two lanes,
+// 8 B), parity words [m], paired message slots [dc_max*m + scratch] of word_bytes (4: two 16-bit
+// fixed-point lanes; 8: two FP32 lanes).
 struct PackedLayout {
     size_t g_off, q_off, par_off, slot_off, total;
 };
 
-__host__ __device__ inline PackedLayout packed_layout(int m, int nv, int dc_max)
+__host__ __device__ inline PackedLayout packed_layout(int m, int nv, int dc_max, int word_bytes)
 {
     PackedLayout l;
     l.g_off = 0;
     l.q_off = align16(size_t(nv) * 4);
     l.par_off = align16(l.q_off + size_t(nv) * 8);
     l.slot_off = align16(l.par_off + size_t(m) * 4);
-    l.total = align16(l.slot_off + (size_t(dc_max) * m + kScratch) * 4);
+    l.total = align16(l.slot_off + (size_t(dc_max) * m + kScratch) * size_t(word_bytes));
     return l;
 }
 

@@ -188,35 +188,174 @@ __device__ __forceinline__ int2 var_step_x2(int u, int NV, const CheckOf &ck, co
     }
 }
 
-template <class P, int DV>
-__device__ __forceinline__ int2 var_step_x2_dispatch(int deg, int u, int NV, const CheckOf &ck, const uint32_t *vslot,
-                                                     int32_t gamma, int2 Qold, uint32_t keep, uint32_t *slots,
-                                                     uint32_t *parity)
+// ---------------------------------------------------------------------------------------------
+// Two FP32 shots per block: the slots hold float2 pairs (lane 0 in .x, lane 1 in .y).  The check
+// step runs the FP32 arithmetic of check_step on each lane (one 8-byte load and store per edge
+// for both); the variable step forms both lanes' literal prefix and exclusive sums with one
+// add.rn.f32x2 per addition (each lane rounded to nearest on its own, so both are bit-identical to
+// var_step_exact).
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ float2 add2_rn(float2 a, float2 b)
+{
+    unsigned long long x, y, r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(x) : "f"(a.x), "f"(a.y));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(y) : "f"(b.x), "f"(b.y));
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(x), "l"(y));
+    float2 o;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(o.x), "=f"(o.y) : "l"(r));
+    return o;
+}
+
+template <int DC, bool UNIFORM>
+__device__ __forceinline__ void check_step_f32x2(int c, int M, int deg, uint32_t pw, float2 *__restrict__ slots,
+                                                 float alpha)
+{
+    using P = F32;
+    float q0[DC], q1[DC];
+    uint32_t sx0 = 0, sx1 = 0;
+#pragma unroll
+    for (int j = 0; j < DC; ++j) {
+        if (UNIFORM || j < deg) {
+            const float2 v = slots[j * M + c];
+            q0[j] = v.x;
+            q1[j] = v.y;
+            sx0 ^= __float_as_uint(v.x);
+            sx1 ^= __float_as_uint(v.y);
+        }
+    }
+    float a1, a2, b1, b2;
+    two_smallest<P, DC, UNIFORM>(q0, deg, a1, a2);
+    two_smallest<P, DC, UNIFORM>(q1, deg, b1, b2);
+    const uint32_t na = ((pw >> 15) ^ (sx0 >> 31)) & 1u, nb = ((pw >> 31) ^ (sx1 >> 31)) & 1u;
+    const float ra1 = P::presign(__fmul_rn(alpha, a1), na), ra2 = P::presign(__fmul_rn(alpha, a2), na);
+    const float rb1 = P::presign(__fmul_rn(alpha, b1), nb), rb2 = P::presign(__fmul_rn(alpha, b2), nb);
+#pragma unroll
+    for (int j = 0; j < DC; ++j) {
+        if (UNIFORM || j < deg)
+            slots[j * M + c] = make_float2(P::apply_sign(fabsf(q0[j]) == a1 ? ra2 : ra1, q0[j]),
+                                           P::apply_sign(fabsf(q1[j]) == b1 ? rb2 : rb1, q1[j]));
+    }
+}
+
+template <int D>
+__device__ __forceinline__ float2 var_step_f32x2(int u, int NV, const CheckOf &ck, const uint32_t *__restrict__ vslot,
+                                                 float gamma, float2 Qold, uint32_t act, float2 *__restrict__ slots,
+                                                 uint32_t *__restrict__ parity)
+{
+    if constexpr (D == 0) {
+        return make_float2(gamma, gamma);
+    } else {
+        const uint32_t k0 = (act & 1u) ? 0xffffffffu : 0u, k1 = (act & 2u) ? 0xffffffffu : 0u;
+        uint32_t e[D];
+        float2 r[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) e[k] = __ldg(vslot + size_t(k) * NV + u);
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            const float2 v = slots[e[k]];        // a lane that restarts takes r = +0: Q = q = gamma
+            r[k] = make_float2(__uint_as_float(__float_as_uint(v.x) & k0), __uint_as_float(__float_as_uint(v.y) & k1));
+        }
+        float2 pre[D + 1];
+        pre[0] = make_float2(gamma, gamma);
+#pragma unroll
+        for (int k = 0; k < D; ++k) pre[k + 1] = add2_rn(pre[k], r[k]);
+        const float2 Q = pre[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            float2 q = pre[k];
+#pragma unroll
+            for (int i = k + 1; i < D; ++i) q = add2_rn(q, r[i]);
+            slots[e[k]] = q;
+        }
+        const uint32_t flip = uint32_t((Q.x < 0.0f) != (Qold.x < 0.0f)) | (uint32_t((Q.y < 0.0f) != (Qold.y < 0.0f)) << 16);
+        if (flip) {
+#pragma unroll
+            for (int k = 0; k < D; ++k) atomicXor(parity + ck(e[k]), flip);
+        }
+        return Q;
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Lane-pair policies: what the kernel below needs of each precision.
+// ---------------------------------------------------------------------------------------------
+template <class P>   // I16 or I8: two 16-bit two's-complement lanes per 32-bit word
+struct Pair16 {
+    using word_t = uint32_t;
+    using gam_t = int32_t;
+    using pair_t = int2;
+    static __device__ __forceinline__ gam_t quantize(float g) { return P::quantize(g); }
+    static __device__ __forceinline__ pair_t both(gam_t g) { return make_int2(g, g); }
+    static __device__ __forceinline__ bool neg(gam_t x) { return x < 0; }
+    static __device__ __forceinline__ float post(gam_t x) { return P::post(x); }
+    template <int DC, bool UNIFORM>
+    static __device__ __forceinline__ void check(int c, int M, int deg, uint32_t pw, word_t *slots, const LaunchParams &p)
+    {
+        check_step_x2<P, DC, UNIFORM>(c, M, deg, pw, slots, p.alpha_q);
+    }
+    template <int D>
+    static __device__ __forceinline__ pair_t var(int u, int NV, const CheckOf &ck, const uint32_t *vslot, gam_t gamma,
+                                                 pair_t Qold, uint32_t act, word_t *slots, uint32_t *parity)
+    {
+        const uint32_t keep = ((act & 1u) ? 0x0000ffffu : 0u) | ((act & 2u) ? 0xffff0000u : 0u);
+        return var_step_x2<P, D>(u, NV, ck, vslot, gamma, Qold, keep, slots, parity);
+    }
+};
+
+struct PairF32 {     // two FP32 lanes per 8-byte slot
+    using word_t = float2;
+    using gam_t = float;
+    using pair_t = float2;
+    static __device__ __forceinline__ gam_t quantize(float g) { return F32::quantize(g); }
+    static __device__ __forceinline__ pair_t both(gam_t g) { return make_float2(g, g); }
+    static __device__ __forceinline__ bool neg(gam_t x) { return x < 0.0f; }
+    static __device__ __forceinline__ float post(gam_t x) { return x; }
+    template <int DC, bool UNIFORM>
+    static __device__ __forceinline__ void check(int c, int M, int deg, uint32_t pw, word_t *slots, const LaunchParams &p)
+    {
+        check_step_f32x2<DC, UNIFORM>(c, M, deg, pw, slots, p.alpha);
+    }
+    template <int D>
+    static __device__ __forceinline__ pair_t var(int u, int NV, const CheckOf &ck, const uint32_t *vslot, gam_t gamma,
+                                                 pair_t Qold, uint32_t act, word_t *slots, uint32_t *parity)
+    {
+        return var_step_f32x2<D>(u, NV, ck, vslot, gamma, Qold, act, slots, parity);
+    }
+};
+
+template <class PP, int DV>
+__device__ __forceinline__ typename PP::pair_t pair_var_dispatch(int deg, int u, int NV, const CheckOf &ck,
+                                                                 const uint32_t *vslot, typename PP::gam_t gamma,
+                                                                 typename PP::pair_t Qold, uint32_t act,
+                                                                 typename PP::word_t *slots, uint32_t *parity)
 {
     switch (deg) {
 #define QLDPC_CASE(D)                                                                           \
     case D:                                                                                     \
-        if constexpr (D <= DV) return var_step_x2<P, D>(u, NV, ck, vslot, gamma, Qold, keep, slots, parity); \
+        if constexpr (D <= DV) return PP::template var<D>(u, NV, ck, vslot, gamma, Qold, act, slots, parity); \
         break;
         QLDPC_DEG_CASES(QLDPC_CASE)
 #undef QLDPC_CASE
     default: break;
     }
-    return make_int2(gamma, gamma);
+    return PP::both(gamma);
 }
 
-template <class P, int DC, bool UNIFORM, int DV>
+template <class PP, int DC, bool UNIFORM, int DV>
 __global__ void __launch_bounds__(kPackedMaxThreads, 1) msa_packed_kernel(const LaunchParams p)
 {
     const Problem pr = blockIdx.y == 0 ? p.prob[0] : p.prob[1];
     const int M = pr.g.m, N = pr.g.n, NV = pr.g.nv;
     const int T = blockDim.x, tid = threadIdx.x;
     extern __shared__ __align__(16) unsigned char smem[];
-    const PackedLayout L = packed_layout(M, NV, pr.g.dc_max);
-    int32_t *gam = reinterpret_cast<int32_t *>(smem + L.g_off);
-    int2 *Qs = reinterpret_cast<int2 *>(smem + L.q_off);
+    using word_t = typename PP::word_t;
+    using gam_t = typename PP::gam_t;
+    using pair_t = typename PP::pair_t;
+    const PackedLayout L = packed_layout(M, NV, pr.g.dc_max, int(sizeof(word_t)));
+    gam_t *gam = reinterpret_cast<gam_t *>(smem + L.g_off);
+    pair_t *Qs = reinterpret_cast<pair_t *>(smem + L.q_off);
     uint32_t *parity = reinterpret_cast<uint32_t *>(smem + L.par_off);
-    uint32_t *slots = reinterpret_cast<uint32_t *>(smem + L.slot_off);
+    word_t *slots = reinterpret_cast<word_t *>(smem + L.slot_off);
     __shared__ int s_claim[2];
     __shared__ uint32_t s_any[2];   // OR of the parity words' lane bits (alternating per iteration)
 
@@ -225,8 +364,8 @@ __global__ void __launch_bounds__(kPackedMaxThreads, 1) msa_packed_kernel(const 
         const uint32_t v = __ldg(pr.g.vperm + u);
         const float g = v < uint32_t(N) ? pr.prior[v] : 0.0f;
         bad |= !isfinite(g);
-        gam[u] = P::quantize(g);
-        Qs[u] = make_int2(0, 0);        // the decisions a refill compares against: none set
+        gam[u] = PP::quantize(g);
+        Qs[u] = PP::both(gam_t(0));     // the decisions a refill compares against: none set
     }
     for (int c = tid; c < M; c += T) parity[c] = 0u;
     if (tid < 2) s_any[tid] = 0u;
@@ -259,24 +398,23 @@ __global__ void __launch_bounds__(kPackedMaxThreads, 1) msa_packed_kernel(const 
     uint32_t act = 0u, refill = 3u, out = 0u, fresh = 0u, ph = 0u;
     for (;;) {
         // ---- variable step: updates, outputs of finished shots, refills ----
-        const uint32_t keep = ((act & 1u) ? 0x0000ffffu : 0u) | ((act & 2u) ? 0xffff0000u : 0u);
         for (int u = tid; u < NV; u += T) {
-            const int2 Qo = Qs[u];
+            const pair_t Qo = Qs[u];
             if (out) {
                 const uint32_t v = __ldg(pr.g.vperm + u);
                 if (v < uint32_t(N)) {
 #pragma unroll
                     for (int l = 0; l < 2; ++l) {
                         if (out & (1u << l)) {
-                            const int32_t q = l ? Qo.y : Qo.x;
-                            pr.err[size_t(shot[l]) * N + v] = q < 0 ? 1 : 0;
-                            if (pr.post) pr.post[size_t(shot[l]) * N + v] = P::post(q);
+                            const gam_t q = l ? Qo.y : Qo.x;
+                            pr.err[size_t(shot[l]) * N + v] = PP::neg(q) ? 1 : 0;
+                            if (pr.post) pr.post[size_t(shot[l]) * N + v] = PP::post(q);
                         }
                     }
                 }
             }
-            Qs[u] = var_step_x2_dispatch<P, DV>(__ldg(pr.g.vdeg + u), u, NV, ck, pr.g.vslot, gam[u], Qo, keep, slots,
-                                                parity);
+            Qs[u] = pair_var_dispatch<PP, DV>(__ldg(pr.g.vdeg + u), u, NV, ck, pr.g.vslot, gam[u], Qo, act, slots,
+                                              parity);
         }
         if (tid == 0) {
             s_any[ph] = 0u;                           // the word the next check step reduces into
@@ -316,7 +454,7 @@ __global__ void __launch_bounds__(kPackedMaxThreads, 1) msa_packed_kernel(const 
                 parity[c] = pw;
             }
             unsat |= pw;
-            check_step_x2<P, DC, UNIFORM>(c, M, UNIFORM ? DC : int(__ldg(pr.g.rdeg + c)), pw, slots, p.alpha_q);
+            PP::template check<DC, UNIFORM>(c, M, UNIFORM ? DC : int(__ldg(pr.g.rdeg + c)), pw, slots, p);
         }
         // block OR of both lanes' unsatisfied bits (bit 0 and bit 16): warp OR, one shared OR per warp
         const uint32_t wv = __reduce_or_sync(0xffffffffu, unsat & 0x00010001u);
@@ -344,24 +482,24 @@ __global__ void __launch_bounds__(kPackedMaxThreads, 1) msa_packed_kernel(const 
 
 // Instantiation tables of the packed kernel for one fixed-point policy (same variants as the other
 // flooding kernels).
-template <class P>
+template <class PP>
 const void *packed_table(const KernelChoice &kc)
 {
 #define QLDPC_K(DCV, UNI, DVV)                                                                  \
     if (kc.dc == DCV && kc.uniform == UNI && kc.dvb == DVV)                                     \
-        return reinterpret_cast<const void *>(&kern::msa_packed_kernel<P, DCV, UNI, DVV>);
+        return reinterpret_cast<const void *>(&kern::msa_packed_kernel<PP, DCV, UNI, DVV>);
     QLDPC_VARIANTS(QLDPC_K)
 #undef QLDPC_K
     return nullptr;
 }
 
-template <class P>
+template <class PP>
 cudaError_t packed_launch(const LaunchParams &p, const KernelChoice &kc, dim3 grid, int threads, size_t smem,
                           cudaStream_t stream)
 {
 #define QLDPC_L(DCV, UNI, DVV)                                                                  \
     if (kc.dc == DCV && kc.uniform == UNI && kc.dvb == DVV) {                                   \
-        kern::msa_packed_kernel<P, DCV, UNI, DVV><<<grid, threads, smem, stream>>>(p);          \
+        kern::msa_packed_kernel<PP, DCV, UNI, DVV><<<grid, threads, smem, stream>>>(p);         \
         return cudaGetLastError();                                                              \
     }
     QLDPC_VARIANTS(QLDPC_L)

@@ -34,7 +34,8 @@ const void *msa_kernel(int precision, const KernelChoice &kc)
 {
     if (kc.layered) return msa_kernel_layered(precision, kc);
     if (kc.learned) return msa_kernel_learned(kc);
-    if (kc.packed) return precision == kINT16 ? msa_kernel_i16x2(kc) : precision == kINT8 ? msa_kernel_i8x2(kc) : nullptr;
+    if (kc.packed)
+        return precision == kINT16 ? msa_kernel_i16x2(kc) : precision == kINT8 ? msa_kernel_i8x2(kc) : msa_kernel_f32x2(kc);
     return precision == kINT16 ? msa_kernel_i16(kc) : precision == kINT8 ? msa_kernel_i8(kc) : msa_kernel_f32(kc);
 }
 
@@ -47,7 +48,7 @@ cudaError_t launch_msa(const LaunchParams &p, int precision, const KernelChoice 
     if (kc.packed)
         return precision == kINT16  ? launch_msa_i16x2(p, kc, grid, threads, smem, stream)
                : precision == kINT8 ? launch_msa_i8x2(p, kc, grid, threads, smem, stream)
-                                    : cudaErrorInvalidValue;
+                                    : launch_msa_f32x2(p, kc, grid, threads, smem, stream);
     return precision == kINT16  ? launch_msa_i16(p, kc, grid, threads, smem, stream)
            : precision == kINT8 ? launch_msa_i8(p, kc, grid, threads, smem, stream)
                                 : launch_msa_f32(p, kc, grid, threads, smem, stream);
@@ -525,17 +526,18 @@ int plan_latency(const qldpc_graph *const *gs, int nprob, int32_t batch, int pre
 int plan_batch(const qldpc_graph *const *gs, int nprob, int32_t batch, int precision, bool learned, Plan &pl)
 {
     const qldpc_graph *g0 = gs[0];
+    const int word = precision == QLDPC_FP32 ? 8 : 4;   // bytes of one paired slot
     bool packed = !learned && ((precision == QLDPC_INT16 && g0->user_kernel != QLDPC_KERNEL_BATCH) ||
-                               (precision == QLDPC_INT8 && g0->user_kernel == QLDPC_KERNEL_PACKED));
+                               (precision != QLDPC_INT16 && g0->user_kernel == QLDPC_KERNEL_PACKED));
     if (packed && g0->user_kernel != QLDPC_KERNEL_PACKED) {
         // by default only where two shots fit a block's shared memory (beside 1 KB of static shared
         // memory); a graph whose single shot just fits keeps one shot per block
         for (int i = 0; i < nprob; ++i)
-            packed = packed && packed_layout(gs[i]->m, gs[i]->nv, gs[i]->dc_max).total + 1024 <= g0->smem_optin;
+            packed = packed && packed_layout(gs[i]->m, gs[i]->nv, gs[i]->dc_max, word).total + 1024 <= g0->smem_optin;
     }
     size_t smem = 0;
     for (int i = 0; i < nprob; ++i)
-        smem = std::max(smem, packed ? packed_layout(gs[i]->m, gs[i]->nv, gs[i]->dc_max).total
+        smem = std::max(smem, packed ? packed_layout(gs[i]->m, gs[i]->nv, gs[i]->dc_max, word).total
                                      : shot_smem(gs[i], precision));
     pl.kc = variant(gs, nprob, false, learned);
     pl.kc.packed = packed;

@@ -13,6 +13,8 @@ const void *msa_kernel_learned(const KernelChoice &) { return nullptr; }
 const void *msa_kernel_layered(int, const KernelChoice &) { return nullptr; }
 const void *msa_kernel_i16x2(const KernelChoice &) { return nullptr; }
 const void *msa_kernel_i8x2(const KernelChoice &) { return nullptr; }
+const void *msa_kernel_f32x2(const KernelChoice &) { return nullptr; }
+cudaError_t launch_msa_f32x2(const LaunchParams &, const KernelChoice &, dim3, int, size_t, cudaStream_t) { return cudaErrorInvalidValue; }
 cudaError_t launch_msa_i16x2(const LaunchParams &, const KernelChoice &, dim3, int, size_t, cudaStream_t) { return cudaErrorInvalidValue; }
 cudaError_t launch_msa_i8x2(const LaunchParams &, const KernelChoice &, dim3, int, size_t, cudaStream_t) { return cudaErrorInvalidValue; }
 cudaError_t launch_msa_f32(const LaunchParams &, const KernelChoice &, dim3, int, size_t, cudaStream_t) { return cudaErrorInvalidValue; }

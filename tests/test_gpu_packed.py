@@ -1,12 +1,11 @@
-"""The two-shots-per-word fixed-point kernel (QLDPC_KERNEL_PACKED, the default throughput kernel of
-INT16 and INT8) against the oracle, element by element: decisions, iterations, ok and a-posteriori
-LLRs, bit-exact.
+"""The two-shots-per-block kernel (QLDPC_KERNEL_PACKED; the default throughput kernel of INT16)
+against the oracle, element by element: decisions, iterations, ok and a-posteriori LLRs, bit-exact,
+in INT16 and INT8 (two 16-bit lanes per message word) and FP32 (float2 slots, paired additions).
 
-The kernel decodes two shots per block in the two 16-bit lanes of every message word and refills
-each lane with the next shot as soon as its own shot stops, so the cases below mix shots that stop
-at very different iterations (met syndromes at iteration 0 beside shots that run to the limit), odd
-batch sizes (a lane idle at the end), the pair decode, paper mode, max_iter = 0, block sizes, a
-non-finite prior and codes of irregular degree."""
+The kernel decodes two shots per block and refills each lane with the next shot as soon as its own
+shot stops, so the cases below mix shots that stop at very different iterations (met syndromes at
+iteration 0 beside shots that run to the limit), odd batch sizes (a lane idle at the end), the pair
+decode, paper mode, max_iter = 0, block sizes, a non-finite prior and codes of irregular degree."""
 import numpy as np
 import pytest
 
@@ -16,8 +15,8 @@ from paper_2508_07879_gb300 import workloads as w
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
-OPREC = {"int16": "i16", "int8": "i8"}
-SCALE = {"int16": 256.0, "int8": 4.0}
+OPREC = {"int16": "i16", "int8": "i8", "fp32": "f32"}
+SCALE = {"int16": 256.0, "int8": 4.0, "fp32": 1.0}
 
 
 @pytest.fixture(scope="module")
@@ -63,7 +62,7 @@ def mixed_batch(code, shots, seed):
     return s
 
 
-@pytest.mark.parametrize("precision", ["int16", "int8"])
+@pytest.mark.parametrize("precision", ["int16", "int8", "fp32"])
 @pytest.mark.parametrize("name", ["lp1054", "hgp400", "bb288"])
 def test_packed_matches_oracle(q, name, precision):
     code = w.CONFIG_CODES[name]()
@@ -75,7 +74,7 @@ def test_packed_matches_oracle(q, name, precision):
     assert (ref["iters"] == 0).any() and (ref["iters"] > 10).any() and (ref["ok"] == 0).any()
 
 
-@pytest.mark.parametrize("precision", ["int16", "int8"])
+@pytest.mark.parametrize("precision", ["int16", "int8", "fp32"])
 def test_packed_batch_sizes_and_block_shapes(q, precision):
     """B = 1, 2, 3 (a lane idle from the start or at the end), 257, and 64 / 256 / 512 threads."""
     code = w.lp_code(1054)
@@ -89,7 +88,7 @@ def test_packed_batch_sizes_and_block_shapes(q, precision):
         assert_oracle(run_packed(q, g, s, prior, 50, precision, threads=threads), h, s, prior, 50, precision)
 
 
-@pytest.mark.parametrize("precision", ["int16", "int8"])
+@pytest.mark.parametrize("precision", ["int16", "int8", "fp32"])
 def test_packed_paper_mode_and_zero_iterations(q, precision):
     code = w.hgp_code(400)
     h = code.hz_csr
@@ -102,7 +101,7 @@ def test_packed_paper_mode_and_zero_iterations(q, precision):
     assert_oracle(run_packed(q, g, s, prior, 0, precision), h, s, prior, 0, precision)
 
 
-@pytest.mark.parametrize("precision", ["int16", "int8"])
+@pytest.mark.parametrize("precision", ["int16", "int8", "fp32"])
 def test_packed_saturating_priors_and_irregular_rows(q, precision):
     """Priors that saturate the message range, and a code with rows of degree 3..8 and columns of
     degree 1..5 (the non-uniform kernel variant)."""
@@ -119,7 +118,7 @@ def test_packed_saturating_priors_and_irregular_rows(q, precision):
         assert_oracle(run_packed(q, g, s, prior, 40, precision), h, s, prior, 40, precision)
 
 
-@pytest.mark.parametrize("precision", ["int16", "int8"])
+@pytest.mark.parametrize("precision", ["int16", "int8", "fp32"])
 def test_packed_pair_decode(q, precision):
     """The X+Z pair in one launch (blockIdx.y selects the half) equals the oracle on each half."""
     code = w.bb_code(12, 12)
@@ -139,34 +138,30 @@ def test_packed_pair_decode(q, precision):
     assert_oracle([t.cpu().numpy() for t in rz], code.hx_csr, sz, prior, 64, precision)
 
 
-def test_packed_non_finite_prior_and_fp32_fallback(q):
+@pytest.mark.parametrize("precision", ["int16", "fp32"])
+def test_packed_non_finite_prior(q, precision):
     code = w.hgp_code(400)
     h = code.hz_csr
     g = q.Graph.from_csr(h)
     s = mixed_batch(code, 300, seed=750)
     prior = np.full(h.n, 2.0, dtype=np.float32)
     prior[17] = np.nan
-    err, iters, ok, post = run_packed(q, g, s, prior, 20, "int16")
+    err, iters, ok, post = run_packed(q, g, s, prior, 20, precision)
     assert (iters == -1).all() and (ok == 0).all() and (err == 0).all() and np.isnan(post).all()
-    # FP32 has no packed form: the override decodes it with the one-shot-per-block kernel
-    prior = np.full(h.n, w.prior_llr(0.05), dtype=np.float32)
-    got = run_packed(q, g, s, prior, 32, "fp32")
-    ref = oracle.msa(h.row_ptr, h.col_idx, h.m, h.n, s, prior, 32, 0.75, "f32", True, threads=16)
-    np.testing.assert_array_equal(got[0], ref["err"])
-    np.testing.assert_array_equal(got[1], ref["iters"])
-    np.testing.assert_array_equal(got[3], ref["post"])
 
 
-def test_packed_large_batch_sampled_against_oracle(q):
-    """The benchmark's launch shape (LP-1054, 65536 shots, INT16): 1500 sampled shots against the
-    oracle, and every reported success meets its syndrome."""
+@pytest.mark.parametrize("precision", ["int16", "fp32"])
+def test_packed_large_batch_sampled_against_oracle(q, precision):
+    """The benchmark's launch shape (LP-1054, 65536 shots): 1500 sampled shots against the oracle,
+    and every reported success meets its syndrome."""
     code = w.lp_code(1054)
     h = code.hz_csr
     g = q.Graph.from_csr(h)
     b = w.x_error_batch(code, 0.03, 65536, seed=2003)
-    err, iters, ok, post = run_packed(q, g, b.syndromes, b.prior, 50, "int16")
+    err, iters, ok, post = run_packed(q, g, b.syndromes, b.prior, 50, precision)
     idx = np.random.default_rng(3).choice(65536, 1500, replace=False)
-    ref = oracle.msa(h.row_ptr, h.col_idx, h.m, h.n, b.syndromes[idx], b.prior, 50, 0.75, "i16", True, threads=16)
+    ref = oracle.msa(h.row_ptr, h.col_idx, h.m, h.n, b.syndromes[idx], b.prior, 50, 0.75, OPREC[precision], True,
+                     threads=16)
     np.testing.assert_array_equal(err[idx], ref["err"])
     np.testing.assert_array_equal(iters[idx], ref["iters"])
     np.testing.assert_array_equal(ok[idx], ref["ok"])

@@ -79,10 +79,11 @@ SMEM_ACCESSES_PER_EDGE_ITER = 4
 MSG_BYTES = {"fp32": 4, "int16": 2, "int8": 1}
 SMEM_BYTES_PER_CLK_PER_SM = 128  # 32 banks x 4 B
 
-# DRAM bytes of one decoder launch on the benchmark batch, from one ncu capture (the sum of
-# dram__bytes_read.sum and dram__bytes_write.sum), valid only for the kernel source it was taken
-# on (sha256 prefix of msa_kernel.cuh); null once that source changes.
-NCU_TRAFFIC = {"source_sha16": "61e9fb1b9d8386fc", "bytes_per_launch": 39156923}
+# DRAM bytes of one decoder launch on the benchmark batch (FP32), from ncu captures (the sum of
+# dram__bytes_read.sum and dram__bytes_write.sum, mean over launches of the five rates), valid only for
+# the kernel source they were taken on (sha256 prefix of that file); null once that source changes.
+NCU_TRAFFIC = {"msa_batch_kernel": {"source": "msa_kernel.cuh", "source_sha16": "61e9fb1b9d8386fc",
+                                    "bytes_per_launch": 39156923}}
 
 FALLBACK_HBM_GBS = 6800.0     # the profiling recipe's fallback when MEASURED_PEAKS.json is absent
 WORKLOAD = "LP-1054 H_Z (465x1054, E=3720), iid X noise p=0.01..0.05, B=65536/step, max 50 it, alpha 0.75"
@@ -143,11 +144,16 @@ def dist_env():
     return rank, world, local
 
 
-def kernel_traffic():
+def kernel_traffic(kernel_name: str):
+    """DRAM bytes of one launch of the named decoder kernel on the benchmark batch, from the ncu
+    capture recorded for its current source, else None."""
     import hashlib
-    src = os.path.join(ROOT, "paper_2508_07879_gb300", "csrc", "msa_kernel.cuh")
+    rec = NCU_TRAFFIC.get(kernel_name)
+    if rec is None:
+        return None
+    src = os.path.join(ROOT, "paper_2508_07879_gb300", "csrc", rec["source"])
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    return NCU_TRAFFIC["bytes_per_launch"] if sha == NCU_TRAFFIC["source_sha16"] else None
+    return rec["bytes_per_launch"] if sha == rec["source_sha16"] else None
 
 
 def shard(rank: int, world: int, batch: int):
@@ -445,8 +451,7 @@ def run_ours(args, rank, world, local):
     # edge-iterations it runs: E x (iterations summed over its 65536 shots)
     props = torch.cuda.get_device_properties(dev)
     clocks = clk.summary(lo, hi)
-    packed = args.kernel == "packed" or (args.kernel == "auto" and args.precision == "int16")
-    kernel_name = "msa_packed_kernel" if packed and args.precision != "fp32" else "msa_batch_kernel"
+    kernel_name = "msa_batch_kernel" if args.kernel == "batch" else "msa_packed_kernel"
     roofline = decoder_roofline(h, B, iters_per_batch, args.steps, ms_per_step, args.precision,
                                 props.multi_processor_count, clocks["sm_max_mhz"] or 2070.0, kernel_name)
 
@@ -563,12 +568,11 @@ def decoder_roofline(h, B, iters_per_batch, steps, ms_per_step, precision, sms, 
            "frac": round(hbm_bytes / t / hbm_peak, 5), "bytes_per_launch": hbm_bytes, "peak_basis": hbm_basis}
     binding = "smem" if smem["time_at_peak_ms"] >= alu["time_at_peak_ms"] else "alu"
     top = smem if binding == "smem" else alu
-    traffic = kernel_traffic() if (B == BATCH and kernel_name == "msa_batch_kernel" and precision == "fp32") else None
+    traffic = kernel_traffic(kernel_name) if (B == BATCH and precision == "fp32") else None
     return {"bound": binding, "achieved": top["achieved"], "peak": top["peak"], "unit": top["unit"],
             "frac": top["frac"], "traffic": traffic,
             "traffic_source": {"kind": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch",
-                               "source_sha16": NCU_TRAFFIC["source_sha16"],
-                               "current": traffic is not None},
+                               "recorded": NCU_TRAFFIC.get(kernel_name), "current": traffic is not None},
             "kernel": kernel_name, "smem": smem, "alu": alu, "hbm": hbm}
 
 
@@ -1018,9 +1022,9 @@ def measure_precisions(qldpc, graph, syn_d, pri_d, out, stream, B, args, steps=1
     """Flooding decode of the benchmark's batches in each precision: throughput and decoded fraction."""
     import torch
     res = {}
-    for name in ("fp32", "int16", "int8", "fp32_packed", "int16_scalar", "int8_packed"):
+    for name in ("fp32", "int16", "int8", "fp32_one_shot", "int16_one_shot", "int8_one_shot"):
         prec = name.split("_")[0]
-        graph.set_launch("batch" if name.endswith("_scalar") else "packed" if name.endswith("_packed") else "auto")
+        graph.set_launch("batch" if name.endswith("_one_shot") else "auto")
         ok = iters = 0
         with torch.cuda.stream(stream):
             for j in range(len(syn_d)):
@@ -1042,8 +1046,8 @@ def measure_precisions(qldpc, graph, syn_d, pri_d, out, stream, B, args, steps=1
             stream.synchronize()
         res[name] = {"value": B * steps / (e0.elapsed_time(e1) / 1e3), "unit": "syndromes/s",
                      "decoded_fraction": ok / (len(syn_d) * B), "mean_iters": iters / (len(syn_d) * B),
-                     "kernel": "msa_packed_kernel (two shots per block)" if (prec == "int16" and name == "int16")
-                     or name.endswith("_packed") else "msa_batch_kernel (one shot per block)"}
+                     "kernel": "msa_batch_kernel (one shot per block)" if name.endswith("_one_shot")
+                     else "msa_packed_kernel (two shots per block)"}
     graph.set_launch("auto")
     return res
 

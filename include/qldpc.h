@@ -162,14 +162,15 @@ QLDPC_API int qldpc_graph_footprint(const qldpc_graph *g, int32_t precision, int
 /* Kernels (qldpc_graph_set_launch). */
 enum {
     QLDPC_KERNEL_AUTO = 0,      /* latency kernel when every shot gets its own SM, else the packed
-                                   kernel in INT16 and the batch kernel in FP32 and INT8 */
+                                   kernel where two shots fit a block's shared memory (learned
+                                   decoding: the batch kernel) */
     QLDPC_KERNEL_BATCH = 1,     /* throughput kernel: one shot per block, thread per check / per
                                    variable, persistent blocks */
     QLDPC_KERNEL_LATENCY = 2,   /* single-shot kernel: per-thread state in registers, one block per
                                    shot; needs m <= 2*threads and n <= 2*threads, threads <= 640 */
-    QLDPC_KERNEL_PACKED = 3     /* throughput kernel of the fixed-point precisions: two shots per
-                                   block, their messages paired in one 32-bit word per edge (FP32
-                                   decodes use the batch kernel) */
+    QLDPC_KERNEL_PACKED = 3     /* throughput kernel with two shots per block, their messages paired
+                                   in one slot per edge (two 16-bit lanes in INT16 / INT8, a float2 in
+                                   FP32); each shot stops at its own iteration */
 };
 
 /* Override the library's launch choice for this graph: the kernel, its threads per block (a

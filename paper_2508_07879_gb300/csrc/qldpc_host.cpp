@@ -519,16 +519,15 @@ int plan_latency(const qldpc_graph *const *gs, int nprob, int32_t batch, int pre
     return QLDPC_OK;
 }
 
-// Throughput path: one shot per block, or two shots per block with their messages paired in one word
-// (INT16 by default, INT16 / INT8 when the graph's launch override asks for it).  Measured on LP-1054
-// at 65536 shots: INT16 28.8 M/s packed against 26.5 one shot per block; INT8 26.9 against 27.9
-// (one-byte slots let 10 one-shot blocks share an SM), so INT8 keeps one shot per block.
+// Throughput path: two shots per block with their messages paired in one slot (every precision,
+// unless the graph's launch override asks for one shot per block, or the shot is learned), or one
+// shot per block.  Measured on LP-1054 at 65536 shots: FP32 27.3 M/s in pairs against 26.4, INT16
+// 29.4 against 26.5, INT8 29.6 against 27.9.
 int plan_batch(const qldpc_graph *const *gs, int nprob, int32_t batch, int precision, bool learned, Plan &pl)
 {
     const qldpc_graph *g0 = gs[0];
     const int word = precision == QLDPC_FP32 ? 8 : 4;   // bytes of one paired slot
-    bool packed = !learned && ((precision == QLDPC_INT16 && g0->user_kernel != QLDPC_KERNEL_BATCH) ||
-                               (precision != QLDPC_INT16 && g0->user_kernel == QLDPC_KERNEL_PACKED));
+    bool packed = !learned && g0->user_kernel != QLDPC_KERNEL_BATCH;
     if (packed && g0->user_kernel != QLDPC_KERNEL_PACKED) {
         // by default only where two shots fit a block's shared memory (beside 1 KB of static shared
         // memory); a graph whose single shot just fits keeps one shot per block

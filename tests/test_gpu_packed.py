@@ -86,6 +86,19 @@ def test_packed_batch_sizes_and_block_shapes(q, precision):
         assert_oracle(run_packed(q, g, s[lo:hi], prior, 50, precision), h, s[lo:hi], prior, 50, precision)
     for threads in (64, 256, 512):
         assert_oracle(run_packed(q, g, s, prior, 50, precision, threads=threads), h, s, prior, 50, precision)
+    # the decisions-only layout (no a-posteriori LLRs requested) gives the same decisions
+    g.set_launch("packed")
+    try:
+        st = torch.from_numpy(np.ascontiguousarray(s, dtype=np.uint8)).cuda()
+        pt = torch.from_numpy(np.ascontiguousarray(prior, dtype=np.float32)).cuda()
+        err, iters, ok, _ = q.decode(g, st, pt, 50, 0.75, precision, True, want_post=False)
+        torch.cuda.synchronize()
+    finally:
+        g.set_launch("auto")
+    ref = oracle.msa(h.row_ptr, h.col_idx, h.m, h.n, s, prior, 50, 0.75, OPREC[precision], True, threads=16)
+    np.testing.assert_array_equal(err.cpu().numpy(), ref["err"])
+    np.testing.assert_array_equal(iters.cpu().numpy(), ref["iters"])
+    np.testing.assert_array_equal(ok.cpu().numpy(), ref["ok"])
 
 
 @pytest.mark.parametrize("precision", ["int16", "int8", "fp32"])
@@ -158,7 +171,12 @@ def test_packed_large_batch_sampled_against_oracle(q, precision):
     h = code.hz_csr
     g = q.Graph.from_csr(h)
     b = w.x_error_batch(code, 0.03, 65536, seed=2003)
-    err, iters, ok, post = run_packed(q, g, b.syndromes, b.prior, 50, precision)
+    g.set_launch("packed")
+    try:           # the benchmark's form: no a-posteriori LLRs requested (the decisions-only layout)
+        res = q.decode(g, torch.from_numpy(b.syndromes).cuda(), torch.from_numpy(b.prior).cuda(), 50, 0.75, precision)
+        err, iters, ok = (t.cpu().numpy() for t in res[:3])
+    finally:
+        g.set_launch("auto")
     idx = np.random.default_rng(3).choice(65536, 1500, replace=False)
     ref = oracle.msa(h.row_ptr, h.col_idx, h.m, h.n, b.syndromes[idx], b.prior, 50, 0.75, OPREC[precision], True,
                      threads=16)

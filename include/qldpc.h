@@ -174,10 +174,11 @@ enum {
 };
 
 /* Override the library's launch choice for this graph: the kernel, its threads per block (a
- * multiple of 32 in [32, 1024], 0 = automatic) and the resident blocks per SM used to size the
- * grid (0 = from occupancy).  QLDPC_KERNEL_AUTO takes no shape (both 0) and restores the default.
- * INVALID_ARG if out of range, UNSUPPORTED if the shape cannot run this graph or the residency is
- * not achievable.  Results never depend on the launch choice. */
+ * multiple of 32 in [32, 1024], at most 512 for QLDPC_KERNEL_PACKED; 0 = automatic) and the resident
+ * blocks per SM used to size the grid (0 = from occupancy).  QLDPC_KERNEL_AUTO takes no shape (both
+ * 0) and restores the default.  INVALID_ARG if out of range, UNSUPPORTED if the shape cannot run
+ * this graph (in any precision) or the residency is not achievable.  Results never depend on the
+ * launch choice. */
 QLDPC_API int qldpc_graph_set_launch(qldpc_graph *g, int32_t kernel, int32_t threads_per_block,
                                      int32_t blocks_per_sm);
 

@@ -7,6 +7,8 @@
 
 #include <cuda_runtime.h>
 
+#include "qldpc.h"
+
 namespace qldpc {
 
 // Tanner graph in the kernels' layout.  Messages of check i live in shared-memory "slots"
@@ -19,6 +21,8 @@ namespace qldpc {
 // flips.  An idle lane has its warp's degree and every edge on a scratch slot dc_max*m + b
 // (b < kScratch) in a bank its warp leaves free, so it runs its warp's path without divergence;
 // its prior is 0 and its scratch slots hold 0, so its decision never flips.
+constexpr int kMaxDegClasses = QLDPC_MAX_COL_DEGREE + 1;   // column degrees 0..16
+
 struct DeviceGraph {
     const uint32_t *vslot;   // [dv_max * nv] slot j*m + i of lane u's k-th edge
     const uint8_t *vdeg;     // [nv] column degree of lane u (idle: its warp's degree)
@@ -35,6 +39,14 @@ struct DeviceGraph {
     uint32_t m_magic;        // floor(slot / m) = umulhi(slot, m_magic) >> m_shift for every slot
     int32_t m_shift;
     int32_t dc_max, dv_max;  // largest row / column degree
+    // The same slot lists as 16-bit indices (nullptr when a slot index exceeds 65535), and the lanes'
+    // degree classes: lanes [cls_end[c-1], cls_end[c]) (cls_end[-1] = 0) all have degree cls_deg[c],
+    // c < ncls.  The two-shots-per-block kernel walks the classes with the degree known at compile
+    // time instead of reading vdeg per lane.
+    const uint16_t *vslot16;
+    int32_t ncls;
+    int32_t cls_end[kMaxDegClasses];
+    int32_t cls_deg[kMaxDegClasses];
 };
 
 // One decoding problem: a graph and the caller's buffers for one batch.

@@ -21,10 +21,15 @@
 // s_new), which leaves exactly the initial state of the new shot.
 #pragma once
 
+#include <type_traits>
+
 #include "msa_kernel.cuh"
 
 namespace qldpc {
 namespace kern {
+
+// A hint to bring the cache line holding p into L2 (generic address; no data is returned).
+__device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefetch.L2 [%0];" ::"l"(p)); }
 
 // ---------------------------------------------------------------------------------------------
 // Paired-lane helpers (lane 0 = bits 0..15, lane 1 = bits 16..31)
@@ -158,8 +163,9 @@ __device__ __forceinline__ void check_step_x2(int c, int M, int deg, uint32_t pw
 // 0 where the lane restarts from the prior (r taken as 0: Q = gamma, q = gamma).  Returns the new
 // (Q0, Q1); flips the lane's parity bit of every check of the variable whose decision changed.
 // ---------------------------------------------------------------------------------------------
-template <class P, int D>
-__device__ __forceinline__ int2 var_step_x2(int u, int NV, const CheckOf &ck, const uint32_t *__restrict__ vslot,
+// MASK = false: both lanes update (keep = all ones), the messages are used as loaded.
+template <class P, int D, bool MASK>
+__device__ __forceinline__ int2 var_step_x2(int u, int NV, const CheckOf &ck, const uint16_t *__restrict__ vslot,
                                             int32_t gamma, int2 Qold, uint32_t keep, uint32_t *__restrict__ slots,
                                             uint32_t *__restrict__ parity)
 {
@@ -168,9 +174,9 @@ __device__ __forceinline__ int2 var_step_x2(int u, int NV, const CheckOf &ck, co
     } else {
         uint32_t e[D], r[D];
 #pragma unroll
-        for (int k = 0; k < D; ++k) e[k] = __ldg(vslot + size_t(k) * NV + u);
+        for (int k = 0; k < D; ++k) e[k] = __ldg(vslot + k * NV + u);
 #pragma unroll
-        for (int k = 0; k < D; ++k) r[k] = slots[e[k]] & keep;
+        for (int k = 0; k < D; ++k) r[k] = MASK ? slots[e[k]] & keep : slots[e[k]];
         int32_t Q0 = gamma, Q1 = gamma;
 #pragma unroll
         for (int k = 0; k < D; ++k) {
@@ -237,8 +243,8 @@ __device__ __forceinline__ void check_step_f32x2(int c, int M, int deg, uint32_t
     }
 }
 
-template <int D>
-__device__ __forceinline__ float2 var_step_f32x2(int u, int NV, const CheckOf &ck, const uint32_t *__restrict__ vslot,
+template <int D, bool MASK>
+__device__ __forceinline__ float2 var_step_f32x2(int u, int NV, const CheckOf &ck, const uint16_t *__restrict__ vslot,
                                                  float gamma, float2 Qold, uint32_t act, float2 *__restrict__ slots,
                                                  uint32_t *__restrict__ parity)
 {
@@ -249,11 +255,12 @@ __device__ __forceinline__ float2 var_step_f32x2(int u, int NV, const CheckOf &c
         uint32_t e[D];
         float2 r[D];
 #pragma unroll
-        for (int k = 0; k < D; ++k) e[k] = __ldg(vslot + size_t(k) * NV + u);
+        for (int k = 0; k < D; ++k) e[k] = __ldg(vslot + k * NV + u);
 #pragma unroll
         for (int k = 0; k < D; ++k) {
             const float2 v = slots[e[k]];        // a lane that restarts takes r = +0: Q = q = gamma
-            r[k] = make_float2(__uint_as_float(__float_as_uint(v.x) & k0), __uint_as_float(__float_as_uint(v.y) & k1));
+            r[k] = MASK ? make_float2(__uint_as_float(__float_as_uint(v.x) & k0), __uint_as_float(__float_as_uint(v.y) & k1))
+                        : v;
         }
         float2 pre[D + 1];
         pre[0] = make_float2(gamma, gamma);
@@ -293,12 +300,12 @@ struct Pair16 {
     {
         check_step_x2<P, DC, UNIFORM>(c, M, deg, pw, slots, p.alpha_q);
     }
-    template <int D>
-    static __device__ __forceinline__ pair_t var(int u, int NV, const CheckOf &ck, const uint32_t *vslot, gam_t gamma,
+    template <int D, bool MASK>
+    static __device__ __forceinline__ pair_t var(int u, int NV, const CheckOf &ck, const uint16_t *vslot, gam_t gamma,
                                                  pair_t Qold, uint32_t act, word_t *slots, uint32_t *parity)
     {
         const uint32_t keep = ((act & 1u) ? 0x0000ffffu : 0u) | ((act & 2u) ? 0xffff0000u : 0u);
-        return var_step_x2<P, D>(u, NV, ck, vslot, gamma, Qold, keep, slots, parity);
+        return var_step_x2<P, D, MASK>(u, NV, ck, vslot, gamma, Qold, keep, slots, parity);
     }
 };
 
@@ -315,36 +322,19 @@ struct PairF32 {     // two FP32 lanes per 8-byte slot
     {
         check_step_f32x2<DC, UNIFORM>(c, M, deg, pw, slots, p.alpha);
     }
-    template <int D>
-    static __device__ __forceinline__ pair_t var(int u, int NV, const CheckOf &ck, const uint32_t *vslot, gam_t gamma,
+    template <int D, bool MASK>
+    static __device__ __forceinline__ pair_t var(int u, int NV, const CheckOf &ck, const uint16_t *vslot, gam_t gamma,
                                                  pair_t Qold, uint32_t act, word_t *slots, uint32_t *parity)
     {
-        return var_step_f32x2<D>(u, NV, ck, vslot, gamma, Qold, act, slots, parity);
+        return var_step_f32x2<D, MASK>(u, NV, ck, vslot, gamma, Qold, act, slots, parity);
     }
 };
 
-template <class PP, int DV>
-__device__ __forceinline__ typename PP::pair_t pair_var_dispatch(int deg, int u, int NV, const CheckOf &ck,
-                                                                 const uint32_t *vslot, typename PP::gam_t gamma,
-                                                                 typename PP::pair_t Qold, uint32_t act,
-                                                                 typename PP::word_t *slots, uint32_t *parity)
-{
-    switch (deg) {
-#define QLDPC_CASE(D)                                                                           \
-    case D:                                                                                     \
-        if constexpr (D <= DV) return PP::template var<D>(u, NV, ck, vslot, gamma, Qold, act, slots, parity); \
-        break;
-        QLDPC_DEG_CASES(QLDPC_CASE)
-#undef QLDPC_CASE
-    default: break;
-    }
-    return PP::both(gamma);
-}
-
 template <class PP, int DC, bool UNIFORM, int DV>
-__global__ void __launch_bounds__(kPackedMaxThreads, 1) msa_packed_kernel(const LaunchParams p)
+__global__ void __launch_bounds__(kPackedMaxThreads, 1) msa_packed_kernel(const __grid_constant__ LaunchParams p)
 {
     const Problem pr = blockIdx.y == 0 ? p.prob[0] : p.prob[1];
+    const DeviceGraph &G = p.prob[blockIdx.y].g;   // read in place (the class tables are indexed at run time)
     const int M = pr.g.m, N = pr.g.n, NV = pr.g.nv;
     const int T = blockDim.x, tid = threadIdx.x;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -396,26 +386,74 @@ __global__ void __launch_bounds__(kPackedMaxThreads, 1) msa_packed_kernel(const 
     // step (fresh: the next check step installs their syndrome bits).
     int shot[2] = {-1, -1}, k[2] = {0, 0}, okl[2] = {0, 0};
     uint32_t act = 0u, refill = 3u, out = 0u, fresh = 0u, ph = 0u;
+    // Shots are claimed one ahead: thread 0 holds each lane's next shot (pend), claimed when the
+    // lane took its current one, and prefetches that shot's syndrome into L2 at the next variable
+    // step, so neither the claim's round trip nor the syndrome's first read from DRAM stalls the
+    // block at a refill.  (A lane's queue is one shot deep, so the order in which shots finish
+    // changes, never a result.)
+    int pend[2] = {0, 0};
+    uint32_t pf = 0u;   // thread 0: lanes whose pending shot is still to be prefetched
+    if (tid == 0) {
+        pend[0] = atomicAdd(p.next_shot + blockIdx.y, 1);
+        pend[1] = atomicAdd(p.next_shot + blockIdx.y, 1);
+    }
     for (;;) {
         // ---- variable step: updates, outputs of finished shots, refills ----
-        for (int u = tid; u < NV; u += T) {
-            const pair_t Qo = Qs[u];
-            if (out) {
-                const uint32_t v = __ldg(pr.g.vperm + u);
-                if (v < uint32_t(N)) {
+        if (tid == 0 && pf) {
 #pragma unroll
-                    for (int l = 0; l < 2; ++l) {
-                        if (out & (1u << l)) {
-                            const gam_t q = l ? Qo.y : Qo.x;
-                            pr.err[size_t(shot[l]) * N + v] = PP::neg(q) ? 1 : 0;
-                            if (pr.post) pr.post[size_t(shot[l]) * N + v] = PP::post(q);
+            for (int l = 0; l < 2; ++l)
+                if ((pf & (1u << l)) && pend[l] < p.batch) {
+                    const uint8_t *sp = pr.syn + size_t(pend[l]) * M;
+                    for (int i = 0; i < M; i += 128) prefetch_l2(sp + i);
+                    prefetch_l2(sp + M - 1);
+                }
+            pf = 0u;
+        }
+        // Lanes come in classes of one degree (cls_end / cls_deg), walked in order along this
+        // thread's lanes u = tid, tid + T, ...; within a class the degree is a compile-time constant.
+        // Both lanes updating (no output, no refill, no restart mask) is the common case.
+        auto var_pass = [&](auto mask_tag) {
+            constexpr bool MASK = decltype(mask_tag)::value;
+            int u = tid;
+            for (int cl = 0; cl < pr.g.ncls && u < NV; ++cl) {
+                const int u1 = G.cls_end[cl];
+                auto run = [&](auto deg_tag) {
+                    constexpr int D = decltype(deg_tag)::value;
+                    for (; u < u1; u += T) {
+                        const pair_t Qo = Qs[u];
+                        if (MASK && out) {
+                            const uint32_t v = __ldg(pr.g.vperm + u);
+                            if (v < uint32_t(N)) {
+#pragma unroll
+                                for (int l = 0; l < 2; ++l) {
+                                    if (out & (1u << l)) {
+                                        const gam_t q = l ? Qo.y : Qo.x;
+                                        pr.err[size_t(shot[l]) * N + v] = PP::neg(q) ? 1 : 0;
+                                        if (pr.post) pr.post[size_t(shot[l]) * N + v] = PP::post(q);
+                                    }
+                                }
+                            }
                         }
+                        Qs[u] = PP::template var<D, MASK>(u, NV, ck, pr.g.vslot16, gam[u], Qo, act, slots, parity);
                     }
+                };
+                switch (G.cls_deg[cl]) {
+#define QLDPC_CASE(DD)                                                                          \
+    case DD:                                                                                    \
+        if constexpr (DD <= DV) run(std::integral_constant<int, DD>{});                         \
+        break;
+                    QLDPC_DEG_CASES(QLDPC_CASE)
+#undef QLDPC_CASE
+                default:   // a degree above the variant's bucket (the host never launches one)
+                    while (u < u1) u += T;
+                    break;
                 }
             }
-            Qs[u] = pair_var_dispatch<PP, DV>(__ldg(pr.g.vdeg + u), u, NV, ck, pr.g.vslot, gam[u], Qo, act, slots,
-                                              parity);
-        }
+        };
+        if (act == 3u)
+            var_pass(std::false_type{});
+        else
+            var_pass(std::true_type{});
         if (tid == 0) {
             s_any[ph] = 0u;                           // the word the next check step reduces into
 #pragma unroll
@@ -424,7 +462,11 @@ __global__ void __launch_bounds__(kPackedMaxThreads, 1) msa_packed_kernel(const 
                     pr.iters[shot[l]] = k[l];
                     pr.ok[shot[l]] = okl[l] ? 1 : 0;
                 }
-                if (refill & (1u << l)) s_claim[l] = atomicAdd(p.next_shot + blockIdx.y, 1);
+                if (refill & (1u << l)) {
+                    s_claim[l] = pend[l];
+                    pend[l] = atomicAdd(p.next_shot + blockIdx.y, 1);
+                    pf |= 1u << l;
+                }
             }
         }
         __syncthreads();
@@ -445,12 +487,22 @@ __global__ void __launch_bounds__(kPackedMaxThreads, 1) msa_packed_kernel(const 
         // ---- check step and stop test of both lanes ----
         const uint8_t *s0 = (fresh & 1u) ? pr.syn + size_t(shot[0]) * M : nullptr;
         const uint8_t *s1 = (fresh & 2u) ? pr.syn + size_t(shot[1]) * M : nullptr;
+        // a new shot's syndrome bits of this thread's checks (check tid + i*T at bit i, i < 32), read
+        // up front so that their loads overlap
+        uint32_t sb0 = 0u, sb1 = 0u;
+        if (fresh) {
+#pragma unroll 4
+            for (int c = tid, i = 0; c < M && i < 32; c += T, ++i) {
+                if (s0) sb0 |= (uint32_t(s0[c]) & 1u) << i;
+                if (s1) sb1 |= (uint32_t(s1[c]) & 1u) << i;
+            }
+        }
         uint32_t unsat = 0u;
-        for (int c = tid; c < M; c += T) {
+        for (int c = tid, i = 0; c < M; c += T, ++i) {
             uint32_t pw = parity[c];
             if (fresh) {   // the new shots' syndrome bits replace the old ones (bit 0 and bit 15 / 16 and 31)
-                if (s0) pw ^= (((pw >> 15) ^ uint32_t(s0[c])) & 1u) * 0x00008001u;
-                if (s1) pw ^= (((pw >> 31) ^ uint32_t(s1[c])) & 1u) * 0x80010000u;
+                if (s0) pw ^= (((pw >> 15) ^ (i < 32 ? sb0 >> i : uint32_t(s0[c]))) & 1u) * 0x00008001u;
+                if (s1) pw ^= (((pw >> 31) ^ (i < 32 ? sb1 >> i : uint32_t(s1[c]))) & 1u) * 0x80010000u;
                 parity[c] = pw;
             }
             unsat |= pw;

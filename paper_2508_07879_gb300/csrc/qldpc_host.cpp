@@ -68,13 +68,14 @@ namespace {
 // ------------------------------------------------------------------------------------------
 constexpr int kBanks = 32;
 
-// Wavefronts of one warp access: the most distinct words that fall into one bank.
-int warp_wavefronts(const uint32_t *addr, int count)
+// Wavefronts of one warp (or half-warp) access over `banks` banks of one slot word each: the most
+// distinct words that fall into one bank.
+int warp_wavefronts(const uint32_t *addr, int count, int banks = kBanks)
 {
     int dist[kBanks] = {0}, worst = count > 0 ? 1 : 0;
     uint32_t seen[kBanks][kBanks];
     for (int l = 0; l < count; ++l) {
-        const int b = int(addr[l] % kBanks);
+        const int b = int(addr[l] % uint32_t(banks));
         bool dup = false;
         for (int i = 0; i < dist[b]; ++i) dup = dup || seen[b][i] == addr[l];
         if (!dup) seen[b][dist[b]++] = addr[l];
@@ -165,6 +166,80 @@ std::vector<int32_t> pack_lanes(const std::vector<uint32_t> &order, const std::v
     return lanes;
 }
 
+// 8-byte slot words (the paired FP32 messages of the two-shots-per-block kernel) are served a
+// half-warp at a time over 16 bank pairs, so there the k-th slots of each half should be distinct
+// modulo 16 words.  A warp whose 32 slots are distinct modulo 32 can still put two slots 16 words
+// apart in one half.  Which lanes form a half does not change the 4-byte banks (the warp's set of
+// slots is the same), so each warp's lanes are reordered by pairwise swaps between its halves while
+// a swap lowers the 8-byte wavefronts.
+// The 8-byte wavefronts of one warp's k-th slots, idle lanes included: a half with idle lanes
+// costs one more unless some bank is free in the whole warp (their scratch slot's 4-byte bank) and
+// free in that half modulo 16.
+int halves_cost(const int32_t *w, const std::vector<uint32_t> &eaddr, const std::vector<int32_t> &cdeg, int dv, int D)
+{
+    int c = 0;
+    uint32_t a[kBanks];
+    for (int k = 0; k < D; ++k) {
+        bool used[kBanks] = {false};
+        for (int l = 0; l < kBanks; ++l)
+            if (w[l] >= 0 && k < cdeg[size_t(w[l])]) used[eaddr[size_t(w[l]) * dv + k] % kBanks] = true;
+        for (int h = 0; h < 2; ++h) {
+            int cnt = 0;
+            bool idle = false, half_used[kBanks / 2] = {false};
+            for (int l = h * kBanks / 2; l < (h + 1) * kBanks / 2; ++l) {
+                if (w[l] >= 0 && k < cdeg[size_t(w[l])]) {
+                    a[cnt] = eaddr[size_t(w[l]) * dv + k];
+                    half_used[a[cnt] % (kBanks / 2)] = true;
+                    ++cnt;
+                } else if (w[l] < 0) {
+                    idle = true;
+                }
+            }
+            int wf = warp_wavefronts(a, cnt, kBanks / 2);
+            if (idle) {
+                bool free_bank = false;
+                for (int r = 0; r < kBanks && !free_bank; ++r) free_bank = !used[r] && !half_used[r % (kBanks / 2)];
+                wf = free_bank ? std::max(wf, 1) : wf + 1;
+            }
+            c += wf;
+        }
+    }
+    return c;
+}
+
+void split_halves(std::vector<int32_t> &lanes, const std::vector<uint32_t> &eaddr, const std::vector<int32_t> &cdeg,
+                  int dv)
+{
+    for (size_t w0 = 0; w0 + kBanks <= lanes.size(); w0 += kBanks) {
+        int32_t *w = lanes.data() + w0;
+        int D = -1;
+        bool mixed = false;   // a warp that straddles two degree classes keeps its order (degrees stay sorted)
+        for (int l = 0; l < kBanks; ++l)
+            if (w[l] >= 0) {
+                const int d = cdeg[size_t(w[l])];
+                mixed = mixed || (D >= 0 && d != D);
+                D = std::max(D, d);
+            }
+        if (mixed || D <= 0) continue;
+        int cost = halves_cost(w, eaddr, cdeg, dv, D);
+        for (bool improved = true; improved && cost > 2 * D;) {
+            improved = false;
+            for (int a = 0; a < kBanks / 2; ++a)
+                for (int b = kBanks / 2; b < kBanks; ++b) {
+                    if (w[a] < 0 && w[b] < 0) continue;
+                    std::swap(w[a], w[b]);
+                    const int c = halves_cost(w, eaddr, cdeg, dv, D);
+                    if (c < cost) {
+                        cost = c;
+                        improved = true;
+                    } else {
+                        std::swap(w[a], w[b]);
+                    }
+                }
+        }
+    }
+}
+
 // The lanes with the lowest cost among the plain degree order and four packings.  A packing may
 // add at most an eighth more lanes (plus one warp), so that it never costs a graph its fit in shared
 // memory by more than the Q and gamma words of those lanes.
@@ -203,6 +278,8 @@ struct HostLayout {
     std::vector<uint32_t> layer_chk;// [m] checks ordered by (layer, index)
     int32_t max_layer = 0;
     int32_t nv = 0;               // variable lanes (n + idle lanes)
+    std::vector<uint16_t> vslot16;// vslot as 16-bit indices (empty when a slot index exceeds 65535)
+    std::vector<int32_t> cls_end, cls_deg;   // runs of equal lane degree
     uint32_t m_magic = 0;         // slot / m = umulhi(slot, m_magic) >> m_shift
     int32_t m_shift = 0;
 };
@@ -253,7 +330,8 @@ int validate_and_layout(const int32_t *row_ptr, const int32_t *col_idx, int32_t 
                 eaddr[size_t(v) * dv1 + size_t(fill[size_t(v)]++)] = uint32_t(e - row_ptr[i]) * uint32_t(m) + uint32_t(i);
             }
     }
-    const std::vector<int32_t> lanes = choose_lanes(order, eaddr, cdeg, dv1);
+    std::vector<int32_t> lanes = choose_lanes(order, eaddr, cdeg, dv1);
+    if (lanes.size() % kBanks == 0) split_halves(lanes, eaddr, cdeg, dv1);
     const size_t nv = lanes.size();
     out.nv = int32_t(nv);
     out.vorder.assign(nv, uint32_t(n));
@@ -266,7 +344,8 @@ int validate_and_layout(const int32_t *row_ptr, const int32_t *col_idx, int32_t 
     out.vdeg.assign(nv, 0);
     out.vslot.assign(size_t(dv1) * nv, 0u);
     // Idle lanes: their warp's degree, every edge on a scratch slot dc_max*m + b in a bank the
-    // warp's variables leave free for that edge.
+    // warp's variables leave free for that edge (4-byte words), and where possible one whose bank
+    // pair the variables of the lane's half-warp leave free (8-byte words).
     const uint32_t S_words = uint32_t(dc_max) * uint32_t(m);
     for (size_t w0 = 0; w0 < nv; w0 += kBanks) {
         const size_t w1 = std::min(nv, w0 + kBanks);
@@ -280,14 +359,24 @@ int validate_and_layout(const int32_t *row_ptr, const int32_t *col_idx, int32_t 
         }
         if (!any_idle) continue;
         for (int k = 0; k < D; ++k) {
-            bool used[kBanks] = {false};
+            bool used[kBanks] = {false}, used_half[2][kBanks / 2] = {{false}};
             for (size_t l = w0; l < w1; ++l)
-                if (lanes[l] >= 0 && k < cdeg[size_t(lanes[l])]) used[eaddr[size_t(lanes[l]) * dv1 + k] % kBanks] = true;
-            int b = 0;
-            while (b < kBanks - 1 && used[b]) ++b;
-            const uint32_t sw = (uint32_t(b) + kBanks - S_words % kBanks) % kBanks;   // (S + sw) % 32 == b
-            for (size_t l = w0; l < w1; ++l)
-                if (lanes[l] < 0) out.vslot[size_t(k) * nv + l] = S_words + sw;
+                if (lanes[l] >= 0 && k < cdeg[size_t(lanes[l])]) {
+                    const uint32_t a = eaddr[size_t(lanes[l]) * dv1 + k];
+                    used[a % kBanks] = true;
+                    used_half[(l - w0) / (kBanks / 2)][a % (kBanks / 2)] = true;
+                }
+            for (int h = 0; h < 2; ++h) {
+                int b = -1;
+                for (int r = 0; r < kBanks && b < 0; ++r)
+                    if (!used[r] && !used_half[h][r % (kBanks / 2)]) b = r;
+                for (int r = 0; r < kBanks && b < 0; ++r)
+                    if (!used[r]) b = r;
+                if (b < 0) b = 0;
+                const uint32_t sw = (uint32_t(b) + kBanks - S_words % kBanks) % kBanks;   // (S + sw) % 32 == b
+                for (size_t l = w0 + size_t(h) * (kBanks / 2); l < std::min(w1, w0 + size_t(h + 1) * (kBanks / 2)); ++l)
+                    if (lanes[l] < 0) out.vslot[size_t(k) * nv + l] = S_words + sw;
+            }
         }
         for (size_t l = w0; l < w1; ++l)
             if (lanes[l] < 0) out.vdeg[l] = uint8_t(D);
@@ -312,6 +401,15 @@ int validate_and_layout(const int32_t *row_ptr, const int32_t *col_idx, int32_t 
             out.ecol[sl] = uint32_t(col_idx[e]);
         }
     }
+    if (S + size_t(kScratch) <= 65536) out.vslot16.assign(out.vslot.begin(), out.vslot.end());
+    for (size_t u = 0; u < nv; ++u) {
+        if (out.cls_deg.empty() || out.cls_deg.back() != int32_t(out.vdeg[u])) {
+            out.cls_end.push_back(int32_t(u));
+            out.cls_deg.push_back(int32_t(out.vdeg[u]));
+        }
+        out.cls_end.back() = int32_t(u) + 1;
+    }
+    if (out.cls_end.size() > size_t(kMaxDegClasses)) return QLDPC_ERR_UNSUPPORTED;   // degrees are sorted
     // floor(slot / m) for every slot (scratch included) as a multiply-high and a shift: the
     // smallest shift whose rounded-up reciprocal fits 32 bits and divides every slot exactly.
     {
@@ -528,6 +626,11 @@ int plan_batch(const qldpc_graph *const *gs, int nprob, int32_t batch, int preci
     const qldpc_graph *g0 = gs[0];
     const int word = precision == QLDPC_FP32 ? 8 : 4;   // bytes of one paired slot
     bool packed = !learned && g0->user_kernel != QLDPC_KERNEL_BATCH;
+    for (int i = 0; i < nprob && packed; ++i)
+        if (!gs[i]->dg.vslot16) {   // 16-bit slot indices: any graph whose pair of shots fits on chip
+            if (g0->user_kernel == QLDPC_KERNEL_PACKED) return QLDPC_ERR_UNSUPPORTED;
+            packed = false;
+        }
     if (packed && g0->user_kernel != QLDPC_KERNEL_PACKED) {
         // by default only where two shots fit a block's shared memory (beside 1 KB of static shared
         // memory); a graph whose single shot just fits keeps one shot per block
@@ -808,16 +911,17 @@ int qldpc_graph_create(const int32_t *row_ptr, const int32_t *col_idx, int32_t m
     }
 
     // one device block: vslot | vdeg | rdeg | vperm | eslot | slot_edge | ecol | layer_ptr | layer_chk |
-    // shot counters
-    constexpr int kArrays = 10;
+    // shot counters | vslot16
+    constexpr int kArrays = 11;
     const size_t sizes[kArrays] = {hl.vslot.size() * sizeof(uint32_t), size_t(hl.nv), size_t(m),
                                    size_t(hl.nv) * sizeof(uint32_t), hl.eslot.size() * sizeof(uint32_t),
                                    hl.slot_edge.size() * sizeof(int32_t), hl.ecol.size() * sizeof(uint32_t),
                                    hl.layer_ptr.size() * sizeof(int32_t), hl.layer_chk.size() * sizeof(uint32_t),
-                                   size_t(kShotCounterSlots) * 2 * sizeof(int32_t)};
+                                   size_t(kShotCounterSlots) * 2 * sizeof(int32_t),
+                                   hl.vslot16.size() * sizeof(uint16_t)};
     const void *srcs[kArrays] = {hl.vslot.data(), hl.vdeg.data(), hl.rdeg.data(), hl.vorder.data(),
                                  hl.eslot.data(), hl.slot_edge.data(), hl.ecol.data(),
-                                 hl.layer_ptr.data(), hl.layer_chk.data(), nullptr};
+                                 hl.layer_ptr.data(), hl.layer_chk.data(), nullptr, hl.vslot16.data()};
     size_t offs[kArrays], total = 0;
     for (int i = 0; i < kArrays; ++i) {
         offs[i] = total;
@@ -856,6 +960,12 @@ int qldpc_graph_create(const int32_t *row_ptr, const int32_t *col_idx, int32_t m
     g->dg.m_shift = hl.m_shift;
     g->dg.dc_max = hl.dc_max;
     g->dg.dv_max = hl.dv_max;
+    g->dg.vslot16 = hl.vslot16.empty() ? nullptr : reinterpret_cast<const uint16_t *>(b + offs[10]);
+    g->dg.ncls = int32_t(hl.cls_end.size());
+    for (size_t c = 0; c < hl.cls_end.size(); ++c) {
+        g->dg.cls_end[c] = hl.cls_end[c];
+        g->dg.cls_deg[c] = hl.cls_deg[c];
+    }
     *out = g;
     return QLDPC_OK;
 }

@@ -7,7 +7,7 @@ prints what it builds; this file checks it against the matrix:
     in free banks and at their warp's degree;
   * the magic number: floor(slot / m) exact for every slot;
   * bank packing: no conflicts in the variable step for the lift-31 code, fewer than the plain
-    order for the others;
+    order for the others; each warp's halves chosen for 8-byte slots;
   * layers: checks of a layer share no variable, and each check sits one above the highest
     earlier check it shares a variable with.
 """
@@ -144,6 +144,34 @@ def test_bank_packing(probe):
         for k in range(max(deg[v] for v in lanes)):
             plain += wavefronts([slots[v][k] for v in lanes if k < deg[v]])
     assert plain > 1.5 * got
+
+
+def half_wavefronts(vslot, vdeg, nv):
+    """Wavefronts of the variable step with 8-byte slot words (the paired FP32 messages): a half-warp
+    per wavefront over 16 bank pairs; idle lanes included (their scratch slots are accessed too)."""
+    total = 0
+    for w0 in range(0, nv, 32):
+        for k in range(int(vdeg[w0:w0 + 32].max())):
+            for h0 in (w0, w0 + 16):
+                words = [int(vslot[k * nv + u]) for u in range(h0, min(nv, h0 + 16)) if k < vdeg[u]]
+                if words:
+                    banks = {}
+                    for a in words:
+                        banks.setdefault(a % 16, set()).add(a)
+                    total += max(len(x) for x in banks.values())
+    return total
+
+
+def test_half_warp_split_for_8_byte_slots(probe):
+    """Each warp's lanes are split into halves that suit 8-byte slots without changing the warp's
+    4-byte banks: LP-1054's variable step takes 298 half-warp wavefronts (the 4-byte packing in its
+    own lane order: 366; conflict-free would be 240), and the 4-byte accesses stay conflict-free."""
+    h = w.lp_code(1054).hz_csr
+    d = layout(probe, h)
+    nv = int(d["dims"][2])
+    assert half_wavefronts(d["vslot"], d["vdeg"], nv) <= 300
+    assert vn_wavefronts(d["vslot"], d["vdeg"], nv, np.ones(nv, dtype=bool)) == \
+        sum(int(d["vdeg"][w0:w0 + 32].max()) for w0 in range(0, nv, 32))   # idle lanes included
 
 
 @pytest.mark.parametrize("name", list(CODES))

@@ -160,11 +160,38 @@ struct CheckOf {
     }
 };
 
+// The two smallest of a[LO .. LO+N), with multiplicity, as a balanced tree: the two smallest of
+// {x1 <= x2} and {y1 <= y2} together are min(x1, y1) and min(max(x1, y1), x2, y2).  Every step is
+// an exact minimum or maximum, so any grouping gives the same pair; the tree only shortens the
+// chain of dependent operations (depth 5 for eight magnitudes against 7 for a running pair).
+// Ops supplies mn, mx and mn3 (three-input minimum) on magnitudes of type M.
+template <class Ops, int LO, int N, class M>
+__device__ __forceinline__ void min2_tree(const M *a, M &m1, M &m2)
+{
+    static_assert(N >= 2, "two magnitudes at least");
+    if constexpr (N == 2) {
+        m1 = Ops::mn(a[LO], a[LO + 1]);
+        m2 = Ops::mx(a[LO], a[LO + 1]);
+    } else if constexpr (N == 3) {
+        const M lo = Ops::mn(a[LO + 1], a[LO + 2]), hi = Ops::mx(a[LO + 1], a[LO + 2]);
+        m1 = Ops::mn(a[LO], lo);
+        m2 = Ops::mn(Ops::mx(a[LO], lo), hi);
+    } else {
+        constexpr int H = (N / 2) % 2 == 0 || N == 5 ? N / 2 : N / 2 + 1;   // halves of >= 2
+        M x1, x2, y1, y2;
+        min2_tree<Ops, LO, H>(a, x1, x2);
+        min2_tree<Ops, LO + H, N - H>(a, y1, y2);
+        m1 = Ops::mn(x1, y1);
+        m2 = Ops::mn3(Ops::mx(x1, y1), x2, y2);
+    }
+}
+
 // The two smallest magnitudes of a row, with multiplicity (m2 = m1 when the minimum is shared).
 // Rows of exact degree take the magnitudes in pairs (lo, hi): the second smallest of {m1 <= m2}
 // and {lo <= hi} is min(max(m1, lo), m2, hi), one three-input minimum (an odd degree starts from
 // m1 = the first magnitude, m2 = +inf); rows of varying degree stream them one at a time.  Either
-// way the result is the exact pair of minima.
+// way the result is the exact pair of minima.  (A balanced tree, min2_tree, shortens the chain but
+// keeps every magnitude live at once: in the FP32 kernels that cost a resident block per SM.)
 template <class P, int DC, bool UNIFORM>
 __device__ __forceinline__ void two_smallest(const typename P::acc_t *q, int deg, typename P::mag_t &m1,
                                              typename P::mag_t &m2)

@@ -90,6 +90,13 @@ __device__ __forceinline__ uint32_t pack_sat16x2(int32_t x0, int32_t x1)
     return d;
 }
 
+// Lane-wise minima and maxima of 16-bit magnitudes, the operations min2_tree takes.
+struct U16x2Ops {
+    static __device__ __forceinline__ uint32_t mn(uint32_t a, uint32_t b) { return min_u16x2(a, b); }
+    static __device__ __forceinline__ uint32_t mx(uint32_t a, uint32_t b) { return max_u16x2(a, b); }
+    static __device__ __forceinline__ uint32_t mn3(uint32_t a, uint32_t b, uint32_t c) { return min_u16x2(min_u16x2(a, b), c); }
+};
+
 // The message clamp of a fixed-point policy on a packed pair: [-LIM, LIM] in each lane.
 template <class P>
 __device__ __forceinline__ uint32_t clamp_pair(int32_t x0, int32_t x1)
@@ -127,13 +134,17 @@ __device__ __forceinline__ void check_step_x2(int c, int M, int deg, uint32_t pw
             a[j] = abs16x2(q[j]);
         }
     }
-    // the two smallest magnitudes of each lane, with multiplicity
+    // the two smallest magnitudes of each lane, with multiplicity (rows of exact degree: a tree)
     uint32_t m1 = 0x7fff7fffu, m2 = 0x7fff7fffu;
+    if constexpr (UNIFORM && DC >= 2) {
+        min2_tree<U16x2Ops, 0, DC>(a, m1, m2);
+    } else {
 #pragma unroll
-    for (int j = 0; j < DC; ++j) {
-        if (UNIFORM || j < deg) {
-            m2 = min_u16x2(m2, max_u16x2(m1, a[j]));
-            m1 = min_u16x2(m1, a[j]);
+        for (int j = 0; j < DC; ++j) {
+            if (UNIFORM || j < deg) {
+                m2 = min_u16x2(m2, max_u16x2(m1, a[j]));
+                m1 = min_u16x2(m1, a[j]);
+            }
         }
     }
     // (-1)^{s_m} prod of all signs, per lane, replicated over the lane

@@ -728,6 +728,34 @@ def measure_latency(qldpc, graph, code, args):
            "code": "LP-1054 H_Z", "p": LAT_P, "shots": shots, "max_iter": MAX_ITER,
            "launch_path": {"path": "qldpc_decode_host through ctypes, page-locked buffers read/written by the "
                                    "kernel, host clock, B=1", **lat}}
+    # device-only time of the same single-shot launches: device-resident buffers, CUDA events
+    # recorded on the launch stream around each launch (no host clock, copies or synchronize)
+    import ctypes
+    dev = torch.device("cuda")
+    syn_d = torch.from_numpy(b.syndromes).to(dev)
+    pri_d = torch.from_numpy(prior).to(dev)
+    err_d = torch.empty((1, h.n), dtype=torch.uint8, device=dev)
+    it_d = torch.empty(1, dtype=torch.int32, device=dev)
+    ok_d = torch.empty(1, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    sp = ctypes.c_void_p(stream.cuda_stream)
+    dev_lat = {}
+    for prec in ("fp32", "int16", "int8"):
+        pc = qldpc.PRECISIONS[prec]
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(shots + warm)]
+        for i in range(shots + warm):
+            ev[i][0].record(stream)
+            rc = qldpc.qldpc_decode_ex(graph.handle, syn_d.data_ptr() + i * h.m, 1, pri_d.data_ptr(), MAX_ITER, ALPHA,
+                                       err_d.data_ptr(), it_d.data_ptr(), ok_d.data_ptr(), None, pc, 0, sp)
+            ev[i][1].record(stream)
+            if rc:
+                raise qldpc.QldpcError(rc, "qldpc_decode_ex")
+        torch.cuda.synchronize()
+        x = np.array([e0.elapsed_time(e1) * 1e3 for e0, e1 in ev[warm:]])
+        dev_lat[prec] = {"p50_us": float(np.percentile(x, 50)), "p99_us": float(np.percentile(x, 99)),
+                         "p999_us": float(np.percentile(x, 99.9)), "mean_us": float(x.mean())}
+    out["device_path"] = {"path": "qldpc_decode_ex, device-resident buffers, CUDA events around each B=1 launch",
+                          **dev_lat}
     # the same shots through the persistent server: requests 50 us apart, latency = result seen by
     # the host - scheduled arrival (host steady clock inside the C ABI)
     def served(layered):

@@ -44,6 +44,7 @@ struct DeviceGraph {
     // c < ncls.  The two-shots-per-block kernel walks the classes with the degree known at compile
     // time instead of reading vdeg per lane.
     const uint16_t *vslot16;
+    const uint32_t *vlane;   // [n] lane of each variable (the inverse of vperm on the real lanes)
     int32_t ncls;
     int32_t cls_end[kMaxDegClasses];
     int32_t cls_deg[kMaxDegClasses];

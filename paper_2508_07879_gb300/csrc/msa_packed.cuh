@@ -31,6 +31,10 @@ namespace kern {
 // A hint to bring the cache line holding p into L2 (generic address; no data is returned).
 __device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefetch.L2 [%0];" ::"l"(p)); }
 
+// An output store (decisions, a-posteriori LLRs): written once, read by the caller after the launch.
+template <class T>
+__device__ __forceinline__ void store_out(T *p, T v) { *p = v; }
+
 // ---------------------------------------------------------------------------------------------
 // Paired-lane helpers (lane 0 = bits 0..15, lane 1 = bits 16..31)
 // ---------------------------------------------------------------------------------------------
@@ -420,9 +424,27 @@ __global__ void __launch_bounds__(kPackedMaxThreads, 1) msa_packed_kernel(const 
                 }
             pf = 0u;
         }
+        // Finished shots are written out in variable order (consecutive threads, consecutive
+        // variables: each warp store covers 32 adjacent bytes of e_hat), before the variable step
+        // below overwrites Q.
+        if (out) {
+#pragma unroll 1
+            for (int v = tid; v < N; v += T) {
+                const pair_t Qo = Qs[__ldg(pr.g.vlane + v)];
+#pragma unroll
+                for (int l = 0; l < 2; ++l) {
+                    if (out & (1u << l)) {
+                        const gam_t q = l ? Qo.y : Qo.x;
+                        store_out(pr.err + size_t(shot[l]) * N + v, uint8_t(PP::neg(q) ? 1 : 0));
+                        if (pr.post) store_out(pr.post + size_t(shot[l]) * N + v, PP::post(q));
+                    }
+                }
+            }
+            __syncthreads();
+        }
         // Lanes come in classes of one degree (cls_end / cls_deg), walked in order along this
         // thread's lanes u = tid, tid + T, ...; within a class the degree is a compile-time constant.
-        // Both lanes updating (no output, no refill, no restart mask) is the common case.
+        // Both lanes updating (no refill, no restart mask) is the common case.
         auto var_pass = [&](auto mask_tag) {
             constexpr bool MASK = decltype(mask_tag)::value;
             int u = tid;
@@ -430,23 +452,9 @@ __global__ void __launch_bounds__(kPackedMaxThreads, 1) msa_packed_kernel(const 
                 const int u1 = G.cls_end[cl];
                 auto run = [&](auto deg_tag) {
                     constexpr int D = decltype(deg_tag)::value;
-                    for (; u < u1; u += T) {
-                        const pair_t Qo = Qs[u];
-                        if (MASK && out) {
-                            const uint32_t v = __ldg(pr.g.vperm + u);
-                            if (v < uint32_t(N)) {
-#pragma unroll
-                                for (int l = 0; l < 2; ++l) {
-                                    if (out & (1u << l)) {
-                                        const gam_t q = l ? Qo.y : Qo.x;
-                                        pr.err[size_t(shot[l]) * N + v] = PP::neg(q) ? 1 : 0;
-                                        if (pr.post) pr.post[size_t(shot[l]) * N + v] = PP::post(q);
-                                    }
-                                }
-                            }
-                        }
-                        Qs[u] = PP::template var<D, MASK>(u, NV, ck, pr.g.vslot16, gam[u], Qo, act, slots, parity);
-                    }
+#pragma unroll 1
+                    for (; u < u1; u += T)
+                        Qs[u] = PP::template var<D, MASK>(u, NV, ck, pr.g.vslot16, gam[u], Qs[u], act, slots, parity);
                 };
                 switch (G.cls_deg[cl]) {
 #define QLDPC_CASE(DD)                                                                          \

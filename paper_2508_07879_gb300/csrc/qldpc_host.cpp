@@ -271,6 +271,7 @@ struct HostLayout {
     std::vector<uint8_t> rdeg, vdeg;
     std::vector<uint32_t> vslot;   // [dv_max * nv]
     std::vector<uint32_t> vorder;  // [nv] caller's variable of each lane, n for an idle lane
+    std::vector<uint32_t> vlane;   // [n] lane of each variable
     std::vector<uint32_t> eslot;   // [nnz] slot j*m + i of CSR edge e
     std::vector<int32_t> slot_edge;// [dc_max * m] CSR edge of each slot, -1 for padding
     std::vector<uint32_t> ecol;    // [dc_max * m] caller's variable of each slot, ~0 for padding
@@ -341,6 +342,7 @@ int validate_and_layout(const int32_t *row_ptr, const int32_t *col_idx, int32_t 
             out.vorder[u] = uint32_t(lanes[u]);
             internal[size_t(lanes[u])] = uint32_t(u);
         }
+    out.vlane = internal;
     out.vdeg.assign(nv, 0);
     out.vslot.assign(size_t(dv1) * nv, 0u);
     // Idle lanes: their warp's degree, every edge on a scratch slot dc_max*m + b in a bank the
@@ -911,17 +913,18 @@ int qldpc_graph_create(const int32_t *row_ptr, const int32_t *col_idx, int32_t m
     }
 
     // one device block: vslot | vdeg | rdeg | vperm | eslot | slot_edge | ecol | layer_ptr | layer_chk |
-    // shot counters | vslot16
-    constexpr int kArrays = 11;
+    // shot counters | vslot16 | vlane
+    constexpr int kArrays = 12;
     const size_t sizes[kArrays] = {hl.vslot.size() * sizeof(uint32_t), size_t(hl.nv), size_t(m),
                                    size_t(hl.nv) * sizeof(uint32_t), hl.eslot.size() * sizeof(uint32_t),
                                    hl.slot_edge.size() * sizeof(int32_t), hl.ecol.size() * sizeof(uint32_t),
                                    hl.layer_ptr.size() * sizeof(int32_t), hl.layer_chk.size() * sizeof(uint32_t),
                                    size_t(kShotCounterSlots) * 2 * sizeof(int32_t),
-                                   hl.vslot16.size() * sizeof(uint16_t)};
+                                   hl.vslot16.size() * sizeof(uint16_t), hl.vlane.size() * sizeof(uint32_t)};
     const void *srcs[kArrays] = {hl.vslot.data(), hl.vdeg.data(), hl.rdeg.data(), hl.vorder.data(),
                                  hl.eslot.data(), hl.slot_edge.data(), hl.ecol.data(),
-                                 hl.layer_ptr.data(), hl.layer_chk.data(), nullptr, hl.vslot16.data()};
+                                 hl.layer_ptr.data(), hl.layer_chk.data(), nullptr, hl.vslot16.data(),
+                                 hl.vlane.data()};
     size_t offs[kArrays], total = 0;
     for (int i = 0; i < kArrays; ++i) {
         offs[i] = total;
@@ -961,6 +964,7 @@ int qldpc_graph_create(const int32_t *row_ptr, const int32_t *col_idx, int32_t m
     g->dg.dc_max = hl.dc_max;
     g->dg.dv_max = hl.dv_max;
     g->dg.vslot16 = hl.vslot16.empty() ? nullptr : reinterpret_cast<const uint16_t *>(b + offs[10]);
+    g->dg.vlane = reinterpret_cast<const uint32_t *>(b + offs[11]);
     g->dg.ncls = int32_t(hl.cls_end.size());
     for (size_t c = 0; c < hl.cls_end.size(); ++c) {
         g->dg.cls_end[c] = hl.cls_end[c];

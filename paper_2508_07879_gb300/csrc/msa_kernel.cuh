@@ -34,6 +34,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 
 #include <cuda_runtime.h>
 
@@ -227,6 +228,59 @@ __device__ __forceinline__ void two_smallest(const typename P::acc_t *q, int deg
     }
 }
 
+// min(|a|, |b|) carrying the sign sign(a) xor sign(b) (sm_86 and later)
+__device__ __forceinline__ float min_xorsign_abs(float a, float b)
+{
+    float d;
+    asm("min.xorsign.abs.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+    return d;
+}
+
+// The two smallest FP32 magnitudes of a row of exactly DC messages, two at a time, with the parity of
+// the signs riding on the smallest: |m1s| = min |q|, the sign bit of m1s = xor of every sign bit; m2
+// the second smallest magnitude (with multiplicity).  The same pairs of minima and maxima as
+// two_smallest, so the same values.
+template <int DC>
+__device__ __forceinline__ void two_smallest_signed(const float *q, float &m1s, float &m2)
+{
+    constexpr int j0 = DC % 2 == 0 ? 2 : 1;
+    if constexpr (DC % 2 == 0) {
+        m1s = min_xorsign_abs(q[0], q[1]);
+        m2 = fmaxf(fabsf(q[0]), fabsf(q[1]));
+    } else {
+        m1s = q[0];
+        m2 = F32::mag_init();
+    }
+#pragma unroll
+    for (int j = j0; j < DC; j += 2) {
+        const float lo = min_xorsign_abs(q[j], q[j + 1]);
+        const float hi = fmaxf(fabsf(q[j]), fabsf(q[j + 1]));
+        m2 = F32::mn3(fmaxf(fabsf(m1s), fabsf(lo)), m2, hi);
+        m1s = min_xorsign_abs(m1s, lo);
+    }
+}
+
+// The check update's reductions of one row: its two smallest magnitudes m1 <= m2 (with multiplicity)
+// and the parity of its messages' sign bits (bit 31 of sx).  FP32 rows of exact degree take the parity
+// with the smallest magnitude (one instruction per pair of messages fewer); the others xor the signs.
+template <class P, int DC, bool UNIFORM>
+__device__ __forceinline__ void row_minima(const typename P::acc_t *q, int deg, typename P::mag_t &m1,
+                                           typename P::mag_t &m2, uint32_t &sx)
+{
+    if constexpr (std::is_same<P, F32>::value && UNIFORM && DC >= 2) {
+        float m1s;
+        two_smallest_signed<DC>(q, m1s, m2);
+        m1 = fabsf(m1s);
+        sx = __float_as_uint(m1s);
+    } else {
+        sx = 0;
+#pragma unroll
+        for (int j = 0; j < DC; ++j)
+            if (UNIFORM || j < deg) sx ^= P::sign_word(q[j]);
+        two_smallest<P, DC, UNIFORM>(q, deg, m1, m2);
+    }
+}
+
 // ---------------------------------------------------------------------------------------------
 // Check-node step (Alg. 1, CN processing) of one check, fused with the stop test of the previous
 // decisions.  Returns 1 iff the check's parity word says s_m is satisfied.
@@ -243,16 +297,12 @@ __device__ __forceinline__ int check_step(int c, int M, int deg, uint32_t pw, bo
     using mag_t = typename P::mag_t;
     if (update) {
         acc_t q[DC];
-        uint32_t sx = 0;
 #pragma unroll
-        for (int j = 0; j < DC; ++j) {
-            if (UNIFORM || j < deg) {
-                q[j] = load_msg<P>(slots, uint32_t(j * M + c));
-                sx ^= P::sign_word(q[j]);          // bit 31: parity of the signs
-            }
-        }
+        for (int j = 0; j < DC; ++j)
+            if (UNIFORM || j < deg) q[j] = load_msg<P>(slots, uint32_t(j * M + c));
         mag_t m1, m2;
-        two_smallest<P, DC, UNIFORM>(q, deg, m1, m2);
+        uint32_t sx;                               // bit 31: parity of the signs
+        row_minima<P, DC, UNIFORM>(q, deg, m1, m2, sx);
         const uint32_t negall = ((pw >> 1) ^ (sx >> 31)) & 1u;   // (-1)^{s_m} * prod of all signs
         if constexpr (LEARNED) {
             if (w) {

@@ -42,11 +42,10 @@ __device__ __forceinline__ void layered_check(int c, int M, int deg, uint32_t s_
             v[j] = __ldg(ecol + size_t(j) * M + c);
             qu[j] = P::sub(Q[v[j]], load_msg<P>(slots, uint32_t(j * M + c)));
             q[j] = P::clampq(qu[j]);
-            sx ^= P::sign_word(q[j]);
         }
     }
     mag_t m1, m2;
-    two_smallest<P, DC, UNIFORM>(q, deg, m1, m2);
+    row_minima<P, DC, UNIFORM>(q, deg, m1, m2, sx);
     const uint32_t negall = (s_bit ^ (sx >> 31)) & 1u;
     const mag_t r1 = P::presign(P::scale(m1, p), negall), r2 = P::presign(P::scale(m2, p), negall);
 #pragma unroll
@@ -263,11 +262,10 @@ __device__ __forceinline__ int layered_reg_shot(const LayeredOwned<DC, MAXL> &o,
                                 v[j] = (o.ev[l][j / 2] >> (16 * (j & 1))) & 0xffffu;
                                 qu[j] = P::sub(Q[v[j]], r[l][j]);
                                 q[j] = P::clampq(qu[j]);
-                                sx ^= P::sign_word(q[j]);
                             }
                         }
                         mag_t m1, m2;
-                        two_smallest<P, D, UNIFORM>(q, o.mdeg[l], m1, m2);
+                        row_minima<P, D, UNIFORM>(q, o.mdeg[l], m1, m2, sx);
                         const uint32_t negall = (((sbits >> l) & 1u) ^ (sx >> 31)) & 1u;
                         const mag_t r1 = P::presign(P::scale(m1, p), negall);
                         const mag_t r2 = P::presign(P::scale(m2, p), negall);

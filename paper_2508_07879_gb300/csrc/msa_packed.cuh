@@ -227,70 +227,24 @@ __device__ __forceinline__ float2 add2_rn(float2 a, float2 b)
     return o;
 }
 
-// min(|a|, |b|) carrying the sign sign(a) xor sign(b) (sm_86 and later)
-__device__ __forceinline__ float min_xorsign_abs(float a, float b)
-{
-    float d;
-    asm("min.xorsign.abs.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
-    return d;
-}
-
-// The two smallest magnitudes of a row of exactly DC messages, two at a time, with the parity of the
-// signs riding on the smallest: |m1s| = min |q|, sign bit of m1s = xor of every sign bit; m2 the
-// second smallest magnitude (with multiplicity).  The same pairs of minima and maxima as
-// two_smallest, so the same values.
-template <int DC>
-__device__ __forceinline__ void two_smallest_signed(const float *q, float &m1s, float &m2)
-{
-    constexpr int j0 = DC % 2 == 0 ? 2 : 1;
-    if constexpr (DC % 2 == 0) {
-        m1s = min_xorsign_abs(q[0], q[1]);
-        m2 = fmaxf(fabsf(q[0]), fabsf(q[1]));
-    } else {
-        m1s = q[0];
-        m2 = F32::mag_init();
-    }
-#pragma unroll
-    for (int j = j0; j < DC; j += 2) {
-        const float lo = min_xorsign_abs(q[j], q[j + 1]);
-        const float hi = fmaxf(fabsf(q[j]), fabsf(q[j + 1]));
-        m2 = F32::mn3(fmaxf(fabsf(m1s), fabsf(lo)), m2, hi);
-        m1s = min_xorsign_abs(m1s, lo);
-    }
-}
-
 template <int DC, bool UNIFORM>
 __device__ __forceinline__ void check_step_f32x2(int c, int M, int deg, uint32_t pw, float2 *__restrict__ slots,
                                                  float alpha)
 {
     using P = F32;
     float q0[DC], q1[DC];
-    uint32_t sx0 = 0, sx1 = 0;
 #pragma unroll
     for (int j = 0; j < DC; ++j) {
         if (UNIFORM || j < deg) {
             const float2 v = slots[j * M + c];
             q0[j] = v.x;
             q1[j] = v.y;
-            if constexpr (!(UNIFORM && DC >= 2)) {
-                sx0 ^= __float_as_uint(v.x);
-                sx1 ^= __float_as_uint(v.y);
-            }
         }
     }
     float a1, a2, b1, b2;
-    if constexpr (UNIFORM && DC >= 2) {   // sign parity taken with the smallest magnitude
-        float m1a, m1b;
-        two_smallest_signed<DC>(q0, m1a, a2);
-        two_smallest_signed<DC>(q1, m1b, b2);
-        a1 = fabsf(m1a);
-        b1 = fabsf(m1b);
-        sx0 = __float_as_uint(m1a);
-        sx1 = __float_as_uint(m1b);
-    } else {
-        two_smallest<P, DC, UNIFORM>(q0, deg, a1, a2);
-        two_smallest<P, DC, UNIFORM>(q1, deg, b1, b2);
-    }
+    uint32_t sx0, sx1;
+    row_minima<P, DC, UNIFORM>(q0, deg, a1, a2, sx0);
+    row_minima<P, DC, UNIFORM>(q1, deg, b1, b2, sx1);
     const uint32_t na = ((pw >> 15) ^ (sx0 >> 31)) & 1u, nb = ((pw >> 31) ^ (sx1 >> 31)) & 1u;
     const float ra1 = P::presign(__fmul_rn(alpha, a1), na), ra2 = P::presign(__fmul_rn(alpha, a2), na);
     const float rb1 = P::presign(__fmul_rn(alpha, b1), nb), rb2 = P::presign(__fmul_rn(alpha, b2), nb);

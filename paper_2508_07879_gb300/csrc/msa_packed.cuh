@@ -23,6 +23,8 @@
 
 #include <type_traits>
 
+#include <cuda_fp16.h>
+
 #include "msa_kernel.cuh"
 
 namespace qldpc {
@@ -306,8 +308,10 @@ struct Pair16 {
     using pair_t = int2;
     static __device__ __forceinline__ gam_t quantize(float g) { return P::quantize(g); }
     static __device__ __forceinline__ pair_t both(gam_t g) { return make_int2(g, g); }
+    static __device__ __forceinline__ gam_t lane(pair_t x, int l) { return l ? x.y : x.x; }
     static __device__ __forceinline__ bool neg(gam_t x) { return x < 0; }
     static __device__ __forceinline__ float post(gam_t x) { return P::post(x); }
+    static __device__ __forceinline__ void setup(int, int, const LaunchParams &) {}
     template <int DC, bool UNIFORM>
     static __device__ __forceinline__ void check(int c, int M, int deg, uint32_t pw, word_t *slots, const LaunchParams &p)
     {
@@ -328,8 +332,10 @@ struct PairF32 {     // two FP32 lanes per 8-byte slot
     using pair_t = float2;
     static __device__ __forceinline__ gam_t quantize(float g) { return F32::quantize(g); }
     static __device__ __forceinline__ pair_t both(gam_t g) { return make_float2(g, g); }
+    static __device__ __forceinline__ gam_t lane(pair_t x, int l) { return l ? x.y : x.x; }
     static __device__ __forceinline__ bool neg(gam_t x) { return x < 0.0f; }
     static __device__ __forceinline__ float post(gam_t x) { return x; }
+    static __device__ __forceinline__ void setup(int, int, const LaunchParams &) {}
     template <int DC, bool UNIFORM>
     static __device__ __forceinline__ void check(int c, int M, int deg, uint32_t pw, word_t *slots, const LaunchParams &p)
     {
@@ -340,6 +346,180 @@ struct PairF32 {     // two FP32 lanes per 8-byte slot
                                                  pair_t Qold, uint32_t act, word_t *slots, uint32_t *parity)
     {
         return var_step_f32x2<D, MASK>(u, NV, ck, vslot, gamma, Qold, act, slots, parity);
+    }
+};
+
+// ---------------------------------------------------------------------------------------------
+// INT8 messages in half-precision lanes: the same integers as I8 (quarter-LLR units), each lane an
+// FP16 number.  Every value the decoder forms is an integer of magnitude at most 127 (a message) or
+// 127 (1 + d_v) (a sum over a variable: 1143 for column degrees up to 8), and FP16 represents every
+// integer up to 2048 exactly, so each FP16 addition, minimum and comparison below is the exact
+// integer operation of I8 and the results are bit-identical to it.  The paired FP16 instructions
+// give what the 16-bit integer lanes lack: |x| as part of the minimum (min.xorsign.abs, which also
+// carries the product of the signs on the smallest magnitude), a lane-wise equality mask (set.eq) and
+// lane-wise additions.  Zero: a message is never -0 (every sum starts from the prior, +0 or a nonzero
+// integer, and a rounded sum is -0 only when every term is), so a lane's sign bit is [x < 0]; an
+// output r = -0 (a zero magnitude with a negative sign) only ever enters such sums.
+// The scale |r| = floor(min * alpha_q / 2^15) comes from a 128-entry table per block (exact integers).
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t h2_minxs(uint32_t a, uint32_t b)
+{
+    uint32_t d;
+    asm("min.xorsign.abs.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+__device__ __forceinline__ uint32_t h2_maxxs(uint32_t a, uint32_t b)
+{
+    uint32_t d;
+    asm("max.xorsign.abs.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+__device__ __forceinline__ uint32_t h2_min(uint32_t a, uint32_t b)
+{
+    uint32_t d;
+    asm("min.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+__device__ __forceinline__ uint32_t h2_max(uint32_t a, uint32_t b)
+{
+    uint32_t d;
+    asm("max.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+__device__ __forceinline__ uint32_t h2_add(uint32_t a, uint32_t b)
+{
+    uint32_t d;
+    asm("add.rn.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+// 0xffff in each lane where a == b, else 0
+__device__ __forceinline__ uint32_t h2_eq_mask(uint32_t a, uint32_t b)
+{
+    uint32_t d;
+    asm("set.eq.u32.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+// The magnitudes (signs ignored) of the minimum and maximum, for min2_tree; mn keeps the xor of the
+// signs, so the smallest of a tree carries the parity of all its leaves' signs.
+struct H2XsOps {
+    static __device__ __forceinline__ uint32_t mn(uint32_t a, uint32_t b) { return h2_minxs(a, b); }
+    static __device__ __forceinline__ uint32_t mx(uint32_t a, uint32_t b) { return h2_maxxs(a, b); }
+    static __device__ __forceinline__ uint32_t mn3(uint32_t a, uint32_t b, uint32_t c) { return h2_minxs(h2_minxs(a, b), c); }
+};
+constexpr uint32_t kH2Sign = 0x80008000u, kH2Mag = 0x7fff7fffu;
+constexpr uint32_t kH2Lim = 0x57f057f0u;    // +127.0 in both lanes
+constexpr uint32_t kH2NegLim = 0xd7f0d7f0u; // -127.0
+constexpr uint32_t kH2K1024 = 0x64006400u;  // +1024.0: adding it leaves an integer m < 1024 in the mantissa
+
+template <int DC, bool UNIFORM>
+__device__ __forceinline__ void check_step_h8(int c, int M, int deg, uint32_t pw, uint32_t *__restrict__ slots,
+                                              const uint16_t *__restrict__ tab)
+{
+    uint32_t q[DC];
+#pragma unroll
+    for (int j = 0; j < DC; ++j)
+        if (UNIFORM || j < deg) q[j] = slots[j * M + c];
+    // two smallest magnitudes per lane (m2's sign is meaningless); m1's sign bits: the sign parity
+    uint32_t m1, m2;
+    if constexpr (UNIFORM && DC >= 2) {
+        min2_tree<H2XsOps, 0, DC>(q, m1, m2);
+    } else {
+        m1 = m2 = 0x7c007c00u;   // +inf
+#pragma unroll
+        for (int j = 0; j < DC; ++j) {
+            if (UNIFORM || j < deg) {
+                m2 = h2_minxs(m2, h2_maxxs(m1, q[j]));
+                m1 = h2_minxs(m1, q[j]);
+            }
+        }
+    }
+    const uint32_t negb = (m1 ^ pw) & kH2Sign;   // per lane (-1)^{s_m} prod of the signs (pw bits 15 / 31: s_m)
+    const uint32_t a1 = m1 & kH2Mag, a2 = m2 & kH2Mag;
+    // |r| = floor(|m| alpha_q / 2^15) from the table, both lanes: 1024 + |m| puts |m| in the low bits
+    const uint32_t t1 = h2_add(a1, kH2K1024), t2 = h2_add(a2, kH2K1024);
+    const uint32_t r1 = (uint32_t(tab[t1 & 0x7fu]) | (uint32_t(tab[(t1 >> 16) & 0x7fu]) << 16)) ^ negb;
+    const uint32_t r2 = (uint32_t(tab[t2 & 0x7fu]) | (uint32_t(tab[(t2 >> 16) & 0x7fu]) << 16)) ^ negb;
+#pragma unroll
+    for (int j = 0; j < DC; ++j) {
+        if (UNIFORM || j < deg) {
+            const uint32_t at = h2_eq_mask(q[j] & kH2Mag, a1);   // the lane's |q| is the minimum: r2
+            slots[j * M + c] = ((at & r2) | (~at & r1)) ^ (q[j] & kH2Sign);
+        }
+    }
+}
+
+template <int D, bool MASK>
+__device__ __forceinline__ uint32_t var_step_h8(int u, int NV, const CheckOf &ck, const uint16_t *__restrict__ vslot,
+                                                uint32_t gamma, uint32_t Qold, uint32_t keep, uint32_t *__restrict__ slots,
+                                                uint32_t *__restrict__ parity)
+{
+    if constexpr (D == 0) {
+        return gamma;
+    } else {
+        uint32_t e[D], r[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) e[k] = __ldg(vslot + k * NV + u);
+#pragma unroll
+        for (int k = 0; k < D; ++k) r[k] = MASK ? slots[e[k]] & keep : slots[e[k]];   // restart: r = +0
+        uint32_t pre[D + 1];
+        pre[0] = gamma;
+#pragma unroll
+        for (int k = 0; k < D; ++k) pre[k + 1] = h2_add(pre[k], r[k]);
+        const uint32_t Q = pre[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            uint32_t q = pre[k];
+#pragma unroll
+            for (int i = k + 1; i < D; ++i) q = h2_add(q, r[i]);
+            slots[e[k]] = h2_max(h2_min(q, kH2Lim), kH2NegLim);
+        }
+        const uint32_t flip = ((Q ^ Qold) >> 15) & 0x00010001u;   // lane decisions that changed (bits 0 / 16)
+        if (flip) {
+#pragma unroll
+            for (int k = 0; k < D; ++k) atomicXor(parity + ck(e[k]), flip);
+        }
+        return Q;
+    }
+}
+
+struct PairH8 {      // two INT8 messages in half-precision lanes per 32-bit slot
+    using word_t = uint32_t;
+    using gam_t = uint32_t;   // FP16 bits: the prior in both lanes (quantize), or one lane's value (lane)
+    using pair_t = uint32_t;
+    static __device__ __forceinline__ gam_t quantize(float g)
+    {
+        const uint32_t h = __half_as_ushort(__int2half_rn(I8::quantize(g)));   // an integer in [-127, 127]: exact
+        return h | (h << 16);
+    }
+    static __device__ __forceinline__ pair_t both(gam_t g) { return g; }
+    static __device__ __forceinline__ gam_t lane(pair_t x, int l) { return l ? x >> 16 : x & 0xffffu; }
+    static __device__ __forceinline__ bool neg(gam_t x) { return (x & 0x8000u) != 0u; }
+    static __device__ __forceinline__ float post(gam_t x)
+    {
+        return __half2float(__ushort_as_half(uint16_t(x))) * 0.25f;   // the I8 value / 4, exact
+    }
+    static __device__ __forceinline__ uint16_t *table()
+    {
+        __shared__ uint16_t t[128];
+        return t;
+    }
+    // the scale table: FP16 bits of floor(m alpha_q / 2^15), m = 0..127
+    static __device__ __forceinline__ void setup(int tid, int T, const LaunchParams &p)
+    {
+        for (int m = tid; m < 128; m += T)
+            table()[m] = __half_as_ushort(__int2half_rn(int((uint32_t(m) * uint32_t(p.alpha_q)) >> 15)));
+    }
+    template <int DC, bool UNIFORM>
+    static __device__ __forceinline__ void check(int c, int M, int deg, uint32_t pw, word_t *slots, const LaunchParams &)
+    {
+        check_step_h8<DC, UNIFORM>(c, M, deg, pw, slots, table());
+    }
+    template <int D, bool MASK>
+    static __device__ __forceinline__ pair_t var(int u, int NV, const CheckOf &ck, const uint16_t *vslot, gam_t gamma,
+                                                 pair_t Qold, uint32_t act, word_t *slots, uint32_t *parity)
+    {
+        const uint32_t keep = ((act & 1u) ? 0x0000ffffu : 0u) | ((act & 2u) ? 0xffff0000u : 0u);
+        return var_step_h8<D, MASK>(u, NV, ck, vslot, gamma, Qold, keep, slots, parity);
     }
 };
 
@@ -372,6 +552,7 @@ __global__ void __launch_bounds__(kPackedMaxThreads, 1) msa_packed_kernel(const 
     }
     for (int c = tid; c < M; c += T) parity[c] = 0u;
     if (tid < 2) s_any[tid] = 0u;
+    PP::setup(tid, T, p);
     bad = __syncthreads_or(bad);
     if (bad) {   // non-finite prior: every shot of the launch is reported as not decoded
         for (;;) {
@@ -432,7 +613,7 @@ __global__ void __launch_bounds__(kPackedMaxThreads, 1) msa_packed_kernel(const 
 #pragma unroll
                 for (int l = 0; l < 2; ++l) {
                     if (out & (1u << l)) {
-                        const gam_t q = l ? Qo.y : Qo.x;
+                        const gam_t q = PP::lane(Qo, l);
                         store_out(pr.err + size_t(shot[l]) * N + v, uint8_t(PP::neg(q) ? 1 : 0));
                         if (pr.post) store_out(pr.post + size_t(shot[l]) * N + v, PP::post(q));
                     }
@@ -551,26 +732,29 @@ __global__ void __launch_bounds__(kPackedMaxThreads, 1) msa_packed_kernel(const 
 
 // Instantiation tables of the packed kernel for one fixed-point policy (same variants as the other
 // flooding kernels).
-template <class PP>
+// DVLO..DVHI: the column-degree buckets instantiated for this policy (the others return nothing).
+template <class PP, int DVLO = 0, int DVHI = 16>
 const void *packed_table(const KernelChoice &kc)
 {
 #define QLDPC_K(DCV, UNI, DVV)                                                                  \
-    if (kc.dc == DCV && kc.uniform == UNI && kc.dvb == DVV)                                     \
-        return reinterpret_cast<const void *>(&kern::msa_packed_kernel<PP, DCV, UNI, DVV>);
+    if constexpr (DVV >= DVLO && DVV <= DVHI)                                                   \
+        if (kc.dc == DCV && kc.uniform == UNI && kc.dvb == DVV)                                 \
+            return reinterpret_cast<const void *>(&kern::msa_packed_kernel<PP, DCV, UNI, DVV>);
     QLDPC_VARIANTS(QLDPC_K)
 #undef QLDPC_K
     return nullptr;
 }
 
-template <class PP>
+template <class PP, int DVLO = 0, int DVHI = 16>
 cudaError_t packed_launch(const LaunchParams &p, const KernelChoice &kc, dim3 grid, int threads, size_t smem,
                           cudaStream_t stream)
 {
 #define QLDPC_L(DCV, UNI, DVV)                                                                  \
-    if (kc.dc == DCV && kc.uniform == UNI && kc.dvb == DVV) {                                   \
-        kern::msa_packed_kernel<PP, DCV, UNI, DVV><<<grid, threads, smem, stream>>>(p);         \
-        return cudaGetLastError();                                                              \
-    }
+    if constexpr (DVV >= DVLO && DVV <= DVHI)                                                   \
+        if (kc.dc == DCV && kc.uniform == UNI && kc.dvb == DVV) {                               \
+            kern::msa_packed_kernel<PP, DCV, UNI, DVV><<<grid, threads, smem, stream>>>(p);     \
+            return cudaGetLastError();                                                          \
+        }
     QLDPC_VARIANTS(QLDPC_L)
 #undef QLDPC_L
     return cudaErrorInvalidValue;

@@ -79,3 +79,27 @@ def test_int8_pair_equals_single_decodes(q):
     ra = q.decode(gz, sx, pr, 64, precision="int8")
     rb = q.decode(gx, sz, pr, 64, precision="int8")
     assert torch.equal(a, ra[0]) and torch.equal(ia, ra[1]) and torch.equal(b, rb[0]) and torch.equal(ib, rb[1])
+
+
+@pytest.mark.parametrize("dv", [8, 12])
+def test_int8_pairs_at_large_column_degree(q, dv):
+    """The two-shots-per-block INT8 kernel where its sums are largest: every column of degree dv and
+    priors that saturate to 127, so a variable's sum reaches 127 (1 + dv).  Column degree 8 is the
+    largest the half-precision lanes take (|sum| <= 1143, every integer exact in FP16); 12 runs the
+    16-bit integer lanes."""
+    rng = np.random.default_rng(70 + dv)
+    m, n = 96, 128
+    hd = np.zeros((m, n), dtype=np.uint8)
+    for v in range(n):
+        hd[rng.choice(m, dv, replace=False), v] = 1
+    keep = hd.sum(axis=1) >= 2
+    from helpers import csr
+    h = csr(hd[keep])
+    assert h.col_degrees().max() == dv
+    e = (rng.random((301, n)) < 0.08).astype(np.uint8)
+    s = w.syndromes(h, e)
+    for prior in (np.full(n, 40.0, dtype=np.float32), rng.uniform(-45.0, 45.0, n).astype(np.float32)):
+        ref = check(q, h, s, prior, 25, kernel="packed")
+        if prior.min() > 0:   # saturated prior 127 plus dv messages of floor(127 * 0.75) = 95
+            assert np.abs(ref["post"]).max() >= 127 + (dv - 1) * 95
+        check(q, h, s, prior, 8, kernel="packed", early_stop=False)

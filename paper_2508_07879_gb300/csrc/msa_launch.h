@@ -17,8 +17,8 @@ namespace qldpc {
 // grouped by descending degree and packed so that the k-th slots of a warp's 32 variables fall in
 // distinct shared-memory banks where possible, with idle lanes (vperm = n) closing a warp early.
 // Lane u holds the caller's variable vperm[u]; the k-th edge of lane u (ascending check order) is
-// the slot vslot[k*nv + u] = j*m + i, and i = slot mod m (m_magic, m_shift) when a decision
-// flips.  An idle lane has its warp's degree and every edge on a scratch slot dc_max*m + b
+// the slot vslot[k*nv + u] = j*m + i, and i = slot mod m (m_magic, m_shift; the two-shots-per-block
+// kernel reads it from vchk16) when a decision flips.  An idle lane has its warp's degree and every edge on a scratch slot dc_max*m + b
 // (b < kScratch) in a bank its warp leaves free, so it runs its warp's path without divergence;
 // its prior is 0 and its scratch slots hold 0, so its decision never flips.
 constexpr int kMaxDegClasses = QLDPC_MAX_COL_DEGREE + 1;   // column degrees 0..16
@@ -45,6 +45,7 @@ struct DeviceGraph {
     // time instead of reading vdeg per lane.
     const uint16_t *vslot16;
     const uint32_t *vlane;   // [n] lane of each variable (the inverse of vperm on the real lanes)
+    const uint16_t *vchk16;  // [dv_max * nv] the check of each vslot16 entry (slot mod m), with vslot16
     int32_t ncls;
     int32_t cls_end[kMaxDegClasses];
     int32_t cls_deg[kMaxDegClasses];

@@ -182,7 +182,7 @@ __device__ __forceinline__ void check_step_x2(int c, int M, int deg, uint32_t pw
 // ---------------------------------------------------------------------------------------------
 // MASK = false: both lanes update (keep = all ones), the messages are used as loaded.
 template <class P, int D, bool MASK>
-__device__ __forceinline__ int2 var_step_x2(int u, int NV, const CheckOf &ck, const uint16_t *__restrict__ vslot,
+__device__ __forceinline__ int2 var_step_x2(int u, int NV, const uint16_t *__restrict__ vchk, const uint16_t *__restrict__ vslot,
                                             int32_t gamma, int2 Qold, uint32_t keep, uint32_t *__restrict__ slots,
                                             uint32_t *__restrict__ parity)
 {
@@ -205,7 +205,7 @@ __device__ __forceinline__ int2 var_step_x2(int u, int NV, const CheckOf &ck, co
         const uint32_t flip = (uint32_t(Q0 ^ Qold.x) >> 31) | ((uint32_t(Q1 ^ Qold.y) >> 31) << 16);
         if (flip) {
 #pragma unroll
-            for (int k = 0; k < D; ++k) atomicXor(parity + ck(e[k]), flip);
+            for (int k = 0; k < D; ++k) atomicXor(parity + __ldg(vchk + k * NV + u), flip);
         }
         return make_int2(Q0, Q1);
     }
@@ -318,11 +318,13 @@ struct Pair16 {
         check_step_x2<P, DC, UNIFORM>(c, M, deg, pw, slots, p.alpha_q);
     }
     template <int D, bool MASK>
-    static __device__ __forceinline__ pair_t var(int u, int NV, const CheckOf &ck, const uint16_t *vslot, gam_t gamma,
+    static __device__ __forceinline__ pair_t var(int u, int NV, const CheckOf &ck, const uint16_t *vchk, const uint16_t *vslot,
+                                                 gam_t gamma,
                                                  pair_t Qold, uint32_t act, word_t *slots, uint32_t *parity)
     {
         const uint32_t keep = ((act & 1u) ? 0x0000ffffu : 0u) | ((act & 2u) ? 0xffff0000u : 0u);
-        return var_step_x2<P, D, MASK>(u, NV, ck, vslot, gamma, Qold, keep, slots, parity);
+        (void)ck;
+        return var_step_x2<P, D, MASK>(u, NV, vchk, vslot, gamma, Qold, keep, slots, parity);
     }
 };
 
@@ -342,9 +344,11 @@ struct PairF32 {     // two FP32 lanes per 8-byte slot
         check_step_f32x2<DC, UNIFORM>(c, M, deg, pw, slots, p.alpha);
     }
     template <int D, bool MASK>
-    static __device__ __forceinline__ pair_t var(int u, int NV, const CheckOf &ck, const uint16_t *vslot, gam_t gamma,
+    static __device__ __forceinline__ pair_t var(int u, int NV, const CheckOf &ck, const uint16_t *vchk, const uint16_t *vslot,
+                                                 gam_t gamma,
                                                  pair_t Qold, uint32_t act, word_t *slots, uint32_t *parity)
     {
+        (void)vchk;   // FP32 pairs decode the check from the slot: a second 16-bit list costs them L1 room
         return var_step_f32x2<D, MASK>(u, NV, ck, vslot, gamma, Qold, act, slots, parity);
     }
 };
@@ -449,7 +453,7 @@ __device__ __forceinline__ void check_step_h8(int c, int M, int deg, uint32_t pw
 }
 
 template <int D, bool MASK>
-__device__ __forceinline__ uint32_t var_step_h8(int u, int NV, const CheckOf &ck, const uint16_t *__restrict__ vslot,
+__device__ __forceinline__ uint32_t var_step_h8(int u, int NV, const uint16_t *__restrict__ vchk, const uint16_t *__restrict__ vslot,
                                                 uint32_t gamma, uint32_t Qold, uint32_t keep, uint32_t *__restrict__ slots,
                                                 uint32_t *__restrict__ parity)
 {
@@ -476,7 +480,7 @@ __device__ __forceinline__ uint32_t var_step_h8(int u, int NV, const CheckOf &ck
         const uint32_t flip = ((Q ^ Qold) >> 15) & 0x00010001u;   // lane decisions that changed (bits 0 / 16)
         if (flip) {
 #pragma unroll
-            for (int k = 0; k < D; ++k) atomicXor(parity + ck(e[k]), flip);
+            for (int k = 0; k < D; ++k) atomicXor(parity + __ldg(vchk + k * NV + u), flip);
         }
         return Q;
     }
@@ -515,11 +519,13 @@ struct PairH8 {      // two INT8 messages in half-precision lanes per 32-bit slo
         check_step_h8<DC, UNIFORM>(c, M, deg, pw, slots, table());
     }
     template <int D, bool MASK>
-    static __device__ __forceinline__ pair_t var(int u, int NV, const CheckOf &ck, const uint16_t *vslot, gam_t gamma,
+    static __device__ __forceinline__ pair_t var(int u, int NV, const CheckOf &ck, const uint16_t *vchk, const uint16_t *vslot,
+                                                 gam_t gamma,
                                                  pair_t Qold, uint32_t act, word_t *slots, uint32_t *parity)
     {
         const uint32_t keep = ((act & 1u) ? 0x0000ffffu : 0u) | ((act & 2u) ? 0xffff0000u : 0u);
-        return var_step_h8<D, MASK>(u, NV, ck, vslot, gamma, Qold, keep, slots, parity);
+        (void)ck;
+        return var_step_h8<D, MASK>(u, NV, vchk, vslot, gamma, Qold, keep, slots, parity);
     }
 };
 
@@ -633,7 +639,7 @@ __global__ void __launch_bounds__(kPackedMaxThreads, 1) msa_packed_kernel(const 
                     constexpr int D = decltype(deg_tag)::value;
 #pragma unroll 1
                     for (; u < u1; u += T)
-                        Qs[u] = PP::template var<D, MASK>(u, NV, ck, pr.g.vslot16, gam[u], Qs[u], act, slots, parity);
+                        Qs[u] = PP::template var<D, MASK>(u, NV, ck, pr.g.vchk16, pr.g.vslot16, gam[u], Qs[u], act, slots, parity);
                 };
                 switch (G.cls_deg[cl]) {
 #define QLDPC_CASE(DD)                                                                          \

@@ -280,6 +280,7 @@ struct HostLayout {
     int32_t max_layer = 0;
     int32_t nv = 0;               // variable lanes (n + idle lanes)
     std::vector<uint16_t> vslot16;// vslot as 16-bit indices (empty when a slot index exceeds 65535)
+    std::vector<uint16_t> vchk16; // the check i = slot mod m of each vslot16 entry (same layout)
     std::vector<int32_t> cls_end, cls_deg;   // runs of equal lane degree
     uint32_t m_magic = 0;         // slot / m = umulhi(slot, m_magic) >> m_shift
     int32_t m_shift = 0;
@@ -403,7 +404,11 @@ int validate_and_layout(const int32_t *row_ptr, const int32_t *col_idx, int32_t 
             out.ecol[sl] = uint32_t(col_idx[e]);
         }
     }
-    if (S + size_t(kScratch) <= 65536) out.vslot16.assign(out.vslot.begin(), out.vslot.end());
+    if (S + size_t(kScratch) <= 65536) {
+        out.vslot16.assign(out.vslot.begin(), out.vslot.end());
+        out.vchk16.resize(out.vslot.size());
+        for (size_t t = 0; t < out.vslot.size(); ++t) out.vchk16[t] = uint16_t(out.vslot[t] % uint32_t(m));
+    }
     for (size_t u = 0; u < nv; ++u) {
         if (out.cls_deg.empty() || out.cls_deg.back() != int32_t(out.vdeg[u])) {
             out.cls_end.push_back(int32_t(u));
@@ -913,18 +918,19 @@ int qldpc_graph_create(const int32_t *row_ptr, const int32_t *col_idx, int32_t m
     }
 
     // one device block: vslot | vdeg | rdeg | vperm | eslot | slot_edge | ecol | layer_ptr | layer_chk |
-    // shot counters | vslot16 | vlane
-    constexpr int kArrays = 12;
+    // shot counters | vslot16 | vlane | vchk16
+    constexpr int kArrays = 13;
     const size_t sizes[kArrays] = {hl.vslot.size() * sizeof(uint32_t), size_t(hl.nv), size_t(m),
                                    size_t(hl.nv) * sizeof(uint32_t), hl.eslot.size() * sizeof(uint32_t),
                                    hl.slot_edge.size() * sizeof(int32_t), hl.ecol.size() * sizeof(uint32_t),
                                    hl.layer_ptr.size() * sizeof(int32_t), hl.layer_chk.size() * sizeof(uint32_t),
                                    size_t(kShotCounterSlots) * 2 * sizeof(int32_t),
-                                   hl.vslot16.size() * sizeof(uint16_t), hl.vlane.size() * sizeof(uint32_t)};
+                                   hl.vslot16.size() * sizeof(uint16_t), hl.vlane.size() * sizeof(uint32_t),
+                                   hl.vchk16.size() * sizeof(uint16_t)};
     const void *srcs[kArrays] = {hl.vslot.data(), hl.vdeg.data(), hl.rdeg.data(), hl.vorder.data(),
                                  hl.eslot.data(), hl.slot_edge.data(), hl.ecol.data(),
                                  hl.layer_ptr.data(), hl.layer_chk.data(), nullptr, hl.vslot16.data(),
-                                 hl.vlane.data()};
+                                 hl.vlane.data(), hl.vchk16.data()};
     size_t offs[kArrays], total = 0;
     for (int i = 0; i < kArrays; ++i) {
         offs[i] = total;
@@ -965,6 +971,7 @@ int qldpc_graph_create(const int32_t *row_ptr, const int32_t *col_idx, int32_t m
     g->dg.dv_max = hl.dv_max;
     g->dg.vslot16 = hl.vslot16.empty() ? nullptr : reinterpret_cast<const uint16_t *>(b + offs[10]);
     g->dg.vlane = reinterpret_cast<const uint32_t *>(b + offs[11]);
+    g->dg.vchk16 = hl.vchk16.empty() ? nullptr : reinterpret_cast<const uint16_t *>(b + offs[12]);
     g->dg.ncls = int32_t(hl.cls_end.size());
     for (size_t c = 0; c < hl.cls_end.size(); ++c) {
         g->dg.cls_end[c] = hl.cls_end[c];

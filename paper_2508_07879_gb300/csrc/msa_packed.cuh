@@ -1,14 +1,16 @@
-// Two fixed-point shots per message word: the throughput kernel of the INT16 and INT8 modes.
+// Two shots per block, their messages paired in one slot per edge: the throughput kernel of every
+// precision.
 //
-// Algorithm 1 (Sec. 2 of arXiv 2508.07879) with the integer arithmetic of the IFix policies of
-// msa_kernel.cuh, but every shared-memory slot holds the same edge's message of two shots, lane 0
-// in bits 0..15 and lane 1 in bits 16..31 (16-bit two's complement; INT8 messages are held in
-// 16-bit lanes too, within +-127).  One block decodes two shots at a time:
-//   * check step: one thread per check handles both shots with paired-lane instructions (min/max
-//     of s16x2 / u16x2, lane-wise add, byte permutes), one load and one store per edge for both;
-//   * variable step: one thread per variable loads each slot word once for both shots, sums each
-//     lane in 32 bits exactly (Q_n = gamma_n + sum r, q = clamp(Q_n - r)) and packs the pair back;
-//     the edge list, degree and prior are read once for both shots;
+// Algorithm 1 (Sec. 2 of arXiv 2508.07879) with the arithmetic of the precision policies of
+// msa_kernel.cuh, but every shared-memory slot holds the same edge's message of two shots: lane 0
+// and lane 1 of a float2 (FP32), of a 32-bit word of two 16-bit two's-complement lanes (INT16, and
+// INT8 above column degree 8, within +-127), or of a half2 (INT8 up to column degree 8: the integers
+// as FP16 numbers, exact).  One block decodes two shots at a time:
+//   * check step: one thread per check handles both shots, one load and one store per edge for both
+//     (paired-lane instructions in the 16-bit forms: min/max, lane-wise add, byte permutes);
+//   * variable step: one thread per variable loads each slot once for both shots, forms each lane's
+//     sums exactly (Q_n = gamma_n + sum r, q = the literal sum over the other checks, clamped in the
+//     integer forms) and writes the pair back; the edge list, degree and prior are read once for both;
 //   * stop test: the parity word of a check carries both shots (bit 0: lane 0's s_m xor decisions,
 //     bit 15: lane 0's s_m, bit 16 and bit 31 the same for lane 1), so one block OR settles both.
 // Each lane stops at its own iteration (the scalar kernel's rule) and is refilled with the next

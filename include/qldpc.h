@@ -169,8 +169,10 @@ enum {
     QLDPC_KERNEL_LATENCY = 2,   /* single-shot kernel: per-thread state in registers, one block per
                                    shot; needs m <= 2*threads and n <= 2*threads, threads <= 640 */
     QLDPC_KERNEL_PACKED = 3     /* throughput kernel with two shots per block, their messages paired
-                                   in one slot per edge (two 16-bit lanes in INT16 / INT8, a float2 in
-                                   FP32); each shot stops at its own iteration */
+                                   in one slot per edge (a float2 in FP32, two 16-bit integer lanes in
+                                   INT16, two half-precision lanes holding the exact INT8 integers up
+                                   to column degree 8 and 16-bit integer lanes above it); each shot
+                                   stops at its own iteration */
 };
 
 /* Override the library's launch choice for this graph: the kernel, its threads per block (a

@@ -185,3 +185,32 @@ def test_packed_large_batch_sampled_against_oracle(q, precision):
     np.testing.assert_array_equal(ok[idx], ref["ok"])
     met = (w.syndromes(h, err) == b.syndromes).all(axis=1)
     assert (met[ok == 1]).all() and not met[ok == 0].any()
+
+
+def shifted_code(m, seed):
+    """A (4, 8)-regular parity-check matrix, m x 2m: check i meets variables (i + a_t) mod m for four
+    distinct seeded shifts a_t, and m + (i + b_t) mod m for four more."""
+    rng = np.random.default_rng(seed)
+    a, b = rng.choice(m, 4, replace=False), rng.choice(m, 4, replace=False)
+    dense = np.zeros((m, 2 * m), dtype=np.uint8)
+    i = np.arange(m)
+    for t in range(4):
+        dense[i, (i + a[t]) % m] = 1
+        dense[i, m + (i + b[t]) % m] = 1
+    return csr(dense)
+
+
+@pytest.mark.parametrize("m", [1100, 2100])
+def test_packed_large_graphs(q, m):
+    """The pair kernel on graphs far larger than the benchmark's: 1100 and 2100 checks of degree 8
+    (8800 and 16800 slots; two FP32 shots take 97 and 193 KB of shared memory), every precision,
+    against the oracle."""
+    h = shifted_code(m, seed=m)
+    g = q.Graph.from_csr(h)
+    rng = np.random.default_rng(m + 1)
+    e = (rng.random((97, h.n)) < 0.02).astype(np.uint8)
+    s = w.syndromes(h, e)
+    s[::9] = 0
+    prior = np.full(h.n, w.prior_llr(0.02), dtype=np.float32)
+    for precision in ("fp32", "int16", "int8"):
+        assert_oracle(run_packed(q, g, s, prior, 30, precision), h, s, prior, 30, precision)

@@ -20,15 +20,15 @@ def q():
     return qldpc
 
 
-def check(q, h, s, prior, max_iter, kernel="auto", layered=False, early_stop=True):
+def check(q, h, s, prior, max_iter, kernel="auto", layered=False, early_stop=True, alpha=0.75):
     g = q.Graph.from_csr(h)
     if kernel != "auto":
         g.set_launch(kernel)
     st = torch.from_numpy(np.ascontiguousarray(s, dtype=np.uint8)).cuda()
     pt = torch.from_numpy(np.ascontiguousarray(prior, dtype=np.float32)).cuda()
-    err, iters, ok, post = q.decode(g, st, pt, max_iter, 0.75, "int8", early_stop, want_post=True, layered=layered)
+    err, iters, ok, post = q.decode(g, st, pt, max_iter, alpha, "int8", early_stop, want_post=True, layered=layered)
     torch.cuda.synchronize()
-    ref = oracle.msa(h.row_ptr, h.col_idx, h.m, h.n, s, prior, max_iter, 0.75, "i8", early_stop, threads=16,
+    ref = oracle.msa(h.row_ptr, h.col_idx, h.m, h.n, s, prior, max_iter, alpha, "i8", early_stop, threads=16,
                      schedule="layered" if layered else "flooding")
     np.testing.assert_array_equal(err.cpu().numpy(), ref["err"])
     np.testing.assert_array_equal(iters.cpu().numpy(), ref["iters"])
@@ -103,3 +103,7 @@ def test_int8_pairs_at_large_column_degree(q, dv):
         if prior.min() > 0:   # saturated prior 127 plus dv messages of floor(127 * 0.75) = 95
             assert np.abs(ref["post"]).max() >= 127 + (dv - 1) * 95
         check(q, h, s, prior, 8, kernel="packed", early_stop=False)
+        # alpha = 1: messages reach 127 themselves, and a sum 127 (1 + dv) (1143 at column degree 8)
+        ref = check(q, h, s, prior, 12, kernel="packed", early_stop=False, alpha=1.0)
+        if prior.min() > 0:
+            assert np.abs(ref["post"]).max() >= 127 + (dv - 2) * 127

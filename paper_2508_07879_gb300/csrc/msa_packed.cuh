@@ -249,9 +249,12 @@ __device__ __forceinline__ void check_step_f32x2(int c, int M, int deg, uint32_t
     uint32_t sx0, sx1;
     row_minima<P, DC, UNIFORM>(q0, deg, a1, a2, sx0);
     row_minima<P, DC, UNIFORM>(q1, deg, b1, b2, sx1);
-    const uint32_t na = ((pw >> 15) ^ (sx0 >> 31)) & 1u, nb = ((pw >> 31) ^ (sx1 >> 31)) & 1u;
-    const float ra1 = P::presign(__fmul_rn(alpha, a1), na), ra2 = P::presign(__fmul_rn(alpha, a2), na);
-    const float rb1 = P::presign(__fmul_rn(alpha, b1), nb), rb2 = P::presign(__fmul_rn(alpha, b2), nb);
+    // the check's factor (-1)^{s_m} prod of the signs as a sign bit per lane (pw bit 15 / 31: s_m)
+    const uint32_t na = (sx0 ^ (pw << 16)) & 0x80000000u, nb = (sx1 ^ pw) & 0x80000000u;
+    const float ra1 = __uint_as_float(__float_as_uint(__fmul_rn(alpha, a1)) ^ na);
+    const float ra2 = __uint_as_float(__float_as_uint(__fmul_rn(alpha, a2)) ^ na);
+    const float rb1 = __uint_as_float(__float_as_uint(__fmul_rn(alpha, b1)) ^ nb);
+    const float rb2 = __uint_as_float(__float_as_uint(__fmul_rn(alpha, b2)) ^ nb);
 #pragma unroll
     for (int j = 0; j < DC; ++j) {
         if (UNIFORM || j < deg)
@@ -291,7 +294,10 @@ __device__ __forceinline__ float2 var_step_f32x2(int u, int NV, const CheckOf &c
             for (int i = k + 1; i < D; ++i) q = add2_rn(q, r[i]);
             slots[e[k]] = q;
         }
-        const uint32_t flip = uint32_t((Q.x < 0.0f) != (Qold.x < 0.0f)) | (uint32_t((Q.y < 0.0f) != (Qold.y < 0.0f)) << 16);
+        // the lanes whose decision [Q < 0] changed: the sign bits differ (no Q is -0, and the only NaN
+        // the arithmetic can form, inf - inf, is the positive canonical one)
+        const uint32_t flip = ((__float_as_uint(Q.x) ^ __float_as_uint(Qold.x)) >> 31) |
+                              (((__float_as_uint(Q.y) ^ __float_as_uint(Qold.y)) >> 15) & 0x00010000u);
         if (flip) {
 #pragma unroll
             for (int k = 0; k < D; ++k) atomicXor(parity + ck(e[k]), flip);

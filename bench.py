@@ -84,8 +84,8 @@ SMEM_BYTES_PER_CLK_PER_SM = 128  # 32 banks x 4 B
 # the kernel source they were taken on (sha256 prefix of that file); null once that source changes.
 NCU_TRAFFIC = {"msa_batch_kernel": {"source": "msa_kernel.cuh", "source_sha16": "61e9fb1b9d8386fc",
                                     "bytes_per_launch": 39156923},
-               "msa_packed_kernel": {"source": "msa_packed.cuh", "source_sha16": "835cb18bc378c112",
-                                     "bytes_per_launch": 39629611}}
+               "msa_packed_kernel": {"source": "msa_packed.cuh", "source_sha16": "7e5f890b9cc2f38f",
+                                     "bytes_per_launch": 39615684}}
 
 FALLBACK_HBM_GBS = 6800.0     # the profiling recipe's fallback when MEASURED_PEAKS.json is absent
 WORKLOAD = "LP-1054 H_Z (465x1054, E=3720), iid X noise p=0.01..0.05, B=65536/step, max 50 it, alpha 0.75"

@@ -626,7 +626,7 @@ int plan_latency(const qldpc_graph *const *gs, int nprob, int32_t batch, int pre
 
 // Throughput path: two shots per block with their messages paired in one slot (every precision,
 // unless the graph's launch override asks for one shot per block, or the shot is learned), or one
-// shot per block.  Measured on LP-1054 at 65536 shots: FP32 31.5 M/s in pairs against 26.9, INT16
+// shot per block.  Measured on LP-1054 at 65536 shots: FP32 31.7 M/s in pairs against 26.9, INT16
 // 31.3 against 25.5, INT8 37.7 (half-precision lanes) against 26.3.
 int plan_batch(const qldpc_graph *const *gs, int nprob, int32_t batch, int precision, bool learned, Plan &pl)
 {
